@@ -1,0 +1,55 @@
+"""Test-side helpers: small random graphs and spanning-tree enumeration.
+
+Nothing here computes TIMEST quantities; it only builds inputs.
+"""
+import itertools
+
+import numpy as np
+
+
+def spanning_trees(nv, edges):
+    """All sets of nv-1 motif-edge indices forming a spanning tree of the
+    underlying undirected multigraph."""
+    out = []
+    for comb in itertools.combinations(range(len(edges)), nv - 1):
+        comp = list(range(nv))
+        ok = True
+        for e in comb:
+            a, b = edges[e]
+            ca, cb = comp[a], comp[b]
+            if ca == cb:
+                ok = False
+                break
+            comp = [ca if c == cb else c for c in comp]
+        if ok and len(set(comp)) == 1:
+            out.append(list(comb))
+    return out
+
+
+def small_random_graph(seed, n=7, m=70, t_hi=40, t0=1000):
+    """Dense small multigraph: unique (u,v,t), no self loops, many repeats."""
+    rng = np.random.default_rng(seed)
+    seen = set()
+    src, dst, t = [], [], []
+    while len(src) < m:
+        u = int(rng.integers(0, n)); v = int(rng.integers(0, n - 1)); v += v >= u
+        tt = int(rng.integers(0, t_hi))
+        if (u, v, tt) in seen:
+            continue
+        seen.add((u, v, tt))
+        src.append(u); dst.append(v); t.append(tt + t0)
+    return n, np.array(src, np.uint32), np.array(dst, np.uint32), np.array(t, np.int64)
+
+
+SMALL_MOTIFS = {
+    "triangle": (3, [(0, 1), (1, 2), (2, 0)], [0, 1, 2]),
+    "triangle_ff": (3, [(0, 1), (1, 2), (0, 2)], [0, 2, 1]),
+    "cycle4": (4, [(0, 1), (1, 2), (2, 3), (3, 0)], [0, 1, 2, 3]),
+    "cycle5_chord": (5, [(0, 1), (1, 2), (0, 2), (2, 3), (3, 4), (4, 0)], [0, 1, 2, 3, 4, 5]),
+    "out_star3": (4, [(0, 1), (0, 2), (0, 3)], [1, 0, 2]),
+    "in_star3": (4, [(1, 0), (2, 0), (3, 0)], [0, 1, 2]),
+    "path4_mixed": (4, [(0, 1), (2, 1), (2, 3)], [2, 0, 1]),
+    "bowtie": (5, [(0, 1), (1, 2), (2, 0), (2, 3), (3, 4), (4, 2)], [3, 0, 5, 1, 4, 2]),
+    "antiparallel": (3, [(0, 1), (1, 0), (1, 2)], [1, 0, 2]),
+    "parallel": (3, [(0, 1), (1, 2), (0, 1)], [0, 1, 2]),
+}

@@ -1,0 +1,317 @@
+"""Pins for the CPU oracle, checked against what the paper and mathematics fix
+rather than against the oracle itself:
+
+* hand-derived counts of the M-match definition (tests/golden, Def. 1.2);
+* two independent exact counters agree: chronological backtracking (O1) and
+  the sum of cnt/N_phi over every delta-partial match (O4; proof of the
+  unbiasedness lemma);
+* the weight DP's per-window totals equal a brute-force count of partial
+  matches (O2; Claims 3.2-3.4);
+* closed forms (single-edge motif; 2-path count by an independent numpy count);
+* Philox4x32-10 equals a library implementation (triton's, run on the CPU);
+* the sampler's output law P(phi) = N_phi / W (Lemma 3.5) by a chi-square test;
+* unbiasedness across 100 seeds (Lemma 3.6).
+"""
+import glob
+import math
+import os
+
+import numpy as np
+import pytest
+
+from conftest import read_golden
+from helpers import SMALL_MOTIFS, small_random_graph, spanning_trees
+
+GOLDEN = sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "*.txt")))
+
+
+def _graph_from_golden(orc, g):
+    src = [e[0] for e in g["edges"]]; dst = [e[1] for e in g["edges"]]; t = [e[2] for e in g["edges"]]
+    return orc.Graph(g["n"], src, dst, t)
+
+
+def _motif_from_golden(g):
+    edges = [(a, b) for a, b, _ in g["medges"]]
+    rank = [r for _, _, r in g["medges"]]
+    return g["nv"], edges, rank, g["delta"]
+
+
+@pytest.mark.parametrize("path", GOLDEN, ids=[os.path.basename(p) for p in GOLDEN])
+def test_golden_brute_force(oracle_mod, path):
+    g = read_golden(path)
+    G = _graph_from_golden(oracle_mod, g)
+    nv, edges, rank, delta = _motif_from_golden(g)
+    assert G.brute_count(nv, edges, rank, delta) == g["count"]
+
+
+@pytest.mark.parametrize("path", GOLDEN, ids=[os.path.basename(p) for p in GOLDEN])
+def test_golden_exact_by_every_tree(oracle_mod, path):
+    g = read_golden(path)
+    G = _graph_from_golden(oracle_mod, g)
+    nv, edges, rank, delta = _motif_from_golden(g)
+    for tree in spanning_trees(nv, edges):
+        for root in tree:
+            G.set_motif(nv, edges, rank, delta, tree, root)
+            assert G.exact_by_trees() == 2 * g["count"], (tree, root)
+
+
+@pytest.mark.parametrize("name", sorted(SMALL_MOTIFS))
+def test_brute_equals_tree_sum(oracle_mod, name):
+    """O1 == O4 for every spanning tree and root on random dense multigraphs."""
+    nv, edges, rank = SMALL_MOTIFS[name]
+    trees = spanning_trees(nv, edges)
+    for seed in range(3):
+        n, s, d, t = small_random_graph(seed, n=nv + 2, m=60 if nv <= 4 else 45, t_hi=40)
+        G = oracle_mod.Graph(n, s, d, t)
+        for delta in (5, 12):
+            C = G.brute_count(nv, edges, rank, delta)
+            for tree in trees[:6]:
+                for root in tree:
+                    G.set_motif(nv, edges, rank, delta, tree, root)
+                    assert G.exact_by_trees() == 2 * C, (seed, delta, tree, root)
+
+
+@pytest.mark.parametrize("name", ["triangle", "cycle4", "cycle5_chord", "out_star3", "path4_mixed", "bowtie"])
+def test_window_totals_equal_partial_match_count(oracle_mod, name):
+    """W_i from the weight DP == brute-force count of partial matches in window i."""
+    nv, edges, rank = SMALL_MOTIFS[name]
+    trees = spanning_trees(nv, edges)
+    for seed in range(2):
+        n, s, d, t = small_random_graph(100 + seed, n=nv + 2, m=50, t_hi=30)
+        G = oracle_mod.Graph(n, s, d, t)
+        for delta in (4, 9):
+            for tree in trees[:4]:
+                for root in tree:
+                    G.set_motif(nv, edges, rank, delta, tree, root)
+                    W = G.weights()
+                    Wi = G.window_totals()
+                    assert int(Wi.astype(object).sum()) == W
+                    for i in range(len(Wi)):
+                        assert G.partial_count(i) == int(Wi[i]), (seed, delta, tree, root, i)
+
+
+def test_single_edge_closed_form(oracle_mod):
+    """Single-edge motif: C = m; every edge with t' >= delta lies in two
+    windows, so W = 2m - |{t' < delta}|; every sample is valid, and the
+    estimate is m up to sampling error."""
+    n, s, d, t = small_random_graph(7, n=20, m=300, t_hi=500)
+    G = oracle_mod.Graph(n, s, d, t)
+    delta = 37
+    G.set_motif(2, [(0, 1)], [0], delta, [0], 0)
+    W = G.weights()
+    tp = t - t.min()
+    assert W == 2 * len(t) - int((tp < delta).sum())
+    assert G.brute_count(2, [(0, 1)], [0], delta) == len(t)
+    for seed in range(5):
+        r = G.sample(1000, seed)
+        assert r.valid == 1000
+        assert abs(r.estimate - len(t)) / len(t) < 0.2
+
+
+def test_two_path_independent_count(oracle_mod):
+    """2-path a->b, b->c (t1 < t2 <= t1 + delta, c != a): counted here
+    directly from the edge arrays, compared with O1 and O4."""
+    n, s, d, t = small_random_graph(11, n=9, m=120, t_hi=60)
+    delta = 7
+    C = 0
+    for i in range(len(s)):
+        for j in range(len(s)):
+            if d[i] == s[j] and d[j] != s[i] and t[i] < t[j] <= t[i] + delta:
+                C += 1
+    G = oracle_mod.Graph(n, s, d, t)
+    edges, rank = [(0, 1), (1, 2)], [0, 1]
+    assert G.brute_count(3, edges, rank, delta) == C
+    for root in (0, 1):
+        G.set_motif(3, edges, rank, delta, [0, 1], root)
+        assert G.exact_by_trees() == 2 * C
+
+
+def test_philox_matches_library():
+    """Philox4x32-10 equals triton's implementation (Salmon et al. SC'11),
+    executed by triton's CPU interpreter."""
+    triton = pytest.importorskip("triton")
+    import subprocess, sys, json
+    code = r'''
+import os, json
+os.environ["TRITON_INTERPRET"] = "1"
+import numpy as np, torch, triton, triton.language as tl
+@triton.jit
+def k(out_ptr, c0_ptr, c1_ptr, c2_ptr, c3_ptr, seed, N: tl.constexpr):
+    off = tl.arange(0, N)
+    a, b, c, d = tl.philox(seed, tl.load(c0_ptr + off), tl.load(c1_ptr + off), tl.load(c2_ptr + off), tl.load(c3_ptr + off))
+    tl.store(out_ptr + off * 4 + 0, a); tl.store(out_ptr + off * 4 + 1, b)
+    tl.store(out_ptr + off * 4 + 2, c); tl.store(out_ptr + off * 4 + 3, d)
+N = 64
+rng = np.random.default_rng(5)
+res = []
+for seed in (0, 1, 0x1234567890ABCDEF, 2**64 - 1):
+    cs = [torch.from_numpy(rng.integers(0, 2**32, N, dtype=np.uint64).astype(np.uint32).view(np.int32)) for _ in range(4)]
+    out = torch.zeros(N * 4, dtype=torch.int32)
+    k[(1,)](out, cs[0], cs[1], cs[2], cs[3], seed if seed < 2**63 else seed - 2**64, N=N)
+    res.append(dict(seed=seed, ctr=[c.numpy().view(np.uint32).tolist() for c in cs], out=out.numpy().view(np.uint32).tolist()))
+print(json.dumps(res))
+'''
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    if p.returncode != 0:
+        pytest.skip("triton CPU interpreter unavailable: " + p.stderr[-300:])
+    import oracle
+    for case in json.loads(p.stdout.strip().splitlines()[-1]):
+        seed = case["seed"]
+        key = [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF]
+        for i in range(64):
+            ctr = [case["ctr"][w][i] for w in range(4)]
+            assert oracle.philox4x32_10(ctr, key).tolist() == case["out"][4 * i: 4 * i + 4]
+
+
+def test_philox_bits_uniform(oracle_mod):
+    """Chi-square on the low byte of each word and lag-1 correlation."""
+    vals = np.array([oracle_mod.philox4x32_10([j, 0, 0, 0], [7, 9]) for j in range(20000)], dtype=np.uint64)
+    low = (vals & 0xFF).ravel()
+    hist = np.bincount(low.astype(np.int64), minlength=256)
+    exp = low.size / 256
+    chi2 = float(((hist - exp) ** 2 / exp).sum())
+    assert chi2 < 255 + 6 * math.sqrt(2 * 255)
+    x = (vals[:, 0].astype(np.float64) / 2**32) - 0.5
+    corr = float(np.corrcoef(x[:-1], x[1:])[0, 1])
+    assert abs(corr) < 5 / math.sqrt(len(x))
+
+
+def test_uniform_draw_law(oracle_mod):
+    """U[0,n) by masked rejection is uniform and in range; n <= 1 uses no draw."""
+    assert oracle_mod.uniform_u64(1, 2, 0, 1) == (0, 0)
+    for n in (3, 5, 6, 17):
+        xs = [oracle_mod.uniform_u64(3, j, 0, n)[0] for j in range(6000)]
+        assert min(xs) >= 0 and max(xs) < n
+        hist = np.bincount(xs, minlength=n)
+        exp = len(xs) / n
+        chi2 = float(((hist - exp) ** 2 / exp).sum())
+        assert chi2 < (n - 1) + 6 * math.sqrt(2 * (n - 1))
+
+
+def _partial_law(G, nwin):
+    """All partial matches with their window multiplicity N_phi."""
+    mult = {}
+    for i in range(nwin):
+        cnt, lst = G.partial_count(i, want_list=True, cap=200000)
+        assert cnt == lst.shape[0]
+        for row in lst:
+            key = tuple(int(x) for x in row)
+            mult[key] = mult.get(key, 0) + 1
+    return mult
+
+
+def _outcome_by_definition(G, nv, edges, rank, delta, order, treegids, gs, gd, gt):
+    """Reject reason and contribution of one sampled tree, from Def. 1.2 and
+    Alg. 4 directly: pure-Python enumeration of the non-tree edges."""
+    phi = {}
+    tau = {}
+    for s_edge, g in zip(order, treegids):
+        a, b = edges[s_edge]
+        phi[a] = int(gs[g]); phi[b] = int(gd[g]); tau[s_edge] = int(gt[g])
+    if len(set(phi.values())) < nv:
+        return 1, 0
+    lo, hi = min(tau.values()), max(tau.values())
+    if hi - lo > delta:
+        return 2, 0
+    by_rank = sorted(tau, key=lambda e: rank[e])
+    if any(tau[by_rank[i]] >= tau[by_rank[i + 1]] for i in range(len(by_rank) - 1)):
+        return 3, 0
+    nontree = [e for e in range(len(edges)) if e not in tau]
+    cands = []
+    for e in nontree:
+        a, b = edges[e]
+        cands.append([int(gt[x]) for x in range(len(gs)) if gs[x] == phi[a] and gd[x] == phi[b]])
+    cnt = 0
+    import itertools
+    for combo in itertools.product(*cands):
+        times = dict(tau)
+        times.update(zip(nontree, combo))
+        seq = [times[e] for e in sorted(times, key=lambda e: rank[e])]
+        if all(seq[i] < seq[i + 1] for i in range(len(seq) - 1)) and seq[-1] - seq[0] <= delta:
+            cnt += 1
+    T = int(gt.max())
+    N = sum(1 for i in range(T // delta + 1) if i * delta <= lo and hi < (i + 2) * delta)
+    return 0, cnt * 2 // N
+
+
+@pytest.mark.parametrize("name,tree,root,delta", [("triangle", [0, 1], 1, 6), ("cycle4", [0, 1, 2], 1, 8),
+                                                  ("bowtie", [0, 1, 3, 4], 3, 7), ("parallel", [0, 1], 0, 6)])
+def test_sampler_law_and_outcomes(oracle_mod, name, tree, root, delta):
+    """Each partial match phi is output with probability N_phi / W (Lemma
+    3.5), and each sample's reject reason and contribution 2*cnt/N_phi equal
+    those computed from the definition."""
+    nv, edges, rank = SMALL_MOTIFS[name]
+    n, s, d, t = small_random_graph(21, n=nv + 2, m=40, t_hi=30)
+    G = oracle_mod.Graph(n, s, d, t)
+    G.set_motif(nv, edges, rank, delta, tree, root)
+    W = G.weights()
+    nwin = len(G.window_totals())
+    law = _partial_law(G, nwin)
+    assert sum(law.values()) == W and 5 <= len(law) <= 5000
+    k = 200_000
+    res, tg, tc, tr = G.sample(k, seed=99, trace=True)
+    obs = {}
+    first = {}
+    for i, row in enumerate(tg):
+        key = tuple(int(x) for x in row)
+        assert key in law
+        obs[key] = obs.get(key, 0) + 1
+        first.setdefault(key, i)
+    chi2 = 0.0
+    for key, nphi in law.items():
+        e = k * nphi / W
+        chi2 += (obs.get(key, 0) - e) ** 2 / e
+    dof = len(law) - 1
+    assert chi2 < dof + 6 * math.sqrt(2 * dof)
+    assert res.valid + res.rej_vertex + res.rej_delta + res.rej_order == k
+    order, _, _, _ = G.plan_info()
+    gs, gd, gt = G.edges()
+    for key, i in first.items():
+        reason, contrib = _outcome_by_definition(G, nv, edges, rank, delta, list(order), key, gs, gd, gt)
+        assert (int(tr[i]), int(tc[i])) == (reason, contrib), key
+    counts = np.bincount(tr, minlength=4)
+    assert (counts[0], counts[1], counts[2], counts[3]) == (res.valid, res.rej_vertex, res.rej_delta, res.rej_order)
+    assert res.hits2 == int(tc.astype(object).sum())
+
+
+def test_unbiased_over_100_seeds(oracle_mod):
+    """E[C_hat] = C (Lemma 3.6): mean of 100 independent estimates within
+    3 standard errors of the exact count."""
+    nv, edges, rank = SMALL_MOTIFS["cycle4"]
+    n, s, d, t = small_random_graph(5, n=7, m=120, t_hi=50)
+    G = oracle_mod.Graph(n, s, d, t)
+    delta = 12
+    C = G.brute_count(nv, edges, rank, delta)
+    assert C > 20
+    G.set_motif(nv, edges, rank, delta, [0, 1, 2], 1)
+    G.weights()
+    est = np.array([G.sample(3000, seed).estimate for seed in range(1, 101)])
+    se = est.std(ddof=1) / math.sqrt(len(est))
+    assert abs(est.mean() - C) <= 3 * se + 1e-9, (est.mean(), C, se)
+
+
+def test_input_contract(oracle_mod):
+    with pytest.raises(oracle_mod.OracleError) as e:
+        oracle_mod.Graph(3, [0, 0], [1, 1], [5, 5])
+    assert e.value.code == oracle_mod.E_DUP
+    G = oracle_mod.Graph(3, [0, 0, 1], [1, 1, 2], [5, 5, 6], flags=oracle_mod.DEDUP)
+    assert G.m == 2
+    with pytest.raises(oracle_mod.OracleError) as e:
+        oracle_mod.Graph(3, [0, 1], [0, 2], [5, 6])
+    assert e.value.code == oracle_mod.E_SELFLOOP
+    G = oracle_mod.Graph(3, [0, 1], [0, 2], [5, 6], flags=oracle_mod.DROP_SELF)
+    assert G.m == 1
+    assert G.t_min == 6 and G.span == 0
+
+
+def test_overflow_detected(oracle_mod):
+    """Out-star with 6 leaves on a hub with 2000 out-edges inside delta: the
+    root weight is a product of six ~2000 sums, ~6.4e19 >= 2^64."""
+    hub_edges = 2000
+    src = np.zeros(hub_edges, np.uint32)
+    dst = np.arange(1, hub_edges + 1, dtype=np.uint32)
+    t = np.arange(hub_edges, dtype=np.int64)
+    G = oracle_mod.Graph(hub_edges + 1, src, dst, t)
+    edges = [(0, i) for i in range(1, 8)]
+    G.set_motif(8, edges, list(range(7)), 10_000, list(range(7)), 0)
+    assert G.weights(allow_overflow=True) is None

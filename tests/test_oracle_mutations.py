@@ -1,0 +1,55 @@
+"""Planted mistakes: each plausible slip in the oracle (a dropped term, a
+wrong strictness, a wrong constant, an off-by-one) must make at least one of
+the pins in test_oracle.py fail.  The mistake is planted in a temporary copy
+of the oracle source on the CPU; the committed oracle is untouched."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "timest_oracle.c")
+
+MUTATIONS = {
+    "c1_not_strict": ("if (P->rank[c] > P->rank[s]) { lo = te + 1; hi = te + d; }",
+                      "if (P->rank[c] > P->rank[s]) { lo = te; hi = te + d; }"),
+    "exclusion_dropped": ("if (cand_nbr(g, &R, x) != R.excl)\n                                    sum +=",
+                          "if (1)\n                                    sum +="),
+    "window_closed": ("int64_t wlo = wi * d, whi = (wi + 2) * d - 1;",
+                      "int64_t wlo = wi * d, whi = (wi + 2) * d;"),
+    "nphi_ignores_first_window": ("int N = 1 + ((a >= d && (b / d) == (a / d)) ? 1 : 0);",
+                                  "int N = 1 + (((b / d) == (a / d)) ? 1 : 0);"),
+    "derive_not_strict": ("if (pos > 0 && t <= prev) continue;",
+                          "if (pos > 0 && t < prev) continue;"),
+    "validate_order_not_strict": ("if (have && S.tau[e] <= prev) return RS_ORDER;",
+                                  "if (have && S.tau[e] < prev) return RS_ORDER;"),
+    "philox_multiplier": ("0xD2511F53u", "0xD2511F57u"),
+    "philox_key_schedule": ("if (r > 0) { k0 += 0x9E3779B9u;", "if (r >= 0) { k0 += 0x9E3779B9u;"),
+    "brute_not_injective": ("if (pa < 0) { if (vertex_used(B, u)) return;", "if (pa < 0) { if (0) return;"),
+    "brute_delta_off_by_one": ("int64_t hi = (pos == 0) ? g->T : first + P->delta;",
+                               "int64_t hi = (pos == 0) ? g->T : first + P->delta - 1;"),
+    "child_pick_off_by_one": ("if (run > rc) { pick = x; break; }", "if (run >= rc) { pick = x; break; }"),
+    "root_pick_off_by_one": ("if (C->rootcum[p][mid] <= rr) lo = mid + 1;", "if (C->rootcum[p][mid] < rr) lo = mid + 1;"),
+    "window_pick_off_by_one": ("if (r < (u128)C->Wi[i]) { wi = i; break; }", "if (r <= (u128)C->Wi[i]) { wi = i; break; }"),
+    "estimate_scale": ("res->estimate = (double)C->W * (double)hits / (2.0 * (double)k);",
+                       "res->estimate = (double)C->W * (double)hits / ((double)k);"),
+    "root_total_wrong_layer": ("int64_t wi = window_of(g->t[e], p, d);\n            if (wi < 0) { C->rootcum[p][e] = 0; continue; }",
+                               "int64_t wi = window_of(g->t[e], 0, d);\n            if (wi < 0) { C->rootcum[p][e] = 0; continue; }"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    mutant = tmp_path / "mutant.c"
+    mutant.write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-o", str(lib), str(mutant)])
+    env = dict(os.environ, TIMEST_ORACLE_LIB=str(lib))
+    p = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    assert p.returncode != 0, f"planted mistake {name} was not caught by any pin"
