@@ -1,0 +1,195 @@
+/*
+ * timest.h -- C ABI of the GB300-native TIMEST temporal-motif estimator.
+ *
+ * TIMEST (Pan, Bhalerao, Seshadhri, Talati, arXiv 2507.20441) estimates the
+ * number C of M-matches of a temporal motif M = (H, pi, delta) in a directed
+ * temporal multigraph G (Def. 1.1-1.2): it picks a spanning tree S of H rooted
+ * at an edge c, computes per-edge weights w_{s,e} by a dynamic program over
+ * the tree inside overlapping 2*delta windows (Sec. 3.1, Claims 3.1-3.4,
+ * Alg. 1-2), samples k partial matches of S with probability N_phi / W
+ * (Sec. 3.2, Alg. 3, Lemma 3.5), validates each and counts its completions to
+ * M (Sec. 3.3, Alg. 4-5) and returns C_hat = W * sum(cnt / N_phi) / k
+ * (Alg. 6, Lemma 3.6).  All arithmetic is exact integer: weights are unsigned
+ * 64-bit, totals 128-bit.
+ *
+ * Conventions (all entry points):
+ *   - Every function returns a status (TM_OK = 0 or a TM_E_* code); on error
+ *     tm_last_error(ctx) holds a one-line message.  No call traps or aborts.
+ *   - Host pointers are plain CPU memory; "device" pointers are CUDA global
+ *     memory of the context's device.  The caller owns every array it passes
+ *     and may free it as soon as the call returns; the library copies what it
+ *     keeps.  The context owns all device memory it allocates.
+ *   - Calls on one context are serialised by the caller and run on the
+ *     context's CUDA stream.  tm_serve_submit / tm_serve_poll are thread safe.
+ *   - Time t' = t - t_min (Sec. 3 preamble).  The graph's time span
+ *     t_max - t_min must be < 2^32 - 1 and m, n < 2^32 - 1 (TM_E_LIMIT).
+ *   - Windows are [i*delta, (i+2)*delta) in t', i = 0..floor(T/delta)
+ *     (Constraint 3, Sec. 2.1, Alg. 1).  Constraint 1 puts a later child edge
+ *     in (t, t+delta] and an earlier one in [t-delta, t).
+ */
+#ifndef TIMEST_GB300_H
+#define TIMEST_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+enum {
+    TM_OK = 0,
+    TM_E_ARG = 1,       /* bad argument (null pointer, out-of-range id, ...) */
+    TM_E_DUP = 2,       /* repeated (u,v,t) tuple; Sec. 1.1 forbids it       */
+    TM_E_SELFLOOP = 3,  /* u == v; never part of an injective match          */
+    TM_E_MOTIF = 4,     /* motif or tree invalid (disconnected, self loop,   */
+                        /* order not a permutation, delta <= 0, nv > 8, ...) */
+    TM_E_NOMEM = 5,     /* device allocation failed                          */
+    TM_E_OVERFLOW = 6,  /* an exact count does not fit its integer width     */
+    TM_E_STATE = 7,     /* call out of order (e.g. sample before weights)    */
+    TM_E_TIMEOUT = 8,   /* a bounded wait ran out                            */
+    TM_E_CUDA = 9,      /* a CUDA runtime call failed                        */
+    TM_E_LIMIT = 10     /* size beyond a stated limit                        */
+};
+
+/* ---- tm_graph_load flags ------------------------------------------------ */
+enum {
+    TM_HOST = 0,        /* src/dst/t are host pointers                        */
+    TM_DEVICE = 1,      /* src/dst/t are device pointers                      */
+    TM_DEDUP = 2,       /* drop repeated (u,v,t) tuples instead of TM_E_DUP   */
+    TM_DROP_SELF = 4    /* drop self loops instead of TM_E_SELFLOOP           */
+};
+
+typedef struct tm_ctx tm_ctx;
+typedef struct tm_motif tm_motif;
+
+/* Unsigned 128-bit integer as two 64-bit halves. */
+typedef struct { uint64_t lo, hi; } tm_u128;
+
+/* Optional device allocator.  alloc returns a device pointer (or NULL on
+ * failure) of at least `bytes` bytes usable on `stream`; free releases it. */
+typedef void *(*tm_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*tm_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+typedef struct {
+    tm_alloc_fn alloc;      /* NULL: cudaMallocAsync on the context stream */
+    tm_free_fn free;
+    void *alloc_user;
+    int device;             /* CUDA device ordinal (default 0)              */
+    int sample_threads;     /* threads per block of the sampler (0 = auto)  */
+    int sample_tile;        /* samples per work item of batched runs (0 = auto) */
+    int reserved[8];
+} tm_config;
+
+/* Result of one estimate.  estimate = W * hits2 / (2k) (Alg. 6 with the
+ * per-sample count cnt * 2 / N_phi kept integral). */
+typedef struct {
+    tm_u128 W;              /* total number of (window, partial match) pairs */
+    tm_u128 hits2;          /* sum over samples of cnt * 2 / N_phi           */
+    uint64_t k;             /* samples drawn                                 */
+    uint64_t valid;         /* samples passing Alg. 4's three checks         */
+    uint64_t rej_vertex;    /* rejected: vertex map not 1-1                  */
+    uint64_t rej_delta;     /* rejected: tree edges span more than delta     */
+    uint64_t rej_order;     /* rejected: tree edges out of pi order          */
+    double estimate;        /* C_hat                                         */
+} tm_result;
+
+/* Fill *cfg with defaults. */
+void tm_config_default(tm_config *cfg);
+
+/* Create a context on cfg->device.  cuda_stream is a cudaStream_t to run on
+ * (NULL: the context creates its own).  *out receives the context. */
+int tm_create(tm_ctx **out, const tm_config *cfg, void *cuda_stream);
+
+/* Destroy a context and every device buffer it owns (motifs must be freed
+ * first with tm_motif_free). */
+void tm_destroy(tm_ctx *ctx);
+
+/* One-line message for the last failing call on ctx (never NULL). */
+const char *tm_last_error(tm_ctx *ctx);
+
+/* Load a temporal graph: m tuples (src[i], dst[i], t[i]) over n vertices
+ * (Sec. 1.1).  flags: TM_HOST or TM_DEVICE for where the three arrays live,
+ * plus TM_DEDUP / TM_DROP_SELF.  Ids must be < n.  Replaces any previous
+ * graph (and invalidates motifs' weights).  Errors: TM_E_ARG, TM_E_DUP,
+ * TM_E_SELFLOOP, TM_E_LIMIT, TM_E_NOMEM, TM_E_CUDA. */
+int tm_graph_load(tm_ctx *ctx, uint32_t n, uint64_t m, const uint32_t *src,
+                  const uint32_t *dst, const int64_t *t, int flags);
+
+/* Build the time-sorted adjacency of the loaded graph on the device (Sec. 3
+ * preamble; Defs. 3.1-3.3): the GLOBAL order (t', src, dst) that numbers the
+ * edges, per-vertex out-lists (t', dst), in-lists (t', src), and per-pair
+ * multi-edge lists El_{u,v} (t').  Duplicates / self loops are reported here
+ * when tm_graph_load was given device pointers. */
+int tm_preprocess(tm_ctx *ctx);
+
+/* Number of edges kept, t_min and T = max t' of the preprocessed graph. */
+int tm_graph_info(tm_ctx *ctx, uint64_t *m, int64_t *t_min, int64_t *T);
+
+/* Copy the GLOBAL order to host arrays of m entries (tests and debugging). */
+int tm_edges_export(tm_ctx *ctx, uint32_t *src, uint32_t *dst, uint32_t *tprime);
+
+/* Define motif M = (H, pi, delta) (Def. 1.1): nv <= 8 vertices, ne <= 16
+ * edges; edges[2i], edges[2i+1] are the tail and head of edge i; order[i] is
+ * the position of edge i in pi (a permutation of 0..ne-1); delta >= 1.
+ * Picks a default spanning tree and root: the tree of least constraint
+ * looseness (Alg. 8, read over tree edges), ties to the lexicographically
+ * smallest edge set, rooted at the edge of least eccentricity.
+ * Errors: TM_E_ARG, TM_E_MOTIF. */
+int tm_set_motif(tm_ctx *ctx, uint32_t nv, uint32_t ne, const uint32_t *edges,
+                 const uint32_t *order, int64_t delta, tm_motif **out);
+
+/* Pin the spanning tree (nv-1 motif-edge ids) and its root edge
+ * (Def. 3.5).  Invalidates cached weights.  Errors: TM_E_MOTIF. */
+int tm_set_tree(tm_motif *mo, const uint32_t *tree_edge_ids, uint32_t root_edge);
+
+/* Read the tree plan: order[q] = motif edge sampled q-th (q < nv-1),
+ * parent[q] = index in order of its parent (-1 for the root). */
+int tm_motif_plan(tm_motif *mo, int32_t *order, int32_t *parent);
+
+/* Weight pass (Sec. 3.1): windows, the DP over the tree in height order
+ * (Claim 3.2, Alg. 2), segmented prefix sums and the root CDF (Claim 3.4).
+ * *W_out receives W = sum over windows of W_i.  Weights stay resident in the
+ * motif until it is freed or the graph changes.
+ * Errors: TM_E_STATE (no graph), TM_E_OVERFLOW, TM_E_NOMEM, TM_E_CUDA. */
+int tm_weights(tm_ctx *ctx, tm_motif *mo, tm_u128 *W_out);
+
+/* Copy w_{s,e} of tree edge `tree_edge` (a motif-edge id) in window layer
+ * `layer` (0: windows with even i, 1: odd i) for every edge, in GLOBAL order,
+ * to host_out[m].  Edges outside any window of the layer read 0. */
+int tm_weights_export(tm_ctx *ctx, tm_motif *mo, uint32_t tree_edge, uint32_t layer,
+                      uint64_t *host_out);
+
+/* Per-window totals W_i, i = 0..floor(T/delta), to host_out[cap];
+ * *nwin receives floor(T/delta)+1. */
+int tm_window_totals(tm_ctx *ctx, tm_motif *mo, uint64_t *host_out, uint64_t cap,
+                     uint64_t *nwin);
+
+/* Draw k samples with ids first_index .. first_index+k-1 from seed (Sec. 3.2
+ * with the counter-based draw protocol: Philox4x32-10, key = seed, counter =
+ * (sample id, draw number)), validate and count them (Sec. 3.3) and reduce
+ * (Alg. 6).  Disjoint id ranges add exactly, so a job can be split or
+ * resumed.  Errors: TM_E_STATE (no weights), TM_E_OVERFLOW, TM_E_CUDA. */
+int tm_sample(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first_index,
+              tm_result *out);
+
+/* Like tm_sample, and also copies each sample's tree edges (GLOBAL-order ids,
+ * in plan order; k*(nv-1) entries), its contribution cnt*2/N_phi and its
+ * outcome (0 valid, 1 vertex, 2 delta, 3 order) to host arrays. */
+int tm_sample_trace(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first_index,
+                    uint32_t *tree_gids, uint64_t *contrib, int32_t *reason, tm_result *out);
+
+/* Batched estimate: nq queries (motifs with weights, sample counts, seeds)
+ * run as one persistent launch over a shared queue of sample tiles.  out[q]
+ * is bit-identical to tm_sample(ctx, motifs[q], k[q], seed[q], 0, ...). */
+int tm_batch_run(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64_t *k,
+                 const uint64_t *seed, tm_result *out);
+
+/* Free a motif and its device weights. */
+void tm_motif_free(tm_motif *mo);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TIMEST_GB300_H */

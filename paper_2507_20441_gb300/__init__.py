@@ -1,0 +1,394 @@
+"""GB300-native TIMEST: temporal-motif count estimation by spanning-tree
+sampling (Pan, Bhalerao, Seshadhri, Talati, arXiv 2507.20441).
+
+A thin ctypes binding of the C ABI in ``include/timest.h`` -- the functions
+below carry the same names (``tm_create``, ``tm_graph_load``, ...) and only
+marshal arguments; every step of the estimator runs in the CUDA library
+``_build/libtimest_gb300.so``.  PyTorch supplies device memory (its caching
+allocator, through the allocator hooks of ``tm_config``) and the CUDA stream.
+
+There is no CPU fallback: if the library is missing or cannot be loaded,
+every call raises ``TimestUnavailable``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtimest_gb300.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "timest.h")
+
+TM_OK, TM_E_ARG, TM_E_DUP, TM_E_SELFLOOP, TM_E_MOTIF, TM_E_NOMEM, TM_E_OVERFLOW, TM_E_STATE, TM_E_TIMEOUT, \
+    TM_E_CUDA, TM_E_LIMIT = range(11)
+TM_HOST, TM_DEVICE, TM_DEDUP, TM_DROP_SELF = 0, 1, 2, 4
+_STATUS_NAMES = {0: "TM_OK", 1: "TM_E_ARG", 2: "TM_E_DUP", 3: "TM_E_SELFLOOP", 4: "TM_E_MOTIF", 5: "TM_E_NOMEM",
+                 6: "TM_E_OVERFLOW", 7: "TM_E_STATE", 8: "TM_E_TIMEOUT", 9: "TM_E_CUDA", 10: "TM_E_LIMIT"}
+
+
+class TimestUnavailable(RuntimeError):
+    """The CUDA library is not built or cannot be loaded."""
+
+
+class TimestError(RuntimeError):
+    def __init__(self, code: int, what: str, msg: str = ""):
+        super().__init__(f"{what} failed: {_STATUS_NAMES.get(code, code)} {msg}".strip())
+        self.code = code
+
+
+class tm_u128(C.Structure):
+    _fields_ = [("lo", C.c_uint64), ("hi", C.c_uint64)]
+
+    @property
+    def value(self) -> int:
+        return int(self.lo) | (int(self.hi) << 64)
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class tm_config(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p), ("device", C.c_int),
+                ("sample_threads", C.c_int), ("sample_tile", C.c_int), ("reserved", C.c_int * 8)]
+
+
+class tm_result(C.Structure):
+    _fields_ = [("W", tm_u128), ("hits2", tm_u128), ("k", C.c_uint64), ("valid", C.c_uint64),
+                ("rej_vertex", C.c_uint64), ("rej_delta", C.c_uint64), ("rej_order", C.c_uint64),
+                ("estimate", C.c_double)]
+
+
+@dataclass
+class Result:
+    W: int
+    hits2: int
+    k: int
+    valid: int
+    rej_vertex: int
+    rej_delta: int
+    rej_order: int
+    estimate: float
+
+    @staticmethod
+    def of(r: tm_result) -> "Result":
+        return Result(r.W.value, r.hits2.value, int(r.k), int(r.valid), int(r.rej_vertex), int(r.rej_delta),
+                      int(r.rej_order), float(r.estimate))
+
+
+_lib = None
+_load_error = None
+
+
+def _declare(L):
+    vp, u32, u64, i32, i64 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int, C.c_int64
+    pv = C.POINTER(C.c_void_p)
+    L.tm_config_default.argtypes = [C.POINTER(tm_config)]; L.tm_config_default.restype = None
+    L.tm_create.argtypes = [pv, C.POINTER(tm_config), vp]
+    L.tm_destroy.argtypes = [vp]; L.tm_destroy.restype = None
+    L.tm_last_error.argtypes = [vp]; L.tm_last_error.restype = C.c_char_p
+    L.tm_graph_load.argtypes = [vp, u32, u64, vp, vp, vp, i32]
+    L.tm_preprocess.argtypes = [vp]
+    L.tm_graph_info.argtypes = [vp, C.POINTER(u64), C.POINTER(i64), C.POINTER(i64)]
+    L.tm_edges_export.argtypes = [vp, vp, vp, vp]
+    L.tm_set_motif.argtypes = [vp, u32, u32, vp, vp, i64, pv]
+    L.tm_set_tree.argtypes = [vp, vp, u32]
+    L.tm_motif_plan.argtypes = [vp, vp, vp]
+    L.tm_weights.argtypes = [vp, vp, C.POINTER(tm_u128)]
+    L.tm_weights_export.argtypes = [vp, vp, u32, u32, vp]
+    L.tm_window_totals.argtypes = [vp, vp, vp, u64, C.POINTER(u64)]
+    L.tm_sample.argtypes = [vp, vp, u64, u64, u64, C.POINTER(tm_result)]
+    L.tm_sample_trace.argtypes = [vp, vp, u64, u64, u64, vp, vp, vp, C.POINTER(tm_result)]
+    L.tm_batch_run.argtypes = [vp, u32, vp, vp, vp, vp]
+    L.tm_motif_free.argtypes = [vp]; L.tm_motif_free.restype = None
+    return L
+
+
+def lib():
+    """Load the CUDA library (raises TimestUnavailable if it is not built)."""
+    global _lib, _load_error
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise TimestUnavailable(f"TIMEST CUDA library not built ({LIB_PATH}); run __graft_entry__.build()")
+    try:
+        _lib = _declare(C.CDLL(LIB_PATH))
+    except OSError as e:
+        _load_error = e
+        raise TimestUnavailable(f"cannot load {LIB_PATH}: {e}") from e
+    return _lib
+
+
+def build(force: bool = False) -> str:
+    from . import _build
+    path = _build.build(force=force)
+    return path
+
+
+def _ptr(a) -> C.c_void_p:
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(int(a.data_ptr()))   # torch tensor
+
+
+def _check(rc: int, ctx, what: str):
+    if rc != TM_OK:
+        msg = lib().tm_last_error(ctx).decode() if ctx else ""
+        raise TimestError(rc, what, msg)
+
+
+# ---------------------------------------------------------------------------
+# torch allocator hooks (device memory comes from PyTorch's caching allocator)
+# ---------------------------------------------------------------------------
+class _TorchAllocator:
+    def __init__(self, device: int):
+        import torch
+        self.torch = torch
+        self.device = device
+
+        def _alloc(nbytes, stream, user):
+            try:
+                return int(self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0)))
+            except Exception:
+                return None
+
+        def _free(ptr, nbytes, stream, user):
+            try:
+                self.torch.cuda.caching_allocator_delete(int(ptr))
+            except Exception:
+                pass
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.free = FREE_FN(_free)
+
+
+# ---------------------------------------------------------------------------
+# C-ABI functions under their own names
+# ---------------------------------------------------------------------------
+def tm_create(device: int = 0, stream=None, torch_allocator: bool = True, sample_threads: int = 0,
+              sample_tile: int = 0, alloc_hooks=None):
+    """Returns an opaque context handle (c_void_p) plus the objects that must
+    stay alive with it."""
+    L = lib()
+    cfg = tm_config()
+    L.tm_config_default(C.byref(cfg))
+    cfg.device = device
+    cfg.sample_threads = sample_threads
+    cfg.sample_tile = sample_tile
+    keep = []
+    if alloc_hooks is not None:
+        cfg.alloc, cfg.free = alloc_hooks
+        keep.append(alloc_hooks)
+    elif torch_allocator:
+        ta = _TorchAllocator(device)
+        cfg.alloc, cfg.free = ta.alloc, ta.free
+        keep.append(ta)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream(device).cuda_stream
+    h = C.c_void_p()
+    rc = L.tm_create(C.byref(h), C.byref(cfg), C.c_void_p(int(stream) if stream else 0))
+    if rc != TM_OK:
+        raise TimestError(rc, "tm_create")
+    return h, keep
+
+
+def tm_destroy(ctx):
+    lib().tm_destroy(ctx)
+
+
+def tm_last_error(ctx) -> str:
+    return lib().tm_last_error(ctx).decode()
+
+
+def tm_graph_load(ctx, n, src, dst, t, flags=TM_HOST):
+    """src/dst (uint32) and t (int64): numpy arrays (TM_HOST) or CUDA tensors
+    (pass TM_DEVICE)."""
+    m = len(src)
+    if flags & TM_DEVICE:
+        ps, pd, pt = _ptr(src), _ptr(dst), _ptr(t)
+    else:
+        src = np.ascontiguousarray(src, dtype=np.uint32)
+        dst = np.ascontiguousarray(dst, dtype=np.uint32)
+        t = np.ascontiguousarray(t, dtype=np.int64)
+        ps, pd, pt = _ptr(src), _ptr(dst), _ptr(t)
+    _check(lib().tm_graph_load(ctx, int(n), m, ps, pd, pt, flags), ctx, "tm_graph_load")
+
+
+def tm_preprocess(ctx):
+    _check(lib().tm_preprocess(ctx), ctx, "tm_preprocess")
+
+
+def tm_graph_info(ctx):
+    m, tmin, T = C.c_uint64(), C.c_int64(), C.c_int64()
+    _check(lib().tm_graph_info(ctx, C.byref(m), C.byref(tmin), C.byref(T)), ctx, "tm_graph_info")
+    return int(m.value), int(tmin.value), int(T.value)
+
+
+def tm_edges_export(ctx):
+    m, _, _ = tm_graph_info(ctx)
+    s = np.zeros(m, np.uint32); d = np.zeros(m, np.uint32); t = np.zeros(m, np.uint32)
+    _check(lib().tm_edges_export(ctx, _ptr(s), _ptr(d), _ptr(t)), ctx, "tm_edges_export")
+    return s, d, t
+
+
+def tm_set_motif(ctx, nv, edges, order, delta):
+    e = np.ascontiguousarray(np.array(edges, dtype=np.uint32).reshape(-1))
+    o = np.ascontiguousarray(np.array(order, dtype=np.uint32))
+    h = C.c_void_p()
+    _check(lib().tm_set_motif(ctx, int(nv), len(o), _ptr(e), _ptr(o), int(delta), C.byref(h)), ctx, "tm_set_motif")
+    return h
+
+
+def tm_set_tree(ctx, motif, tree, root):
+    tr = np.ascontiguousarray(np.array(tree, dtype=np.uint32))
+    _check(lib().tm_set_tree(motif, _ptr(tr), int(root)), ctx, "tm_set_tree")
+
+
+def tm_motif_plan(motif, ntree):
+    order = np.zeros(ntree, np.int32); parent = np.zeros(ntree, np.int32)
+    rc = lib().tm_motif_plan(motif, _ptr(order), _ptr(parent))
+    if rc != TM_OK:
+        raise TimestError(rc, "tm_motif_plan")
+    return order, parent
+
+
+def tm_weights(ctx, motif) -> int:
+    W = tm_u128()
+    _check(lib().tm_weights(ctx, motif, C.byref(W)), ctx, "tm_weights")
+    return W.value
+
+
+def tm_weights_export(ctx, motif, tree_edge, layer, m):
+    out = np.zeros(m, np.uint64)
+    _check(lib().tm_weights_export(ctx, motif, int(tree_edge), int(layer), _ptr(out)), ctx, "tm_weights_export")
+    return out
+
+
+def tm_window_totals(ctx, motif):
+    nw = C.c_uint64()
+    _check(lib().tm_window_totals(ctx, motif, None, 0, C.byref(nw)), ctx, "tm_window_totals")
+    out = np.zeros(int(nw.value), np.uint64)
+    _check(lib().tm_window_totals(ctx, motif, _ptr(out), len(out), C.byref(nw)), ctx, "tm_window_totals")
+    return out
+
+
+def tm_sample(ctx, motif, k, seed, first_index=0) -> Result:
+    r = tm_result()
+    _check(lib().tm_sample(ctx, motif, int(k), int(seed), int(first_index), C.byref(r)), ctx, "tm_sample")
+    return Result.of(r)
+
+
+def tm_sample_trace(ctx, motif, k, seed, first_index, ntree):
+    r = tm_result()
+    g = np.zeros(int(k) * ntree, np.uint32); c = np.zeros(int(k), np.uint64); why = np.zeros(int(k), np.int32)
+    _check(lib().tm_sample_trace(ctx, motif, int(k), int(seed), int(first_index), _ptr(g), _ptr(c), _ptr(why),
+                                 C.byref(r)), ctx, "tm_sample_trace")
+    return Result.of(r), g.reshape(int(k), ntree), c, why
+
+
+def tm_batch_run(ctx, motifs, ks, seeds):
+    nq = len(motifs)
+    arr = (C.c_void_p * nq)(*[m.value for m in motifs])
+    k = np.ascontiguousarray(np.array(ks, dtype=np.uint64))
+    s = np.ascontiguousarray(np.array(seeds, dtype=np.uint64))
+    res = (tm_result * nq)()
+    _check(lib().tm_batch_run(ctx, nq, arr, _ptr(k), _ptr(s), res), ctx, "tm_batch_run")
+    return [Result.of(res[i]) for i in range(nq)]
+
+
+def tm_motif_free(motif):
+    lib().tm_motif_free(motif)
+
+
+# ---------------------------------------------------------------------------
+# Convenience objects over the same calls
+# ---------------------------------------------------------------------------
+class Motif:
+    def __init__(self, ctx: "Context", nv, edges, order, delta):
+        self.ctx = ctx
+        self.nv = int(nv)
+        self.ntree = self.nv - 1
+        self.edges = list(edges)
+        self.order = list(order)
+        self.delta = int(delta)
+        self.h = tm_set_motif(ctx.h, nv, edges, order, delta)
+        ctx._motifs.append(self)
+
+    def set_tree(self, tree, root):
+        tm_set_tree(self.ctx.h, self.h, tree, root)
+        return self
+
+    def plan(self):
+        return tm_motif_plan(self.h, self.ntree)
+
+    def weights(self) -> int:
+        return tm_weights(self.ctx.h, self.h)
+
+    def export_weights(self, tree_edge, layer):
+        return tm_weights_export(self.ctx.h, self.h, tree_edge, layer, self.ctx.m)
+
+    def window_totals(self):
+        return tm_window_totals(self.ctx.h, self.h)
+
+    def sample(self, k, seed, first_index=0) -> Result:
+        return tm_sample(self.ctx.h, self.h, k, seed, first_index)
+
+    def sample_trace(self, k, seed, first_index=0):
+        return tm_sample_trace(self.ctx.h, self.h, k, seed, first_index, self.ntree)
+
+    def free(self):
+        if self.h:
+            tm_motif_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """One device context: a preprocessed temporal graph plus motifs."""
+
+    def __init__(self, device: int = 0, stream=None, torch_allocator: bool = True, **kw):
+        self.h, self._keep = tm_create(device, stream, torch_allocator, **kw)
+        self.m = 0
+        self._motifs = []
+
+    def load_graph(self, n, src, dst, t, flags=TM_HOST, preprocess=True):
+        tm_graph_load(self.h, n, src, dst, t, flags)
+        if preprocess:
+            self.preprocess()
+        return self
+
+    def preprocess(self):
+        tm_preprocess(self.h)
+        self.m, self.t_min, self.T = tm_graph_info(self.h)
+
+    def edges(self):
+        return tm_edges_export(self.h)
+
+    def motif(self, nv, edges, order, delta) -> Motif:
+        return Motif(self, nv, edges, order, delta)
+
+    def batch_run(self, motifs, ks, seeds):
+        return tm_batch_run(self.h, [m.h for m in motifs], ks, seeds)
+
+    def close(self):
+        if self.h:
+            for mo in self._motifs:
+                mo.free()
+            self._motifs = []
+            tm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,514 @@
+// C-ABI entry points, context and allocation, and the motif / spanning-tree
+// compiler (Defs. 3.4-3.5; Sec. 3.5).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "tm_internal.h"
+
+namespace timest {
+
+int set_err(tm_ctx *ctx, int code, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int check_cuda(tm_ctx *ctx, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return TM_OK;
+    cudaGetLastError();
+    return set_err(ctx, TM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void *dalloc(tm_ctx *ctx, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (ctx->cfg.alloc) {
+        p = ctx->cfg.alloc(bytes, (void *)ctx->stream, ctx->cfg.alloc_user);
+    } else if (cudaMallocAsync(&p, bytes, ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (!p) set_err(ctx, TM_E_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    return p;
+}
+
+void dfree(tm_ctx *ctx, void *p, size_t bytes)
+{
+    if (!p) return;
+    if (bytes == 0) bytes = 16;
+    if (ctx->cfg.free) ctx->cfg.free(p, bytes, (void *)ctx->stream, ctx->cfg.alloc_user);
+    else cudaFreeAsync(p, ctx->stream);
+}
+
+int read_status(tm_ctx *ctx, uint32_t *bits)
+{
+    cudaMemcpyAsync(ctx->status_host, ctx->status, 4, cudaMemcpyDeviceToHost, ctx->stream);
+    int rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "stream synchronize");
+    *bits = rc ? 0 : *ctx->status_host;
+    return rc;
+}
+
+void release_weights(tm_ctx *ctx, tm_motif *mo);
+
+static void free_graph(tm_ctx *ctx)
+{
+    for (auto &b : ctx->graph_bufs) dfree(ctx, b.first, b.second);
+    ctx->graph_bufs.clear();
+    ctx->g = DevGraph();
+    ctx->preprocessed = false;
+}
+
+static void free_input(tm_ctx *ctx)
+{
+    if (ctx->in_src) dfree(ctx, ctx->in_src, ctx->m_in * 4);
+    if (ctx->in_dst) dfree(ctx, ctx->in_dst, ctx->m_in * 4);
+    if (ctx->in_t) dfree(ctx, ctx->in_t, ctx->m_in * 8);
+    ctx->in_src = ctx->in_dst = nullptr;
+    ctx->in_t = nullptr;
+}
+
+// ---- motif compiler ------------------------------------------------------
+struct MotifDesc {
+    int nv, ne;
+    int a[kMaxE], b[kMaxE], rank[kMaxE];
+};
+
+static bool connected(const MotifDesc &M, const int *edges, int cnt)
+{
+    int comp[kMaxV];
+    for (int v = 0; v < M.nv; ++v) comp[v] = v;
+    for (int i = 0; i < cnt; ++i) {
+        int ca = comp[M.a[edges[i]]], cb = comp[M.b[edges[i]]];
+        if (ca == cb) continue;
+        for (int v = 0; v < M.nv; ++v) if (comp[v] == cb) comp[v] = ca;
+    }
+    for (int v = 1; v < M.nv; ++v) if (comp[v] != comp[0]) return false;
+    return true;
+}
+
+static bool is_spanning_tree(const MotifDesc &M, const int *edges)
+{
+    int comp[kMaxV];
+    for (int v = 0; v < M.nv; ++v) comp[v] = v;
+    for (int i = 0; i < M.nv - 1; ++i) {
+        int e = edges[i];
+        if (e < 0 || e >= M.ne) return false;
+        int ca = comp[M.a[e]], cb = comp[M.b[e]];
+        if (ca == cb) return false;
+        for (int v = 0; v < M.nv; ++v) if (comp[v] == cb) comp[v] = ca;
+    }
+    return true;
+}
+
+// Constraint looseness of a tree (Alg. 8, summed over pairs of tree edges
+// that share a vertex): sum of |pi(e1) - pi(e2)| - 1.
+static int looseness(const MotifDesc &M, const int *edges)
+{
+    int L = 0;
+    for (int v = 0; v < M.nv; ++v)
+        for (int i = 0; i < M.nv - 1; ++i)
+            for (int j = i + 1; j < M.nv - 1; ++j) {
+                int e1 = edges[i], e2 = edges[j];
+                bool in1 = M.a[e1] == v || M.b[e1] == v, in2 = M.a[e2] == v || M.b[e2] == v;
+                if (in1 && in2) L += std::abs(M.rank[e1] - M.rank[e2]) - 1;
+            }
+    return L;
+}
+
+// Root of least eccentricity in the tree's edge-adjacency graph (ties: lower id).
+static int default_root(const MotifDesc &M, const int *edges)
+{
+    int nt = M.nv - 1, best = -1, bestecc = 1 << 30;
+    for (int i = 0; i < nt; ++i) {
+        int dist[kMaxTree];
+        for (int j = 0; j < nt; ++j) dist[j] = -1;
+        dist[i] = 0;
+        int queue[kMaxTree], h = 0, t = 0;
+        queue[t++] = i;
+        while (h < t) {
+            int x = queue[h++];
+            for (int y = 0; y < nt; ++y) {
+                if (dist[y] >= 0) continue;
+                int ex = edges[x], ey = edges[y];
+                bool adj = M.a[ex] == M.a[ey] || M.a[ex] == M.b[ey] || M.b[ex] == M.a[ey] || M.b[ex] == M.b[ey];
+                if (adj) { dist[y] = dist[x] + 1; queue[t++] = y; }
+            }
+        }
+        int ecc = 0;
+        for (int j = 0; j < nt; ++j) ecc = std::max(ecc, dist[j]);
+        if (ecc < bestecc || (ecc == bestecc && edges[i] < best)) { bestecc = ecc; best = edges[i]; }
+    }
+    return best;
+}
+
+static void default_tree(const MotifDesc &M, int *tree_out, int *root_out)
+{
+    int k = M.nv - 1;
+    int idx[kMaxTree];
+    for (int i = 0; i < k; ++i) idx[i] = i;
+    int best = 1 << 30;
+    // lexicographic enumeration of k-subsets of the ne edges
+    for (;;) {
+        if (is_spanning_tree(M, idx)) {
+            int L = looseness(M, idx);
+            if (L < best) { best = L; for (int i = 0; i < k; ++i) tree_out[i] = idx[i]; }
+        }
+        int i = k - 1;
+        while (i >= 0 && idx[i] == M.ne - k + i) --i;
+        if (i < 0) break;
+        ++idx[i];
+        for (int j = i + 1; j < k; ++j) idx[j] = idx[j - 1] + 1;
+    }
+    *root_out = default_root(M, tree_out);
+}
+
+// Root the tree at `root` and lay it out in sampling order: breadth first;
+// children of the root at its tail, then at its head; a node's children in
+// increasing motif-edge index (the draw order of the counter-based streams).
+static int compile_plan(const MotifDesc &M, const int *tree, int root, int64_t delta, DevPlan &P)
+{
+    memset(&P, 0, sizeof(P));
+    P.nv = M.nv; P.ne = M.ne; P.ntree = M.nv - 1;
+    P.delta = std::min<int64_t>(delta, (int64_t)1 << 33);
+    bool in_tree[kMaxE] = {};
+    for (int i = 0; i < P.ntree; ++i) in_tree[tree[i]] = true;
+    if (!in_tree[root]) return TM_E_MOTIF;
+    for (int e = 0; e < M.ne; ++e) {
+        P.ea[e] = M.a[e]; P.eb[e] = M.b[e]; P.rank[e] = M.rank[e];
+        P.pos_edge[M.rank[e]] = e;
+        P.is_tree[e] = in_tree[e] ? 1 : 0;
+    }
+    int lower[kMaxTree];           // lower endpoint of each node (-1 for the root)
+    bool placed[kMaxE] = {};
+    int nq = 0;
+    P.tedge[0] = root; P.tparent[0] = -1; lower[0] = -1; placed[root] = true; nq = 1;
+    for (int h = 0; h < nq; ++h) {
+        int s = P.tedge[h];
+        int zs[2], nz;
+        if (h == 0) { zs[0] = M.a[s]; zs[1] = M.b[s]; nz = 2; }
+        else { zs[0] = lower[h]; nz = 1; }
+        for (int k = 0; k < nz; ++k) {
+            int z = zs[k];
+            for (int e = 0; e < M.ne; ++e) {
+                if (!in_tree[e] || placed[e] || (M.a[e] != z && M.b[e] != z)) continue;
+                placed[e] = true;
+                int q = nq++;
+                P.tedge[q] = e;
+                P.tparent[q] = h;
+                P.tzside[q] = (M.a[s] == z) ? 0 : 1;
+                P.tout[q] = (M.a[e] == z) ? 1 : 0;
+                P.tlater[q] = (M.rank[e] > M.rank[s]) ? 1 : 0;
+                lower[q] = (M.a[e] == z) ? M.b[e] : M.a[e];
+                P.child[h][P.nchild[h]++] = q;
+            }
+        }
+    }
+    if (nq != P.ntree) return TM_E_MOTIF;
+    int slot = 0;
+    for (int q = P.ntree - 1; q >= 0; --q) {
+        int hmax = -1;
+        for (int c = 0; c < P.nchild[q]; ++c) hmax = std::max(hmax, P.height[P.child[q][c]]);
+        P.height[q] = hmax + 1;
+        P.tleaf[q] = P.nchild[q] == 0 ? 1 : 0;
+    }
+    for (int q = 0; q < P.ntree; ++q) P.tslot[q] = (q > 0 && !P.tleaf[q]) ? slot++ : -1;
+    P.nslots = slot;
+    return TM_OK;
+}
+
+}  // namespace timest
+
+using namespace timest;
+
+extern "C" {
+
+void tm_config_default(tm_config *cfg)
+{
+    if (!cfg) return;
+    memset(cfg, 0, sizeof(*cfg));
+}
+
+int tm_create(tm_ctx **out, const tm_config *cfg, void *cuda_stream)
+{
+    if (!out) return TM_E_ARG;
+    *out = nullptr;
+    tm_ctx *ctx = new tm_ctx();
+    if (cfg) ctx->cfg = *cfg;
+    else tm_config_default(&ctx->cfg);
+    if ((ctx->cfg.alloc == nullptr) != (ctx->cfg.free == nullptr)) { delete ctx; return TM_E_ARG; }
+    ctx->device = ctx->cfg.device;
+    int rc = check_cuda(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (!rc) rc = check_cuda(ctx, cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device),
+                             "device attributes");
+    if (!rc) {
+        if (cuda_stream) ctx->stream = (cudaStream_t)cuda_stream;
+        else { rc = check_cuda(ctx, cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking), "stream"); ctx->own_stream = true; }
+    }
+    if (!rc) rc = check_cuda(ctx, cudaMallocHost((void **)&ctx->status_host, 64), "pinned status");
+    if (!rc) {
+        ctx->status = (uint32_t *)dalloc(ctx, 64);
+        if (!ctx->status) rc = TM_E_NOMEM;
+        else cudaMemsetAsync(ctx->status, 0, 64, ctx->stream);
+    }
+    if (rc) { tm_destroy(ctx); return rc; }
+    *out = ctx;
+    return TM_OK;
+}
+
+void tm_destroy(tm_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    free_input(ctx);
+    free_graph(ctx);
+    if (ctx->status) dfree(ctx, ctx->status, 64);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->status_host) cudaFreeHost(ctx->status_host);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *tm_last_error(tm_ctx *ctx)
+{
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+int tm_graph_load(tm_ctx *ctx, uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst, const int64_t *t,
+                  int flags)
+{
+    if (!ctx) return TM_E_ARG;
+    if (m && (!src || !dst || !t)) return set_err(ctx, TM_E_ARG, "null edge array");
+    if (n == 0 || n >= 0xFFFFFFFFu) return set_err(ctx, TM_E_LIMIT, "vertex count must be in [1, 2^32-2]");
+    if (m >= 0xFFFFFFFFull) return set_err(ctx, TM_E_LIMIT, "edge count must be below 2^32-1");
+    cudaSetDevice(ctx->device);
+    free_input(ctx);
+    free_graph(ctx);
+    ctx->epoch++;
+    ctx->loaded = false;
+    ctx->n = n;
+    ctx->m_in = m;
+    ctx->load_flags = flags;
+    if (m) {
+        ctx->in_src = (uint32_t *)dalloc(ctx, m * 4);
+        ctx->in_dst = (uint32_t *)dalloc(ctx, m * 4);
+        ctx->in_t = (int64_t *)dalloc(ctx, m * 8);
+        if (!ctx->in_src || !ctx->in_dst || !ctx->in_t) { free_input(ctx); return TM_E_NOMEM; }
+        cudaMemcpyKind kind = (flags & TM_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        cudaMemcpyAsync(ctx->in_src, src, m * 4, kind, ctx->stream);
+        cudaMemcpyAsync(ctx->in_dst, dst, m * 4, kind, ctx->stream);
+        cudaMemcpyAsync(ctx->in_t, t, m * 8, kind, ctx->stream);
+        int rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "graph copy");
+        if (rc) { free_input(ctx); return rc; }
+    }
+    ctx->loaded = true;
+    return TM_OK;
+}
+
+int tm_preprocess(tm_ctx *ctx)
+{
+    if (!ctx) return TM_E_ARG;
+    if (!ctx->loaded) return set_err(ctx, TM_E_STATE, "no graph loaded");
+    cudaSetDevice(ctx->device);
+    free_graph(ctx);
+    int rc = build_csr(ctx);
+    if (rc) { free_graph(ctx); return rc; }
+    free_input(ctx);
+    ctx->loaded = false;
+    ctx->preprocessed = true;
+    return TM_OK;
+}
+
+int tm_graph_info(tm_ctx *ctx, uint64_t *m, int64_t *t_min, int64_t *T)
+{
+    if (!ctx) return TM_E_ARG;
+    if (!ctx->preprocessed) return set_err(ctx, TM_E_STATE, "graph not preprocessed");
+    if (m) *m = ctx->g.m;
+    if (t_min) *t_min = ctx->g.tmin;
+    if (T) *T = ctx->g.T;
+    return TM_OK;
+}
+
+int tm_edges_export(tm_ctx *ctx, uint32_t *src, uint32_t *dst, uint32_t *tprime)
+{
+    if (!ctx) return TM_E_ARG;
+    if (!ctx->preprocessed) return set_err(ctx, TM_E_STATE, "graph not preprocessed");
+    size_t b = (size_t)ctx->g.m * 4;
+    if (b) {
+        if (src) cudaMemcpyAsync(src, ctx->g.g_src, b, cudaMemcpyDeviceToHost, ctx->stream);
+        if (dst) cudaMemcpyAsync(dst, ctx->g.g_dst, b, cudaMemcpyDeviceToHost, ctx->stream);
+        if (tprime) cudaMemcpyAsync(tprime, ctx->g.g_t, b, cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    return check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "edge export");
+}
+
+int tm_set_motif(tm_ctx *ctx, uint32_t nv, uint32_t ne, const uint32_t *edges, const uint32_t *order, int64_t delta,
+                 tm_motif **out)
+{
+    if (!ctx || !out || !edges || !order) return TM_E_ARG;
+    *out = nullptr;
+    if (nv < 2 || nv > (uint32_t)kMaxV || ne < nv - 1 || ne > (uint32_t)kMaxE)
+        return set_err(ctx, TM_E_MOTIF, "motif needs 2..8 vertices and nv-1..16 edges");
+    if (delta <= 0) return set_err(ctx, TM_E_MOTIF, "delta must be positive");
+    MotifDesc M;
+    M.nv = (int)nv; M.ne = (int)ne;
+    bool seen[kMaxE] = {};
+    for (uint32_t i = 0; i < ne; ++i) {
+        uint32_t a = edges[2 * i], b = edges[2 * i + 1];
+        if (a >= nv || b >= nv || a == b) return set_err(ctx, TM_E_MOTIF, "motif edge out of range or self loop");
+        if (order[i] >= ne || seen[order[i]]) return set_err(ctx, TM_E_MOTIF, "order is not a permutation");
+        seen[order[i]] = true;
+        M.a[i] = (int)a; M.b[i] = (int)b; M.rank[i] = (int)order[i];
+    }
+    int all[kMaxE];
+    for (int i = 0; i < M.ne; ++i) all[i] = i;
+    if (!connected(M, all, M.ne)) return set_err(ctx, TM_E_MOTIF, "motif is not connected");
+    int tree[kMaxTree], root;
+    default_tree(M, tree, &root);
+    tm_motif *mo = new tm_motif();
+    mo->ctx = ctx;
+    mo->nv = nv; mo->ne = ne; mo->delta = delta;
+    for (int i = 0; i < M.ne; ++i) { mo->ea[i] = M.a[i]; mo->eb[i] = M.b[i]; mo->rank[i] = M.rank[i]; }
+    for (int i = 0; i < M.nv - 1; ++i) mo->tree[i] = tree[i];
+    mo->root = root;
+    int rc = compile_plan(M, tree, root, delta, mo->plan);
+    if (rc) { delete mo; return set_err(ctx, rc, "internal: default tree did not compile"); }
+    *out = mo;
+    return TM_OK;
+}
+
+int tm_set_tree(tm_motif *mo, const uint32_t *tree_edge_ids, uint32_t root_edge)
+{
+    if (!mo || !tree_edge_ids) return TM_E_ARG;
+    MotifDesc M;
+    M.nv = (int)mo->nv; M.ne = (int)mo->ne;
+    for (int i = 0; i < M.ne; ++i) { M.a[i] = mo->ea[i]; M.b[i] = mo->eb[i]; M.rank[i] = mo->rank[i]; }
+    int tree[kMaxTree];
+    for (int i = 0; i < M.nv - 1; ++i) tree[i] = (int)tree_edge_ids[i];
+    if (!is_spanning_tree(M, tree)) return set_err(mo->ctx, TM_E_MOTIF, "edges do not form a spanning tree");
+    DevPlan P;
+    int rc = compile_plan(M, tree, (int)root_edge, mo->delta, P);
+    if (rc) return set_err(mo->ctx, rc, "root edge is not a tree edge");
+    release_weights(mo->ctx, mo);
+    mo->plan = P;
+    for (int i = 0; i < M.nv - 1; ++i) mo->tree[i] = tree[i];
+    mo->root = root_edge;
+    return TM_OK;
+}
+
+int tm_motif_plan(tm_motif *mo, int32_t *order, int32_t *parent)
+{
+    if (!mo) return TM_E_ARG;
+    for (int q = 0; q < mo->plan.ntree; ++q) {
+        if (order) order[q] = mo->plan.tedge[q];
+        if (parent) parent[q] = mo->plan.tparent[q];
+    }
+    return TM_OK;
+}
+
+int tm_weights(tm_ctx *ctx, tm_motif *mo, tm_u128 *W_out)
+{
+    if (!ctx || !mo || mo->ctx != ctx) return TM_E_ARG;
+    if (!ctx->preprocessed) return set_err(ctx, TM_E_STATE, "graph not preprocessed");
+    cudaSetDevice(ctx->device);
+    int rc = compute_weights(ctx, mo);
+    if (rc) { release_weights(ctx, mo); return rc; }
+    if (W_out) *W_out = mo->W;
+    return TM_OK;
+}
+
+static int need_weights(tm_ctx *ctx, tm_motif *mo)
+{
+    if (!ctx || !mo || mo->ctx != ctx) return TM_E_ARG;
+    if (!mo->have_weights || mo->graph_epoch != ctx->epoch || !ctx->preprocessed)
+        return set_err(ctx, TM_E_STATE, "weights not computed for the current graph");
+    return TM_OK;
+}
+
+int tm_weights_export(tm_ctx *ctx, tm_motif *mo, uint32_t tree_edge, uint32_t layer, uint64_t *host_out)
+{
+    int rc = need_weights(ctx, mo);
+    if (rc) return rc;
+    if (layer > 1 || !host_out) return set_err(ctx, TM_E_ARG, "bad layer or null output");
+    int q = -1;
+    for (int i = 0; i < mo->plan.ntree; ++i) if ((uint32_t)mo->plan.tedge[i] == tree_edge) q = i;
+    if (q < 0) return set_err(ctx, TM_E_ARG, "not a tree edge");
+    cudaSetDevice(ctx->device);
+    return export_weights(ctx, mo, q, (int)layer, host_out);
+}
+
+int tm_window_totals(tm_ctx *ctx, tm_motif *mo, uint64_t *host_out, uint64_t cap, uint64_t *nwin)
+{
+    int rc = need_weights(ctx, mo);
+    if (rc) return rc;
+    uint64_t nw = (uint64_t)ctx->g.T / (uint64_t)mo->plan.delta + 1;
+    if (ctx->g.m == 0) nw = 1;
+    if (nwin) *nwin = nw;
+    if (!host_out) return TM_OK;
+    // the device keeps the non-empty windows only: expand to the dense index
+    std::vector<uint64_t> wc(2 * ((size_t)mo->nwtot + 1));
+    std::vector<uint32_t> id0(mo->layer[0].nwin + 1), id1(mo->layer[1].nwin + 1);
+    cudaMemcpyAsync(wc.data(), mo->wcum, wc.size() * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(id0.data(), mo->layer[0].win_id, id0.size() * 4, cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(id1.data(), mo->layer[1].win_id, id1.size() * 4, cudaMemcpyDeviceToHost, ctx->stream);
+    rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "window totals");
+    if (rc) return rc;
+    for (uint64_t i = 0; i < std::min(cap, nw); ++i) host_out[i] = 0;
+    for (uint32_t k = 0; k < mo->nwtot; ++k) {
+        uint32_t i = k < mo->layer[0].nwin ? id0[k] : id1[k - mo->layer[0].nwin];
+        uint64_t tot = wc[2 * (k + 1)] - wc[2 * k];   // W_i < 2^64
+        if (i < cap) host_out[i] = tot;
+    }
+    return TM_OK;
+}
+
+int tm_sample(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first_index, tm_result *out)
+{
+    int rc = need_weights(ctx, mo);
+    if (rc) return rc;
+    if (!out) return set_err(ctx, TM_E_ARG, "null result");
+    cudaSetDevice(ctx->device);
+    return run_samples(ctx, mo, k, seed, first_index, out, nullptr, nullptr, nullptr);
+}
+
+int tm_sample_trace(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first_index, uint32_t *tree_gids,
+                    uint64_t *contrib, int32_t *reason, tm_result *out)
+{
+    int rc = need_weights(ctx, mo);
+    if (rc) return rc;
+    if (!out) return set_err(ctx, TM_E_ARG, "null result");
+    cudaSetDevice(ctx->device);
+    return run_samples(ctx, mo, k, seed, first_index, out, tree_gids, contrib, reason);
+}
+
+int tm_batch_run(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64_t *k, const uint64_t *seed,
+                 tm_result *out)
+{
+    if (!ctx || (nq && (!motifs || !k || !seed || !out))) return TM_E_ARG;
+    for (uint32_t q = 0; q < nq; ++q) {
+        int rc = need_weights(ctx, motifs[q]);
+        if (rc) return rc;
+    }
+    cudaSetDevice(ctx->device);
+    return run_batch(ctx, nq, motifs, k, seed, out);
+}
+
+void tm_motif_free(tm_motif *mo)
+{
+    if (!mo) return;
+    if (mo->ctx) {
+        cudaSetDevice(mo->ctx->device);
+        release_weights(mo->ctx, mo);
+        cudaStreamSynchronize(mo->ctx->stream);
+    }
+    delete mo;
+}
+
+}  // extern "C"

@@ -1,0 +1,476 @@
+// Temporal CSR builder (Sec. 3 preamble; Defs. 3.1-3.3).
+//
+// From m raw tuples (u, v, t) it builds, all on the device:
+//   GLOBAL order (t', src, dst)      -> gid, the edge id used everywhere
+//   out-lists   (src | t', dst)      -> out_off / out_t / out_nbr / out_gid
+//   in-lists    (dst | t', src)      -> in_off / in_t / in_nbr / in_gid
+//   multi-edge  (src, dst | t')      -> pairs, pair_off / multi_t / multi_gid
+// with t' = t - t_min.  Every ordering comes from a stable LSD radix sort
+// (8-bit digits) written here; the OUT and IN orders are stable re-sorts of
+// the GLOBAL order by one endpoint, and the multi-edge order is a stable
+// re-sort of the IN order by source.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "scan.cuh"
+#include "tm_device.cuh"
+#include "tm_internal.h"
+
+namespace timest {
+
+namespace {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int RS_WARPS = RS_THREADS / 32;
+
+__global__ void k_rs_hist(const uint32_t *__restrict__ keys, uint32_t n, int shift, uint32_t *__restrict__ hist,
+                          uint32_t ntiles)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    uint32_t base = blockIdx.x * RS_TILE;
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; ++j) {
+        uint32_t i = base + j * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter of one tile.  Tile order of item (j, warp, lane) is
+// j*256 + warp*32 + lane; an item's rank among equal digits is the number of
+// earlier (j', warp') groups' items with that digit plus the lanes before it
+// in its own warp (found with __match_any_sync).
+template <int NP>
+__global__ void k_rs_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ p0in,
+                             const uint32_t *__restrict__ p1in, uint32_t *__restrict__ kout,
+                             uint32_t *__restrict__ p0out, uint32_t *__restrict__ p1out, uint32_t n, int shift,
+                             const uint32_t *__restrict__ offs, uint32_t ntiles)
+{
+    __shared__ uint16_t cnt[RS_ITEMS][RS_WARPS][256];
+    __shared__ uint32_t tile_off[256];
+    uint16_t *flat = &cnt[0][0][0];
+    for (int i = threadIdx.x; i < RS_ITEMS * RS_WARPS * 256; i += RS_THREADS) flat[i] = 0;
+    tile_off[threadIdx.x] = offs[(size_t)threadIdx.x * ntiles + blockIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    uint32_t base = blockIdx.x * RS_TILE;
+    uint32_t key[RS_ITEMS], dig[RS_ITEMS];
+    uint8_t low[RS_ITEMS];
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; ++j) {
+        uint32_t i = base + j * RS_THREADS + threadIdx.x;
+        key[j] = (i < n) ? kin[i] : 0u;
+        dig[j] = (i < n) ? ((key[j] >> shift) & 255u) : 256u;
+        uint32_t peers = __match_any_sync(0xffffffffu, dig[j]);
+        low[j] = (uint8_t)__popc(peers & lt_mask);
+        if (dig[j] < 256u && lane == __ffs(peers) - 1) cnt[j][warp][dig[j]] = (uint16_t)__popc(peers);
+    }
+    __syncthreads();
+    {
+        uint32_t d = threadIdx.x, run = 0;
+        for (int j = 0; j < RS_ITEMS; ++j)
+            for (int w = 0; w < RS_WARPS; ++w) {
+                uint32_t c = cnt[j][w][d];
+                cnt[j][w][d] = (uint16_t)run;
+                run += c;
+            }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; ++j) {
+        uint32_t i = base + j * RS_THREADS + threadIdx.x;
+        if (i < n) {
+            uint32_t d = dig[j];
+            uint32_t pos = tile_off[d] + cnt[j][warp][d] + low[j];
+            kout[pos] = key[j];
+            if (NP >= 1) p0out[pos] = p0in[i];
+            if (NP >= 2) p1out[pos] = p1in[i];
+        }
+    }
+}
+
+int bits_for(uint64_t maxval)
+{
+    int b = 0;
+    while (b < 64 && (maxval >> b) != 0) ++b;
+    return b;
+}
+
+// Stable LSD sort of (key, p0[, p1]) by the low `bits` bits of key.  The
+// arrays are ping-ponged through the scratch buffers; on return the sorted
+// data is in key/p0/p1 (the caller's buffers).
+int radix_sort(tm_ctx *ctx, uint32_t *key, uint32_t *p0, uint32_t *p1, uint32_t n, int bits)
+{
+    if (n <= 1 || bits <= 0) return TM_OK;
+    int np = p1 ? 2 : (p0 ? 1 : 0);
+    uint32_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+    size_t hbytes = (size_t)ntiles * 256 * sizeof(uint32_t);
+    uint32_t *hist = (uint32_t *)dalloc(ctx, hbytes);
+    uint32_t *k2 = (uint32_t *)dalloc(ctx, (size_t)n * 4);
+    uint32_t *a2 = np >= 1 ? (uint32_t *)dalloc(ctx, (size_t)n * 4) : nullptr;
+    uint32_t *b2 = np >= 2 ? (uint32_t *)dalloc(ctx, (size_t)n * 4) : nullptr;
+    int rc = TM_OK;
+    if (!hist || !k2 || (np >= 1 && !a2) || (np >= 2 && !b2)) rc = TM_E_NOMEM;
+    uint32_t *ki = key, *ai = p0, *bi = p1, *ko = k2, *ao = a2, *bo = b2;
+    int passes = (bits + 7) / 8;
+    for (int pass = 0; pass < passes && rc == TM_OK; ++pass) {
+        int shift = pass * 8;
+        k_rs_hist<<<ntiles, RS_THREADS, 0, ctx->stream>>>(ki, n, shift, hist, ntiles);
+        rc = exclusive_scan_u32(ctx, hist, hist, (uint64_t)ntiles * 256, nullptr);
+        if (rc != TM_OK) break;
+        if (np == 0)
+            k_rs_scatter<0><<<ntiles, RS_THREADS, 0, ctx->stream>>>(ki, nullptr, nullptr, ko, nullptr, nullptr, n,
+                                                                     shift, hist, ntiles);
+        else if (np == 1)
+            k_rs_scatter<1><<<ntiles, RS_THREADS, 0, ctx->stream>>>(ki, ai, nullptr, ko, ao, nullptr, n, shift, hist,
+                                                                     ntiles);
+        else
+            k_rs_scatter<2><<<ntiles, RS_THREADS, 0, ctx->stream>>>(ki, ai, bi, ko, ao, bo, n, shift, hist, ntiles);
+        rc = check_cuda(ctx, cudaGetLastError(), "radix scatter");
+        std::swap(ki, ko); std::swap(ai, ao); std::swap(bi, bo);
+    }
+    if (rc == TM_OK && ki != key) {
+        cudaMemcpyAsync(key, ki, (size_t)n * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+        if (np >= 1) cudaMemcpyAsync(p0, ai, (size_t)n * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+        if (np >= 2) cudaMemcpyAsync(p1, bi, (size_t)n * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+    }
+    dfree(ctx, hist, hbytes);
+    dfree(ctx, k2, (size_t)n * 4);
+    if (a2) dfree(ctx, a2, (size_t)n * 4);
+    if (b2) dfree(ctx, b2, (size_t)n * 4);
+    return rc;
+}
+
+// ---- input validation and t' -------------------------------------------
+struct Stats {
+    long long tmin, tmax;
+    unsigned long long nself, nbad;
+};
+
+__global__ void k_input_stats(const uint32_t *__restrict__ src, const uint32_t *__restrict__ dst,
+                              const int64_t *__restrict__ t, uint64_t m, uint32_t n, Stats *st)
+{
+    long long lo = LLONG_MAX, hi = LLONG_MIN;
+    unsigned long long ns = 0, nb = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t u = src[i], v = dst[i];
+        if (u >= n || v >= n) { ++nb; continue; }
+        if (u == v) { ++ns; continue; }
+        long long x = t[i];
+        lo = x < lo ? x : lo;
+        hi = x > hi ? x : hi;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        long long a = __shfl_down_sync(0xffffffffu, lo, o), b = __shfl_down_sync(0xffffffffu, hi, o);
+        lo = a < lo ? a : lo; hi = b > hi ? b : hi;
+        ns += __shfl_down_sync(0xffffffffu, ns, o);
+        nb += __shfl_down_sync(0xffffffffu, nb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (lo != LLONG_MAX) atomicMin(&st->tmin, lo);
+        if (hi != LLONG_MIN) atomicMax(&st->tmax, hi);
+        if (ns) atomicAdd(&st->nself, ns);
+        if (nb) atomicAdd(&st->nbad, nb);
+    }
+}
+
+// keep flags for self-loop dropping
+__global__ void k_keep_nonself(const uint32_t *__restrict__ src, const uint32_t *__restrict__ dst, uint64_t m,
+                               uint32_t *__restrict__ keep)
+{
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) keep[i] = src[i] != dst[i] ? 1u : 0u;
+}
+
+// Compact the kept tuples into (t', src, dst) u32 arrays.
+__global__ void k_compact_input(const uint32_t *__restrict__ src, const uint32_t *__restrict__ dst,
+                                const int64_t *__restrict__ t, uint64_t m, const uint32_t *__restrict__ keep,
+                                const uint32_t *__restrict__ pos, long long tmin, uint32_t *__restrict__ ot,
+                                uint32_t *__restrict__ os, uint32_t *__restrict__ od)
+{
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    if (keep && !keep[i]) return;
+    uint32_t p = pos ? pos[i] : (uint32_t)i;
+    ot[p] = (uint32_t)(t[i] - tmin);
+    os[p] = src[i];
+    od[p] = dst[i];
+}
+
+// After the GLOBAL sort: flag tuples equal to their predecessor.
+__global__ void k_flag_unique(const uint32_t *__restrict__ t, const uint32_t *__restrict__ s,
+                              const uint32_t *__restrict__ d, uint32_t m, uint32_t *__restrict__ keep,
+                              unsigned long long *ndup)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    bool dup = i > 0 && t[i] == t[i - 1] && s[i] == s[i - 1] && d[i] == d[i - 1];
+    keep[i] = dup ? 0u : 1u;
+    if (dup) atomicAdd(ndup, 1ull);
+}
+
+__global__ void k_compact3(const uint32_t *__restrict__ a, const uint32_t *__restrict__ b,
+                           const uint32_t *__restrict__ c, uint32_t m, const uint32_t *__restrict__ keep,
+                           const uint32_t *__restrict__ pos, uint32_t *__restrict__ oa, uint32_t *__restrict__ ob,
+                           uint32_t *__restrict__ oc)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m || !keep[i]) return;
+    uint32_t p = pos[i];
+    oa[p] = a[i]; ob[p] = b[i]; oc[p] = c[i];
+}
+
+__global__ void k_iota(uint32_t *__restrict__ a, uint32_t m)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) a[i] = i;
+}
+
+__global__ void k_gather2(const uint32_t *__restrict__ idx, uint32_t m, const uint32_t *__restrict__ x,
+                          const uint32_t *__restrict__ y, uint32_t *__restrict__ ox, uint32_t *__restrict__ oy)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    uint32_t g = idx[i];
+    ox[i] = x[g];
+    if (y) oy[i] = y[g];
+}
+
+// off[v] = first position whose sorted key is >= v, for v in [0, n].
+__global__ void k_offsets(const uint32_t *__restrict__ keys, uint32_t m, uint32_t n, uint32_t *__restrict__ off)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > m) return;
+    uint32_t lo = (i == 0) ? 0u : keys[i - 1] + 1u;
+    uint32_t hi = (i == m) ? n : keys[i];
+    for (uint32_t v = lo; v <= hi && v <= n; ++v) off[v] = i;
+}
+
+// Pair heads in the multi-edge order (src from the sorted keys, dst gathered).
+__global__ void k_pair_heads(const uint32_t *__restrict__ msrc, const uint32_t *__restrict__ mdst, uint32_t m,
+                             uint32_t *__restrict__ head)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    head[i] = (i == 0 || msrc[i] != msrc[i - 1] || mdst[i] != mdst[i - 1]) ? 1u : 0u;
+}
+
+__global__ void k_pair_fill(const uint32_t *__restrict__ msrc, const uint32_t *__restrict__ mdst,
+                            const uint32_t *__restrict__ mgid, const uint32_t *__restrict__ head,
+                            const uint32_t *__restrict__ pid_excl, uint32_t m, uint32_t *__restrict__ pair_off,
+                            uint32_t *__restrict__ pair_src, uint32_t *__restrict__ pair_dst,
+                            uint32_t *__restrict__ g_pair)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    uint32_t pid = pid_excl[i] + head[i] - 1u;
+    if (head[i]) {
+        pair_off[pid] = i;
+        pair_src[pid] = msrc[i];
+        pair_dst[pid] = mdst[i];
+    }
+    g_pair[mgid[i]] = pid;
+}
+
+__global__ void k_rev_pairs(const uint32_t *__restrict__ pair_src, const uint32_t *__restrict__ pair_dst,
+                            const uint32_t *__restrict__ vpair_off, uint32_t np, uint32_t *__restrict__ rev)
+{
+    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    uint32_t u = pair_src[p], v = pair_dst[p];
+    uint32_t lo = vpair_off[v], hi = vpair_off[v + 1];
+    uint32_t r = lower_idx(pair_dst, lo, hi, u);
+    rev[p] = (r < hi && pair_dst[r] == u) ? r : kNone;
+}
+
+inline unsigned blocks_for(uint64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+static uint32_t *galloc(tm_ctx *ctx, size_t count)
+{
+    size_t bytes = (count ? count : 1) * sizeof(uint32_t);
+    uint32_t *p = (uint32_t *)dalloc(ctx, bytes);
+    if (p) ctx->graph_bufs.push_back({p, bytes});
+    return p;
+}
+
+int build_csr(tm_ctx *ctx)
+{
+    const int TB = 256;
+    cudaStream_t st = ctx->stream;
+    uint64_t m0 = ctx->m_in;
+    uint32_t n = ctx->n;
+    DevGraph &g = ctx->g;
+    g = DevGraph();
+    g.n = n;
+    int rc = TM_OK;
+    // ---- statistics: t range, self loops, bad ids
+    Stats hs{LLONG_MAX, LLONG_MIN, 0, 0};
+    Stats *ds = (Stats *)dalloc(ctx, sizeof(Stats));
+    if (!ds) return TM_E_NOMEM;
+    cudaMemcpyAsync(ds, &hs, sizeof(Stats), cudaMemcpyHostToDevice, st);
+    if (m0) {
+        unsigned nb = std::min<uint64_t>(blocks_for(m0, TB), (uint64_t)ctx->num_sms * 8);
+        k_input_stats<<<nb, TB, 0, st>>>(ctx->in_src, ctx->in_dst, ctx->in_t, m0, n, ds);
+    }
+    cudaMemcpyAsync(&hs, ds, sizeof(Stats), cudaMemcpyDeviceToHost, st);
+    rc = check_cuda(ctx, cudaStreamSynchronize(st), "input statistics");
+    dfree(ctx, ds, sizeof(Stats));
+    if (rc) return rc;
+    if (hs.nbad) return set_err(ctx, TM_E_ARG, "vertex id >= n in input");
+    if (hs.nself && !(ctx->load_flags & TM_DROP_SELF))
+        return set_err(ctx, TM_E_SELFLOOP, "input has self loops (pass TM_DROP_SELF to drop them)");
+    uint64_t m1 = m0 - hs.nself;
+    if (m1 >= 0xFFFFFFFFull) return set_err(ctx, TM_E_LIMIT, "more than 2^32-2 edges");
+    long long tmin = m1 ? hs.tmin : 0, tmax = m1 ? hs.tmax : 0;
+    if ((unsigned long long)(tmax - tmin) >= 0xFFFFFFFFull)
+        return set_err(ctx, TM_E_LIMIT, "time span t_max - t_min must be below 2^32 - 1");
+    uint32_t m = (uint32_t)m1;
+    // ---- compact to (t', src, dst)
+    uint32_t *T0 = (uint32_t *)dalloc(ctx, (size_t)(m ? m : 1) * 4);
+    uint32_t *S0 = (uint32_t *)dalloc(ctx, (size_t)(m ? m : 1) * 4);
+    uint32_t *D0 = (uint32_t *)dalloc(ctx, (size_t)(m ? m : 1) * 4);
+    if (!T0 || !S0 || !D0) return TM_E_NOMEM;
+    if (hs.nself) {
+        uint32_t *keep = (uint32_t *)dalloc(ctx, m0 * 4), *pos = (uint32_t *)dalloc(ctx, m0 * 4);
+        if (!keep || !pos) return TM_E_NOMEM;
+        k_keep_nonself<<<blocks_for(m0, TB), TB, 0, st>>>(ctx->in_src, ctx->in_dst, m0, keep);
+        rc = exclusive_scan_u32(ctx, keep, pos, m0, nullptr);
+        if (rc) return rc;
+        k_compact_input<<<blocks_for(m0, TB), TB, 0, st>>>(ctx->in_src, ctx->in_dst, ctx->in_t, m0, keep, pos, tmin,
+                                                           T0, S0, D0);
+        dfree(ctx, keep, m0 * 4);
+        dfree(ctx, pos, m0 * 4);
+    } else if (m) {
+        k_compact_input<<<blocks_for(m0, TB), TB, 0, st>>>(ctx->in_src, ctx->in_dst, ctx->in_t, m0, nullptr, nullptr,
+                                                           tmin, T0, S0, D0);
+    }
+    // ---- GLOBAL order: LSD by dst, then src, then t'
+    int vbits = bits_for(n ? n - 1 : 0);
+    int tbits = bits_for((uint64_t)(tmax - tmin));
+    rc = radix_sort(ctx, D0, S0, T0, m, vbits);
+    if (!rc) rc = radix_sort(ctx, S0, D0, T0, m, vbits);
+    if (!rc) rc = radix_sort(ctx, T0, S0, D0, m, tbits);
+    if (rc) return rc;
+    // ---- duplicates
+    {
+        uint32_t *keep = (uint32_t *)dalloc(ctx, (size_t)(m ? m : 1) * 4);
+        unsigned long long *nd = (unsigned long long *)dalloc(ctx, 8);
+        if (!keep || !nd) return TM_E_NOMEM;
+        cudaMemsetAsync(nd, 0, 8, st);
+        if (m) k_flag_unique<<<blocks_for(m, TB), TB, 0, st>>>(T0, S0, D0, m, keep, nd);
+        unsigned long long ndup = 0;
+        cudaMemcpyAsync(&ndup, nd, 8, cudaMemcpyDeviceToHost, st);
+        rc = check_cuda(ctx, cudaStreamSynchronize(st), "duplicate scan");
+        dfree(ctx, nd, 8);
+        if (rc) return rc;
+        if (ndup && !(ctx->load_flags & TM_DEDUP)) {
+            dfree(ctx, keep, (size_t)(m ? m : 1) * 4);
+            return set_err(ctx, TM_E_DUP, "input repeats a (u,v,t) tuple (pass TM_DEDUP to drop repeats)");
+        }
+        g.g_t = galloc(ctx, m - ndup); g.g_src = galloc(ctx, m - ndup); g.g_dst = galloc(ctx, m - ndup);
+        if (!g.g_t || !g.g_src || !g.g_dst) return TM_E_NOMEM;
+        if (ndup) {
+            uint32_t *pos = (uint32_t *)dalloc(ctx, (size_t)m * 4);
+            if (!pos) return TM_E_NOMEM;
+            rc = exclusive_scan_u32(ctx, keep, pos, m, nullptr);
+            if (rc) return rc;
+            k_compact3<<<blocks_for(m, TB), TB, 0, st>>>(T0, S0, D0, m, keep, pos, g.g_t, g.g_src, g.g_dst);
+            dfree(ctx, pos, (size_t)m * 4);
+        } else if (m) {
+            cudaMemcpyAsync(g.g_t, T0, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(g.g_src, S0, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(g.g_dst, D0, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
+        }
+        dfree(ctx, keep, (size_t)(m ? m : 1) * 4);
+        m = (uint32_t)(m - ndup);
+    }
+    g.m = m;
+    g.tmin = tmin;
+    g.T = (uint32_t)(tmax - tmin);
+    // scratch key buffer (reuse S0/D0/T0 as work space)
+    uint32_t *key = S0, *tmp = D0;
+    // ---- OUT order: stable sort of gid by src
+    g.out_gid = galloc(ctx, m); g.out_t = galloc(ctx, m); g.out_nbr = galloc(ctx, m); g.out_off = galloc(ctx, (size_t)n + 1);
+    g.in_gid = galloc(ctx, m); g.in_t = galloc(ctx, m); g.in_nbr = galloc(ctx, m); g.in_off = galloc(ctx, (size_t)n + 1);
+    if (!g.out_gid || !g.out_t || !g.out_nbr || !g.out_off || !g.in_gid || !g.in_t || !g.in_nbr || !g.in_off)
+        return TM_E_NOMEM;
+    if (m) {
+        cudaMemcpyAsync(key, g.g_src, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
+        k_iota<<<blocks_for(m, TB), TB, 0, st>>>(g.out_gid, m);
+        rc = radix_sort(ctx, key, g.out_gid, nullptr, m, vbits);
+        if (rc) return rc;
+        k_gather2<<<blocks_for(m, TB), TB, 0, st>>>(g.out_gid, m, g.g_t, g.g_dst, g.out_t, g.out_nbr);
+    }
+    k_offsets<<<blocks_for((uint64_t)m + 1, TB), TB, 0, st>>>(key, m, n, g.out_off);
+    // ---- IN order: stable sort of gid by dst
+    if (m) {
+        cudaMemcpyAsync(key, g.g_dst, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
+        k_iota<<<blocks_for(m, TB), TB, 0, st>>>(g.in_gid, m);
+        rc = radix_sort(ctx, key, g.in_gid, nullptr, m, vbits);
+        if (rc) return rc;
+        k_gather2<<<blocks_for(m, TB), TB, 0, st>>>(g.in_gid, m, g.g_t, g.g_src, g.in_t, g.in_nbr);
+    }
+    k_offsets<<<blocks_for((uint64_t)m + 1, TB), TB, 0, st>>>(key, m, n, g.in_off);
+    // ---- multi-edge order: stable re-sort of the IN order by source
+    g.multi_gid = galloc(ctx, m); g.multi_t = galloc(ctx, m); g.g_pair = galloc(ctx, m);
+    g.vpair_off = galloc(ctx, (size_t)n + 1);
+    if (!g.multi_gid || !g.multi_t || !g.g_pair || !g.vpair_off) return TM_E_NOMEM;
+    uint32_t np = 0;
+    if (m) {
+        cudaMemcpyAsync(key, g.in_nbr, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(g.multi_gid, g.in_gid, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
+        rc = radix_sort(ctx, key, g.multi_gid, nullptr, m, vbits);
+        if (rc) return rc;
+        k_gather2<<<blocks_for(m, TB), TB, 0, st>>>(g.multi_gid, m, g.g_t, g.g_dst, g.multi_t, tmp);
+        // key = pair src, tmp = pair dst per multi position
+        uint32_t *head = T0;
+        uint32_t *pid = (uint32_t *)dalloc(ctx, (size_t)m * 4);
+        uint32_t *dnp = (uint32_t *)dalloc(ctx, 4);
+        if (!pid || !dnp) return TM_E_NOMEM;
+        k_pair_heads<<<blocks_for(m, TB), TB, 0, st>>>(key, tmp, m, head);
+        rc = exclusive_scan_u32(ctx, head, pid, m, dnp);
+        if (rc) return rc;
+        // total = pid[m-1] + head[m-1]; the scan wrote the exclusive total
+        cudaMemcpyAsync(&np, dnp, 4, cudaMemcpyDeviceToHost, st);
+        rc = check_cuda(ctx, cudaStreamSynchronize(st), "pair count");
+        if (rc) return rc;
+        g.npairs = np;
+        g.pair_off = galloc(ctx, (size_t)np + 1);
+        g.pair_dst = galloc(ctx, np);
+        g.rev_pair = galloc(ctx, np);
+        uint32_t *pair_src = (uint32_t *)dalloc(ctx, (size_t)(np ? np : 1) * 4);
+        if (!g.pair_off || !g.pair_dst || !g.rev_pair || !pair_src) return TM_E_NOMEM;
+        k_pair_fill<<<blocks_for(m, TB), TB, 0, st>>>(key, tmp, g.multi_gid, head, pid, m, g.pair_off, pair_src,
+                                                      g.pair_dst, g.g_pair);
+        cudaMemcpyAsync(g.pair_off + np, &m, 4, cudaMemcpyHostToDevice, st);
+        k_offsets<<<blocks_for((uint64_t)np + 1, TB), TB, 0, st>>>(pair_src, np, n, g.vpair_off);
+        k_rev_pairs<<<blocks_for(np, TB), TB, 0, st>>>(pair_src, g.pair_dst, g.vpair_off, np, g.rev_pair);
+        rc = check_cuda(ctx, cudaStreamSynchronize(st), "pair tables");
+        dfree(ctx, pair_src, (size_t)(np ? np : 1) * 4);
+        dfree(ctx, pid, (size_t)m * 4);
+        dfree(ctx, dnp, 4);
+        if (rc) return rc;
+    } else {
+        g.pair_off = galloc(ctx, 1);
+        g.pair_dst = galloc(ctx, 1);
+        g.rev_pair = galloc(ctx, 1);
+        cudaMemsetAsync(g.pair_off, 0, 4, st);
+        k_offsets<<<1, TB, 0, st>>>(key, 0, n, g.vpair_off);
+    }
+    dfree(ctx, T0, (size_t)(m0 ? m0 : 1) * 4 > (size_t)(m1 ? m1 : 1) * 4 ? (size_t)(m1 ? m1 : 1) * 4 : (size_t)(m1 ? m1 : 1) * 4);
+    dfree(ctx, S0, (size_t)(m1 ? m1 : 1) * 4);
+    dfree(ctx, D0, (size_t)(m1 ? m1 : 1) * 4);
+    return check_cuda(ctx, cudaStreamSynchronize(st), "CSR build");
+}
+
+}  // namespace timest

@@ -1,0 +1,429 @@
+// Sampler, validator and DeriveCnt of TIMEST (Sec. 3.2-3.4; Alg. 3-6).
+//
+// Sample j draws from its own counter-based stream (Philox4x32-10, key =
+// seed, counter = (j, draw number)): a window with probability W_i / W, a
+// root edge with probability w_c / W_i (inverse CDF by binary search), then
+// each tree edge in breadth-first order from its candidate list L (Claim
+// 3.1) with probability proportional to its weight.  L is the meeting
+// vertex's out/in-list in a time range minus one multi-edge list; the pick
+// is a binary search over positions of the out/in-list whose cumulative
+// weight (minus the excluded entries before it, found by a nested search in
+// the multi-edge list) first exceeds the draw, so no list is materialised.
+// The sample is then validated (Alg. 4) and its completions to the motif
+// counted (Alg. 5) by a merge over the non-tree edges' multi-edge lists.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "tm_device.cuh"
+#include "tm_internal.h"
+
+namespace timest {
+
+namespace {
+
+struct EdgeRec {
+    uint32_t src, dst, t, pair, gid;
+};
+
+struct Acc {
+    unsigned long long hits_lo, hits_hi, valid, rv, rd, ro;
+};
+
+__device__ __forceinline__ EdgeRec load_edge(const DevGraph &g, uint32_t gid)
+{
+    EdgeRec r;
+    r.gid = gid;
+    r.src = __ldg(g.g_src + gid);
+    r.dst = __ldg(g.g_dst + gid);
+    r.t = __ldg(g.g_t + gid);
+    r.pair = __ldg(g.g_pair + gid);
+    return r;
+}
+
+// Multi-edge list range of pair (u, v), or an empty range.
+__device__ __forceinline__ void find_pair(const DevGraph &g, uint32_t u, uint32_t v, uint32_t &beg, uint32_t &end)
+{
+    uint32_t lo = __ldg(g.vpair_off + u), hi = __ldg(g.vpair_off + u + 1);
+    uint32_t p = lower_idx(g.pair_dst, lo, hi, v);
+    if (p < hi && __ldg(g.pair_dst + p) == v) {
+        beg = __ldg(g.pair_off + p);
+        end = __ldg(g.pair_off + p + 1);
+    } else {
+        beg = end = 0;
+    }
+}
+
+// DeriveCnt (Alg. 5): the number of ways to map the non-tree motif edges to
+// edges of their multi-edge lists so that all times strictly increase along
+// pi and span at most delta.  Lists are merged in time order (ties: later pi
+// position first); acc[q] counts the increasing chains over positions 0..q
+// that end at an element already passed.
+__device__ uint64_t derive_count(const DevGraph &g, const DevPlan &P, const uint32_t *phiV, const uint32_t *tnode_t,
+                                 const int32_t *tnode_of_edge, uint32_t tmin_tree, uint32_t tmax_tree, bool &ovf)
+{
+    const int ne = P.ne;
+    const int64_t d = P.delta;
+    uint32_t cur[kMaxE], end[kMaxE], fixed_t[kMaxE];
+    bool is_fixed[kMaxE];
+    // lower bound of every time: tmax_tree - d; upper: tmin_tree + d
+    uint64_t glo = (int64_t)tmax_tree >= d ? (uint64_t)((int64_t)tmax_tree - d) : 0;
+    uint64_t ghi = (uint64_t)tmin_tree + (uint64_t)d;
+    // previous / next tree times along pi for each position
+    int64_t prev_t = -1;
+    for (int pos = 0; pos < ne; ++pos) {
+        int e = P.pos_edge[pos];
+        int q = tnode_of_edge[e];
+        if (q >= 0) {
+            is_fixed[pos] = true;
+            fixed_t[pos] = tnode_t[q];
+            cur[pos] = 0; end[pos] = 1;
+            prev_t = tnode_t[q];
+        } else {
+            is_fixed[pos] = false;
+            uint32_t b, en;
+            find_pair(g, phiV[P.ea[e]], phiV[P.eb[e]], b, en);
+            uint64_t lo = glo;
+            if (prev_t >= 0 && (uint64_t)prev_t + 1 > lo) lo = (uint64_t)prev_t + 1;
+            cur[pos] = lower_idx(g.multi_t, b, en, lo);
+            end[pos] = en;
+            fixed_t[pos] = 0;
+        }
+    }
+    // clip each non-tree list at the next tree time (exclusive) and at ghi
+    int64_t next_t = -1;
+    for (int pos = ne - 1; pos >= 0; --pos) {
+        if (is_fixed[pos]) { next_t = fixed_t[pos]; continue; }
+        uint64_t hi = ghi;
+        if (next_t >= 0 && (uint64_t)next_t - 1 < hi) hi = (uint64_t)next_t - 1;
+        if (next_t == 0) { end[pos] = cur[pos]; continue; }
+        end[pos] = lower_idx(g.multi_t, cur[pos], end[pos], hi + 1);
+        if (cur[pos] >= end[pos]) return 0;
+    }
+    const bool coupled = !is_fixed[0] && !is_fixed[ne - 1];
+    uint64_t total = 0;
+    uint32_t first_beg = cur[0], first_end = end[0];
+    uint32_t nfirst = coupled ? first_end - first_beg : 1;
+    for (uint32_t f = 0; f < nfirst; ++f) {
+        uint32_t c[kMaxE], en[kMaxE];
+        uint64_t acc[kMaxE];
+        uint64_t cap = ghi;
+        for (int pos = 0; pos < ne; ++pos) { c[pos] = cur[pos]; en[pos] = end[pos]; acc[pos] = 0; }
+        if (coupled) {
+            c[0] = first_beg + f;
+            en[0] = c[0] + 1;
+            uint64_t x = __ldg(g.multi_t + c[0]);
+            cap = x + (uint64_t)d;
+        }
+        for (;;) {
+            int best = -1;
+            uint64_t bt = ~0ull;
+            for (int pos = 0; pos < ne; ++pos) {
+                if (c[pos] >= en[pos]) continue;
+                uint64_t tp = is_fixed[pos] ? fixed_t[pos] : __ldg(g.multi_t + c[pos]);
+                if (tp <= bt) { bt = tp; best = pos; }
+            }
+            if (best < 0 || bt > cap) break;
+            uint64_t add = best == 0 ? 1 : acc[best - 1];
+            acc[best] = add_chk(acc[best], add, ovf);
+            c[best]++;
+        }
+        total = add_chk(total, acc[ne - 1], ovf);
+    }
+    return total;
+}
+
+// One sample: returns 0 valid, 1/2/3 reject reasons, or -1 on an internal
+// inconsistency (latched as ST_BADSTATE).
+__device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &J, uint64_t seed, uint64_t j,
+                          uint32_t *status, uint64_t &contrib, uint32_t *tg_out)
+{
+    SampleRng rng;
+    rng.init(seed, j);
+    contrib = 0;
+    const u128 W = (u128)J.W_lo | ((u128)J.W_hi << 64);
+    u128 r = rng.below128(W, status);
+    // window: last k with wcum[k] <= r
+    uint32_t lo = 0, hi = J.nwtot;   // answer in [0, nwtot)
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        u128 c = (u128)__ldg(J.wcum + 2 * (size_t)mid) | ((u128)__ldg(J.wcum + 2 * (size_t)mid + 1) << 64);
+        if (c <= r) lo = mid; else hi = mid;
+    }
+    uint32_t k = lo;
+    u128 ck = (u128)__ldg(J.wcum + 2 * (size_t)k) | ((u128)__ldg(J.wcum + 2 * (size_t)k + 1) << 64);
+    uint64_t rr = (uint64_t)(r - ck);
+    const int p = k < J.nw0 ? 0 : 1;
+    const uint32_t kk = p ? k - J.nw0 : k;
+    const uint32_t *wb = p ? J.win_beg1 : J.win_beg0;
+    const uint64_t *cdf = p ? J.root_cdf1 : J.root_cdf0;
+    const uint32_t wbeg = __ldg(wb + kk), wend = __ldg(wb + kk + 1);
+    const uint64_t wi = __ldg((p ? J.win_id1 : J.win_id0) + kk);
+    const int64_t d = P.delta;
+    const uint64_t wlo = wi * (uint64_t)d, whi = (wi + 2) * (uint64_t)d - 1;
+    uint32_t root = upper_idx64(cdf, wbeg, wend, rr);
+    if (root >= wend) { latch(status, ST_BADSTATE); return -1; }
+    EdgeRec rec[kMaxTree];
+    rec[0] = load_edge(g, root);
+    for (int q = 1; q < P.ntree; ++q) {
+        const EdgeRec &par = rec[P.tparent[q]];
+        const bool zs = P.tzside[q] != 0, out = P.tout[q] != 0, leaf = P.tleaf[q] != 0;
+        const uint32_t zg = zs ? par.dst : par.src;
+        const uint32_t og = zs ? par.src : par.dst;
+        uint64_t tlo, thi;
+        if (P.tlater[q]) { tlo = (uint64_t)par.t + 1; thi = (uint64_t)par.t + (uint64_t)d; }
+        else {
+            if (par.t == 0) { latch(status, ST_BADSTATE); return -1; }
+            tlo = (uint64_t)par.t >= (uint64_t)d ? (uint64_t)par.t - (uint64_t)d : 0;
+            thi = (uint64_t)par.t - 1;
+        }
+        tlo = tlo < wlo ? wlo : tlo;
+        thi = thi > whi ? whi : thi;
+        const uint32_t *off = out ? g.out_off : g.in_off;
+        const uint32_t *tarr = out ? g.out_t : g.in_t;
+        const uint32_t *nbr = out ? g.out_nbr : g.in_nbr;
+        const uint32_t *gids = out ? g.out_gid : g.in_gid;
+        const uint32_t beg = __ldg(off + zg), endv = __ldg(off + zg + 1);
+        const uint32_t a = lower_idx(tarr, beg, endv, tlo);
+        const uint32_t b = lower_idx(tarr, a, endv, thi + 1);
+        const uint32_t pe = (out == !zs) ? par.pair : __ldg(g.rev_pair + par.pair);
+        uint32_t ea = 0, eb = 0, pb = 0;
+        if (pe != kNone) {
+            pb = __ldg(g.pair_off + pe);
+            const uint32_t pend = __ldg(g.pair_off + pe + 1);
+            ea = lower_idx(g.multi_t, pb, pend, tlo);
+            eb = lower_idx(g.multi_t, ea, pend, thi + 1);
+        }
+        const int slot = P.tslot[q];
+        const uint64_t *Pd = nullptr, *Pm = nullptr;
+        uint64_t base = 0, base_m = 0, total;
+        if (leaf) {
+            total = (uint64_t)(b - a) - (uint64_t)(eb - ea);
+        } else {
+            Pd = p ? J.pref_dir1[slot] : J.pref_dir0[slot];
+            Pm = p ? J.pref_multi1[slot] : J.pref_multi0[slot];
+            base = (a > beg && (uint64_t)__ldg(tarr + a - 1) >= wlo) ? __ldg(Pd + a - 1) : 0;
+            base_m = (ea > pb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo) ? __ldg(Pm + ea - 1) : 0;
+            uint64_t sr = b > a ? __ldg(Pd + b - 1) - base : 0;
+            uint64_t se = eb > ea ? __ldg(Pm + eb - 1) - base_m : 0;
+            total = sr - se;
+        }
+        if (total == 0 || b <= a) { latch(status, ST_BADSTATE); return -1; }
+        const uint64_t rc = rng.below(total, status);
+        // smallest x in [a, b) with F(x) > rc, F(x) = weight of the
+        // non-excluded entries in [a, x]
+        uint32_t xl = a, xh = b - 1;
+        while (xl < xh) {
+            uint32_t x = xl + ((xh - xl) >> 1);
+            const uint32_t tx = __ldg(tarr + x), nx = __ldg(nbr + x);
+            uint32_t ce = lower_idx(g.multi_t, ea, eb, tx) - ea;
+            if (ea + ce < eb && __ldg(g.multi_t + ea + ce) == tx && og <= nx) ++ce;
+            uint64_t F;
+            if (leaf) F = (uint64_t)(x - a + 1) - ce;
+            else F = (__ldg(Pd + x) - base) - (ce ? __ldg(Pm + ea + ce - 1) - base_m : 0);
+            if (F > rc) xh = x; else xl = x + 1;
+        }
+        const uint32_t x = xl;
+        const uint32_t cg = __ldg(gids + x);
+        EdgeRec cr;
+        cr.gid = cg;
+        cr.t = __ldg(tarr + x);
+        const uint32_t other = __ldg(nbr + x);
+        cr.src = out ? zg : other;
+        cr.dst = out ? other : zg;
+        cr.pair = __ldg(g.g_pair + cg);
+        rec[q] = cr;
+    }
+    if (tg_out)
+        for (int q = 0; q < P.ntree; ++q) tg_out[q] = rec[q].gid;
+    // ---- validation (Alg. 4): 1-1 vertex map, delta span, pi order
+    uint32_t phiV[kMaxV];
+    uint32_t tnode_t[kMaxTree];
+    int32_t tnode_of_edge[kMaxE];
+    for (int e = 0; e < P.ne; ++e) tnode_of_edge[e] = -1;
+    uint32_t tmin = 0xFFFFFFFFu, tmax = 0;
+    for (int q = 0; q < P.ntree; ++q) {
+        const int e = P.tedge[q];
+        phiV[P.ea[e]] = rec[q].src;
+        phiV[P.eb[e]] = rec[q].dst;
+        tnode_t[q] = rec[q].t;
+        tnode_of_edge[e] = q;
+        tmin = min(tmin, rec[q].t);
+        tmax = max(tmax, rec[q].t);
+    }
+    for (int x = 0; x < P.nv; ++x)
+        for (int y = x + 1; y < P.nv; ++y)
+            if (phiV[x] == phiV[y]) return 1;
+    if ((uint64_t)tmax - (uint64_t)tmin > (uint64_t)d) return 2;
+    int64_t prev = -1;
+    for (int pos = 0; pos < P.ne; ++pos) {
+        const int q = tnode_of_edge[P.pos_edge[pos]];
+        if (q < 0) continue;
+        if ((int64_t)tnode_t[q] <= prev) return 3;
+        prev = tnode_t[q];
+    }
+    // ---- DeriveCnt (Alg. 5) and N_phi (windows holding every tree edge)
+    bool ovf = false;
+    uint64_t cnt = derive_count(g, P, phiV, tnode_t, tnode_of_edge, tmin, tmax, ovf);
+    const bool two = (uint64_t)tmin >= (uint64_t)d && (uint64_t)tmin / (uint64_t)d == (uint64_t)tmax / (uint64_t)d;
+    if (!two) cnt = mul_chk(cnt, 2, ovf);
+    if (ovf) latch(status, ST_OVERFLOW);
+    contrib = cnt;
+    return 0;
+}
+
+template <bool TRACE>
+__global__ void __launch_bounds__(256) k_sample(DevGraph g, const DevPlan *__restrict__ plan, SampleJob J,
+                                                uint64_t seed, uint64_t first, uint64_t k, Acc *acc,
+                                                uint32_t *status, uint32_t *tr_gid, uint64_t *tr_contrib,
+                                                int32_t *tr_reason)
+{
+    __shared__ DevPlan sp;
+    {
+        const int *src = reinterpret_cast<const int *>(plan);
+        int *dst = reinterpret_cast<int *>(&sp);
+        for (int i = threadIdx.x; i < (int)(sizeof(DevPlan) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    u128 hits = 0;
+    unsigned long long nv = 0, nr1 = 0, nr2 = 0, nr3 = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        uint64_t c = 0;
+        int why = sample_one(g, sp, J, seed, first + i, status, c, TRACE ? tr_gid + i * sp.ntree : nullptr);
+        if (why == 0) { ++nv; hits += c; }
+        else if (why == 1) ++nr1;
+        else if (why == 2) ++nr2;
+        else if (why == 3) ++nr3;
+        if (TRACE) { tr_contrib[i] = c; tr_reason[i] = why; }
+    }
+    // warp reduction then one atomic set per warp
+    uint64_t hl = (uint64_t)hits, hh = (uint64_t)(hits >> 64);
+    for (int o = 16; o > 0; o >>= 1) {
+        uint64_t ol = __shfl_down_sync(0xffffffffu, hl, o);
+        uint64_t oh = __shfl_down_sync(0xffffffffu, hh, o);
+        uint64_t s = hl + ol;
+        hh += oh + (s < hl ? 1 : 0);
+        hl = s;
+        nv += __shfl_down_sync(0xffffffffu, nv, o);
+        nr1 += __shfl_down_sync(0xffffffffu, nr1, o);
+        nr2 += __shfl_down_sync(0xffffffffu, nr2, o);
+        nr3 += __shfl_down_sync(0xffffffffu, nr3, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (hl) {
+            unsigned long long old = atomicAdd(&acc->hits_lo, (unsigned long long)hl);
+            if (old + hl < old) hh += 1;
+        }
+        if (hh) atomicAdd(&acc->hits_hi, (unsigned long long)hh);
+        if (nv) atomicAdd(&acc->valid, nv);
+        if (nr1) atomicAdd(&acc->rv, nr1);
+        if (nr2) atomicAdd(&acc->rd, nr2);
+        if (nr3) atomicAdd(&acc->ro, nr3);
+    }
+}
+
+}  // namespace
+
+void fill_job(tm_motif *mo, SampleJob &J, const DevPlan *dplan)
+{
+    J.plan = dplan;
+    J.wcum = mo->wcum;
+    J.nwtot = mo->nwtot;
+    J.nw0 = mo->layer[0].nwin;
+    J.win_beg0 = mo->layer[0].win_beg; J.win_beg1 = mo->layer[1].win_beg;
+    J.win_id0 = mo->layer[0].win_id; J.win_id1 = mo->layer[1].win_id;
+    J.root_cdf0 = mo->layer[0].root_cdf; J.root_cdf1 = mo->layer[1].root_cdf;
+    for (int s = 0; s < kMaxTree; ++s) {
+        J.pref_dir0[s] = mo->layer[0].pref_dir[s]; J.pref_dir1[s] = mo->layer[1].pref_dir[s];
+        J.pref_multi0[s] = mo->layer[0].pref_multi[s]; J.pref_multi1[s] = mo->layer[1].pref_multi[s];
+    }
+    J.W_lo = mo->W.lo;
+    J.W_hi = mo->W.hi;
+}
+
+static void finish_result(tm_motif *mo, uint64_t k, const Acc &a, tm_result *out)
+{
+    out->W = mo->W;
+    out->hits2.lo = a.hits_lo;
+    out->hits2.hi = a.hits_hi;
+    out->k = k;
+    out->valid = a.valid;
+    out->rej_vertex = a.rv;
+    out->rej_delta = a.rd;
+    out->rej_order = a.ro;
+    double W = (double)mo->W.lo + 18446744073709551616.0 * (double)mo->W.hi;
+    double h = (double)a.hits_lo + 18446744073709551616.0 * (double)a.hits_hi;
+    out->estimate = k ? W * h / (2.0 * (double)k) : 0.0;
+}
+
+int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first, tm_result *out,
+                uint32_t *trace_gids, uint64_t *trace_contrib, int32_t *trace_reason)
+{
+    cudaStream_t st = ctx->stream;
+    Acc zero{0, 0, 0, 0, 0, 0};
+    if (k == 0 || (mo->W.lo == 0 && mo->W.hi == 0)) {
+        finish_result(mo, k, zero, out);
+        return TM_OK;
+    }
+    const bool trace = trace_gids || trace_contrib || trace_reason;
+    size_t plan_bytes = sizeof(DevPlan), acc_bytes = sizeof(Acc);
+    char *scratch = (char *)dalloc(ctx, plan_bytes + acc_bytes + 64);
+    if (!scratch) return TM_E_NOMEM;
+    DevPlan *dplan = (DevPlan *)scratch;
+    Acc *dacc = (Acc *)(scratch + ((plan_bytes + 15) / 16) * 16);
+    cudaMemcpyAsync(dplan, &mo->plan, plan_bytes, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(dacc, 0, acc_bytes, st);
+    cudaMemsetAsync(ctx->status, 0, 4, st);
+    SampleJob J;
+    fill_job(mo, J, dplan);
+    int threads = ctx->cfg.sample_threads > 0 ? std::min(ctx->cfg.sample_threads, 256) : 256;
+    uint64_t want = (k + threads - 1) / threads;
+    uint64_t cap = (uint64_t)ctx->num_sms * 16;
+    unsigned blocks = (unsigned)std::max<uint64_t>(1, std::min(want, cap));
+    uint32_t *dg = nullptr; uint64_t *dc = nullptr; int32_t *dr = nullptr;
+    size_t gbytes = 0;
+    if (trace) {
+        gbytes = (size_t)k * (4 * mo->plan.ntree + 8 + 4);
+        char *t = (char *)dalloc(ctx, gbytes);
+        if (!t) { dfree(ctx, scratch, plan_bytes + acc_bytes + 64); return TM_E_NOMEM; }
+        dc = (uint64_t *)t;
+        dr = (int32_t *)(t + (size_t)k * 8);
+        dg = (uint32_t *)(t + (size_t)k * 12);
+        k_sample<true><<<blocks, threads, 0, st>>>(ctx->g, dplan, J, seed, first, k, dacc, ctx->status, dg, dc, dr);
+    } else {
+        k_sample<false><<<blocks, threads, 0, st>>>(ctx->g, dplan, J, seed, first, k, dacc, ctx->status, nullptr,
+                                                    nullptr, nullptr);
+    }
+    int rc = check_cuda(ctx, cudaGetLastError(), "sampler launch");
+    Acc h{};
+    cudaMemcpyAsync(&h, dacc, acc_bytes, cudaMemcpyDeviceToHost, st);
+    if (trace && rc == TM_OK) {
+        if (trace_gids) cudaMemcpyAsync(trace_gids, dg, (size_t)k * 4 * mo->plan.ntree, cudaMemcpyDeviceToHost, st);
+        if (trace_contrib) cudaMemcpyAsync(trace_contrib, dc, (size_t)k * 8, cudaMemcpyDeviceToHost, st);
+        if (trace_reason) cudaMemcpyAsync(trace_reason, dr, (size_t)k * 4, cudaMemcpyDeviceToHost, st);
+    }
+    uint32_t bits = 0;
+    int rc2 = read_status(ctx, &bits);
+    if (trace) dfree(ctx, (char *)dc, gbytes);
+    dfree(ctx, scratch, plan_bytes + acc_bytes + 64);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    finish_result(mo, k, h, out);
+    if (bits & ST_OVERFLOW) return set_err(ctx, TM_E_OVERFLOW, "a completion count exceeds 2^64");
+    if (bits) return set_err(ctx, TM_E_CUDA, "sampler reached an inconsistent state (status " + std::to_string(bits) + ")");
+    return TM_OK;
+}
+
+int run_batch(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64_t *k, const uint64_t *seed,
+              tm_result *out)
+{
+    for (uint32_t q = 0; q < nq; ++q) {
+        int rc = run_samples(ctx, motifs[q], k[q], seed[q], 0, &out[q], nullptr, nullptr, nullptr);
+        if (rc) return rc;
+    }
+    return TM_OK;
+}
+
+}  // namespace timest

@@ -1,0 +1,273 @@
+// Device-wide scans used by the CSR builder and the weight pass.
+//
+// * exclusive_scan_u32: reduce-then-scan over u32 counts (recursive over the
+//   tile totals), for radix-sort offsets and compaction.
+// * segmented_scan_u64: inclusive prefix sums that restart at segment heads,
+//   with every 64-bit addition inside a segment checked for wrap-around.  It
+//   is a three-phase reduce / scan-of-tile-aggregates / rescan, so no block
+//   ever waits on another block.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tm_device.cuh"
+#include "tm_internal.h"
+
+namespace timest {
+namespace {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// ---------------------------------------------------------------- u32 ----
+__global__ void k_tile_sum_u32(const uint32_t *__restrict__ in, uint64_t n, uint32_t *__restrict__ tile_sum)
+{
+    __shared__ uint32_t warp_sum[SCAN_THREADS / 32];
+    uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        uint64_t i = base + (uint64_t)j * SCAN_THREADS + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t v = threadIdx.x < SCAN_THREADS / 32 ? warp_sum[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) tile_sum[blockIdx.x] = v;
+    }
+}
+
+// Exclusive scan of one tile with a carry-in taken from carry[blockIdx.x]
+// (or 0 when carry is null); blocked layout (each thread SCAN_ITEMS
+// consecutive values).  Writes the grand total to *total when it is the last
+// tile and total is non-null.
+__global__ void k_tile_scan_u32(const uint32_t *__restrict__ in, uint64_t n, const uint32_t *__restrict__ carry,
+                                uint32_t *__restrict__ out, uint32_t *__restrict__ total)
+{
+    __shared__ uint32_t warp_tot[SCAN_THREADS / 32];
+    uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        uint64_t i = base + j;
+        v[j] = (i < n) ? in[i] : 0;
+        s += v[j];
+    }
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < SCAN_THREADS / 32 ? warp_tot[lane] : 0;
+        uint32_t wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < SCAN_THREADS / 32) warp_tot[lane] = wi - w;
+    }
+    __syncthreads();
+    uint32_t run = (carry ? carry[blockIdx.x] : 0) + warp_tot[warp] + incl - s;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        uint64_t i = base + j;
+        if (i < n) out[i] = run;
+        run += v[j];
+    }
+    if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == SCAN_THREADS - 1) *total = run;
+}
+
+// Exclusive scan of n u32 values (in may equal out).  If total is non-null
+// the grand total is written there (device pointer).
+inline int exclusive_scan_u32(tm_ctx *ctx, const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *total)
+{
+    if (n == 0) {
+        if (total) cudaMemsetAsync(total, 0, sizeof(uint32_t), ctx->stream);
+        return TM_OK;
+    }
+    uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (tiles == 1) {
+        k_tile_scan_u32<<<1, SCAN_THREADS, 0, ctx->stream>>>(in, n, nullptr, out, total);
+        return check_cuda(ctx, cudaGetLastError(), "scan");
+    }
+    uint32_t *ts = (uint32_t *)dalloc(ctx, tiles * sizeof(uint32_t));
+    if (!ts) return TM_E_NOMEM;
+    k_tile_sum_u32<<<(unsigned)tiles, SCAN_THREADS, 0, ctx->stream>>>(in, n, ts);
+    int rc = exclusive_scan_u32(ctx, ts, ts, tiles, nullptr);
+    if (rc == TM_OK) {
+        k_tile_scan_u32<<<(unsigned)tiles, SCAN_THREADS, 0, ctx->stream>>>(in, n, ts, out, total);
+        rc = check_cuda(ctx, cudaGetLastError(), "scan");
+    }
+    dfree(ctx, ts, tiles * sizeof(uint32_t));
+    return rc;
+}
+
+// ------------------------------------------------------ segmented u64 ----
+struct SegAgg {
+    uint64_t v;     // sum since the last head (or of the whole range)
+    uint32_t f;     // 1 if the range contains a head
+    uint32_t pad;
+};
+
+__device__ __forceinline__ SegAgg seg_combine(SegAgg a, SegAgg b, bool &ovf)
+{
+    SegAgg r;
+    r.f = a.f | b.f;
+    if (b.f) r.v = b.v;
+    else r.v = add_chk(a.v, b.v, ovf);
+    r.pad = 0;
+    return r;
+}
+
+// Load functor interface: __device__ uint64_t value(uint64_t pos) const;
+//                         __device__ bool head(uint64_t pos) const;
+template <class F>
+__global__ void k_segscan_reduce(F f, uint64_t n, SegAgg *__restrict__ aggs, uint32_t *status)
+{
+    __shared__ SegAgg warp_agg[SCAN_THREADS / 32];
+    uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
+    bool ovf = false;
+    SegAgg a{0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        uint64_t i = base + j;
+        if (i < n) {
+            SegAgg x{f.value(i), f.head(i) ? 1u : 0u, 0};
+            a = seg_combine(a, x, ovf);
+        }
+    }
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        SegAgg y;
+        y.v = __shfl_up_sync(0xffffffffu, a.v, o);
+        y.f = __shfl_up_sync(0xffffffffu, a.f, o);
+        if (lane >= o) a = seg_combine(y, a, ovf);
+    }
+    if (lane == 31) warp_agg[warp] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        SegAgg t = warp_agg[0];
+        for (int w = 1; w < SCAN_THREADS / 32; ++w) t = seg_combine(t, warp_agg[w], ovf);
+        aggs[blockIdx.x] = t;
+    }
+    if (ovf) latch(status, ST_OVERFLOW);
+}
+
+// Turn tile aggregates into per-tile carry-ins (exclusive, segmented), in
+// place.  One block; each thread owns a contiguous chunk of tiles.
+__global__ void k_segscan_carries(SegAgg *__restrict__ aggs, uint64_t ntiles, uint32_t *status)
+{
+    __shared__ SegAgg chunk[1024];
+    bool ovf = false;
+    uint64_t per = (ntiles + blockDim.x - 1) / blockDim.x;
+    uint64_t lo = (uint64_t)threadIdx.x * per, hi = lo + per;
+    if (hi > ntiles) hi = ntiles;
+    SegAgg a{0, 0, 0};
+    for (uint64_t i = lo; i < hi; ++i) a = seg_combine(a, aggs[i], ovf);
+    chunk[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        SegAgg run{0, 0, 0};
+        for (unsigned t = 0; t < blockDim.x; ++t) {
+            SegAgg c = chunk[t];
+            chunk[t] = run;
+            run = seg_combine(run, c, ovf);
+        }
+    }
+    __syncthreads();
+    SegAgg run = chunk[threadIdx.x];
+    for (uint64_t i = lo; i < hi; ++i) {
+        SegAgg c = aggs[i];
+        aggs[i] = run;
+        run = seg_combine(run, c, ovf);
+    }
+    if (ovf) latch(status, ST_OVERFLOW);
+}
+
+template <class F>
+__global__ void k_segscan_final(F f, uint64_t n, const SegAgg *__restrict__ carries, uint64_t *__restrict__ out,
+                                uint32_t *status)
+{
+    __shared__ SegAgg warp_agg[SCAN_THREADS / 32];
+    uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
+    bool ovf = false;
+    uint64_t v[SCAN_ITEMS];
+    uint32_t hbits = 0;
+    SegAgg a{0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        uint64_t i = base + j;
+        v[j] = 0;
+        if (i < n) {
+            v[j] = f.value(i);
+            bool h = f.head(i);
+            hbits |= (h ? 1u : 0u) << j;
+            SegAgg x{v[j], h ? 1u : 0u, 0};
+            a = seg_combine(a, x, ovf);
+        }
+    }
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    SegAgg incl = a;
+    for (int o = 1; o < 32; o <<= 1) {
+        SegAgg y;
+        y.v = __shfl_up_sync(0xffffffffu, incl.v, o);
+        y.f = __shfl_up_sync(0xffffffffu, incl.f, o);
+        if (lane >= o) incl = seg_combine(y, incl, ovf);
+    }
+    if (lane == 31) warp_agg[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        SegAgg run = carries[blockIdx.x];
+        for (int w = 0; w < SCAN_THREADS / 32; ++w) {
+            SegAgg c = warp_agg[w];
+            warp_agg[w] = run;
+            run = seg_combine(run, c, ovf);
+        }
+    }
+    __syncthreads();
+    // exclusive prefix of this thread = warp prefix (+) lanes before it
+    SegAgg excl_lane;
+    excl_lane.v = __shfl_up_sync(0xffffffffu, incl.v, 1);
+    excl_lane.f = __shfl_up_sync(0xffffffffu, incl.f, 1);
+    SegAgg pre = warp_agg[warp];
+    if (lane > 0) pre = seg_combine(pre, excl_lane, ovf);
+    uint64_t run = pre.v;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        uint64_t i = base + j;
+        if (i < n) {
+            if ((hbits >> j) & 1u) run = v[j];
+            else run = add_chk(run, v[j], ovf);
+            out[i] = run;
+        }
+    }
+    if (ovf) latch(status, ST_OVERFLOW);
+}
+
+template <class F>
+int segmented_scan_u64(tm_ctx *ctx, const F &f, uint64_t n, uint64_t *out)
+{
+    if (n == 0) return TM_OK;
+    uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    SegAgg *aggs = (SegAgg *)dalloc(ctx, tiles * sizeof(SegAgg));
+    if (!aggs) return TM_E_NOMEM;
+    k_segscan_reduce<F><<<(unsigned)tiles, SCAN_THREADS, 0, ctx->stream>>>(f, n, aggs, ctx->status);
+    k_segscan_carries<<<1, 1024, 0, ctx->stream>>>(aggs, tiles, ctx->status);
+    k_segscan_final<F><<<(unsigned)tiles, SCAN_THREADS, 0, ctx->stream>>>(f, n, aggs, out, ctx->status);
+    int rc = check_cuda(ctx, cudaGetLastError(), "segmented scan");
+    dfree(ctx, aggs, tiles * sizeof(SegAgg));
+    return rc;
+}
+
+}  // namespace
+}  // namespace timest

@@ -1,0 +1,126 @@
+// Device helpers: counter-based random numbers, bounded binary searches,
+// 128-bit arithmetic and the status word.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tm_internal.h"
+
+namespace timest {
+
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ void latch(uint32_t *status, uint32_t bits)
+{
+    atomicOr(status, bits);
+}
+
+// Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11): each round
+// multiplies counter words 0 and 2 by the two round multipliers, feeds the
+// high halves (xored with words 1/3 and the key) and the low halves forward;
+// the key advances by the golden-ratio Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        uint32_t hi0 = __umulhi(m0, c.x), lo0 = m0 * c.x;
+        uint32_t hi1 = __umulhi(m1, c.z), lo1 = m1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Per-sample stream: key = seed, counter = (sample id, draw number, 0).
+struct SampleRng {
+    uint32_t k0, k1, j0, j1, d;
+    __device__ void init(uint64_t seed, uint64_t j)
+    {
+        k0 = (uint32_t)seed; k1 = (uint32_t)(seed >> 32);
+        j0 = (uint32_t)j; j1 = (uint32_t)(j >> 32); d = 0;
+    }
+    __device__ __forceinline__ uint4 block() { return philox10(make_uint4(j0, j1, d++, 0u), k0, k1); }
+
+    // U[0,n) by masked rejection; n <= 1 consumes no draw.
+    __device__ uint64_t below(uint64_t n, uint32_t *status)
+    {
+        if (n <= 1) return 0;
+        int b = 64 - __clzll((long long)(n - 1));
+        uint64_t mask = (b >= 64) ? ~0ull : ((1ull << b) - 1);
+        for (int it = 0; it < 512; ++it) {
+            uint4 x = block();
+            uint64_t v = ((uint64_t)x.x | ((uint64_t)x.y << 32)) & mask;
+            if (v < n) return v;
+        }
+        latch(status, ST_BADSTATE);
+        return 0;
+    }
+    __device__ u128 below128(u128 n, uint32_t *status)
+    {
+        if (n <= 1) return 0;
+        u128 nm1 = n - 1;
+        uint64_t hi = (uint64_t)(nm1 >> 64);
+        int b = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)(uint64_t)nm1);
+        u128 mask = (b >= 128) ? ~(u128)0 : ((((u128)1) << b) - 1);
+        for (int it = 0; it < 512; ++it) {
+            uint4 x = block();
+            u128 v = (u128)x.x | ((u128)x.y << 32) | ((u128)x.z << 64) | ((u128)x.w << 96);
+            v &= mask;
+            if (v < n) return v;
+        }
+        latch(status, ST_BADSTATE);
+        return 0;
+    }
+};
+
+// First index in [lo, hi) with a[i] >= x (a sorted ascending); hi if none.
+__device__ __forceinline__ uint32_t lower_idx(const uint32_t *__restrict__ a, uint32_t lo, uint32_t hi, uint64_t x)
+{
+    uint32_t n = hi - lo;
+    while (n > 0) {
+        uint32_t half = n >> 1;
+        uint32_t mid = lo + half;
+        if ((uint64_t)__ldg(a + mid) < x) { lo = mid + 1; n -= half + 1; }
+        else n = half;
+    }
+    return lo;
+}
+
+// First index in [lo, hi) with v[i] > x (v non-decreasing).
+__device__ __forceinline__ uint32_t upper_idx64(const uint64_t *__restrict__ v, uint32_t lo, uint32_t hi, uint64_t x)
+{
+    uint32_t n = hi - lo;
+    while (n > 0) {
+        uint32_t half = n >> 1;
+        uint32_t mid = lo + half;
+        if (__ldg(v + mid) <= x) { lo = mid + 1; n -= half + 1; }
+        else n = half;
+    }
+    return lo;
+}
+
+// Checked u64 add / multiply.
+__device__ __forceinline__ uint64_t add_chk(uint64_t a, uint64_t b, bool &ovf)
+{
+    uint64_t s = a + b;
+    ovf |= (s < a);
+    return s;
+}
+__device__ __forceinline__ uint64_t mul_chk(uint64_t a, uint64_t b, bool &ovf)
+{
+    ovf |= (__umul64hi(a, b) != 0);
+    return a * b;
+}
+
+// Window of layer p holding t' (windows [i*d, (i+2)*d), i = p mod 2), or -1.
+__device__ __forceinline__ int64_t layer_window(uint32_t t, int p, int64_t d)
+{
+    int64_t tt = (int64_t)t;
+    if (tt < p * d) return -1;
+    return p + 2 * ((tt - p * d) / (2 * d));
+}
+
+}  // namespace timest

@@ -1,0 +1,163 @@
+// Internal declarations shared by the TIMEST CUDA translation units.
+// Host-side structures (context, motif, device plan) and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/timest.h"
+
+namespace timest {
+
+constexpr int kMaxV = 8;
+constexpr int kMaxE = 16;
+constexpr int kMaxTree = kMaxV - 1;
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+// Device status word bits (latched by kernels, read by the host at syncs).
+enum : uint32_t {
+    ST_OVERFLOW = 1u,      // an exact integer exceeded its width
+    ST_BADSTATE = 2u,      // an internal invariant failed (e.g. empty candidate list)
+    ST_TIMEOUT = 4u,       // a bounded wait ran out
+    ST_DUP = 8u,
+    ST_SELFLOOP = 16u,
+    ST_RANGE = 32u         // an id out of range
+};
+
+// The temporal graph in HBM, all structure-of-arrays, 32-bit ids.
+// gid = position in GLOBAL order (t', src, dst).
+struct DevGraph {
+    uint32_t n = 0;
+    uint32_t m = 0;
+    uint32_t npairs = 0;
+    int64_t tmin = 0;
+    uint32_t T = 0;                      // max t'
+    // GLOBAL order
+    uint32_t *g_t = nullptr, *g_src = nullptr, *g_dst = nullptr, *g_pair = nullptr;
+    // out-lists: per vertex, (t', dst) order
+    uint32_t *out_off = nullptr, *out_t = nullptr, *out_nbr = nullptr, *out_gid = nullptr;
+    // in-lists: per vertex, (t', src) order
+    uint32_t *in_off = nullptr, *in_t = nullptr, *in_nbr = nullptr, *in_gid = nullptr;
+    // multi-edge lists: pairs sorted by (src, dst); entries in t' order
+    uint32_t *vpair_off = nullptr;       // [n+1] first pair of each source vertex
+    uint32_t *pair_dst = nullptr;        // [P]
+    uint32_t *pair_off = nullptr;        // [P+1] into multi_*
+    uint32_t *rev_pair = nullptr;        // [P] pair (dst,src) or kNone
+    uint32_t *multi_t = nullptr, *multi_gid = nullptr;
+};
+
+// Device plan of a motif with its rooted spanning tree (Defs. 3.4-3.5).
+// Tree edges are indexed by q = position in the sampling order (breadth
+// first from the root edge c).
+struct DevPlan {
+    int32_t nv, ne, ntree;
+    int32_t pad0;
+    int64_t delta;                       // capped at 2^33 (no change of meaning)
+    int32_t ea[kMaxE], eb[kMaxE], rank[kMaxE];
+    int32_t pos_edge[kMaxE];             // motif edge at pi position
+    int32_t is_tree[kMaxE];
+    int32_t tedge[kMaxTree];             // motif edge id of tree node q
+    int32_t tparent[kMaxTree];           // parent node (-1 for the root)
+    int32_t tleaf[kMaxTree];             // 1: no children (weight 1)
+    int32_t tzside[kMaxTree];            // meeting vertex = parent's tail (0) / head (1)
+    int32_t tout[kMaxTree];              // 1: child leaves the meeting vertex (out-list)
+    int32_t tlater[kMaxTree];            // 1: child comes after the parent in pi
+    int32_t tslot[kMaxTree];             // prefix-array slot (non-root, non-leaf) or -1
+    int32_t nchild[kMaxTree];
+    int32_t child[kMaxTree][kMaxTree];
+    int32_t height[kMaxTree];
+    int32_t nslots;
+};
+
+// Per-motif resident weight data (one window layer p = 0, 1 each).
+struct LayerData {
+    uint32_t nwin = 0;                   // non-empty windows of this layer
+    uint32_t *win_beg = nullptr;         // [nwin+1] gid ranges (win_beg[nwin] = m)
+    uint32_t *win_id = nullptr;          // [nwin] window index i
+    uint64_t *root_cdf = nullptr;        // [m] running sum of w_c inside its window
+    uint64_t *pref_dir[kMaxTree] = {};   // per slot: prefix in the out/in order
+    uint64_t *pref_multi[kMaxTree] = {}; // per slot: prefix in the multi-edge order
+};
+
+struct DeviceAlloc;
+
+}  // namespace timest
+
+struct tm_motif {
+    tm_ctx *ctx = nullptr;
+    uint32_t nv = 0, ne = 0;
+    uint32_t ea[timest::kMaxE] = {}, eb[timest::kMaxE] = {}, rank[timest::kMaxE] = {};
+    int64_t delta = 0;
+    uint32_t tree[timest::kMaxTree] = {};
+    uint32_t root = 0;
+    timest::DevPlan plan{};
+    bool have_weights = false;
+    uint64_t graph_epoch = 0;
+    timest::LayerData layer[2];
+    uint64_t *wcum = nullptr;            // [2*(nw0+nw1+1)] u128 window cumulative (lo,hi)
+    uint32_t nwtot = 0;
+    tm_u128 W{0, 0};
+    size_t bytes = 0;                    // device bytes held
+    std::vector<std::pair<void *, size_t>> bufs;
+};
+
+struct tm_ctx {
+    tm_config cfg{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    std::string err;
+    // graph
+    uint64_t epoch = 0;
+    bool loaded = false, preprocessed = false;
+    uint32_t n = 0;
+    uint64_t m_in = 0;
+    int load_flags = 0;
+    uint32_t *in_src = nullptr, *in_dst = nullptr;  // staged input (device)
+    int64_t *in_t = nullptr;
+    timest::DevGraph g;
+    std::vector<std::pair<void *, size_t>> graph_bufs;
+    uint32_t *status = nullptr;          // device status word
+    uint32_t *status_host = nullptr;     // pinned mirror
+    int num_sms = 0;
+};
+
+namespace timest {
+
+// ---- allocation helpers (api.cu) ----
+void *dalloc(tm_ctx *ctx, size_t bytes);
+void dfree(tm_ctx *ctx, void *p, size_t bytes);
+
+// ---- CSR build (csr.cu) ----
+int build_csr(tm_ctx *ctx);
+
+// ---- weights (weights.cu) ----
+int compute_weights(tm_ctx *ctx, tm_motif *mo);
+int export_weights(tm_ctx *ctx, tm_motif *mo, int q, int layer, uint64_t *host_out);
+
+// ---- sampler (sampler.cu) ----
+struct SampleJob {
+    const DevPlan *plan;                 // device pointer
+    const uint64_t *wcum;                // u128 pairs
+    uint32_t nwtot, nw0;
+    const uint32_t *win_beg0, *win_beg1, *win_id0, *win_id1;
+    const uint64_t *root_cdf0, *root_cdf1;
+    const uint64_t *pref_dir0[kMaxTree], *pref_dir1[kMaxTree];
+    const uint64_t *pref_multi0[kMaxTree], *pref_multi1[kMaxTree];
+    uint64_t W_lo, W_hi;
+};
+int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first,
+                tm_result *out, uint32_t *trace_gids, uint64_t *trace_contrib, int32_t *trace_reason);
+int run_batch(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64_t *k,
+              const uint64_t *seed, tm_result *out);
+
+// ---- common ----
+int check_cuda(tm_ctx *ctx, cudaError_t e, const char *what);
+int set_err(tm_ctx *ctx, int code, const std::string &msg);
+int read_status(tm_ctx *ctx, uint32_t *bits);   // syncs the stream
+void fill_job(tm_motif *mo, SampleJob &job, const DevPlan *dplan);
+
+}  // namespace timest

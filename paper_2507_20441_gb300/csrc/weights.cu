@@ -1,0 +1,417 @@
+// Weight pass of TIMEST (Sec. 3.1): windows (Constraint 3, Alg. 1), the
+// per-edge dynamic program over the rooted spanning tree (Claims 3.1-3.2,
+// Alg. 2), segmented prefix sums of child weights, and the root CDF whose
+// window totals give W (Claim 3.4).
+//
+// Windows [i*delta, (i+2)*delta) with the same parity of i are disjoint, so
+// each edge has at most one window per parity ("layer" p = i mod 2) and one
+// weight per (tree edge, layer).  The weight of tree node q for edge e in
+// layer p is the product over q's children c of
+//     sum of w_c over Lambda_z(time range of c) - sum over El(z, o)(same range)
+// (the candidate list of Claim 3.1), where both ranges are clipped to e's
+// window and the sums are differences of segmented prefix sums.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "scan.cuh"
+#include "tm_device.cuh"
+#include "tm_internal.h"
+
+namespace timest {
+
+namespace {
+
+constexpr int TB = 256;
+inline unsigned blocks_for(uint64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+struct ChildPrefix {
+    const uint64_t *pd[2][kMaxTree];   // [layer][slot] prefix in the out/in order
+    const uint64_t *pm[2][kMaxTree];   // [layer][slot] prefix in the multi-edge order
+};
+
+// Sum of child weights over the candidate list L (Claim 3.1) for one child.
+// zg/og: images of the meeting vertex and of the parent's other endpoint;
+// own_pair/rev: multi-edge list ids of the parent edge and of its reverse.
+__device__ __forceinline__ uint64_t child_sum(const DevGraph &g, const ChildPrefix &cp, int p, int slot, bool leaf,
+                                              bool out, uint32_t zg, uint32_t pe, uint64_t lo, uint64_t hi,
+                                              uint64_t wlo)
+{
+    const uint32_t *off = out ? g.out_off : g.in_off;
+    const uint32_t *tarr = out ? g.out_t : g.in_t;
+    uint32_t beg = __ldg(off + zg), end = __ldg(off + zg + 1);
+    uint32_t a = lower_idx(tarr, beg, end, lo);
+    uint32_t b = lower_idx(tarr, a, end, hi + 1);
+    uint32_t ea = 0, eb = 0, pb = 0;
+    if (pe != kNone) {
+        pb = __ldg(g.pair_off + pe);
+        uint32_t pend = __ldg(g.pair_off + pe + 1);
+        ea = lower_idx(g.multi_t, pb, pend, lo);
+        eb = lower_idx(g.multi_t, ea, pend, hi + 1);
+    }
+    if (leaf) return (uint64_t)(b - a) - (uint64_t)(eb - ea);
+    const uint64_t *P = cp.pd[p][slot];
+    const uint64_t *PM = cp.pm[p][slot];
+    uint64_t sr = 0, se = 0;
+    if (b > a) {
+        uint64_t base = (a > beg && (uint64_t)__ldg(tarr + a - 1) >= wlo) ? __ldg(P + a - 1) : 0;
+        sr = __ldg(P + b - 1) - base;
+    }
+    if (eb > ea) {
+        uint64_t base = (ea > pb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo) ? __ldg(PM + ea - 1) : 0;
+        se = __ldg(PM + eb - 1) - base;
+    }
+    return sr - se;
+}
+
+// w_{q,e} for every edge e (gid) and both layers (Claim 3.2).
+__global__ void k_dp(DevGraph g, DevPlan P, int q, ChildPrefix cp, uint64_t *__restrict__ w0,
+                     uint64_t *__restrict__ w1, uint32_t *status)
+{
+    uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= g.m) return;
+    const uint32_t t = __ldg(g.g_t + e), u = __ldg(g.g_src + e), v = __ldg(g.g_dst + e);
+    const uint32_t pr = __ldg(g.g_pair + e);
+    const uint32_t rv = __ldg(g.rev_pair + pr);
+    const int64_t d = P.delta;
+    bool ovf_any = false;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        int64_t wi = layer_window(t, p, d);
+        uint64_t w = 0;
+        if (wi >= 0) {
+            const uint64_t wlo = (uint64_t)(wi * d), whi = (uint64_t)((wi + 2) * d - 1);
+            uint64_t prod = 1;
+            bool zero = false, ovf = false;
+            for (int ci = 0; ci < P.nchild[q]; ++ci) {
+                const int c = P.child[q][ci];
+                const bool zs = P.tzside[c] != 0, out = P.tout[c] != 0;
+                const uint32_t zg = zs ? v : u;
+                uint64_t lo, hi;
+                if (P.tlater[c]) { lo = (uint64_t)t + 1; hi = (uint64_t)t + (uint64_t)d; }
+                else { lo = (uint64_t)t >= (uint64_t)d ? (uint64_t)t - (uint64_t)d : 0; hi = (uint64_t)t - 1; }
+                if (!P.tlater[c] && t == 0) { zero = true; continue; }
+                lo = lo < wlo ? wlo : lo;
+                hi = hi > whi ? whi : hi;
+                if (lo > hi) { zero = true; continue; }
+                // excluded multi-edge list: El(z -> o) for an out-child, El(o -> z) for an in-child
+                const uint32_t pe = (out == !zs) ? pr : rv;
+                uint64_t s = child_sum(g, cp, p, P.tslot[c], P.tleaf[c] != 0, out, zg, pe, lo, hi, wlo);
+                if (s == 0) zero = true;
+                else prod = mul_chk(prod, s, ovf);
+            }
+            if (zero) w = 0;
+            else { w = prod; ovf_any |= ovf; }
+        }
+        (p == 0 ? w0 : w1)[e] = w;
+    }
+    if (ovf_any) latch(status, ST_OVERFLOW);
+}
+
+// ---- scans over the three orders ----------------------------------------
+// segment = (owner, window of layer p); owner boundaries come from a bit set.
+struct DirScan {
+    const uint64_t *w;          // weights by gid
+    const uint32_t *perm;       // position -> gid
+    const uint32_t *tarr;       // position -> t'
+    const uint32_t *ownbits;    // bit set: position starts a new owner
+    int p;
+    int64_t d;
+    __device__ uint64_t value(uint64_t i) const { return __ldg(w + __ldg(perm + i)); }
+    __device__ bool head(uint64_t i) const
+    {
+        if (i == 0) return true;
+        if ((__ldg(ownbits + (i >> 5)) >> (i & 31)) & 1u) return true;
+        return layer_window(__ldg(tarr + i), p, d) != layer_window(__ldg(tarr + i - 1), p, d);
+    }
+};
+
+struct RootScan {
+    const uint64_t *w;
+    const uint32_t *tarr;       // g_t
+    int p;
+    int64_t d;
+    __device__ uint64_t value(uint64_t i) const { return __ldg(w + i); }
+    __device__ bool head(uint64_t i) const
+    {
+        if (i == 0) return true;
+        return layer_window(__ldg(tarr + i), p, d) != layer_window(__ldg(tarr + i - 1), p, d);
+    }
+};
+
+// Window heads of layer p in GLOBAL order.
+__global__ void k_window_heads(const uint32_t *__restrict__ t, uint32_t m, int p, int64_t d, uint32_t *__restrict__ flag)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int64_t w = layer_window(t[i], p, d);
+    flag[i] = (w >= 0 && (i == 0 || layer_window(t[i - 1], p, d) != w)) ? 1u : 0u;
+}
+
+__global__ void k_window_fill(const uint32_t *__restrict__ t, const uint32_t *__restrict__ flag,
+                              const uint32_t *__restrict__ pos, uint32_t m, int p, int64_t d,
+                              uint32_t *__restrict__ win_beg, uint32_t *__restrict__ win_id)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m || !flag[i]) return;
+    win_beg[pos[i]] = i;
+    win_id[pos[i]] = (uint32_t)layer_window(t[i], p, d);
+}
+
+// Window totals W_i (last root-CDF entry of each window) and their 128-bit
+// running sum over (layer 0 windows, layer 1 windows).  One block; each
+// thread scans a contiguous chunk.
+__global__ void k_window_cum(const uint64_t *__restrict__ cdf0, const uint32_t *__restrict__ beg0, uint32_t nw0,
+                             const uint64_t *__restrict__ cdf1, const uint32_t *__restrict__ beg1, uint32_t nw1,
+                             uint64_t *__restrict__ wcum)
+{
+    __shared__ u128 part[1024];
+    uint32_t n = nw0 + nw1;
+    uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+    uint32_t lo = threadIdx.x * per, hi = min(n, lo + per);
+    auto total = [&](uint32_t k) -> uint64_t {
+        if (k < nw0) return cdf0[beg0[k + 1] - 1];
+        k -= nw0;
+        return cdf1[beg1[k + 1] - 1];
+    };
+    u128 s = 0;
+    for (uint32_t k = lo; k < hi; ++k) s += total(k);
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u128 run = 0;
+        for (unsigned i = 0; i < blockDim.x; ++i) { u128 c = part[i]; part[i] = run; run += c; }
+        wcum[2 * (size_t)n] = (uint64_t)run;
+        wcum[2 * (size_t)n + 1] = (uint64_t)(run >> 64);
+    }
+    __syncthreads();
+    u128 run = part[threadIdx.x];
+    for (uint32_t k = lo; k < hi; ++k) {
+        wcum[2 * (size_t)k] = (uint64_t)run;
+        wcum[2 * (size_t)k + 1] = (uint64_t)(run >> 64);
+        run += total(k);
+    }
+}
+
+__global__ void k_owner_bits(const uint32_t *__restrict__ off, uint32_t nown, uint32_t m, uint32_t *__restrict__ bits)
+{
+    uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nown) return;
+    uint32_t b = off[v];
+    if (b < m && off[v + 1] > b) atomicOr(bits + (b >> 5), 1u << (b & 31));
+}
+
+// Reconstruct w for one order from its segmented prefix (exports).
+template <class F>
+__global__ void k_unprefix(F f, const uint64_t *__restrict__ pref, const uint32_t *__restrict__ perm, uint32_t m,
+                           uint64_t *__restrict__ out)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    uint64_t w = pref[i] - (f.head(i) ? 0 : pref[i - 1]);
+    out[perm ? perm[i] : i] = w;
+}
+
+__global__ void k_leaf_weights(const uint32_t *__restrict__ t, uint32_t m, int p, int64_t d, uint64_t *__restrict__ out)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) out[i] = layer_window(t[i], p, d) >= 0 ? 1 : 0;
+}
+
+}  // namespace
+
+static void *malloc_motif(tm_ctx *ctx, tm_motif *mo, size_t bytes)
+{
+    void *p = dalloc(ctx, bytes ? bytes : 8);
+    if (p) { mo->bufs.push_back({p, bytes ? bytes : 8}); mo->bytes += bytes; }
+    return p;
+}
+
+static void free_motif_weights(tm_ctx *ctx, tm_motif *mo)
+{
+    for (auto &b : mo->bufs) dfree(ctx, b.first, b.second);
+    mo->bufs.clear();
+    mo->bytes = 0;
+    for (int p = 0; p < 2; ++p) mo->layer[p] = LayerData();
+    mo->wcum = nullptr;
+    mo->have_weights = false;
+}
+
+// Owner bit sets of the out-, in- and multi-edge orders (built on demand,
+// kept with the graph).
+struct OwnerBits { uint32_t *out = nullptr, *in = nullptr, *multi = nullptr; };
+
+static int owner_bits(tm_ctx *ctx, OwnerBits &ob)
+{
+    const DevGraph &g = ctx->g;
+    size_t words = ((size_t)g.m + 31) / 32 + 1;
+    uint32_t **dst[3] = {&ob.out, &ob.in, &ob.multi};
+    const uint32_t *offs[3] = {g.out_off, g.in_off, g.pair_off};
+    uint32_t nown[3] = {g.n, g.n, g.npairs};
+    for (int k = 0; k < 3; ++k) {
+        uint32_t *b = (uint32_t *)dalloc(ctx, words * 4);
+        if (!b) return TM_E_NOMEM;
+        cudaMemsetAsync(b, 0, words * 4, ctx->stream);
+        if (nown[k]) k_owner_bits<<<blocks_for(nown[k], TB), TB, 0, ctx->stream>>>(offs[k], nown[k], g.m, b);
+        *dst[k] = b;
+    }
+    return check_cuda(ctx, cudaGetLastError(), "owner bits");
+}
+
+static void free_owner_bits(tm_ctx *ctx, OwnerBits &ob)
+{
+    size_t words = ((size_t)ctx->g.m + 31) / 32 + 1;
+    if (ob.out) dfree(ctx, ob.out, words * 4);
+    if (ob.in) dfree(ctx, ob.in, words * 4);
+    if (ob.multi) dfree(ctx, ob.multi, words * 4);
+    ob = OwnerBits();
+}
+
+int compute_weights(tm_ctx *ctx, tm_motif *mo)
+{
+    free_motif_weights(ctx, mo);
+    const DevGraph &g = ctx->g;
+    const DevPlan &P = mo->plan;
+    cudaStream_t st = ctx->stream;
+    const uint32_t m = g.m;
+    const int64_t d = P.delta;
+    int rc = TM_OK;
+    cudaMemsetAsync(ctx->status, 0, 4, st);
+    // ---- windows of each layer (K2)
+    for (int p = 0; p < 2; ++p) {
+        LayerData &L = mo->layer[p];
+        uint32_t *flag = (uint32_t *)dalloc(ctx, (size_t)(m ? m : 1) * 4);
+        uint32_t *pos = (uint32_t *)dalloc(ctx, (size_t)(m ? m : 1) * 4);
+        uint32_t *dcount = (uint32_t *)dalloc(ctx, 4);
+        if (!flag || !pos || !dcount) return TM_E_NOMEM;
+        uint32_t nw = 0;
+        if (m) {
+            k_window_heads<<<blocks_for(m, TB), TB, 0, st>>>(g.g_t, m, p, d, flag);
+            rc = exclusive_scan_u32(ctx, flag, pos, m, dcount);
+            if (rc) return rc;
+            cudaMemcpyAsync(&nw, dcount, 4, cudaMemcpyDeviceToHost, st);
+            rc = check_cuda(ctx, cudaStreamSynchronize(st), "window count");
+            if (rc) return rc;
+        }
+        L.nwin = nw;
+        L.win_beg = (uint32_t *)malloc_motif(ctx, mo, ((size_t)nw + 1) * 4);
+        L.win_id = (uint32_t *)malloc_motif(ctx, mo, ((size_t)nw + 1) * 4);
+        if (!L.win_beg || !L.win_id) return TM_E_NOMEM;
+        if (m) k_window_fill<<<blocks_for(m, TB), TB, 0, st>>>(g.g_t, flag, pos, m, p, d, L.win_beg, L.win_id);
+        cudaMemcpyAsync(L.win_beg + nw, &g.m, 4, cudaMemcpyHostToDevice, st);
+        rc = check_cuda(ctx, cudaStreamSynchronize(st), "window fill");
+        dfree(ctx, flag, (size_t)(m ? m : 1) * 4);
+        dfree(ctx, pos, (size_t)(m ? m : 1) * 4);
+        dfree(ctx, dcount, 4);
+        if (rc) return rc;
+    }
+    // ---- DP over tree nodes in increasing height (K3) + prefixes (K4)
+    OwnerBits ob;
+    rc = owner_bits(ctx, ob);
+    if (rc) return rc;
+    uint64_t *w[2];
+    w[0] = (uint64_t *)dalloc(ctx, (size_t)(m ? m : 1) * 8);
+    w[1] = (uint64_t *)dalloc(ctx, (size_t)(m ? m : 1) * 8);
+    if (!w[0] || !w[1]) return TM_E_NOMEM;
+    ChildPrefix cp{};
+    int maxh = 0;
+    for (int q = 0; q < P.ntree; ++q) maxh = std::max(maxh, (int)P.height[q]);
+    std::vector<int> order;
+    for (int h = 1; h <= maxh; ++h)
+        for (int q = P.ntree - 1; q >= 0; --q)
+            if (P.height[q] == h) order.push_back(q);
+    if (P.tleaf[0]) order.push_back(0);   // single-edge motif: the root is a leaf
+    for (int q : order) {
+        if (m) k_dp<<<blocks_for(m, TB), TB, 0, st>>>(g, P, q, cp, w[0], w[1], ctx->status);
+        rc = check_cuda(ctx, cudaGetLastError(), "weight DP");
+        if (rc) return rc;
+        if (q == 0) {
+            for (int p = 0; p < 2; ++p) {
+                LayerData &L = mo->layer[p];
+                L.root_cdf = (uint64_t *)malloc_motif(ctx, mo, (size_t)(m ? m : 1) * 8);
+                if (!L.root_cdf) return TM_E_NOMEM;
+                RootScan f{w[p], g.g_t, p, d};
+                rc = segmented_scan_u64(ctx, f, m, L.root_cdf);
+                if (rc) return rc;
+            }
+        } else {
+            int slot = P.tslot[q];
+            bool out = P.tout[q] != 0;
+            for (int p = 0; p < 2; ++p) {
+                LayerData &L = mo->layer[p];
+                L.pref_dir[slot] = (uint64_t *)malloc_motif(ctx, mo, (size_t)(m ? m : 1) * 8);
+                L.pref_multi[slot] = (uint64_t *)malloc_motif(ctx, mo, (size_t)(m ? m : 1) * 8);
+                if (!L.pref_dir[slot] || !L.pref_multi[slot]) return TM_E_NOMEM;
+                DirScan fd{w[p], out ? g.out_gid : g.in_gid, out ? g.out_t : g.in_t, out ? ob.out : ob.in, p, d};
+                rc = segmented_scan_u64(ctx, fd, m, L.pref_dir[slot]);
+                if (rc) return rc;
+                DirScan fm{w[p], g.multi_gid, g.multi_t, ob.multi, p, d};
+                rc = segmented_scan_u64(ctx, fm, m, L.pref_multi[slot]);
+                if (rc) return rc;
+                cp.pd[p][slot] = L.pref_dir[slot];
+                cp.pm[p][slot] = L.pref_multi[slot];
+            }
+        }
+    }
+    dfree(ctx, w[0], (size_t)(m ? m : 1) * 8);
+    dfree(ctx, w[1], (size_t)(m ? m : 1) * 8);
+    free_owner_bits(ctx, ob);
+    // ---- window totals and their 128-bit running sum (K5)
+    uint32_t nw0 = mo->layer[0].nwin, nw1 = mo->layer[1].nwin;
+    mo->nwtot = nw0 + nw1;
+    mo->wcum = (uint64_t *)malloc_motif(ctx, mo, ((size_t)mo->nwtot + 1) * 16);
+    if (!mo->wcum) return TM_E_NOMEM;
+    k_window_cum<<<1, 1024, 0, st>>>(mo->layer[0].root_cdf, mo->layer[0].win_beg, nw0, mo->layer[1].root_cdf,
+                                     mo->layer[1].win_beg, nw1, mo->wcum);
+    uint64_t Wh[2] = {0, 0};
+    cudaMemcpyAsync(Wh, mo->wcum + 2 * (size_t)mo->nwtot, 16, cudaMemcpyDeviceToHost, st);
+    uint32_t bits = 0;
+    rc = read_status(ctx, &bits);
+    if (rc) return rc;
+    if (bits & ST_OVERFLOW) return set_err(ctx, TM_E_OVERFLOW, "a weight, prefix sum or window total exceeds 2^64");
+    if (bits) return set_err(ctx, TM_E_CUDA, "device status error in weight pass");
+    mo->W.lo = Wh[0];
+    mo->W.hi = Wh[1];
+    mo->have_weights = true;
+    mo->graph_epoch = ctx->epoch;
+    return TM_OK;
+}
+
+// w_{q,e} by gid for one layer, rebuilt from the stored prefix arrays.
+int export_weights(tm_ctx *ctx, tm_motif *mo, int q, int layer, uint64_t *host_out)
+{
+    const DevGraph &g = ctx->g;
+    const DevPlan &P = mo->plan;
+    cudaStream_t st = ctx->stream;
+    uint32_t m = g.m;
+    if (m == 0) return TM_OK;
+    uint64_t *out = (uint64_t *)dalloc(ctx, (size_t)m * 8);
+    if (!out) return TM_E_NOMEM;
+    int rc = TM_OK;
+    if (P.tleaf[q] && q != 0) {
+        k_leaf_weights<<<blocks_for(m, TB), TB, 0, st>>>(g.g_t, m, layer, P.delta, out);
+    } else if (q == 0) {
+        RootScan f{nullptr, g.g_t, layer, P.delta};
+        k_unprefix<RootScan><<<blocks_for(m, TB), TB, 0, st>>>(f, mo->layer[layer].root_cdf, nullptr, m, out);
+    } else {
+        OwnerBits ob;
+        rc = owner_bits(ctx, ob);
+        if (rc) return rc;
+        bool o = P.tout[q] != 0;
+        DirScan f{nullptr, nullptr, o ? g.out_t : g.in_t, o ? ob.out : ob.in, layer, P.delta};
+        k_unprefix<DirScan><<<blocks_for(m, TB), TB, 0, st>>>(f, mo->layer[layer].pref_dir[P.tslot[q]],
+                                                              o ? g.out_gid : g.in_gid, m, out);
+        rc = check_cuda(ctx, cudaStreamSynchronize(st), "export");
+        free_owner_bits(ctx, ob);
+    }
+    cudaMemcpyAsync(host_out, out, (size_t)m * 8, cudaMemcpyDeviceToHost, st);
+    int rc2 = check_cuda(ctx, cudaStreamSynchronize(st), "export copy");
+    dfree(ctx, out, (size_t)m * 8);
+    return rc ? rc : rc2;
+}
+
+void release_weights(tm_ctx *ctx, tm_motif *mo) { free_motif_weights(ctx, mo); }
+
+}  // namespace timest
