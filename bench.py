@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300-native TIMEST hot path.
+
+One step = one pass of the whole path over one synthetic input: load the
+device-resident edge arrays, build the temporal CSR, compute the weights of
+the motif's spanning tree (windows, DP, prefix sums, root CDF) and draw,
+validate and count k samples.  `value` is samples per second of whole steps
+(k / step time), timed with CUDA events on the library's stream; L2 is
+flushed (a 512 MB write) before every timed step, outside its events.
+
+Extra keys: per-phase times and launch counts from the library's event
+timers, the weight pass's achieved bandwidth, a roofline object for the
+dominant kernel, an end-to-end figure through the C ABI with host buffers
+(pinned), and the CPU oracle timed on a bounded sample of the same workload.
+
+`--impl reference` times the CPU oracle alone (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "cl2m_cycle4"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--k", type=int, default=0, help="override the sample count")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks ----
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------ algorithmic byte models ----
+def dp_bytes_per_edge(plan_children):
+    """Bytes one weight-DP launch must move per edge for a tree node with the
+    given children (list of (leaf, has_exclusion)), both layers:
+    the edge record (t, src, dst, pair) and the reverse-pair id, read once;
+    per layer and child the two list bounds (2 x 4 B offsets) and, for a
+    non-leaf child, the four prefix values that bound the candidate range
+    and its exclusion (4 x 8 B); per layer the 8 B weight written."""
+    b = 16 + 4
+    for _ in range(2):
+        for leaf in plan_children:
+            b += 8
+            if not leaf:
+                b += 32
+        b += 8
+    return b
+
+
+def sampler_bytes_per_sample(ntree, m, avg_deg):
+    """Reads a sample must make that no cache can share: the root draw's CDF
+    entry and edge record (8 + 16 B), and per tree edge the picked list entry
+    (t, nbr, gid: 12 B), its edge's pair id (4 B) and the prefix value at the
+    pick (8 B)."""
+    return 24 + (ntree - 1) * 24
+
+
+# ------------------------------------------------------------------ ours ----
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import paper_2507_20441_gb300 as tg
+    from paper_2507_20441_gb300 import synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    gr = synth.make_graph(args.workload)
+    mo = synth.make_motif(args.workload)
+    k = args.k or mo.k
+    stream = torch.cuda.Stream(device=dev)
+    ctx = tg.Context(device=local_rank, stream=stream.cuda_stream, profile=True)
+    src_d = torch.from_numpy(gr.src.view(np.int32)).to(dev)
+    dst_d = torch.from_numpy(gr.dst.view(np.int32)).to(dev)
+    t_d = torch.from_numpy(gr.t).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+
+    state = {}
+
+    def step(i, host=False):
+        first = (rank * 1_000_000 + i) * k
+        if host:
+            ctx.load_graph(gr.n, state["src_h"], state["dst_h"], state["t_h"], flags=tg.TM_HOST)
+        else:
+            ctx.load_graph(gr.n, src_d, dst_d, t_d, flags=tg.TM_DEVICE)
+        m = ctx.motif(mo.nv, mo.edges, mo.rank, mo.delta)
+        W = m.weights()
+        res = m.sample(k, args.seed, first)
+        state["plan"] = m.plan()
+        state["W"] = W
+        m.free()
+        return res
+
+    def timed(nsteps, host=False):
+        times = []
+        for i in range(nsteps):
+            with torch.cuda.stream(stream):
+                flush.fill_(i)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = step(i, host)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return times, res
+
+    for i in range(args.warmup):
+        step(10_000 + i)
+    ctx.phase_times()
+    ctx.io_bytes()
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times, res = timed(args.steps)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    phases = ctx.phase_times()
+    ctx.io_bytes()
+    my_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([my_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        my_ms = float(t.item())
+    ms_per_step = my_ms / args.steps
+    value = world * k * args.steps / (my_ms / 1e3)
+    launches = sum(n for _, n in phases.values())
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        state["src_h"] = torch.from_numpy(gr.src.view(np.int32)).pin_memory().numpy().view(np.uint32)
+        state["dst_h"] = torch.from_numpy(gr.dst.view(np.int32)).pin_memory().numpy().view(np.uint32)
+        state["t_h"] = torch.from_numpy(gr.t).pin_memory().numpy()
+        step(20_000, host=True)
+        ctx.phase_times(); ctx.io_bytes()
+        n_e2e = max(3, args.steps // 4)
+        t_e2e, _ = timed(n_e2e, host=True)
+        h2d, d2h = ctx.io_bytes()
+        ctx.phase_times()
+        e2e = {"value": k * n_e2e / (sum(t_e2e) / 1e3), "unit": "samples/s",
+               "h2d_bytes_per_step": h2d // n_e2e, "d2h_bytes_per_step": d2h // n_e2e,
+               "ms_per_step": sum(t_e2e) / n_e2e}
+
+    # ---- roofline of the dominant kernel
+    peak, peak_kind = measured_peaks()
+    per = {name: (ms / args.steps, n / args.steps) for name, (ms, n) in phases.items() if n}
+    order, parent = state["plan"]
+    ntree = len(order)
+    children = {q: [] for q in range(ntree)}
+    for q in range(1, ntree):
+        children[int(parent[q])].append(q)
+    m_edges = ctx.m
+    dp_bytes = 0
+    for q in range(ntree):
+        if children[q]:
+            dp_bytes += m_edges * dp_bytes_per_edge([not children[c] for c in children[q]])
+    dp_ms, dp_n = per.get("dp", (0.0, 0))
+    samp_ms, samp_n = per.get("sample", (0.0, 0))
+    weight_ms = sum(per.get(p, (0.0, 0))[0] for p in ("windows", "dp", "prefix", "root"))
+    candidates = {name: ms for name, (ms, n) in per.items()}
+    dominant = max(candidates, key=candidates.get)
+    if dominant == "sample":
+        algo = k * sampler_bytes_per_sample(ntree, m_edges, 0)
+        kern_ms = samp_ms / max(samp_n, 1)
+        kname = "k_sample"
+    else:
+        algo = dp_bytes / max(dp_n, 1)
+        kern_ms = dp_ms / max(dp_n, 1)
+        kname = "k_dp"
+    achieved = algo / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "algorithmic_bytes_per_launch": int(algo),
+                "launch_ms": round(kern_ms, 4), "dominant_phase": dominant}
+
+    out = {
+        "metric": "samples/s", "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": gr.n, "m": int(ctx.m), "motif": mo.name, "delta": mo.delta,
+                   "k": k, "tree": [int(x) for x in order], "root": int(order[0]),
+                   "l2": "flushed (512 MB write) before every timed step",
+                   "graph": "Chung-Lu bursty" if "cl" in args.workload else "uniform"},
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "phases_ms_per_step": {k_: round(v[0], 4) for k_, v in per.items()},
+        "weight_pass": {"ms": round(weight_ms, 4), "edges_per_s": m_edges / (weight_ms / 1e3) if weight_ms else None,
+                        "dp_GBps": round(dp_bytes / (dp_ms / 1e3) / 1e9, 1) if dp_ms else None,
+                        "dp_frac_of_peak": round(dp_bytes / (dp_ms / 1e3) / 1e9 / peak, 4) if dp_ms else None},
+        "estimate": res.estimate, "W": state["W"], "hits2": res.hits2, "valid": res.valid,
+    }
+    ctx.close()
+    return out
+
+
+# ------------------------------------------------------------- oracle ----
+def time_oracle(workload, k_full, seed, tree, root, k_sample, threads):
+    """The CPU oracle on the same workload: graph build and weights in full
+    (single thread), the sampler on k_sample of the k samples with OpenMP,
+    scaled to a whole step of k samples."""
+    import oracle
+    from paper_2507_20441_gb300 import synth
+    gr = synth.make_graph(workload)
+    mo = synth.make_motif(workload)
+    t0 = time.perf_counter()
+    G = oracle.Graph(gr.n, gr.src, gr.dst, gr.t)
+    t1 = time.perf_counter()
+    G.set_motif(mo.nv, mo.edges, mo.rank, mo.delta, tree, root)
+    G.weights()
+    t2 = time.perf_counter()
+    G.sample(k_sample, seed, 0, threads=threads)
+    t3 = time.perf_counter()
+    step_s = (t1 - t0) + (t2 - t1) + (t3 - t2) * (k_full / k_sample)
+    return {"value": k_full / step_s, "unit": "samples/s", "cores": threads, "kind": "oracle",
+            "sample": f"graph build + weights in full, {k_sample} of {k_full} samples timed and scaled",
+            "graph_s": round(t1 - t0, 3), "weights_s": round(t2 - t1, 3), "sample_s": round(t3 - t2, 3)}
+
+
+def default_tree(workload):
+    """The tree and root the library picks by default for this motif."""
+    import paper_2507_20441_gb300 as tg  # noqa: F401
+    from paper_2507_20441_gb300 import synth
+    mo = synth.make_motif(workload)
+    return mo
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+    from paper_2507_20441_gb300 import synth
+    oracle.build()
+    mo = synth.make_motif(args.workload)
+    k = args.k or mo.k
+    tree, root = reference_tree(mo)
+    threads = os.cpu_count() or 1
+    k_sample = min(k, 100_000)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = time_oracle(args.workload, k, args.seed + i, tree, root, k_sample, threads)
+        if i >= args.warmup:
+            vals.append(r)
+    step_s = statistics.mean(k / v["value"] for v in vals)
+    value = k / step_s
+    return {"impl": "reference", "metric": "samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": args.workload, "motif": mo.name, "delta": mo.delta, "k": k,
+                       "tree": tree, "root": root},
+            "cpu_baseline": {"kind": "oracle", "cores": threads, "value": value, "unit": "samples/s",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def reference_tree(mo):
+    """Default spanning tree and root, computed on the host exactly as
+    tm_set_motif documents: least looseness (pairs of tree edges at a
+    vertex, |pi(e1)-pi(e2)|-1), lexicographically first, rooted at the edge
+    of least eccentricity (ties: lower id)."""
+    import itertools
+    nv, edges, rank = mo.nv, mo.edges, mo.rank
+    best = None
+    for comb in itertools.combinations(range(len(edges)), nv - 1):
+        comp = list(range(nv)); ok = True
+        for e in comb:
+            a, b = edges[e]; ca, cb = comp[a], comp[b]
+            if ca == cb:
+                ok = False; break
+            comp = [ca if c == cb else c for c in comp]
+        if not ok:
+            continue
+        L = 0
+        for v in range(nv):
+            inc = [e for e in comb if v in edges[e]]
+            for i in range(len(inc)):
+                for j in range(i + 1, len(inc)):
+                    L += abs(rank[inc[i]] - rank[inc[j]]) - 1
+        if best is None or L < best[0]:
+            best = (L, list(comb))
+    tree = best[1]
+
+    def adj(x, y):
+        return bool(set(edges[x]) & set(edges[y]))
+    bestr = None
+    for r in tree:
+        dist = {r: 0}; frontier = [r]
+        while frontier:
+            nxt = []
+            for x in frontier:
+                for y in tree:
+                    if y not in dist and adj(x, y):
+                        dist[y] = dist[x] + 1; nxt.append(y)
+            frontier = nxt
+        ecc = max(dist.values())
+        if bestr is None or ecc < bestr[0]:
+            bestr = (ecc, r)
+    return tree, bestr[1]
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            tree = out["config"]["tree"]
+            out["cpu_baseline"] = time_oracle(args.workload, out["config"]["k"], args.seed, sorted(tree),
+                                              out["config"]["root"], min(out["config"]["k"], 100_000),
+                                              os.cpu_count() or 1)
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -79,7 +79,8 @@ typedef struct {
     int device;             /* CUDA device ordinal (default 0)              */
     int sample_threads;     /* threads per block of the sampler (0 = auto)  */
     int sample_tile;        /* samples per work item of batched runs (0 = auto) */
-    int reserved[8];
+    int profile;            /* 1: time every phase with CUDA events        */
+    int reserved[7];
 } tm_config;
 
 /* Result of one estimate.  estimate = W * hits2 / (2k) (Alg. 6 with the
@@ -185,6 +186,28 @@ int tm_sample_trace(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64
  * is bit-identical to tm_sample(ctx, motifs[q], k[q], seed[q], 0, ...). */
 int tm_batch_run(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64_t *k,
                  const uint64_t *seed, tm_result *out);
+
+/* Phases timed when cfg.profile = 1 (CUDA events on the context stream). */
+enum {
+    TM_PH_LOAD = 0,     /* tm_graph_load copy                               */
+    TM_PH_CSR = 1,      /* tm_preprocess: sorts, offsets, pair tables       */
+    TM_PH_WINDOWS = 2,  /* window lists of both layers                      */
+    TM_PH_DP = 3,       /* weight DP kernels (Claim 3.2)                    */
+    TM_PH_PREFIX = 4,   /* segmented prefix sums of child weights           */
+    TM_PH_ROOT = 5,     /* root CDF and window totals (Claim 3.4)           */
+    TM_PH_SAMPLE = 6,   /* sampler + validator + DeriveCnt + reduction      */
+    TM_PH_BATCH = 7,    /* batched sampler                                  */
+    TM_NUM_PHASES = 8
+};
+
+/* Accumulated milliseconds and kernel-launch counts per phase since the last
+ * call (ms[cap], launches[cap]; either may be NULL); resets the counters.
+ * Returns TM_NUM_PHASES in *nphases. */
+int tm_phase_times(tm_ctx *ctx, double *ms, uint64_t *launches, int cap, int *nphases);
+
+/* Host->device and device->host bytes copied by the library on ctx since the
+ * last call (inputs, results, counts and status words); resets them. */
+int tm_io_bytes(tm_ctx *ctx, uint64_t *h2d, uint64_t *d2h);
 
 /* Free a motif and its device weights. */
 void tm_motif_free(tm_motif *mo);

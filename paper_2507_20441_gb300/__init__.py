@@ -53,7 +53,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
 class tm_config(C.Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p), ("device", C.c_int),
-                ("sample_threads", C.c_int), ("sample_tile", C.c_int), ("reserved", C.c_int * 8)]
+                ("sample_threads", C.c_int), ("sample_tile", C.c_int), ("profile", C.c_int),
+                ("reserved", C.c_int * 7)]
 
 
 class tm_result(C.Structure):
@@ -104,6 +105,8 @@ def _declare(L):
     L.tm_sample_trace.argtypes = [vp, vp, u64, u64, u64, vp, vp, vp, C.POINTER(tm_result)]
     L.tm_batch_run.argtypes = [vp, u32, vp, vp, vp, vp]
     L.tm_motif_free.argtypes = [vp]; L.tm_motif_free.restype = None
+    L.tm_phase_times.argtypes = [vp, vp, vp, i32, C.POINTER(i32)]
+    L.tm_io_bytes.argtypes = [vp, C.POINTER(u64), C.POINTER(u64)]
     return L
 
 
@@ -169,7 +172,7 @@ class _TorchAllocator:
 # C-ABI functions under their own names
 # ---------------------------------------------------------------------------
 def tm_create(device: int = 0, stream=None, torch_allocator: bool = True, sample_threads: int = 0,
-              sample_tile: int = 0, alloc_hooks=None):
+              sample_tile: int = 0, alloc_hooks=None, profile: bool = False):
     """Returns an opaque context handle (c_void_p) plus the objects that must
     stay alive with it."""
     L = lib()
@@ -178,6 +181,7 @@ def tm_create(device: int = 0, stream=None, torch_allocator: bool = True, sample
     cfg.device = device
     cfg.sample_threads = sample_threads
     cfg.sample_tile = sample_tile
+    cfg.profile = 1 if profile else 0
     keep = []
     if alloc_hooks is not None:
         cfg.alloc, cfg.free = alloc_hooks
@@ -209,6 +213,8 @@ def tm_graph_load(ctx, n, src, dst, t, flags=TM_HOST):
     (pass TM_DEVICE)."""
     m = len(src)
     if flags & TM_DEVICE:
+        import torch
+        torch.cuda.synchronize()          # inputs written on torch's streams
         ps, pd, pt = _ptr(src), _ptr(dst), _ptr(t)
     else:
         src = np.ascontiguousarray(src, dtype=np.uint32)
@@ -304,6 +310,22 @@ def tm_motif_free(motif):
     lib().tm_motif_free(motif)
 
 
+PHASES = ["load", "csr", "windows", "dp", "prefix", "root", "sample", "batch"]
+
+
+def tm_phase_times(ctx):
+    """{phase: (ms, kernel launches)} accumulated since the last call."""
+    ms = np.zeros(16, np.float64); ln = np.zeros(16, np.uint64); n = C.c_int()
+    _check(lib().tm_phase_times(ctx, _ptr(ms), _ptr(ln), 16, C.byref(n)), ctx, "tm_phase_times")
+    return {PHASES[i] if i < len(PHASES) else str(i): (float(ms[i]), int(ln[i])) for i in range(n.value)}
+
+
+def tm_io_bytes(ctx):
+    h, d = C.c_uint64(), C.c_uint64()
+    _check(lib().tm_io_bytes(ctx, C.byref(h), C.byref(d)), ctx, "tm_io_bytes")
+    return int(h.value), int(d.value)
+
+
 # ---------------------------------------------------------------------------
 # Convenience objects over the same calls
 # ---------------------------------------------------------------------------
@@ -375,6 +397,12 @@ class Context:
 
     def motif(self, nv, edges, order, delta) -> Motif:
         return Motif(self, nv, edges, order, delta)
+
+    def phase_times(self):
+        return tm_phase_times(self.h)
+
+    def io_bytes(self):
+        return tm_io_bytes(self.h)
 
     def batch_run(self, motifs, ks, seeds):
         return tm_batch_run(self.h, [m.h for m in motifs], ks, seeds)

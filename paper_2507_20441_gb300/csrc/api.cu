@@ -47,15 +47,75 @@ void dfree(tm_ctx *ctx, void *p, size_t bytes)
     else cudaFreeAsync(p, ctx->stream);
 }
 
+void copy_h2d(tm_ctx *ctx, void *dst, const void *src, size_t bytes)
+{
+    ctx->h2d_bytes += bytes;
+    cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
+}
+
+void copy_d2h(tm_ctx *ctx, void *dst, const void *src, size_t bytes)
+{
+    ctx->d2h_bytes += bytes;
+    cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+}
+
 int read_status(tm_ctx *ctx, uint32_t *bits)
 {
-    cudaMemcpyAsync(ctx->status_host, ctx->status, 4, cudaMemcpyDeviceToHost, ctx->stream);
+    copy_d2h(ctx, ctx->status_host, ctx->status, 4);
     int rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "stream synchronize");
     *bits = rc ? 0 : *ctx->status_host;
+    if (!rc) prof_collect(ctx);
     return rc;
 }
 
 void release_weights(tm_ctx *ctx, tm_motif *mo);
+
+static cudaEvent_t take_event(tm_ctx *ctx)
+{
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    return e;
+}
+
+PhaseScope::PhaseScope(tm_ctx *c, int ph) : ctx(c), phase(ph), launches0(c->kernel_launches)
+{
+    if (ctx->cfg.profile) {
+        a = take_event(ctx);
+        if (a) cudaEventRecord(a, ctx->stream);
+    }
+}
+
+PhaseScope::~PhaseScope()
+{
+    uint64_t launches = ctx->kernel_launches - launches0;
+    if (!a) {
+        ctx->phase_launches[phase] += launches;
+        return;
+    }
+    cudaEvent_t b = take_event(ctx);
+    if (!b) { ctx->ev_pool.push_back(a); ctx->phase_launches[phase] += launches; return; }
+    cudaEventRecord(b, ctx->stream);
+    ctx->pending.push_back({phase, a, b, launches});
+}
+
+void prof_collect(tm_ctx *ctx)
+{
+    for (auto &p : ctx->pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
+            ctx->phase_ms[p.phase] += ms;
+        else cudaGetLastError();
+        ctx->phase_launches[p.phase] += p.launches;
+        ctx->ev_pool.push_back(p.a);
+        ctx->ev_pool.push_back(p.b);
+    }
+    ctx->pending.clear();
+}
 
 static void free_graph(tm_ctx *ctx)
 {
@@ -266,6 +326,10 @@ void tm_destroy(tm_ctx *ctx)
 {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    prof_collect(ctx);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    ctx->ev_pool.clear();
     free_input(ctx);
     free_graph(ctx);
     if (ctx->status) dfree(ctx, ctx->status, 64);
@@ -302,10 +366,15 @@ int tm_graph_load(tm_ctx *ctx, uint32_t n, uint64_t m, const uint32_t *src, cons
         ctx->in_t = (int64_t *)dalloc(ctx, m * 8);
         if (!ctx->in_src || !ctx->in_dst || !ctx->in_t) { free_input(ctx); return TM_E_NOMEM; }
         cudaMemcpyKind kind = (flags & TM_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-        cudaMemcpyAsync(ctx->in_src, src, m * 4, kind, ctx->stream);
-        cudaMemcpyAsync(ctx->in_dst, dst, m * 4, kind, ctx->stream);
-        cudaMemcpyAsync(ctx->in_t, t, m * 8, kind, ctx->stream);
+        {
+            PhaseScope ph(ctx, TM_PH_LOAD);
+            if (kind == cudaMemcpyHostToDevice) ctx->h2d_bytes += m * 16;
+            cudaMemcpyAsync(ctx->in_src, src, m * 4, kind, ctx->stream);
+            cudaMemcpyAsync(ctx->in_dst, dst, m * 4, kind, ctx->stream);
+            cudaMemcpyAsync(ctx->in_t, t, m * 8, kind, ctx->stream);
+        }
         int rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "graph copy");
+        prof_collect(ctx);
         if (rc) { free_input(ctx); return rc; }
     }
     ctx->loaded = true;
@@ -318,7 +387,13 @@ int tm_preprocess(tm_ctx *ctx)
     if (!ctx->loaded) return set_err(ctx, TM_E_STATE, "no graph loaded");
     cudaSetDevice(ctx->device);
     free_graph(ctx);
-    int rc = build_csr(ctx);
+    int rc;
+    {
+        PhaseScope ph(ctx, TM_PH_CSR);
+        rc = build_csr(ctx);
+    }
+    cudaStreamSynchronize(ctx->stream);
+    prof_collect(ctx);
     if (rc) { free_graph(ctx); return rc; }
     free_input(ctx);
     ctx->loaded = false;
@@ -342,9 +417,9 @@ int tm_edges_export(tm_ctx *ctx, uint32_t *src, uint32_t *dst, uint32_t *tprime)
     if (!ctx->preprocessed) return set_err(ctx, TM_E_STATE, "graph not preprocessed");
     size_t b = (size_t)ctx->g.m * 4;
     if (b) {
-        if (src) cudaMemcpyAsync(src, ctx->g.g_src, b, cudaMemcpyDeviceToHost, ctx->stream);
-        if (dst) cudaMemcpyAsync(dst, ctx->g.g_dst, b, cudaMemcpyDeviceToHost, ctx->stream);
-        if (tprime) cudaMemcpyAsync(tprime, ctx->g.g_t, b, cudaMemcpyDeviceToHost, ctx->stream);
+        if (src) copy_d2h(ctx, src, ctx->g.g_src, b);
+        if (dst) copy_d2h(ctx, dst, ctx->g.g_dst, b);
+        if (tprime) copy_d2h(ctx, tprime, ctx->g.g_t, b);
     }
     return check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "edge export");
 }
@@ -455,9 +530,9 @@ int tm_window_totals(tm_ctx *ctx, tm_motif *mo, uint64_t *host_out, uint64_t cap
     // the device keeps the non-empty windows only: expand to the dense index
     std::vector<uint64_t> wc(2 * ((size_t)mo->nwtot + 1));
     std::vector<uint32_t> id0(mo->layer[0].nwin + 1), id1(mo->layer[1].nwin + 1);
-    cudaMemcpyAsync(wc.data(), mo->wcum, wc.size() * 8, cudaMemcpyDeviceToHost, ctx->stream);
-    cudaMemcpyAsync(id0.data(), mo->layer[0].win_id, id0.size() * 4, cudaMemcpyDeviceToHost, ctx->stream);
-    cudaMemcpyAsync(id1.data(), mo->layer[1].win_id, id1.size() * 4, cudaMemcpyDeviceToHost, ctx->stream);
+    copy_d2h(ctx, wc.data(), mo->wcum, wc.size() * 8);
+    copy_d2h(ctx, id0.data(), mo->layer[0].win_id, id0.size() * 4);
+    copy_d2h(ctx, id1.data(), mo->layer[1].win_id, id1.size() * 4);
     rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "window totals");
     if (rc) return rc;
     for (uint64_t i = 0; i < std::min(cap, nw); ++i) host_out[i] = 0;
@@ -498,6 +573,30 @@ int tm_batch_run(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64
     }
     cudaSetDevice(ctx->device);
     return run_batch(ctx, nq, motifs, k, seed, out);
+}
+
+int tm_io_bytes(tm_ctx *ctx, uint64_t *h2d, uint64_t *d2h)
+{
+    if (!ctx) return TM_E_ARG;
+    if (h2d) *h2d = ctx->h2d_bytes;
+    if (d2h) *d2h = ctx->d2h_bytes;
+    ctx->h2d_bytes = ctx->d2h_bytes = 0;
+    return TM_OK;
+}
+
+int tm_phase_times(tm_ctx *ctx, double *ms, uint64_t *launches, int cap, int *nphases)
+{
+    if (!ctx) return TM_E_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    prof_collect(ctx);
+    for (int i = 0; i < TM_NUM_PHASES && i < cap; ++i) {
+        if (ms) ms[i] = ctx->phase_ms[i];
+        if (launches) launches[i] = ctx->phase_launches[i];
+    }
+    for (int i = 0; i < TM_NUM_PHASES; ++i) { ctx->phase_ms[i] = 0; ctx->phase_launches[i] = 0; }
+    if (nphases) *nphases = TM_NUM_PHASES;
+    return TM_OK;
 }
 
 void tm_motif_free(tm_motif *mo)

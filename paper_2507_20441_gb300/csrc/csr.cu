@@ -123,17 +123,17 @@ int radix_sort(tm_ctx *ctx, uint32_t *key, uint32_t *p0, uint32_t *p1, uint32_t 
     int passes = (bits + 7) / 8;
     for (int pass = 0; pass < passes && rc == TM_OK; ++pass) {
         int shift = pass * 8;
-        k_rs_hist<<<ntiles, RS_THREADS, 0, ctx->stream>>>(ki, n, shift, hist, ntiles);
+        launch(ctx, k_rs_hist, ntiles, RS_THREADS, ki, n, shift, hist, ntiles);
         rc = exclusive_scan_u32(ctx, hist, hist, (uint64_t)ntiles * 256, nullptr);
         if (rc != TM_OK) break;
         if (np == 0)
-            k_rs_scatter<0><<<ntiles, RS_THREADS, 0, ctx->stream>>>(ki, nullptr, nullptr, ko, nullptr, nullptr, n,
+            launch(ctx, k_rs_scatter<0>, ntiles, RS_THREADS, ki, nullptr, nullptr, ko, nullptr, nullptr, n,
                                                                      shift, hist, ntiles);
         else if (np == 1)
-            k_rs_scatter<1><<<ntiles, RS_THREADS, 0, ctx->stream>>>(ki, ai, nullptr, ko, ao, nullptr, n, shift, hist,
+            launch(ctx, k_rs_scatter<1>, ntiles, RS_THREADS, ki, ai, nullptr, ko, ao, nullptr, n, shift, hist,
                                                                      ntiles);
         else
-            k_rs_scatter<2><<<ntiles, RS_THREADS, 0, ctx->stream>>>(ki, ai, bi, ko, ao, bo, n, shift, hist, ntiles);
+            launch(ctx, k_rs_scatter<2>, ntiles, RS_THREADS, ki, ai, bi, ko, ao, bo, n, shift, hist, ntiles);
         rc = check_cuda(ctx, cudaGetLastError(), "radix scatter");
         std::swap(ki, ko); std::swap(ai, ao); std::swap(bi, bo);
     }
@@ -317,12 +317,12 @@ int build_csr(tm_ctx *ctx)
     Stats hs{LLONG_MAX, LLONG_MIN, 0, 0};
     Stats *ds = (Stats *)dalloc(ctx, sizeof(Stats));
     if (!ds) return TM_E_NOMEM;
-    cudaMemcpyAsync(ds, &hs, sizeof(Stats), cudaMemcpyHostToDevice, st);
+    copy_h2d(ctx, ds, &hs, sizeof(Stats));
     if (m0) {
         unsigned nb = std::min<uint64_t>(blocks_for(m0, TB), (uint64_t)ctx->num_sms * 8);
-        k_input_stats<<<nb, TB, 0, st>>>(ctx->in_src, ctx->in_dst, ctx->in_t, m0, n, ds);
+        launch(ctx, k_input_stats, nb, TB, ctx->in_src, ctx->in_dst, ctx->in_t, m0, n, ds);
     }
-    cudaMemcpyAsync(&hs, ds, sizeof(Stats), cudaMemcpyDeviceToHost, st);
+    copy_d2h(ctx, &hs, ds, sizeof(Stats));
     rc = check_cuda(ctx, cudaStreamSynchronize(st), "input statistics");
     dfree(ctx, ds, sizeof(Stats));
     if (rc) return rc;
@@ -343,15 +343,15 @@ int build_csr(tm_ctx *ctx)
     if (hs.nself) {
         uint32_t *keep = (uint32_t *)dalloc(ctx, m0 * 4), *pos = (uint32_t *)dalloc(ctx, m0 * 4);
         if (!keep || !pos) return TM_E_NOMEM;
-        k_keep_nonself<<<blocks_for(m0, TB), TB, 0, st>>>(ctx->in_src, ctx->in_dst, m0, keep);
+        launch(ctx, k_keep_nonself, blocks_for(m0, TB), TB, ctx->in_src, ctx->in_dst, m0, keep);
         rc = exclusive_scan_u32(ctx, keep, pos, m0, nullptr);
         if (rc) return rc;
-        k_compact_input<<<blocks_for(m0, TB), TB, 0, st>>>(ctx->in_src, ctx->in_dst, ctx->in_t, m0, keep, pos, tmin,
+        launch(ctx, k_compact_input, blocks_for(m0, TB), TB, ctx->in_src, ctx->in_dst, ctx->in_t, m0, keep, pos, tmin,
                                                            T0, S0, D0);
         dfree(ctx, keep, m0 * 4);
         dfree(ctx, pos, m0 * 4);
     } else if (m) {
-        k_compact_input<<<blocks_for(m0, TB), TB, 0, st>>>(ctx->in_src, ctx->in_dst, ctx->in_t, m0, nullptr, nullptr,
+        launch(ctx, k_compact_input, blocks_for(m0, TB), TB, ctx->in_src, ctx->in_dst, ctx->in_t, m0, nullptr, nullptr,
                                                            tmin, T0, S0, D0);
     }
     // ---- GLOBAL order: LSD by dst, then src, then t'
@@ -367,9 +367,9 @@ int build_csr(tm_ctx *ctx)
         unsigned long long *nd = (unsigned long long *)dalloc(ctx, 8);
         if (!keep || !nd) return TM_E_NOMEM;
         cudaMemsetAsync(nd, 0, 8, st);
-        if (m) k_flag_unique<<<blocks_for(m, TB), TB, 0, st>>>(T0, S0, D0, m, keep, nd);
+        if (m) launch(ctx, k_flag_unique, blocks_for(m, TB), TB, T0, S0, D0, m, keep, nd);
         unsigned long long ndup = 0;
-        cudaMemcpyAsync(&ndup, nd, 8, cudaMemcpyDeviceToHost, st);
+        copy_d2h(ctx, &ndup, nd, 8);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "duplicate scan");
         dfree(ctx, nd, 8);
         if (rc) return rc;
@@ -384,7 +384,7 @@ int build_csr(tm_ctx *ctx)
             if (!pos) return TM_E_NOMEM;
             rc = exclusive_scan_u32(ctx, keep, pos, m, nullptr);
             if (rc) return rc;
-            k_compact3<<<blocks_for(m, TB), TB, 0, st>>>(T0, S0, D0, m, keep, pos, g.g_t, g.g_src, g.g_dst);
+            launch(ctx, k_compact3, blocks_for(m, TB), TB, T0, S0, D0, m, keep, pos, g.g_t, g.g_src, g.g_dst);
             dfree(ctx, pos, (size_t)m * 4);
         } else if (m) {
             cudaMemcpyAsync(g.g_t, T0, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
@@ -406,21 +406,21 @@ int build_csr(tm_ctx *ctx)
         return TM_E_NOMEM;
     if (m) {
         cudaMemcpyAsync(key, g.g_src, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
-        k_iota<<<blocks_for(m, TB), TB, 0, st>>>(g.out_gid, m);
+        launch(ctx, k_iota, blocks_for(m, TB), TB, g.out_gid, m);
         rc = radix_sort(ctx, key, g.out_gid, nullptr, m, vbits);
         if (rc) return rc;
-        k_gather2<<<blocks_for(m, TB), TB, 0, st>>>(g.out_gid, m, g.g_t, g.g_dst, g.out_t, g.out_nbr);
+        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.out_gid, m, g.g_t, g.g_dst, g.out_t, g.out_nbr);
     }
-    k_offsets<<<blocks_for((uint64_t)m + 1, TB), TB, 0, st>>>(key, m, n, g.out_off);
+    launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, key, m, n, g.out_off);
     // ---- IN order: stable sort of gid by dst
     if (m) {
         cudaMemcpyAsync(key, g.g_dst, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
-        k_iota<<<blocks_for(m, TB), TB, 0, st>>>(g.in_gid, m);
+        launch(ctx, k_iota, blocks_for(m, TB), TB, g.in_gid, m);
         rc = radix_sort(ctx, key, g.in_gid, nullptr, m, vbits);
         if (rc) return rc;
-        k_gather2<<<blocks_for(m, TB), TB, 0, st>>>(g.in_gid, m, g.g_t, g.g_src, g.in_t, g.in_nbr);
+        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.in_gid, m, g.g_t, g.g_src, g.in_t, g.in_nbr);
     }
-    k_offsets<<<blocks_for((uint64_t)m + 1, TB), TB, 0, st>>>(key, m, n, g.in_off);
+    launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, key, m, n, g.in_off);
     // ---- multi-edge order: stable re-sort of the IN order by source
     g.multi_gid = galloc(ctx, m); g.multi_t = galloc(ctx, m); g.g_pair = galloc(ctx, m);
     g.vpair_off = galloc(ctx, (size_t)n + 1);
@@ -431,17 +431,17 @@ int build_csr(tm_ctx *ctx)
         cudaMemcpyAsync(g.multi_gid, g.in_gid, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
         rc = radix_sort(ctx, key, g.multi_gid, nullptr, m, vbits);
         if (rc) return rc;
-        k_gather2<<<blocks_for(m, TB), TB, 0, st>>>(g.multi_gid, m, g.g_t, g.g_dst, g.multi_t, tmp);
+        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.multi_gid, m, g.g_t, g.g_dst, g.multi_t, tmp);
         // key = pair src, tmp = pair dst per multi position
         uint32_t *head = T0;
         uint32_t *pid = (uint32_t *)dalloc(ctx, (size_t)m * 4);
         uint32_t *dnp = (uint32_t *)dalloc(ctx, 4);
         if (!pid || !dnp) return TM_E_NOMEM;
-        k_pair_heads<<<blocks_for(m, TB), TB, 0, st>>>(key, tmp, m, head);
+        launch(ctx, k_pair_heads, blocks_for(m, TB), TB, key, tmp, m, head);
         rc = exclusive_scan_u32(ctx, head, pid, m, dnp);
         if (rc) return rc;
         // total = pid[m-1] + head[m-1]; the scan wrote the exclusive total
-        cudaMemcpyAsync(&np, dnp, 4, cudaMemcpyDeviceToHost, st);
+        copy_d2h(ctx, &np, dnp, 4);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "pair count");
         if (rc) return rc;
         g.npairs = np;
@@ -450,11 +450,11 @@ int build_csr(tm_ctx *ctx)
         g.rev_pair = galloc(ctx, np);
         uint32_t *pair_src = (uint32_t *)dalloc(ctx, (size_t)(np ? np : 1) * 4);
         if (!g.pair_off || !g.pair_dst || !g.rev_pair || !pair_src) return TM_E_NOMEM;
-        k_pair_fill<<<blocks_for(m, TB), TB, 0, st>>>(key, tmp, g.multi_gid, head, pid, m, g.pair_off, pair_src,
+        launch(ctx, k_pair_fill, blocks_for(m, TB), TB, key, tmp, g.multi_gid, head, pid, m, g.pair_off, pair_src,
                                                       g.pair_dst, g.g_pair);
-        cudaMemcpyAsync(g.pair_off + np, &m, 4, cudaMemcpyHostToDevice, st);
-        k_offsets<<<blocks_for((uint64_t)np + 1, TB), TB, 0, st>>>(pair_src, np, n, g.vpair_off);
-        k_rev_pairs<<<blocks_for(np, TB), TB, 0, st>>>(pair_src, g.pair_dst, g.vpair_off, np, g.rev_pair);
+        copy_h2d(ctx, g.pair_off + np, &m, 4);
+        launch(ctx, k_offsets, blocks_for((uint64_t)np + 1, TB), TB, pair_src, np, n, g.vpair_off);
+        launch(ctx, k_rev_pairs, blocks_for(np, TB), TB, pair_src, g.pair_dst, g.vpair_off, np, g.rev_pair);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "pair tables");
         dfree(ctx, pair_src, (size_t)(np ? np : 1) * 4);
         dfree(ctx, pid, (size_t)m * 4);
@@ -465,7 +465,7 @@ int build_csr(tm_ctx *ctx)
         g.pair_dst = galloc(ctx, 1);
         g.rev_pair = galloc(ctx, 1);
         cudaMemsetAsync(g.pair_off, 0, 4, st);
-        k_offsets<<<1, TB, 0, st>>>(key, 0, n, g.vpair_off);
+        launch(ctx, k_offsets, 1, TB, key, 0, n, g.vpair_off);
     }
     dfree(ctx, T0, (size_t)(m0 ? m0 : 1) * 4 > (size_t)(m1 ? m1 : 1) * 4 ? (size_t)(m1 ? m1 : 1) * 4 : (size_t)(m1 ? m1 : 1) * 4);
     dfree(ctx, S0, (size_t)(m1 ? m1 : 1) * 4);

@@ -373,7 +373,7 @@ int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t f
     if (!scratch) return TM_E_NOMEM;
     DevPlan *dplan = (DevPlan *)scratch;
     Acc *dacc = (Acc *)(scratch + ((plan_bytes + 15) / 16) * 16);
-    cudaMemcpyAsync(dplan, &mo->plan, plan_bytes, cudaMemcpyHostToDevice, st);
+    copy_h2d(ctx, dplan, &mo->plan, plan_bytes);
     cudaMemsetAsync(dacc, 0, acc_bytes, st);
     cudaMemsetAsync(ctx->status, 0, 4, st);
     SampleJob J;
@@ -384,25 +384,29 @@ int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t f
     unsigned blocks = (unsigned)std::max<uint64_t>(1, std::min(want, cap));
     uint32_t *dg = nullptr; uint64_t *dc = nullptr; int32_t *dr = nullptr;
     size_t gbytes = 0;
-    if (trace) {
-        gbytes = (size_t)k * (4 * mo->plan.ntree + 8 + 4);
-        char *t = (char *)dalloc(ctx, gbytes);
-        if (!t) { dfree(ctx, scratch, plan_bytes + acc_bytes + 64); return TM_E_NOMEM; }
-        dc = (uint64_t *)t;
-        dr = (int32_t *)(t + (size_t)k * 8);
-        dg = (uint32_t *)(t + (size_t)k * 12);
-        k_sample<true><<<blocks, threads, 0, st>>>(ctx->g, dplan, J, seed, first, k, dacc, ctx->status, dg, dc, dr);
-    } else {
-        k_sample<false><<<blocks, threads, 0, st>>>(ctx->g, dplan, J, seed, first, k, dacc, ctx->status, nullptr,
-                                                    nullptr, nullptr);
+    int rc;
+    {
+        PhaseScope ph(ctx, TM_PH_SAMPLE);
+        if (trace) {
+            gbytes = (size_t)k * (4 * mo->plan.ntree + 8 + 4);
+            char *t = (char *)dalloc(ctx, gbytes);
+            if (!t) { dfree(ctx, scratch, plan_bytes + acc_bytes + 64); return TM_E_NOMEM; }
+            dc = (uint64_t *)t;
+            dr = (int32_t *)(t + (size_t)k * 8);
+            dg = (uint32_t *)(t + (size_t)k * 12);
+            launch(ctx, k_sample<true>, blocks, threads, ctx->g, dplan, J, seed, first, k, dacc, ctx->status, dg, dc, dr);
+        } else {
+            launch(ctx, k_sample<false>, blocks, threads, ctx->g, dplan, J, seed, first, k, dacc, ctx->status, nullptr,
+                                                        nullptr, nullptr);
+        }
+        rc = check_cuda(ctx, cudaGetLastError(), "sampler launch");
     }
-    int rc = check_cuda(ctx, cudaGetLastError(), "sampler launch");
     Acc h{};
-    cudaMemcpyAsync(&h, dacc, acc_bytes, cudaMemcpyDeviceToHost, st);
+    copy_d2h(ctx, &h, dacc, acc_bytes);
     if (trace && rc == TM_OK) {
-        if (trace_gids) cudaMemcpyAsync(trace_gids, dg, (size_t)k * 4 * mo->plan.ntree, cudaMemcpyDeviceToHost, st);
-        if (trace_contrib) cudaMemcpyAsync(trace_contrib, dc, (size_t)k * 8, cudaMemcpyDeviceToHost, st);
-        if (trace_reason) cudaMemcpyAsync(trace_reason, dr, (size_t)k * 4, cudaMemcpyDeviceToHost, st);
+        if (trace_gids) copy_d2h(ctx, trace_gids, dg, (size_t)k * 4 * mo->plan.ntree);
+        if (trace_contrib) copy_d2h(ctx, trace_contrib, dc, (size_t)k * 8);
+        if (trace_reason) copy_d2h(ctx, trace_reason, dr, (size_t)k * 4);
     }
     uint32_t bits = 0;
     int rc2 = read_status(ctx, &bits);

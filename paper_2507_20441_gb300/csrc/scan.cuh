@@ -97,15 +97,15 @@ inline int exclusive_scan_u32(tm_ctx *ctx, const uint32_t *in, uint32_t *out, ui
     }
     uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (tiles == 1) {
-        k_tile_scan_u32<<<1, SCAN_THREADS, 0, ctx->stream>>>(in, n, nullptr, out, total);
+        launch(ctx, k_tile_scan_u32, 1, SCAN_THREADS, in, n, nullptr, out, total);
         return check_cuda(ctx, cudaGetLastError(), "scan");
     }
     uint32_t *ts = (uint32_t *)dalloc(ctx, tiles * sizeof(uint32_t));
     if (!ts) return TM_E_NOMEM;
-    k_tile_sum_u32<<<(unsigned)tiles, SCAN_THREADS, 0, ctx->stream>>>(in, n, ts);
+    launch(ctx, k_tile_sum_u32, (unsigned)tiles, SCAN_THREADS, in, n, ts);
     int rc = exclusive_scan_u32(ctx, ts, ts, tiles, nullptr);
     if (rc == TM_OK) {
-        k_tile_scan_u32<<<(unsigned)tiles, SCAN_THREADS, 0, ctx->stream>>>(in, n, ts, out, total);
+        launch(ctx, k_tile_scan_u32, (unsigned)tiles, SCAN_THREADS, in, n, ts, out, total);
         rc = check_cuda(ctx, cudaGetLastError(), "scan");
     }
     dfree(ctx, ts, tiles * sizeof(uint32_t));
@@ -261,9 +261,9 @@ int segmented_scan_u64(tm_ctx *ctx, const F &f, uint64_t n, uint64_t *out)
     uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     SegAgg *aggs = (SegAgg *)dalloc(ctx, tiles * sizeof(SegAgg));
     if (!aggs) return TM_E_NOMEM;
-    k_segscan_reduce<F><<<(unsigned)tiles, SCAN_THREADS, 0, ctx->stream>>>(f, n, aggs, ctx->status);
-    k_segscan_carries<<<1, 1024, 0, ctx->stream>>>(aggs, tiles, ctx->status);
-    k_segscan_final<F><<<(unsigned)tiles, SCAN_THREADS, 0, ctx->stream>>>(f, n, aggs, out, ctx->status);
+    launch(ctx, k_segscan_reduce<F>, (unsigned)tiles, SCAN_THREADS, f, n, aggs, ctx->status);
+    launch(ctx, k_segscan_carries, 1, 1024, aggs, tiles, ctx->status);
+    launch(ctx, k_segscan_final<F>, (unsigned)tiles, SCAN_THREADS, f, n, aggs, out, ctx->status);
     int rc = check_cuda(ctx, cudaGetLastError(), "segmented scan");
     dfree(ctx, aggs, tiles * sizeof(SegAgg));
     return rc;

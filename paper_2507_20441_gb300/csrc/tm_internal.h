@@ -123,6 +123,14 @@ struct tm_ctx {
     uint32_t *status = nullptr;          // device status word
     uint32_t *status_host = nullptr;     // pinned mirror
     int num_sms = 0;
+    // phase timing (cfg.profile)
+    struct PendingPhase { int phase; cudaEvent_t a, b; uint64_t launches; };
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<PendingPhase> pending;
+    double phase_ms[TM_NUM_PHASES] = {};
+    uint64_t h2d_bytes = 0, d2h_bytes = 0;     // host<->device traffic issued
+    uint64_t kernel_launches = 0;              // kernels launched by this context
+    uint64_t phase_launches[TM_NUM_PHASES] = {};
 };
 
 namespace timest {
@@ -153,6 +161,33 @@ int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t f
                 tm_result *out, uint32_t *trace_gids, uint64_t *trace_contrib, int32_t *trace_reason);
 int run_batch(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64_t *k,
               const uint64_t *seed, tm_result *out);
+
+// ---- phase timing ----
+// Scope that records CUDA events around a group of launches of one phase;
+// the elapsed time is folded in by prof_collect() after the next sync.
+struct PhaseScope {
+    tm_ctx *ctx;
+    int phase;
+    cudaEvent_t a = nullptr;
+    uint64_t launches0 = 0;
+    PhaseScope(tm_ctx *c, int ph);
+    ~PhaseScope();
+};
+
+// Every kernel of the library is launched through here (counted per context).
+#ifdef __CUDACC__
+template <typename... KArgs, typename... Args>
+inline void launch(tm_ctx *ctx, void (*kernel)(KArgs...), dim3 grid, dim3 block, Args &&...args)
+{
+    ++ctx->kernel_launches;
+    kernel<<<grid, block, 0, ctx->stream>>>(static_cast<KArgs>(args)...);
+}
+#endif
+void prof_collect(tm_ctx *ctx);   // call after the stream is synchronized
+
+// ---- counted host<->device copies on the context stream ----
+void copy_h2d(tm_ctx *ctx, void *dst, const void *src, size_t bytes);
+void copy_d2h(tm_ctx *ctx, void *dst, const void *src, size_t bytes);
 
 // ---- common ----
 int check_cuda(tm_ctx *ctx, cudaError_t e, const char *what);

@@ -254,7 +254,7 @@ static int owner_bits(tm_ctx *ctx, OwnerBits &ob)
         uint32_t *b = (uint32_t *)dalloc(ctx, words * 4);
         if (!b) return TM_E_NOMEM;
         cudaMemsetAsync(b, 0, words * 4, ctx->stream);
-        if (nown[k]) k_owner_bits<<<blocks_for(nown[k], TB), TB, 0, ctx->stream>>>(offs[k], nown[k], g.m, b);
+        if (nown[k]) launch(ctx, k_owner_bits, blocks_for(nown[k], TB), TB, offs[k], nown[k], g.m, b);
         *dst[k] = b;
     }
     return check_cuda(ctx, cudaGetLastError(), "owner bits");
@@ -281,6 +281,7 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     cudaMemsetAsync(ctx->status, 0, 4, st);
     // ---- windows of each layer (K2)
     for (int p = 0; p < 2; ++p) {
+        PhaseScope ph(ctx, TM_PH_WINDOWS);
         LayerData &L = mo->layer[p];
         uint32_t *flag = (uint32_t *)dalloc(ctx, (size_t)(m ? m : 1) * 4);
         uint32_t *pos = (uint32_t *)dalloc(ctx, (size_t)(m ? m : 1) * 4);
@@ -288,10 +289,10 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
         if (!flag || !pos || !dcount) return TM_E_NOMEM;
         uint32_t nw = 0;
         if (m) {
-            k_window_heads<<<blocks_for(m, TB), TB, 0, st>>>(g.g_t, m, p, d, flag);
+            launch(ctx, k_window_heads, blocks_for(m, TB), TB, g.g_t, m, p, d, flag);
             rc = exclusive_scan_u32(ctx, flag, pos, m, dcount);
             if (rc) return rc;
-            cudaMemcpyAsync(&nw, dcount, 4, cudaMemcpyDeviceToHost, st);
+            copy_d2h(ctx, &nw, dcount, 4);
             rc = check_cuda(ctx, cudaStreamSynchronize(st), "window count");
             if (rc) return rc;
         }
@@ -299,8 +300,8 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
         L.win_beg = (uint32_t *)malloc_motif(ctx, mo, ((size_t)nw + 1) * 4);
         L.win_id = (uint32_t *)malloc_motif(ctx, mo, ((size_t)nw + 1) * 4);
         if (!L.win_beg || !L.win_id) return TM_E_NOMEM;
-        if (m) k_window_fill<<<blocks_for(m, TB), TB, 0, st>>>(g.g_t, flag, pos, m, p, d, L.win_beg, L.win_id);
-        cudaMemcpyAsync(L.win_beg + nw, &g.m, 4, cudaMemcpyHostToDevice, st);
+        if (m) launch(ctx, k_window_fill, blocks_for(m, TB), TB, g.g_t, flag, pos, m, p, d, L.win_beg, L.win_id);
+        copy_h2d(ctx, L.win_beg + nw, &g.m, 4);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "window fill");
         dfree(ctx, flag, (size_t)(m ? m : 1) * 4);
         dfree(ctx, pos, (size_t)(m ? m : 1) * 4);
@@ -324,10 +325,14 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
             if (P.height[q] == h) order.push_back(q);
     if (P.tleaf[0]) order.push_back(0);   // single-edge motif: the root is a leaf
     for (int q : order) {
-        if (m) k_dp<<<blocks_for(m, TB), TB, 0, st>>>(g, P, q, cp, w[0], w[1], ctx->status);
+        {
+            PhaseScope ph(ctx, TM_PH_DP);
+            if (m) { launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, q, cp, w[0], w[1], ctx->status); }
+        }
         rc = check_cuda(ctx, cudaGetLastError(), "weight DP");
         if (rc) return rc;
         if (q == 0) {
+            PhaseScope ph(ctx, TM_PH_ROOT);
             for (int p = 0; p < 2; ++p) {
                 LayerData &L = mo->layer[p];
                 L.root_cdf = (uint64_t *)malloc_motif(ctx, mo, (size_t)(m ? m : 1) * 8);
@@ -337,6 +342,7 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
                 if (rc) return rc;
             }
         } else {
+            PhaseScope ph(ctx, TM_PH_PREFIX);
             int slot = P.tslot[q];
             bool out = P.tout[q] != 0;
             for (int p = 0; p < 2; ++p) {
@@ -363,10 +369,13 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     mo->nwtot = nw0 + nw1;
     mo->wcum = (uint64_t *)malloc_motif(ctx, mo, ((size_t)mo->nwtot + 1) * 16);
     if (!mo->wcum) return TM_E_NOMEM;
-    k_window_cum<<<1, 1024, 0, st>>>(mo->layer[0].root_cdf, mo->layer[0].win_beg, nw0, mo->layer[1].root_cdf,
-                                     mo->layer[1].win_beg, nw1, mo->wcum);
     uint64_t Wh[2] = {0, 0};
-    cudaMemcpyAsync(Wh, mo->wcum + 2 * (size_t)mo->nwtot, 16, cudaMemcpyDeviceToHost, st);
+    {
+        PhaseScope ph(ctx, TM_PH_ROOT);
+        launch(ctx, k_window_cum, 1, 1024, mo->layer[0].root_cdf, mo->layer[0].win_beg, nw0, mo->layer[1].root_cdf,
+                                         mo->layer[1].win_beg, nw1, mo->wcum);
+        copy_d2h(ctx, Wh, mo->wcum + 2 * (size_t)mo->nwtot, 16);
+    }
     uint32_t bits = 0;
     rc = read_status(ctx, &bits);
     if (rc) return rc;
@@ -391,22 +400,22 @@ int export_weights(tm_ctx *ctx, tm_motif *mo, int q, int layer, uint64_t *host_o
     if (!out) return TM_E_NOMEM;
     int rc = TM_OK;
     if (P.tleaf[q] && q != 0) {
-        k_leaf_weights<<<blocks_for(m, TB), TB, 0, st>>>(g.g_t, m, layer, P.delta, out);
+        launch(ctx, k_leaf_weights, blocks_for(m, TB), TB, g.g_t, m, layer, P.delta, out);
     } else if (q == 0) {
         RootScan f{nullptr, g.g_t, layer, P.delta};
-        k_unprefix<RootScan><<<blocks_for(m, TB), TB, 0, st>>>(f, mo->layer[layer].root_cdf, nullptr, m, out);
+        launch(ctx, k_unprefix<RootScan>, blocks_for(m, TB), TB, f, mo->layer[layer].root_cdf, nullptr, m, out);
     } else {
         OwnerBits ob;
         rc = owner_bits(ctx, ob);
         if (rc) return rc;
         bool o = P.tout[q] != 0;
         DirScan f{nullptr, nullptr, o ? g.out_t : g.in_t, o ? ob.out : ob.in, layer, P.delta};
-        k_unprefix<DirScan><<<blocks_for(m, TB), TB, 0, st>>>(f, mo->layer[layer].pref_dir[P.tslot[q]],
+        launch(ctx, k_unprefix<DirScan>, blocks_for(m, TB), TB, f, mo->layer[layer].pref_dir[P.tslot[q]],
                                                               o ? g.out_gid : g.in_gid, m, out);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "export");
         free_owner_bits(ctx, ob);
     }
-    cudaMemcpyAsync(host_out, out, (size_t)m * 8, cudaMemcpyDeviceToHost, st);
+    copy_d2h(ctx, host_out, out, (size_t)m * 8);
     int rc2 = check_cuda(ctx, cudaStreamSynchronize(st), "export copy");
     dfree(ctx, out, (size_t)m * 8);
     return rc ? rc : rc2;
