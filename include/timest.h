@@ -181,6 +181,24 @@ int tm_sample(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t fir
 int tm_sample_trace(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first_index,
                     uint32_t *tree_gids, uint64_t *contrib, int32_t *reason, tm_result *out);
 
+/* Allocation-free variant of tm_sample, for callers that cannot allocate
+ * device memory while sampling (a serving loop whose memory pool is held by
+ * resident weights, a host framework that owns the allocator, a loop that
+ * cannot afford an allocator call).  The paper has no counterpart: it is an
+ * interface choice of this library.  Results are bit-identical to tm_sample
+ * with the same arguments.  The call allocates nothing: its scratch (the
+ * device copy of the motif plan and the result accumulators) is a fixed
+ * 4096-byte array that every device loading the library holds until the
+ * process exits; a plan that does not fit returns TM_E_LIMIT.  The first
+ * call on a device looks up the array's device address (once per device,
+ * with that device current), so make that first call before any stream
+ * capture.  The accumulators are cleared at the start of every call, but all
+ * calls share the one array: calls whose GPU work overlaps (on different
+ * streams or contexts of one device) race.  Weights must already exist
+ * (tm_weights).  Errors: TM_E_STATE, TM_E_LIMIT, TM_E_OVERFLOW, TM_E_CUDA. */
+int tm_sample_noalloc(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first_index,
+                      tm_result *out);
+
 /* Batched estimate: nq queries (motifs with weights, sample counts, seeds)
  * run as one persistent launch over a shared queue of sample tiles.  out[q]
  * is bit-identical to tm_sample(ctx, motifs[q], k[q], seed[q], 0, ...). */

@@ -103,6 +103,7 @@ def _declare(L):
     L.tm_window_totals.argtypes = [vp, vp, vp, u64, C.POINTER(u64)]
     L.tm_sample.argtypes = [vp, vp, u64, u64, u64, C.POINTER(tm_result)]
     L.tm_sample_trace.argtypes = [vp, vp, u64, u64, u64, vp, vp, vp, C.POINTER(tm_result)]
+    L.tm_sample_noalloc.argtypes = [vp, vp, u64, u64, u64, C.POINTER(tm_result)]
     L.tm_batch_run.argtypes = [vp, u32, vp, vp, vp, vp]
     L.tm_motif_free.argtypes = [vp]; L.tm_motif_free.restype = None
     L.tm_phase_times.argtypes = [vp, vp, vp, i32, C.POINTER(i32)]
@@ -285,6 +286,14 @@ def tm_window_totals(ctx, motif):
 def tm_sample(ctx, motif, k, seed, first_index=0) -> Result:
     r = tm_result()
     _check(lib().tm_sample(ctx, motif, int(k), int(seed), int(first_index), C.byref(r)), ctx, "tm_sample")
+    return Result.of(r)
+
+
+def tm_sample_noalloc(ctx, motif, k, seed, first_index=0) -> Result:
+    """tm_sample without any device allocation (scratch in a fixed array)."""
+    r = tm_result()
+    _check(lib().tm_sample_noalloc(ctx, motif, int(k), int(seed), int(first_index), C.byref(r)), ctx,
+           "tm_sample_noalloc")
     return Result.of(r)
 
 

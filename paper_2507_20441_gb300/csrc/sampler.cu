@@ -15,6 +15,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "tm_device.cuh"
 #include "tm_internal.h"
@@ -431,3 +433,97 @@ int run_batch(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64_t 
 }
 
 }  // namespace timest
+
+// ---------------------------------------------------------------------------
+// Allocation-free sampling.
+//
+// Some callers cannot allocate device memory while they sample: a serving
+// loop that has handed the whole memory pool to resident weights, a host
+// framework that owns the allocator and forbids allocations from plug-ins,
+// or a latency-bound loop that cannot afford an allocator call (which may
+// synchronise the device).  tm_sample_noalloc runs the same sampling kernel
+// as tm_sample, but its scratch -- the device copy of the motif plan and the
+// result accumulators -- lives in the fixed array below instead of memory
+// obtained from the allocator.
+// ---------------------------------------------------------------------------
+namespace timest {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 4096;   // plan copy + accumulators
+constexpr int kNoAllocMaxDevices = 64;
+
+// One array per device that loads the library, held until the process exits.
+static __device__ __align__(256) unsigned char g_sample_scratch[kNoAllocScratchBytes];
+
+std::mutex g_scratch_mu;
+void *g_scratch_addr[kNoAllocMaxDevices] = {};
+
+// Device address of g_sample_scratch on the current device (ctx->device);
+// looked up once per device.  The symbol's name in host code is only a
+// host-side stand-in, so the kernel must be given this address instead.
+int scratch_address(tm_ctx *ctx, unsigned char **out)
+{
+    if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
+        return set_err(ctx, TM_E_LIMIT, "tm_sample_noalloc supports device ordinals below 64");
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[ctx->device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_sample_scratch);
+        if (e != cudaSuccess) return check_cuda(ctx, e, "cudaGetSymbolAddress(sample scratch)");
+        g_scratch_addr[ctx->device] = p;
+    }
+    *out = (unsigned char *)g_scratch_addr[ctx->device];
+    return TM_OK;
+}
+
+}  // namespace
+}  // namespace timest
+
+extern "C" int tm_sample_noalloc(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first_index,
+                                 tm_result *out)
+{
+    using namespace timest;
+    if (!ctx || !mo || mo->ctx != ctx || !out) return TM_E_ARG;
+    if (!mo->have_weights || mo->graph_epoch != ctx->epoch || !ctx->preprocessed)
+        return set_err(ctx, TM_E_STATE, "weights not computed for the current graph");
+    const size_t plan_bytes = ((sizeof(DevPlan) + 15) / 16) * 16;
+    const size_t need = plan_bytes + sizeof(Acc);
+    if (need > kNoAllocScratchBytes)
+        return set_err(ctx, TM_E_LIMIT, "motif plan (" + std::to_string(need) + " bytes) exceeds the " +
+                                            std::to_string(kNoAllocScratchBytes) + "-byte allocation-free scratch");
+    int rc = check_cuda(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (rc) return rc;
+    unsigned char *scratch = nullptr;
+    rc = scratch_address(ctx, &scratch);
+    if (rc) return rc;
+    Acc zero{0, 0, 0, 0, 0, 0};
+    if (k == 0 || (mo->W.lo == 0 && mo->W.hi == 0)) {
+        finish_result(mo, k, zero, out);
+        return TM_OK;
+    }
+    DevPlan *dplan = (DevPlan *)scratch;
+    Acc *dacc = (Acc *)(scratch + plan_bytes);
+    cudaStream_t st = ctx->stream;
+    copy_h2d(ctx, dplan, &mo->plan, sizeof(DevPlan));
+    cudaMemsetAsync(dacc, 0, sizeof(Acc), st);   // the array keeps the previous call's sums
+    cudaMemsetAsync(ctx->status, 0, 4, st);
+    SampleJob J;
+    fill_job(mo, J, dplan);
+    int threads = ctx->cfg.sample_threads > 0 ? std::min(ctx->cfg.sample_threads, 256) : 256;
+    uint64_t want = (k + threads - 1) / threads;
+    uint64_t cap = (uint64_t)ctx->num_sms * 16;
+    unsigned blocks = (unsigned)std::max<uint64_t>(1, std::min(want, cap));
+    launch(ctx, k_sample<false>, blocks, threads, ctx->g, dplan, J, seed, first_index, k, dacc, ctx->status, nullptr,
+           nullptr, nullptr);
+    rc = check_cuda(ctx, cudaGetLastError(), "sampler launch");
+    Acc h{};
+    copy_d2h(ctx, &h, dacc, sizeof(Acc));
+    uint32_t bits = 0;
+    int rc2 = read_status(ctx, &bits);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    finish_result(mo, k, h, out);
+    if (bits & ST_OVERFLOW) return set_err(ctx, TM_E_OVERFLOW, "a completion count exceeds 2^64");
+    if (bits) return set_err(ctx, TM_E_CUDA, "sampler reached an inconsistent state (status " + std::to_string(bits) + ")");
+    return TM_OK;
+}
