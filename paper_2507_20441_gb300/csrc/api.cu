@@ -47,6 +47,53 @@ void dfree(tm_ctx *ctx, void *p, size_t bytes)
     else cudaFreeAsync(p, ctx->stream);
 }
 
+void *salloc(tm_ctx *ctx, size_t bytes)
+{
+    bytes = ((bytes ? bytes : 1) + 255) / 256 * 256;
+    auto &A = ctx->arena;
+    if (!A.empty()) {
+        auto &c = A[ctx->arena_cur];
+        if (c.used + bytes <= c.size) {
+            void *p = c.base + c.used;
+            c.used += bytes;
+            return p;
+        }
+        for (size_t j = ctx->arena_cur + 1; j < A.size(); ++j)
+            if (A[j].size >= bytes) {
+                ctx->arena_cur = j;
+                A[j].used = bytes;
+                return A[j].base;
+            }
+    }
+    size_t total = 0;
+    for (auto &c : A) total += c.size;
+    size_t size = std::max<size_t>(bytes, std::max<size_t>((size_t)64 << 20, total / 2));
+    size = (size + 255) / 256 * 256;
+    char *base = (char *)dalloc(ctx, size);
+    if (!base) return nullptr;
+    A.push_back({base, size, bytes});
+    ctx->arena_cur = A.size() - 1;
+    return base;
+}
+
+ScratchScope::ScratchScope(tm_ctx *c) : ctx(c), cur(c->arena_cur), used(c->arena.empty() ? 0 : c->arena[c->arena_cur].used) {}
+
+ScratchScope::~ScratchScope()
+{
+    auto &A = ctx->arena;
+    if (A.empty()) return;
+    if (cur < A.size()) A[cur].used = used;
+    for (size_t j = cur + 1; j < A.size(); ++j) A[j].used = 0;
+    ctx->arena_cur = cur < A.size() ? cur : 0;
+}
+
+void arena_free(tm_ctx *ctx)
+{
+    for (auto &c : ctx->arena) dfree(ctx, c.base, c.size);
+    ctx->arena.clear();
+    ctx->arena_cur = 0;
+}
+
 void copy_h2d(tm_ctx *ctx, void *dst, const void *src, size_t bytes)
 {
     ctx->h2d_bytes += bytes;
@@ -332,6 +379,7 @@ void tm_destroy(tm_ctx *ctx)
     ctx->ev_pool.clear();
     free_input(ctx);
     free_graph(ctx);
+    arena_free(ctx);
     if (ctx->status) dfree(ctx, ctx->status, 64);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->status_host) cudaFreeHost(ctx->status_host);

@@ -109,14 +109,15 @@ int bits_for(uint64_t maxval)
 // data is in key/p0/p1 (the caller's buffers).
 int radix_sort(tm_ctx *ctx, uint32_t *key, uint32_t *p0, uint32_t *p1, uint32_t n, int bits)
 {
+    ScratchScope scope(ctx);
     if (n <= 1 || bits <= 0) return TM_OK;
     int np = p1 ? 2 : (p0 ? 1 : 0);
     uint32_t ntiles = (n + RS_TILE - 1) / RS_TILE;
     size_t hbytes = (size_t)ntiles * 256 * sizeof(uint32_t);
-    uint32_t *hist = (uint32_t *)dalloc(ctx, hbytes);
-    uint32_t *k2 = (uint32_t *)dalloc(ctx, (size_t)n * 4);
-    uint32_t *a2 = np >= 1 ? (uint32_t *)dalloc(ctx, (size_t)n * 4) : nullptr;
-    uint32_t *b2 = np >= 2 ? (uint32_t *)dalloc(ctx, (size_t)n * 4) : nullptr;
+    uint32_t *hist = (uint32_t *)salloc(ctx, hbytes);
+    uint32_t *k2 = (uint32_t *)salloc(ctx, (size_t)n * 4);
+    uint32_t *a2 = np >= 1 ? (uint32_t *)salloc(ctx, (size_t)n * 4) : nullptr;
+    uint32_t *b2 = np >= 2 ? (uint32_t *)salloc(ctx, (size_t)n * 4) : nullptr;
     int rc = TM_OK;
     if (!hist || !k2 || (np >= 1 && !a2) || (np >= 2 && !b2)) rc = TM_E_NOMEM;
     uint32_t *ki = key, *ai = p0, *bi = p1, *ko = k2, *ao = a2, *bo = b2;
@@ -142,10 +143,6 @@ int radix_sort(tm_ctx *ctx, uint32_t *key, uint32_t *p0, uint32_t *p1, uint32_t 
         if (np >= 1) cudaMemcpyAsync(p0, ai, (size_t)n * 4, cudaMemcpyDeviceToDevice, ctx->stream);
         if (np >= 2) cudaMemcpyAsync(p1, bi, (size_t)n * 4, cudaMemcpyDeviceToDevice, ctx->stream);
     }
-    dfree(ctx, hist, hbytes);
-    dfree(ctx, k2, (size_t)n * 4);
-    if (a2) dfree(ctx, a2, (size_t)n * 4);
-    if (b2) dfree(ctx, b2, (size_t)n * 4);
     return rc;
 }
 
@@ -305,6 +302,7 @@ static uint32_t *galloc(tm_ctx *ctx, size_t count)
 
 int build_csr(tm_ctx *ctx)
 {
+    ScratchScope scope(ctx);
     const int TB = 256;
     cudaStream_t st = ctx->stream;
     uint64_t m0 = ctx->m_in;
@@ -315,7 +313,7 @@ int build_csr(tm_ctx *ctx)
     int rc = TM_OK;
     // ---- statistics: t range, self loops, bad ids
     Stats hs{LLONG_MAX, LLONG_MIN, 0, 0};
-    Stats *ds = (Stats *)dalloc(ctx, sizeof(Stats));
+    Stats *ds = (Stats *)salloc(ctx, sizeof(Stats));
     if (!ds) return TM_E_NOMEM;
     copy_h2d(ctx, ds, &hs, sizeof(Stats));
     if (m0) {
@@ -324,7 +322,6 @@ int build_csr(tm_ctx *ctx)
     }
     copy_d2h(ctx, &hs, ds, sizeof(Stats));
     rc = check_cuda(ctx, cudaStreamSynchronize(st), "input statistics");
-    dfree(ctx, ds, sizeof(Stats));
     if (rc) return rc;
     if (hs.nbad) return set_err(ctx, TM_E_ARG, "vertex id >= n in input");
     if (hs.nself && !(ctx->load_flags & TM_DROP_SELF))
@@ -336,20 +333,18 @@ int build_csr(tm_ctx *ctx)
         return set_err(ctx, TM_E_LIMIT, "time span t_max - t_min must be below 2^32 - 1");
     uint32_t m = (uint32_t)m1;
     // ---- compact to (t', src, dst)
-    uint32_t *T0 = (uint32_t *)dalloc(ctx, (size_t)(m ? m : 1) * 4);
-    uint32_t *S0 = (uint32_t *)dalloc(ctx, (size_t)(m ? m : 1) * 4);
-    uint32_t *D0 = (uint32_t *)dalloc(ctx, (size_t)(m ? m : 1) * 4);
+    uint32_t *T0 = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);
+    uint32_t *S0 = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);
+    uint32_t *D0 = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);
     if (!T0 || !S0 || !D0) return TM_E_NOMEM;
     if (hs.nself) {
-        uint32_t *keep = (uint32_t *)dalloc(ctx, m0 * 4), *pos = (uint32_t *)dalloc(ctx, m0 * 4);
+        uint32_t *keep = (uint32_t *)salloc(ctx, m0 * 4), *pos = (uint32_t *)salloc(ctx, m0 * 4);
         if (!keep || !pos) return TM_E_NOMEM;
         launch(ctx, k_keep_nonself, blocks_for(m0, TB), TB, ctx->in_src, ctx->in_dst, m0, keep);
         rc = exclusive_scan_u32(ctx, keep, pos, m0, nullptr);
         if (rc) return rc;
         launch(ctx, k_compact_input, blocks_for(m0, TB), TB, ctx->in_src, ctx->in_dst, ctx->in_t, m0, keep, pos, tmin,
                                                            T0, S0, D0);
-        dfree(ctx, keep, m0 * 4);
-        dfree(ctx, pos, m0 * 4);
     } else if (m) {
         launch(ctx, k_compact_input, blocks_for(m0, TB), TB, ctx->in_src, ctx->in_dst, ctx->in_t, m0, nullptr, nullptr,
                                                            tmin, T0, S0, D0);
@@ -363,35 +358,31 @@ int build_csr(tm_ctx *ctx)
     if (rc) return rc;
     // ---- duplicates
     {
-        uint32_t *keep = (uint32_t *)dalloc(ctx, (size_t)(m ? m : 1) * 4);
-        unsigned long long *nd = (unsigned long long *)dalloc(ctx, 8);
+        uint32_t *keep = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);
+        unsigned long long *nd = (unsigned long long *)salloc(ctx, 8);
         if (!keep || !nd) return TM_E_NOMEM;
         cudaMemsetAsync(nd, 0, 8, st);
         if (m) launch(ctx, k_flag_unique, blocks_for(m, TB), TB, T0, S0, D0, m, keep, nd);
         unsigned long long ndup = 0;
         copy_d2h(ctx, &ndup, nd, 8);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "duplicate scan");
-        dfree(ctx, nd, 8);
         if (rc) return rc;
         if (ndup && !(ctx->load_flags & TM_DEDUP)) {
-            dfree(ctx, keep, (size_t)(m ? m : 1) * 4);
             return set_err(ctx, TM_E_DUP, "input repeats a (u,v,t) tuple (pass TM_DEDUP to drop repeats)");
         }
         g.g_t = galloc(ctx, m - ndup); g.g_src = galloc(ctx, m - ndup); g.g_dst = galloc(ctx, m - ndup);
         if (!g.g_t || !g.g_src || !g.g_dst) return TM_E_NOMEM;
         if (ndup) {
-            uint32_t *pos = (uint32_t *)dalloc(ctx, (size_t)m * 4);
+            uint32_t *pos = (uint32_t *)salloc(ctx, (size_t)m * 4);
             if (!pos) return TM_E_NOMEM;
             rc = exclusive_scan_u32(ctx, keep, pos, m, nullptr);
             if (rc) return rc;
             launch(ctx, k_compact3, blocks_for(m, TB), TB, T0, S0, D0, m, keep, pos, g.g_t, g.g_src, g.g_dst);
-            dfree(ctx, pos, (size_t)m * 4);
         } else if (m) {
             cudaMemcpyAsync(g.g_t, T0, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
             cudaMemcpyAsync(g.g_src, S0, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
             cudaMemcpyAsync(g.g_dst, D0, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
         }
-        dfree(ctx, keep, (size_t)(m ? m : 1) * 4);
         m = (uint32_t)(m - ndup);
     }
     g.m = m;
@@ -434,8 +425,8 @@ int build_csr(tm_ctx *ctx)
         launch(ctx, k_gather2, blocks_for(m, TB), TB, g.multi_gid, m, g.g_t, g.g_dst, g.multi_t, tmp);
         // key = pair src, tmp = pair dst per multi position
         uint32_t *head = T0;
-        uint32_t *pid = (uint32_t *)dalloc(ctx, (size_t)m * 4);
-        uint32_t *dnp = (uint32_t *)dalloc(ctx, 4);
+        uint32_t *pid = (uint32_t *)salloc(ctx, (size_t)m * 4);
+        uint32_t *dnp = (uint32_t *)salloc(ctx, 4);
         if (!pid || !dnp) return TM_E_NOMEM;
         launch(ctx, k_pair_heads, blocks_for(m, TB), TB, key, tmp, m, head);
         rc = exclusive_scan_u32(ctx, head, pid, m, dnp);
@@ -448,7 +439,7 @@ int build_csr(tm_ctx *ctx)
         g.pair_off = galloc(ctx, (size_t)np + 1);
         g.pair_dst = galloc(ctx, np);
         g.rev_pair = galloc(ctx, np);
-        uint32_t *pair_src = (uint32_t *)dalloc(ctx, (size_t)(np ? np : 1) * 4);
+        uint32_t *pair_src = (uint32_t *)salloc(ctx, (size_t)(np ? np : 1) * 4);
         if (!g.pair_off || !g.pair_dst || !g.rev_pair || !pair_src) return TM_E_NOMEM;
         launch(ctx, k_pair_fill, blocks_for(m, TB), TB, key, tmp, g.multi_gid, head, pid, m, g.pair_off, pair_src,
                                                       g.pair_dst, g.g_pair);
@@ -456,9 +447,6 @@ int build_csr(tm_ctx *ctx)
         launch(ctx, k_offsets, blocks_for((uint64_t)np + 1, TB), TB, pair_src, np, n, g.vpair_off);
         launch(ctx, k_rev_pairs, blocks_for(np, TB), TB, pair_src, g.pair_dst, g.vpair_off, np, g.rev_pair);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "pair tables");
-        dfree(ctx, pair_src, (size_t)(np ? np : 1) * 4);
-        dfree(ctx, pid, (size_t)m * 4);
-        dfree(ctx, dnp, 4);
         if (rc) return rc;
     } else {
         g.pair_off = galloc(ctx, 1);
@@ -467,9 +455,6 @@ int build_csr(tm_ctx *ctx)
         cudaMemsetAsync(g.pair_off, 0, 4, st);
         launch(ctx, k_offsets, 1, TB, key, 0, n, g.vpair_off);
     }
-    dfree(ctx, T0, (size_t)(m0 ? m0 : 1) * 4 > (size_t)(m1 ? m1 : 1) * 4 ? (size_t)(m1 ? m1 : 1) * 4 : (size_t)(m1 ? m1 : 1) * 4);
-    dfree(ctx, S0, (size_t)(m1 ? m1 : 1) * 4);
-    dfree(ctx, D0, (size_t)(m1 ? m1 : 1) * 4);
     return check_cuda(ctx, cudaStreamSynchronize(st), "CSR build");
 }
 

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "tm_device.cuh"
 #include "tm_internal.h"
@@ -326,6 +327,108 @@ __global__ void __launch_bounds__(256) k_sample(DevGraph g, const DevPlan *__res
     }
 }
 
+
+// ---- batched sampling (many queries, one persistent launch) ----
+// Work item i is a tile of `tile` consecutive sample ids of one query; query
+// q owns items [tile_base[q], tile_base[q+1]).  Blocks take items from a
+// device counter until none is left, so queries with very different k share
+// the GPU; each sample still draws from its own stream, so every query's
+// result equals a separate tm_sample call.
+struct BatchQuery {
+    DevPlan plan;
+    SampleJob job;
+    uint64_t seed, k;
+};
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_batch(DevGraph g, const BatchQuery *__restrict__ qs,
+                                                  const uint32_t *__restrict__ tile_base, uint32_t nq, uint32_t tile,
+                                                  uint32_t *counter, Acc *accs, uint32_t *status)
+{
+    __shared__ BatchQuery sq;
+    __shared__ uint32_t s_item;
+    __shared__ int s_q;
+    __shared__ unsigned long long red[THREADS / 32][6];
+    const uint32_t total = __ldg(tile_base + nq);
+    int cur_q = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            uint32_t item = atomicAdd(counter, 1u);
+            s_item = item;
+            int q = -1;
+            if (item < total) {
+                uint32_t lo = 0, hi = nq;          // last q with tile_base[q] <= item
+                while (hi - lo > 1) {
+                    uint32_t mid = (lo + hi) >> 1;
+                    if (__ldg(tile_base + mid) <= item) lo = mid; else hi = mid;
+                }
+                q = (int)lo;
+            }
+            s_q = q;
+        }
+        __syncthreads();
+        const uint32_t item = s_item;
+        const int q = s_q;
+        if (item >= total) break;
+        if (q != cur_q) {
+            const int *src = reinterpret_cast<const int *>(qs + q);
+            int *dst = reinterpret_cast<int *>(&sq);
+            for (int i = threadIdx.x; i < (int)(sizeof(BatchQuery) / sizeof(int)); i += THREADS) dst[i] = src[i];
+            cur_q = q;
+            __syncthreads();
+        }
+        const uint64_t t0 = (uint64_t)(item - __ldg(tile_base + q)) * tile;
+        const uint64_t t1 = min(t0 + tile, sq.k);
+        u128 hits = 0;
+        unsigned long long nv = 0, n1 = 0, n2 = 0, n3 = 0;
+        for (uint64_t i = t0 + threadIdx.x; i < t1; i += THREADS) {
+            uint64_t c = 0;
+            int why = sample_one(g, sq.plan, sq.job, sq.seed, i, status, c, nullptr);
+            if (why == 0) { ++nv; hits += c; }
+            else if (why == 1) ++n1;
+            else if (why == 2) ++n2;
+            else if (why == 3) ++n3;
+        }
+        uint64_t hl = (uint64_t)hits, hh = (uint64_t)(hits >> 64);
+        for (int o = 16; o > 0; o >>= 1) {
+            uint64_t ol = __shfl_down_sync(0xffffffffu, hl, o), oh = __shfl_down_sync(0xffffffffu, hh, o);
+            uint64_t sum = hl + ol;
+            hh += oh + (sum < hl ? 1 : 0);
+            hl = sum;
+            nv += __shfl_down_sync(0xffffffffu, nv, o);
+            n1 += __shfl_down_sync(0xffffffffu, n1, o);
+            n2 += __shfl_down_sync(0xffffffffu, n2, o);
+            n3 += __shfl_down_sync(0xffffffffu, n3, o);
+        }
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0) {
+            red[warp][0] = hl; red[warp][1] = hh; red[warp][2] = nv;
+            red[warp][3] = n1; red[warp][4] = n2; red[warp][5] = n3;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint64_t L = 0, H = 0, a = 0, b = 0, c = 0, d = 0;
+            for (int w = 0; w < THREADS / 32; ++w) {
+                uint64_t sum = L + red[w][0];
+                H += red[w][1] + (sum < L ? 1 : 0);
+                L = sum;
+                a += red[w][2]; b += red[w][3]; c += red[w][4]; d += red[w][5];
+            }
+            Acc *A = accs + q;
+            if (L) {
+                unsigned long long old = atomicAdd(&A->hits_lo, (unsigned long long)L);
+                if (old + L < old) H += 1;
+            }
+            if (H) atomicAdd(&A->hits_hi, (unsigned long long)H);
+            if (a) atomicAdd(&A->valid, (unsigned long long)a);
+            if (b) atomicAdd(&A->rv, (unsigned long long)b);
+            if (c) atomicAdd(&A->rd, (unsigned long long)c);
+            if (d) atomicAdd(&A->ro, (unsigned long long)d);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 void fill_job(tm_motif *mo, SampleJob &J, const DevPlan *dplan)
@@ -363,6 +466,7 @@ static void finish_result(tm_motif *mo, uint64_t k, const Acc &a, tm_result *out
 int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first, tm_result *out,
                 uint32_t *trace_gids, uint64_t *trace_contrib, int32_t *trace_reason)
 {
+    ScratchScope scope(ctx);
     cudaStream_t st = ctx->stream;
     Acc zero{0, 0, 0, 0, 0, 0};
     if (k == 0 || (mo->W.lo == 0 && mo->W.hi == 0)) {
@@ -371,7 +475,7 @@ int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t f
     }
     const bool trace = trace_gids || trace_contrib || trace_reason;
     size_t plan_bytes = sizeof(DevPlan), acc_bytes = sizeof(Acc);
-    char *scratch = (char *)dalloc(ctx, plan_bytes + acc_bytes + 64);
+    char *scratch = (char *)salloc(ctx, plan_bytes + acc_bytes + 64);
     if (!scratch) return TM_E_NOMEM;
     DevPlan *dplan = (DevPlan *)scratch;
     Acc *dacc = (Acc *)(scratch + ((plan_bytes + 15) / 16) * 16);
@@ -391,8 +495,8 @@ int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t f
         PhaseScope ph(ctx, TM_PH_SAMPLE);
         if (trace) {
             gbytes = (size_t)k * (4 * mo->plan.ntree + 8 + 4);
-            char *t = (char *)dalloc(ctx, gbytes);
-            if (!t) { dfree(ctx, scratch, plan_bytes + acc_bytes + 64); return TM_E_NOMEM; }
+            char *t = (char *)salloc(ctx, gbytes);
+            if (!t) return TM_E_NOMEM;
             dc = (uint64_t *)t;
             dr = (int32_t *)(t + (size_t)k * 8);
             dg = (uint32_t *)(t + (size_t)k * 12);
@@ -412,8 +516,6 @@ int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t f
     }
     uint32_t bits = 0;
     int rc2 = read_status(ctx, &bits);
-    if (trace) dfree(ctx, (char *)dc, gbytes);
-    dfree(ctx, scratch, plan_bytes + acc_bytes + 64);
     if (rc) return rc;
     if (rc2) return rc2;
     finish_result(mo, k, h, out);
@@ -422,13 +524,64 @@ int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t f
     return TM_OK;
 }
 
+
+// One persistent launch over every query's sample tiles (spec batching).
 int run_batch(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64_t *k, const uint64_t *seed,
               tm_result *out)
 {
+    ScratchScope scope(ctx);
+    cudaStream_t st = ctx->stream;
+    if (nq == 0) return TM_OK;
+    uint32_t tile = ctx->cfg.sample_tile > 0 ? (uint32_t)ctx->cfg.sample_tile : 2048;
+    std::vector<BatchQuery> hq(nq);
+    std::vector<uint32_t> base(nq + 1, 0);
+    uint64_t total = 0;
     for (uint32_t q = 0; q < nq; ++q) {
-        int rc = run_samples(ctx, motifs[q], k[q], seed[q], 0, &out[q], nullptr, nullptr, nullptr);
-        if (rc) return rc;
+        tm_motif *mo = motifs[q];
+        bool empty = (mo->W.lo == 0 && mo->W.hi == 0);
+        uint64_t tiles = empty ? 0 : (k[q] + tile - 1) / tile;
+        base[q] = (uint32_t)total;
+        total += tiles;
+        if (total >= 0xFFFFFFF0ull) return set_err(ctx, TM_E_LIMIT, "too many sample tiles in one batch");
+        hq[q].plan = mo->plan;
+        hq[q].seed = seed[q];
+        hq[q].k = empty ? 0 : k[q];
     }
+    base[nq] = (uint32_t)total;
+    size_t qbytes = sizeof(BatchQuery) * nq, bbytes = 4 * (size_t)(nq + 1), abytes = sizeof(Acc) * nq;
+    char *buf = (char *)salloc(ctx, qbytes + bbytes + abytes + 512);
+    if (!buf) return TM_E_NOMEM;
+    BatchQuery *dq = (BatchQuery *)buf;
+    uint32_t *dbase = (uint32_t *)(buf + ((qbytes + 255) / 256) * 256);
+    Acc *dacc = (Acc *)((char *)dbase + ((bbytes + 255) / 256) * 256);
+    uint32_t *dcounter = (uint32_t *)((char *)dacc + ((abytes + 255) / 256) * 256);
+    for (uint32_t q = 0; q < nq; ++q) fill_job(motifs[q], hq[q].job, &dq[q].plan);
+    copy_h2d(ctx, dq, hq.data(), qbytes);
+    copy_h2d(ctx, dbase, base.data(), bbytes);
+    cudaMemsetAsync(dacc, 0, abytes, st);
+    cudaMemsetAsync(dcounter, 0, 4, st);
+    cudaMemsetAsync(ctx->status, 0, 4, st);
+    int rc;
+    {
+        PhaseScope ph(ctx, TM_PH_BATCH);
+        constexpr int THREADS = 256;
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<THREADS>, THREADS, 0);
+        uint64_t blocks = (uint64_t)std::max(1, per_sm) * (uint64_t)ctx->num_sms;
+        blocks = std::min<uint64_t>(blocks, std::max<uint64_t>(total, 1));
+        launch(ctx, k_batch<THREADS>, (unsigned)blocks, THREADS, ctx->g, (const BatchQuery *)dq,
+               (const uint32_t *)dbase, nq, tile, dcounter, dacc, ctx->status);
+        rc = check_cuda(ctx, cudaGetLastError(), "batch launch");
+    }
+    std::vector<Acc> h(nq);
+    copy_d2h(ctx, h.data(), dacc, abytes);
+    uint32_t bits = 0;
+    int rc2 = read_status(ctx, &bits);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    for (uint32_t q = 0; q < nq; ++q) finish_result(motifs[q], k[q], h[q], &out[q]);
+    if (bits & ST_OVERFLOW) return set_err(ctx, TM_E_OVERFLOW, "a completion count exceeds 2^64");
+    if (bits) return set_err(ctx, TM_E_CUDA, "batched sampler reached an inconsistent state");
     return TM_OK;
 }
 

@@ -100,7 +100,8 @@ inline int exclusive_scan_u32(tm_ctx *ctx, const uint32_t *in, uint32_t *out, ui
         launch(ctx, k_tile_scan_u32, 1, SCAN_THREADS, in, n, nullptr, out, total);
         return check_cuda(ctx, cudaGetLastError(), "scan");
     }
-    uint32_t *ts = (uint32_t *)dalloc(ctx, tiles * sizeof(uint32_t));
+    ScratchScope scope(ctx);
+    uint32_t *ts = (uint32_t *)salloc(ctx, tiles * sizeof(uint32_t));
     if (!ts) return TM_E_NOMEM;
     launch(ctx, k_tile_sum_u32, (unsigned)tiles, SCAN_THREADS, in, n, ts);
     int rc = exclusive_scan_u32(ctx, ts, ts, tiles, nullptr);
@@ -108,7 +109,6 @@ inline int exclusive_scan_u32(tm_ctx *ctx, const uint32_t *in, uint32_t *out, ui
         launch(ctx, k_tile_scan_u32, (unsigned)tiles, SCAN_THREADS, in, n, ts, out, total);
         rc = check_cuda(ctx, cudaGetLastError(), "scan");
     }
-    dfree(ctx, ts, tiles * sizeof(uint32_t));
     return rc;
 }
 
@@ -259,14 +259,13 @@ int segmented_scan_u64(tm_ctx *ctx, const F &f, uint64_t n, uint64_t *out)
 {
     if (n == 0) return TM_OK;
     uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
-    SegAgg *aggs = (SegAgg *)dalloc(ctx, tiles * sizeof(SegAgg));
+    ScratchScope scope(ctx);
+    SegAgg *aggs = (SegAgg *)salloc(ctx, tiles * sizeof(SegAgg));
     if (!aggs) return TM_E_NOMEM;
     launch(ctx, k_segscan_reduce<F>, (unsigned)tiles, SCAN_THREADS, f, n, aggs, ctx->status);
     launch(ctx, k_segscan_carries, 1, 1024, aggs, tiles, ctx->status);
     launch(ctx, k_segscan_final<F>, (unsigned)tiles, SCAN_THREADS, f, n, aggs, out, ctx->status);
-    int rc = check_cuda(ctx, cudaGetLastError(), "segmented scan");
-    dfree(ctx, aggs, tiles * sizeof(SegAgg));
-    return rc;
+    return check_cuda(ctx, cudaGetLastError(), "segmented scan");
 }
 
 }  // namespace

@@ -130,6 +130,10 @@ struct tm_ctx {
     double phase_ms[TM_NUM_PHASES] = {};
     uint64_t h2d_bytes = 0, d2h_bytes = 0;     // host<->device traffic issued
     uint64_t kernel_launches = 0;              // kernels launched by this context
+    // scratch arena: device chunks reused last-in first-out across calls
+    struct ArenaChunk { char *base; size_t size; size_t used; };
+    std::vector<ArenaChunk> arena;
+    size_t arena_cur = 0;
     uint64_t phase_launches[TM_NUM_PHASES] = {};
 };
 
@@ -138,6 +142,19 @@ namespace timest {
 // ---- allocation helpers (api.cu) ----
 void *dalloc(tm_ctx *ctx, size_t bytes);
 void dfree(tm_ctx *ctx, void *p, size_t bytes);
+
+// ---- scratch arena (api.cu) ----
+// salloc hands out 256-byte aligned scratch from the context's chunks; a
+// ScratchScope returns everything allocated inside it when it closes.  All
+// work runs on the context stream, so reuse is ordered after earlier use.
+void *salloc(tm_ctx *ctx, size_t bytes);
+struct ScratchScope {
+    tm_ctx *ctx;
+    size_t cur, used;
+    explicit ScratchScope(tm_ctx *c);
+    ~ScratchScope();
+};
+void arena_free(tm_ctx *ctx);
 
 // ---- CSR build (csr.cu) ----
 int build_csr(tm_ctx *ctx);

@@ -251,7 +251,7 @@ static int owner_bits(tm_ctx *ctx, OwnerBits &ob)
     const uint32_t *offs[3] = {g.out_off, g.in_off, g.pair_off};
     uint32_t nown[3] = {g.n, g.n, g.npairs};
     for (int k = 0; k < 3; ++k) {
-        uint32_t *b = (uint32_t *)dalloc(ctx, words * 4);
+        uint32_t *b = (uint32_t *)salloc(ctx, words * 4);
         if (!b) return TM_E_NOMEM;
         cudaMemsetAsync(b, 0, words * 4, ctx->stream);
         if (nown[k]) launch(ctx, k_owner_bits, blocks_for(nown[k], TB), TB, offs[k], nown[k], g.m, b);
@@ -260,17 +260,11 @@ static int owner_bits(tm_ctx *ctx, OwnerBits &ob)
     return check_cuda(ctx, cudaGetLastError(), "owner bits");
 }
 
-static void free_owner_bits(tm_ctx *ctx, OwnerBits &ob)
-{
-    size_t words = ((size_t)ctx->g.m + 31) / 32 + 1;
-    if (ob.out) dfree(ctx, ob.out, words * 4);
-    if (ob.in) dfree(ctx, ob.in, words * 4);
-    if (ob.multi) dfree(ctx, ob.multi, words * 4);
-    ob = OwnerBits();
-}
+static void free_owner_bits(tm_ctx *, OwnerBits &ob) { ob = OwnerBits(); }   // scratch: freed by the scope
 
 int compute_weights(tm_ctx *ctx, tm_motif *mo)
 {
+    ScratchScope scope(ctx);
     free_motif_weights(ctx, mo);
     const DevGraph &g = ctx->g;
     const DevPlan &P = mo->plan;
@@ -283,9 +277,9 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     for (int p = 0; p < 2; ++p) {
         PhaseScope ph(ctx, TM_PH_WINDOWS);
         LayerData &L = mo->layer[p];
-        uint32_t *flag = (uint32_t *)dalloc(ctx, (size_t)(m ? m : 1) * 4);
-        uint32_t *pos = (uint32_t *)dalloc(ctx, (size_t)(m ? m : 1) * 4);
-        uint32_t *dcount = (uint32_t *)dalloc(ctx, 4);
+        uint32_t *flag = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);
+        uint32_t *pos = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);
+        uint32_t *dcount = (uint32_t *)salloc(ctx, 4);
         if (!flag || !pos || !dcount) return TM_E_NOMEM;
         uint32_t nw = 0;
         if (m) {
@@ -303,9 +297,6 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
         if (m) launch(ctx, k_window_fill, blocks_for(m, TB), TB, g.g_t, flag, pos, m, p, d, L.win_beg, L.win_id);
         copy_h2d(ctx, L.win_beg + nw, &g.m, 4);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "window fill");
-        dfree(ctx, flag, (size_t)(m ? m : 1) * 4);
-        dfree(ctx, pos, (size_t)(m ? m : 1) * 4);
-        dfree(ctx, dcount, 4);
         if (rc) return rc;
     }
     // ---- DP over tree nodes in increasing height (K3) + prefixes (K4)
@@ -313,8 +304,8 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     rc = owner_bits(ctx, ob);
     if (rc) return rc;
     uint64_t *w[2];
-    w[0] = (uint64_t *)dalloc(ctx, (size_t)(m ? m : 1) * 8);
-    w[1] = (uint64_t *)dalloc(ctx, (size_t)(m ? m : 1) * 8);
+    w[0] = (uint64_t *)salloc(ctx, (size_t)(m ? m : 1) * 8);
+    w[1] = (uint64_t *)salloc(ctx, (size_t)(m ? m : 1) * 8);
     if (!w[0] || !w[1]) return TM_E_NOMEM;
     ChildPrefix cp{};
     int maxh = 0;
@@ -361,8 +352,6 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
             }
         }
     }
-    dfree(ctx, w[0], (size_t)(m ? m : 1) * 8);
-    dfree(ctx, w[1], (size_t)(m ? m : 1) * 8);
     free_owner_bits(ctx, ob);
     // ---- window totals and their 128-bit running sum (K5)
     uint32_t nw0 = mo->layer[0].nwin, nw1 = mo->layer[1].nwin;
@@ -391,12 +380,13 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
 // w_{q,e} by gid for one layer, rebuilt from the stored prefix arrays.
 int export_weights(tm_ctx *ctx, tm_motif *mo, int q, int layer, uint64_t *host_out)
 {
+    ScratchScope scope(ctx);
     const DevGraph &g = ctx->g;
     const DevPlan &P = mo->plan;
     cudaStream_t st = ctx->stream;
     uint32_t m = g.m;
     if (m == 0) return TM_OK;
-    uint64_t *out = (uint64_t *)dalloc(ctx, (size_t)m * 8);
+    uint64_t *out = (uint64_t *)salloc(ctx, (size_t)m * 8);
     if (!out) return TM_E_NOMEM;
     int rc = TM_OK;
     if (P.tleaf[q] && q != 0) {
@@ -417,7 +407,6 @@ int export_weights(tm_ctx *ctx, tm_motif *mo, int q, int layer, uint64_t *host_o
     }
     copy_d2h(ctx, host_out, out, (size_t)m * 8);
     int rc2 = check_cuda(ctx, cudaStreamSynchronize(st), "export copy");
-    dfree(ctx, out, (size_t)m * 8);
     return rc ? rc : rc2;
 }
 
