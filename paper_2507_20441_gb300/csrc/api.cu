@@ -327,6 +327,25 @@ static int compile_plan(const MotifDesc &M, const int *tree, int root, int64_t d
     }
     for (int q = 0; q < P.ntree; ++q) P.tslot[q] = (q > 0 && !P.tleaf[q]) ? slot++ : -1;
     P.nslots = slot;
+    // non-tree edges along pi and their neighbouring tree positions
+    for (int e = 0; e < M.ne; ++e) P.tnode_of_edge[e] = -1;
+    for (int q = 0; q < P.ntree; ++q) P.tnode_of_edge[P.tedge[q]] = q;
+    P.nnt = 0;
+    P.derive_simple = 1;
+    for (int pos = 0; pos < M.ne; ++pos) {
+        int e = P.pos_edge[pos];
+        if (P.tnode_of_edge[e] >= 0) continue;
+        int i = P.nnt++;
+        P.nt_pos[i] = pos;
+        P.nt_prev[i] = -1;
+        P.nt_next[i] = -1;
+        for (int b = pos - 1; b >= 0; --b)
+            if (P.tnode_of_edge[P.pos_edge[b]] >= 0) { P.nt_prev[i] = P.tnode_of_edge[P.pos_edge[b]]; break; }
+        for (int a = pos + 1; a < M.ne; ++a)
+            if (P.tnode_of_edge[P.pos_edge[a]] >= 0) { P.nt_next[i] = P.tnode_of_edge[P.pos_edge[a]]; break; }
+        if (pos > 0 && P.tnode_of_edge[P.pos_edge[pos - 1]] < 0) P.derive_simple = 0;
+    }
+    P.coupled = (P.nnt > 0 && P.nt_pos[0] == 0 && P.nt_pos[P.nnt - 1] == M.ne - 1) ? 1 : 0;
     return TM_OK;
 }
 

@@ -26,24 +26,26 @@ namespace timest {
 
 namespace {
 
-struct EdgeRec {
-    uint32_t src, dst, t, pair, gid;
-};
-
 struct Acc {
     unsigned long long hits_lo, hits_hi, valid, rv, rd, ro;
 };
 
-__device__ __forceinline__ EdgeRec load_edge(const DevGraph &g, uint32_t gid)
-{
-    EdgeRec r;
-    r.gid = gid;
-    r.src = __ldg(g.g_src + gid);
-    r.dst = __ldg(g.g_dst + gid);
-    r.t = __ldg(g.g_t + gid);
-    r.pair = __ldg(g.g_pair + gid);
-    return r;
-}
+// Per-thread sample state kept in shared memory, one column per thread:
+// rows 0..6 tree-edge sources, 7..13 destinations, 14..20 times, 21..27 pair
+// ids, 28..34 edge ids, 35..42 the vertex map.  Dynamic indexing into shared
+// memory keeps these arrays out of local memory.
+constexpr int kRecRows = 5 * kMaxTree + kMaxV;
+
+struct Recs {
+    uint32_t *base;
+    int stride;
+    __device__ __forceinline__ uint32_t &src(int q) { return base[(0 * kMaxTree + q) * stride]; }
+    __device__ __forceinline__ uint32_t &dst(int q) { return base[(1 * kMaxTree + q) * stride]; }
+    __device__ __forceinline__ uint32_t &t(int q) { return base[(2 * kMaxTree + q) * stride]; }
+    __device__ __forceinline__ uint32_t &pair(int q) { return base[(3 * kMaxTree + q) * stride]; }
+    __device__ __forceinline__ uint32_t &gid(int q) { return base[(4 * kMaxTree + q) * stride]; }
+    __device__ __forceinline__ uint32_t &phi(int v) { return base[(5 * kMaxTree + v) * stride]; }
+};
 
 // Multi-edge list range of pair (u, v), or an empty range.
 __device__ __forceinline__ void find_pair(const DevGraph &g, uint32_t u, uint32_t v, uint32_t &beg, uint32_t &end)
@@ -58,35 +60,81 @@ __device__ __forceinline__ void find_pair(const DevGraph &g, uint32_t u, uint32_
     }
 }
 
-// DeriveCnt (Alg. 5): the number of ways to map the non-tree motif edges to
-// edges of their multi-edge lists so that all times strictly increase along
-// pi and span at most delta.  Lists are merged in time order (ties: later pi
+// DeriveCnt (Alg. 5) when every run of consecutive non-tree pi positions has
+// length 1: each non-tree edge only has to lie strictly between its two
+// neighbouring tree times (and within [tmax - delta, tmin + delta]), so the
+// count is a product of range sizes of multi-edge lists.  When both the
+// first and the last pi edge are non-tree their times are coupled by the
+// delta span: sum over the first edge's candidates x of the last edge's
+// candidates up to x + delta (two pointers over the two sorted lists).
+__device__ uint64_t derive_simple(const DevGraph &g, const DevPlan &P, Recs &R, uint32_t tmin, uint32_t tmax,
+                                  bool &ovf)
+{
+    const uint64_t d = (uint64_t)P.delta;
+    const uint64_t glo = (uint64_t)tmax >= d ? (uint64_t)tmax - d : 0;
+    const uint64_t ghi = (uint64_t)tmin + d;
+    uint64_t prod = 1;
+    uint32_t ra[2] = {0, 0}, rb[2] = {0, 0};   // ranges of the coupled first / last edges
+    for (int i = 0; i < P.nnt; ++i) {
+        const int e = P.pos_edge[P.nt_pos[i]];
+        uint32_t b, en;
+        find_pair(g, R.phi(P.ea[e]), R.phi(P.eb[e]), b, en);
+        if (b == en) return 0;
+        uint64_t lo = glo, hi = ghi;
+        if (P.nt_prev[i] >= 0) { uint64_t x = (uint64_t)R.t(P.nt_prev[i]) + 1; lo = x > lo ? x : lo; }
+        if (P.nt_next[i] >= 0) {
+            uint32_t nt = R.t(P.nt_next[i]);
+            if (nt == 0) return 0;
+            hi = (uint64_t)nt - 1 < hi ? (uint64_t)nt - 1 : hi;
+        }
+        if (lo > hi) return 0;
+        const uint32_t x0 = lower_idx(g.multi_t, b, en, lo);
+        const uint32_t x1 = lower_idx(g.multi_t, x0, en, hi + 1);
+        if (x1 == x0) return 0;
+        if (P.coupled && (i == 0 || i == P.nnt - 1)) {
+            const int w = (i == 0) ? 0 : 1;
+            ra[w] = x0;
+            rb[w] = x1;
+        } else {
+            prod = mul_chk(prod, (uint64_t)(x1 - x0), ovf);
+        }
+    }
+    if (!P.coupled) return prod;
+    uint64_t sum = 0;
+    uint32_t j = ra[1];
+    for (uint32_t x = ra[0]; x < rb[0]; ++x) {
+        const uint64_t cap = (uint64_t)__ldg(g.multi_t + x) + d;
+        while (j < rb[1] && (uint64_t)__ldg(g.multi_t + j) <= cap) ++j;
+        sum = add_chk(sum, (uint64_t)(j - ra[1]), ovf);
+    }
+    return mul_chk(prod, sum, ovf);
+}
+
+// DeriveCnt, general case: the lists are merged in time order (ties: later pi
 // position first); acc[q] counts the increasing chains over positions 0..q
 // that end at an element already passed.
-__device__ uint64_t derive_count(const DevGraph &g, const DevPlan &P, const uint32_t *phiV, const uint32_t *tnode_t,
-                                 const int32_t *tnode_of_edge, uint32_t tmin_tree, uint32_t tmax_tree, bool &ovf)
+__device__ uint64_t derive_merge(const DevGraph &g, const DevPlan &P, Recs &R, uint32_t tmin_tree, uint32_t tmax_tree,
+                                 bool &ovf)
 {
     const int ne = P.ne;
     const int64_t d = P.delta;
     uint32_t cur[kMaxE], end[kMaxE], fixed_t[kMaxE];
     bool is_fixed[kMaxE];
-    // lower bound of every time: tmax_tree - d; upper: tmin_tree + d
     uint64_t glo = (int64_t)tmax_tree >= d ? (uint64_t)((int64_t)tmax_tree - d) : 0;
     uint64_t ghi = (uint64_t)tmin_tree + (uint64_t)d;
-    // previous / next tree times along pi for each position
     int64_t prev_t = -1;
     for (int pos = 0; pos < ne; ++pos) {
         int e = P.pos_edge[pos];
-        int q = tnode_of_edge[e];
+        int q = P.tnode_of_edge[e];
         if (q >= 0) {
             is_fixed[pos] = true;
-            fixed_t[pos] = tnode_t[q];
+            fixed_t[pos] = R.t(q);
             cur[pos] = 0; end[pos] = 1;
-            prev_t = tnode_t[q];
+            prev_t = R.t(q);
         } else {
             is_fixed[pos] = false;
             uint32_t b, en;
-            find_pair(g, phiV[P.ea[e]], phiV[P.eb[e]], b, en);
+            find_pair(g, R.phi(P.ea[e]), R.phi(P.eb[e]), b, en);
             uint64_t lo = glo;
             if (prev_t >= 0 && (uint64_t)prev_t + 1 > lo) lo = (uint64_t)prev_t + 1;
             cur[pos] = lower_idx(g.multi_t, b, en, lo);
@@ -94,20 +142,19 @@ __device__ uint64_t derive_count(const DevGraph &g, const DevPlan &P, const uint
             fixed_t[pos] = 0;
         }
     }
-    // clip each non-tree list at the next tree time (exclusive) and at ghi
     int64_t next_t = -1;
     for (int pos = ne - 1; pos >= 0; --pos) {
         if (is_fixed[pos]) { next_t = fixed_t[pos]; continue; }
+        if (next_t == 0) return 0;
         uint64_t hi = ghi;
-        if (next_t >= 0 && (uint64_t)next_t - 1 < hi) hi = (uint64_t)next_t - 1;
-        if (next_t == 0) { end[pos] = cur[pos]; continue; }
+        if (next_t > 0 && (uint64_t)next_t - 1 < hi) hi = (uint64_t)next_t - 1;
         end[pos] = lower_idx(g.multi_t, cur[pos], end[pos], hi + 1);
         if (cur[pos] >= end[pos]) return 0;
     }
     const bool coupled = !is_fixed[0] && !is_fixed[ne - 1];
     uint64_t total = 0;
-    uint32_t first_beg = cur[0], first_end = end[0];
-    uint32_t nfirst = coupled ? first_end - first_beg : 1;
+    const uint32_t first_beg = cur[0], first_end = end[0];
+    const uint32_t nfirst = coupled ? first_end - first_beg : 1;
     for (uint32_t f = 0; f < nfirst; ++f) {
         uint32_t c[kMaxE], en[kMaxE];
         uint64_t acc[kMaxE];
@@ -116,8 +163,7 @@ __device__ uint64_t derive_count(const DevGraph &g, const DevPlan &P, const uint
         if (coupled) {
             c[0] = first_beg + f;
             en[0] = c[0] + 1;
-            uint64_t x = __ldg(g.multi_t + c[0]);
-            cap = x + (uint64_t)d;
+            cap = (uint64_t)__ldg(g.multi_t + c[0]) + (uint64_t)d;
         }
         for (;;) {
             int best = -1;
@@ -137,10 +183,19 @@ __device__ uint64_t derive_count(const DevGraph &g, const DevPlan &P, const uint
     return total;
 }
 
+__device__ __forceinline__ void load_edge(const DevGraph &g, uint32_t gid, Recs &R, int q)
+{
+    R.gid(q) = gid;
+    R.src(q) = __ldg(g.g_src + gid);
+    R.dst(q) = __ldg(g.g_dst + gid);
+    R.t(q) = __ldg(g.g_t + gid);
+    R.pair(q) = __ldg(g.g_pair + gid);
+}
+
 // One sample: returns 0 valid, 1/2/3 reject reasons, or -1 on an internal
 // inconsistency (latched as ST_BADSTATE).
 __device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &J, uint64_t seed, uint64_t j,
-                          uint32_t *status, uint64_t &contrib, uint32_t *tg_out)
+                          uint32_t *status, uint64_t &contrib, uint32_t *tg_out, Recs R)
 {
     SampleRng rng;
     rng.init(seed, j);
@@ -148,38 +203,38 @@ __device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &
     const u128 W = (u128)J.W_lo | ((u128)J.W_hi << 64);
     u128 r = rng.below128(W, status);
     // window: last k with wcum[k] <= r
-    uint32_t lo = 0, hi = J.nwtot;   // answer in [0, nwtot)
+    uint32_t lo = 0, hi = J.nwtot;
     while (hi - lo > 1) {
         uint32_t mid = (lo + hi) >> 1;
         u128 c = (u128)__ldg(J.wcum + 2 * (size_t)mid) | ((u128)__ldg(J.wcum + 2 * (size_t)mid + 1) << 64);
         if (c <= r) lo = mid; else hi = mid;
     }
-    uint32_t k = lo;
-    u128 ck = (u128)__ldg(J.wcum + 2 * (size_t)k) | ((u128)__ldg(J.wcum + 2 * (size_t)k + 1) << 64);
-    uint64_t rr = (uint64_t)(r - ck);
+    const uint32_t k = lo;
+    const u128 ck = (u128)__ldg(J.wcum + 2 * (size_t)k) | ((u128)__ldg(J.wcum + 2 * (size_t)k + 1) << 64);
+    const uint64_t rr = (uint64_t)(r - ck);
     const int p = k < J.nw0 ? 0 : 1;
     const uint32_t kk = p ? k - J.nw0 : k;
     const uint32_t *wb = p ? J.win_beg1 : J.win_beg0;
     const uint64_t *cdf = p ? J.root_cdf1 : J.root_cdf0;
     const uint32_t wbeg = __ldg(wb + kk), wend = __ldg(wb + kk + 1);
     const uint64_t wi = __ldg((p ? J.win_id1 : J.win_id0) + kk);
-    const int64_t d = P.delta;
-    const uint64_t wlo = wi * (uint64_t)d, whi = (wi + 2) * (uint64_t)d - 1;
-    uint32_t root = upper_idx64(cdf, wbeg, wend, rr);
+    const uint64_t d = (uint64_t)P.delta;
+    const uint64_t wlo = wi * d, whi = (wi + 2) * d - 1;
+    const uint32_t root = upper_idx64(cdf, wbeg, wend, rr);
     if (root >= wend) { latch(status, ST_BADSTATE); return -1; }
-    EdgeRec rec[kMaxTree];
-    rec[0] = load_edge(g, root);
+    load_edge(g, root, R, 0);
     for (int q = 1; q < P.ntree; ++q) {
-        const EdgeRec &par = rec[P.tparent[q]];
+        const int pq = P.tparent[q];
         const bool zs = P.tzside[q] != 0, out = P.tout[q] != 0, leaf = P.tleaf[q] != 0;
-        const uint32_t zg = zs ? par.dst : par.src;
-        const uint32_t og = zs ? par.src : par.dst;
+        const uint32_t ps = R.src(pq), pd = R.dst(pq), pt = R.t(pq), ppair = R.pair(pq);
+        const uint32_t zg = zs ? pd : ps;
+        const uint32_t og = zs ? ps : pd;
         uint64_t tlo, thi;
-        if (P.tlater[q]) { tlo = (uint64_t)par.t + 1; thi = (uint64_t)par.t + (uint64_t)d; }
+        if (P.tlater[q]) { tlo = (uint64_t)pt + 1; thi = (uint64_t)pt + d; }
         else {
-            if (par.t == 0) { latch(status, ST_BADSTATE); return -1; }
-            tlo = (uint64_t)par.t >= (uint64_t)d ? (uint64_t)par.t - (uint64_t)d : 0;
-            thi = (uint64_t)par.t - 1;
+            if (pt == 0) { latch(status, ST_BADSTATE); return -1; }
+            tlo = (uint64_t)pt >= d ? (uint64_t)pt - d : 0;
+            thi = (uint64_t)pt - 1;
         }
         tlo = tlo < wlo ? wlo : tlo;
         thi = thi > whi ? whi : thi;
@@ -190,7 +245,7 @@ __device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &
         const uint32_t beg = __ldg(off + zg), endv = __ldg(off + zg + 1);
         const uint32_t a = lower_idx(tarr, beg, endv, tlo);
         const uint32_t b = lower_idx(tarr, a, endv, thi + 1);
-        const uint32_t pe = (out == !zs) ? par.pair : __ldg(g.rev_pair + par.pair);
+        const uint32_t pe = (out == !zs) ? ppair : __ldg(g.rev_pair + ppair);
         uint32_t ea = 0, eb = 0, pb = 0;
         if (pe != kNone) {
             pb = __ldg(g.pair_off + pe);
@@ -208,8 +263,8 @@ __device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &
             Pm = p ? J.pref_multi1[slot] : J.pref_multi0[slot];
             base = (a > beg && (uint64_t)__ldg(tarr + a - 1) >= wlo) ? __ldg(Pd + a - 1) : 0;
             base_m = (ea > pb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo) ? __ldg(Pm + ea - 1) : 0;
-            uint64_t sr = b > a ? __ldg(Pd + b - 1) - base : 0;
-            uint64_t se = eb > ea ? __ldg(Pm + eb - 1) - base_m : 0;
+            const uint64_t sr = b > a ? __ldg(Pd + b - 1) - base : 0;
+            const uint64_t se = eb > ea ? __ldg(Pm + eb - 1) - base_m : 0;
             total = sr - se;
         }
         if (total == 0 || b <= a) { latch(status, ST_BADSTATE); return -1; }
@@ -218,7 +273,7 @@ __device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &
         // non-excluded entries in [a, x]
         uint32_t xl = a, xh = b - 1;
         while (xl < xh) {
-            uint32_t x = xl + ((xh - xl) >> 1);
+            const uint32_t x = xl + ((xh - xl) >> 1);
             const uint32_t tx = __ldg(tarr + x), nx = __ldg(nbr + x);
             uint32_t ce = lower_idx(g.multi_t, ea, eb, tx) - ea;
             if (ea + ce < eb && __ldg(g.multi_t + ea + ce) == tx && og <= nx) ++ce;
@@ -227,74 +282,74 @@ __device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &
             else F = (__ldg(Pd + x) - base) - (ce ? __ldg(Pm + ea + ce - 1) - base_m : 0);
             if (F > rc) xh = x; else xl = x + 1;
         }
-        const uint32_t x = xl;
-        const uint32_t cg = __ldg(gids + x);
-        EdgeRec cr;
-        cr.gid = cg;
-        cr.t = __ldg(tarr + x);
-        const uint32_t other = __ldg(nbr + x);
-        cr.src = out ? zg : other;
-        cr.dst = out ? other : zg;
-        cr.pair = __ldg(g.g_pair + cg);
-        rec[q] = cr;
+        const uint32_t cg = __ldg(gids + xl);
+        const uint32_t other = __ldg(nbr + xl);
+        R.gid(q) = cg;
+        R.t(q) = __ldg(tarr + xl);
+        R.src(q) = out ? zg : other;
+        R.dst(q) = out ? other : zg;
+        R.pair(q) = __ldg(g.g_pair + cg);
     }
     if (tg_out)
-        for (int q = 0; q < P.ntree; ++q) tg_out[q] = rec[q].gid;
+        for (int q = 0; q < P.ntree; ++q) tg_out[q] = R.gid(q);
     // ---- validation (Alg. 4): 1-1 vertex map, delta span, pi order
-    uint32_t phiV[kMaxV];
-    uint32_t tnode_t[kMaxTree];
-    int32_t tnode_of_edge[kMaxE];
-    for (int e = 0; e < P.ne; ++e) tnode_of_edge[e] = -1;
     uint32_t tmin = 0xFFFFFFFFu, tmax = 0;
     for (int q = 0; q < P.ntree; ++q) {
         const int e = P.tedge[q];
-        phiV[P.ea[e]] = rec[q].src;
-        phiV[P.eb[e]] = rec[q].dst;
-        tnode_t[q] = rec[q].t;
-        tnode_of_edge[e] = q;
-        tmin = min(tmin, rec[q].t);
-        tmax = max(tmax, rec[q].t);
+        R.phi(P.ea[e]) = R.src(q);
+        R.phi(P.eb[e]) = R.dst(q);
+        const uint32_t tq = R.t(q);
+        tmin = min(tmin, tq);
+        tmax = max(tmax, tq);
     }
-    for (int x = 0; x < P.nv; ++x)
+    for (int x = 0; x < P.nv; ++x) {
+        const uint32_t px = R.phi(x);
         for (int y = x + 1; y < P.nv; ++y)
-            if (phiV[x] == phiV[y]) return 1;
-    if ((uint64_t)tmax - (uint64_t)tmin > (uint64_t)d) return 2;
+            if (px == R.phi(y)) return 1;
+    }
+    if ((uint64_t)tmax - (uint64_t)tmin > d) return 2;
     int64_t prev = -1;
     for (int pos = 0; pos < P.ne; ++pos) {
-        const int q = tnode_of_edge[P.pos_edge[pos]];
+        const int q = P.tnode_of_edge[P.pos_edge[pos]];
         if (q < 0) continue;
-        if ((int64_t)tnode_t[q] <= prev) return 3;
-        prev = tnode_t[q];
+        const int64_t tq = R.t(q);
+        if (tq <= prev) return 3;
+        prev = tq;
     }
     // ---- DeriveCnt (Alg. 5) and N_phi (windows holding every tree edge)
     bool ovf = false;
-    uint64_t cnt = derive_count(g, P, phiV, tnode_t, tnode_of_edge, tmin, tmax, ovf);
-    const bool two = (uint64_t)tmin >= (uint64_t)d && (uint64_t)tmin / (uint64_t)d == (uint64_t)tmax / (uint64_t)d;
+    uint64_t cnt = P.nnt == 0 ? 1
+                 : (P.derive_simple ? derive_simple(g, P, R, tmin, tmax, ovf) : derive_merge(g, P, R, tmin, tmax, ovf));
+    const bool two = (uint64_t)tmin >= d && (uint64_t)tmin / d == (uint64_t)tmax / d;
     if (!two) cnt = mul_chk(cnt, 2, ovf);
     if (ovf) latch(status, ST_OVERFLOW);
     contrib = cnt;
     return 0;
 }
 
+constexpr int kSampleThreads = 256;
+
 template <bool TRACE>
-__global__ void __launch_bounds__(256) k_sample(DevGraph g, const DevPlan *__restrict__ plan, SampleJob J,
-                                                uint64_t seed, uint64_t first, uint64_t k, Acc *acc,
-                                                uint32_t *status, uint32_t *tr_gid, uint64_t *tr_contrib,
-                                                int32_t *tr_reason)
+__global__ void __launch_bounds__(kSampleThreads, 4) k_sample(DevGraph g, const DevPlan *__restrict__ plan,
+                                                              SampleJob J, uint64_t seed, uint64_t first, uint64_t k,
+                                                              Acc *acc, uint32_t *status, uint32_t *tr_gid,
+                                                              uint64_t *tr_contrib, int32_t *tr_reason)
 {
     __shared__ DevPlan sp;
+    __shared__ uint32_t recs[kRecRows * kSampleThreads];
     {
         const int *src = reinterpret_cast<const int *>(plan);
         int *dst = reinterpret_cast<int *>(&sp);
         for (int i = threadIdx.x; i < (int)(sizeof(DevPlan) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
+    Recs R{recs + threadIdx.x, kSampleThreads};
     u128 hits = 0;
     unsigned long long nv = 0, nr1 = 0, nr2 = 0, nr3 = 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
         uint64_t c = 0;
-        int why = sample_one(g, sp, J, seed, first + i, status, c, TRACE ? tr_gid + i * sp.ntree : nullptr);
+        int why = sample_one(g, sp, J, seed, first + i, status, c, TRACE ? tr_gid + i * sp.ntree : nullptr, R);
         if (why == 0) { ++nv; hits += c; }
         else if (why == 1) ++nr1;
         else if (why == 2) ++nr2;
@@ -327,7 +382,6 @@ __global__ void __launch_bounds__(256) k_sample(DevGraph g, const DevPlan *__res
     }
 }
 
-
 // ---- batched sampling (many queries, one persistent launch) ----
 // Work item i is a tile of `tile` consecutive sample ids of one query; query
 // q owns items [tile_base[q], tile_base[q+1]).  Blocks take items from a
@@ -341,7 +395,7 @@ struct BatchQuery {
 };
 
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS) k_batch(DevGraph g, const BatchQuery *__restrict__ qs,
+__global__ void __launch_bounds__(THREADS, 3) k_batch(DevGraph g, const BatchQuery *__restrict__ qs,
                                                   const uint32_t *__restrict__ tile_base, uint32_t nq, uint32_t tile,
                                                   uint32_t *counter, Acc *accs, uint32_t *status)
 {
@@ -349,6 +403,8 @@ __global__ void __launch_bounds__(THREADS) k_batch(DevGraph g, const BatchQuery 
     __shared__ uint32_t s_item;
     __shared__ int s_q;
     __shared__ unsigned long long red[THREADS / 32][6];
+    __shared__ uint32_t recs[kRecRows * THREADS];
+    Recs R{recs + threadIdx.x, THREADS};
     const uint32_t total = __ldg(tile_base + nq);
     int cur_q = -1;
     for (;;) {
@@ -383,7 +439,7 @@ __global__ void __launch_bounds__(THREADS) k_batch(DevGraph g, const BatchQuery 
         unsigned long long nv = 0, n1 = 0, n2 = 0, n3 = 0;
         for (uint64_t i = t0 + threadIdx.x; i < t1; i += THREADS) {
             uint64_t c = 0;
-            int why = sample_one(g, sq.plan, sq.job, sq.seed, i, status, c, nullptr);
+            int why = sample_one(g, sq.plan, sq.job, sq.seed, i, status, c, nullptr, R);
             if (why == 0) { ++nv; hits += c; }
             else if (why == 1) ++n1;
             else if (why == 2) ++n2;
@@ -484,7 +540,7 @@ int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t f
     cudaMemsetAsync(ctx->status, 0, 4, st);
     SampleJob J;
     fill_job(mo, J, dplan);
-    int threads = ctx->cfg.sample_threads > 0 ? std::min(ctx->cfg.sample_threads, 256) : 256;
+    const int threads = kSampleThreads;
     uint64_t want = (k + threads - 1) / threads;
     uint64_t cap = (uint64_t)ctx->num_sms * 16;
     unsigned blocks = (unsigned)std::max<uint64_t>(1, std::min(want, cap));
@@ -662,7 +718,7 @@ extern "C" int tm_sample_noalloc(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t
     cudaMemsetAsync(ctx->status, 0, 4, st);
     SampleJob J;
     fill_job(mo, J, dplan);
-    int threads = ctx->cfg.sample_threads > 0 ? std::min(ctx->cfg.sample_threads, 256) : 256;
+    const int threads = kSampleThreads;
     uint64_t want = (k + threads - 1) / threads;
     uint64_t cap = (uint64_t)ctx->num_sms * 16;
     unsigned blocks = (unsigned)std::max<uint64_t>(1, std::min(want, cap));

@@ -70,6 +70,14 @@ struct DevPlan {
     int32_t child[kMaxTree][kMaxTree];
     int32_t height[kMaxTree];
     int32_t nslots;
+    // DeriveCnt layout (Alg. 5): non-tree edges by pi position
+    int32_t tnode_of_edge[kMaxE];        // tree node of a motif edge, -1 if non-tree
+    int32_t nnt;                         // number of non-tree edges
+    int32_t nt_pos[kMaxE];               // their pi positions, increasing
+    int32_t nt_prev[kMaxE];              // tree node at the previous tree position (-1: none)
+    int32_t nt_next[kMaxE];              // tree node at the next tree position (-1: none)
+    int32_t derive_simple;               // every run of consecutive non-tree positions has length 1
+    int32_t coupled;                     // the first and the last pi positions are both non-tree
 };
 
 // Per-motif resident weight data (one window layer p = 0, 1 each).

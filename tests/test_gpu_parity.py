@@ -103,7 +103,7 @@ def test_small_motifs_every_tree(tg, oracle_mod, name):
     n, s, d, t = small_random_graph(40, n=nv + 3, m=400, t_hi=120)
     ctx, G = make_pair(tg, oracle_mod, n, s, d, t)
     for delta in (7, 25):
-        for tree in spanning_trees(nv, edges)[:5]:
+        for tree in spanning_trees(nv, edges):
             for root in tree:
                 run_case(tg, ctx, G, nv, edges, rank, delta, tree, root, k=3000, seed=delta + root)
 
@@ -127,7 +127,10 @@ def test_chung_lu_cycle4_and_chord(tg, oracle_mod):
     run_case(tg, ctx, G, c4.nv, c4.edges, c4.rank, c4.delta, [0, 1, 2], 1, k=20000, seed=5)
     run_case(tg, ctx, G, c4.nv, c4.edges, c4.rank, c4.delta, [1, 2, 3], 3, k=20000, seed=6)
     c5 = synth.cycle5_chord(3_600)
-    for tree, root in (([0, 1, 3, 4], 1), ([0, 2, 3, 4], 3), ([1, 2, 4, 5], 2)):
+    # ([1, 2, 3, 4], 2): the first and last pi edges are non-tree (coupled span);
+    # ([0, 3, 4, 5], 4): non-tree edges at consecutive pi positions (merge path)
+    for tree, root in (([0, 1, 3, 4], 1), ([0, 2, 3, 4], 3), ([1, 2, 4, 5], 2), ([1, 2, 3, 4], 2),
+                       ([0, 3, 4, 5], 4)):
         run_case(tg, ctx, G, c5.nv, c5.edges, c5.rank, c5.delta, tree, root, k=20000, seed=9)
 
 
