@@ -50,7 +50,8 @@ enum {
     TM_E_STATE = 7,     /* call out of order (e.g. sample before weights)    */
     TM_E_TIMEOUT = 8,   /* a bounded wait ran out                            */
     TM_E_CUDA = 9,      /* a CUDA runtime call failed                        */
-    TM_E_LIMIT = 10     /* size beyond a stated limit                        */
+    TM_E_LIMIT = 10,    /* size beyond a stated limit                        */
+    TM_E_PENDING = 11   /* a served query has not finished yet (poll again)  */
 };
 
 /* ---- tm_graph_load flags ------------------------------------------------ */
@@ -204,6 +205,54 @@ int tm_sample_noalloc(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint
  * is bit-identical to tm_sample(ctx, motifs[q], k[q], seed[q], 0, ...). */
 int tm_batch_run(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64_t *k,
                  const uint64_t *seed, tm_result *out);
+
+/* ---- serving: continuous batching over a resident graph ----------------
+ * Between tm_serve_start and tm_serve_stop only the tm_serve_* calls (and
+ * tm_last_error) may be made on ctx; submit and poll are thread safe.
+ * Each query runs on its motif's default tree (tm_set_motif) with sample ids
+ * 0..k-1, so its result equals tm_sample on that tree with the same k and
+ * seed whatever else is being served. */
+typedef struct {
+    uint32_t max_active;      /* queries sampled concurrently (0 = 64)                 */
+    uint32_t tile;            /* samples per work item (0 = 4096)                      */
+    uint32_t round_tiles;     /* work items per scheduling round (0 = 2 per SM, >= 64) */
+    int32_t poll_timeout_ms;  /* bound on each wait for a round on the GPU (0 = 60 s)  */
+    uint64_t weight_budget;   /* device bytes for resident weights (0 = half the free
+                                 memory at start); least recently used weights that no
+                                 query holds are evicted to admit new ones            */
+    int32_t reserved[8];
+} tm_serve_cfg;
+
+typedef struct {
+    uint64_t submitted, completed, failed;
+    uint64_t cache_hits, cache_misses, evictions, rounds;
+    uint64_t resident_bytes, waiting, active;
+    double p50_ms, p99_ms, mean_ms;   /* submit-to-completion latency          */
+    double qps;                       /* completed / (last completion - first submit) */
+} tm_serve_stats_t;
+
+/* Start the admission and scheduling threads on a preprocessed graph.
+ * Errors: TM_E_STATE (already serving, no graph), TM_E_NOMEM, TM_E_CUDA. */
+int tm_serve_start(tm_ctx *ctx, const tm_serve_cfg *cfg);
+
+/* Queue a query M = (H, pi, delta) (arguments as tm_set_motif) with k samples
+ * from seed; *ticket identifies it.  Errors: TM_E_STATE (not serving),
+ * TM_E_MOTIF, TM_E_ARG. */
+int tm_serve_submit(tm_ctx *ctx, uint32_t nv, uint32_t ne, const uint32_t *edges, const uint32_t *order,
+                    int64_t delta, uint64_t k, uint64_t seed, uint64_t *ticket);
+
+/* Wait at most timeout_ms for a query; on completion copy its result and
+ * release the ticket.  Returns the query's own status (TM_OK, or e.g.
+ * TM_E_TIMEOUT if a bounded device wait ran out), or TM_E_PENDING while it is
+ * still running (the ticket stays valid). */
+int tm_serve_poll(tm_ctx *ctx, uint64_t ticket, tm_result *out, int timeout_ms);
+
+/* Counters, cache behaviour and latency percentiles since tm_serve_start. */
+int tm_serve_stats(tm_ctx *ctx, tm_serve_stats_t *out);
+
+/* Stop serving: queries being sampled finish their rounds, queued ones are
+ * dropped, cached weights are freed. */
+int tm_serve_stop(tm_ctx *ctx);
 
 /* Phases timed when cfg.profile = 1 (CUDA events on the context stream). */
 enum {

@@ -23,10 +23,11 @@ LIB_PATH = os.path.join(_HERE, "_build", "libtimest_gb300.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "timest.h")
 
 TM_OK, TM_E_ARG, TM_E_DUP, TM_E_SELFLOOP, TM_E_MOTIF, TM_E_NOMEM, TM_E_OVERFLOW, TM_E_STATE, TM_E_TIMEOUT, \
-    TM_E_CUDA, TM_E_LIMIT = range(11)
+    TM_E_CUDA, TM_E_LIMIT, TM_E_PENDING = range(12)
 TM_HOST, TM_DEVICE, TM_DEDUP, TM_DROP_SELF = 0, 1, 2, 4
 _STATUS_NAMES = {0: "TM_OK", 1: "TM_E_ARG", 2: "TM_E_DUP", 3: "TM_E_SELFLOOP", 4: "TM_E_MOTIF", 5: "TM_E_NOMEM",
-                 6: "TM_E_OVERFLOW", 7: "TM_E_STATE", 8: "TM_E_TIMEOUT", 9: "TM_E_CUDA", 10: "TM_E_LIMIT"}
+                 6: "TM_E_OVERFLOW", 7: "TM_E_STATE", 8: "TM_E_TIMEOUT", 9: "TM_E_CUDA", 10: "TM_E_LIMIT",
+                 11: "TM_E_PENDING"}
 
 
 class TimestUnavailable(RuntimeError):
@@ -80,6 +81,22 @@ class Result:
                       int(r.rej_order), float(r.estimate))
 
 
+class tm_serve_cfg(C.Structure):
+    _fields_ = [("max_active", C.c_uint32), ("tile", C.c_uint32), ("round_tiles", C.c_uint32),
+                ("poll_timeout_ms", C.c_int32), ("weight_budget", C.c_uint64), ("reserved", C.c_int32 * 8)]
+
+
+class tm_serve_stats_t(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("cache_hits", C.c_uint64), ("cache_misses", C.c_uint64), ("evictions", C.c_uint64),
+                ("rounds", C.c_uint64), ("resident_bytes", C.c_uint64), ("waiting", C.c_uint64),
+                ("active", C.c_uint64), ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
+                ("qps", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lib = None
 _load_error = None
 
@@ -107,6 +124,11 @@ def _declare(L):
     L.tm_batch_run.argtypes = [vp, u32, vp, vp, vp, vp]
     L.tm_motif_free.argtypes = [vp]; L.tm_motif_free.restype = None
     L.tm_phase_times.argtypes = [vp, vp, vp, i32, C.POINTER(i32)]
+    L.tm_serve_start.argtypes = [vp, C.POINTER(tm_serve_cfg)]
+    L.tm_serve_submit.argtypes = [vp, u32, u32, vp, vp, i64, u64, u64, C.POINTER(u64)]
+    L.tm_serve_poll.argtypes = [vp, u64, C.POINTER(tm_result), i32]
+    L.tm_serve_stats.argtypes = [vp, C.POINTER(tm_serve_stats_t)]
+    L.tm_serve_stop.argtypes = [vp]
     L.tm_io_bytes.argtypes = [vp, C.POINTER(u64), C.POINTER(u64)]
     return L
 
@@ -319,6 +341,40 @@ def tm_motif_free(motif):
     lib().tm_motif_free(motif)
 
 
+def tm_serve_start(ctx, max_active=0, tile=0, round_tiles=0, poll_timeout_ms=0, weight_budget=0):
+    cfg = tm_serve_cfg(max_active, tile, round_tiles, poll_timeout_ms, weight_budget)
+    _check(lib().tm_serve_start(ctx, C.byref(cfg)), ctx, "tm_serve_start")
+
+
+def tm_serve_submit(ctx, nv, edges, order, delta, k, seed) -> int:
+    e = np.ascontiguousarray(np.array(edges, dtype=np.uint32).reshape(-1))
+    o = np.ascontiguousarray(np.array(order, dtype=np.uint32))
+    t = C.c_uint64()
+    _check(lib().tm_serve_submit(ctx, int(nv), len(o), _ptr(e), _ptr(o), int(delta), int(k), int(seed),
+                                 C.byref(t)), ctx, "tm_serve_submit")
+    return int(t.value)
+
+
+def tm_serve_poll(ctx, ticket, timeout_ms=0):
+    """Result of a finished query, or None while it is still running."""
+    r = tm_result()
+    rc = lib().tm_serve_poll(ctx, int(ticket), C.byref(r), int(timeout_ms))
+    if rc == TM_E_PENDING:
+        return None
+    _check(rc, ctx, "tm_serve_poll")
+    return Result.of(r)
+
+
+def tm_serve_stats(ctx) -> dict:
+    st = tm_serve_stats_t()
+    _check(lib().tm_serve_stats(ctx, C.byref(st)), ctx, "tm_serve_stats")
+    return st.as_dict()
+
+
+def tm_serve_stop(ctx):
+    _check(lib().tm_serve_stop(ctx), ctx, "tm_serve_stop")
+
+
 PHASES = ["load", "csr", "windows", "dp", "prefix", "root", "sample", "batch"]
 
 
@@ -406,6 +462,22 @@ class Context:
 
     def motif(self, nv, edges, order, delta) -> Motif:
         return Motif(self, nv, edges, order, delta)
+
+    # ---- serving (continuous batching); only these calls while serving
+    def serve_start(self, **cfg):
+        tm_serve_start(self.h, **cfg)
+
+    def submit(self, nv, edges, order, delta, k, seed) -> int:
+        return tm_serve_submit(self.h, nv, edges, order, delta, k, seed)
+
+    def poll(self, ticket, timeout_ms=0):
+        return tm_serve_poll(self.h, ticket, timeout_ms)
+
+    def serve_stats(self) -> dict:
+        return tm_serve_stats(self.h)
+
+    def serve_stop(self):
+        tm_serve_stop(self.h)
 
     def phase_times(self):
         return tm_phase_times(self.h)

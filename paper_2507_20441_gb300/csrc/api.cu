@@ -391,6 +391,7 @@ int tm_create(tm_ctx **out, const tm_config *cfg, void *cuda_stream)
 void tm_destroy(tm_ctx *ctx)
 {
     if (!ctx) return;
+    if (ctx->server) tm_serve_stop(ctx);
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     prof_collect(ctx);
@@ -402,6 +403,7 @@ void tm_destroy(tm_ctx *ctx)
     if (ctx->status) dfree(ctx, ctx->status, 64);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->status_host) cudaFreeHost(ctx->status_host);
+    if (ctx->pinned_acc) cudaFreeHost(ctx->pinned_acc);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }

@@ -14,8 +14,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string.h>
+
 #include <algorithm>
+#include <chrono>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -26,14 +30,13 @@ namespace timest {
 
 namespace {
 
-struct Acc {
-    unsigned long long hits_lo, hits_hi, valid, rv, rd, ro;
-};
+typedef SampleAcc Acc;
 
-// Per-thread sample state kept in shared memory, one column per thread:
-// rows 0..6 tree-edge sources, 7..13 destinations, 14..20 times, 21..27 pair
-// ids, 28..34 edge ids, 35..42 the vertex map.  Dynamic indexing into shared
-// memory keeps these arrays out of local memory.
+// Per-thread sample state: rows 0..6 tree-edge sources, 7..13 destinations,
+// 14..20 times, 21..27 pair ids, 28..34 edge ids, 35..42 the vertex map,
+// `stride` apart.  The sampler keeps them in (L1-cached) local memory; a
+// shared-memory layout measured slower because it shrinks L1 for the
+// searches.
 constexpr int kRecRows = 5 * kMaxTree + kMaxV;
 
 struct Recs {
@@ -113,7 +116,7 @@ __device__ uint64_t derive_simple(const DevGraph &g, const DevPlan &P, Recs &R, 
 // DeriveCnt, general case: the lists are merged in time order (ties: later pi
 // position first); acc[q] counts the increasing chains over positions 0..q
 // that end at an element already passed.
-__device__ uint64_t derive_merge(const DevGraph &g, const DevPlan &P, Recs &R, uint32_t tmin_tree, uint32_t tmax_tree,
+__device__ __noinline__ uint64_t derive_merge(const DevGraph &g, const DevPlan &P, Recs &R, uint32_t tmin_tree, uint32_t tmax_tree,
                                  bool &ovf)
 {
     const int ne = P.ne;
@@ -244,14 +247,14 @@ __device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &
         const uint32_t *gids = out ? g.out_gid : g.in_gid;
         const uint32_t beg = __ldg(off + zg), endv = __ldg(off + zg + 1);
         const uint32_t a = lower_idx(tarr, beg, endv, tlo);
-        const uint32_t b = lower_idx(tarr, a, endv, thi + 1);
+        const uint32_t b = gallop_idx(tarr, a, endv, thi + 1);
         const uint32_t pe = (out == !zs) ? ppair : __ldg(g.rev_pair + ppair);
         uint32_t ea = 0, eb = 0, pb = 0;
         if (pe != kNone) {
             pb = __ldg(g.pair_off + pe);
             const uint32_t pend = __ldg(g.pair_off + pe + 1);
             ea = lower_idx(g.multi_t, pb, pend, tlo);
-            eb = lower_idx(g.multi_t, ea, pend, thi + 1);
+            eb = gallop_idx(g.multi_t, ea, pend, thi + 1);
         }
         const int slot = P.tslot[q];
         const uint64_t *Pd = nullptr, *Pm = nullptr;
@@ -328,22 +331,35 @@ __device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &
 }
 
 constexpr int kSampleThreads = 256;
+#ifndef TM_SAMPLE_MINB
+#define TM_SAMPLE_MINB 4
+#endif
+#ifndef TM_RECS_SMEM
+#define TM_RECS_SMEM 0   // per-sample records in local memory: L1 stays large for the searches
+#endif
 
 template <bool TRACE>
-__global__ void __launch_bounds__(kSampleThreads, 4) k_sample(DevGraph g, const DevPlan *__restrict__ plan,
+__global__ void __launch_bounds__(kSampleThreads, TM_SAMPLE_MINB) k_sample(DevGraph g, const DevPlan *__restrict__ plan,
                                                               SampleJob J, uint64_t seed, uint64_t first, uint64_t k,
                                                               Acc *acc, uint32_t *status, uint32_t *tr_gid,
                                                               uint64_t *tr_contrib, int32_t *tr_reason)
 {
     __shared__ DevPlan sp;
+#if TM_RECS_SMEM
     __shared__ uint32_t recs[kRecRows * kSampleThreads];
+#endif
     {
         const int *src = reinterpret_cast<const int *>(plan);
         int *dst = reinterpret_cast<int *>(&sp);
         for (int i = threadIdx.x; i < (int)(sizeof(DevPlan) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
+#if TM_RECS_SMEM
     Recs R{recs + threadIdx.x, kSampleThreads};
+#else
+    uint32_t recs_local[kRecRows];
+    Recs R{recs_local, 1};
+#endif
     u128 hits = 0;
     unsigned long long nv = 0, nr1 = 0, nr2 = 0, nr3 = 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -391,7 +407,7 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_sample(DevGraph g, const 
 struct BatchQuery {
     DevPlan plan;
     SampleJob job;
-    uint64_t seed, k;
+    uint64_t seed, first, k;   // sample ids first .. first+k-1
 };
 
 template <int THREADS>
@@ -439,7 +455,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_batch(DevGraph g, const BatchQue
         unsigned long long nv = 0, n1 = 0, n2 = 0, n3 = 0;
         for (uint64_t i = t0 + threadIdx.x; i < t1; i += THREADS) {
             uint64_t c = 0;
-            int why = sample_one(g, sq.plan, sq.job, sq.seed, i, status, c, nullptr, R);
+            int why = sample_one(g, sq.plan, sq.job, sq.seed, sq.first + i, status, c, nullptr, R);
             if (why == 0) { ++nv; hits += c; }
             else if (why == 1) ++n1;
             else if (why == 2) ++n2;
@@ -581,37 +597,41 @@ int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t f
 }
 
 
-// One persistent launch over every query's sample tiles (spec batching).
-int run_batch(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64_t *k, const uint64_t *seed,
-              tm_result *out)
+void finish_result_acc(tm_motif *mo, uint64_t k, const SampleAcc &a, tm_result *out) { finish_result(mo, k, a, out); }
+
+// One persistent launch over every item's sample tiles (spec batching).
+int run_batch_items(tm_ctx *ctx, const BatchItem *items, uint32_t n, uint32_t tile, SampleAcc *acc, int wait_ms)
 {
     ScratchScope scope(ctx);
     cudaStream_t st = ctx->stream;
-    if (nq == 0) return TM_OK;
-    uint32_t tile = ctx->cfg.sample_tile > 0 ? (uint32_t)ctx->cfg.sample_tile : 2048;
-    std::vector<BatchQuery> hq(nq);
-    std::vector<uint32_t> base(nq + 1, 0);
+    for (uint32_t i = 0; i < n; ++i) acc[i] = SampleAcc{0, 0, 0, 0, 0, 0};
+    if (n == 0) return TM_OK;
+    if (tile == 0) tile = 2048;
+    std::vector<BatchQuery> hq(n);
+    std::vector<uint32_t> base(n + 1, 0);
     uint64_t total = 0;
-    for (uint32_t q = 0; q < nq; ++q) {
-        tm_motif *mo = motifs[q];
+    for (uint32_t q = 0; q < n; ++q) {
+        tm_motif *mo = items[q].mo;
         bool empty = (mo->W.lo == 0 && mo->W.hi == 0);
-        uint64_t tiles = empty ? 0 : (k[q] + tile - 1) / tile;
+        uint64_t cnt = empty ? 0 : items[q].count;
         base[q] = (uint32_t)total;
-        total += tiles;
+        total += (cnt + tile - 1) / tile;
         if (total >= 0xFFFFFFF0ull) return set_err(ctx, TM_E_LIMIT, "too many sample tiles in one batch");
         hq[q].plan = mo->plan;
-        hq[q].seed = seed[q];
-        hq[q].k = empty ? 0 : k[q];
+        hq[q].seed = items[q].seed;
+        hq[q].first = items[q].first;
+        hq[q].k = cnt;
     }
-    base[nq] = (uint32_t)total;
-    size_t qbytes = sizeof(BatchQuery) * nq, bbytes = 4 * (size_t)(nq + 1), abytes = sizeof(Acc) * nq;
-    char *buf = (char *)salloc(ctx, qbytes + bbytes + abytes + 512);
+    base[n] = (uint32_t)total;
+    if (total == 0) return TM_OK;
+    size_t qbytes = sizeof(BatchQuery) * n, bbytes = 4 * (size_t)(n + 1), abytes = sizeof(Acc) * n;
+    char *buf = (char *)salloc(ctx, qbytes + bbytes + abytes + 1024);
     if (!buf) return TM_E_NOMEM;
     BatchQuery *dq = (BatchQuery *)buf;
     uint32_t *dbase = (uint32_t *)(buf + ((qbytes + 255) / 256) * 256);
     Acc *dacc = (Acc *)((char *)dbase + ((bbytes + 255) / 256) * 256);
     uint32_t *dcounter = (uint32_t *)((char *)dacc + ((abytes + 255) / 256) * 256);
-    for (uint32_t q = 0; q < nq; ++q) fill_job(motifs[q], hq[q].job, &dq[q].plan);
+    for (uint32_t q = 0; q < n; ++q) fill_job(items[q].mo, hq[q].job, &dq[q].plan);
     copy_h2d(ctx, dq, hq.data(), qbytes);
     copy_h2d(ctx, dbase, base.data(), bbytes);
     cudaMemsetAsync(dacc, 0, abytes, st);
@@ -626,18 +646,65 @@ int run_batch(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64_t 
         uint64_t blocks = (uint64_t)std::max(1, per_sm) * (uint64_t)ctx->num_sms;
         blocks = std::min<uint64_t>(blocks, std::max<uint64_t>(total, 1));
         launch(ctx, k_batch<THREADS>, (unsigned)blocks, THREADS, ctx->g, (const BatchQuery *)dq,
-               (const uint32_t *)dbase, nq, tile, dcounter, dacc, ctx->status);
+               (const uint32_t *)dbase, n, tile, dcounter, dacc, ctx->status);
         rc = check_cuda(ctx, cudaGetLastError(), "batch launch");
     }
-    std::vector<Acc> h(nq);
-    copy_d2h(ctx, h.data(), dacc, abytes);
-    uint32_t bits = 0;
-    int rc2 = read_status(ctx, &bits);
-    if (rc) return rc;
-    if (rc2) return rc2;
-    for (uint32_t q = 0; q < nq; ++q) finish_result(motifs[q], k[q], h[q], &out[q]);
+    // sums land in a pinned staging buffer of the context: after a timed-out
+    // wait the copy still completes later, into memory that stays valid
+    if (ctx->pinned_acc_bytes < abytes) {
+        cudaStreamSynchronize(st);
+        if (ctx->pinned_acc) cudaFreeHost(ctx->pinned_acc);
+        ctx->pinned_acc = nullptr;
+        ctx->pinned_acc_bytes = 0;
+        size_t want = std::max<size_t>(abytes, 4096 * sizeof(Acc));
+        if (cudaMallocHost(&ctx->pinned_acc, want) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->pinned_acc = nullptr;
+            return set_err(ctx, TM_E_NOMEM, "pinned staging buffer");
+        }
+        ctx->pinned_acc_bytes = want;
+    }
+    copy_d2h(ctx, ctx->pinned_acc, dacc, abytes);
+    copy_d2h(ctx, ctx->status_host, ctx->status, 4);
+    if (rc) { cudaStreamSynchronize(st); return rc; }
+    if (wait_ms > 0) {
+        // bounded wait: poll the stream until it drains or the limit passes
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return check_cuda(ctx, cudaGetLastError(), "event");
+        cudaEventRecord(ev, st);
+        auto t0 = std::chrono::steady_clock::now();
+        cudaError_t q;
+        while ((q = cudaEventQuery(ev)) == cudaErrorNotReady) {
+            if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(wait_ms)) {
+                cudaEventDestroy(ev);
+                return set_err(ctx, TM_E_TIMEOUT, "batched sampler did not finish within the wait limit");
+            }
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+        cudaEventDestroy(ev);
+        if (q != cudaSuccess) return check_cuda(ctx, q, "batched sampler");
+    } else {
+        rc = check_cuda(ctx, cudaStreamSynchronize(st), "batched sampler");
+        if (rc) return rc;
+    }
+    prof_collect(ctx);
+    memcpy(acc, ctx->pinned_acc, abytes);
+    uint32_t bits = *ctx->status_host;
     if (bits & ST_OVERFLOW) return set_err(ctx, TM_E_OVERFLOW, "a completion count exceeds 2^64");
     if (bits) return set_err(ctx, TM_E_CUDA, "batched sampler reached an inconsistent state");
+    return TM_OK;
+}
+
+int run_batch(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64_t *k, const uint64_t *seed,
+              tm_result *out)
+{
+    std::vector<BatchItem> items(nq);
+    std::vector<SampleAcc> acc(nq);
+    for (uint32_t q = 0; q < nq; ++q) items[q] = BatchItem{motifs[q], seed[q], 0, k[q]};
+    uint32_t tile = ctx->cfg.sample_tile > 0 ? (uint32_t)ctx->cfg.sample_tile : 2048;
+    int rc = run_batch_items(ctx, items.data(), nq, tile, acc.data(), 0);
+    if (rc) return rc;
+    for (uint32_t q = 0; q < nq; ++q) finish_result(motifs[q], k[q], acc[q], &out[q]);
     return TM_OK;
 }
 

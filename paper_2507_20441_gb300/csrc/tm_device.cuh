@@ -89,6 +89,22 @@ __device__ __forceinline__ uint32_t lower_idx(const uint32_t *__restrict__ a, ui
     return lo;
 }
 
+// Same result as lower_idx, searching outward from lo first (1, 2, 4, ...
+// entries ahead): cheaper when the answer is close to lo.
+__device__ __forceinline__ uint32_t gallop_idx(const uint32_t *__restrict__ a, uint32_t lo, uint32_t hi, uint64_t x)
+{
+    // invariant: every index below `lo` holds a value < x
+    uint32_t step = 1;
+    uint32_t probe = lo;
+    while (probe < hi && (uint64_t)__ldg(a + probe) < x) {
+        lo = probe + 1;
+        probe = (hi - probe > step) ? probe + step : hi;
+        step = step < 0x40000000u ? step << 1 : step;
+    }
+    // the answer lies in [lo, probe]: probe == hi or a[probe] >= x
+    return lower_idx(a, lo, probe, x);
+}
+
 // First index in [lo, hi) with v[i] > x (v non-decreasing).
 __device__ __forceinline__ uint32_t upper_idx64(const uint64_t *__restrict__ v, uint32_t lo, uint32_t hi, uint64_t x)
 {

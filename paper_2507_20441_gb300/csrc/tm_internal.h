@@ -90,7 +90,7 @@ struct LayerData {
     uint64_t *pref_multi[kMaxTree] = {}; // per slot: prefix in the multi-edge order
 };
 
-struct DeviceAlloc;
+struct Server;
 
 }  // namespace timest
 
@@ -142,6 +142,9 @@ struct tm_ctx {
     struct ArenaChunk { char *base; size_t size; size_t used; };
     std::vector<ArenaChunk> arena;
     size_t arena_cur = 0;
+    timest::Server *server = nullptr;          // serving loop (serve.cu), if running
+    void *pinned_acc = nullptr;                // staging for batched sums (device -> host)
+    size_t pinned_acc_bytes = 0;
     uint64_t phase_launches[TM_NUM_PHASES] = {};
 };
 
@@ -186,6 +189,22 @@ int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t f
                 tm_result *out, uint32_t *trace_gids, uint64_t *trace_contrib, int32_t *trace_reason);
 int run_batch(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64_t *k,
               const uint64_t *seed, tm_result *out);
+
+// Sums of one sample range (device accumulators, host copy).
+struct SampleAcc {
+    unsigned long long hits_lo, hits_hi, valid, rv, rd, ro;
+};
+// One query's share of a batched launch: sample ids first .. first+count-1.
+struct BatchItem {
+    tm_motif *mo;
+    uint64_t seed, first, count;
+};
+// Launch the persistent batched sampler over the items (tiles of `tile`
+// samples) and copy each item's sums to acc[i].  wait_ms > 0 bounds the wait
+// for the GPU (TM_E_TIMEOUT when it runs out); 0 waits for completion.
+int run_batch_items(tm_ctx *ctx, const BatchItem *items, uint32_t n, uint32_t tile, SampleAcc *acc, int wait_ms);
+// Fold sums into a result (estimate = W * hits2 / (2k)).
+void finish_result_acc(tm_motif *mo, uint64_t k, const SampleAcc &a, tm_result *out);
 
 // ---- phase timing ----
 // Scope that records CUDA events around a group of launches of one phase;

@@ -43,13 +43,13 @@ __device__ __forceinline__ uint64_t child_sum(const DevGraph &g, const ChildPref
     const uint32_t *tarr = out ? g.out_t : g.in_t;
     uint32_t beg = __ldg(off + zg), end = __ldg(off + zg + 1);
     uint32_t a = lower_idx(tarr, beg, end, lo);
-    uint32_t b = lower_idx(tarr, a, end, hi + 1);
+    uint32_t b = gallop_idx(tarr, a, end, hi + 1);
     uint32_t ea = 0, eb = 0, pb = 0;
     if (pe != kNone) {
         pb = __ldg(g.pair_off + pe);
         uint32_t pend = __ldg(g.pair_off + pe + 1);
         ea = lower_idx(g.multi_t, pb, pend, lo);
-        eb = lower_idx(g.multi_t, ea, pend, hi + 1);
+        eb = gallop_idx(g.multi_t, ea, pend, hi + 1);
     }
     if (leaf) return (uint64_t)(b - a) - (uint64_t)(eb - ea);
     const uint64_t *P = cp.pd[p][slot];
