@@ -625,6 +625,22 @@ int run_batch_items(tm_ctx *ctx, const BatchItem *items, uint32_t n, uint32_t ti
     base[n] = (uint32_t)total;
     if (total == 0) return TM_OK;
     size_t qbytes = sizeof(BatchQuery) * n, bbytes = 4 * (size_t)(n + 1), abytes = sizeof(Acc) * n;
+    // sums land in a pinned staging buffer of the context: after a timed-out
+    // wait the copy still completes later, into memory that stays valid.
+    // Growing it synchronizes, so it happens before anything is launched.
+    if (ctx->pinned_acc_bytes < abytes) {
+        cudaStreamSynchronize(st);
+        if (ctx->pinned_acc) cudaFreeHost(ctx->pinned_acc);
+        ctx->pinned_acc = nullptr;
+        ctx->pinned_acc_bytes = 0;
+        size_t want = std::max<size_t>(abytes, 4096 * sizeof(Acc));
+        if (cudaMallocHost(&ctx->pinned_acc, want) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->pinned_acc = nullptr;
+            return set_err(ctx, TM_E_NOMEM, "pinned staging buffer");
+        }
+        ctx->pinned_acc_bytes = want;
+    }
     char *buf = (char *)salloc(ctx, qbytes + bbytes + abytes + 1024);
     if (!buf) return TM_E_NOMEM;
     BatchQuery *dq = (BatchQuery *)buf;
@@ -648,21 +664,6 @@ int run_batch_items(tm_ctx *ctx, const BatchItem *items, uint32_t n, uint32_t ti
         launch(ctx, k_batch<THREADS>, (unsigned)blocks, THREADS, ctx->g, (const BatchQuery *)dq,
                (const uint32_t *)dbase, n, tile, dcounter, dacc, ctx->status);
         rc = check_cuda(ctx, cudaGetLastError(), "batch launch");
-    }
-    // sums land in a pinned staging buffer of the context: after a timed-out
-    // wait the copy still completes later, into memory that stays valid
-    if (ctx->pinned_acc_bytes < abytes) {
-        cudaStreamSynchronize(st);
-        if (ctx->pinned_acc) cudaFreeHost(ctx->pinned_acc);
-        ctx->pinned_acc = nullptr;
-        ctx->pinned_acc_bytes = 0;
-        size_t want = std::max<size_t>(abytes, 4096 * sizeof(Acc));
-        if (cudaMallocHost(&ctx->pinned_acc, want) != cudaSuccess) {
-            cudaGetLastError();
-            ctx->pinned_acc = nullptr;
-            return set_err(ctx, TM_E_NOMEM, "pinned staging buffer");
-        }
-        ctx->pinned_acc_bytes = want;
     }
     copy_d2h(ctx, ctx->pinned_acc, dacc, abytes);
     copy_d2h(ctx, ctx->status_host, ctx->status, 4);
