@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-queries", type=int, default=100)
+    ap.add_argument("--serve-rate", type=float, default=50.0)
     return ap.parse_args()
 
 
@@ -120,12 +124,34 @@ def dp_bytes_per_edge(plan_children):
     return b
 
 
-def sampler_bytes_per_sample(ntree, m, avg_deg):
-    """Reads a sample must make that no cache can share: the root draw's CDF
-    entry and edge record (8 + 16 B), and per tree edge the picked list entry
-    (t, nbr, gid: 12 B), its edge's pair id (4 B) and the prefix value at the
-    pick (8 B)."""
-    return 24 + (ntree - 1) * 24
+def graph_stats(gr):
+    """Edge-weighted mean list lengths of the workload graph: the out/in-list
+    length and the multi-edge-list length seen from a uniformly random edge
+    (sum of squares over sum)."""
+    import numpy as np
+    outd = np.bincount(gr.src, minlength=gr.n).astype(np.float64)
+    ind = np.bincount(gr.dst, minlength=gr.n).astype(np.float64)
+    key = gr.src.astype(np.uint64) * np.uint64(gr.n) + gr.dst.astype(np.uint64)
+    _, sig = np.unique(key, return_counts=True)
+    sig = sig.astype(np.float64)
+    m = float(len(gr.src))
+    return {"list_len": float(((outd ** 2).sum() + (ind ** 2).sum()) / (2 * m)),
+            "pair_len": float((sig ** 2).sum() / m), "m": m}
+
+
+def sampler_bytes_per_sample(ntree, nontree, stats, nwin):
+    """The per-sample traffic model of the survey (Sec. 8(d)), every probe of
+    every search counted at 8 B: the window search over the window totals
+    (16 B entries) and the root search over the root CDF, 16 B for the root
+    edge record; per non-root tree edge a 16 B record and five searches of the
+    meeting vertex's list (two window bounds, two exclusion bounds, the
+    inverse-CDF pick); per non-tree edge one search of its multi-edge list."""
+    import math
+    lg = lambda x: max(1, math.ceil(math.log2(max(x, 2.0))))
+    b = lg(nwin) * 16 + lg(2 * stats["m"]) * 8 + 16
+    b += (ntree - 1) * (16 + lg(stats["list_len"]) * 8 * 5)
+    b += nontree * lg(stats["pair_len"]) * 8
+    return b
 
 
 # ------------------------------------------------------------------ ours ----
@@ -234,21 +260,27 @@ def run_ours(args, rank, world, local_rank):
     dp_ms, dp_n = per.get("dp", (0.0, 0))
     samp_ms, samp_n = per.get("sample", (0.0, 0))
     weight_ms = sum(per.get(p, (0.0, 0))[0] for p in ("windows", "dp", "prefix", "root"))
-    candidates = {name: ms for name, (ms, n) in per.items()}
-    dominant = max(candidates, key=candidates.get)
-    if dominant == "sample":
-        algo = k * sampler_bytes_per_sample(ntree, m_edges, 0)
+    # the dominant single kernel: the sampler or the weight DP (the CSR phase
+    # is dozens of small sort kernels, none of which leads the launch list)
+    if samp_ms >= dp_ms:
+        gst = graph_stats(gr)
+        nwin = 2 * (ctx.T // mo.delta + 1)
+        per_sample = sampler_bytes_per_sample(ntree, len(mo.edges) - ntree, gst, nwin)
+        algo = k * per_sample
         kern_ms = samp_ms / max(samp_n, 1)
-        kname = "k_sample"
+        kname, model = "k_sample", f"survey 8(d) effective bytes: {per_sample} B/sample x k"
     else:
         algo = dp_bytes / max(dp_n, 1)
         kern_ms = dp_ms / max(dp_n, 1)
-        kname = "k_dp"
+        kname, model = "k_dp", "streamed edge record, list bounds, prefix reads and weight writes per edge"
     achieved = algo / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "algorithmic_bytes_per_launch": int(algo),
-                "launch_ms": round(kern_ms, 4), "dominant_phase": dominant}
+                "traffic": None, "algorithmic_bytes_per_launch": int(algo), "model": model,
+                "launch_ms": round(kern_ms, 4)}
+
+    batched = None if args.no_batch else run_batched(ctx, tg, synth, stream)
+    served = None if args.no_serve else run_served(ctx, tg, synth, args.serve_queries, args.serve_rate)
 
     out = {
         "metric": "samples/s", "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
@@ -267,9 +299,87 @@ def run_ours(args, rank, world, local_rank):
                         "dp_GBps": round(dp_bytes / (dp_ms / 1e3) / 1e9, 1) if dp_ms else None,
                         "dp_frac_of_peak": round(dp_bytes / (dp_ms / 1e3) / 1e9 / peak, 4) if dp_ms else None},
         "estimate": res.estimate, "W": state["W"], "hits2": res.hits2, "valid": res.valid,
+        "batched": batched,
+        "served": served,
     }
     ctx.close()
     return out
+
+
+# ------------------------------------------------------ batched / served ----
+def run_batched(ctx, tg, synth, stream, reps=3):
+    """32-query pool (3-7 vertices; delta in {600, 3600, 86400}; k log-uniform
+    in [1e4, 1e7]) on the bench graph: one persistent batched launch against
+    32 separate tm_sample calls, same weights and seeds; results must be
+    identical.  Weights are computed once beforehand for both."""
+    import torch
+    pool = synth.motif_pool(seed=7, count=32)
+    motifs = []
+    for mo in pool:
+        m = ctx.motif(mo.nv, mo.edges, mo.rank, mo.delta)
+        m.weights()
+        motifs.append(m)
+    ks = [mo.k for mo in pool]
+    seeds = [1000 + i for i in range(len(pool))]
+
+    def timed(fn):
+        best = None
+        out = None
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        return best, out
+
+    ms_plain, plain = timed(lambda: [m.sample(k, s) for m, k, s in zip(motifs, ks, seeds)])
+    ms_batch, batch = timed(lambda: ctx.batch_run(motifs, ks, seeds))
+    same = all((a.hits2, a.valid, a.rej_vertex, a.rej_delta, a.rej_order) ==
+               (b.hits2, b.valid, b.rej_vertex, b.rej_delta, b.rej_order) for a, b in zip(plain, batch))
+    ctx.phase_times()
+    for m in motifs:
+        m.free()
+    return {"queries": len(pool), "samples": int(sum(ks)), "k_range": [int(min(ks)), int(max(ks))],
+            "plain_ms": round(ms_plain, 3), "batched_ms": round(ms_batch, 3),
+            "plain_qps": round(len(pool) / (ms_plain / 1e3), 1), "batched_qps": round(len(pool) / (ms_batch / 1e3), 1),
+            "speedup": round(ms_plain / ms_batch, 3), "identical_results": bool(same),
+            "timing": "best of %d, CUDA events on the library stream, weights precomputed" % reps}
+
+
+def run_served(ctx, tg, synth, nq, rate):
+    """Poisson arrivals at `rate` queries/s drawn from the 32-motif pool (k
+    log-uniform in [1e4, 1e7]), served by continuous batching with cached
+    weights; latency is submit-to-result on the host clock."""
+    import numpy as np
+    pool = synth.motif_pool(seed=7, count=32)
+    rng = np.random.default_rng(17)
+    gaps = rng.exponential(1.0 / rate, size=nq)
+    picks = rng.integers(0, len(pool), size=nq)
+    ctx.serve_start(max_active=64)
+    tickets = []
+    t0 = time.perf_counter()
+    due = t0
+    for i in range(nq):
+        due += gaps[i]
+        now = time.perf_counter()
+        if due > now:
+            time.sleep(due - now)
+        mo = pool[int(picks[i])]
+        tickets.append(ctx.submit(mo.nv, mo.edges, mo.rank, mo.delta, mo.k, 5000 + i))
+    for t in tickets:
+        r = ctx.poll(t, timeout_ms=600_000)
+        assert r is not None
+    wall = time.perf_counter() - t0
+    st = ctx.serve_stats()
+    ctx.serve_stop()
+    return {"queries": nq, "arrival_rate_qps": rate, "wall_s": round(wall, 3),
+            "completed": st["completed"], "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+            "mean_ms": round(st["mean_ms"], 3), "qps": round(st["qps"], 2), "cache_hits": st["cache_hits"],
+            "cache_misses": st["cache_misses"], "evictions": st["evictions"], "rounds": st["rounds"]}
 
 
 # ------------------------------------------------------------- oracle ----
@@ -293,14 +403,6 @@ def time_oracle(workload, k_full, seed, tree, root, k_sample, threads):
     return {"value": k_full / step_s, "unit": "samples/s", "cores": threads, "kind": "oracle",
             "sample": f"graph build + weights in full, {k_sample} of {k_full} samples timed and scaled",
             "graph_s": round(t1 - t0, 3), "weights_s": round(t2 - t1, 3), "sample_s": round(t3 - t2, 3)}
-
-
-def default_tree(workload):
-    """The tree and root the library picks by default for this motif."""
-    import paper_2507_20441_gb300 as tg  # noqa: F401
-    from paper_2507_20441_gb300 import synth
-    mo = synth.make_motif(workload)
-    return mo
 
 
 def run_reference(args, rank, world):
