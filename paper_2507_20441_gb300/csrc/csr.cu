@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <string>
 
 #include "scan.cuh"
 #include "tm_device.cuh"
@@ -22,78 +23,208 @@ namespace timest {
 
 namespace {
 
-constexpr int RS_THREADS = 256;
-constexpr int RS_ITEMS = 8;
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
-constexpr int RS_WARPS = RS_THREADS / 32;
+// ---- radix sort: one kernel per digit pass (decoupled look-back) ---------
+// Keys are sorted least significant digit first, with up to 9-bit digits.
+// A first kernel counts every pass's digits over the whole array (the counts
+// of a pass do not depend on the order earlier passes leave), so each pass
+// knows where every digit's output run starts.  In a pass, each block takes
+// the next tile of 4096 keys from a counter, ranks them stably inside the
+// tile (per warp with __match_any_sync, then across warps), publishes the
+// tile's digit counts, and adds up its predecessors' counts by walking back
+// over their published values (a predecessor that has finished its own walk
+// publishes an inclusive prefix, which ends the walk).  The tile is then
+// reordered by digit in shared memory and written out in contiguous runs.
+constexpr int OS_THREADS = 256;
+constexpr int OS_ITEMS = 16;
+constexpr int OS_TILE = OS_THREADS * OS_ITEMS;     // 4096 keys per tile
+constexpr int OS_WARPS = OS_THREADS / 32;
+constexpr int OS_WCHUNK = OS_ITEMS * 32;           // keys per warp chunk
+constexpr int OS_MAXBITS = 9;
+constexpr int OS_MAXRADIX = 1 << OS_MAXBITS;
+constexpr int OS_MAXPASS = 4;
+constexpr unsigned long long OS_AGG = 1ull << 62, OS_PRE = 2ull << 62, OS_VAL = (1ull << 62) - 1;
+constexpr size_t OS_SMEM = (size_t)OS_TILE * 4 * 3 + (size_t)OS_TILE * 2 + (size_t)OS_WARPS * OS_MAXRADIX * 2 +
+                           (size_t)OS_MAXRADIX * 4 * 3;
 
-__global__ void k_rs_hist(const uint32_t *__restrict__ keys, uint32_t n, int shift, uint32_t *__restrict__ hist,
-                          uint32_t ntiles)
+struct PassDesc {
+    int npass;
+    int shift[OS_MAXPASS];
+    int bits[OS_MAXPASS];
+};
+
+__global__ void k_os_hist(const uint32_t *__restrict__ keys, uint32_t n, PassDesc pd, uint32_t *__restrict__ ghist)
 {
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
+    __shared__ uint32_t h[OS_MAXPASS][OS_MAXRADIX];
+    for (int i = threadIdx.x; i < OS_MAXPASS * OS_MAXRADIX; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
-    uint32_t base = blockIdx.x * RS_TILE;
-#pragma unroll
-    for (int j = 0; j < RS_ITEMS; ++j) {
-        uint32_t i = base + j * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t k = __ldg(keys + i);
+        for (int p = 0; p < pd.npass; ++p) atomicAdd(&h[p][(k >> pd.shift[p]) & ((1u << pd.bits[p]) - 1u)], 1u);
     }
     __syncthreads();
-    hist[(size_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+    for (int p = 0; p < pd.npass; ++p)
+        for (int d = threadIdx.x; d < (1 << pd.bits[p]); d += blockDim.x)
+            if (h[p][d]) atomicAdd(&ghist[p * OS_MAXRADIX + d], h[p][d]);
 }
 
-// Stable scatter of one tile.  Tile order of item (j, warp, lane) is
-// j*256 + warp*32 + lane; an item's rank among equal digits is the number of
-// earlier (j', warp') groups' items with that digit plus the lanes before it
-// in its own warp (found with __match_any_sync).
-template <int NP>
-__global__ void k_rs_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ p0in,
-                             const uint32_t *__restrict__ p1in, uint32_t *__restrict__ kout,
-                             uint32_t *__restrict__ p0out, uint32_t *__restrict__ p1out, uint32_t n, int shift,
-                             const uint32_t *__restrict__ offs, uint32_t ntiles)
+// exclusive scan of each pass's digit counts (one thread per pass; 512 entries)
+__global__ void k_os_base(uint32_t *__restrict__ ghist, PassDesc pd)
 {
-    __shared__ uint16_t cnt[RS_ITEMS][RS_WARPS][256];
-    __shared__ uint32_t tile_off[256];
-    uint16_t *flat = &cnt[0][0][0];
-    for (int i = threadIdx.x; i < RS_ITEMS * RS_WARPS * 256; i += RS_THREADS) flat[i] = 0;
-    tile_off[threadIdx.x] = offs[(size_t)threadIdx.x * ntiles + blockIdx.x];
+    int p = threadIdx.x;
+    if (p >= pd.npass) return;
+    uint32_t run = 0;
+    for (int d = 0; d < (1 << pd.bits[p]); ++d) {
+        uint32_t c = ghist[p * OS_MAXRADIX + d];
+        ghist[p * OS_MAXRADIX + d] = run;
+        run += c;
+    }
+}
+
+// block-wide exclusive scan of two values per thread (512 entries)
+__device__ __forceinline__ void os_block_scan512(uint32_t *vals /* smem [512] in/out */, uint32_t *warp_tot /* smem [8] */)
+{
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    uint32_t a = vals[2 * t], b = vals[2 * t + 1];
+    uint32_t s = a + b, incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    uint32_t base = blockIdx.x * RS_TILE;
-    uint32_t key[RS_ITEMS], dig[RS_ITEMS];
-    uint8_t low[RS_ITEMS];
-#pragma unroll
-    for (int j = 0; j < RS_ITEMS; ++j) {
-        uint32_t i = base + j * RS_THREADS + threadIdx.x;
-        key[j] = (i < n) ? kin[i] : 0u;
-        dig[j] = (i < n) ? ((key[j] >> shift) & 255u) : 256u;
-        uint32_t peers = __match_any_sync(0xffffffffu, dig[j]);
-        low[j] = (uint8_t)__popc(peers & lt_mask);
-        if (dig[j] < 256u && lane == __ffs(peers) - 1) cnt[j][warp][dig[j]] = (uint16_t)__popc(peers);
+    if (warp == 0) {
+        uint32_t w = lane < OS_WARPS ? warp_tot[lane] : 0, wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < OS_WARPS) warp_tot[lane] = wi - w;
     }
     __syncthreads();
-    {
-        uint32_t d = threadIdx.x, run = 0;
-        for (int j = 0; j < RS_ITEMS; ++j)
-            for (int w = 0; w < RS_WARPS; ++w) {
-                uint32_t c = cnt[j][w][d];
-                cnt[j][w][d] = (uint16_t)run;
+    uint32_t ex = warp_tot[warp] + incl - s;
+    vals[2 * t] = ex;
+    vals[2 * t + 1] = ex + a;
+    __syncthreads();
+}
+
+template <int NP>
+__global__ void __launch_bounds__(OS_THREADS) k_os_pass(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ p0in,
+                                                       const uint32_t *__restrict__ p1in, uint32_t *__restrict__ kout,
+                                                       uint32_t *__restrict__ p0out, uint32_t *__restrict__ p1out,
+                                                       uint32_t n, int shift, int bits,
+                                                       const uint32_t *__restrict__ gbase,
+                                                       unsigned long long *status, uint32_t *tile_counter,
+                                                       uint32_t *err)
+{
+    extern __shared__ __align__(16) unsigned char os_smem[];
+    uint32_t *s_key = reinterpret_cast<uint32_t *>(os_smem);
+    uint32_t *s_p0 = s_key + OS_TILE;
+    uint32_t *s_p1 = s_p0 + OS_TILE;
+    uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_p1 + OS_TILE);
+    uint16_t *s_wcnt = s_rank + OS_TILE;                                   // [warp][digit]
+    uint32_t *s_tex = reinterpret_cast<uint32_t *>(s_wcnt + OS_WARPS * OS_MAXRADIX);  // tile exclusive per digit
+    uint32_t *s_gpos = s_tex + OS_MAXRADIX;                                // output start per digit
+    uint32_t *s_tot = s_gpos + OS_MAXRADIX;                                // tile count per digit
+    __shared__ uint32_t s_tile, s_wt[OS_WARPS];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t radix = 1u << bits, dmask = radix - 1u;
+    if (t == 0) s_tile = atomicAdd(tile_counter, 1u);
+    for (int i = t; i < OS_WARPS * OS_MAXRADIX; i += OS_THREADS) s_wcnt[i] = 0;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint32_t base = tile * OS_TILE;
+    const uint32_t lt = (1u << lane) - 1u;
+    // ---- rank inside each warp's chunk (order: warp, item, lane)
+    uint16_t *wc = s_wcnt + warp * OS_MAXRADIX;
+#pragma unroll 4
+    for (int j = 0; j < OS_ITEMS; ++j) {
+        const uint32_t li = warp * OS_WCHUNK + j * 32 + lane;
+        const uint32_t i = base + li;
+        const bool valid = i < n;
+        const uint32_t d = valid ? ((__ldg(kin + i) >> shift) & dmask) : radix;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t cur = valid ? wc[d] : 0;
+        __syncwarp();
+        if (valid) {
+            s_rank[li] = (uint16_t)(cur + __popc(peers & lt));
+            if ((peers & lt) == 0) wc[d] = (uint16_t)(cur + __popc(peers));
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // ---- per digit: tile total, warp offsets
+    for (uint32_t d = t; d < (uint32_t)OS_MAXRADIX; d += OS_THREADS) {
+        uint32_t run = 0;
+        if (d < radix)
+            for (int w = 0; w < OS_WARPS; ++w) {
+                uint32_t c = s_wcnt[w * OS_MAXRADIX + d];
+                s_wcnt[w * OS_MAXRADIX + d] = (uint16_t)run;
                 run += c;
             }
+        s_tot[d] = run;
+        s_tex[d] = run;
     }
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < RS_ITEMS; ++j) {
-        uint32_t i = base + j * RS_THREADS + threadIdx.x;
-        if (i < n) {
-            uint32_t d = dig[j];
-            uint32_t pos = tile_off[d] + cnt[j][warp][d] + low[j];
-            kout[pos] = key[j];
-            if (NP >= 1) p0out[pos] = p0in[i];
-            if (NP >= 2) p1out[pos] = p1in[i];
+    // ---- publish this tile's counts, then walk back over predecessors
+    for (uint32_t d = t; d < radix; d += OS_THREADS) {
+        unsigned long long *st = status + (size_t)tile * radix + d;
+        if (tile == 0) {
+            atomicExch(st, OS_PRE | (unsigned long long)s_tot[d]);
+            s_gpos[d] = __ldg(gbase + d);
+        } else {
+            atomicExch(st, OS_AGG | (unsigned long long)s_tot[d]);
         }
+    }
+    if (tile > 0) {
+        for (uint32_t d = t; d < radix; d += OS_THREADS) {
+            unsigned long long excl = 0;
+            int64_t j = (int64_t)tile - 1;
+            uint32_t spins = 0;                   // bounded over the whole walk (about 0.3 s)
+            while (j >= 0) {
+                const volatile unsigned long long *q = status + (size_t)j * radix + d;
+                unsigned long long v = *q;
+                while (v == 0) {
+                    if (++spins > (1u << 22)) {   // a predecessor never published: give up, flag it
+                        atomicOr(err, ST_TIMEOUT);
+                        v = OS_PRE;
+                        break;
+                    }
+                    __nanosleep(64);
+                    v = *q;
+                }
+                excl += v & OS_VAL;
+                if (v & OS_PRE) break;
+                --j;
+            }
+            atomicExch(status + (size_t)tile * radix + d, OS_PRE | (excl + s_tot[d]));
+            s_gpos[d] = __ldg(gbase + d) + (uint32_t)excl;
+        }
+    }
+    os_block_scan512(s_tex, s_wt);   // s_tex: start of each digit inside the tile
+    // ---- place keys (and payloads) in digit order inside shared memory
+#pragma unroll 4
+    for (int j = 0; j < OS_ITEMS; ++j) {
+        const uint32_t li = warp * OS_WCHUNK + j * 32 + lane;
+        const uint32_t i = base + li;
+        if (i < n) {
+            const uint32_t k = __ldg(kin + i);
+            const uint32_t d = (k >> shift) & dmask;
+            const uint32_t pos = s_tex[d] + s_wcnt[warp * OS_MAXRADIX + d] + s_rank[li];
+            s_key[pos] = k;
+            if (NP >= 1) s_p0[pos] = __ldg(p0in + i);
+            if (NP >= 2) s_p1[pos] = __ldg(p1in + i);
+        }
+    }
+    __syncthreads();
+    // ---- write the tile's digit runs out
+    const uint32_t tile_n = min((uint32_t)OS_TILE, n - base);
+    for (uint32_t p = t; p < tile_n; p += OS_THREADS) {
+        const uint32_t k = s_key[p];
+        const uint32_t d = (k >> shift) & dmask;
+        const uint32_t g = s_gpos[d] + (p - s_tex[d]);
+        kout[g] = k;
+        if (NP >= 1) p0out[g] = s_p0[p];
+        if (NP >= 2) p1out[g] = s_p1[p];
     }
 }
 
@@ -104,44 +235,68 @@ int bits_for(uint64_t maxval)
     return b;
 }
 
-// Stable LSD sort of (key, p0[, p1]) by the low `bits` bits of key.  The
-// arrays are ping-ponged through the scratch buffers; on return the sorted
-// data is in key/p0/p1 (the caller's buffers).
+// Stable LSD sort of (key, p0[, p1]) by the low `bits` bits of key; on return
+// the sorted data is in key/p0/p1 (the caller's buffers).
 int radix_sort(tm_ctx *ctx, uint32_t *key, uint32_t *p0, uint32_t *p1, uint32_t n, int bits)
 {
     ScratchScope scope(ctx);
     if (n <= 1 || bits <= 0) return TM_OK;
-    int np = p1 ? 2 : (p0 ? 1 : 0);
-    uint32_t ntiles = (n + RS_TILE - 1) / RS_TILE;
-    size_t hbytes = (size_t)ntiles * 256 * sizeof(uint32_t);
-    uint32_t *hist = (uint32_t *)salloc(ctx, hbytes);
+    const int np = p1 ? 2 : (p0 ? 1 : 0);
+    PassDesc pd{};
+    pd.npass = (bits + OS_MAXBITS - 1) / OS_MAXBITS;
+    if (pd.npass > OS_MAXPASS) return set_err(ctx, TM_E_LIMIT, "radix key wider than 36 bits");
+    for (int p = 0, sh = 0; p < pd.npass; ++p) {
+        int rest = bits - sh, left = pd.npass - p;
+        pd.bits[p] = (rest + left - 1) / left;
+        pd.shift[p] = sh;
+        sh += pd.bits[p];
+    }
+    const uint32_t ntiles = (n + OS_TILE - 1) / OS_TILE;
+    uint32_t *ghist = (uint32_t *)salloc(ctx, (size_t)OS_MAXPASS * OS_MAXRADIX * 4);
+    unsigned long long *status = (unsigned long long *)salloc(ctx, (size_t)ntiles * OS_MAXRADIX * 8);
+    uint32_t *counter = (uint32_t *)salloc(ctx, 256);
     uint32_t *k2 = (uint32_t *)salloc(ctx, (size_t)n * 4);
     uint32_t *a2 = np >= 1 ? (uint32_t *)salloc(ctx, (size_t)n * 4) : nullptr;
     uint32_t *b2 = np >= 2 ? (uint32_t *)salloc(ctx, (size_t)n * 4) : nullptr;
-    int rc = TM_OK;
-    if (!hist || !k2 || (np >= 1 && !a2) || (np >= 2 && !b2)) rc = TM_E_NOMEM;
+    if (!ghist || !status || !counter || !k2 || (np >= 1 && !a2) || (np >= 2 && !b2)) return TM_E_NOMEM;
+    {
+        // per device and cheap: set on every call
+        cudaError_t e = np == 0 ? cudaFuncSetAttribute(k_os_pass<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OS_SMEM)
+                      : np == 1 ? cudaFuncSetAttribute(k_os_pass<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OS_SMEM)
+                                : cudaFuncSetAttribute(k_os_pass<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OS_SMEM);
+        int rc = check_cuda(ctx, e, "radix pass shared memory");
+        if (rc) return rc;
+    }
+    cudaStream_t st = ctx->stream;
+    cudaMemsetAsync(ghist, 0, (size_t)OS_MAXPASS * OS_MAXRADIX * 4, st);
+    unsigned hb = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 4);
+    launch(ctx, k_os_hist, hb, 256, key, n, pd, ghist);
+    launch(ctx, k_os_base, 1, 32, ghist, pd);
     uint32_t *ki = key, *ai = p0, *bi = p1, *ko = k2, *ao = a2, *bo = b2;
-    int passes = (bits + 7) / 8;
-    for (int pass = 0; pass < passes && rc == TM_OK; ++pass) {
-        int shift = pass * 8;
-        launch(ctx, k_rs_hist, ntiles, RS_THREADS, ki, n, shift, hist, ntiles);
-        rc = exclusive_scan_u32(ctx, hist, hist, (uint64_t)ntiles * 256, nullptr);
-        if (rc != TM_OK) break;
+    int rc = TM_OK;
+    for (int pass = 0; pass < pd.npass && rc == TM_OK; ++pass) {
+        const uint32_t radix = 1u << pd.bits[pass];
+        cudaMemsetAsync(status, 0, (size_t)ntiles * radix * 8, st);
+        cudaMemsetAsync(counter, 0, 4, st);
+        const uint32_t *gb = ghist + pass * OS_MAXRADIX;
+        ++ctx->kernel_launches;
         if (np == 0)
-            launch(ctx, k_rs_scatter<0>, ntiles, RS_THREADS, ki, nullptr, nullptr, ko, nullptr, nullptr, n,
-                                                                     shift, hist, ntiles);
+            k_os_pass<0><<<ntiles, OS_THREADS, OS_SMEM, st>>>(ki, nullptr, nullptr, ko, nullptr, nullptr, n,
+                                                             pd.shift[pass], pd.bits[pass], gb, status, counter,
+                                                             ctx->status);
         else if (np == 1)
-            launch(ctx, k_rs_scatter<1>, ntiles, RS_THREADS, ki, ai, nullptr, ko, ao, nullptr, n, shift, hist,
-                                                                     ntiles);
+            k_os_pass<1><<<ntiles, OS_THREADS, OS_SMEM, st>>>(ki, ai, nullptr, ko, ao, nullptr, n, pd.shift[pass],
+                                                             pd.bits[pass], gb, status, counter, ctx->status);
         else
-            launch(ctx, k_rs_scatter<2>, ntiles, RS_THREADS, ki, ai, bi, ko, ao, bo, n, shift, hist, ntiles);
-        rc = check_cuda(ctx, cudaGetLastError(), "radix scatter");
+            k_os_pass<2><<<ntiles, OS_THREADS, OS_SMEM, st>>>(ki, ai, bi, ko, ao, bo, n, pd.shift[pass],
+                                                             pd.bits[pass], gb, status, counter, ctx->status);
+        rc = check_cuda(ctx, cudaGetLastError(), "radix pass");
         std::swap(ki, ko); std::swap(ai, ao); std::swap(bi, bo);
     }
     if (rc == TM_OK && ki != key) {
-        cudaMemcpyAsync(key, ki, (size_t)n * 4, cudaMemcpyDeviceToDevice, ctx->stream);
-        if (np >= 1) cudaMemcpyAsync(p0, ai, (size_t)n * 4, cudaMemcpyDeviceToDevice, ctx->stream);
-        if (np >= 2) cudaMemcpyAsync(p1, bi, (size_t)n * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+        cudaMemcpyAsync(key, ki, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+        if (np >= 1) cudaMemcpyAsync(p0, ai, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+        if (np >= 2) cudaMemcpyAsync(p1, bi, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
     }
     return rc;
 }
@@ -303,6 +458,7 @@ static uint32_t *galloc(tm_ctx *ctx, size_t count)
 int build_csr(tm_ctx *ctx)
 {
     ScratchScope scope(ctx);
+    cudaMemsetAsync(ctx->status, 0, 4, ctx->stream);
     const int TB = 256;
     cudaStream_t st = ctx->stream;
     uint64_t m0 = ctx->m_in;
@@ -455,7 +611,12 @@ int build_csr(tm_ctx *ctx)
         cudaMemsetAsync(g.pair_off, 0, 4, st);
         launch(ctx, k_offsets, 1, TB, key, 0, n, g.vpair_off);
     }
-    return check_cuda(ctx, cudaStreamSynchronize(st), "CSR build");
+    uint32_t bits = 0;
+    int rc2 = read_status(ctx, &bits);
+    if (rc2) return rc2;
+    if (bits & ST_TIMEOUT) return set_err(ctx, TM_E_TIMEOUT, "radix sort: a tile's predecessor never published its counts");
+    if (bits) return set_err(ctx, TM_E_CUDA, "CSR build: device status " + std::to_string(bits));
+    return TM_OK;
 }
 
 }  // namespace timest

@@ -411,7 +411,7 @@ struct BatchQuery {
 };
 
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, 3) k_batch(DevGraph g, const BatchQuery *__restrict__ qs,
+__global__ void __launch_bounds__(THREADS, 4) k_batch(DevGraph g, const BatchQuery *__restrict__ qs,
                                                   const uint32_t *__restrict__ tile_base, uint32_t nq, uint32_t tile,
                                                   uint32_t *counter, Acc *accs, uint32_t *status)
 {
@@ -419,8 +419,8 @@ __global__ void __launch_bounds__(THREADS, 3) k_batch(DevGraph g, const BatchQue
     __shared__ uint32_t s_item;
     __shared__ int s_q;
     __shared__ unsigned long long red[THREADS / 32][6];
-    __shared__ uint32_t recs[kRecRows * THREADS];
-    Recs R{recs + threadIdx.x, THREADS};
+    uint32_t recs_local[kRecRows];
+    Recs R{recs_local, 1};
     const uint32_t total = __ldg(tile_base + nq);
     int cur_q = -1;
     for (;;) {
