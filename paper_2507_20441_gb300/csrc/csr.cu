@@ -57,27 +57,23 @@ __global__ void k_os_hist(const uint32_t *__restrict__ keys, uint32_t n, PassDes
     __shared__ uint32_t h[OS_MAXPASS][OS_MAXRADIX];
     for (int i = threadIdx.x; i < OS_MAXPASS * OS_MAXRADIX; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        uint32_t k = __ldg(keys + i);
-        for (int p = 0; p < pd.npass; ++p) atomicAdd(&h[p][(k >> pd.shift[p]) & ((1u << pd.bits[p]) - 1u)], 1u);
+    const uint32_t lt = (1u << (threadIdx.x & 31)) - 1u;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // every lane runs the same number of rounds so the warp votes stay uniform
+    for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+        const uint32_t i = i0 + threadIdx.x;
+        const bool valid = i < n;
+        const uint32_t k = valid ? __ldg(keys + i) : 0u;
+        for (int p = 0; p < pd.npass; ++p) {
+            const uint32_t d = valid ? ((k >> pd.shift[p]) & ((1u << pd.bits[p]) - 1u)) : OS_MAXRADIX;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);   // one atomic per distinct digit
+            if (valid && (peers & lt) == 0) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
+        }
     }
     __syncthreads();
     for (int p = 0; p < pd.npass; ++p)
         for (int d = threadIdx.x; d < (1 << pd.bits[p]); d += blockDim.x)
             if (h[p][d]) atomicAdd(&ghist[p * OS_MAXRADIX + d], h[p][d]);
-}
-
-// exclusive scan of each pass's digit counts (one thread per pass; 512 entries)
-__global__ void k_os_base(uint32_t *__restrict__ ghist, PassDesc pd)
-{
-    int p = threadIdx.x;
-    if (p >= pd.npass) return;
-    uint32_t run = 0;
-    for (int d = 0; d < (1 << pd.bits[p]); ++d) {
-        uint32_t c = ghist[p * OS_MAXRADIX + d];
-        ghist[p * OS_MAXRADIX + d] = run;
-        run += c;
-    }
 }
 
 // block-wide exclusive scan of two values per thread (512 entries)
@@ -105,6 +101,20 @@ __device__ __forceinline__ void os_block_scan512(uint32_t *vals /* smem [512] in
     vals[2 * t] = ex;
     vals[2 * t + 1] = ex + a;
     __syncthreads();
+}
+
+// exclusive scan of each pass's digit counts: one block of 256 threads per
+// pass, two entries per thread
+__global__ void k_os_base(uint32_t *__restrict__ ghist)
+{
+    __shared__ uint32_t v[OS_MAXRADIX], wt[OS_WARPS];
+    uint32_t *g = ghist + blockIdx.x * OS_MAXRADIX;
+    v[2 * threadIdx.x] = g[2 * threadIdx.x];
+    v[2 * threadIdx.x + 1] = g[2 * threadIdx.x + 1];
+    __syncthreads();
+    os_block_scan512(v, wt);
+    g[2 * threadIdx.x] = v[2 * threadIdx.x];
+    g[2 * threadIdx.x + 1] = v[2 * threadIdx.x + 1];
 }
 
 template <int NP>
@@ -178,23 +188,46 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const uint32_t *__restri
     if (tile > 0) {
         for (uint32_t d = t; d < radix; d += OS_THREADS) {
             unsigned long long excl = 0;
-            int64_t j = (int64_t)tile - 1;
-            uint32_t spins = 0;                   // bounded over the whole walk (about 0.3 s)
-            while (j >= 0) {
-                const volatile unsigned long long *q = status + (size_t)j * radix + d;
-                unsigned long long v = *q;
-                while (v == 0) {
+            int64_t j = (int64_t)tile - 1;          // nearest predecessor not yet added
+            uint32_t spins = 0;                     // bounded over the whole walk (about 0.3 s)
+            constexpr int LB = 8;                   // predecessors read per round trip
+            bool done = false;
+            while (!done && j >= 0) {
+                const int w = j + 1 < LB ? (int)(j + 1) : LB;
+                unsigned long long v[LB];
+#pragma unroll
+                for (int x = 0; x < LB; ++x)
+                    v[x] = x < w ? *(const volatile unsigned long long *)(status + (size_t)(j - x) * radix + d) : OS_PRE;
+                // every entry up to the nearest inclusive prefix must be published
+                for (;;) {
+                    int need = -1;
+#pragma unroll
+                    for (int x = LB - 1; x >= 0; --x)
+                        if (x < w && v[x] == 0) need = x;
+                    int pre = LB;
+#pragma unroll
+                    for (int x = LB - 1; x >= 0; --x)
+                        if (x < w && (v[x] & OS_PRE)) pre = x;
+                    if (need < 0 || need > pre) {
+                        const int upto = pre < w ? pre : w - 1;
+#pragma unroll
+                        for (int x = 0; x < LB; ++x)
+                            if (x <= upto) excl += v[x] & OS_VAL;
+                        if (pre < w) done = true;
+                        j -= w;
+                        break;
+                    }
                     if (++spins > (1u << 22)) {   // a predecessor never published: give up, flag it
                         atomicOr(err, ST_TIMEOUT);
-                        v = OS_PRE;
+                        done = true;
                         break;
                     }
                     __nanosleep(64);
-                    v = *q;
+#pragma unroll
+                    for (int x = 0; x < LB; ++x)
+                        if (x < w && v[x] == 0)
+                            v[x] = *(const volatile unsigned long long *)(status + (size_t)(j - x) * radix + d);
                 }
-                excl += v & OS_VAL;
-                if (v & OS_PRE) break;
-                --j;
             }
             atomicExch(status + (size_t)tile * radix + d, OS_PRE | (excl + s_tot[d]));
             s_gpos[d] = __ldg(gbase + d) + (uint32_t)excl;
@@ -271,7 +304,7 @@ int radix_sort(tm_ctx *ctx, uint32_t *key, uint32_t *p0, uint32_t *p1, uint32_t 
     cudaMemsetAsync(ghist, 0, (size_t)OS_MAXPASS * OS_MAXRADIX * 4, st);
     unsigned hb = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 4);
     launch(ctx, k_os_hist, hb, 256, key, n, pd, ghist);
-    launch(ctx, k_os_base, 1, 32, ghist, pd);
+    launch(ctx, k_os_base, (unsigned)pd.npass, 256, ghist);
     uint32_t *ki = key, *ai = p0, *bi = p1, *ko = k2, *ao = a2, *bo = b2;
     int rc = TM_OK;
     for (int pass = 0; pass < pd.npass && rc == TM_OK; ++pass) {
