@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-queries", type=int, default=100)
     ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--alloc", choices=["native", "torch"], default="native",
+                    help="device memory: the library's stream-ordered pool or PyTorch's caching allocator")
     return ap.parse_args()
 
 
@@ -167,7 +169,8 @@ def run_ours(args, rank, world, local_rank):
     mo = synth.make_motif(args.workload)
     k = args.k or mo.k
     stream = torch.cuda.Stream(device=dev)
-    ctx = tg.Context(device=local_rank, stream=stream.cuda_stream, profile=True)
+    ctx = tg.Context(device=local_rank, stream=stream.cuda_stream, profile=True,
+                     torch_allocator=(args.alloc == "torch"))
     src_d = torch.from_numpy(gr.src.view(np.int32)).to(dev)
     dst_d = torch.from_numpy(gr.dst.view(np.int32)).to(dev)
     t_d = torch.from_numpy(gr.t).to(dev)
@@ -288,7 +291,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": args.workload, "n": gr.n, "m": int(ctx.m), "motif": mo.name, "delta": mo.delta,
                    "k": k, "tree": [int(x) for x in order], "root": int(order[0]),
-                   "l2": "flushed (512 MB write) before every timed step",
+                   "l2": "flushed (512 MB write) before every timed step", "alloc": args.alloc,
                    "graph": "Chung-Lu bursty" if "cl" in args.workload else "uniform"},
         "clocks": clk,
         "e2e": e2e,

@@ -264,7 +264,13 @@ enum {
     TM_PH_ROOT = 5,     /* root CDF and window totals (Claim 3.4)           */
     TM_PH_SAMPLE = 6,   /* sampler + validator + DeriveCnt + reduction      */
     TM_PH_BATCH = 7,    /* batched sampler                                  */
-    TM_NUM_PHASES = 8
+    /* parts of TM_PH_CSR (also counted in it) */
+    TM_PH_CSR_STATS = 8,   /* input checks, t range, compaction             */
+    TM_PH_CSR_GLOBAL = 9,  /* sort into (t', src, dst) order and duplicates */
+    TM_PH_CSR_OUT = 10,    /* out-lists                                     */
+    TM_PH_CSR_IN = 11,     /* in-lists                                      */
+    TM_PH_CSR_MULTI = 12,  /* multi-edge lists and pair tables              */
+    TM_NUM_PHASES = 13
 };
 
 /* Accumulated milliseconds and kernel-launch counts per phase since the last

@@ -375,7 +375,8 @@ def tm_serve_stop(ctx):
     _check(lib().tm_serve_stop(ctx), ctx, "tm_serve_stop")
 
 
-PHASES = ["load", "csr", "windows", "dp", "prefix", "root", "sample", "batch"]
+PHASES = ["load", "csr", "windows", "dp", "prefix", "root", "sample", "batch",
+          "csr.stats", "csr.global", "csr.out", "csr.in", "csr.multi"]
 
 
 def tm_phase_times(ctx):

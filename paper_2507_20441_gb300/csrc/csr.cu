@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <memory>
 #include <string>
 
 #include "scan.cuh"
@@ -23,17 +24,16 @@ namespace timest {
 
 namespace {
 
-// ---- radix sort: one kernel per digit pass (decoupled look-back) ---------
-// Keys are sorted least significant digit first, with up to 9-bit digits.
-// A first kernel counts every pass's digits over the whole array (the counts
-// of a pass do not depend on the order earlier passes leave), so each pass
-// knows where every digit's output run starts.  In a pass, each block takes
-// the next tile of 4096 keys from a counter, ranks them stably inside the
-// tile (per warp with __match_any_sync, then across warps), publishes the
-// tile's digit counts, and adds up its predecessors' counts by walking back
-// over their published values (a predecessor that has finished its own walk
-// publishes an inclusive prefix, which ends the walk).  The tile is then
-// reordered by digit in shared memory and written out in contiguous runs.
+// ---- radix sort --------------------------------------------------------
+// Keys are sorted least significant digit first, with up to 9-bit digits
+// (a 17-bit vertex id takes two passes, a 25-bit time three).  A pass is
+//   1. per-tile digit counts (4096 keys per tile), stored digit-major;
+//   2. an exclusive scan of those counts, which gives, for every (digit,
+//      tile), where the tile's run of that digit starts in the output;
+//   3. the scatter: each tile ranks its keys stably (per warp with
+//      __match_any_sync, then across warps), reorders them by digit in shared
+//      memory and writes each digit's run out contiguously.
+// No block waits on another.
 constexpr int OS_THREADS = 256;
 constexpr int OS_ITEMS = 16;
 constexpr int OS_TILE = OS_THREADS * OS_ITEMS;     // 4096 keys per tile
@@ -42,38 +42,29 @@ constexpr int OS_WCHUNK = OS_ITEMS * 32;           // keys per warp chunk
 constexpr int OS_MAXBITS = 9;
 constexpr int OS_MAXRADIX = 1 << OS_MAXBITS;
 constexpr int OS_MAXPASS = 4;
-constexpr unsigned long long OS_AGG = 1ull << 62, OS_PRE = 2ull << 62, OS_VAL = (1ull << 62) - 1;
 constexpr size_t OS_SMEM = (size_t)OS_TILE * 4 * 3 + (size_t)OS_TILE * 2 + (size_t)OS_WARPS * OS_MAXRADIX * 2 +
-                           (size_t)OS_MAXRADIX * 4 * 3;
+                           (size_t)OS_MAXRADIX * 4 * 2;
 
-struct PassDesc {
-    int npass;
-    int shift[OS_MAXPASS];
-    int bits[OS_MAXPASS];
-};
-
-__global__ void k_os_hist(const uint32_t *__restrict__ keys, uint32_t n, PassDesc pd, uint32_t *__restrict__ ghist)
+// per-tile digit counts, written to counts[d * ntiles + tile]
+__global__ void __launch_bounds__(OS_THREADS) k_rs_count(const uint32_t *__restrict__ kin, uint32_t n, int shift,
+                                                          int bits, uint32_t ntiles, uint32_t *__restrict__ counts)
 {
-    __shared__ uint32_t h[OS_MAXPASS][OS_MAXRADIX];
-    for (int i = threadIdx.x; i < OS_MAXPASS * OS_MAXRADIX; i += blockDim.x) (&h[0][0])[i] = 0;
+    __shared__ uint32_t h[OS_MAXRADIX];
+    const uint32_t radix = 1u << bits, dmask = radix - 1u;
+    for (uint32_t d = threadIdx.x; d < radix; d += OS_THREADS) h[d] = 0;
     __syncthreads();
     const uint32_t lt = (1u << (threadIdx.x & 31)) - 1u;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    // every lane runs the same number of rounds so the warp votes stay uniform
-    for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
-        const uint32_t i = i0 + threadIdx.x;
+    const uint32_t base = blockIdx.x * OS_TILE;
+#pragma unroll 4
+    for (int j = 0; j < OS_ITEMS; ++j) {
+        const uint32_t i = base + j * OS_THREADS + threadIdx.x;
         const bool valid = i < n;
-        const uint32_t k = valid ? __ldg(keys + i) : 0u;
-        for (int p = 0; p < pd.npass; ++p) {
-            const uint32_t d = valid ? ((k >> pd.shift[p]) & ((1u << pd.bits[p]) - 1u)) : OS_MAXRADIX;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);   // one atomic per distinct digit
-            if (valid && (peers & lt) == 0) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
-        }
+        const uint32_t d = valid ? ((__ldg(kin + i) >> shift) & dmask) : radix;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (valid && (peers & lt) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
-    for (int p = 0; p < pd.npass; ++p)
-        for (int d = threadIdx.x; d < (1 << pd.bits[p]); d += blockDim.x)
-            if (h[p][d]) atomicAdd(&ghist[p * OS_MAXRADIX + d], h[p][d]);
+    for (uint32_t d = threadIdx.x; d < radix; d += OS_THREADS) counts[(size_t)d * ntiles + blockIdx.x] = h[d];
 }
 
 // block-wide exclusive scan of two values per thread (512 entries)
@@ -103,46 +94,31 @@ __device__ __forceinline__ void os_block_scan512(uint32_t *vals /* smem [512] in
     __syncthreads();
 }
 
-// exclusive scan of each pass's digit counts: one block of 256 threads per
-// pass, two entries per thread
-__global__ void k_os_base(uint32_t *__restrict__ ghist)
-{
-    __shared__ uint32_t v[OS_MAXRADIX], wt[OS_WARPS];
-    uint32_t *g = ghist + blockIdx.x * OS_MAXRADIX;
-    v[2 * threadIdx.x] = g[2 * threadIdx.x];
-    v[2 * threadIdx.x + 1] = g[2 * threadIdx.x + 1];
-    __syncthreads();
-    os_block_scan512(v, wt);
-    g[2 * threadIdx.x] = v[2 * threadIdx.x];
-    g[2 * threadIdx.x + 1] = v[2 * threadIdx.x + 1];
-}
-
 template <int NP>
-__global__ void __launch_bounds__(OS_THREADS) k_os_pass(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ p0in,
-                                                       const uint32_t *__restrict__ p1in, uint32_t *__restrict__ kout,
-                                                       uint32_t *__restrict__ p0out, uint32_t *__restrict__ p1out,
-                                                       uint32_t n, int shift, int bits,
-                                                       const uint32_t *__restrict__ gbase,
-                                                       unsigned long long *status, uint32_t *tile_counter,
-                                                       uint32_t *err)
+__global__ void __launch_bounds__(OS_THREADS) k_rs_scatter(const uint32_t *__restrict__ kin,
+                                                          const uint32_t *__restrict__ p0in,
+                                                          const uint32_t *__restrict__ p1in, uint32_t *__restrict__ kout,
+                                                          uint32_t *__restrict__ p0out, uint32_t *__restrict__ p1out,
+                                                          uint32_t n, int shift, int bits, uint32_t ntiles,
+                                                          const uint32_t *__restrict__ offs)
 {
     extern __shared__ __align__(16) unsigned char os_smem[];
     uint32_t *s_key = reinterpret_cast<uint32_t *>(os_smem);
     uint32_t *s_p0 = s_key + OS_TILE;
     uint32_t *s_p1 = s_p0 + OS_TILE;
     uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_p1 + OS_TILE);
-    uint16_t *s_wcnt = s_rank + OS_TILE;                                   // [warp][digit]
-    uint32_t *s_tex = reinterpret_cast<uint32_t *>(s_wcnt + OS_WARPS * OS_MAXRADIX);  // tile exclusive per digit
-    uint32_t *s_gpos = s_tex + OS_MAXRADIX;                                // output start per digit
-    uint32_t *s_tot = s_gpos + OS_MAXRADIX;                                // tile count per digit
-    __shared__ uint32_t s_tile, s_wt[OS_WARPS];
+    uint16_t *s_wcnt = s_rank + OS_TILE;                                            // [warp][digit]
+    uint32_t *s_tex = reinterpret_cast<uint32_t *>(s_wcnt + OS_WARPS * OS_MAXRADIX);  // digit start in the tile
+    uint32_t *s_gpos = s_tex + OS_MAXRADIX;                                         // digit start in the output
+    __shared__ uint32_t s_wt[OS_WARPS];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const uint32_t radix = 1u << bits, dmask = radix - 1u;
-    if (t == 0) s_tile = atomicAdd(tile_counter, 1u);
-    for (int i = t; i < OS_WARPS * OS_MAXRADIX; i += OS_THREADS) s_wcnt[i] = 0;
-    __syncthreads();
-    const uint32_t tile = s_tile;
+    const uint32_t tile = blockIdx.x;
     const uint32_t base = tile * OS_TILE;
+    for (int i = t; i < OS_WARPS * OS_MAXRADIX; i += OS_THREADS) s_wcnt[i] = 0;
+    for (uint32_t d = t; d < (uint32_t)OS_MAXRADIX; d += OS_THREADS)
+        s_gpos[d] = d < radix ? __ldg(offs + (size_t)d * ntiles + tile) : 0u;
+    __syncthreads();
     const uint32_t lt = (1u << lane) - 1u;
     // ---- rank inside each warp's chunk (order: warp, item, lane)
     uint16_t *wc = s_wcnt + warp * OS_MAXRADIX;
@@ -162,7 +138,7 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const uint32_t *__restri
         __syncwarp();
     }
     __syncthreads();
-    // ---- per digit: tile total, warp offsets
+    // ---- per digit: tile total and warp offsets
     for (uint32_t d = t; d < (uint32_t)OS_MAXRADIX; d += OS_THREADS) {
         uint32_t run = 0;
         if (d < radix)
@@ -171,69 +147,10 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const uint32_t *__restri
                 s_wcnt[w * OS_MAXRADIX + d] = (uint16_t)run;
                 run += c;
             }
-        s_tot[d] = run;
         s_tex[d] = run;
     }
     __syncthreads();
-    // ---- publish this tile's counts, then walk back over predecessors
-    for (uint32_t d = t; d < radix; d += OS_THREADS) {
-        unsigned long long *st = status + (size_t)tile * radix + d;
-        if (tile == 0) {
-            atomicExch(st, OS_PRE | (unsigned long long)s_tot[d]);
-            s_gpos[d] = __ldg(gbase + d);
-        } else {
-            atomicExch(st, OS_AGG | (unsigned long long)s_tot[d]);
-        }
-    }
-    if (tile > 0) {
-        for (uint32_t d = t; d < radix; d += OS_THREADS) {
-            unsigned long long excl = 0;
-            int64_t j = (int64_t)tile - 1;          // nearest predecessor not yet added
-            uint32_t spins = 0;                     // bounded over the whole walk (about 0.3 s)
-            constexpr int LB = 8;                   // predecessors read per round trip
-            bool done = false;
-            while (!done && j >= 0) {
-                const int w = j + 1 < LB ? (int)(j + 1) : LB;
-                unsigned long long v[LB];
-#pragma unroll
-                for (int x = 0; x < LB; ++x)
-                    v[x] = x < w ? *(const volatile unsigned long long *)(status + (size_t)(j - x) * radix + d) : OS_PRE;
-                // every entry up to the nearest inclusive prefix must be published
-                for (;;) {
-                    int need = -1;
-#pragma unroll
-                    for (int x = LB - 1; x >= 0; --x)
-                        if (x < w && v[x] == 0) need = x;
-                    int pre = LB;
-#pragma unroll
-                    for (int x = LB - 1; x >= 0; --x)
-                        if (x < w && (v[x] & OS_PRE)) pre = x;
-                    if (need < 0 || need > pre) {
-                        const int upto = pre < w ? pre : w - 1;
-#pragma unroll
-                        for (int x = 0; x < LB; ++x)
-                            if (x <= upto) excl += v[x] & OS_VAL;
-                        if (pre < w) done = true;
-                        j -= w;
-                        break;
-                    }
-                    if (++spins > (1u << 22)) {   // a predecessor never published: give up, flag it
-                        atomicOr(err, ST_TIMEOUT);
-                        done = true;
-                        break;
-                    }
-                    __nanosleep(64);
-#pragma unroll
-                    for (int x = 0; x < LB; ++x)
-                        if (x < w && v[x] == 0)
-                            v[x] = *(const volatile unsigned long long *)(status + (size_t)(j - x) * radix + d);
-                }
-            }
-            atomicExch(status + (size_t)tile * radix + d, OS_PRE | (excl + s_tot[d]));
-            s_gpos[d] = __ldg(gbase + d) + (uint32_t)excl;
-        }
-    }
-    os_block_scan512(s_tex, s_wt);   // s_tex: start of each digit inside the tile
+    os_block_scan512(s_tex, s_wt);
     // ---- place keys (and payloads) in digit order inside shared memory
 #pragma unroll 4
     for (int j = 0; j < OS_ITEMS; ++j) {
@@ -275,56 +192,43 @@ int radix_sort(tm_ctx *ctx, uint32_t *key, uint32_t *p0, uint32_t *p1, uint32_t 
     ScratchScope scope(ctx);
     if (n <= 1 || bits <= 0) return TM_OK;
     const int np = p1 ? 2 : (p0 ? 1 : 0);
-    PassDesc pd{};
-    pd.npass = (bits + OS_MAXBITS - 1) / OS_MAXBITS;
-    if (pd.npass > OS_MAXPASS) return set_err(ctx, TM_E_LIMIT, "radix key wider than 36 bits");
-    for (int p = 0, sh = 0; p < pd.npass; ++p) {
-        int rest = bits - sh, left = pd.npass - p;
-        pd.bits[p] = (rest + left - 1) / left;
-        pd.shift[p] = sh;
-        sh += pd.bits[p];
-    }
+    const int npass = (bits + OS_MAXBITS - 1) / OS_MAXBITS;
+    if (npass > OS_MAXPASS) return set_err(ctx, TM_E_LIMIT, "radix key wider than 36 bits");
     const uint32_t ntiles = (n + OS_TILE - 1) / OS_TILE;
-    uint32_t *ghist = (uint32_t *)salloc(ctx, (size_t)OS_MAXPASS * OS_MAXRADIX * 4);
-    unsigned long long *status = (unsigned long long *)salloc(ctx, (size_t)ntiles * OS_MAXRADIX * 8);
-    uint32_t *counter = (uint32_t *)salloc(ctx, 256);
+    uint32_t *counts = (uint32_t *)salloc(ctx, (size_t)ntiles * OS_MAXRADIX * 4);
     uint32_t *k2 = (uint32_t *)salloc(ctx, (size_t)n * 4);
     uint32_t *a2 = np >= 1 ? (uint32_t *)salloc(ctx, (size_t)n * 4) : nullptr;
     uint32_t *b2 = np >= 2 ? (uint32_t *)salloc(ctx, (size_t)n * 4) : nullptr;
-    if (!ghist || !status || !counter || !k2 || (np >= 1 && !a2) || (np >= 2 && !b2)) return TM_E_NOMEM;
+    if (!counts || !k2 || (np >= 1 && !a2) || (np >= 2 && !b2)) return TM_E_NOMEM;
     {
         // per device and cheap: set on every call
-        cudaError_t e = np == 0 ? cudaFuncSetAttribute(k_os_pass<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OS_SMEM)
-                      : np == 1 ? cudaFuncSetAttribute(k_os_pass<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OS_SMEM)
-                                : cudaFuncSetAttribute(k_os_pass<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OS_SMEM);
+        cudaError_t e = np == 0 ? cudaFuncSetAttribute(k_rs_scatter<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OS_SMEM)
+                      : np == 1 ? cudaFuncSetAttribute(k_rs_scatter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OS_SMEM)
+                                : cudaFuncSetAttribute(k_rs_scatter<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OS_SMEM);
         int rc = check_cuda(ctx, e, "radix pass shared memory");
         if (rc) return rc;
     }
     cudaStream_t st = ctx->stream;
-    cudaMemsetAsync(ghist, 0, (size_t)OS_MAXPASS * OS_MAXRADIX * 4, st);
-    unsigned hb = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 4);
-    launch(ctx, k_os_hist, hb, 256, key, n, pd, ghist);
-    launch(ctx, k_os_base, (unsigned)pd.npass, 256, ghist);
     uint32_t *ki = key, *ai = p0, *bi = p1, *ko = k2, *ao = a2, *bo = b2;
     int rc = TM_OK;
-    for (int pass = 0; pass < pd.npass && rc == TM_OK; ++pass) {
-        const uint32_t radix = 1u << pd.bits[pass];
-        cudaMemsetAsync(status, 0, (size_t)ntiles * radix * 8, st);
-        cudaMemsetAsync(counter, 0, 4, st);
-        const uint32_t *gb = ghist + pass * OS_MAXRADIX;
+    for (int pass = 0, sh = 0; pass < npass && rc == TM_OK; ++pass) {
+        const int left = npass - pass, pb = (bits - sh + left - 1) / left;
+        const uint64_t ncount = (uint64_t)ntiles << pb;
+        launch(ctx, k_rs_count, ntiles, OS_THREADS, ki, n, sh, pb, ntiles, counts);
+        rc = exclusive_scan_u32(ctx, counts, counts, ncount, nullptr);
+        if (rc) break;
         ++ctx->kernel_launches;
         if (np == 0)
-            k_os_pass<0><<<ntiles, OS_THREADS, OS_SMEM, st>>>(ki, nullptr, nullptr, ko, nullptr, nullptr, n,
-                                                             pd.shift[pass], pd.bits[pass], gb, status, counter,
-                                                             ctx->status);
+            k_rs_scatter<0><<<ntiles, OS_THREADS, OS_SMEM, st>>>(ki, nullptr, nullptr, ko, nullptr, nullptr, n, sh, pb,
+                                                                ntiles, counts);
         else if (np == 1)
-            k_os_pass<1><<<ntiles, OS_THREADS, OS_SMEM, st>>>(ki, ai, nullptr, ko, ao, nullptr, n, pd.shift[pass],
-                                                             pd.bits[pass], gb, status, counter, ctx->status);
+            k_rs_scatter<1><<<ntiles, OS_THREADS, OS_SMEM, st>>>(ki, ai, nullptr, ko, ao, nullptr, n, sh, pb, ntiles,
+                                                                counts);
         else
-            k_os_pass<2><<<ntiles, OS_THREADS, OS_SMEM, st>>>(ki, ai, bi, ko, ao, bo, n, pd.shift[pass],
-                                                             pd.bits[pass], gb, status, counter, ctx->status);
+            k_rs_scatter<2><<<ntiles, OS_THREADS, OS_SMEM, st>>>(ki, ai, bi, ko, ao, bo, n, sh, pb, ntiles, counts);
         rc = check_cuda(ctx, cudaGetLastError(), "radix pass");
         std::swap(ki, ko); std::swap(ai, ao); std::swap(bi, bo);
+        sh += pb;
     }
     if (rc == TM_OK && ki != key) {
         cudaMemcpyAsync(key, ki, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
@@ -501,6 +405,7 @@ int build_csr(tm_ctx *ctx)
     g.n = n;
     int rc = TM_OK;
     // ---- statistics: t range, self loops, bad ids
+    std::unique_ptr<PhaseScope> sec(new PhaseScope(ctx, TM_PH_CSR_STATS));
     Stats hs{LLONG_MAX, LLONG_MIN, 0, 0};
     Stats *ds = (Stats *)salloc(ctx, sizeof(Stats));
     if (!ds) return TM_E_NOMEM;
@@ -539,6 +444,8 @@ int build_csr(tm_ctx *ctx)
                                                            tmin, T0, S0, D0);
     }
     // ---- GLOBAL order: LSD by dst, then src, then t'
+    sec.reset();
+    sec.reset(new PhaseScope(ctx, TM_PH_CSR_GLOBAL));
     int vbits = bits_for(n ? n - 1 : 0);
     int tbits = bits_for((uint64_t)(tmax - tmin));
     rc = radix_sort(ctx, D0, S0, T0, m, vbits);
@@ -580,6 +487,8 @@ int build_csr(tm_ctx *ctx)
     // scratch key buffer (reuse S0/D0/T0 as work space)
     uint32_t *key = S0, *tmp = D0;
     // ---- OUT order: stable sort of gid by src
+    sec.reset();
+    sec.reset(new PhaseScope(ctx, TM_PH_CSR_OUT));
     g.out_gid = galloc(ctx, m); g.out_t = galloc(ctx, m); g.out_nbr = galloc(ctx, m); g.out_off = galloc(ctx, (size_t)n + 1);
     g.in_gid = galloc(ctx, m); g.in_t = galloc(ctx, m); g.in_nbr = galloc(ctx, m); g.in_off = galloc(ctx, (size_t)n + 1);
     if (!g.out_gid || !g.out_t || !g.out_nbr || !g.out_off || !g.in_gid || !g.in_t || !g.in_nbr || !g.in_off)
@@ -593,6 +502,8 @@ int build_csr(tm_ctx *ctx)
     }
     launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, key, m, n, g.out_off);
     // ---- IN order: stable sort of gid by dst
+    sec.reset();
+    sec.reset(new PhaseScope(ctx, TM_PH_CSR_IN));
     if (m) {
         cudaMemcpyAsync(key, g.g_dst, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
         launch(ctx, k_iota, blocks_for(m, TB), TB, g.in_gid, m);
@@ -602,6 +513,8 @@ int build_csr(tm_ctx *ctx)
     }
     launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, key, m, n, g.in_off);
     // ---- multi-edge order: stable re-sort of the IN order by source
+    sec.reset();
+    sec.reset(new PhaseScope(ctx, TM_PH_CSR_MULTI));
     g.multi_gid = galloc(ctx, m); g.multi_t = galloc(ctx, m); g.g_pair = galloc(ctx, m);
     g.vpair_off = galloc(ctx, (size_t)n + 1);
     if (!g.multi_gid || !g.multi_t || !g.g_pair || !g.vpair_off) return TM_E_NOMEM;
@@ -647,7 +560,6 @@ int build_csr(tm_ctx *ctx)
     uint32_t bits = 0;
     int rc2 = read_status(ctx, &bits);
     if (rc2) return rc2;
-    if (bits & ST_TIMEOUT) return set_err(ctx, TM_E_TIMEOUT, "radix sort: a tile's predecessor never published its counts");
     if (bits) return set_err(ctx, TM_E_CUDA, "CSR build: device status " + std::to_string(bits));
     return TM_OK;
 }
