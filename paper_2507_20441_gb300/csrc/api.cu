@@ -174,9 +174,8 @@ static void free_graph(tm_ctx *ctx)
 
 static void free_input(tm_ctx *ctx)
 {
-    if (ctx->in_src) dfree(ctx, ctx->in_src, ctx->m_in * 4);
-    if (ctx->in_dst) dfree(ctx, ctx->in_dst, ctx->m_in * 4);
-    if (ctx->in_t) dfree(ctx, ctx->in_t, ctx->m_in * 8);
+    // in_t heads the single staging block (t, then src, then dst)
+    if (ctx->in_t) dfree(ctx, ctx->in_t, ctx->m_in * 16);
     ctx->in_src = ctx->in_dst = nullptr;
     ctx->in_t = nullptr;
 }
@@ -371,6 +370,15 @@ int tm_create(tm_ctx **out, const tm_config *cfg, void *cuda_stream)
     if ((ctx->cfg.alloc == nullptr) != (ctx->cfg.free == nullptr)) { delete ctx; return TM_E_ARG; }
     ctx->device = ctx->cfg.device;
     int rc = check_cuda(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (!rc && !ctx->cfg.alloc) {
+        // keep freed blocks in this process's stream-ordered pool for reuse
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) {
+            uint64_t keep = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    }
     if (!rc) rc = check_cuda(ctx, cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device),
                              "device attributes");
     if (!rc) {
@@ -430,10 +438,11 @@ int tm_graph_load(tm_ctx *ctx, uint32_t n, uint64_t m, const uint32_t *src, cons
     ctx->m_in = m;
     ctx->load_flags = flags;
     if (m) {
-        ctx->in_src = (uint32_t *)dalloc(ctx, m * 4);
-        ctx->in_dst = (uint32_t *)dalloc(ctx, m * 4);
-        ctx->in_t = (int64_t *)dalloc(ctx, m * 8);
-        if (!ctx->in_src || !ctx->in_dst || !ctx->in_t) { free_input(ctx); return TM_E_NOMEM; }
+        char *blk = (char *)dalloc(ctx, m * 16);
+        if (!blk) return TM_E_NOMEM;
+        ctx->in_t = (int64_t *)blk;
+        ctx->in_src = (uint32_t *)(blk + m * 8);
+        ctx->in_dst = (uint32_t *)(blk + m * 12);
         cudaMemcpyKind kind = (flags & TM_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         {
             PhaseScope ph(ctx, TM_PH_LOAD);

@@ -384,17 +384,37 @@ inline unsigned blocks_for(uint64_t n, int threads) { return (unsigned)((n + thr
 
 }  // namespace
 
-static uint32_t *galloc(tm_ctx *ctx, size_t count)
+// Graph arrays come from a few large blocks (one allocator call each), cut
+// into 256-byte aligned arrays.
+struct GraphBlock {
+    char *base = nullptr;
+    size_t size = 0, off = 0;
+};
+
+static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+static bool gblock_open(tm_ctx *ctx, GraphBlock &b, size_t bytes)
 {
-    size_t bytes = (count ? count : 1) * sizeof(uint32_t);
-    uint32_t *p = (uint32_t *)dalloc(ctx, bytes);
-    if (p) ctx->graph_bufs.push_back({p, bytes});
+    b.size = bytes ? bytes : 256;
+    b.off = 0;
+    b.base = (char *)dalloc(ctx, b.size);
+    if (b.base) ctx->graph_bufs.push_back({b.base, b.size});
+    return b.base != nullptr;
+}
+
+static uint32_t *gtake(GraphBlock &b, size_t count)
+{
+    size_t bytes = align256((count ? count : 1) * sizeof(uint32_t));
+    if (b.off + bytes > b.size) return nullptr;
+    uint32_t *p = (uint32_t *)(b.base + b.off);
+    b.off += bytes;
     return p;
 }
 
 int build_csr(tm_ctx *ctx)
 {
     ScratchScope scope(ctx);
+    GraphBlock gb;
     cudaMemsetAsync(ctx->status, 0, 4, ctx->stream);
     const int TB = 256;
     cudaStream_t st = ctx->stream;
@@ -466,7 +486,12 @@ int build_csr(tm_ctx *ctx)
         if (ndup && !(ctx->load_flags & TM_DEDUP)) {
             return set_err(ctx, TM_E_DUP, "input repeats a (u,v,t) tuple (pass TM_DEDUP to drop repeats)");
         }
-        g.g_t = galloc(ctx, m - ndup); g.g_src = galloc(ctx, m - ndup); g.g_dst = galloc(ctx, m - ndup);
+        {
+            // every m- and n-sized array of the graph in one block
+            const size_t mf = (size_t)(m - ndup), a_m = align256((mf ? mf : 1) * 4), a_n = align256(((size_t)n + 1) * 4);
+            if (!gblock_open(ctx, gb, 13 * a_m + 3 * a_n)) return TM_E_NOMEM;
+        }
+        g.g_t = gtake(gb, m - ndup); g.g_src = gtake(gb, m - ndup); g.g_dst = gtake(gb, m - ndup);
         if (!g.g_t || !g.g_src || !g.g_dst) return TM_E_NOMEM;
         if (ndup) {
             uint32_t *pos = (uint32_t *)salloc(ctx, (size_t)m * 4);
@@ -489,8 +514,8 @@ int build_csr(tm_ctx *ctx)
     // ---- OUT order: stable sort of gid by src
     sec.reset();
     sec.reset(new PhaseScope(ctx, TM_PH_CSR_OUT));
-    g.out_gid = galloc(ctx, m); g.out_t = galloc(ctx, m); g.out_nbr = galloc(ctx, m); g.out_off = galloc(ctx, (size_t)n + 1);
-    g.in_gid = galloc(ctx, m); g.in_t = galloc(ctx, m); g.in_nbr = galloc(ctx, m); g.in_off = galloc(ctx, (size_t)n + 1);
+    g.out_gid = gtake(gb, m); g.out_t = gtake(gb, m); g.out_nbr = gtake(gb, m); g.out_off = gtake(gb, (size_t)n + 1);
+    g.in_gid = gtake(gb, m); g.in_t = gtake(gb, m); g.in_nbr = gtake(gb, m); g.in_off = gtake(gb, (size_t)n + 1);
     if (!g.out_gid || !g.out_t || !g.out_nbr || !g.out_off || !g.in_gid || !g.in_t || !g.in_nbr || !g.in_off)
         return TM_E_NOMEM;
     if (m) {
@@ -515,8 +540,8 @@ int build_csr(tm_ctx *ctx)
     // ---- multi-edge order: stable re-sort of the IN order by source
     sec.reset();
     sec.reset(new PhaseScope(ctx, TM_PH_CSR_MULTI));
-    g.multi_gid = galloc(ctx, m); g.multi_t = galloc(ctx, m); g.g_pair = galloc(ctx, m);
-    g.vpair_off = galloc(ctx, (size_t)n + 1);
+    g.multi_gid = gtake(gb, m); g.multi_t = gtake(gb, m); g.g_pair = gtake(gb, m);
+    g.vpair_off = gtake(gb, (size_t)n + 1);
     if (!g.multi_gid || !g.multi_t || !g.g_pair || !g.vpair_off) return TM_E_NOMEM;
     uint32_t np = 0;
     if (m) {
@@ -538,9 +563,11 @@ int build_csr(tm_ctx *ctx)
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "pair count");
         if (rc) return rc;
         g.npairs = np;
-        g.pair_off = galloc(ctx, (size_t)np + 1);
-        g.pair_dst = galloc(ctx, np);
-        g.rev_pair = galloc(ctx, np);
+        GraphBlock pbk;
+        if (!gblock_open(ctx, pbk, 3 * align256(((size_t)np + 1) * 4))) return TM_E_NOMEM;
+        g.pair_off = gtake(pbk, (size_t)np + 1);
+        g.pair_dst = gtake(pbk, np);
+        g.rev_pair = gtake(pbk, np);
         uint32_t *pair_src = (uint32_t *)salloc(ctx, (size_t)(np ? np : 1) * 4);
         if (!g.pair_off || !g.pair_dst || !g.rev_pair || !pair_src) return TM_E_NOMEM;
         launch(ctx, k_pair_fill, blocks_for(m, TB), TB, key, tmp, g.multi_gid, head, pid, m, g.pair_off, pair_src,
@@ -551,9 +578,11 @@ int build_csr(tm_ctx *ctx)
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "pair tables");
         if (rc) return rc;
     } else {
-        g.pair_off = galloc(ctx, 1);
-        g.pair_dst = galloc(ctx, 1);
-        g.rev_pair = galloc(ctx, 1);
+        GraphBlock pbk;
+        if (!gblock_open(ctx, pbk, 3 * 256)) return TM_E_NOMEM;
+        g.pair_off = gtake(pbk, 1);
+        g.pair_dst = gtake(pbk, 1);
+        g.rev_pair = gtake(pbk, 1);
         cudaMemsetAsync(g.pair_off, 0, 4, st);
         launch(ctx, k_offsets, 1, TB, key, 0, n, g.vpair_off);
     }

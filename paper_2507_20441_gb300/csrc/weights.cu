@@ -273,31 +273,58 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     const int64_t d = P.delta;
     int rc = TM_OK;
     cudaMemsetAsync(ctx->status, 0, 4, st);
-    // ---- windows of each layer (K2)
-    for (int p = 0; p < 2; ++p) {
+    // ---- windows of each layer (K2): count both layers, then one block for
+    // everything the motif keeps (windows, root CDF, prefix arrays, totals)
+    uint32_t *flag[2], *pos[2], *dcount;
+    uint32_t nwh[2] = {0, 0};
+    {
         PhaseScope ph(ctx, TM_PH_WINDOWS);
-        LayerData &L = mo->layer[p];
-        uint32_t *flag = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);
-        uint32_t *pos = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);
-        uint32_t *dcount = (uint32_t *)salloc(ctx, 4);
-        if (!flag || !pos || !dcount) return TM_E_NOMEM;
-        uint32_t nw = 0;
-        if (m) {
-            launch(ctx, k_window_heads, blocks_for(m, TB), TB, g.g_t, m, p, d, flag);
-            rc = exclusive_scan_u32(ctx, flag, pos, m, dcount);
-            if (rc) return rc;
-            copy_d2h(ctx, &nw, dcount, 4);
-            rc = check_cuda(ctx, cudaStreamSynchronize(st), "window count");
-            if (rc) return rc;
+        dcount = (uint32_t *)salloc(ctx, 8);
+        if (!dcount) return TM_E_NOMEM;
+        cudaMemsetAsync(dcount, 0, 8, st);
+        for (int p = 0; p < 2; ++p) {
+            flag[p] = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);
+            pos[p] = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);
+            if (!flag[p] || !pos[p]) return TM_E_NOMEM;
+            if (m) {
+                launch(ctx, k_window_heads, blocks_for(m, TB), TB, g.g_t, m, p, d, flag[p]);
+                rc = exclusive_scan_u32(ctx, flag[p], pos[p], m, dcount + p);
+                if (rc) return rc;
+            }
         }
-        L.nwin = nw;
-        L.win_beg = (uint32_t *)malloc_motif(ctx, mo, ((size_t)nw + 1) * 4);
-        L.win_id = (uint32_t *)malloc_motif(ctx, mo, ((size_t)nw + 1) * 4);
-        if (!L.win_beg || !L.win_id) return TM_E_NOMEM;
-        if (m) launch(ctx, k_window_fill, blocks_for(m, TB), TB, g.g_t, flag, pos, m, p, d, L.win_beg, L.win_id);
-        copy_h2d(ctx, L.win_beg + nw, &g.m, 4);
-        rc = check_cuda(ctx, cudaStreamSynchronize(st), "window fill");
+        copy_d2h(ctx, nwh, dcount, 8);
+        rc = check_cuda(ctx, cudaStreamSynchronize(st), "window count");
         if (rc) return rc;
+    }
+    {
+        auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+        const size_t mm = (size_t)(m ? m : 1);
+        size_t total = al(((size_t)nwh[0] + 1) * 4) * 2 + al(((size_t)nwh[1] + 1) * 4) * 2 + 2 * al(mm * 8) +
+                       (size_t)P.nslots * 4 * al(mm * 8) + al(((size_t)nwh[0] + nwh[1] + 1) * 16);
+        char *blk = (char *)malloc_motif(ctx, mo, total);
+        if (!blk) return TM_E_NOMEM;
+        size_t off = 0;
+        auto take = [&](size_t bytes) { char *q = blk + off; off += al(bytes); return (void *)q; };
+        for (int p = 0; p < 2; ++p) {
+            LayerData &L = mo->layer[p];
+            L.nwin = nwh[p];
+            L.win_beg = (uint32_t *)take(((size_t)nwh[p] + 1) * 4);
+            L.win_id = (uint32_t *)take(((size_t)nwh[p] + 1) * 4);
+            L.root_cdf = (uint64_t *)take(mm * 8);
+            for (int sl = 0; sl < P.nslots; ++sl) {
+                L.pref_dir[sl] = (uint64_t *)take(mm * 8);
+                L.pref_multi[sl] = (uint64_t *)take(mm * 8);
+            }
+        }
+        mo->wcum = (uint64_t *)take(((size_t)nwh[0] + nwh[1] + 1) * 16);
+    }
+    {
+        PhaseScope ph(ctx, TM_PH_WINDOWS);
+        for (int p = 0; p < 2; ++p) {
+            LayerData &L = mo->layer[p];
+            if (m) launch(ctx, k_window_fill, blocks_for(m, TB), TB, g.g_t, flag[p], pos[p], m, p, d, L.win_beg, L.win_id);
+            copy_h2d(ctx, L.win_beg + L.nwin, &g.m, 4);
+        }
     }
     // ---- DP over tree nodes in increasing height (K3) + prefixes (K4)
     OwnerBits ob;
@@ -326,8 +353,6 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
             PhaseScope ph(ctx, TM_PH_ROOT);
             for (int p = 0; p < 2; ++p) {
                 LayerData &L = mo->layer[p];
-                L.root_cdf = (uint64_t *)malloc_motif(ctx, mo, (size_t)(m ? m : 1) * 8);
-                if (!L.root_cdf) return TM_E_NOMEM;
                 RootScan f{w[p], g.g_t, p, d};
                 rc = segmented_scan_u64(ctx, f, m, L.root_cdf);
                 if (rc) return rc;
@@ -338,9 +363,6 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
             bool out = P.tout[q] != 0;
             for (int p = 0; p < 2; ++p) {
                 LayerData &L = mo->layer[p];
-                L.pref_dir[slot] = (uint64_t *)malloc_motif(ctx, mo, (size_t)(m ? m : 1) * 8);
-                L.pref_multi[slot] = (uint64_t *)malloc_motif(ctx, mo, (size_t)(m ? m : 1) * 8);
-                if (!L.pref_dir[slot] || !L.pref_multi[slot]) return TM_E_NOMEM;
                 DirScan fd{w[p], out ? g.out_gid : g.in_gid, out ? g.out_t : g.in_t, out ? ob.out : ob.in, p, d};
                 rc = segmented_scan_u64(ctx, fd, m, L.pref_dir[slot]);
                 if (rc) return rc;
@@ -356,8 +378,6 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     // ---- window totals and their 128-bit running sum (K5)
     uint32_t nw0 = mo->layer[0].nwin, nw1 = mo->layer[1].nwin;
     mo->nwtot = nw0 + nw1;
-    mo->wcum = (uint64_t *)malloc_motif(ctx, mo, ((size_t)mo->nwtot + 1) * 16);
-    if (!mo->wcum) return TM_E_NOMEM;
     uint64_t Wh[2] = {0, 0};
     {
         PhaseScope ph(ctx, TM_PH_ROOT);
