@@ -55,11 +55,17 @@ __global__ void __launch_bounds__(OS_THREADS) k_rs_count(const uint32_t *__restr
     __syncthreads();
     const uint32_t lt = (1u << (threadIdx.x & 31)) - 1u;
     const uint32_t base = blockIdx.x * OS_TILE;
-#pragma unroll 4
+    uint32_t kv[OS_ITEMS];
+#pragma unroll
+    for (int j = 0; j < OS_ITEMS; ++j) {   // all loads in flight before any vote
+        const uint32_t i = base + j * OS_THREADS + threadIdx.x;
+        kv[j] = i < n ? __ldg(kin + i) : 0u;
+    }
+#pragma unroll
     for (int j = 0; j < OS_ITEMS; ++j) {
         const uint32_t i = base + j * OS_THREADS + threadIdx.x;
         const bool valid = i < n;
-        const uint32_t d = valid ? ((__ldg(kin + i) >> shift) & dmask) : radix;
+        const uint32_t d = valid ? ((kv[j] >> shift) & dmask) : radix;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         if (valid && (peers & lt) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
     }
@@ -122,12 +128,18 @@ __global__ void __launch_bounds__(OS_THREADS) k_rs_scatter(const uint32_t *__res
     const uint32_t lt = (1u << lane) - 1u;
     // ---- rank inside each warp's chunk (order: warp, item, lane)
     uint16_t *wc = s_wcnt + warp * OS_MAXRADIX;
-#pragma unroll 4
+    uint32_t kv[OS_ITEMS];
+#pragma unroll
+    for (int j = 0; j < OS_ITEMS; ++j) {   // all loads in flight before any vote
+        const uint32_t i = base + warp * OS_WCHUNK + j * 32 + lane;
+        kv[j] = i < n ? __ldg(kin + i) : 0u;
+    }
+#pragma unroll
     for (int j = 0; j < OS_ITEMS; ++j) {
         const uint32_t li = warp * OS_WCHUNK + j * 32 + lane;
         const uint32_t i = base + li;
         const bool valid = i < n;
-        const uint32_t d = valid ? ((__ldg(kin + i) >> shift) & dmask) : radix;
+        const uint32_t d = valid ? ((kv[j] >> shift) & dmask) : radix;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         uint32_t cur = valid ? wc[d] : 0;
         __syncwarp();
@@ -152,17 +164,20 @@ __global__ void __launch_bounds__(OS_THREADS) k_rs_scatter(const uint32_t *__res
     __syncthreads();
     os_block_scan512(s_tex, s_wt);
     // ---- place keys (and payloads) in digit order inside shared memory
-#pragma unroll 4
+#pragma unroll
     for (int j = 0; j < OS_ITEMS; ++j) {
         const uint32_t li = warp * OS_WCHUNK + j * 32 + lane;
         const uint32_t i = base + li;
+        uint32_t a = 0, b = 0;
+        if (NP >= 1 && i < n) a = __ldg(p0in + i);
+        if (NP >= 2 && i < n) b = __ldg(p1in + i);
         if (i < n) {
-            const uint32_t k = __ldg(kin + i);
+            const uint32_t k = kv[j];
             const uint32_t d = (k >> shift) & dmask;
             const uint32_t pos = s_tex[d] + s_wcnt[warp * OS_MAXRADIX + d] + s_rank[li];
             s_key[pos] = k;
-            if (NP >= 1) s_p0[pos] = __ldg(p0in + i);
-            if (NP >= 2) s_p1[pos] = __ldg(p1in + i);
+            if (NP >= 1) s_p0[pos] = a;
+            if (NP >= 2) s_p1[pos] = b;
         }
     }
     __syncthreads();
