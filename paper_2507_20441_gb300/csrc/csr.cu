@@ -504,7 +504,7 @@ int build_csr(tm_ctx *ctx)
         {
             // every m- and n-sized array of the graph in one block
             const size_t mf = (size_t)(m - ndup), a_m = align256((mf ? mf : 1) * 4), a_n = align256(((size_t)n + 1) * 4);
-            if (!gblock_open(ctx, gb, 13 * a_m + 3 * a_n)) return TM_E_NOMEM;
+            if (!gblock_open(ctx, gb, 17 * a_m + 3 * a_n)) return TM_E_NOMEM;
         }
         g.g_t = gtake(gb, m - ndup); g.g_src = gtake(gb, m - ndup); g.g_dst = gtake(gb, m - ndup);
         if (!g.g_t || !g.g_src || !g.g_dst) return TM_E_NOMEM;
@@ -531,7 +531,9 @@ int build_csr(tm_ctx *ctx)
     sec.reset(new PhaseScope(ctx, TM_PH_CSR_OUT));
     g.out_gid = gtake(gb, m); g.out_t = gtake(gb, m); g.out_nbr = gtake(gb, m); g.out_off = gtake(gb, (size_t)n + 1);
     g.in_gid = gtake(gb, m); g.in_t = gtake(gb, m); g.in_nbr = gtake(gb, m); g.in_off = gtake(gb, (size_t)n + 1);
-    if (!g.out_gid || !g.out_t || !g.out_nbr || !g.out_off || !g.in_gid || !g.in_t || !g.in_nbr || !g.in_off)
+    g.out_src = gtake(gb, m); g.out_pair = gtake(gb, m); g.in_dst = gtake(gb, m); g.in_pair = gtake(gb, m);
+    if (!g.out_gid || !g.out_t || !g.out_nbr || !g.out_off || !g.in_gid || !g.in_t || !g.in_nbr || !g.in_off ||
+        !g.out_src || !g.out_pair || !g.in_dst || !g.in_pair)
         return TM_E_NOMEM;
     if (m) {
         cudaMemcpyAsync(key, g.g_src, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
@@ -539,6 +541,7 @@ int build_csr(tm_ctx *ctx)
         rc = radix_sort(ctx, key, g.out_gid, nullptr, m, vbits);
         if (rc) return rc;
         launch(ctx, k_gather2, blocks_for(m, TB), TB, g.out_gid, m, g.g_t, g.g_dst, g.out_t, g.out_nbr);
+        cudaMemcpyAsync(g.out_src, key, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
     }
     launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, key, m, n, g.out_off);
     // ---- IN order: stable sort of gid by dst
@@ -550,6 +553,7 @@ int build_csr(tm_ctx *ctx)
         rc = radix_sort(ctx, key, g.in_gid, nullptr, m, vbits);
         if (rc) return rc;
         launch(ctx, k_gather2, blocks_for(m, TB), TB, g.in_gid, m, g.g_t, g.g_src, g.in_t, g.in_nbr);
+        cudaMemcpyAsync(g.in_dst, key, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
     }
     launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, key, m, n, g.in_off);
     // ---- multi-edge order: stable re-sort of the IN order by source
@@ -590,6 +594,11 @@ int build_csr(tm_ctx *ctx)
         copy_h2d(ctx, g.pair_off + np, &m, 4);
         launch(ctx, k_offsets, blocks_for((uint64_t)np + 1, TB), TB, pair_src, np, n, g.vpair_off);
         launch(ctx, k_rev_pairs, blocks_for(np, TB), TB, pair_src, g.pair_dst, g.vpair_off, np, g.rev_pair);
+        // pair id of every out-/in-list position (the weight pass walks those lists)
+        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.out_gid, m, g.g_pair, (const uint32_t *)nullptr, g.out_pair,
+               (uint32_t *)nullptr);
+        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.in_gid, m, g.g_pair, (const uint32_t *)nullptr, g.in_pair,
+               (uint32_t *)nullptr);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "pair tables");
         if (rc) return rc;
     } else {

@@ -37,10 +37,12 @@ struct DevGraph {
     uint32_t T = 0;                      // max t'
     // GLOBAL order
     uint32_t *g_t = nullptr, *g_src = nullptr, *g_dst = nullptr, *g_pair = nullptr;
-    // out-lists: per vertex, (t', dst) order
+    // out-lists: per vertex, (t', dst) order; owner (src) and pair id per position
     uint32_t *out_off = nullptr, *out_t = nullptr, *out_nbr = nullptr, *out_gid = nullptr;
-    // in-lists: per vertex, (t', src) order
+    uint32_t *out_src = nullptr, *out_pair = nullptr;
+    // in-lists: per vertex, (t', src) order; owner (dst) and pair id per position
     uint32_t *in_off = nullptr, *in_t = nullptr, *in_nbr = nullptr, *in_gid = nullptr;
+    uint32_t *in_dst = nullptr, *in_pair = nullptr;
     // multi-edge lists: pairs sorted by (src, dst); entries in t' order
     uint32_t *vpair_off = nullptr;       // [n+1] first pair of each source vertex
     uint32_t *pair_dst = nullptr;        // [P]

@@ -32,80 +32,126 @@ struct ChildPrefix {
     const uint64_t *pm[2][kMaxTree];   // [layer][slot] prefix in the multi-edge order
 };
 
-// Sum of child weights over the candidate list L (Claim 3.1) for one child.
-// zg/og: images of the meeting vertex and of the parent's other endpoint;
-// own_pair/rev: multi-edge list ids of the parent edge and of its reverse.
-__device__ __forceinline__ uint64_t child_sum(const DevGraph &g, const ChildPrefix &cp, int p, int slot, bool leaf,
-                                              bool out, uint32_t zg, uint32_t pe, uint64_t lo, uint64_t hi,
-                                              uint64_t wlo)
+// Warp-narrowed lower bound: the first index in [beg, end) with tarr >= key.
+// When every lane of the warp walks the same vertex's list with keys that do
+// not decrease from lane to lane (`same`), only the first and last active
+// lanes search the whole list; every other lane's answer lies between theirs,
+// so it searches that short, cache-hot stretch only.
+__device__ __forceinline__ uint32_t warp_lower(const uint32_t *tarr, uint32_t beg, uint32_t end, uint64_t key,
+                                               bool active, bool same)
 {
-    const uint32_t *off = out ? g.out_off : g.in_off;
-    const uint32_t *tarr = out ? g.out_t : g.in_t;
-    uint32_t beg = __ldg(off + zg), end = __ldg(off + zg + 1);
-    uint32_t a = lower_idx(tarr, beg, end, lo);
-    uint32_t b = gallop_idx(tarr, a, end, hi + 1);
-    uint32_t ea = 0, eb = 0, pb = 0;
-    if (pe != kNone) {
-        pb = __ldg(g.pair_off + pe);
-        uint32_t pend = __ldg(g.pair_off + pe + 1);
-        ea = lower_idx(g.multi_t, pb, pend, lo);
-        eb = gallop_idx(g.multi_t, ea, pend, hi + 1);
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    if (same && act) {
+        const int lane = threadIdx.x & 31, f = __ffs(act) - 1, l = 31 - __clz(act);
+        uint32_t edge = 0;
+        if (lane == f || lane == l) edge = lower_idx(tarr, beg, end, key);
+        const uint32_t lo = __shfl_sync(0xffffffffu, edge, f), hi = __shfl_sync(0xffffffffu, edge, l);
+        return active ? lower_idx(tarr, lo, hi, key) : 0;
     }
-    if (leaf) return (uint64_t)(b - a) - (uint64_t)(eb - ea);
-    const uint64_t *P = cp.pd[p][slot];
-    const uint64_t *PM = cp.pm[p][slot];
-    uint64_t sr = 0, se = 0;
-    if (b > a) {
-        uint64_t base = (a > beg && (uint64_t)__ldg(tarr + a - 1) >= wlo) ? __ldg(P + a - 1) : 0;
-        sr = __ldg(P + b - 1) - base;
-    }
-    if (eb > ea) {
-        uint64_t base = (ea > pb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo) ? __ldg(PM + ea - 1) : 0;
-        se = __ldg(PM + eb - 1) - base;
-    }
-    return sr - se;
+    return active ? lower_idx(tarr, beg, end, key) : 0;
 }
 
-// w_{q,e} for every edge e (gid) and both layers (Claim 3.2).
-__global__ void k_dp(DevGraph g, DevPlan P, int q, ChildPrefix cp, uint64_t *__restrict__ w0,
-                     uint64_t *__restrict__ w1, uint32_t *status)
+// One side of tree node q: the product of the factors of q's children that
+// meet q at its tail (side 0) or head (side 1), for every edge e matched to q
+// and both layers (Claim 3.2).  Threads walk the meeting vertex's own list
+// (out-list order for side 0, in-list order for side 1), so neighbouring
+// lanes share the vertex and its candidate lists and have non-decreasing
+// times.  A node with children on both sides (the root) runs side 0 with
+// first = 1 and side 1 with last = 1; the partial product and a pending
+// overflow bit carry between the passes, so the result and the overflow rule
+// (a factor >= 2^64, or an exact product >= 2^64 with no zero factor) are
+// those of the whole product.
+__global__ void __launch_bounds__(256) k_dp_side(DevGraph g, DevPlan P, int q, int side, int first, int last,
+                                                 ChildPrefix cp, uint64_t *__restrict__ w0, uint64_t *__restrict__ w1,
+                                                 uint8_t *__restrict__ pend, uint32_t *status)
 {
-    uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= g.m) return;
-    const uint32_t t = __ldg(g.g_t + e), u = __ldg(g.g_src + e), v = __ldg(g.g_dst + e);
-    const uint32_t pr = __ldg(g.g_pair + e);
+    const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = pos < g.m;
+    const uint32_t ps = valid ? pos : g.m - 1;
+    const uint32_t e = __ldg((side ? g.in_gid : g.out_gid) + ps);
+    const uint32_t t = __ldg((side ? g.in_t : g.out_t) + ps);
+    const uint32_t zg = __ldg((side ? g.in_dst : g.out_src) + ps);
+    const uint32_t og = __ldg((side ? g.in_nbr : g.out_nbr) + ps);
+    const uint32_t pr = __ldg((side ? g.in_pair : g.out_pair) + ps);
     const uint32_t rv = __ldg(g.rev_pair + pr);
+    // the warp shares one vertex (times then never decrease from lane to lane)
+    const uint32_t z0 = __shfl_sync(0xffffffffu, zg, 0);
+    const bool same = __all_sync(0xffffffffu, valid && zg == z0);
     const int64_t d = P.delta;
     bool ovf_any = false;
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
-        int64_t wi = layer_window(t, p, d);
-        uint64_t w = 0;
-        if (wi >= 0) {
-            const uint64_t wlo = (uint64_t)(wi * d), whi = (uint64_t)((wi + 2) * d - 1);
-            uint64_t prod = 1;
-            bool zero = false, ovf = false;
-            for (int ci = 0; ci < P.nchild[q]; ++ci) {
-                const int c = P.child[q][ci];
-                const bool zs = P.tzside[c] != 0, out = P.tout[c] != 0;
-                const uint32_t zg = zs ? v : u;
-                uint64_t lo, hi;
-                if (P.tlater[c]) { lo = (uint64_t)t + 1; hi = (uint64_t)t + (uint64_t)d; }
-                else { lo = (uint64_t)t >= (uint64_t)d ? (uint64_t)t - (uint64_t)d : 0; hi = (uint64_t)t - 1; }
-                if (!P.tlater[c] && t == 0) { zero = true; continue; }
-                lo = lo < wlo ? wlo : lo;
-                hi = hi > whi ? whi : hi;
-                if (lo > hi) { zero = true; continue; }
-                // excluded multi-edge list: El(z -> o) for an out-child, El(o -> z) for an in-child
-                const uint32_t pe = (out == !zs) ? pr : rv;
-                uint64_t s = child_sum(g, cp, p, P.tslot[c], P.tleaf[c] != 0, out, zg, pe, lo, hi, wlo);
-                if (s == 0) zero = true;
-                else prod = mul_chk(prod, s, ovf);
-            }
-            if (zero) w = 0;
-            else { w = prod; ovf_any |= ovf; }
+        const int64_t wi = layer_window(t, p, d);
+        const bool inwin = valid && wi >= 0;
+        const uint64_t wlo = inwin ? (uint64_t)(wi * d) : 0, whi = inwin ? (uint64_t)((wi + 2) * d - 1) : 0;
+        uint64_t prod = 1;
+        bool zero = !inwin, ovf = false;
+        uint64_t *W = p == 0 ? w0 : w1;
+        if (!first && inwin) {
+            prod = W[e];
+            ovf = (pend[(size_t)p * g.m + e] != 0);
+            if (prod == 0) zero = true;
         }
-        (p == 0 ? w0 : w1)[e] = w;
+        for (int ci = 0; ci < P.nchild[q]; ++ci) {
+            const int c = P.child[q][ci];
+            if (P.tzside[c] != side) continue;
+            const bool out = P.tout[c] != 0;
+            uint64_t lo, hi;
+            if (P.tlater[c]) { lo = (uint64_t)t + 1; hi = (uint64_t)t + (uint64_t)d; }
+            else { lo = (uint64_t)t >= (uint64_t)d ? (uint64_t)t - (uint64_t)d : 0; hi = t ? (uint64_t)t - 1 : 0; }
+            lo = lo < wlo ? wlo : lo;
+            hi = hi > whi ? whi : hi;
+            const bool act = inwin && !(!P.tlater[c] && t == 0);
+            const uint32_t *off = out ? g.out_off : g.in_off;
+            const uint32_t *tarr = out ? g.out_t : g.in_t;
+            const uint32_t beg = __ldg(off + zg), end = __ldg(off + zg + 1);
+            const uint32_t a = warp_lower(tarr, beg, end, lo, act, same);
+            const uint32_t b = warp_lower(tarr, beg, end, hi + 1, act, same);
+            if (!act || lo > hi) { zero = true; continue; }
+            // excluded multi-edge list: El(z -> o) for an out-child, El(o -> z) for an in-child
+            const uint32_t pe = (out == (side == 0)) ? pr : rv;
+            uint32_t ea = 0, eb = 0, pb = 0;
+            if (pe != kNone) {
+                pb = __ldg(g.pair_off + pe);
+                const uint32_t pend_ = __ldg(g.pair_off + pe + 1);
+                ea = lower_idx(g.multi_t, pb, pend_, lo);
+                eb = gallop_idx(g.multi_t, ea, pend_, hi + 1);
+            }
+            uint64_t sum;
+            if (P.tleaf[c]) {
+                sum = (uint64_t)(b - a) - (uint64_t)(eb - ea);
+            } else {
+                const uint64_t *Pd = cp.pd[p][P.tslot[c]];
+                const uint64_t *Pm = cp.pm[p][P.tslot[c]];
+                uint64_t sr = 0, se = 0;
+                if (b > a) {
+                    const uint64_t base = (a > beg && (uint64_t)__ldg(tarr + a - 1) >= wlo) ? __ldg(Pd + a - 1) : 0;
+                    sr = __ldg(Pd + b - 1) - base;
+                }
+                if (eb > ea) {
+                    const uint64_t base = (ea > pb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo) ? __ldg(Pm + ea - 1) : 0;
+                    se = __ldg(Pm + eb - 1) - base;
+                }
+                sum = sr - se;
+            }
+            if (sum == 0) zero = true;
+            else prod = mul_chk(prod, sum, ovf);
+        }
+        if (!valid) continue;
+        if (!inwin) {
+            W[e] = 0;
+            continue;
+        }
+        if (zero) {
+            W[e] = 0;
+            if (!last) pend[(size_t)p * g.m + e] = 0;
+        } else if (last) {
+            W[e] = prod;
+            ovf_any |= ovf;
+        } else {
+            W[e] = prod;
+            pend[(size_t)p * g.m + e] = ovf ? 1 : 0;
+        }
     }
     if (ovf_any) latch(status, ST_OVERFLOW);
 }
@@ -335,6 +381,7 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     w[1] = (uint64_t *)salloc(ctx, (size_t)(m ? m : 1) * 8);
     if (!w[0] || !w[1]) return TM_E_NOMEM;
     ChildPrefix cp{};
+    uint8_t *pend = nullptr;
     int maxh = 0;
     for (int q = 0; q < P.ntree; ++q) maxh = std::max(maxh, (int)P.height[q]);
     std::vector<int> order;
@@ -345,7 +392,22 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     for (int q : order) {
         {
             PhaseScope ph(ctx, TM_PH_DP);
-            if (m) { launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, q, cp, w[0], w[1], ctx->status); }
+            bool has[2] = {false, false};
+            for (int ci = 0; ci < P.nchild[q]; ++ci) has[P.tzside[P.child[q][ci]]] = true;
+            if (!has[0] && !has[1]) has[0] = true;   // a leaf root (single-edge motif): weight 1 per window
+            if (m) {
+                const bool two = has[0] && has[1];
+                if (two && !pend) {
+                    pend = (uint8_t *)salloc(ctx, 2 * (size_t)m);
+                    if (!pend) return TM_E_NOMEM;
+                }
+                if (has[0])
+                    launch(ctx, k_dp_side, blocks_for(m, TB), TB, g, P, q, 0, 1, two ? 0 : 1, cp, w[0], w[1], pend,
+                           ctx->status);
+                if (has[1])
+                    launch(ctx, k_dp_side, blocks_for(m, TB), TB, g, P, q, 1, two ? 0 : 1, 1, cp, w[0], w[1], pend,
+                           ctx->status);
+            }
         }
         rc = check_cuda(ctx, cudaGetLastError(), "weight DP");
         if (rc) return rc;
