@@ -395,6 +395,24 @@ __global__ void k_rev_pairs(const uint32_t *__restrict__ pair_src, const uint32_
     rev[p] = (r < hi && pair_dst[r] == u) ? r : kNone;
 }
 
+// where each list time falls in the same vertex's other list
+__global__ void k_cross_rank(const uint32_t *__restrict__ own_t, const uint32_t *__restrict__ owner, uint32_t m,
+                             const uint32_t *__restrict__ other_off, const uint32_t *__restrict__ other_t,
+                             uint32_t *__restrict__ xrank)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const uint32_t z = owner[i];
+    xrank[i] = lower_idx(other_t, other_off[z], other_off[z + 1], own_t[i]);
+}
+
+// inverse of a position -> edge-id permutation
+__global__ void k_inverse(const uint32_t *__restrict__ gid, uint32_t m, uint32_t *__restrict__ pos)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) pos[gid[i]] = i;
+}
+
 inline unsigned blocks_for(uint64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 }  // namespace
@@ -504,7 +522,7 @@ int build_csr(tm_ctx *ctx)
         {
             // every m- and n-sized array of the graph in one block
             const size_t mf = (size_t)(m - ndup), a_m = align256((mf ? mf : 1) * 4), a_n = align256(((size_t)n + 1) * 4);
-            if (!gblock_open(ctx, gb, 17 * a_m + 3 * a_n)) return TM_E_NOMEM;
+            if (!gblock_open(ctx, gb, 21 * a_m + 3 * a_n)) return TM_E_NOMEM;
         }
         g.g_t = gtake(gb, m - ndup); g.g_src = gtake(gb, m - ndup); g.g_dst = gtake(gb, m - ndup);
         if (!g.g_t || !g.g_src || !g.g_dst) return TM_E_NOMEM;
@@ -532,8 +550,9 @@ int build_csr(tm_ctx *ctx)
     g.out_gid = gtake(gb, m); g.out_t = gtake(gb, m); g.out_nbr = gtake(gb, m); g.out_off = gtake(gb, (size_t)n + 1);
     g.in_gid = gtake(gb, m); g.in_t = gtake(gb, m); g.in_nbr = gtake(gb, m); g.in_off = gtake(gb, (size_t)n + 1);
     g.out_src = gtake(gb, m); g.out_pair = gtake(gb, m); g.in_dst = gtake(gb, m); g.in_pair = gtake(gb, m);
+    g.out_xrank = gtake(gb, m); g.in_xrank = gtake(gb, m); g.out_pos = gtake(gb, m); g.in_pos = gtake(gb, m);
     if (!g.out_gid || !g.out_t || !g.out_nbr || !g.out_off || !g.in_gid || !g.in_t || !g.in_nbr || !g.in_off ||
-        !g.out_src || !g.out_pair || !g.in_dst || !g.in_pair)
+        !g.out_src || !g.out_pair || !g.in_dst || !g.in_pair || !g.out_xrank || !g.in_xrank || !g.out_pos || !g.in_pos)
         return TM_E_NOMEM;
     if (m) {
         cudaMemcpyAsync(key, g.g_src, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
@@ -599,6 +618,11 @@ int build_csr(tm_ctx *ctx)
                (uint32_t *)nullptr);
         launch(ctx, k_gather2, blocks_for(m, TB), TB, g.in_gid, m, g.g_pair, (const uint32_t *)nullptr, g.in_pair,
                (uint32_t *)nullptr);
+        // cross ranks between a vertex's out- and in-lists, and list positions by edge id
+        launch(ctx, k_cross_rank, blocks_for(m, TB), TB, g.out_t, g.out_src, m, g.in_off, g.in_t, g.out_xrank);
+        launch(ctx, k_cross_rank, blocks_for(m, TB), TB, g.in_t, g.in_dst, m, g.out_off, g.out_t, g.in_xrank);
+        launch(ctx, k_inverse, blocks_for(m, TB), TB, g.out_gid, m, g.out_pos);
+        launch(ctx, k_inverse, blocks_for(m, TB), TB, g.in_gid, m, g.in_pos);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "pair tables");
         if (rc) return rc;
     } else {

@@ -241,13 +241,14 @@ __device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &
         }
         tlo = tlo < wlo ? wlo : tlo;
         thi = thi > whi ? whi : thi;
-        const uint32_t *off = out ? g.out_off : g.in_off;
-        const uint32_t *tarr = out ? g.out_t : g.in_t;
         const uint32_t *nbr = out ? g.out_nbr : g.in_nbr;
         const uint32_t *gids = out ? g.out_gid : g.in_gid;
-        const uint32_t beg = __ldg(off + zg), endv = __ldg(off + zg + 1);
-        const uint32_t a = lower_idx(tarr, beg, endv, tlo);
-        const uint32_t b = gallop_idx(tarr, a, endv, thi + 1);
+        // the parent edge's position in the meeting vertex's out-list (z is its
+        // source) or in-list (z is its destination)
+        const uint32_t ppos = __ldg((zs ? g.in_pos : g.out_pos) + R.gid(pq));
+        uint32_t a, b, beg;
+        const uint32_t *tarr;
+        child_range(g, zs ? 1 : 0, out, zg, ppos, pt, P.tlater[q] != 0, tlo, thi, a, b, beg, tarr);
         const uint32_t pe = (out == !zs) ? ppair : __ldg(g.rev_pair + ppair);
         uint32_t ea = 0, eb = 0, pb = 0;
         if (pe != kNone) {

@@ -164,28 +164,52 @@ __global__ void k_segscan_reduce(F f, uint64_t n, SegAgg *__restrict__ aggs, uin
 }
 
 // Turn tile aggregates into per-tile carry-ins (exclusive, segmented), in
-// place.  One block; each thread owns a contiguous chunk of tiles.
+// place.  One block of 1024 threads; each thread owns a contiguous chunk of
+// tiles, and the chunk totals are combined by a warp-shuffle scan.
+__device__ __forceinline__ SegAgg seg_shfl_up(SegAgg a, int o)
+{
+    SegAgg y;
+    y.v = __shfl_up_sync(0xffffffffu, a.v, o);
+    y.f = __shfl_up_sync(0xffffffffu, a.f, o);
+    y.pad = 0;
+    return y;
+}
+
 __global__ void k_segscan_carries(SegAgg *__restrict__ aggs, uint64_t ntiles, uint32_t *status)
 {
-    __shared__ SegAgg chunk[1024];
+    __shared__ SegAgg warp_tot[32];
     bool ovf = false;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t per = (ntiles + blockDim.x - 1) / blockDim.x;
     uint64_t lo = (uint64_t)threadIdx.x * per, hi = lo + per;
     if (hi > ntiles) hi = ntiles;
+    if (lo > ntiles) lo = ntiles;
     SegAgg a{0, 0, 0};
     for (uint64_t i = lo; i < hi; ++i) a = seg_combine(a, aggs[i], ovf);
-    chunk[threadIdx.x] = a;
+    // inclusive scan of chunk totals inside the warp, then across warps
+    SegAgg incl = a;
+    for (int o = 1; o < 32; o <<= 1) {
+        SegAgg y = seg_shfl_up(incl, o);
+        if (lane >= o) incl = seg_combine(y, incl, ovf);
+    }
+    if (lane == 31) warp_tot[warp] = incl;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        SegAgg run{0, 0, 0};
-        for (unsigned t = 0; t < blockDim.x; ++t) {
-            SegAgg c = chunk[t];
-            chunk[t] = run;
-            run = seg_combine(run, c, ovf);
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) / 32;
+        SegAgg w = lane < nw ? warp_tot[lane] : SegAgg{0, 0, 0};
+        SegAgg wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            SegAgg y = seg_shfl_up(wi, o);
+            if (lane >= o) wi = seg_combine(y, wi, ovf);
         }
+        SegAgg ex = seg_shfl_up(wi, 1);
+        if (lane == 0) ex = SegAgg{0, 0, 0};
+        if (lane < nw) warp_tot[lane] = ex;
     }
     __syncthreads();
-    SegAgg run = chunk[threadIdx.x];
+    SegAgg ex_lane = seg_shfl_up(incl, 1);
+    SegAgg run = warp_tot[warp];
+    if (lane > 0) run = seg_combine(run, ex_lane, ovf);
     for (uint64_t i = lo; i < hi; ++i) {
         SegAgg c = aggs[i];
         aggs[i] = run;

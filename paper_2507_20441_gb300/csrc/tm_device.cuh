@@ -105,6 +105,47 @@ __device__ __forceinline__ uint32_t gallop_idx(const uint32_t *__restrict__ a, u
     return lower_idx(a, lo, probe, x);
 }
 
+// First index in [beg, base] with a[i] >= x, when every index >= base is
+// known to hold a value >= x: searches backward from base (1, 2, 4, ...).
+__device__ __forceinline__ uint32_t gallop_back(const uint32_t *__restrict__ a, uint32_t beg, uint32_t base, uint64_t x)
+{
+    uint32_t hi = base, step = 1;
+    while (hi > beg) {
+        const uint32_t probe = (hi - beg > step) ? hi - step : beg;
+        if ((uint64_t)__ldg(a + probe) < x) return lower_idx(a, probe + 1, hi, x);
+        hi = probe;
+        step = step < 0x40000000u ? step << 1 : step;
+    }
+    return beg;
+}
+
+// Candidate range [a, b) of a child edge at vertex z (Claim 3.1): the entries
+// of z's out-list (out_c) or in-list with times in [lo, hi], found from the
+// parent edge's own position `pos` in z's out-list (side 0) or in-list
+// (side 1) and its time t.  The first entry with time >= t is reached from
+// `pos` (same list) or from the precomputed cross rank (other list); the
+// bounds are then galloped to from there.  A later child has lo > t, an
+// earlier one hi = t - 1.
+__device__ __forceinline__ void child_range(const DevGraph &g, int side, bool out_c, uint32_t z, uint32_t pos,
+                                            uint32_t t, bool later, uint64_t lo, uint64_t hi, uint32_t &a,
+                                            uint32_t &b, uint32_t &beg, const uint32_t *&tarr)
+{
+    const uint32_t *off = out_c ? g.out_off : g.in_off;
+    tarr = out_c ? g.out_t : g.in_t;
+    beg = __ldg(off + z);
+    const uint32_t end = __ldg(off + z + 1);
+    uint32_t base;
+    if ((side == 0) == out_c) base = gallop_back(tarr, beg, pos, t);
+    else base = __ldg((side == 0 ? g.out_xrank : g.in_xrank) + pos);
+    if (later) {
+        a = gallop_idx(tarr, base, end, lo);
+        b = gallop_idx(tarr, a, end, hi + 1);
+    } else {
+        b = base;
+        a = gallop_back(tarr, beg, base, lo);
+    }
+}
+
 // First index in [lo, hi) with v[i] > x (v non-decreasing).
 __device__ __forceinline__ uint32_t upper_idx64(const uint64_t *__restrict__ v, uint32_t lo, uint32_t hi, uint64_t x)
 {

@@ -40,9 +40,13 @@ struct DevGraph {
     // out-lists: per vertex, (t', dst) order; owner (src) and pair id per position
     uint32_t *out_off = nullptr, *out_t = nullptr, *out_nbr = nullptr, *out_gid = nullptr;
     uint32_t *out_src = nullptr, *out_pair = nullptr;
+    uint32_t *out_xrank = nullptr;       // where each out-list time falls in the owner's in-list
+    uint32_t *out_pos = nullptr;         // [gid] position of the edge in its source's out-list
     // in-lists: per vertex, (t', src) order; owner (dst) and pair id per position
     uint32_t *in_off = nullptr, *in_t = nullptr, *in_nbr = nullptr, *in_gid = nullptr;
     uint32_t *in_dst = nullptr, *in_pair = nullptr;
+    uint32_t *in_xrank = nullptr;        // where each in-list time falls in the owner's out-list
+    uint32_t *in_pos = nullptr;          // [gid] position of the edge in its destination's in-list
     // multi-edge lists: pairs sorted by (src, dst); entries in t' order
     uint32_t *vpair_off = nullptr;       // [n+1] first pair of each source vertex
     uint32_t *pair_dst = nullptr;        // [P]

@@ -32,25 +32,6 @@ struct ChildPrefix {
     const uint64_t *pm[2][kMaxTree];   // [layer][slot] prefix in the multi-edge order
 };
 
-// Warp-narrowed lower bound: the first index in [beg, end) with tarr >= key.
-// When every lane of the warp walks the same vertex's list with keys that do
-// not decrease from lane to lane (`same`), only the first and last active
-// lanes search the whole list; every other lane's answer lies between theirs,
-// so it searches that short, cache-hot stretch only.
-__device__ __forceinline__ uint32_t warp_lower(const uint32_t *tarr, uint32_t beg, uint32_t end, uint64_t key,
-                                               bool active, bool same)
-{
-    const unsigned act = __ballot_sync(0xffffffffu, active);
-    if (same && act) {
-        const int lane = threadIdx.x & 31, f = __ffs(act) - 1, l = 31 - __clz(act);
-        uint32_t edge = 0;
-        if (lane == f || lane == l) edge = lower_idx(tarr, beg, end, key);
-        const uint32_t lo = __shfl_sync(0xffffffffu, edge, f), hi = __shfl_sync(0xffffffffu, edge, l);
-        return active ? lower_idx(tarr, lo, hi, key) : 0;
-    }
-    return active ? lower_idx(tarr, beg, end, key) : 0;
-}
-
 // One side of tree node q: the product of the factors of q's children that
 // meet q at its tail (side 0) or head (side 1), for every edge e matched to q
 // and both layers (Claim 3.2).  Threads walk the meeting vertex's own list
@@ -74,9 +55,6 @@ __global__ void __launch_bounds__(256) k_dp_side(DevGraph g, DevPlan P, int q, i
     const uint32_t og = __ldg((side ? g.in_nbr : g.out_nbr) + ps);
     const uint32_t pr = __ldg((side ? g.in_pair : g.out_pair) + ps);
     const uint32_t rv = __ldg(g.rev_pair + pr);
-    // the warp shares one vertex (times then never decrease from lane to lane)
-    const uint32_t z0 = __shfl_sync(0xffffffffu, zg, 0);
-    const bool same = __all_sync(0xffffffffu, valid && zg == z0);
     const int64_t d = P.delta;
     bool ovf_any = false;
 #pragma unroll
@@ -102,12 +80,10 @@ __global__ void __launch_bounds__(256) k_dp_side(DevGraph g, DevPlan P, int q, i
             lo = lo < wlo ? wlo : lo;
             hi = hi > whi ? whi : hi;
             const bool act = inwin && !(!P.tlater[c] && t == 0);
-            const uint32_t *off = out ? g.out_off : g.in_off;
-            const uint32_t *tarr = out ? g.out_t : g.in_t;
-            const uint32_t beg = __ldg(off + zg), end = __ldg(off + zg + 1);
-            const uint32_t a = warp_lower(tarr, beg, end, lo, act, same);
-            const uint32_t b = warp_lower(tarr, beg, end, hi + 1, act, same);
             if (!act || lo > hi) { zero = true; continue; }
+            uint32_t a, b, beg;
+            const uint32_t *tarr;
+            child_range(g, side, out, zg, pos, t, P.tlater[c] != 0, lo, hi, a, b, beg, tarr);
             // excluded multi-edge list: El(z -> o) for an out-child, El(o -> z) for an in-child
             const uint32_t pe = (out == (side == 0)) ? pr : rv;
             uint32_t ea = 0, eb = 0, pb = 0;
@@ -213,10 +189,11 @@ __global__ void k_window_cum(const uint64_t *__restrict__ cdf0, const uint32_t *
                              const uint64_t *__restrict__ cdf1, const uint32_t *__restrict__ beg1, uint32_t nw1,
                              uint64_t *__restrict__ wcum)
 {
-    __shared__ u128 part[1024];
-    uint32_t n = nw0 + nw1;
-    uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+    __shared__ u128 warp_tot[32];
+    const uint32_t n = nw0 + nw1;
+    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
     uint32_t lo = threadIdx.x * per, hi = min(n, lo + per);
+    if (lo > n) lo = n;
     auto total = [&](uint32_t k) -> uint64_t {
         if (k < nw0) return cdf0[beg0[k + 1] - 1];
         k -= nw0;
@@ -224,16 +201,25 @@ __global__ void k_window_cum(const uint64_t *__restrict__ cdf0, const uint32_t *
     };
     u128 s = 0;
     for (uint32_t k = lo; k < hi; ++k) s += total(k);
-    part[threadIdx.x] = s;
+    // exclusive scan of the chunk sums (128-bit) across the block
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    u128 incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t yl = __shfl_up_sync(0xffffffffu, (uint64_t)incl, o);
+        uint64_t yh = __shfl_up_sync(0xffffffffu, (uint64_t)(incl >> 64), o);
+        if (lane >= o) incl += (u128)yl | ((u128)yh << 64);
+    }
+    if (lane == 31) warp_tot[warp] = incl;
     __syncthreads();
     if (threadIdx.x == 0) {
         u128 run = 0;
-        for (unsigned i = 0; i < blockDim.x; ++i) { u128 c = part[i]; part[i] = run; run += c; }
+        const int nw = (blockDim.x + 31) / 32;
+        for (int w = 0; w < nw; ++w) { u128 c = warp_tot[w]; warp_tot[w] = run; run += c; }
         wcum[2 * (size_t)n] = (uint64_t)run;
         wcum[2 * (size_t)n + 1] = (uint64_t)(run >> 64);
     }
     __syncthreads();
-    u128 run = part[threadIdx.x];
+    u128 run = warp_tot[warp] + incl - s;
     for (uint32_t k = lo; k < hi; ++k) {
         wcum[2 * (size_t)k] = (uint64_t)run;
         wcum[2 * (size_t)k + 1] = (uint64_t)(run >> 64);
