@@ -240,6 +240,9 @@ WORKLOADS = {
     # Chung-Lu 50M edges, 5-cycle plus chord
     "cl50m_cycle5chord": dict(kind="chung_lu", n=2_000_000, m=50_000_000, gamma=2.1, span=100_000_000,
                               seed=1, motif=lambda: cycle5_chord(3_600), k=10_000_000),
+    # medium-size companion of the 50M-edge workload (profiling captures)
+    "cl10m_cycle5chord": dict(kind="chung_lu", n=400_000, m=10_000_000, gamma=2.1, span=20_000_000,
+                              seed=1, motif=lambda: cycle5_chord(3_600), k=2_000_000),
     # serving graph: Chung-Lu 200M edges
     "cl200m": dict(kind="chung_lu", n=10_000_000, m=200_000_000, gamma=2.2, span=100_000_000, seed=1,
                    motif=None, k=0),
