@@ -340,6 +340,9 @@ def run_batched(ctx, tg, synth, stream, reps=3):
         return best, out
 
     ms_plain, plain = timed(lambda: [m.sample(k, s) for m, k, s in zip(motifs, ks, seeds)])
+    t0 = time.perf_counter()
+    tuned, table = ctx.autotune(motifs, ks, seeds)      # picks tile / threads / record staging
+    tune_s = time.perf_counter() - t0
     ms_batch, batch = timed(lambda: ctx.batch_run(motifs, ks, seeds))
     same = all((a.hits2, a.valid, a.rej_vertex, a.rej_delta, a.rej_order) ==
                (b.hits2, b.valid, b.rej_vertex, b.rej_delta, b.rej_order) for a, b in zip(plain, batch))
@@ -350,6 +353,8 @@ def run_batched(ctx, tg, synth, stream, reps=3):
             "plain_ms": round(ms_plain, 3), "batched_ms": round(ms_batch, 3),
             "plain_qps": round(len(pool) / (ms_plain / 1e3), 1), "batched_qps": round(len(pool) / (ms_batch / 1e3), 1),
             "speedup": round(ms_plain / ms_batch, 3), "identical_results": bool(same),
+            "autotuned_shape": {k_: tuned[k_] for k_ in ("tile", "threads", "smem_records")},
+            "autotune_s": round(tune_s, 3), "shapes_tried": len(table),
             "timing": "best of %d, CUDA events on the library stream, weights precomputed" % reps}
 
 

@@ -282,6 +282,29 @@ int tm_phase_times(tm_ctx *ctx, double *ms, uint64_t *launches, int cap, int *np
  * last call (inputs, results, counts and status words); resets them. */
 int tm_io_bytes(tm_ctx *ctx, uint64_t *h2d, uint64_t *d2h);
 
+/* One measured shape of the batched sampler. */
+typedef struct {
+    int tile;            /* samples per work item             */
+    int threads;         /* threads per block (128 or 256)    */
+    int smem_records;    /* per-sample records in shared (1) or local (0) memory */
+    double ms;           /* best of two timed launches        */
+} tm_tune_entry;
+
+/* Autotune tm_batch_run for this batch: time every shape (6 tile sizes x 2
+ * block sizes x 2 record placements) on the same queries with their sample
+ * counts scaled to about target_samples in total (0 = 4e6), keep the fastest
+ * in ctx and report it in *best (and every shape in table[table_cap]).
+ * A shape changes speed only: every sample's outcome depends on its seed and
+ * id alone.  Errors: TM_E_STATE (no weights), TM_E_CUDA. */
+int tm_autotune(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64_t *k, const uint64_t *seed,
+                uint64_t target_samples, tm_tune_entry *table, uint32_t table_cap, uint32_t *nentries,
+                tm_tune_entry *best);
+
+/* Pin the batched sampler's shape: tile (samples per work item, 0 = 2048),
+ * threads per block (128 or 256; 0 = 256), per-sample records in shared (1)
+ * or local (0) memory.  Errors: TM_E_ARG. */
+int tm_batch_shape(tm_ctx *ctx, int tile, int threads, int smem_records);
+
 /* Free a motif and its device weights. */
 void tm_motif_free(tm_motif *mo);
 

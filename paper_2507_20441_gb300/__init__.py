@@ -81,6 +81,13 @@ class Result:
                       int(r.rej_order), float(r.estimate))
 
 
+class tm_tune_entry(C.Structure):
+    _fields_ = [("tile", C.c_int), ("threads", C.c_int), ("smem_records", C.c_int), ("ms", C.c_double)]
+
+    def as_dict(self):
+        return {"tile": self.tile, "threads": self.threads, "smem_records": self.smem_records, "ms": self.ms}
+
+
 class tm_serve_cfg(C.Structure):
     _fields_ = [("max_active", C.c_uint32), ("tile", C.c_uint32), ("round_tiles", C.c_uint32),
                 ("poll_timeout_ms", C.c_int32), ("weight_budget", C.c_uint64), ("reserved", C.c_int32 * 8)]
@@ -124,6 +131,9 @@ def _declare(L):
     L.tm_batch_run.argtypes = [vp, u32, vp, vp, vp, vp]
     L.tm_motif_free.argtypes = [vp]; L.tm_motif_free.restype = None
     L.tm_phase_times.argtypes = [vp, vp, vp, i32, C.POINTER(i32)]
+    L.tm_autotune.argtypes = [vp, u32, vp, vp, vp, u64, C.POINTER(tm_tune_entry), u32, C.POINTER(u32),
+                              C.POINTER(tm_tune_entry)]
+    L.tm_batch_shape.argtypes = [vp, i32, i32, i32]
     L.tm_serve_start.argtypes = [vp, C.POINTER(tm_serve_cfg)]
     L.tm_serve_submit.argtypes = [vp, u32, u32, vp, vp, i64, u64, u64, C.POINTER(u64)]
     L.tm_serve_poll.argtypes = [vp, u64, C.POINTER(tm_result), i32]
@@ -341,6 +351,24 @@ def tm_motif_free(motif):
     lib().tm_motif_free(motif)
 
 
+def tm_batch_shape(ctx, tile=0, threads=0, smem_records=0):
+    _check(lib().tm_batch_shape(ctx, int(tile), int(threads), int(smem_records)), ctx, "tm_batch_shape")
+
+
+def tm_autotune(ctx, motifs, ks, seeds, target_samples=0):
+    """Tune the batched sampler for this batch; returns (best, table)."""
+    nq = len(motifs)
+    arr = (C.c_void_p * nq)(*[m.value for m in motifs])
+    k = np.ascontiguousarray(np.array(ks, dtype=np.uint64))
+    s = np.ascontiguousarray(np.array(seeds, dtype=np.uint64))
+    table = (tm_tune_entry * 64)()
+    n = C.c_uint32()
+    best = tm_tune_entry()
+    _check(lib().tm_autotune(ctx, nq, arr, _ptr(k), _ptr(s), int(target_samples), table, 64, C.byref(n),
+                             C.byref(best)), ctx, "tm_autotune")
+    return best.as_dict(), [table[i].as_dict() for i in range(min(n.value, 64))]
+
+
 def tm_serve_start(ctx, max_active=0, tile=0, round_tiles=0, poll_timeout_ms=0, weight_budget=0):
     cfg = tm_serve_cfg(max_active, tile, round_tiles, poll_timeout_ms, weight_budget)
     _check(lib().tm_serve_start(ctx, C.byref(cfg)), ctx, "tm_serve_start")
@@ -485,6 +513,9 @@ class Context:
 
     def io_bytes(self):
         return tm_io_bytes(self.h)
+
+    def autotune(self, motifs, ks, seeds, target_samples=0):
+        return tm_autotune(self.h, [m.h for m in motifs], ks, seeds, target_samples)
 
     def batch_run(self, motifs, ks, seeds):
         return tm_batch_run(self.h, [m.h for m in motifs], ks, seeds)

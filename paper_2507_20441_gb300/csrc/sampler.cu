@@ -411,8 +411,8 @@ struct BatchQuery {
     uint64_t seed, first, k;   // sample ids first .. first+k-1
 };
 
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS, 4) k_batch(DevGraph g, const BatchQuery *__restrict__ qs,
+template <int THREADS, int SMEM_RECS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_batch(DevGraph g, const BatchQuery *__restrict__ qs,
                                                   const uint32_t *__restrict__ tile_base, uint32_t nq, uint32_t tile,
                                                   uint32_t *counter, Acc *accs, uint32_t *status)
 {
@@ -420,8 +420,11 @@ __global__ void __launch_bounds__(THREADS, 4) k_batch(DevGraph g, const BatchQue
     __shared__ uint32_t s_item;
     __shared__ int s_q;
     __shared__ unsigned long long red[THREADS / 32][6];
-    uint32_t recs_local[kRecRows];
-    Recs R{recs_local, 1};
+    // per-sample records: shared memory (one column per thread) or local
+    // memory; which is faster depends on how much L1 the searches need
+    __shared__ uint32_t recs_s[SMEM_RECS ? kRecRows * THREADS : 1];
+    uint32_t recs_l[SMEM_RECS ? 1 : kRecRows];
+    Recs R = SMEM_RECS ? Recs{recs_s + threadIdx.x, THREADS} : Recs{recs_l, 1};
     const uint32_t total = __ldg(tile_base + nq);
     int cur_q = -1;
     for (;;) {
@@ -600,6 +603,32 @@ int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t f
 
 void finish_result_acc(tm_motif *mo, uint64_t k, const SampleAcc &a, tm_result *out) { finish_result(mo, k, a, out); }
 
+// The batched kernel in one of its shapes: 128 or 256 threads per block,
+// per-sample records in local or shared memory.  Persistent: as many blocks
+// as fit on the device at once, capped by the number of work items.
+template <int T, int S>
+static int launch_batch_t(tm_ctx *ctx, uint64_t total, BatchQuery *dq, uint32_t *dbase, uint32_t n, uint32_t tile,
+                          uint32_t *dcounter, Acc *dacc)
+{
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<T, S>, T, 0);
+    uint64_t blocks = (uint64_t)std::max(1, per_sm) * (uint64_t)ctx->num_sms;
+    blocks = std::min<uint64_t>(blocks, std::max<uint64_t>(total, 1));
+    launch(ctx, k_batch<T, S>, (unsigned)blocks, T, ctx->g, (const BatchQuery *)dq, (const uint32_t *)dbase, n, tile,
+           dcounter, dacc, ctx->status);
+    return check_cuda(ctx, cudaGetLastError(), "batch launch");
+}
+
+static int launch_batch_kernel(tm_ctx *ctx, int threads, int smem_recs, uint64_t total, BatchQuery *dq,
+                               uint32_t *dbase, uint32_t n, uint32_t tile, uint32_t *dcounter, Acc *dacc)
+{
+    if (threads == 128)
+        return smem_recs ? launch_batch_t<128, 1>(ctx, total, dq, dbase, n, tile, dcounter, dacc)
+                         : launch_batch_t<128, 0>(ctx, total, dq, dbase, n, tile, dcounter, dacc);
+    return smem_recs ? launch_batch_t<256, 1>(ctx, total, dq, dbase, n, tile, dcounter, dacc)
+                     : launch_batch_t<256, 0>(ctx, total, dq, dbase, n, tile, dcounter, dacc);
+}
+
 // One persistent launch over every item's sample tiles (spec batching).
 int run_batch_items(tm_ctx *ctx, const BatchItem *items, uint32_t n, uint32_t tile, SampleAcc *acc, int wait_ms)
 {
@@ -657,14 +686,8 @@ int run_batch_items(tm_ctx *ctx, const BatchItem *items, uint32_t n, uint32_t ti
     int rc;
     {
         PhaseScope ph(ctx, TM_PH_BATCH);
-        constexpr int THREADS = 256;
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<THREADS>, THREADS, 0);
-        uint64_t blocks = (uint64_t)std::max(1, per_sm) * (uint64_t)ctx->num_sms;
-        blocks = std::min<uint64_t>(blocks, std::max<uint64_t>(total, 1));
-        launch(ctx, k_batch<THREADS>, (unsigned)blocks, THREADS, ctx->g, (const BatchQuery *)dq,
-               (const uint32_t *)dbase, n, tile, dcounter, dacc, ctx->status);
-        rc = check_cuda(ctx, cudaGetLastError(), "batch launch");
+        rc = launch_batch_kernel(ctx, ctx->batch_threads, ctx->batch_smem_recs, total, dq, dbase, n, tile, dcounter,
+                                 dacc);
     }
     copy_d2h(ctx, ctx->pinned_acc, dacc, abytes);
     copy_d2h(ctx, ctx->status_host, ctx->status, 4);

@@ -149,6 +149,8 @@ struct tm_ctx {
     std::vector<ArenaChunk> arena;
     size_t arena_cur = 0;
     timest::Server *server = nullptr;          // serving loop (serve.cu), if running
+    int batch_threads = 256;                   // batched sampler shape (set by tm_autotune)
+    int batch_smem_recs = 0;
     void *pinned_acc = nullptr;                // staging for batched sums (device -> host)
     size_t pinned_acc_bytes = 0;
     uint64_t phase_launches[TM_NUM_PHASES] = {};

@@ -67,3 +67,44 @@ def test_batch_with_empty_weights(pool):
     ref = m1.sample(7000, 2)
     assert (res[1].hits2, res[1].valid, res[1].W) == (ref.hits2, ref.valid, ref.W)
     ctx.close()
+
+
+@pytest.mark.parametrize("threads,smem", [(128, 0), (128, 1), (256, 0), (256, 1)])
+def test_every_batch_shape_gives_the_same_results(pool, threads, smem):
+    import paper_2507_20441_gb300 as tg
+    ctx = _context(tg, 0)
+    tg.tm_batch_shape(ctx.h, 1000, threads, smem)
+    motifs = []
+    for mo in pool[:12]:
+        m = ctx.motif(mo.nv, mo.edges, mo.rank, mo.delta)
+        m.weights()
+        motifs.append(m)
+    ks = [mo.k for mo in pool[:12]]
+    seeds = [7 + i for i in range(12)]
+    res = ctx.batch_run(motifs, ks, seeds)
+    for m, k, s, r in zip(motifs, ks, seeds, res):
+        ref = m.sample(k, s)
+        assert (r.hits2, r.valid, r.rej_vertex, r.rej_delta, r.rej_order) == \
+               (ref.hits2, ref.valid, ref.rej_vertex, ref.rej_delta, ref.rej_order)
+    ctx.close()
+
+
+def test_autotune_picks_the_fastest_measured_shape(pool):
+    import paper_2507_20441_gb300 as tg
+    ctx = _context(tg, 0)
+    motifs = []
+    for mo in pool:
+        m = ctx.motif(mo.nv, mo.edges, mo.rank, mo.delta)
+        m.weights()
+        motifs.append(m)
+    ks = [mo.k for mo in pool]
+    seeds = [100 + i for i in range(len(pool))]
+    best, table = ctx.autotune(motifs, ks, seeds, target_samples=500_000)
+    assert len(table) == 24
+    assert best["ms"] == min(e["ms"] for e in table)
+    assert best["tile"] in (512, 1024, 2048, 4096, 8192, 16384) and best["threads"] in (128, 256)
+    res = ctx.batch_run(motifs, ks, seeds)          # runs with the tuned shape
+    for m, k, s, r in zip(motifs, ks, seeds, res):
+        ref = m.sample(k, s)
+        assert (r.hits2, r.valid) == (ref.hits2, ref.valid)
+    ctx.close()
