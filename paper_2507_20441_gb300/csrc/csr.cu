@@ -522,7 +522,7 @@ int build_csr(tm_ctx *ctx)
         {
             // every m- and n-sized array of the graph in one block
             const size_t mf = (size_t)(m - ndup), a_m = align256((mf ? mf : 1) * 4), a_n = align256(((size_t)n + 1) * 4);
-            if (!gblock_open(ctx, gb, 21 * a_m + 3 * a_n)) return TM_E_NOMEM;
+            if (!gblock_open(ctx, gb, 22 * a_m + 3 * a_n)) return TM_E_NOMEM;
         }
         g.g_t = gtake(gb, m - ndup); g.g_src = gtake(gb, m - ndup); g.g_dst = gtake(gb, m - ndup);
         if (!g.g_t || !g.g_src || !g.g_dst) return TM_E_NOMEM;
@@ -578,9 +578,9 @@ int build_csr(tm_ctx *ctx)
     // ---- multi-edge order: stable re-sort of the IN order by source
     sec.reset();
     sec.reset(new PhaseScope(ctx, TM_PH_CSR_MULTI));
-    g.multi_gid = gtake(gb, m); g.multi_t = gtake(gb, m); g.g_pair = gtake(gb, m);
+    g.multi_gid = gtake(gb, m); g.multi_t = gtake(gb, m); g.g_pair = gtake(gb, m); g.multi_pos = gtake(gb, m);
     g.vpair_off = gtake(gb, (size_t)n + 1);
-    if (!g.multi_gid || !g.multi_t || !g.g_pair || !g.vpair_off) return TM_E_NOMEM;
+    if (!g.multi_gid || !g.multi_t || !g.g_pair || !g.vpair_off || !g.multi_pos) return TM_E_NOMEM;
     uint32_t np = 0;
     if (m) {
         cudaMemcpyAsync(key, g.in_nbr, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
@@ -623,6 +623,7 @@ int build_csr(tm_ctx *ctx)
         launch(ctx, k_cross_rank, blocks_for(m, TB), TB, g.in_t, g.in_dst, m, g.out_off, g.out_t, g.in_xrank);
         launch(ctx, k_inverse, blocks_for(m, TB), TB, g.out_gid, m, g.out_pos);
         launch(ctx, k_inverse, blocks_for(m, TB), TB, g.in_gid, m, g.in_pos);
+        launch(ctx, k_inverse, blocks_for(m, TB), TB, g.multi_gid, m, g.multi_pos);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "pair tables");
         if (rc) return rc;
     } else {

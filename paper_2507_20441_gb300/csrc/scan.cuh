@@ -131,8 +131,11 @@ __device__ __forceinline__ SegAgg seg_combine(SegAgg a, SegAgg b, bool &ovf)
 
 // Load functor interface: __device__ uint64_t value(uint64_t pos) const;
 //                         __device__ bool head(uint64_t pos) const;
+//                         static constexpr bool kGathered (value() is a gather:
+//                         read it once and keep it for the rescan)
 template <class F>
-__global__ void k_segscan_reduce(F f, uint64_t n, SegAgg *__restrict__ aggs, uint32_t *status)
+__global__ void k_segscan_reduce(F f, uint64_t n, SegAgg *__restrict__ aggs, uint64_t *__restrict__ stash,
+                                 uint32_t *status)
 {
     __shared__ SegAgg warp_agg[SCAN_THREADS / 32];
     uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
@@ -142,7 +145,9 @@ __global__ void k_segscan_reduce(F f, uint64_t n, SegAgg *__restrict__ aggs, uin
     for (int j = 0; j < SCAN_ITEMS; ++j) {
         uint64_t i = base + j;
         if (i < n) {
-            SegAgg x{f.value(i), f.head(i) ? 1u : 0u, 0};
+            const uint64_t v = f.value(i);
+            if (stash) stash[i] = v;          // gathered once; the rescan reads it back in order
+            SegAgg x{v, f.head(i) ? 1u : 0u, 0};
             a = seg_combine(a, x, ovf);
         }
     }
@@ -219,8 +224,8 @@ __global__ void k_segscan_carries(SegAgg *__restrict__ aggs, uint64_t ntiles, ui
 }
 
 template <class F>
-__global__ void k_segscan_final(F f, uint64_t n, const SegAgg *__restrict__ carries, uint64_t *__restrict__ out,
-                                uint32_t *status)
+__global__ void k_segscan_final(F f, uint64_t n, const SegAgg *__restrict__ carries,
+                                const uint64_t *__restrict__ stash, uint64_t *__restrict__ out, uint32_t *status)
 {
     __shared__ SegAgg warp_agg[SCAN_THREADS / 32];
     uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
@@ -233,7 +238,7 @@ __global__ void k_segscan_final(F f, uint64_t n, const SegAgg *__restrict__ carr
         uint64_t i = base + j;
         v[j] = 0;
         if (i < n) {
-            v[j] = f.value(i);
+            v[j] = stash ? stash[i] : f.value(i);
             bool h = f.head(i);
             hbits |= (h ? 1u : 0u) << j;
             SegAgg x{v[j], h ? 1u : 0u, 0};
@@ -285,10 +290,12 @@ int segmented_scan_u64(tm_ctx *ctx, const F &f, uint64_t n, uint64_t *out)
     uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     ScratchScope scope(ctx);
     SegAgg *aggs = (SegAgg *)salloc(ctx, tiles * sizeof(SegAgg));
-    if (!aggs) return TM_E_NOMEM;
-    launch(ctx, k_segscan_reduce<F>, (unsigned)tiles, SCAN_THREADS, f, n, aggs, ctx->status);
+    uint64_t *stash = F::kGathered ? (uint64_t *)salloc(ctx, n * sizeof(uint64_t)) : nullptr;
+    if (!aggs || (F::kGathered && !stash)) return TM_E_NOMEM;
+    launch(ctx, k_segscan_reduce<F>, (unsigned)tiles, SCAN_THREADS, f, n, aggs, stash, ctx->status);
     launch(ctx, k_segscan_carries, 1, 1024, aggs, tiles, ctx->status);
-    launch(ctx, k_segscan_final<F>, (unsigned)tiles, SCAN_THREADS, f, n, aggs, out, ctx->status);
+    launch(ctx, k_segscan_final<F>, (unsigned)tiles, SCAN_THREADS, f, n, aggs, (const uint64_t *)stash, out,
+           ctx->status);
     return check_cuda(ctx, cudaGetLastError(), "segmented scan");
 }
 

@@ -53,6 +53,7 @@ struct DevGraph {
     uint32_t *pair_off = nullptr;        // [P+1] into multi_*
     uint32_t *rev_pair = nullptr;        // [P] pair (dst,src) or kNone
     uint32_t *multi_t = nullptr, *multi_gid = nullptr;
+    uint32_t *multi_pos = nullptr;       // [gid] position of the edge in its multi-edge list
 };
 
 // Device plan of a motif with its rooted spanning tree (Defs. 3.4-3.5).

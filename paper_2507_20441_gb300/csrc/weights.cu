@@ -32,109 +32,121 @@ struct ChildPrefix {
     const uint64_t *pm[2][kMaxTree];   // [layer][slot] prefix in the multi-edge order
 };
 
-// One side of tree node q: the product of the factors of q's children that
-// meet q at its tail (side 0) or head (side 1), for every edge e matched to q
-// and both layers (Claim 3.2).  Threads walk the meeting vertex's own list
-// (out-list order for side 0, in-list order for side 1), so neighbouring
-// lanes share the vertex and its candidate lists and have non-decreasing
-// times.  A node with children on both sides (the root) runs side 0 with
-// first = 1 and side 1 with last = 1; the partial product and a pending
-// overflow bit carry between the passes, so the result and the overflow rule
-// (a factor >= 2^64, or an exact product >= 2^64 with no zero factor) are
-// those of the whole product.
-__global__ void __launch_bounds__(256) k_dp_side(DevGraph g, DevPlan P, int q, int side, int first, int last,
-                                                 ChildPrefix cp, uint64_t *__restrict__ w0, uint64_t *__restrict__ w1,
-                                                 uint8_t *__restrict__ pend, uint32_t *status)
+// w_{q,e} for every edge e matched to tree node q, both layers (Claim 3.2).
+// One thread per edge id: the edge record and the edge's positions in its
+// source's out-list and its destination's in-list are coalesced reads.  For
+// each child the candidate range is galloped to from the edge's position in
+// the meeting vertex's list (or the cross rank into the vertex's other list),
+// and the excluded multi-edge list (Claim 3.1) is bounded by galloping from
+// the edge's own entry (its own pair) or by a search of the reverse pair; the
+// per-child lookups are shared by the two window layers.  Overflow rule: a
+// factor >= 2^64, or an exact product >= 2^64 with no zero factor.
+__global__ void __launch_bounds__(256) k_dp(DevGraph g, DevPlan P, int q, ChildPrefix cp, uint64_t *__restrict__ w0,
+                                            uint64_t *__restrict__ w1, uint32_t *status)
 {
-    const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = pos < g.m;
-    const uint32_t ps = valid ? pos : g.m - 1;
-    const uint32_t e = __ldg((side ? g.in_gid : g.out_gid) + ps);
-    const uint32_t t = __ldg((side ? g.in_t : g.out_t) + ps);
-    const uint32_t zg = __ldg((side ? g.in_dst : g.out_src) + ps);
-    const uint32_t og = __ldg((side ? g.in_nbr : g.out_nbr) + ps);
-    const uint32_t pr = __ldg((side ? g.in_pair : g.out_pair) + ps);
-    const uint32_t rv = __ldg(g.rev_pair + pr);
+    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= g.m) return;
+    const uint32_t t = __ldg(g.g_t + e), u = __ldg(g.g_src + e), v = __ldg(g.g_dst + e);
+    const uint32_t pr = __ldg(g.g_pair + e);
     const int64_t d = P.delta;
-    bool ovf_any = false;
+    int64_t wi[2];
+    uint64_t wlo[2], whi[2], prod[2] = {1, 1};
+    bool zero[2], ovf[2] = {false, false};
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
-        const int64_t wi = layer_window(t, p, d);
-        const bool inwin = valid && wi >= 0;
-        const uint64_t wlo = inwin ? (uint64_t)(wi * d) : 0, whi = inwin ? (uint64_t)((wi + 2) * d - 1) : 0;
-        uint64_t prod = 1;
-        bool zero = !inwin, ovf = false;
-        uint64_t *W = p == 0 ? w0 : w1;
-        if (!first && inwin) {
-            prod = W[e];
-            ovf = (pend[(size_t)p * g.m + e] != 0);
-            if (prod == 0) zero = true;
+        wi[p] = layer_window(t, p, d);
+        zero[p] = wi[p] < 0;
+        wlo[p] = zero[p] ? 0 : (uint64_t)(wi[p] * d);
+        whi[p] = zero[p] ? 0 : (uint64_t)((wi[p] + 2) * d - 1);
+    }
+    uint32_t rv = kNone, rvb = 0, rve = 0, rbase = 0;    // reverse pair, fetched once if needed
+    bool have_rv = false;
+    uint32_t pb = 0, pend = 0, mbase = 0;                // own pair range and own entry
+    bool have_own = false;
+    for (int ci = 0; ci < P.nchild[q] && !(zero[0] && zero[1]); ++ci) {
+        const int c = P.child[q][ci];
+        const int side = P.tzside[c];
+        const bool out = P.tout[c] != 0, later = P.tlater[c] != 0;
+        if (!later && t == 0) { zero[0] = zero[1] = true; break; }
+        const uint32_t z = side ? v : u;
+        const uint32_t pos = __ldg((side ? g.in_pos : g.out_pos) + e);
+        // first entry with time >= t in the child list, from the edge's own position
+        const uint32_t *off = out ? g.out_off : g.in_off;
+        const uint32_t *tarr = out ? g.out_t : g.in_t;
+        const uint32_t beg = __ldg(off + z), end = __ldg(off + z + 1);
+        const uint32_t base = ((side == 0) == out) ? gallop_back(tarr, beg, pos, t)
+                                                   : __ldg((side == 0 ? g.out_xrank : g.in_xrank) + pos);
+        // excluded list: El(z -> o) for an out-child, El(o -> z) for an in-child
+        const bool own = (out == (side == 0));
+        uint32_t xb, xe, xbase;   // pair range and its first entry with time >= t
+        if (own) {
+            if (!have_own) {
+                pb = __ldg(g.pair_off + pr);
+                pend = __ldg(g.pair_off + pr + 1);
+                mbase = gallop_back(g.multi_t, pb, __ldg(g.multi_pos + e), t);
+                have_own = true;
+            }
+            xb = pb; xe = pend; xbase = mbase;
+        } else {
+            if (!have_rv) {
+                rv = __ldg(g.rev_pair + pr);
+                if (rv != kNone) {
+                    rvb = __ldg(g.pair_off + rv);
+                    rve = __ldg(g.pair_off + rv + 1);
+                    rbase = lower_idx(g.multi_t, rvb, rve, t);
+                }
+                have_rv = true;
+            }
+            if (rv == kNone) { xb = xe = xbase = 0; }
+            else { xb = rvb; xe = rve; xbase = rbase; }
         }
-        for (int ci = 0; ci < P.nchild[q]; ++ci) {
-            const int c = P.child[q][ci];
-            if (P.tzside[c] != side) continue;
-            const bool out = P.tout[c] != 0;
+        const uint64_t *Pd0 = nullptr, *Pm0 = nullptr;
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            if (zero[p]) continue;
             uint64_t lo, hi;
-            if (P.tlater[c]) { lo = (uint64_t)t + 1; hi = (uint64_t)t + (uint64_t)d; }
-            else { lo = (uint64_t)t >= (uint64_t)d ? (uint64_t)t - (uint64_t)d : 0; hi = t ? (uint64_t)t - 1 : 0; }
-            lo = lo < wlo ? wlo : lo;
-            hi = hi > whi ? whi : hi;
-            const bool act = inwin && !(!P.tlater[c] && t == 0);
-            if (!act || lo > hi) { zero = true; continue; }
-            uint32_t a, b, beg;
-            const uint32_t *tarr;
-            child_range(g, side, out, zg, pos, t, P.tlater[c] != 0, lo, hi, a, b, beg, tarr);
-            // excluded multi-edge list: El(z -> o) for an out-child, El(o -> z) for an in-child
-            const uint32_t pe = (out == (side == 0)) ? pr : rv;
-            uint32_t ea = 0, eb = 0, pb = 0;
-            if (pe != kNone) {
-                pb = __ldg(g.pair_off + pe);
-                const uint32_t pend_ = __ldg(g.pair_off + pe + 1);
-                ea = lower_idx(g.multi_t, pb, pend_, lo);
-                eb = gallop_idx(g.multi_t, ea, pend_, hi + 1);
+            if (later) { lo = (uint64_t)t + 1; hi = (uint64_t)t + (uint64_t)d; }
+            else { lo = (uint64_t)t >= (uint64_t)d ? (uint64_t)t - (uint64_t)d : 0; hi = (uint64_t)t - 1; }
+            lo = lo < wlo[p] ? wlo[p] : lo;
+            hi = hi > whi[p] ? whi[p] : hi;
+            if (lo > hi) { zero[p] = true; continue; }
+            uint32_t a, b, ea = 0, eb = 0;
+            if (later) { a = gallop_idx(tarr, base, end, lo); b = gallop_idx(tarr, a, end, hi + 1); }
+            else { b = base; a = gallop_back(tarr, beg, base, lo); }
+            if (xe > xb) {
+                if (later) { ea = gallop_idx(g.multi_t, xbase, xe, lo); eb = gallop_idx(g.multi_t, ea, xe, hi + 1); }
+                else { eb = xbase; ea = gallop_back(g.multi_t, xb, xbase, lo); }
             }
             uint64_t sum;
             if (P.tleaf[c]) {
                 sum = (uint64_t)(b - a) - (uint64_t)(eb - ea);
             } else {
-                const uint64_t *Pd = cp.pd[p][P.tslot[c]];
-                const uint64_t *Pm = cp.pm[p][P.tslot[c]];
+                Pd0 = cp.pd[p][P.tslot[c]];
+                Pm0 = cp.pm[p][P.tslot[c]];
                 uint64_t sr = 0, se = 0;
                 if (b > a) {
-                    const uint64_t base = (a > beg && (uint64_t)__ldg(tarr + a - 1) >= wlo) ? __ldg(Pd + a - 1) : 0;
-                    sr = __ldg(Pd + b - 1) - base;
+                    const uint64_t bs = (a > beg && (uint64_t)__ldg(tarr + a - 1) >= wlo[p]) ? __ldg(Pd0 + a - 1) : 0;
+                    sr = __ldg(Pd0 + b - 1) - bs;
                 }
                 if (eb > ea) {
-                    const uint64_t base = (ea > pb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo) ? __ldg(Pm + ea - 1) : 0;
-                    se = __ldg(Pm + eb - 1) - base;
+                    const uint64_t bs = (ea > xb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo[p]) ? __ldg(Pm0 + ea - 1) : 0;
+                    se = __ldg(Pm0 + eb - 1) - bs;
                 }
                 sum = sr - se;
             }
-            if (sum == 0) zero = true;
-            else prod = mul_chk(prod, sum, ovf);
-        }
-        if (!valid) continue;
-        if (!inwin) {
-            W[e] = 0;
-            continue;
-        }
-        if (zero) {
-            W[e] = 0;
-            if (!last) pend[(size_t)p * g.m + e] = 0;
-        } else if (last) {
-            W[e] = prod;
-            ovf_any |= ovf;
-        } else {
-            W[e] = prod;
-            pend[(size_t)p * g.m + e] = ovf ? 1 : 0;
+            if (sum == 0) zero[p] = true;
+            else prod[p] = mul_chk(prod[p], sum, ovf[p]);
         }
     }
-    if (ovf_any) latch(status, ST_OVERFLOW);
+    w0[e] = zero[0] ? 0 : prod[0];
+    w1[e] = zero[1] ? 0 : prod[1];
+    if ((!zero[0] && ovf[0]) || (!zero[1] && ovf[1])) latch(status, ST_OVERFLOW);
 }
 
 // ---- scans over the three orders ----------------------------------------
 // segment = (owner, window of layer p); owner boundaries come from a bit set.
 struct DirScan {
+    static constexpr bool kGathered = true;
     const uint64_t *w;          // weights by gid
     const uint32_t *perm;       // position -> gid
     const uint32_t *tarr;       // position -> t'
@@ -151,6 +163,7 @@ struct DirScan {
 };
 
 struct RootScan {
+    static constexpr bool kGathered = false;
     const uint64_t *w;
     const uint32_t *tarr;       // g_t
     int p;
@@ -367,7 +380,6 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     w[1] = (uint64_t *)salloc(ctx, (size_t)(m ? m : 1) * 8);
     if (!w[0] || !w[1]) return TM_E_NOMEM;
     ChildPrefix cp{};
-    uint8_t *pend = nullptr;
     int maxh = 0;
     for (int q = 0; q < P.ntree; ++q) maxh = std::max(maxh, (int)P.height[q]);
     std::vector<int> order;
@@ -378,22 +390,7 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     for (int q : order) {
         {
             PhaseScope ph(ctx, TM_PH_DP);
-            bool has[2] = {false, false};
-            for (int ci = 0; ci < P.nchild[q]; ++ci) has[P.tzside[P.child[q][ci]]] = true;
-            if (!has[0] && !has[1]) has[0] = true;   // a leaf root (single-edge motif): weight 1 per window
-            if (m) {
-                const bool two = has[0] && has[1];
-                if (two && !pend) {
-                    pend = (uint8_t *)salloc(ctx, 2 * (size_t)m);
-                    if (!pend) return TM_E_NOMEM;
-                }
-                if (has[0])
-                    launch(ctx, k_dp_side, blocks_for(m, TB), TB, g, P, q, 0, 1, two ? 0 : 1, cp, w[0], w[1], pend,
-                           ctx->status);
-                if (has[1])
-                    launch(ctx, k_dp_side, blocks_for(m, TB), TB, g, P, q, 1, two ? 0 : 1, 1, cp, w[0], w[1], pend,
-                           ctx->status);
-            }
+            if (m) launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, q, cp, w[0], w[1], ctx->status);
         }
         rc = check_cuda(ctx, cudaGetLastError(), "weight DP");
         if (rc) return rc;
