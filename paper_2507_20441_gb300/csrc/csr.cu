@@ -345,7 +345,7 @@ __global__ void k_gather2(const uint32_t *__restrict__ idx, uint32_t m, const ui
     if (i >= m) return;
     uint32_t g = idx[i];
     ox[i] = x[g];
-    if (y) oy[i] = y[g];
+    if (y && oy) oy[i] = y[g];
 }
 
 // off[v] = first position whose sorted key is >= v, for v in [0, n].
@@ -522,7 +522,7 @@ int build_csr(tm_ctx *ctx)
         {
             // every m- and n-sized array of the graph in one block
             const size_t mf = (size_t)(m - ndup), a_m = align256((mf ? mf : 1) * 4), a_n = align256(((size_t)n + 1) * 4);
-            if (!gblock_open(ctx, gb, 22 * a_m + 3 * a_n)) return TM_E_NOMEM;
+            if (!gblock_open(ctx, gb, 26 * a_m + 3 * a_n)) return TM_E_NOMEM;
         }
         g.g_t = gtake(gb, m - ndup); g.g_src = gtake(gb, m - ndup); g.g_dst = gtake(gb, m - ndup);
         if (!g.g_t || !g.g_src || !g.g_dst) return TM_E_NOMEM;
@@ -579,8 +579,11 @@ int build_csr(tm_ctx *ctx)
     sec.reset();
     sec.reset(new PhaseScope(ctx, TM_PH_CSR_MULTI));
     g.multi_gid = gtake(gb, m); g.multi_t = gtake(gb, m); g.g_pair = gtake(gb, m); g.multi_pos = gtake(gb, m);
+    g.out_to_in = gtake(gb, m); g.in_to_out = gtake(gb, m); g.multi_to_out = gtake(gb, m); g.multi_to_in = gtake(gb, m);
     g.vpair_off = gtake(gb, (size_t)n + 1);
-    if (!g.multi_gid || !g.multi_t || !g.g_pair || !g.vpair_off || !g.multi_pos) return TM_E_NOMEM;
+    if (!g.multi_gid || !g.multi_t || !g.g_pair || !g.vpair_off || !g.multi_pos || !g.out_to_in || !g.in_to_out ||
+        !g.multi_to_out || !g.multi_to_in)
+        return TM_E_NOMEM;
     uint32_t np = 0;
     if (m) {
         cudaMemcpyAsync(key, g.in_nbr, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
@@ -624,6 +627,11 @@ int build_csr(tm_ctx *ctx)
         launch(ctx, k_inverse, blocks_for(m, TB), TB, g.out_gid, m, g.out_pos);
         launch(ctx, k_inverse, blocks_for(m, TB), TB, g.in_gid, m, g.in_pos);
         launch(ctx, k_inverse, blocks_for(m, TB), TB, g.multi_gid, m, g.multi_pos);
+        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.out_gid, m, g.in_pos, (const uint32_t *)nullptr, g.out_to_in,
+               (uint32_t *)nullptr);
+        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.in_gid, m, g.out_pos, (const uint32_t *)nullptr, g.in_to_out,
+               (uint32_t *)nullptr);
+        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.multi_gid, m, g.out_pos, g.in_pos, g.multi_to_out, g.multi_to_in);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "pair tables");
         if (rc) return rc;
     } else {

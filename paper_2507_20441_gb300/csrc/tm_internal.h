@@ -54,6 +54,8 @@ struct DevGraph {
     uint32_t *rev_pair = nullptr;        // [P] pair (dst,src) or kNone
     uint32_t *multi_t = nullptr, *multi_gid = nullptr;
     uint32_t *multi_pos = nullptr;       // [gid] position of the edge in its multi-edge list
+    // position maps between the list orders (same edge): out->in, in->out, multi->out, multi->in
+    uint32_t *out_to_in = nullptr, *in_to_out = nullptr, *multi_to_out = nullptr, *multi_to_in = nullptr;
 };
 
 // Device plan of a motif with its rooted spanning tree (Defs. 3.4-3.5).

@@ -32,75 +32,68 @@ struct ChildPrefix {
     const uint64_t *pm[2][kMaxTree];   // [layer][slot] prefix in the multi-edge order
 };
 
-// w_{q,e} for every edge e matched to tree node q, both layers (Claim 3.2).
-// One thread per edge id: the edge record and the edge's positions in its
-// source's out-list and its destination's in-list are coalesced reads.  For
-// each child the candidate range is galloped to from the edge's position in
-// the meeting vertex's list (or the cross rank into the vertex's other list),
-// and the excluded multi-edge list (Claim 3.1) is bounded by galloping from
-// the edge's own entry (its own pair) or by a search of the reverse pair; the
-// per-child lookups are shared by the two window layers.  Overflow rule: a
-// factor >= 2^64, or an exact product >= 2^64 with no zero factor.
-__global__ void __launch_bounds__(256) k_dp(DevGraph g, DevPlan P, int q, ChildPrefix cp, uint64_t *__restrict__ w0,
-                                            uint64_t *__restrict__ w1, uint32_t *status)
+// Candidate ranges up to this many entries are scanned for the excluded
+// neighbour; longer ones search the excluded multi-edge list instead.
+constexpr uint32_t kScanLimit = 48;
+
+// One side of tree node q (Claim 3.2): the product of the factors of q's
+// children that meet q at its tail (side 0) or head (side 1), for every edge
+// matched to q and both layers.  Threads walk the meeting vertex's own list
+// (out-list order for side 0, in-list order for side 1), so the lanes of a
+// warp share the vertex, its candidate lists and nearby positions in them.
+// Each child's range [a, b) is galloped to from the parent edge's position
+// in that list (or its cross rank into the vertex's other list).  The
+// excluded entries of Claim 3.1 are exactly the entries of [a, b) whose other
+// endpoint is the parent's other endpoint: short ranges are scanned for them
+// in place; long ones search the excluded multi-edge list.
+// Results are written in this list order.  A root with children at both ends
+// runs side 0 (first) then side 1 (last), which reads side 0's partial
+// product and pending-overflow bit through the out->in position map.
+// Overflow rule: a factor >= 2^64, or an exact product >= 2^64 with no zero
+// factor.
+__global__ void __launch_bounds__(256) k_dp(DevGraph g, DevPlan P, int q, int side, int first, int last,
+                                            ChildPrefix cp, uint64_t *__restrict__ o0, uint64_t *__restrict__ o1,
+                                            const uint64_t *__restrict__ i0, const uint64_t *__restrict__ i1,
+                                            const uint8_t *__restrict__ pin, uint8_t *__restrict__ pout,
+                                            uint32_t *status)
 {
-    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= g.m) return;
-    const uint32_t t = __ldg(g.g_t + e), u = __ldg(g.g_src + e), v = __ldg(g.g_dst + e);
-    const uint32_t pr = __ldg(g.g_pair + e);
+    const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= g.m) return;
+    const uint32_t t = __ldg((side ? g.in_t : g.out_t) + pos);
+    const uint32_t z = __ldg((side ? g.in_dst : g.out_src) + pos);
+    const uint32_t o = __ldg((side ? g.in_nbr : g.out_nbr) + pos);
+    const uint32_t pr = __ldg((side ? g.in_pair : g.out_pair) + pos);
     const int64_t d = P.delta;
-    int64_t wi[2];
     uint64_t wlo[2], whi[2], prod[2] = {1, 1};
     bool zero[2], ovf[2] = {false, false};
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
-        wi[p] = layer_window(t, p, d);
-        zero[p] = wi[p] < 0;
-        wlo[p] = zero[p] ? 0 : (uint64_t)(wi[p] * d);
-        whi[p] = zero[p] ? 0 : (uint64_t)((wi[p] + 2) * d - 1);
+        const int64_t wi = layer_window(t, p, d);
+        zero[p] = wi < 0;
+        wlo[p] = zero[p] ? 0 : (uint64_t)(wi * d);
+        whi[p] = zero[p] ? 0 : (uint64_t)((wi + 2) * d - 1);
     }
-    uint32_t rv = kNone, rvb = 0, rve = 0, rbase = 0;    // reverse pair, fetched once if needed
-    bool have_rv = false;
-    uint32_t pb = 0, pend = 0, mbase = 0;                // own pair range and own entry
-    bool have_own = false;
+    if (!first) {
+        const uint32_t xp = __ldg(g.in_to_out + pos);   // side 1 reads side 0's partial
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            if (zero[p]) continue;
+            prod[p] = __ldg((p ? i1 : i0) + xp);
+            ovf[p] = pin[(size_t)p * g.m + xp] != 0;
+            if (prod[p] == 0) zero[p] = true;
+        }
+    }
     for (int ci = 0; ci < P.nchild[q] && !(zero[0] && zero[1]); ++ci) {
         const int c = P.child[q][ci];
-        const int side = P.tzside[c];
-        const bool out = P.tout[c] != 0, later = P.tlater[c] != 0;
+        if (P.tzside[c] != side) continue;
+        const bool out = P.tout[c] != 0, later = P.tlater[c] != 0, leaf = P.tleaf[c] != 0;
         if (!later && t == 0) { zero[0] = zero[1] = true; break; }
-        const uint32_t z = side ? v : u;
-        const uint32_t pos = __ldg((side ? g.in_pos : g.out_pos) + e);
-        // first entry with time >= t in the child list, from the edge's own position
         const uint32_t *off = out ? g.out_off : g.in_off;
         const uint32_t *tarr = out ? g.out_t : g.in_t;
+        const uint32_t *nbr = out ? g.out_nbr : g.in_nbr;
         const uint32_t beg = __ldg(off + z), end = __ldg(off + z + 1);
         const uint32_t base = ((side == 0) == out) ? gallop_back(tarr, beg, pos, t)
                                                    : __ldg((side == 0 ? g.out_xrank : g.in_xrank) + pos);
-        // excluded list: El(z -> o) for an out-child, El(o -> z) for an in-child
-        const bool own = (out == (side == 0));
-        uint32_t xb, xe, xbase;   // pair range and its first entry with time >= t
-        if (own) {
-            if (!have_own) {
-                pb = __ldg(g.pair_off + pr);
-                pend = __ldg(g.pair_off + pr + 1);
-                mbase = gallop_back(g.multi_t, pb, __ldg(g.multi_pos + e), t);
-                have_own = true;
-            }
-            xb = pb; xe = pend; xbase = mbase;
-        } else {
-            if (!have_rv) {
-                rv = __ldg(g.rev_pair + pr);
-                if (rv != kNone) {
-                    rvb = __ldg(g.pair_off + rv);
-                    rve = __ldg(g.pair_off + rv + 1);
-                    rbase = lower_idx(g.multi_t, rvb, rve, t);
-                }
-                have_rv = true;
-            }
-            if (rv == kNone) { xb = xe = xbase = 0; }
-            else { xb = rvb; xe = rve; xbase = rbase; }
-        }
-        const uint64_t *Pd0 = nullptr, *Pm0 = nullptr;
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
             if (zero[p]) continue;
@@ -110,50 +103,61 @@ __global__ void __launch_bounds__(256) k_dp(DevGraph g, DevPlan P, int q, ChildP
             lo = lo < wlo[p] ? wlo[p] : lo;
             hi = hi > whi[p] ? whi[p] : hi;
             if (lo > hi) { zero[p] = true; continue; }
-            uint32_t a, b, ea = 0, eb = 0;
+            uint32_t a, b;
             if (later) { a = gallop_idx(tarr, base, end, lo); b = gallop_idx(tarr, a, end, hi + 1); }
             else { b = base; a = gallop_back(tarr, beg, base, lo); }
-            if (xe > xb) {
-                if (later) { ea = gallop_idx(g.multi_t, xbase, xe, lo); eb = gallop_idx(g.multi_t, ea, xe, hi + 1); }
-                else { eb = xbase; ea = gallop_back(g.multi_t, xb, xbase, lo); }
-            }
-            uint64_t sum;
-            if (P.tleaf[c]) {
-                sum = (uint64_t)(b - a) - (uint64_t)(eb - ea);
+            const uint64_t *Pd = leaf ? nullptr : cp.pd[p][P.tslot[c]];
+            uint64_t pbase = 0, sum;
+            if (!leaf && b > a) pbase = (a > beg && (uint64_t)__ldg(tarr + a - 1) >= wlo[p]) ? __ldg(Pd + a - 1) : 0;
+            uint64_t excl = 0;
+            if (b - a <= kScanLimit) {
+                uint64_t prev = pbase;
+                for (uint32_t x = a; x < b; ++x) {
+                    uint64_t wx = 1;
+                    if (!leaf) { const uint64_t px = __ldg(Pd + x); wx = px - prev; prev = px; }
+                    if (__ldg(nbr + x) == o) excl += wx;
+                }
             } else {
-                Pd0 = cp.pd[p][P.tslot[c]];
-                Pm0 = cp.pm[p][P.tslot[c]];
-                uint64_t sr = 0, se = 0;
-                if (b > a) {
-                    const uint64_t bs = (a > beg && (uint64_t)__ldg(tarr + a - 1) >= wlo[p]) ? __ldg(Pd0 + a - 1) : 0;
-                    sr = __ldg(Pd0 + b - 1) - bs;
+                const uint32_t pe = (out == (side == 0)) ? pr : __ldg(g.rev_pair + pr);
+                if (pe != kNone) {
+                    const uint32_t xb = __ldg(g.pair_off + pe), xe = __ldg(g.pair_off + pe + 1);
+                    const uint32_t ea = lower_idx(g.multi_t, xb, xe, lo);
+                    const uint32_t eb = gallop_idx(g.multi_t, ea, xe, hi + 1);
+                    if (eb > ea) {
+                        if (leaf) excl = eb - ea;
+                        else {
+                            const uint64_t *Pm = cp.pm[p][P.tslot[c]];
+                            const uint64_t bs = (ea > xb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo[p]) ? __ldg(Pm + ea - 1) : 0;
+                            excl = __ldg(Pm + eb - 1) - bs;
+                        }
+                    }
                 }
-                if (eb > ea) {
-                    const uint64_t bs = (ea > xb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo[p]) ? __ldg(Pm0 + ea - 1) : 0;
-                    se = __ldg(Pm0 + eb - 1) - bs;
-                }
-                sum = sr - se;
             }
+            if (leaf) sum = (uint64_t)(b - a) - excl;
+            else sum = (b > a ? __ldg(Pd + b - 1) - pbase : 0) - excl;
             if (sum == 0) zero[p] = true;
             else prod[p] = mul_chk(prod[p], sum, ovf[p]);
         }
     }
-    w0[e] = zero[0] ? 0 : prod[0];
-    w1[e] = zero[1] ? 0 : prod[1];
-    if ((!zero[0] && ovf[0]) || (!zero[1] && ovf[1])) latch(status, ST_OVERFLOW);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        (p ? o1 : o0)[pos] = zero[p] ? 0 : prod[p];
+        if (!last) pout[(size_t)p * g.m + pos] = (!zero[p] && ovf[p]) ? 1 : 0;
+    }
+    if (last && ((!zero[0] && ovf[0]) || (!zero[1] && ovf[1]))) latch(status, ST_OVERFLOW);
 }
 
 // ---- scans over the three orders ----------------------------------------
 // segment = (owner, window of layer p); owner boundaries come from a bit set.
 struct DirScan {
     static constexpr bool kGathered = true;
-    const uint64_t *w;          // weights by gid
-    const uint32_t *perm;       // position -> gid
+    const uint64_t *w;          // weights in the order the DP wrote them
+    const uint32_t *perm;       // scan position -> weight position (null: same order)
     const uint32_t *tarr;       // position -> t'
     const uint32_t *ownbits;    // bit set: position starts a new owner
     int p;
     int64_t d;
-    __device__ uint64_t value(uint64_t i) const { return __ldg(w + __ldg(perm + i)); }
+    __device__ uint64_t value(uint64_t i) const { return perm ? __ldg(w + __ldg(perm + i)) : __ldg(w + i); }
     __device__ bool head(uint64_t i) const
     {
         if (i == 0) return true;
@@ -163,12 +167,13 @@ struct DirScan {
 };
 
 struct RootScan {
-    static constexpr bool kGathered = false;
-    const uint64_t *w;
+    static constexpr bool kGathered = true;
+    const uint64_t *w;          // root weights in list order
     const uint32_t *tarr;       // g_t
     int p;
     int64_t d;
-    __device__ uint64_t value(uint64_t i) const { return __ldg(w + i); }
+    const uint32_t *perm;       // gid -> weight position
+    __device__ uint64_t value(uint64_t i) const { return perm ? __ldg(w + __ldg(perm + i)) : __ldg(w + i); }
     __device__ bool head(uint64_t i) const
     {
         if (i == 0) return true;
@@ -375,7 +380,8 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     OwnerBits ob;
     rc = owner_bits(ctx, ob);
     if (rc) return rc;
-    uint64_t *w[2];
+    uint64_t *w[2], *pw[2] = {nullptr, nullptr};
+    uint8_t *pend = nullptr;
     w[0] = (uint64_t *)salloc(ctx, (size_t)(m ? m : 1) * 8);
     w[1] = (uint64_t *)salloc(ctx, (size_t)(m ? m : 1) * 8);
     if (!w[0] || !w[1]) return TM_E_NOMEM;
@@ -388,9 +394,32 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
             if (P.height[q] == h) order.push_back(q);
     if (P.tleaf[0]) order.push_back(0);   // single-edge motif: the root is a leaf
     for (int q : order) {
+        // sides of q that children meet; the weights come out in the order of
+        // the last side run (out-list order for side 0, in-list for side 1)
+        bool has[2] = {false, false};
+        for (int ci = 0; ci < P.nchild[q]; ++ci) has[P.tzside[P.child[q][ci]]] = true;
+        const bool in_order = has[1];
         {
             PhaseScope ph(ctx, TM_PH_DP);
-            if (m) launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, q, cp, w[0], w[1], ctx->status);
+            if (has[0] && has[1] && !pw[0]) {
+                pw[0] = (uint64_t *)salloc(ctx, (size_t)(m ? m : 1) * 8);
+                pw[1] = (uint64_t *)salloc(ctx, (size_t)(m ? m : 1) * 8);
+                pend = (uint8_t *)salloc(ctx, (size_t)(m ? m : 1) * 2);
+                if (!pw[0] || !pw[1] || !pend) return TM_E_NOMEM;
+            }
+            if (m) {
+                if (has[0] && has[1]) {
+                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, q, 0, 1, 0, cp, pw[0], pw[1],
+                           (const uint64_t *)nullptr, (const uint64_t *)nullptr, (const uint8_t *)nullptr, pend,
+                           ctx->status);
+                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, q, 1, 0, 1, cp, w[0], w[1], (const uint64_t *)pw[0],
+                           (const uint64_t *)pw[1], (const uint8_t *)pend, (uint8_t *)nullptr, ctx->status);
+                } else {
+                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, q, in_order ? 1 : 0, 1, 1, cp, w[0], w[1],
+                           (const uint64_t *)nullptr, (const uint64_t *)nullptr, (const uint8_t *)nullptr,
+                           (uint8_t *)nullptr, ctx->status);
+                }
+            }
         }
         rc = check_cuda(ctx, cudaGetLastError(), "weight DP");
         if (rc) return rc;
@@ -398,7 +427,7 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
             PhaseScope ph(ctx, TM_PH_ROOT);
             for (int p = 0; p < 2; ++p) {
                 LayerData &L = mo->layer[p];
-                RootScan f{w[p], g.g_t, p, d};
+                RootScan f{w[p], g.g_t, p, d, in_order ? g.in_pos : g.out_pos};
                 rc = segmented_scan_u64(ctx, f, m, L.root_cdf);
                 if (rc) return rc;
             }
@@ -406,12 +435,15 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
             PhaseScope ph(ctx, TM_PH_PREFIX);
             int slot = P.tslot[q];
             bool out = P.tout[q] != 0;
+            // scan order of the parent's candidate list -> position of the weight
+            const uint32_t *dmap = (out == !in_order) ? nullptr : (out ? g.out_to_in : g.in_to_out);
+            const uint32_t *mmap = in_order ? g.multi_to_in : g.multi_to_out;
             for (int p = 0; p < 2; ++p) {
                 LayerData &L = mo->layer[p];
-                DirScan fd{w[p], out ? g.out_gid : g.in_gid, out ? g.out_t : g.in_t, out ? ob.out : ob.in, p, d};
+                DirScan fd{w[p], dmap, out ? g.out_t : g.in_t, out ? ob.out : ob.in, p, d};
                 rc = segmented_scan_u64(ctx, fd, m, L.pref_dir[slot]);
                 if (rc) return rc;
-                DirScan fm{w[p], g.multi_gid, g.multi_t, ob.multi, p, d};
+                DirScan fm{w[p], mmap, g.multi_t, ob.multi, p, d};
                 rc = segmented_scan_u64(ctx, fm, m, L.pref_multi[slot]);
                 if (rc) return rc;
                 cp.pd[p][slot] = L.pref_dir[slot];
@@ -457,7 +489,7 @@ int export_weights(tm_ctx *ctx, tm_motif *mo, int q, int layer, uint64_t *host_o
     if (P.tleaf[q] && q != 0) {
         launch(ctx, k_leaf_weights, blocks_for(m, TB), TB, g.g_t, m, layer, P.delta, out);
     } else if (q == 0) {
-        RootScan f{nullptr, g.g_t, layer, P.delta};
+        RootScan f{nullptr, g.g_t, layer, P.delta, nullptr};
         launch(ctx, k_unprefix<RootScan>, blocks_for(m, TB), TB, f, mo->layer[layer].root_cdf, nullptr, m, out);
     } else {
         OwnerBits ob;
