@@ -267,8 +267,8 @@ enum {
     /* parts of TM_PH_CSR (also counted in it) */
     TM_PH_CSR_STATS = 8,   /* input checks, t range, compaction             */
     TM_PH_CSR_GLOBAL = 9,  /* sort into (t', src, dst) order and duplicates */
-    TM_PH_CSR_OUT = 10,    /* out-lists                                     */
-    TM_PH_CSR_IN = 11,     /* in-lists                                      */
+    TM_PH_CSR_OUT = 10,    /* out- and in-list sort (one two-array sort)    */
+    TM_PH_CSR_IN = 11,     /* out- and in-list gathers and offsets          */
     TM_PH_CSR_MULTI = 12,  /* multi-edge lists and pair tables              */
     TM_NUM_PHASES = 13
 };

@@ -6,7 +6,7 @@
 //   in-lists    (dst | t', src)      -> in_off / in_t / in_nbr / in_gid
 //   multi-edge  (src, dst | t')      -> pairs, pair_off / multi_t / multi_gid
 // with t' = t - t_min.  Every ordering comes from a stable LSD radix sort
-// (8-bit digits) written here; the OUT and IN orders are stable re-sorts of
+// (up to 9-bit digits) written here; the OUT and IN orders are stable re-sorts of
 // the GLOBAL order by one endpoint, and the multi-edge order is a stable
 // re-sort of the IN order by source.
 #include <cuda_runtime.h>
@@ -30,9 +30,10 @@ namespace {
 //   1. per-tile digit counts (4096 keys per tile), stored digit-major;
 //   2. an exclusive scan of those counts, which gives, for every (digit,
 //      tile), where the tile's run of that digit starts in the output;
-//   3. the scatter: each tile ranks its keys stably (per warp with
-//      __match_any_sync, then across warps), reorders them by digit in shared
-//      memory and writes each digit's run out contiguously.
+//   3. the scatter: each tile ranks its keys stably (per warp, by one ballot
+//      per digit bit, or at once when the warp's digits agree; then across
+//      warps), reorders them by digit in shared memory and writes each
+//      digit's run out contiguously.
 // No block waits on another.
 constexpr int OS_THREADS = 256;
 constexpr int OS_ITEMS = 16;
@@ -42,22 +43,43 @@ constexpr int OS_WCHUNK = OS_ITEMS * 32;           // keys per warp chunk
 constexpr int OS_MAXBITS = 9;
 constexpr int OS_MAXRADIX = 1 << OS_MAXBITS;
 constexpr int OS_MAXPASS = 4;
-constexpr size_t OS_SMEM = (size_t)OS_TILE * 4 * 3 + (size_t)OS_TILE * 2 + (size_t)OS_WARPS * OS_MAXRADIX * 2 +
-                           (size_t)OS_MAXRADIX * 4 * 2;
-
-// per-tile digit counts, written to counts[d * ntiles + tile]
-__global__ void __launch_bounds__(OS_THREADS) k_rs_count(const uint32_t *__restrict__ kin, uint32_t n, int shift,
-                                                          int bits, uint32_t ntiles, uint32_t *__restrict__ counts)
+// dynamic shared memory of a scatter pass with np payload arrays
+constexpr size_t os_smem(int np)
 {
-    __shared__ uint32_t h[OS_MAXRADIX];
+    return (size_t)OS_TILE * 4 * (1 + np) + (size_t)OS_TILE * 2 + (size_t)OS_WARPS * OS_MAXRADIX * 2 +
+           (size_t)OS_MAXRADIX * 4 * 2;
+}
+
+// per-tile digit counts, written to counts[d * ntiles + tile].  Each warp
+// counts into its own histogram with shared atomics; a warp whose 32 digits
+// agree (sorted or nearly sorted input) adds once.
+// Up to two independent arrays of the same length sorted by the same passes:
+// blocks [0, ntiles) work on set 0, blocks [ntiles, 2 ntiles) on set 1.  The
+// counts of set 1 follow those of set 0, so after one exclusive scan over
+// both, set 1's output offsets are shifted by exactly n.
+struct RsSet {
+    const uint32_t *kin, *p0in, *p1in;
+    uint32_t *kout, *p0out, *p1out;
+};
+struct RsJobs {
+    RsSet s[2];
+};
+
+__global__ void __launch_bounds__(OS_THREADS, 6) k_rs_count(RsJobs J, uint32_t n, int shift, int bits, uint32_t ntiles,
+                                                             uint32_t *__restrict__ counts_all)
+{
+    const uint32_t job = blockIdx.x >= ntiles ? 1u : 0u, tile = blockIdx.x - job * ntiles;
+    const uint32_t *__restrict__ kin = job ? J.s[1].kin : J.s[0].kin;
+    uint32_t *__restrict__ counts = counts_all + ((size_t)job * ntiles << bits);
+    __shared__ uint32_t h[OS_WARPS][OS_MAXRADIX];
     const uint32_t radix = 1u << bits, dmask = radix - 1u;
-    for (uint32_t d = threadIdx.x; d < radix; d += OS_THREADS) h[d] = 0;
+    for (uint32_t i = threadIdx.x; i < (uint32_t)(OS_WARPS * OS_MAXRADIX); i += OS_THREADS) (&h[0][0])[i] = 0;
     __syncthreads();
-    const uint32_t lt = (1u << (threadIdx.x & 31)) - 1u;
-    const uint32_t base = blockIdx.x * OS_TILE;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t base = tile * OS_TILE;
     uint32_t kv[OS_ITEMS];
 #pragma unroll
-    for (int j = 0; j < OS_ITEMS; ++j) {   // all loads in flight before any vote
+    for (int j = 0; j < OS_ITEMS; ++j) {   // all loads in flight before any count
         const uint32_t i = base + j * OS_THREADS + threadIdx.x;
         kv[j] = i < n ? __ldg(kin + i) : 0u;
     }
@@ -66,11 +88,20 @@ __global__ void __launch_bounds__(OS_THREADS) k_rs_count(const uint32_t *__restr
         const uint32_t i = base + j * OS_THREADS + threadIdx.x;
         const bool valid = i < n;
         const uint32_t d = valid ? ((kv[j] >> shift) & dmask) : radix;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (valid && (peers & lt) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
+        const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+        if (__all_sync(0xffffffffu, d == d0)) {
+            if (lane == 0 && d0 < radix) atomicAdd(&h[warp][d0], 32u);
+        } else if (valid) {
+            atomicAdd(&h[warp][d], 1u);
+        }
     }
     __syncthreads();
-    for (uint32_t d = threadIdx.x; d < radix; d += OS_THREADS) counts[(size_t)d * ntiles + blockIdx.x] = h[d];
+    for (uint32_t d = threadIdx.x; d < radix; d += OS_THREADS) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < OS_WARPS; ++w) c += h[w][d];
+        counts[(size_t)d * ntiles + tile] = c;
+    }
 }
 
 // block-wide exclusive scan of two values per thread (512 entries)
@@ -100,47 +131,67 @@ __device__ __forceinline__ void os_block_scan512(uint32_t *vals /* smem [512] in
     __syncthreads();
 }
 
+// Keys (and payloads) of one tile are ranked stably per warp chunk: a warp
+// whose 32 digits agree takes its ranks directly; otherwise the lanes with
+// the same digit are found with one ballot per digit bit.
 template <int NP>
-__global__ void __launch_bounds__(OS_THREADS) k_rs_scatter(const uint32_t *__restrict__ kin,
-                                                          const uint32_t *__restrict__ p0in,
-                                                          const uint32_t *__restrict__ p1in, uint32_t *__restrict__ kout,
-                                                          uint32_t *__restrict__ p0out, uint32_t *__restrict__ p1out,
-                                                          uint32_t n, int shift, int bits, uint32_t ntiles,
-                                                          const uint32_t *__restrict__ offs)
+__global__ void __launch_bounds__(OS_THREADS, NP >= 2 ? 3 : 4)
+    k_rs_scatter(RsJobs J, uint32_t n, int shift, int bits, uint32_t ntiles, const uint32_t *__restrict__ offs_all)
 {
-    extern __shared__ __align__(16) unsigned char os_smem[];
-    uint32_t *s_key = reinterpret_cast<uint32_t *>(os_smem);
+    const uint32_t job = blockIdx.x >= ntiles ? 1u : 0u, tile = blockIdx.x - job * ntiles;
+    // per-field selects keep the parameter block out of local memory
+    const uint32_t *__restrict__ kin = job ? J.s[1].kin : J.s[0].kin;
+    const uint32_t *__restrict__ p0in = job ? J.s[1].p0in : J.s[0].p0in;
+    const uint32_t *__restrict__ p1in = job ? J.s[1].p1in : J.s[0].p1in;
+    uint32_t *__restrict__ kout = job ? J.s[1].kout : J.s[0].kout;
+    uint32_t *__restrict__ p0out = job ? J.s[1].p0out : J.s[0].p0out;
+    uint32_t *__restrict__ p1out = job ? J.s[1].p1out : J.s[0].p1out;
+    const uint32_t *__restrict__ offs = offs_all + ((size_t)job * ntiles << bits);
+    const uint32_t bias = job * n;   // set 1's scanned offsets start at n
+    extern __shared__ __align__(16) unsigned char os_smem_buf[];
+    uint32_t *s_key = reinterpret_cast<uint32_t *>(os_smem_buf);
     uint32_t *s_p0 = s_key + OS_TILE;
-    uint32_t *s_p1 = s_p0 + OS_TILE;
-    uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_p1 + OS_TILE);
+    uint32_t *s_p1 = s_p0 + (NP >= 1 ? OS_TILE : 0);
+    uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_p1 + (NP >= 2 ? OS_TILE : 0));
     uint16_t *s_wcnt = s_rank + OS_TILE;                                            // [warp][digit]
     uint32_t *s_tex = reinterpret_cast<uint32_t *>(s_wcnt + OS_WARPS * OS_MAXRADIX);  // digit start in the tile
     uint32_t *s_gpos = s_tex + OS_MAXRADIX;                                         // digit start in the output
     __shared__ uint32_t s_wt[OS_WARPS];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const uint32_t radix = 1u << bits, dmask = radix - 1u;
-    const uint32_t tile = blockIdx.x;
     const uint32_t base = tile * OS_TILE;
     for (int i = t; i < OS_WARPS * OS_MAXRADIX; i += OS_THREADS) s_wcnt[i] = 0;
     for (uint32_t d = t; d < (uint32_t)OS_MAXRADIX; d += OS_THREADS)
-        s_gpos[d] = d < radix ? __ldg(offs + (size_t)d * ntiles + tile) : 0u;
-    __syncthreads();
+        s_gpos[d] = d < radix ? __ldg(offs + (size_t)d * ntiles + tile) - bias : 0u;
     const uint32_t lt = (1u << lane) - 1u;
-    // ---- rank inside each warp's chunk (order: warp, item, lane)
     uint16_t *wc = s_wcnt + warp * OS_MAXRADIX;
-    uint32_t kv[OS_ITEMS];
+    constexpr int NA = NP >= 1 ? OS_ITEMS : 1, NB = NP >= 2 ? OS_ITEMS : 1;
+    uint32_t kv[OS_ITEMS], av[NA], bv[NB];
 #pragma unroll
-    for (int j = 0; j < OS_ITEMS; ++j) {   // all loads in flight before any vote
+    for (int j = 0; j < OS_ITEMS; ++j) {   // keys and payloads in flight before any vote
         const uint32_t i = base + warp * OS_WCHUNK + j * 32 + lane;
         kv[j] = i < n ? __ldg(kin + i) : 0u;
+        if (NP >= 1) av[j % NA] = i < n ? __ldg(p0in + i) : 0u;
+        if (NP >= 2) bv[j % NB] = i < n ? __ldg(p1in + i) : 0u;
     }
+    __syncthreads();
+    // ---- rank inside each warp's chunk (order: warp, item, lane)
 #pragma unroll
     for (int j = 0; j < OS_ITEMS; ++j) {
         const uint32_t li = warp * OS_WCHUNK + j * 32 + lane;
-        const uint32_t i = base + li;
-        const bool valid = i < n;
+        const bool valid = base + li < n;
         const uint32_t d = valid ? ((kv[j] >> shift) & dmask) : radix;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t peers;
+        if (__all_sync(0xffffffffu, d == __shfl_sync(0xffffffffu, d, 0))) {
+            peers = 0xffffffffu;
+        } else {
+            peers = __ballot_sync(0xffffffffu, valid);
+            if (!valid) peers = ~peers;
+            for (int b = 0; b < bits; ++b) {
+                const uint32_t bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+                peers &= ((d >> b) & 1u) ? bb : ~bb;
+            }
+        }
         uint32_t cur = valid ? wc[d] : 0;
         __syncwarp();
         if (valid) {
@@ -167,17 +218,13 @@ __global__ void __launch_bounds__(OS_THREADS) k_rs_scatter(const uint32_t *__res
 #pragma unroll
     for (int j = 0; j < OS_ITEMS; ++j) {
         const uint32_t li = warp * OS_WCHUNK + j * 32 + lane;
-        const uint32_t i = base + li;
-        uint32_t a = 0, b = 0;
-        if (NP >= 1 && i < n) a = __ldg(p0in + i);
-        if (NP >= 2 && i < n) b = __ldg(p1in + i);
-        if (i < n) {
+        if (base + li < n) {
             const uint32_t k = kv[j];
             const uint32_t d = (k >> shift) & dmask;
             const uint32_t pos = s_tex[d] + s_wcnt[warp * OS_MAXRADIX + d] + s_rank[li];
             s_key[pos] = k;
-            if (NP >= 1) s_p0[pos] = a;
-            if (NP >= 2) s_p1[pos] = b;
+            if (NP >= 1) s_p0[pos] = av[j % NA];
+            if (NP >= 2) s_p1[pos] = bv[j % NB];
         }
     }
     __syncthreads();
@@ -200,57 +247,80 @@ int bits_for(uint64_t maxval)
     return b;
 }
 
-// Stable LSD sort of (key, p0[, p1]) by the low `bits` bits of key; on return
-// the sorted data is in key/p0/p1 (the caller's buffers).
-int radix_sort(tm_ctx *ctx, uint32_t *key, uint32_t *p0, uint32_t *p1, uint32_t n, int bits)
+// Stable LSD sort of (key, p0[, p1]) by the low `bits` bits of key, for one
+// or two independent arrays of the same length (same payload count), sorted
+// by the same launches; on return the sorted data is in the caller's buffers.
+struct RsHost {
+    uint32_t *key, *p0, *p1;
+};
+
+int radix_sort_sets(tm_ctx *ctx, const RsHost *sets, int nsets, uint32_t n, int bits)
 {
     ScratchScope scope(ctx);
-    if (n <= 1 || bits <= 0) return TM_OK;
-    const int np = p1 ? 2 : (p0 ? 1 : 0);
+    if (n <= 1 || bits <= 0 || nsets <= 0) return TM_OK;
+    if (nsets > 2) return set_err(ctx, TM_E_LIMIT, "at most two arrays per radix sort");
+    const int np = sets[0].p1 ? 2 : (sets[0].p0 ? 1 : 0);
     const int npass = (bits + OS_MAXBITS - 1) / OS_MAXBITS;
     if (npass > OS_MAXPASS) return set_err(ctx, TM_E_LIMIT, "radix key wider than 36 bits");
     const uint32_t ntiles = (n + OS_TILE - 1) / OS_TILE;
-    uint32_t *counts = (uint32_t *)salloc(ctx, (size_t)ntiles * OS_MAXRADIX * 4);
-    uint32_t *k2 = (uint32_t *)salloc(ctx, (size_t)n * 4);
-    uint32_t *a2 = np >= 1 ? (uint32_t *)salloc(ctx, (size_t)n * 4) : nullptr;
-    uint32_t *b2 = np >= 2 ? (uint32_t *)salloc(ctx, (size_t)n * 4) : nullptr;
-    if (!counts || !k2 || (np >= 1 && !a2) || (np >= 2 && !b2)) return TM_E_NOMEM;
+    uint32_t *counts = (uint32_t *)salloc(ctx, (size_t)nsets * ntiles * OS_MAXRADIX * 4);
+    if (!counts) return TM_E_NOMEM;
+    RsJobs in{};
+    for (int j = 0; j < nsets; ++j) {
+        uint32_t *k2 = (uint32_t *)salloc(ctx, (size_t)n * 4);
+        uint32_t *a2 = np >= 1 ? (uint32_t *)salloc(ctx, (size_t)n * 4) : nullptr;
+        uint32_t *b2 = np >= 2 ? (uint32_t *)salloc(ctx, (size_t)n * 4) : nullptr;
+        if (!k2 || (np >= 1 && !a2) || (np >= 2 && !b2)) return TM_E_NOMEM;
+        in.s[j] = RsSet{sets[j].key, sets[j].p0, sets[j].p1, k2, a2, b2};
+    }
     {
         // per device and cheap: set on every call
-        cudaError_t e = np == 0 ? cudaFuncSetAttribute(k_rs_scatter<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OS_SMEM)
-                      : np == 1 ? cudaFuncSetAttribute(k_rs_scatter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OS_SMEM)
-                                : cudaFuncSetAttribute(k_rs_scatter<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OS_SMEM);
+        cudaError_t e = np == 0 ? cudaFuncSetAttribute(k_rs_scatter<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem(0))
+                      : np == 1 ? cudaFuncSetAttribute(k_rs_scatter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem(1))
+                                : cudaFuncSetAttribute(k_rs_scatter<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem(2));
         int rc = check_cuda(ctx, e, "radix pass shared memory");
         if (rc) return rc;
     }
     cudaStream_t st = ctx->stream;
-    uint32_t *ki = key, *ai = p0, *bi = p1, *ko = k2, *ao = a2, *bo = b2;
+    const unsigned nblk = ntiles * (unsigned)nsets;
     int rc = TM_OK;
     for (int pass = 0, sh = 0; pass < npass && rc == TM_OK; ++pass) {
         const int left = npass - pass, pb = (bits - sh + left - 1) / left;
-        const uint64_t ncount = (uint64_t)ntiles << pb;
-        launch(ctx, k_rs_count, ntiles, OS_THREADS, ki, n, sh, pb, ntiles, counts);
+        const uint64_t ncount = ((uint64_t)ntiles << pb) * (uint64_t)nsets;
+        launch(ctx, k_rs_count, nblk, OS_THREADS, in, n, sh, pb, ntiles, counts);
         rc = exclusive_scan_u32(ctx, counts, counts, ncount, nullptr);
         if (rc) break;
         ++ctx->kernel_launches;
         if (np == 0)
-            k_rs_scatter<0><<<ntiles, OS_THREADS, OS_SMEM, st>>>(ki, nullptr, nullptr, ko, nullptr, nullptr, n, sh, pb,
-                                                                ntiles, counts);
+            k_rs_scatter<0><<<nblk, OS_THREADS, os_smem(0), st>>>(in, n, sh, pb, ntiles, counts);
         else if (np == 1)
-            k_rs_scatter<1><<<ntiles, OS_THREADS, OS_SMEM, st>>>(ki, ai, nullptr, ko, ao, nullptr, n, sh, pb, ntiles,
-                                                                counts);
+            k_rs_scatter<1><<<nblk, OS_THREADS, os_smem(1), st>>>(in, n, sh, pb, ntiles, counts);
         else
-            k_rs_scatter<2><<<ntiles, OS_THREADS, OS_SMEM, st>>>(ki, ai, bi, ko, ao, bo, n, sh, pb, ntiles, counts);
+            k_rs_scatter<2><<<nblk, OS_THREADS, os_smem(2), st>>>(in, n, sh, pb, ntiles, counts);
         rc = check_cuda(ctx, cudaGetLastError(), "radix pass");
-        std::swap(ki, ko); std::swap(ai, ao); std::swap(bi, bo);
+        // the outputs of this pass are the inputs of the next
+        for (int j = 0; j < nsets; ++j) {
+            RsSet &x = in.s[j];
+            RsSet y{x.kout, x.p0out, x.p1out, const_cast<uint32_t *>(x.kin), const_cast<uint32_t *>(x.p0in),
+                    const_cast<uint32_t *>(x.p1in)};
+            x = y;
+        }
         sh += pb;
     }
-    if (rc == TM_OK && ki != key) {
-        cudaMemcpyAsync(key, ki, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
-        if (np >= 1) cudaMemcpyAsync(p0, ai, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
-        if (np >= 2) cudaMemcpyAsync(p1, bi, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+    for (int j = 0; rc == TM_OK && j < nsets; ++j) {
+        const RsSet &x = in.s[j];
+        if (x.kin == sets[j].key) continue;
+        cudaMemcpyAsync(sets[j].key, x.kin, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+        if (np >= 1) cudaMemcpyAsync(sets[j].p0, x.p0in, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+        if (np >= 2) cudaMemcpyAsync(sets[j].p1, x.p1in, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
     }
     return rc;
+}
+
+int radix_sort(tm_ctx *ctx, uint32_t *key, uint32_t *p0, uint32_t *p1, uint32_t n, int bits)
+{
+    RsHost h{key, p0, p1};
+    return radix_sort_sets(ctx, &h, 1, n, bits);
 }
 
 // ---- input validation and t' -------------------------------------------
@@ -332,10 +402,11 @@ __global__ void k_compact3(const uint32_t *__restrict__ a, const uint32_t *__res
     oa[p] = a[i]; ob[p] = b[i]; oc[p] = c[i];
 }
 
-__global__ void k_iota(uint32_t *__restrict__ a, uint32_t m)
+
+__global__ void k_iota2(uint32_t *__restrict__ a, uint32_t *__restrict__ b, uint32_t m)
 {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) a[i] = i;
+    if (i < m) { a[i] = i; b[i] = i; }
 }
 
 __global__ void k_gather2(const uint32_t *__restrict__ idx, uint32_t m, const uint32_t *__restrict__ x,
@@ -542,9 +613,9 @@ int build_csr(tm_ctx *ctx)
     g.m = m;
     g.tmin = tmin;
     g.T = (uint32_t)(tmax - tmin);
-    // scratch key buffer (reuse S0/D0/T0 as work space)
-    uint32_t *key = S0, *tmp = D0;
-    // ---- OUT order: stable sort of gid by src
+    // S0/D0/T0 are reused below as work space
+    // ---- OUT and IN orders: stable sorts of gid by src and by dst, run as
+    // one two-array sort; the sorted keys are out_src and in_dst themselves
     sec.reset();
     sec.reset(new PhaseScope(ctx, TM_PH_CSR_OUT));
     g.out_gid = gtake(gb, m); g.out_t = gtake(gb, m); g.out_nbr = gtake(gb, m); g.out_off = gtake(gb, (size_t)n + 1);
@@ -555,26 +626,22 @@ int build_csr(tm_ctx *ctx)
         !g.out_src || !g.out_pair || !g.in_dst || !g.in_pair || !g.out_xrank || !g.in_xrank || !g.out_pos || !g.in_pos)
         return TM_E_NOMEM;
     if (m) {
-        cudaMemcpyAsync(key, g.g_src, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
-        launch(ctx, k_iota, blocks_for(m, TB), TB, g.out_gid, m);
-        rc = radix_sort(ctx, key, g.out_gid, nullptr, m, vbits);
+        cudaMemcpyAsync(g.out_src, g.g_src, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(g.in_dst, g.g_dst, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
+        launch(ctx, k_iota2, blocks_for(m, TB), TB, g.out_gid, g.in_gid, m);
+        RsHost sets[2] = {{g.out_src, g.out_gid, nullptr}, {g.in_dst, g.in_gid, nullptr}};
+        rc = radix_sort_sets(ctx, sets, 2, m, vbits);
         if (rc) return rc;
-        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.out_gid, m, g.g_t, g.g_dst, g.out_t, g.out_nbr);
-        cudaMemcpyAsync(g.out_src, key, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
     }
-    launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, key, m, n, g.out_off);
-    // ---- IN order: stable sort of gid by dst
     sec.reset();
     sec.reset(new PhaseScope(ctx, TM_PH_CSR_IN));
     if (m) {
-        cudaMemcpyAsync(key, g.g_dst, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
-        launch(ctx, k_iota, blocks_for(m, TB), TB, g.in_gid, m);
-        rc = radix_sort(ctx, key, g.in_gid, nullptr, m, vbits);
-        if (rc) return rc;
+        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.out_gid, m, g.g_t, g.g_dst, g.out_t, g.out_nbr);
         launch(ctx, k_gather2, blocks_for(m, TB), TB, g.in_gid, m, g.g_t, g.g_src, g.in_t, g.in_nbr);
-        cudaMemcpyAsync(g.in_dst, key, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
     }
-    launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, key, m, n, g.in_off);
+    launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, g.out_src, m, n, g.out_off);
+    launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, g.in_dst, m, n, g.in_off);
+    uint32_t *key = S0, *tmp = D0;
     // ---- multi-edge order: stable re-sort of the IN order by source
     sec.reset();
     sec.reset(new PhaseScope(ctx, TM_PH_CSR_MULTI));
