@@ -47,6 +47,13 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-queries", type=int, default=100)
     ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-workload", default="",
+                    help="also serve the motif pool on this workload's graph (e.g. cl200m) in a fresh context")
+    ap.add_argument("--serve-large-queries", type=int, default=300)
+    ap.add_argument("--serve-large-rates", default="50",
+                    help="comma-separated Poisson arrival rates (q/s) for --serve-workload")
+    ap.add_argument("--serve-budget-frac", type=float, default=0.8,
+                    help="weight budget for --serve-workload as a fraction of free device memory after the build")
     ap.add_argument("--alloc", choices=["native", "torch"], default="native",
                     help="device memory: the library's stream-ordered pool or PyTorch's caching allocator")
     return ap.parse_args()
@@ -306,6 +313,8 @@ def run_ours(args, rank, world, local_rank):
         "served": served,
     }
     ctx.close()
+    if args.serve_workload:
+        out["served_large"] = run_served_large(args, tg, synth, dev, stream)
     return out
 
 
@@ -358,7 +367,7 @@ def run_batched(ctx, tg, synth, stream, reps=3):
             "timing": "best of %d, CUDA events on the library stream, weights precomputed" % reps}
 
 
-def run_served(ctx, tg, synth, nq, rate):
+def run_served(ctx, tg, synth, nq, rate, weight_budget=0):
     """Poisson arrivals at `rate` queries/s drawn from the 32-motif pool (k
     log-uniform in [1e4, 1e7]), served by continuous batching with cached
     weights; latency is submit-to-result on the host clock."""
@@ -367,7 +376,7 @@ def run_served(ctx, tg, synth, nq, rate):
     rng = np.random.default_rng(17)
     gaps = rng.exponential(1.0 / rate, size=nq)
     picks = rng.integers(0, len(pool), size=nq)
-    ctx.serve_start(max_active=64)
+    ctx.serve_start(max_active=64, weight_budget=weight_budget)
     tickets = []
     t0 = time.perf_counter()
     due = t0
@@ -388,6 +397,43 @@ def run_served(ctx, tg, synth, nq, rate):
             "completed": st["completed"], "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
             "mean_ms": round(st["mean_ms"], 3), "qps": round(st["qps"], 2), "cache_hits": st["cache_hits"],
             "cache_misses": st["cache_misses"], "evictions": st["evictions"], "rounds": st["rounds"]}
+
+
+def run_served_large(args, tg, synth, dev, stream):
+    """The serving workload on its own graph: build the graph in a fresh
+    context (the CSR build timed with CUDA events), then serve the pool at
+    each requested arrival rate with a weight budget of a fraction of the
+    device memory left after the build."""
+    import numpy as np
+    import torch
+    t0 = time.perf_counter()
+    gr = synth.make_graph(args.serve_workload)
+    gen_s = time.perf_counter() - t0
+    ctx = tg.Context(device=dev.index or 0, stream=stream.cuda_stream, torch_allocator=(args.alloc == "torch"))
+    src_d = torch.from_numpy(gr.src.view(np.int32)).to(dev)
+    dst_d = torch.from_numpy(gr.dst.view(np.int32)).to(dev)
+    t_d = torch.from_numpy(gr.t).to(dev)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.load_graph(gr.n, src_d, dst_d, t_d, flags=tg.TM_DEVICE)
+    e1.record(stream)
+    e1.synchronize()
+    build_ms = e0.elapsed_time(e1)
+    del src_d, dst_d, t_d
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free, total = torch.cuda.mem_get_info(dev)
+    budget = int(free * args.serve_budget_frac)
+    runs = []
+    for rate in [float(x) for x in args.serve_large_rates.split(",") if x]:
+        r = run_served(ctx, tg, synth, args.serve_large_queries, rate, weight_budget=budget)
+        runs.append(r)
+    out = {"workload": args.serve_workload, "n": gr.n, "m": int(ctx.m), "generate_s": round(gen_s, 1),
+           "build_ms": round(build_ms, 2), "weight_budget_bytes": budget,
+           "free_bytes_after_build": int(free), "runs": runs}
+    ctx.close()
+    return out
 
 
 # ------------------------------------------------------------- oracle ----

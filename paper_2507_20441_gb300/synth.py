@@ -61,14 +61,27 @@ def _dedup_key(src: np.ndarray, dst: np.ndarray, n: int) -> np.ndarray:
 
 
 def _unique_tuples(src, dst, t, n):
-    """Drop repeated (u, v, t) tuples, keeping the first occurrence."""
+    """Drop repeated (u, v, t) tuples, keeping the first occurrence.
+
+    A 64-bit mix of (u*n + v, t) finds the few entries whose hash repeats; only
+    those are compared exactly (sorted by tuple, then by position), so every
+    other entry is known unique without a full two-key sort."""
     key = _dedup_key(src, dst, n)
-    order = np.lexsort((t, key))
-    ks, ts = key[order], t[order]
-    keep_sorted = np.ones(order.shape[0], dtype=bool)
-    keep_sorted[1:] = (ks[1:] != ks[:-1]) | (ts[1:] != ts[:-1])
-    keep = np.zeros(order.shape[0], dtype=bool)
-    keep[order[keep_sorted]] = True
+    with np.errstate(over="ignore"):
+        h = key * np.uint64(0x9E3779B97F4A7C15) ^ (t.astype(np.uint64) * np.uint64(0xC2B2AE3D27D4EB4F))
+        h ^= h >> np.uint64(29)
+    hs = np.sort(h)
+    rep = np.unique(hs[1:][hs[1:] == hs[:-1]])
+    if rep.size == 0:
+        return src, dst, t
+    cand = np.nonzero(np.isin(h, rep))[0]
+    ck, ct = key[cand], t[cand]
+    order = np.lexsort((cand, ct, ck))
+    ks, ts = ck[order], ct[order]
+    dup = np.zeros(order.shape[0], dtype=bool)
+    dup[1:] = (ks[1:] == ks[:-1]) & (ts[1:] == ts[:-1])
+    keep = np.ones(src.shape[0], dtype=bool)
+    keep[cand[order[dup]]] = False
     return src[keep], dst[keep], t[keep]
 
 
