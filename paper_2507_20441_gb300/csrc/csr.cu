@@ -593,7 +593,7 @@ int build_csr(tm_ctx *ctx)
         {
             // every m- and n-sized array of the graph in one block
             const size_t mf = (size_t)(m - ndup), a_m = align256((mf ? mf : 1) * 4), a_n = align256(((size_t)n + 1) * 4);
-            if (!gblock_open(ctx, gb, 26 * a_m + 3 * a_n)) return TM_E_NOMEM;
+            if (!gblock_open(ctx, gb, 23 * a_m + 3 * a_n)) return TM_E_NOMEM;
         }
         g.g_t = gtake(gb, m - ndup); g.g_src = gtake(gb, m - ndup); g.g_dst = gtake(gb, m - ndup);
         if (!g.g_t || !g.g_src || !g.g_dst) return TM_E_NOMEM;
@@ -645,19 +645,20 @@ int build_csr(tm_ctx *ctx)
     // ---- multi-edge order: stable re-sort of the IN order by source
     sec.reset();
     sec.reset(new PhaseScope(ctx, TM_PH_CSR_MULTI));
-    g.multi_gid = gtake(gb, m); g.multi_t = gtake(gb, m); g.g_pair = gtake(gb, m); g.multi_pos = gtake(gb, m);
+    g.multi_t = gtake(gb, m); g.g_pair = gtake(gb, m);
+    uint32_t *multi_gid = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);   // edge id per multi position
     g.out_to_in = gtake(gb, m); g.in_to_out = gtake(gb, m); g.multi_to_out = gtake(gb, m); g.multi_to_in = gtake(gb, m);
     g.vpair_off = gtake(gb, (size_t)n + 1);
-    if (!g.multi_gid || !g.multi_t || !g.g_pair || !g.vpair_off || !g.multi_pos || !g.out_to_in || !g.in_to_out ||
+    if (!multi_gid || !g.multi_t || !g.g_pair || !g.vpair_off || !g.out_to_in || !g.in_to_out ||
         !g.multi_to_out || !g.multi_to_in)
         return TM_E_NOMEM;
     uint32_t np = 0;
     if (m) {
         cudaMemcpyAsync(key, g.in_nbr, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync(g.multi_gid, g.in_gid, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
-        rc = radix_sort(ctx, key, g.multi_gid, nullptr, m, vbits);
+        cudaMemcpyAsync(multi_gid, g.in_gid, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
+        rc = radix_sort(ctx, key, multi_gid, nullptr, m, vbits);
         if (rc) return rc;
-        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.multi_gid, m, g.g_t, g.g_dst, g.multi_t, tmp);
+        launch(ctx, k_gather2, blocks_for(m, TB), TB, multi_gid, m, g.g_t, g.g_dst, g.multi_t, tmp);
         // key = pair src, tmp = pair dst per multi position
         uint32_t *head = T0;
         uint32_t *pid = (uint32_t *)salloc(ctx, (size_t)m * 4);
@@ -678,27 +679,21 @@ int build_csr(tm_ctx *ctx)
         g.rev_pair = gtake(pbk, np);
         uint32_t *pair_src = (uint32_t *)salloc(ctx, (size_t)(np ? np : 1) * 4);
         if (!g.pair_off || !g.pair_dst || !g.rev_pair || !pair_src) return TM_E_NOMEM;
-        launch(ctx, k_pair_fill, blocks_for(m, TB), TB, key, tmp, g.multi_gid, head, pid, m, g.pair_off, pair_src,
+        launch(ctx, k_pair_fill, blocks_for(m, TB), TB, key, tmp, multi_gid, head, pid, m, g.pair_off, pair_src,
                                                       g.pair_dst, g.g_pair);
         copy_h2d(ctx, g.pair_off + np, &m, 4);
         launch(ctx, k_offsets, blocks_for((uint64_t)np + 1, TB), TB, pair_src, np, n, g.vpair_off);
         launch(ctx, k_rev_pairs, blocks_for(np, TB), TB, pair_src, g.pair_dst, g.vpair_off, np, g.rev_pair);
-        // pair id of every out-/in-list position (the weight pass walks those lists)
-        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.out_gid, m, g.g_pair, (const uint32_t *)nullptr, g.out_pair,
-               (uint32_t *)nullptr);
-        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.in_gid, m, g.g_pair, (const uint32_t *)nullptr, g.in_pair,
-               (uint32_t *)nullptr);
-        // cross ranks between a vertex's out- and in-lists, and list positions by edge id
-        launch(ctx, k_cross_rank, blocks_for(m, TB), TB, g.out_t, g.out_src, m, g.in_off, g.in_t, g.out_xrank);
-        launch(ctx, k_cross_rank, blocks_for(m, TB), TB, g.in_t, g.in_dst, m, g.out_off, g.out_t, g.in_xrank);
+        // list positions by edge id; then, per out-/in-list position, its pair
+        // id and its position in the other list (one pass over each order)
         launch(ctx, k_inverse, blocks_for(m, TB), TB, g.out_gid, m, g.out_pos);
         launch(ctx, k_inverse, blocks_for(m, TB), TB, g.in_gid, m, g.in_pos);
-        launch(ctx, k_inverse, blocks_for(m, TB), TB, g.multi_gid, m, g.multi_pos);
-        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.out_gid, m, g.in_pos, (const uint32_t *)nullptr, g.out_to_in,
-               (uint32_t *)nullptr);
-        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.in_gid, m, g.out_pos, (const uint32_t *)nullptr, g.in_to_out,
-               (uint32_t *)nullptr);
-        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.multi_gid, m, g.out_pos, g.in_pos, g.multi_to_out, g.multi_to_in);
+        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.out_gid, m, g.g_pair, g.in_pos, g.out_pair, g.out_to_in);
+        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.in_gid, m, g.g_pair, g.out_pos, g.in_pair, g.in_to_out);
+        launch(ctx, k_gather2, blocks_for(m, TB), TB, multi_gid, m, g.out_pos, g.in_pos, g.multi_to_out, g.multi_to_in);
+        // cross ranks between a vertex's out- and in-lists
+        launch(ctx, k_cross_rank, blocks_for(m, TB), TB, g.out_t, g.out_src, m, g.in_off, g.in_t, g.out_xrank);
+        launch(ctx, k_cross_rank, blocks_for(m, TB), TB, g.in_t, g.in_dst, m, g.out_off, g.out_t, g.in_xrank);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "pair tables");
         if (rc) return rc;
     } else {

@@ -276,15 +276,29 @@ __device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &
         // smallest x in [a, b) with F(x) > rc, F(x) = weight of the
         // non-excluded entries in [a, x]
         uint32_t xl = a, xh = b - 1;
-        while (xl < xh) {
-            const uint32_t x = xl + ((xh - xl) >> 1);
-            const uint32_t tx = __ldg(tarr + x), nx = __ldg(nbr + x);
-            uint32_t ce = lower_idx(g.multi_t, ea, eb, tx) - ea;
-            if (ea + ce < eb && __ldg(g.multi_t + ea + ce) == tx && og <= nx) ++ce;
-            uint64_t F;
-            if (leaf) F = (uint64_t)(x - a + 1) - ce;
-            else F = (__ldg(Pd + x) - base) - (ce ? __ldg(Pm + ea + ce - 1) - base_m : 0);
-            if (F > rc) xh = x; else xl = x + 1;
+        if (eb == ea) {
+            // nothing excluded: F(x) = x - a + 1 for a leaf (the pick is
+            // direct), the prefix difference otherwise
+            if (leaf) xl = a + (uint32_t)rc;
+            else
+                while (xl < xh) {
+                    const uint32_t x = xl + ((xh - xl) >> 1);
+                    if (__ldg(Pd + x) - base > rc) xh = x; else xl = x + 1;
+                }
+        } else {
+            while (xl < xh) {
+                const uint32_t x = xl + ((xh - xl) >> 1);
+                const uint32_t tx = __ldg(tarr + x);
+                // excluded entries at or before x: those earlier in time, and
+                // the one at time tx if it sorts at or before x (the list
+                // orders equal times by the other endpoint)
+                uint32_t ce = lower_idx(g.multi_t, ea, eb, tx) - ea;
+                if (ea + ce < eb && __ldg(g.multi_t + ea + ce) == tx && og <= __ldg(nbr + x)) ++ce;
+                uint64_t F;
+                if (leaf) F = (uint64_t)(x - a + 1) - ce;
+                else F = (__ldg(Pd + x) - base) - (ce ? __ldg(Pm + ea + ce - 1) - base_m : 0);
+                if (F > rc) xh = x; else xl = x + 1;
+            }
         }
         const uint32_t cg = __ldg(gids + xl);
         const uint32_t other = __ldg(nbr + xl);

@@ -52,8 +52,7 @@ struct DevGraph {
     uint32_t *pair_dst = nullptr;        // [P]
     uint32_t *pair_off = nullptr;        // [P+1] into multi_*
     uint32_t *rev_pair = nullptr;        // [P] pair (dst,src) or kNone
-    uint32_t *multi_t = nullptr, *multi_gid = nullptr;
-    uint32_t *multi_pos = nullptr;       // [gid] position of the edge in its multi-edge list
+    uint32_t *multi_t = nullptr;
     // position maps between the list orders (same edge): out->in, in->out, multi->out, multi->in
     uint32_t *out_to_in = nullptr, *in_to_out = nullptr, *multi_to_out = nullptr, *multi_to_in = nullptr;
 };
@@ -151,6 +150,9 @@ struct tm_ctx {
     struct ArenaChunk { char *base; size_t size; size_t used; };
     std::vector<ArenaChunk> arena;
     size_t arena_cur = 0;
+    // large blocks freed through dfree, kept for reuse by a later dalloc of a
+    // similar size (stream-ordered on this context's stream)
+    std::vector<std::pair<void *, size_t>> spare;
     timest::Server *server = nullptr;          // serving loop (serve.cu), if running
     int batch_threads = 256;                   // batched sampler shape (set by tm_autotune)
     int batch_smem_recs = 0;
@@ -177,6 +179,7 @@ struct ScratchScope {
     ~ScratchScope();
 };
 void arena_free(tm_ctx *ctx);
+void spare_free(tm_ctx *ctx);
 
 // ---- CSR build (csr.cu) ----
 int build_csr(tm_ctx *ctx);
