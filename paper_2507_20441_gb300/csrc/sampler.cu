@@ -223,8 +223,14 @@ __device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &
     const uint64_t wi = __ldg((p ? J.win_id1 : J.win_id0) + kk);
     const uint64_t d = (uint64_t)P.delta;
     const uint64_t wlo = wi * d, whi = (wi + 2) * d - 1;
-    const uint32_t root = upper_idx64(cdf, wbeg, wend, rr);
-    if (root >= wend) { latch(status, ST_BADSTATE); return -1; }
+    // the root edge lies between two guide entries: the first edges whose CDF
+    // exceeds the bucket bounds below and above rr
+    const uint32_t gsh = __ldg((p ? J.win_gshift1 : J.win_gshift0) + kk);
+    const uint32_t *G = (p ? J.guide1 : J.guide0) + __ldg((p ? J.win_goff1 : J.win_goff0) + kk) + (rr >> gsh);
+    const uint32_t glo = __ldg(G), ghi = __ldg(G + 1);
+    if (glo < wbeg || ghi >= wend || glo > ghi) { latch(status, ST_BADSTATE); return -1; }
+    const uint32_t root = upper_idx64(cdf, glo, ghi + 1, rr);
+    if (root > ghi) { latch(status, ST_BADSTATE); return -1; }
     load_edge(g, root, R, 0);
     for (int q = 1; q < P.ntree; ++q) {
         const int pq = P.tparent[q];
@@ -347,7 +353,7 @@ __device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &
 
 constexpr int kSampleThreads = 256;
 #ifndef TM_SAMPLE_MINB
-#define TM_SAMPLE_MINB 4
+#define TM_SAMPLE_MINB 6   // 40 registers: six blocks of 256 per SM hide more of the search latency
 #endif
 #ifndef TM_RECS_SMEM
 #define TM_RECS_SMEM 0   // per-sample records in local memory: L1 stays large for the searches
@@ -426,7 +432,7 @@ struct BatchQuery {
 };
 
 template <int THREADS, int SMEM_RECS>
-__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_batch(DevGraph g, const BatchQuery *__restrict__ qs,
+__global__ void __launch_bounds__(THREADS, 1536 / THREADS) k_batch(DevGraph g, const BatchQuery *__restrict__ qs,
                                                   const uint32_t *__restrict__ tile_base, uint32_t nq, uint32_t tile,
                                                   uint32_t *counter, Acc *accs, uint32_t *status)
 {
@@ -530,6 +536,9 @@ void fill_job(tm_motif *mo, SampleJob &J, const DevPlan *dplan)
     J.win_beg0 = mo->layer[0].win_beg; J.win_beg1 = mo->layer[1].win_beg;
     J.win_id0 = mo->layer[0].win_id; J.win_id1 = mo->layer[1].win_id;
     J.root_cdf0 = mo->layer[0].root_cdf; J.root_cdf1 = mo->layer[1].root_cdf;
+    J.win_gshift0 = mo->layer[0].win_gshift; J.win_gshift1 = mo->layer[1].win_gshift;
+    J.win_goff0 = mo->layer[0].win_goff; J.win_goff1 = mo->layer[1].win_goff;
+    J.guide0 = mo->layer[0].guide; J.guide1 = mo->layer[1].guide;
     for (int s = 0; s < kMaxTree; ++s) {
         J.pref_dir0[s] = mo->layer[0].pref_dir[s]; J.pref_dir1[s] = mo->layer[1].pref_dir[s];
         J.pref_multi0[s] = mo->layer[0].pref_multi[s]; J.pref_multi1[s] = mo->layer[1].pref_multi[s];

@@ -94,6 +94,12 @@ struct LayerData {
     uint32_t *win_beg = nullptr;         // [nwin+1] gid ranges (win_beg[nwin] = m)
     uint32_t *win_id = nullptr;          // [nwin] window index i
     uint64_t *root_cdf = nullptr;        // [m] running sum of w_c inside its window
+    // guide table of the root search: window kk's draws r in [j 2^s, (j+1) 2^s)
+    // (s = win_gshift[kk]) have their root edge in [guide[o + j], guide[o + j + 1]]
+    // (o = win_goff[kk]); guide[o + j] is the first edge whose CDF exceeds j 2^s
+    uint32_t *win_gshift = nullptr;      // [nwin]
+    uint32_t *win_goff = nullptr;        // [nwin + 1]
+    uint32_t *guide = nullptr;           // [m/4 + 3 nwin + 1]
     uint64_t *pref_dir[kMaxTree] = {};   // per slot: prefix in the out/in order
     uint64_t *pref_multi[kMaxTree] = {}; // per slot: prefix in the multi-edge order
 };
@@ -195,6 +201,7 @@ struct SampleJob {
     uint32_t nwtot, nw0;
     const uint32_t *win_beg0, *win_beg1, *win_id0, *win_id1;
     const uint64_t *root_cdf0, *root_cdf1;
+    const uint32_t *win_gshift0, *win_gshift1, *win_goff0, *win_goff1, *guide0, *guide1;
     const uint64_t *pref_dir0[kMaxTree], *pref_dir1[kMaxTree];
     const uint64_t *pref_multi0[kMaxTree], *pref_multi1[kMaxTree];
     uint64_t W_lo, W_hi;

@@ -245,6 +245,45 @@ __global__ void k_window_cum(const uint64_t *__restrict__ cdf0, const uint32_t *
     }
 }
 
+// ---- guide table of the root search --------------------------------------
+// Window kk of a layer gets about n/4 buckets of width 2^s over its draws
+// [0, W_kk); the table holds, per bucket j, the first edge whose in-window
+// CDF exceeds j 2^s, then the window's last edge.  count[kk] = buckets + 1.
+__device__ __forceinline__ uint64_t ceil_shift(uint64_t c, uint32_t s) { return (c >> s) + ((c & ((1ull << s) - 1)) != 0); }
+
+__global__ void k_guide_setup(const uint64_t *__restrict__ cdf, const uint32_t *__restrict__ win_beg, uint32_t nwin,
+                              uint32_t *__restrict__ gshift, uint32_t *__restrict__ count)
+{
+    const uint32_t kk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kk >= nwin) return;
+    const uint32_t n = win_beg[kk + 1] - win_beg[kk];
+    const uint64_t W = cdf[win_beg[kk + 1] - 1];
+    const uint64_t target = n >> 2 ? n >> 2 : 1;
+    uint32_t sh = 0;
+    while (sh < 63 && W && ((W - 1) >> sh) + 1 > target) ++sh;
+    gshift[kk] = sh;
+    count[kk] = (uint32_t)(W ? ((W - 1) >> sh) + 1 : 0) + 1;
+}
+
+// one thread per edge of the layer's windows: the buckets whose lower bound
+// falls in [cdf[x-1], cdf[x]) start at x
+__global__ void k_guide_fill(const uint64_t *__restrict__ cdf, const uint32_t *__restrict__ t, const uint32_t *__restrict__ flag,
+                             const uint32_t *__restrict__ pos, const uint32_t *__restrict__ win_beg,
+                             const uint32_t *__restrict__ gshift, const uint32_t *__restrict__ goff, uint32_t m, int p,
+                             int64_t d, uint32_t *__restrict__ guide)
+{
+    const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= m || layer_window(t[x], p, d) < 0) return;
+    const uint32_t kk = pos[x] + flag[x] - 1;
+    const uint32_t wbeg = win_beg[kk], wend = win_beg[kk + 1];
+    const uint32_t sh = gshift[kk];
+    uint32_t *G = guide + goff[kk];
+    const uint64_t c1 = cdf[x], c0 = x > wbeg ? cdf[x - 1] : 0;
+    const uint64_t j1 = ceil_shift(c1, sh);
+    for (uint64_t j = ceil_shift(c0, sh); j < j1; ++j) G[j] = x;
+    if (x == wend - 1) G[j1] = x;
+}
+
 __global__ void k_owner_bits(const uint32_t *__restrict__ off, uint32_t nown, uint32_t m, uint32_t *__restrict__ bits)
 {
     uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -349,8 +388,10 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     {
         auto al = [](size_t b) { return (b + 255) / 256 * 256; };
         const size_t mm = (size_t)(m ? m : 1);
-        size_t total = al(((size_t)nwh[0] + 1) * 4) * 2 + al(((size_t)nwh[1] + 1) * 4) * 2 + 2 * al(mm * 8) +
-                       (size_t)P.nslots * 4 * al(mm * 8) + al(((size_t)nwh[0] + nwh[1] + 1) * 16);
+        auto guide_n = [&](uint32_t nw) { return (size_t)m / 4 + 3 * (size_t)nw + 1; };
+        size_t total = al(((size_t)nwh[0] + 1) * 4) * 4 + al(((size_t)nwh[1] + 1) * 4) * 4 + 2 * al(mm * 8) +
+                       (size_t)P.nslots * 4 * al(mm * 8) + al(((size_t)nwh[0] + nwh[1] + 1) * 16) +
+                       al(guide_n(nwh[0]) * 4) + al(guide_n(nwh[1]) * 4);
         char *blk = (char *)malloc_motif(ctx, mo, total);
         if (!blk) return TM_E_NOMEM;
         size_t off = 0;
@@ -361,6 +402,9 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
             L.win_beg = (uint32_t *)take(((size_t)nwh[p] + 1) * 4);
             L.win_id = (uint32_t *)take(((size_t)nwh[p] + 1) * 4);
             L.root_cdf = (uint64_t *)take(mm * 8);
+            L.win_gshift = (uint32_t *)take(((size_t)nwh[p] + 1) * 4);
+            L.win_goff = (uint32_t *)take(((size_t)nwh[p] + 1) * 4);
+            L.guide = (uint32_t *)take(guide_n(nwh[p]) * 4);
             for (int sl = 0; sl < P.nslots; ++sl) {
                 L.pref_dir[sl] = (uint64_t *)take(mm * 8);
                 L.pref_multi[sl] = (uint64_t *)take(mm * 8);
@@ -430,6 +474,14 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
                 RootScan f{w[p], g.g_t, p, d, in_order ? g.in_pos : g.out_pos};
                 rc = segmented_scan_u64(ctx, f, m, L.root_cdf);
                 if (rc) return rc;
+                if (L.nwin) {
+                    launch(ctx, k_guide_setup, blocks_for(L.nwin, TB), TB, L.root_cdf, L.win_beg, L.nwin, L.win_gshift,
+                           L.win_goff);
+                    rc = exclusive_scan_u32(ctx, L.win_goff, L.win_goff, L.nwin, nullptr);
+                    if (rc) return rc;
+                    launch(ctx, k_guide_fill, blocks_for(m, TB), TB, L.root_cdf, g.g_t, flag[p], pos[p], L.win_beg,
+                           L.win_gshift, L.win_goff, m, p, d, L.guide);
+                }
             }
         } else {
             PhaseScope ph(ctx, TM_PH_PREFIX);
