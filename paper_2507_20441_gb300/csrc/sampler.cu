@@ -306,13 +306,16 @@ __device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &
                 if (F > rc) xh = x; else xl = x + 1;
             }
         }
-        const uint32_t cg = __ldg(gids + xl);
         const uint32_t other = __ldg(nbr + xl);
-        R.gid(q) = cg;
         R.t(q) = __ldg(tarr + xl);
         R.src(q) = out ? zg : other;
         R.dst(q) = out ? other : zg;
-        R.pair(q) = __ldg(g.g_pair + cg);
+        // edge and pair ids are read again only for a node with children (or a trace)
+        if (!leaf || tg_out) {
+            const uint32_t cg = __ldg(gids + xl);
+            R.gid(q) = cg;
+            if (!leaf) R.pair(q) = __ldg(g.g_pair + cg);
+        }
     }
     if (tg_out)
         for (int q = 0; q < P.ntree; ++q) tg_out[q] = R.gid(q);

@@ -251,34 +251,70 @@ __global__ void k_window_cum(const uint64_t *__restrict__ cdf0, const uint32_t *
 // CDF exceeds j 2^s, then the window's last edge.  count[kk] = buckets + 1.
 __device__ __forceinline__ uint64_t ceil_shift(uint64_t c, uint32_t s) { return (c >> s) + ((c & ((1ull << s) - 1)) != 0); }
 
-__global__ void k_guide_setup(const uint64_t *__restrict__ cdf, const uint32_t *__restrict__ win_beg, uint32_t nwin,
-                              uint32_t *__restrict__ gshift, uint32_t *__restrict__ count)
+struct GuideLayer {
+    const uint64_t *cdf;
+    const uint32_t *win_beg, *flag, *pos;
+    uint32_t nwin;
+    uint32_t *gshift, *goff, *guide;
+};
+struct GuideArgs {
+    GuideLayer L[2];
+};
+
+// One block per layer: each thread sizes a contiguous run of windows, then
+// the block turns the counts into the windows' table offsets.
+__global__ void __launch_bounds__(1024) k_guide_setup(GuideArgs A)
 {
-    const uint32_t kk = blockIdx.x * blockDim.x + threadIdx.x;
-    if (kk >= nwin) return;
-    const uint32_t n = win_beg[kk + 1] - win_beg[kk];
-    const uint64_t W = cdf[win_beg[kk + 1] - 1];
-    const uint64_t target = n >> 2 ? n >> 2 : 1;
-    uint32_t sh = 0;
-    while (sh < 63 && W && ((W - 1) >> sh) + 1 > target) ++sh;
-    gshift[kk] = sh;
-    count[kk] = (uint32_t)(W ? ((W - 1) >> sh) + 1 : 0) + 1;
+    __shared__ uint32_t warp_tot[32];
+    const GuideLayer &L = blockIdx.x ? A.L[1] : A.L[0];
+    const uint32_t nw = L.nwin, per = (nw + blockDim.x - 1) / blockDim.x;
+    const uint32_t lo = min(nw, threadIdx.x * per), hi = min(nw, lo + per);
+    uint32_t sum = 0;
+    for (uint32_t kk = lo; kk < hi; ++kk) {
+        const uint32_t n = L.win_beg[kk + 1] - L.win_beg[kk];
+        const uint64_t W = L.cdf[L.win_beg[kk + 1] - 1];
+        const uint64_t target = n >> 2 ? n >> 2 : 1;
+        uint32_t sh = 0;
+        while (sh < 63 && W && ((W - 1) >> sh) + 1 > target) ++sh;
+        L.gshift[kk] = sh;
+        const uint32_t c = (uint32_t)(W ? ((W - 1) >> sh) + 1 : 0) + 1;
+        L.goff[kk] = c;   // count for now, offset below
+        sum += c;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) { const uint32_t c = warp_tot[w]; warp_tot[w] = run; run += c; }
+    }
+    __syncthreads();
+    uint32_t run = warp_tot[warp] + incl - sum;
+    for (uint32_t kk = lo; kk < hi; ++kk) {
+        const uint32_t c = L.goff[kk];
+        L.goff[kk] = run;
+        run += c;
+    }
 }
 
-// one thread per edge of the layer's windows: the buckets whose lower bound
+// one thread per edge and layer (blockIdx.y): the buckets whose lower bound
 // falls in [cdf[x-1], cdf[x]) start at x
-__global__ void k_guide_fill(const uint64_t *__restrict__ cdf, const uint32_t *__restrict__ t, const uint32_t *__restrict__ flag,
-                             const uint32_t *__restrict__ pos, const uint32_t *__restrict__ win_beg,
-                             const uint32_t *__restrict__ gshift, const uint32_t *__restrict__ goff, uint32_t m, int p,
-                             int64_t d, uint32_t *__restrict__ guide)
+__global__ void k_guide_fill(GuideArgs A, const uint32_t *__restrict__ t, uint32_t m, int64_t d)
 {
     const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = blockIdx.y;
     if (x >= m || layer_window(t[x], p, d) < 0) return;
-    const uint32_t kk = pos[x] + flag[x] - 1;
-    const uint32_t wbeg = win_beg[kk], wend = win_beg[kk + 1];
-    const uint32_t sh = gshift[kk];
-    uint32_t *G = guide + goff[kk];
-    const uint64_t c1 = cdf[x], c0 = x > wbeg ? cdf[x - 1] : 0;
+    const GuideLayer &L = p ? A.L[1] : A.L[0];
+    const uint32_t kk = L.pos[x] + L.flag[x] - 1;
+    const uint32_t wbeg = L.win_beg[kk], wend = L.win_beg[kk + 1];
+    const uint32_t sh = L.gshift[kk];
+    uint32_t *G = L.guide + L.goff[kk];
+    const uint64_t c1 = L.cdf[x], c0 = x > wbeg ? L.cdf[x - 1] : 0;
     const uint64_t j1 = ceil_shift(c1, sh);
     for (uint64_t j = ceil_shift(c0, sh); j < j1; ++j) G[j] = x;
     if (x == wend - 1) G[j1] = x;
@@ -469,19 +505,18 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
         if (rc) return rc;
         if (q == 0) {
             PhaseScope ph(ctx, TM_PH_ROOT);
+            GuideArgs ga{};
             for (int p = 0; p < 2; ++p) {
                 LayerData &L = mo->layer[p];
                 RootScan f{w[p], g.g_t, p, d, in_order ? g.in_pos : g.out_pos};
                 rc = segmented_scan_u64(ctx, f, m, L.root_cdf);
                 if (rc) return rc;
-                if (L.nwin) {
-                    launch(ctx, k_guide_setup, blocks_for(L.nwin, TB), TB, L.root_cdf, L.win_beg, L.nwin, L.win_gshift,
-                           L.win_goff);
-                    rc = exclusive_scan_u32(ctx, L.win_goff, L.win_goff, L.nwin, nullptr);
-                    if (rc) return rc;
-                    launch(ctx, k_guide_fill, blocks_for(m, TB), TB, L.root_cdf, g.g_t, flag[p], pos[p], L.win_beg,
-                           L.win_gshift, L.win_goff, m, p, d, L.guide);
-                }
+                ga.L[p] = GuideLayer{L.root_cdf, L.win_beg, flag[p], pos[p], L.nwin, L.win_gshift, L.win_goff, L.guide};
+            }
+            // guide tables of the root search, both layers
+            if (m) {
+                launch(ctx, k_guide_setup, 2, 1024, ga);
+                launch(ctx, k_guide_fill, dim3(blocks_for(m, TB), 2), TB, ga, g.g_t, m, d);
             }
         } else {
             PhaseScope ph(ctx, TM_PH_PREFIX);
