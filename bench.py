@@ -115,6 +115,44 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = {
+    "k_sample": ["sampler.cu", "tm_device.cuh", "tm_internal.h"],
+    "k_dp": ["weights.cu", "tm_device.cuh", "tm_internal.h"],
+}
+
+
+def kernel_source_hash(kernel):
+    """sha256 over the sources that define a kernel (the files in order)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2507_20441_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel, workload):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    from the committed ncu summary profiles/<kernel>_<workload>.md, or None
+    when there is none or the kernel's sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    with open(path) as f:
+        for line in f:
+            line = line.strip().strip("`")
+            for key in ("traffic_bytes_per_launch:", "source_sha256:"):
+                if line.startswith(key):
+                    fields[key[:-1]] = line[len(key):].strip()
+    if fields.get("source_sha256") != kernel_source_hash(kernel):
+        return None
+    try:
+        return int(fields["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 # ------------------------------------------------ algorithmic byte models ----
 def dp_bytes_per_edge(plan_children):
     """Bytes one weight-DP launch must move per edge for a tree node with the
@@ -286,7 +324,8 @@ def run_ours(args, rank, world, local_rank):
     achieved = algo / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "algorithmic_bytes_per_launch": int(algo), "model": model,
+                "traffic": profiled_traffic(kname, args.workload),
+                "algorithmic_bytes_per_launch": int(algo), "model": model,
                 "launch_ms": round(kern_ms, 4)}
 
     batched = None if args.no_batch else run_batched(ctx, tg, synth, stream)
