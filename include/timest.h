@@ -146,6 +146,43 @@ int tm_set_motif(tm_ctx *ctx, uint32_t nv, uint32_t ne, const uint32_t *edges,
  * (Def. 3.5).  Invalidates cached weights.  Errors: TM_E_MOTIF. */
 int tm_set_tree(tm_motif *mo, const uint32_t *tree_edge_ids, uint32_t root_edge);
 
+/* Every spanning tree of motif (nv, ne, edges, order) (the arguments of
+ * tm_set_motif), ranked as in Alg. 7 by constraint looseness (Alg. 8, read
+ * over unordered pairs of tree edges sharing a vertex: sum of
+ * |pi(e1) - pi(e2)| - 1), smallest first, ties to the lexicographically
+ * smallest edge set.  Writes the first min(max_out, total) trees: masks_out[i]
+ * has bit j set when motif edge j is a tree edge, looseness_out[i] its
+ * looseness (either array may be null); *n_total = number of spanning trees.
+ * Host only: no context, no device.  Errors: TM_E_ARG, TM_E_MOTIF. */
+int tm_tree_candidates(uint32_t nv, uint32_t ne, const uint32_t *edges, const uint32_t *order,
+                       uint32_t max_out, uint32_t *masks_out, uint32_t *looseness_out,
+                       uint32_t *n_total);
+
+/* One evaluated (tree, root) candidate of tm_select_tree. */
+typedef struct {
+    uint32_t tree_mask;     /* bit j set: motif edge j is a tree edge        */
+    uint32_t root;          /* root edge (a tree edge)                       */
+    uint32_t looseness;     /* of the tree (Alg. 8)                          */
+    int32_t status;         /* TM_OK, or the weight pass's error (overflow)  */
+    tm_u128 W;              /* exact W of the weight pass (0 on error)       */
+} tm_tree_cand;
+
+/* Spanning tree and root selection (Alg. 7): the n_c trees of least
+ * looseness (order of tm_tree_candidates) are evaluated by the exact W of a
+ * full weight pass on the current graph, each with every tree edge as root
+ * (all_roots != 0) or with the default root of least eccentricity; the
+ * candidate of least W wins (ties: the earlier evaluated, i.e. better ranked
+ * tree, then lower root edge id).  Candidates are evaluated in that order and
+ * recorded in cands[0 .. min(max_cand, evaluated)) when cands is not null;
+ * *n_cand = number evaluated.  *out receives the winning motif with its
+ * weights already computed (free it with tm_motif_free); the others' weights
+ * are freed as the search goes.  A candidate whose weight pass overflows is
+ * skipped.  Errors: TM_E_ARG, TM_E_MOTIF, TM_E_STATE (no preprocessed graph),
+ * TM_E_OVERFLOW (every candidate overflowed), TM_E_NOMEM, TM_E_CUDA. */
+int tm_select_tree(tm_ctx *ctx, uint32_t nv, uint32_t ne, const uint32_t *edges,
+                   const uint32_t *order, int64_t delta, uint32_t n_c, int all_roots,
+                   tm_motif **out, tm_tree_cand *cands, uint32_t max_cand, uint32_t *n_cand);
+
 /* Read the tree plan: order[q] = motif edge sampled q-th (q < nv-1),
  * parent[q] = index in order of its parent (-1 for the root). */
 int tm_motif_plan(tm_motif *mo, int32_t *order, int32_t *parent);

@@ -48,6 +48,11 @@ class tm_u128(C.Structure):
         return int(self.lo) | (int(self.hi) << 64)
 
 
+class tm_tree_cand(C.Structure):
+    _fields_ = [("tree_mask", C.c_uint32), ("root", C.c_uint32), ("looseness", C.c_uint32), ("status", C.c_int32),
+                ("W", tm_u128)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
@@ -121,6 +126,8 @@ def _declare(L):
     L.tm_edges_export.argtypes = [vp, vp, vp, vp]
     L.tm_set_motif.argtypes = [vp, u32, u32, vp, vp, i64, pv]
     L.tm_set_tree.argtypes = [vp, vp, u32]
+    L.tm_tree_candidates.argtypes = [u32, u32, vp, vp, u32, vp, vp, C.POINTER(u32)]
+    L.tm_select_tree.argtypes = [vp, u32, u32, vp, vp, i64, u32, i32, pv, vp, u32, C.POINTER(u32)]
     L.tm_motif_plan.argtypes = [vp, vp, vp]
     L.tm_weights.argtypes = [vp, vp, C.POINTER(tm_u128)]
     L.tm_weights_export.argtypes = [vp, vp, u32, u32, vp]
@@ -287,6 +294,37 @@ def tm_set_tree(ctx, motif, tree, root):
     _check(lib().tm_set_tree(motif, _ptr(tr), int(root)), ctx, "tm_set_tree")
 
 
+def tm_tree_candidates(nv, edges, order):
+    """Every spanning tree, best looseness first: [(edge mask, looseness)]."""
+    e = np.ascontiguousarray(np.array(edges, dtype=np.uint32).reshape(-1))
+    o = np.ascontiguousarray(np.array(order, dtype=np.uint32))
+    total = C.c_uint32()
+    rc = lib().tm_tree_candidates(int(nv), len(o), _ptr(e), _ptr(o), 0, None, None, C.byref(total))
+    if rc != TM_OK:
+        raise TimestError(rc, "tm_tree_candidates")
+    n = total.value
+    masks = np.zeros(max(n, 1), np.uint32); loose = np.zeros(max(n, 1), np.uint32)
+    rc = lib().tm_tree_candidates(int(nv), len(o), _ptr(e), _ptr(o), n, _ptr(masks), _ptr(loose), C.byref(total))
+    if rc != TM_OK:
+        raise TimestError(rc, "tm_tree_candidates")
+    return [(int(masks[i]), int(loose[i])) for i in range(n)]
+
+
+def tm_select_tree(ctx, nv, edges, order, delta, n_c, all_roots=True):
+    """Alg. 7 on the current graph: (winning motif handle, evaluated candidates)."""
+    e = np.ascontiguousarray(np.array(edges, dtype=np.uint32).reshape(-1))
+    o = np.ascontiguousarray(np.array(order, dtype=np.uint32))
+    cap = max(1, int(n_c)) * max(1, int(nv) - 1)
+    cands = (tm_tree_cand * cap)()
+    n = C.c_uint32()
+    h = C.c_void_p()
+    _check(lib().tm_select_tree(ctx, int(nv), len(o), _ptr(e), _ptr(o), int(delta), int(n_c), 1 if all_roots else 0,
+                                C.byref(h), C.cast(cands, C.c_void_p), cap, C.byref(n)), ctx, "tm_select_tree")
+    out = [{"tree_mask": int(c.tree_mask), "root": int(c.root), "looseness": int(c.looseness),
+            "status": int(c.status), "W": c.W.value} for c in cands[:min(n.value, cap)]]
+    return h, out
+
+
 def tm_motif_plan(motif, ntree):
     order = np.zeros(ntree, np.int32); parent = np.zeros(ntree, np.int32)
     rc = lib().tm_motif_plan(motif, _ptr(order), _ptr(parent))
@@ -424,14 +462,14 @@ def tm_io_bytes(ctx):
 # Convenience objects over the same calls
 # ---------------------------------------------------------------------------
 class Motif:
-    def __init__(self, ctx: "Context", nv, edges, order, delta):
+    def __init__(self, ctx: "Context", nv, edges, order, delta, handle=None):
         self.ctx = ctx
         self.nv = int(nv)
         self.ntree = self.nv - 1
         self.edges = list(edges)
         self.order = list(order)
         self.delta = int(delta)
-        self.h = tm_set_motif(ctx.h, nv, edges, order, delta)
+        self.h = handle if handle is not None else tm_set_motif(ctx.h, nv, edges, order, delta)
         ctx._motifs.append(self)
 
     def set_tree(self, tree, root):
@@ -491,6 +529,12 @@ class Context:
 
     def motif(self, nv, edges, order, delta) -> Motif:
         return Motif(self, nv, edges, order, delta)
+
+    def select_tree(self, nv, edges, order, delta, n_c=4, all_roots=True):
+        """Tree and root of least exact W among the n_c best looseness trees
+        (Alg. 7): the winning Motif, weights computed, and the candidates."""
+        h, cands = tm_select_tree(self.h, nv, edges, order, delta, n_c, all_roots)
+        return Motif(self, nv, edges, order, delta, handle=h), cands
 
     # ---- serving (continuous batching); only these calls while serving
     def serve_start(self, **cfg):

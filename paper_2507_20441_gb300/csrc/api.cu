@@ -302,17 +302,29 @@ static int default_root(const MotifDesc &M, const int *edges)
     return best;
 }
 
-static void default_tree(const MotifDesc &M, int *tree_out, int *root_out)
+// Every spanning tree, ranked as in Alg. 7: least looseness first, ties to
+// the lexicographically smallest edge set (the enumeration order, kept by a
+// stable sort).
+struct RankedTree {
+    uint32_t mask;
+    int L;
+    int edges[kMaxTree];
+};
+
+static void rank_trees(const MotifDesc &M, std::vector<RankedTree> &out)
 {
-    int k = M.nv - 1;
+    out.clear();
+    const int k = M.nv - 1;
     int idx[kMaxTree];
     for (int i = 0; i < k; ++i) idx[i] = i;
-    int best = 1 << 30;
     // lexicographic enumeration of k-subsets of the ne edges
     for (;;) {
         if (is_spanning_tree(M, idx)) {
-            int L = looseness(M, idx);
-            if (L < best) { best = L; for (int i = 0; i < k; ++i) tree_out[i] = idx[i]; }
+            RankedTree r;
+            r.mask = 0;
+            for (int i = 0; i < k; ++i) { r.edges[i] = idx[i]; r.mask |= 1u << idx[i]; }
+            r.L = looseness(M, idx);
+            out.push_back(r);
         }
         int i = k - 1;
         while (i >= 0 && idx[i] == M.ne - k + i) --i;
@@ -320,7 +332,40 @@ static void default_tree(const MotifDesc &M, int *tree_out, int *root_out)
         ++idx[i];
         for (int j = i + 1; j < k; ++j) idx[j] = idx[j - 1] + 1;
     }
+    std::stable_sort(out.begin(), out.end(), [](const RankedTree &a, const RankedTree &b) { return a.L < b.L; });
+}
+
+static void default_tree(const MotifDesc &M, int *tree_out, int *root_out)
+{
+    std::vector<RankedTree> R;
+    rank_trees(M, R);   // a connected motif has at least one spanning tree
+    for (int i = 0; i < M.nv - 1; ++i) tree_out[i] = R[0].edges[i];
     *root_out = default_root(M, tree_out);
+}
+
+// Check a motif description (the arguments of tm_set_motif) and fill M.
+static int parse_motif(uint32_t nv, uint32_t ne, const uint32_t *edges, const uint32_t *order, MotifDesc &M,
+                       const char **why)
+{
+    *why = "";
+    if (!edges || !order) { *why = "null motif array"; return TM_E_ARG; }
+    if (nv < 2 || nv > (uint32_t)kMaxV || ne < nv - 1 || ne > (uint32_t)kMaxE) {
+        *why = "motif needs 2..8 vertices and nv-1..16 edges";
+        return TM_E_MOTIF;
+    }
+    M.nv = (int)nv; M.ne = (int)ne;
+    bool seen[kMaxE] = {};
+    for (uint32_t i = 0; i < ne; ++i) {
+        uint32_t a = edges[2 * i], b = edges[2 * i + 1];
+        if (a >= nv || b >= nv || a == b) { *why = "motif edge out of range or self loop"; return TM_E_MOTIF; }
+        if (order[i] >= ne || seen[order[i]]) { *why = "order is not a permutation"; return TM_E_MOTIF; }
+        seen[order[i]] = true;
+        M.a[i] = (int)a; M.b[i] = (int)b; M.rank[i] = (int)order[i];
+    }
+    int all[kMaxE];
+    for (int i = 0; i < M.ne; ++i) all[i] = i;
+    if (!connected(M, all, M.ne)) { *why = "motif is not connected"; return TM_E_MOTIF; }
+    return TM_OK;
 }
 
 // Root the tree at `root` and lay it out in sampling order: breadth first;
@@ -551,38 +596,113 @@ int tm_edges_export(tm_ctx *ctx, uint32_t *src, uint32_t *dst, uint32_t *tprime)
     return check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "edge export");
 }
 
+// A motif planned on (tree, root); nullptr and *rc on failure.
+static tm_motif *new_motif(tm_ctx *ctx, const MotifDesc &M, const int *tree, int root, int64_t delta, int *rc)
+{
+    tm_motif *mo = new tm_motif();
+    mo->ctx = ctx;
+    mo->nv = (uint32_t)M.nv; mo->ne = (uint32_t)M.ne; mo->delta = delta;
+    for (int i = 0; i < M.ne; ++i) { mo->ea[i] = M.a[i]; mo->eb[i] = M.b[i]; mo->rank[i] = M.rank[i]; }
+    for (int i = 0; i < M.nv - 1; ++i) mo->tree[i] = tree[i];
+    mo->root = root;
+    *rc = compile_plan(M, tree, root, delta, mo->plan);
+    if (*rc) { delete mo; return nullptr; }
+    return mo;
+}
+
 int tm_set_motif(tm_ctx *ctx, uint32_t nv, uint32_t ne, const uint32_t *edges, const uint32_t *order, int64_t delta,
                  tm_motif **out)
 {
     if (!ctx || !out || !edges || !order) return TM_E_ARG;
     *out = nullptr;
-    if (nv < 2 || nv > (uint32_t)kMaxV || ne < nv - 1 || ne > (uint32_t)kMaxE)
-        return set_err(ctx, TM_E_MOTIF, "motif needs 2..8 vertices and nv-1..16 edges");
-    if (delta <= 0) return set_err(ctx, TM_E_MOTIF, "delta must be positive");
     MotifDesc M;
-    M.nv = (int)nv; M.ne = (int)ne;
-    bool seen[kMaxE] = {};
-    for (uint32_t i = 0; i < ne; ++i) {
-        uint32_t a = edges[2 * i], b = edges[2 * i + 1];
-        if (a >= nv || b >= nv || a == b) return set_err(ctx, TM_E_MOTIF, "motif edge out of range or self loop");
-        if (order[i] >= ne || seen[order[i]]) return set_err(ctx, TM_E_MOTIF, "order is not a permutation");
-        seen[order[i]] = true;
-        M.a[i] = (int)a; M.b[i] = (int)b; M.rank[i] = (int)order[i];
-    }
-    int all[kMaxE];
-    for (int i = 0; i < M.ne; ++i) all[i] = i;
-    if (!connected(M, all, M.ne)) return set_err(ctx, TM_E_MOTIF, "motif is not connected");
+    const char *why;
+    int rc = parse_motif(nv, ne, edges, order, M, &why);
+    if (rc) return set_err(ctx, rc, why);
+    if (delta <= 0) return set_err(ctx, TM_E_MOTIF, "delta must be positive");
     int tree[kMaxTree], root;
     default_tree(M, tree, &root);
-    tm_motif *mo = new tm_motif();
-    mo->ctx = ctx;
-    mo->nv = nv; mo->ne = ne; mo->delta = delta;
-    for (int i = 0; i < M.ne; ++i) { mo->ea[i] = M.a[i]; mo->eb[i] = M.b[i]; mo->rank[i] = M.rank[i]; }
-    for (int i = 0; i < M.nv - 1; ++i) mo->tree[i] = tree[i];
-    mo->root = root;
-    int rc = compile_plan(M, tree, root, delta, mo->plan);
-    if (rc) { delete mo; return set_err(ctx, rc, "internal: default tree did not compile"); }
+    tm_motif *mo = new_motif(ctx, M, tree, root, delta, &rc);
+    if (!mo) return set_err(ctx, rc, "internal: default tree did not compile");
     *out = mo;
+    return TM_OK;
+}
+
+int tm_tree_candidates(uint32_t nv, uint32_t ne, const uint32_t *edges, const uint32_t *order, uint32_t max_out,
+                       uint32_t *masks_out, uint32_t *looseness_out, uint32_t *n_total)
+{
+    MotifDesc M;
+    const char *why;
+    int rc = parse_motif(nv, ne, edges, order, M, &why);
+    if (rc) return rc;
+    std::vector<RankedTree> R;
+    rank_trees(M, R);
+    for (uint32_t i = 0; i < max_out && i < R.size(); ++i) {
+        if (masks_out) masks_out[i] = R[i].mask;
+        if (looseness_out) looseness_out[i] = (uint32_t)R[i].L;
+    }
+    if (n_total) *n_total = (uint32_t)R.size();
+    return TM_OK;
+}
+
+static bool u128_less(const tm_u128 &a, const tm_u128 &b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+
+int tm_select_tree(tm_ctx *ctx, uint32_t nv, uint32_t ne, const uint32_t *edges, const uint32_t *order, int64_t delta,
+                   uint32_t n_c, int all_roots, tm_motif **out, tm_tree_cand *cands, uint32_t max_cand, uint32_t *n_cand)
+{
+    if (!ctx || !out || !edges || !order) return TM_E_ARG;
+    *out = nullptr;
+    if (n_cand) *n_cand = 0;
+    if (!ctx->preprocessed) return set_err(ctx, TM_E_STATE, "graph not preprocessed");
+    MotifDesc M;
+    const char *why;
+    int rc = parse_motif(nv, ne, edges, order, M, &why);
+    if (rc) return set_err(ctx, rc, why);
+    if (delta <= 0) return set_err(ctx, TM_E_MOTIF, "delta must be positive");
+    std::vector<RankedTree> R;
+    rank_trees(M, R);
+    const size_t ntry = std::min<size_t>(n_c ? n_c : 1, R.size());
+    tm_motif *best = nullptr;
+    tm_u128 bestW{0, 0};
+    uint32_t evaluated = 0;
+    for (size_t t = 0; t < ntry; ++t) {
+        int roots[kMaxTree], nroots = 0;
+        if (all_roots) for (int i = 0; i < M.nv - 1; ++i) roots[nroots++] = R[t].edges[i];   // increasing id
+        else roots[nroots++] = default_root(M, R[t].edges);
+        for (int ri = 0; ri < nroots; ++ri) {
+            tm_motif *mo = new_motif(ctx, M, R[t].edges, roots[ri], delta, &rc);
+            if (!mo) {
+                tm_motif_free(best);
+                return set_err(ctx, rc, "internal: candidate tree did not compile");
+            }
+            tm_u128 W{0, 0};
+            const int crc = tm_weights(ctx, mo, &W);
+            if (cands && evaluated < max_cand) {
+                tm_tree_cand &c = cands[evaluated];
+                c.tree_mask = R[t].mask;
+                c.root = (uint32_t)roots[ri];
+                c.looseness = (uint32_t)R[t].L;
+                c.status = crc;
+                c.W = crc == TM_OK ? W : tm_u128{0, 0};
+            }
+            ++evaluated;
+            if (crc == TM_OK && (!best || u128_less(W, bestW))) {
+                tm_motif_free(best);
+                best = mo;
+                bestW = W;
+                continue;
+            }
+            tm_motif_free(mo);
+            if (crc != TM_OK && crc != TM_E_OVERFLOW) {   // a real failure ends the search
+                tm_motif_free(best);
+                if (n_cand) *n_cand = evaluated;
+                return crc;
+            }
+        }
+    }
+    if (n_cand) *n_cand = evaluated;
+    if (!best) return set_err(ctx, TM_E_OVERFLOW, "every candidate's weight pass overflowed");
+    *out = best;
     return TM_OK;
 }
 
