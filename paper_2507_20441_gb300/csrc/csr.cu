@@ -403,6 +403,14 @@ __global__ void k_compact3(const uint32_t *__restrict__ a, const uint32_t *__res
 }
 
 
+__global__ void k_owner_bits(const uint32_t *__restrict__ off, uint32_t nown, uint32_t m, uint32_t *__restrict__ bits)
+{
+    uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nown) return;
+    uint32_t b = off[v];
+    if (b < m && off[v + 1] > b) atomicOr(bits + (b >> 5), 1u << (b & 31));
+}
+
 __global__ void k_iota2(uint32_t *__restrict__ a, uint32_t *__restrict__ b, uint32_t m)
 {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -593,7 +601,8 @@ int build_csr(tm_ctx *ctx)
         {
             // every m- and n-sized array of the graph in one block
             const size_t mf = (size_t)(m - ndup), a_m = align256((mf ? mf : 1) * 4), a_n = align256(((size_t)n + 1) * 4);
-            if (!gblock_open(ctx, gb, 23 * a_m + 3 * a_n)) return TM_E_NOMEM;
+            const size_t a_b = align256((mf / 32 + 1) * 4);
+            if (!gblock_open(ctx, gb, 23 * a_m + 3 * a_n + 3 * a_b)) return TM_E_NOMEM;
         }
         g.g_t = gtake(gb, m - ndup); g.g_src = gtake(gb, m - ndup); g.g_dst = gtake(gb, m - ndup);
         if (!g.g_t || !g.g_src || !g.g_dst) return TM_E_NOMEM;
@@ -649,8 +658,10 @@ int build_csr(tm_ctx *ctx)
     uint32_t *multi_gid = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);   // edge id per multi position
     g.out_to_in = gtake(gb, m); g.in_to_out = gtake(gb, m); g.multi_to_out = gtake(gb, m); g.multi_to_in = gtake(gb, m);
     g.vpair_off = gtake(gb, (size_t)n + 1);
+    g.own_out = gtake(gb, (size_t)m / 32 + 1); g.own_in = gtake(gb, (size_t)m / 32 + 1);
+    g.own_multi = gtake(gb, (size_t)m / 32 + 1);
     if (!multi_gid || !g.multi_t || !g.g_pair || !g.vpair_off || !g.out_to_in || !g.in_to_out ||
-        !g.multi_to_out || !g.multi_to_in)
+        !g.multi_to_out || !g.multi_to_in || !g.own_out || !g.own_in || !g.own_multi)
         return TM_E_NOMEM;
     uint32_t np = 0;
     if (m) {
@@ -694,6 +705,14 @@ int build_csr(tm_ctx *ctx)
         // cross ranks between a vertex's out- and in-lists
         launch(ctx, k_cross_rank, blocks_for(m, TB), TB, g.out_t, g.out_src, m, g.in_off, g.in_t, g.out_xrank);
         launch(ctx, k_cross_rank, blocks_for(m, TB), TB, g.in_t, g.in_dst, m, g.out_off, g.out_t, g.in_xrank);
+        // owner starts of the three orders (segment heads of the weight pass's scans)
+        const size_t words = (size_t)m / 32 + 1;
+        cudaMemsetAsync(g.own_out, 0, words * 4, st);
+        cudaMemsetAsync(g.own_in, 0, words * 4, st);
+        cudaMemsetAsync(g.own_multi, 0, words * 4, st);
+        launch(ctx, k_owner_bits, blocks_for(n, TB), TB, g.out_off, n, m, g.own_out);
+        launch(ctx, k_owner_bits, blocks_for(n, TB), TB, g.in_off, n, m, g.own_in);
+        if (np) launch(ctx, k_owner_bits, blocks_for(np, TB), TB, g.pair_off, np, m, g.own_multi);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "pair tables");
         if (rc) return rc;
     } else {

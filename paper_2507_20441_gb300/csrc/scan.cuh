@@ -46,10 +46,27 @@ __global__ void k_tile_sum_u32(const uint32_t *__restrict__ in, uint64_t n, uint
 // (or 0 when carry is null); blocked layout (each thread SCAN_ITEMS
 // consecutive values).  Writes the grand total to *total when it is the last
 // tile and total is non-null.
+// With tile_sums non-null the carry-in is instead the sum of the unscanned
+// tile totals tile_sums[0 .. blockIdx.x), added up by the block itself.
 __global__ void k_tile_scan_u32(const uint32_t *__restrict__ in, uint64_t n, const uint32_t *__restrict__ carry,
-                                uint32_t *__restrict__ out, uint32_t *__restrict__ total)
+                                uint32_t *__restrict__ out, uint32_t *__restrict__ total,
+                                const uint32_t *__restrict__ tile_sums = nullptr)
 {
     __shared__ uint32_t warp_tot[SCAN_THREADS / 32];
+    __shared__ uint32_t s_carry;
+    if (tile_sums) {
+        uint32_t c = 0;
+        for (uint32_t i = threadIdx.x; i < blockIdx.x; i += SCAN_THREADS) c += tile_sums[i];
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+        if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int w = 0; w < SCAN_THREADS / 32; ++w) t += warp_tot[w];
+            s_carry = t;
+        }
+        __syncthreads();
+    }
     uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
     uint32_t v[SCAN_ITEMS];
     uint32_t s = 0;
@@ -77,7 +94,7 @@ __global__ void k_tile_scan_u32(const uint32_t *__restrict__ in, uint64_t n, con
         if (lane < SCAN_THREADS / 32) warp_tot[lane] = wi - w;
     }
     __syncthreads();
-    uint32_t run = (carry ? carry[blockIdx.x] : 0) + warp_tot[warp] + incl - s;
+    uint32_t run = (tile_sums ? s_carry : carry ? carry[blockIdx.x] : 0) + warp_tot[warp] + incl - s;
 #pragma unroll
     for (int j = 0; j < SCAN_ITEMS; ++j) {
         uint64_t i = base + j;
@@ -97,16 +114,23 @@ inline int exclusive_scan_u32(tm_ctx *ctx, const uint32_t *in, uint32_t *out, ui
     }
     uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (tiles == 1) {
-        launch(ctx, k_tile_scan_u32, 1, SCAN_THREADS, in, n, nullptr, out, total);
+        launch(ctx, k_tile_scan_u32, 1, SCAN_THREADS, in, n, (const uint32_t *)nullptr, out, total,
+               (const uint32_t *)nullptr);
         return check_cuda(ctx, cudaGetLastError(), "scan");
     }
     ScratchScope scope(ctx);
     uint32_t *ts = (uint32_t *)salloc(ctx, tiles * sizeof(uint32_t));
     if (!ts) return TM_E_NOMEM;
     launch(ctx, k_tile_sum_u32, (unsigned)tiles, SCAN_THREADS, in, n, ts);
+    if (tiles <= 4096) {   // each block adds up the totals before it: two launches in all
+        launch(ctx, k_tile_scan_u32, (unsigned)tiles, SCAN_THREADS, in, n, (const uint32_t *)nullptr, out, total,
+               (const uint32_t *)ts);
+        return check_cuda(ctx, cudaGetLastError(), "scan");
+    }
     int rc = exclusive_scan_u32(ctx, ts, ts, tiles, nullptr);
     if (rc == TM_OK) {
-        launch(ctx, k_tile_scan_u32, (unsigned)tiles, SCAN_THREADS, in, n, ts, out, total);
+        launch(ctx, k_tile_scan_u32, (unsigned)tiles, SCAN_THREADS, in, n, (const uint32_t *)ts, out, total,
+               (const uint32_t *)nullptr);
         rc = check_cuda(ctx, cudaGetLastError(), "scan");
     }
     return rc;

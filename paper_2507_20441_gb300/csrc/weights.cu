@@ -320,14 +320,6 @@ __global__ void k_guide_fill(GuideArgs A, const uint32_t *__restrict__ t, uint32
     if (x == wend - 1) G[j1] = x;
 }
 
-__global__ void k_owner_bits(const uint32_t *__restrict__ off, uint32_t nown, uint32_t m, uint32_t *__restrict__ bits)
-{
-    uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nown) return;
-    uint32_t b = off[v];
-    if (b < m && off[v + 1] > b) atomicOr(bits + (b >> 5), 1u << (b & 31));
-}
-
 // Reconstruct w for one order from its segmented prefix (exports).
 template <class F>
 __global__ void k_unprefix(F f, const uint64_t *__restrict__ pref, const uint32_t *__restrict__ perm, uint32_t m,
@@ -364,28 +356,8 @@ static void free_motif_weights(tm_ctx *ctx, tm_motif *mo)
     mo->have_weights = false;
 }
 
-// Owner bit sets of the out-, in- and multi-edge orders (built on demand,
-// kept with the graph).
-struct OwnerBits { uint32_t *out = nullptr, *in = nullptr, *multi = nullptr; };
-
-static int owner_bits(tm_ctx *ctx, OwnerBits &ob)
-{
-    const DevGraph &g = ctx->g;
-    size_t words = ((size_t)g.m + 31) / 32 + 1;
-    uint32_t **dst[3] = {&ob.out, &ob.in, &ob.multi};
-    const uint32_t *offs[3] = {g.out_off, g.in_off, g.pair_off};
-    uint32_t nown[3] = {g.n, g.n, g.npairs};
-    for (int k = 0; k < 3; ++k) {
-        uint32_t *b = (uint32_t *)salloc(ctx, words * 4);
-        if (!b) return TM_E_NOMEM;
-        cudaMemsetAsync(b, 0, words * 4, ctx->stream);
-        if (nown[k]) launch(ctx, k_owner_bits, blocks_for(nown[k], TB), TB, offs[k], nown[k], g.m, b);
-        *dst[k] = b;
-    }
-    return check_cuda(ctx, cudaGetLastError(), "owner bits");
-}
-
-static void free_owner_bits(tm_ctx *, OwnerBits &ob) { ob = OwnerBits(); }   // scratch: freed by the scope
+// Owner bit sets of the out-, in- and multi-edge orders (built with the graph).
+struct OwnerBits { const uint32_t *out, *in, *multi; };
 
 int compute_weights(tm_ctx *ctx, tm_motif *mo)
 {
@@ -457,9 +429,7 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
         }
     }
     // ---- DP over tree nodes in increasing height (K3) + prefixes (K4)
-    OwnerBits ob;
-    rc = owner_bits(ctx, ob);
-    if (rc) return rc;
+    const OwnerBits ob{g.own_out, g.own_in, g.own_multi};
     uint64_t *w[2], *pw[2] = {nullptr, nullptr};
     uint8_t *pend = nullptr;
     w[0] = (uint64_t *)salloc(ctx, (size_t)(m ? m : 1) * 8);
@@ -538,7 +508,6 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
             }
         }
     }
-    free_owner_bits(ctx, ob);
     // ---- window totals and their 128-bit running sum (K5)
     uint32_t nw0 = mo->layer[0].nwin, nw1 = mo->layer[1].nwin;
     mo->nwtot = nw0 + nw1;
@@ -579,15 +548,12 @@ int export_weights(tm_ctx *ctx, tm_motif *mo, int q, int layer, uint64_t *host_o
         RootScan f{nullptr, g.g_t, layer, P.delta, nullptr};
         launch(ctx, k_unprefix<RootScan>, blocks_for(m, TB), TB, f, mo->layer[layer].root_cdf, nullptr, m, out);
     } else {
-        OwnerBits ob;
-        rc = owner_bits(ctx, ob);
-        if (rc) return rc;
+        const OwnerBits ob{g.own_out, g.own_in, g.own_multi};
         bool o = P.tout[q] != 0;
         DirScan f{nullptr, nullptr, o ? g.out_t : g.in_t, o ? ob.out : ob.in, layer, P.delta};
         launch(ctx, k_unprefix<DirScan>, blocks_for(m, TB), TB, f, mo->layer[layer].pref_dir[P.tslot[q]],
                                                               o ? g.out_gid : g.in_gid, m, out);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "export");
-        free_owner_bits(ctx, ob);
     }
     copy_d2h(ctx, host_out, out, (size_t)m * 8);
     int rc2 = check_cuda(ctx, cudaStreamSynchronize(st), "export copy");
