@@ -205,6 +205,21 @@ int tm_weights_export(tm_ctx *ctx, tm_motif *mo, uint32_t tree_edge, uint32_t la
 int tm_window_totals(tm_ctx *ctx, tm_motif *mo, uint64_t *host_out, uint64_t cap,
                      uint64_t *nwin);
 
+/* Several motifs per sampling run (the paper counts related motifs, e.g.
+ * M4-1..M4-4, from one run): motifs[0..nm), 1 <= nm <= 8, whose spanning
+ * trees (after tm_set_motif / tm_set_tree) are the same temporal pattern -
+ * same vertex count and delta, and per tree node the same endpoint vertex
+ * ids, parent, meeting side, direction, leaf flag and pi relation to its
+ * parent, with the tree edges in the same pi order - share motifs[0]'s
+ * weights (which must be computed) and one stream of sampled trees.  Each
+ * sample is drawn and validated once and completed (Alg. 5) once per motif.
+ * results[i] equals tm_sample(ctx, motifs[i], k, seed, first_index) bit for
+ * bit (W, hits2, counters, estimate).  Errors: TM_E_ARG, TM_E_STATE (no
+ * weights on motifs[0]), TM_E_MOTIF (a tree pattern differs), TM_E_LIMIT
+ * (nm > 8), TM_E_OVERFLOW, TM_E_CUDA. */
+int tm_sample_group(tm_ctx *ctx, tm_motif *const *motifs, uint32_t nm, uint64_t k, uint64_t seed,
+                    uint64_t first_index, tm_result *results);
+
 /* Draw k samples with ids first_index .. first_index+k-1 from seed (Sec. 3.2
  * with the counter-based draw protocol: Philox4x32-10, key = seed, counter =
  * (sample id, draw number)), validate and count them (Sec. 3.3) and reduce

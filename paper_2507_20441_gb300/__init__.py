@@ -127,6 +127,7 @@ def _declare(L):
     L.tm_set_motif.argtypes = [vp, u32, u32, vp, vp, i64, pv]
     L.tm_set_tree.argtypes = [vp, vp, u32]
     L.tm_tree_candidates.argtypes = [u32, u32, vp, vp, u32, vp, vp, C.POINTER(u32)]
+    L.tm_sample_group.argtypes = [vp, vp, u32, u64, u64, u64, vp]
     L.tm_select_tree.argtypes = [vp, u32, u32, vp, vp, i64, u32, i32, pv, vp, u32, C.POINTER(u32)]
     L.tm_motif_plan.argtypes = [vp, vp, vp]
     L.tm_weights.argtypes = [vp, vp, C.POINTER(tm_u128)]
@@ -323,6 +324,16 @@ def tm_select_tree(ctx, nv, edges, order, delta, n_c, all_roots=True):
     out = [{"tree_mask": int(c.tree_mask), "root": int(c.root), "looseness": int(c.looseness),
             "status": int(c.status), "W": c.W.value} for c in cands[:min(n.value, cap)]]
     return h, out
+
+
+def tm_sample_group(ctx, motifs, k, seed, first_index=0):
+    """One sampling run for motifs sharing a tree pattern: a Result per motif."""
+    n = len(motifs)
+    hs = (C.c_void_p * n)(*[m for m in motifs])
+    res = (tm_result * n)()
+    _check(lib().tm_sample_group(ctx, C.cast(hs, C.c_void_p), n, int(k), int(seed), int(first_index),
+                                 C.cast(res, C.c_void_p)), ctx, "tm_sample_group")
+    return [Result.of(r) for r in res]
 
 
 def tm_motif_plan(motif, ntree):
@@ -529,6 +540,11 @@ class Context:
 
     def motif(self, nv, edges, order, delta) -> Motif:
         return Motif(self, nv, edges, order, delta)
+
+    def sample_group(self, motifs, k, seed, first_index=0):
+        """Several motifs sharing a spanning-tree pattern, one sampling run
+        (weights of motifs[0] are used): a Result per motif."""
+        return tm_sample_group(self.h, [m.h for m in motifs], k, seed, first_index)
 
     def select_tree(self, nv, edges, order, delta, n_c=4, all_roots=True):
         """Tree and root of least exact W among the n_c best looseness trees

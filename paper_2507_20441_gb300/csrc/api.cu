@@ -800,6 +800,19 @@ int tm_sample(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t fir
     return run_samples(ctx, mo, k, seed, first_index, out, nullptr, nullptr, nullptr);
 }
 
+int tm_sample_group(tm_ctx *ctx, tm_motif *const *motifs, uint32_t nm, uint64_t k, uint64_t seed, uint64_t first_index,
+                    tm_result *results)
+{
+    if (!ctx || !motifs || !results || nm == 0) return TM_E_ARG;
+    if (nm > kMaxGroup) return set_err(ctx, TM_E_LIMIT, "at most 8 motifs per group");
+    for (uint32_t i = 0; i < nm; ++i)
+        if (!motifs[i] || motifs[i]->ctx != ctx) return set_err(ctx, TM_E_ARG, "motif of another context");
+    int rc = need_weights(ctx, motifs[0]);
+    if (rc) return rc;
+    cudaSetDevice(ctx->device);
+    return run_group(ctx, motifs, nm, k, seed, first_index, results);
+}
+
 int tm_sample_trace(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first_index, uint32_t *tree_gids,
                     uint64_t *contrib, int32_t *reason, tm_result *out)
 {

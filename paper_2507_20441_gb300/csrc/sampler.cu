@@ -195,14 +195,63 @@ __device__ __forceinline__ void load_edge(const DevGraph &g, uint32_t gid, Recs 
     R.pair(q) = __ldg(g.g_pair + gid);
 }
 
-// One sample: returns 0 valid, 1/2/3 reject reasons, or -1 on an internal
-// inconsistency (latched as ST_BADSTATE).
-__device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &J, uint64_t seed, uint64_t j,
-                          uint32_t *status, uint64_t &contrib, uint32_t *tg_out, Recs R)
+// Alg. 4: 0 when the sampled tree is valid, else the reject reason (1 the
+// vertex map is not 1-1, 2 the tree spans more than delta, 3 tree edges out
+// of pi order); fills the vertex map and the tree's time span.
+__device__ int validate_tree(const DevPlan &P, Recs R, uint32_t &tmin, uint32_t &tmax)
+{
+    const uint64_t d = (uint64_t)P.delta;
+    tmin = 0xFFFFFFFFu;
+    tmax = 0;
+    for (int q = 0; q < P.ntree; ++q) {
+        const int e = P.tedge[q];
+        R.phi(P.ea[e]) = R.src(q);
+        R.phi(P.eb[e]) = R.dst(q);
+        const uint32_t tq = R.t(q);
+        tmin = min(tmin, tq);
+        tmax = max(tmax, tq);
+    }
+    for (int x = 0; x < P.nv; ++x) {
+        const uint32_t px = R.phi(x);
+        for (int y = x + 1; y < P.nv; ++y)
+            if (px == R.phi(y)) return 1;
+    }
+    if ((uint64_t)tmax - (uint64_t)tmin > d) return 2;
+    int64_t prev = -1;
+    for (int pos = 0; pos < P.ne; ++pos) {
+        const int q = P.tnode_of_edge[P.pos_edge[pos]];
+        if (q < 0) continue;
+        const int64_t tq = R.t(q);
+        if (tq <= prev) return 3;
+        prev = tq;
+    }
+    return 0;
+}
+
+// DeriveCnt (Alg. 5) of a valid tree and N_phi (windows holding every tree
+// edge): the sample's contribution cnt * 2 / N_phi.
+__device__ uint64_t complete_count(const DevGraph &g, const DevPlan &P, Recs R, uint32_t tmin, uint32_t tmax,
+                                   uint32_t *status)
+{
+    const uint64_t d = (uint64_t)P.delta;
+    bool ovf = false;
+    uint64_t cnt = P.nnt == 0 ? 1
+                 : (P.derive_simple ? derive_simple(g, P, R, tmin, tmax, ovf) : derive_merge(g, P, R, tmin, tmax, ovf));
+    const bool two = (uint64_t)tmin >= d && (uint64_t)tmin / d == (uint64_t)tmax / d;
+    if (!two) cnt = mul_chk(cnt, 2, ovf);
+    if (ovf) latch(status, ST_OVERFLOW);
+    return cnt;
+}
+
+// The tree of sample j (Alg. 3): a window with probability W_i / W, the root
+// edge through the window's guide table and CDF, then every tree edge from
+// its candidate list.  Fills R; 0, or -1 on an internal inconsistency
+// (latched as ST_BADSTATE).
+__device__ int sample_tree(const DevGraph &g, const DevPlan &P, const SampleJob &J, uint64_t seed, uint64_t j,
+                           uint32_t *status, uint32_t *tg_out, Recs R)
 {
     SampleRng rng;
     rng.init(seed, j);
-    contrib = 0;
     const u128 W = (u128)J.W_lo | ((u128)J.W_hi << 64);
     u128 r = rng.below128(W, status);
     // window: last k with wcum[k] <= r
@@ -319,38 +368,21 @@ __device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &
     }
     if (tg_out)
         for (int q = 0; q < P.ntree; ++q) tg_out[q] = R.gid(q);
-    // ---- validation (Alg. 4): 1-1 vertex map, delta span, pi order
-    uint32_t tmin = 0xFFFFFFFFu, tmax = 0;
-    for (int q = 0; q < P.ntree; ++q) {
-        const int e = P.tedge[q];
-        R.phi(P.ea[e]) = R.src(q);
-        R.phi(P.eb[e]) = R.dst(q);
-        const uint32_t tq = R.t(q);
-        tmin = min(tmin, tq);
-        tmax = max(tmax, tq);
-    }
-    for (int x = 0; x < P.nv; ++x) {
-        const uint32_t px = R.phi(x);
-        for (int y = x + 1; y < P.nv; ++y)
-            if (px == R.phi(y)) return 1;
-    }
-    if ((uint64_t)tmax - (uint64_t)tmin > d) return 2;
-    int64_t prev = -1;
-    for (int pos = 0; pos < P.ne; ++pos) {
-        const int q = P.tnode_of_edge[P.pos_edge[pos]];
-        if (q < 0) continue;
-        const int64_t tq = R.t(q);
-        if (tq <= prev) return 3;
-        prev = tq;
-    }
-    // ---- DeriveCnt (Alg. 5) and N_phi (windows holding every tree edge)
-    bool ovf = false;
-    uint64_t cnt = P.nnt == 0 ? 1
-                 : (P.derive_simple ? derive_simple(g, P, R, tmin, tmax, ovf) : derive_merge(g, P, R, tmin, tmax, ovf));
-    const bool two = (uint64_t)tmin >= d && (uint64_t)tmin / d == (uint64_t)tmax / d;
-    if (!two) cnt = mul_chk(cnt, 2, ovf);
-    if (ovf) latch(status, ST_OVERFLOW);
-    contrib = cnt;
+    return 0;
+}
+
+// One sample: returns 0 valid, 1/2/3 reject reasons, or -1 on an internal
+// inconsistency (latched as ST_BADSTATE).
+__device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &J, uint64_t seed, uint64_t j,
+                          uint32_t *status, uint64_t &contrib, uint32_t *tg_out, Recs R)
+{
+    contrib = 0;
+    const int r = sample_tree(g, P, J, seed, j, status, tg_out, R);
+    if (r) return r;
+    uint32_t tmin, tmax;
+    const int why = validate_tree(P, R, tmin, tmax);
+    if (why) return why;
+    contrib = complete_count(g, P, R, tmin, tmax, status);
     return 0;
 }
 
@@ -419,6 +451,72 @@ __global__ void __launch_bounds__(kSampleThreads, TM_SAMPLE_MINB) k_sample(DevGr
         if (nr1) atomicAdd(&acc->rv, nr1);
         if (nr2) atomicAdd(&acc->rd, nr2);
         if (nr3) atomicAdd(&acc->ro, nr3);
+    }
+}
+
+// ---- several motifs per sampling run ------------------------------------
+// Motifs whose spanning trees are the same temporal pattern share one weight
+// pass and one stream of sampled trees: each sample is drawn and validated
+// once with the first plan and completed (Alg. 5) once per motif.
+template <int NM>
+__global__ void __launch_bounds__(kSampleThreads, TM_SAMPLE_MINB)
+    k_sample_group(DevGraph g, const DevPlan *__restrict__ plans, SampleJob J, uint64_t seed, uint64_t first,
+                   uint64_t k, Acc *acc, uint32_t *status)
+{
+    __shared__ DevPlan sp[NM];
+    {
+        const int *src = reinterpret_cast<const int *>(plans);
+        int *dst = reinterpret_cast<int *>(sp);
+        for (int i = threadIdx.x; i < (int)(NM * sizeof(DevPlan) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    uint32_t recs_local[kRecRows];
+    Recs R{recs_local, 1};
+    u128 hits[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) hits[m] = 0;
+    unsigned long long nv = 0, nr1 = 0, nr2 = 0, nr3 = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        if (sample_tree(g, sp[0], J, seed, first + i, status, nullptr, R)) continue;
+        uint32_t tmin, tmax;
+        const int why = validate_tree(sp[0], R, tmin, tmax);
+        if (why == 1) { ++nr1; continue; }
+        if (why == 2) { ++nr2; continue; }
+        if (why == 3) { ++nr3; continue; }
+        ++nv;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) hits[m] += complete_count(g, sp[m], R, tmin, tmax, status);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        nv += __shfl_down_sync(0xffffffffu, nv, o);
+        nr1 += __shfl_down_sync(0xffffffffu, nr1, o);
+        nr2 += __shfl_down_sync(0xffffffffu, nr2, o);
+        nr3 += __shfl_down_sync(0xffffffffu, nr3, o);
+    }
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+        uint64_t hl = (uint64_t)hits[m], hh = (uint64_t)(hits[m] >> 64);
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t ol = __shfl_down_sync(0xffffffffu, hl, o);
+            const uint64_t oh = __shfl_down_sync(0xffffffffu, hh, o);
+            const uint64_t sum = hl + ol;
+            hh += oh + (sum < hl ? 1 : 0);
+            hl = sum;
+        }
+        if ((threadIdx.x & 31) == 0) {
+            if (hl) {
+                const unsigned long long old = atomicAdd(&acc[m].hits_lo, (unsigned long long)hl);
+                if (old + hl < old) hh += 1;
+            }
+            if (hh) atomicAdd(&acc[m].hits_hi, (unsigned long long)hh);
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {   // validity is shared: counted on the first accumulator
+        if (nv) atomicAdd(&acc[0].valid, nv);
+        if (nr1) atomicAdd(&acc[0].rv, nr1);
+        if (nr2) atomicAdd(&acc[0].rd, nr2);
+        if (nr3) atomicAdd(&acc[0].ro, nr3);
     }
 }
 
@@ -628,6 +726,92 @@ int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t f
 
 
 void finish_result_acc(tm_motif *mo, uint64_t k, const SampleAcc &a, tm_result *out) { finish_result(mo, k, a, out); }
+
+// Same temporal pattern of the spanning tree: same vertices and delta, and
+// per tree node the same endpoints, parent, meeting side, direction, leaf
+// flag and pi relation to the parent, in the same pi order.  Then weights,
+// sampled trees and validation are identical; only DeriveCnt differs.
+static bool same_tree_pattern(const DevPlan &A, const DevPlan &B)
+{
+    if (A.nv != B.nv || A.ntree != B.ntree || A.delta != B.delta) return false;
+    for (int q = 0; q < A.ntree; ++q) {
+        if (A.ea[A.tedge[q]] != B.ea[B.tedge[q]] || A.eb[A.tedge[q]] != B.eb[B.tedge[q]]) return false;
+        if (A.tparent[q] != B.tparent[q] || A.tleaf[q] != B.tleaf[q] || A.tzside[q] != B.tzside[q] ||
+            A.tout[q] != B.tout[q] || A.tlater[q] != B.tlater[q])
+            return false;
+    }
+    int sa[kMaxE], sb[kMaxE], na = 0, nb = 0;
+    for (int pos = 0; pos < A.ne; ++pos) if (A.tnode_of_edge[A.pos_edge[pos]] >= 0) sa[na++] = A.tnode_of_edge[A.pos_edge[pos]];
+    for (int pos = 0; pos < B.ne; ++pos) if (B.tnode_of_edge[B.pos_edge[pos]] >= 0) sb[nb++] = B.tnode_of_edge[B.pos_edge[pos]];
+    if (na != nb) return false;
+    for (int i = 0; i < na; ++i) if (sa[i] != sb[i]) return false;
+    return true;
+}
+
+template <int NM>
+static void launch_group(tm_ctx *ctx, unsigned blocks, const DevPlan *dplans, const SampleJob &J, uint64_t seed,
+                         uint64_t first, uint64_t k, Acc *dacc)
+{
+    launch(ctx, k_sample_group<NM>, blocks, kSampleThreads, ctx->g, dplans, J, seed, first, k, dacc, ctx->status);
+}
+
+int run_group(tm_ctx *ctx, tm_motif *const *motifs, uint32_t nm, uint64_t k, uint64_t seed, uint64_t first,
+              tm_result *out)
+{
+    tm_motif *m0 = motifs[0];
+    for (uint32_t i = 1; i < nm; ++i)
+        if (!same_tree_pattern(m0->plan, motifs[i]->plan))
+            return set_err(ctx, TM_E_MOTIF, "motif " + std::to_string(i) + "'s spanning tree differs from motif 0's");
+    ScratchScope scope(ctx);
+    cudaStream_t st = ctx->stream;
+    std::vector<Acc> h(nm, Acc{0, 0, 0, 0, 0, 0});
+    if (k == 0 || (m0->W.lo == 0 && m0->W.hi == 0)) {
+        for (uint32_t i = 0; i < nm; ++i) finish_result(m0, k, h[i], &out[i]);
+        return TM_OK;
+    }
+    const size_t plan_bytes = sizeof(DevPlan) * nm, acc_bytes = sizeof(Acc) * nm;
+    char *scratch = (char *)salloc(ctx, plan_bytes + acc_bytes + 64);
+    if (!scratch) return TM_E_NOMEM;
+    DevPlan *dplans = (DevPlan *)scratch;
+    Acc *dacc = (Acc *)(scratch + ((plan_bytes + 15) / 16) * 16);
+    std::vector<DevPlan> hp(nm);
+    for (uint32_t i = 0; i < nm; ++i) hp[i] = motifs[i]->plan;
+    copy_h2d(ctx, dplans, hp.data(), plan_bytes);
+    cudaMemsetAsync(dacc, 0, acc_bytes, st);
+    cudaMemsetAsync(ctx->status, 0, 4, st);
+    SampleJob J;
+    fill_job(m0, J, dplans);
+    const uint64_t want = (k + kSampleThreads - 1) / kSampleThreads;
+    const unsigned blocks = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)ctx->num_sms * 16));
+    {
+        PhaseScope ph(ctx, TM_PH_SAMPLE);
+        switch (nm) {
+        case 1: launch_group<1>(ctx, blocks, dplans, J, seed, first, k, dacc); break;
+        case 2: launch_group<2>(ctx, blocks, dplans, J, seed, first, k, dacc); break;
+        case 3: launch_group<3>(ctx, blocks, dplans, J, seed, first, k, dacc); break;
+        case 4: launch_group<4>(ctx, blocks, dplans, J, seed, first, k, dacc); break;
+        case 5: launch_group<5>(ctx, blocks, dplans, J, seed, first, k, dacc); break;
+        case 6: launch_group<6>(ctx, blocks, dplans, J, seed, first, k, dacc); break;
+        case 7: launch_group<7>(ctx, blocks, dplans, J, seed, first, k, dacc); break;
+        default: launch_group<8>(ctx, blocks, dplans, J, seed, first, k, dacc); break;
+        }
+    }
+    int rc = check_cuda(ctx, cudaGetLastError(), "group sampler launch");
+    copy_d2h(ctx, h.data(), dacc, acc_bytes);
+    uint32_t bits = 0;
+    const int rc2 = read_status(ctx, &bits);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    for (uint32_t i = 0; i < nm; ++i) {
+        Acc a = h[i];
+        a.valid = h[0].valid; a.rv = h[0].rv; a.rd = h[0].rd; a.ro = h[0].ro;
+        finish_result(m0, k, a, &out[i]);
+    }
+    if (bits & ST_OVERFLOW) return set_err(ctx, TM_E_OVERFLOW, "a completion count exceeds 2^64");
+    if (bits) return set_err(ctx, TM_E_CUDA, "sampler reached an inconsistent state (status " + std::to_string(bits) + ")");
+    return TM_OK;
+}
+
 
 // The batched kernel in one of its shapes: 128 or 256 threads per block,
 // per-sample records in local or shared memory.  Persistent: as many blocks

@@ -211,6 +211,9 @@ struct SampleJob {
 };
 int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first,
                 tm_result *out, uint32_t *trace_gids, uint64_t *trace_contrib, int32_t *trace_reason);
+constexpr uint32_t kMaxGroup = 8;         // motifs per group sampling run
+int run_group(tm_ctx *ctx, tm_motif *const *motifs, uint32_t nm, uint64_t k, uint64_t seed, uint64_t first,
+              tm_result *out);
 int run_batch(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64_t *k,
               const uint64_t *seed, tm_result *out);
 
