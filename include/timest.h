@@ -205,6 +205,21 @@ int tm_weights_export(tm_ctx *ctx, tm_motif *mo, uint32_t tree_edge, uint32_t la
 int tm_window_totals(tm_ctx *ctx, tm_motif *mo, uint64_t *host_out, uint64_t cap,
                      uint64_t *nwin);
 
+/* Motif listing (Alg. 5 emitting the instances it counts): samples
+ * first_index .. first_index+k-1 are drawn as tm_sample draws them; for every
+ * valid sample, each M-match (Def. 1.2) whose tree edges are the sampled tree
+ * is one instance.  Instance rows are ordered by sample id, then depth first
+ * over the non-tree edges in pi order, each multi-edge list in time order.
+ * Row r: inst_gids[r*ne + e] = edge id (GLOBAL order) matched to motif edge
+ * e, inst_sample[r] = its sample id.  At most max_inst rows are written (host
+ * arrays of max_inst*ne and max_inst entries); *n_inst receives the total
+ * number of instances, which may exceed max_inst.  Two passes: counts per
+ * sample, then the instances (the second checks that it finds as many as
+ * DeriveCnt counted).  Errors: TM_E_STATE (no weights), TM_E_ARG,
+ * TM_E_OVERFLOW, TM_E_NOMEM, TM_E_CUDA. */
+int tm_sample_list(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first_index,
+                   uint64_t max_inst, uint32_t *inst_gids, uint64_t *inst_sample, uint64_t *n_inst);
+
 /* Several motifs per sampling run (the paper counts related motifs, e.g.
  * M4-1..M4-4, from one run): motifs[0..nm), 1 <= nm <= 8, whose spanning
  * trees (after tm_set_motif / tm_set_tree) are the same temporal pattern -

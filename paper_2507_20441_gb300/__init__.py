@@ -127,6 +127,7 @@ def _declare(L):
     L.tm_set_motif.argtypes = [vp, u32, u32, vp, vp, i64, pv]
     L.tm_set_tree.argtypes = [vp, vp, u32]
     L.tm_tree_candidates.argtypes = [u32, u32, vp, vp, u32, vp, vp, C.POINTER(u32)]
+    L.tm_sample_list.argtypes = [vp, vp, u64, u64, u64, u64, vp, vp, C.POINTER(u64)]
     L.tm_sample_group.argtypes = [vp, vp, u32, u64, u64, u64, vp]
     L.tm_select_tree.argtypes = [vp, u32, u32, vp, vp, i64, u32, i32, pv, vp, u32, C.POINTER(u32)]
     L.tm_motif_plan.argtypes = [vp, vp, vp]
@@ -326,6 +327,19 @@ def tm_select_tree(ctx, nv, edges, order, delta, n_c, all_roots=True):
     return h, out
 
 
+def tm_sample_list(ctx, motif, ne, k, seed, first_index=0, max_inst=1_000_000):
+    """Motif instances extending the valid samples: (edge ids [rows, ne],
+    sample ids [rows], total instances)."""
+    cap = int(max_inst)
+    gids = np.zeros((max(cap, 1), int(ne)), np.uint32)
+    sids = np.zeros(max(cap, 1), np.uint64)
+    n = C.c_uint64()
+    _check(lib().tm_sample_list(ctx, motif, int(k), int(seed), int(first_index), cap, _ptr(gids), _ptr(sids),
+                                C.byref(n)), ctx, "tm_sample_list")
+    rows = min(cap, n.value)
+    return gids[:rows], sids[:rows], int(n.value)
+
+
 def tm_sample_group(ctx, motifs, k, seed, first_index=0):
     """One sampling run for motifs sharing a tree pattern: a Result per motif."""
     n = len(motifs)
@@ -504,6 +518,9 @@ class Motif:
 
     def sample_trace(self, k, seed, first_index=0):
         return tm_sample_trace(self.ctx.h, self.h, k, seed, first_index, self.ntree)
+
+    def sample_list(self, k, seed, first_index=0, max_inst=1_000_000):
+        return tm_sample_list(self.ctx.h, self.h, len(self.edges), k, seed, first_index, max_inst)
 
     def free(self):
         if self.h:

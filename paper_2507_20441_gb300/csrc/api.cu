@@ -800,6 +800,16 @@ int tm_sample(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t fir
     return run_samples(ctx, mo, k, seed, first_index, out, nullptr, nullptr, nullptr);
 }
 
+int tm_sample_list(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first_index, uint64_t max_inst,
+                   uint32_t *inst_gids, uint64_t *inst_sample, uint64_t *n_inst)
+{
+    int rc = need_weights(ctx, mo);
+    if (rc) return rc;
+    if (!n_inst || (max_inst && (!inst_gids || !inst_sample))) return set_err(ctx, TM_E_ARG, "null listing output");
+    cudaSetDevice(ctx->device);
+    return run_list(ctx, mo, k, seed, first_index, max_inst, inst_gids, inst_sample, n_inst);
+}
+
 int tm_sample_group(tm_ctx *ctx, tm_motif *const *motifs, uint32_t nm, uint64_t k, uint64_t seed, uint64_t first_index,
                     tm_result *results)
 {

@@ -228,6 +228,14 @@ __device__ int validate_tree(const DevPlan &P, Recs R, uint32_t &tmin, uint32_t 
     return 0;
 }
 
+// DeriveCnt (Alg. 5): completions of a valid tree to M-matches.
+__device__ __forceinline__ uint64_t derive_cnt(const DevGraph &g, const DevPlan &P, Recs R, uint32_t tmin,
+                                               uint32_t tmax, bool &ovf)
+{
+    return P.nnt == 0 ? 1
+         : (P.derive_simple ? derive_simple(g, P, R, tmin, tmax, ovf) : derive_merge(g, P, R, tmin, tmax, ovf));
+}
+
 // DeriveCnt (Alg. 5) of a valid tree and N_phi (windows holding every tree
 // edge): the sample's contribution cnt * 2 / N_phi.
 __device__ uint64_t complete_count(const DevGraph &g, const DevPlan &P, Recs R, uint32_t tmin, uint32_t tmax,
@@ -235,8 +243,7 @@ __device__ uint64_t complete_count(const DevGraph &g, const DevPlan &P, Recs R, 
 {
     const uint64_t d = (uint64_t)P.delta;
     bool ovf = false;
-    uint64_t cnt = P.nnt == 0 ? 1
-                 : (P.derive_simple ? derive_simple(g, P, R, tmin, tmax, ovf) : derive_merge(g, P, R, tmin, tmax, ovf));
+    uint64_t cnt = derive_cnt(g, P, R, tmin, tmax, ovf);
     const bool two = (uint64_t)tmin >= d && (uint64_t)tmin / d == (uint64_t)tmax / d;
     if (!two) cnt = mul_chk(cnt, 2, ovf);
     if (ovf) latch(status, ST_OVERFLOW);
@@ -451,6 +458,135 @@ __global__ void __launch_bounds__(kSampleThreads, TM_SAMPLE_MINB) k_sample(DevGr
         if (nr1) atomicAdd(&acc->rv, nr1);
         if (nr2) atomicAdd(&acc->rd, nr2);
         if (nr3) atomicAdd(&acc->ro, nr3);
+    }
+}
+
+// ---- motif listing (Alg. 5 emitting the instances it counts) -------------
+// The completions of a valid tree, depth first over the non-tree edges in pi
+// order, each multi-edge list in time order.  Level i takes an entry of
+// El(phi(a_i), phi(b_i)) later than the pi position before it and earlier than
+// the next tree edge, inside [tmax - delta, tmin + delta]; a full assignment
+// is an instance when its pi span (last time - first time) is at most delta.
+// emit(index, cur) receives each instance (cur[i] = multi-edge position of
+// level i) in that order; returns the number of instances.
+template <class Emit>
+__device__ uint64_t enumerate_completions(const DevGraph &g, const DevPlan &P, Recs R, uint32_t tmin, uint32_t tmax,
+                                          Emit emit)
+{
+    const int nn = P.nnt;
+    if (nn == 0) { emit(0ull, (const uint32_t *)nullptr); return 1; }
+    const uint64_t d = (uint64_t)P.delta;
+    const uint64_t glo = (uint64_t)tmax >= d ? (uint64_t)tmax - d : 0, ghi = (uint64_t)tmin + d;
+    uint32_t lb[kMaxE], le[kMaxE], cur[kMaxE], end[kMaxE];
+    for (int i = 0; i < nn; ++i) {
+        const int e = P.pos_edge[P.nt_pos[i]];
+        find_pair(g, R.phi(P.ea[e]), R.phi(P.eb[e]), lb[i], le[i]);
+        if (lb[i] == le[i]) return 0;
+    }
+    // time at pi position pos given the current choices of levels < i
+    auto time_at = [&](int pos, int i) -> uint64_t {
+        const int q = P.tnode_of_edge[P.pos_edge[pos]];
+        if (q >= 0) return R.t(q);
+        for (int l = 0; l < i; ++l) if (P.nt_pos[l] == pos) return __ldg(g.multi_t + cur[l]);
+        return 0;   // not reached: callers ask for tree positions or earlier levels
+    };
+    auto open_level = [&](int i) {
+        const int pos = P.nt_pos[i];
+        uint64_t lo = glo, hi = ghi;
+        if (pos > 0) { const uint64_t tp = time_at(pos - 1, i) + 1; lo = tp > lo ? tp : lo; }
+        if (P.nt_next[i] >= 0) {
+            const uint64_t tn = R.t(P.nt_next[i]);
+            hi = tn == 0 ? 0 : (tn - 1 < hi ? tn - 1 : hi);
+            if (tn == 0) lo = hi + 1;
+        }
+        if (lo > hi) { cur[i] = end[i] = lb[i]; return; }
+        cur[i] = lower_idx(g.multi_t, lb[i], le[i], lo);
+        end[i] = lower_idx(g.multi_t, cur[i], le[i], hi + 1);
+    };
+    uint64_t count = 0;
+    int i = 0;
+    open_level(0);
+    for (;;) {
+        if (cur[i] >= end[i]) {
+            if (--i < 0) break;
+            ++cur[i];
+            continue;
+        }
+        if (i < nn - 1) {
+            open_level(++i);
+            continue;
+        }
+        const uint64_t first_t = time_at(0, nn), last_t = time_at(P.ne - 1, nn);
+        if (last_t - first_t <= d) emit(count++, (const uint32_t *)cur);
+        ++cur[i];
+    }
+    return count;
+}
+
+// Pass 1 of listing: completions per sample (0 when rejected).
+__global__ void __launch_bounds__(kSampleThreads, TM_SAMPLE_MINB)
+    k_list_count(DevGraph g, const DevPlan *__restrict__ plan, SampleJob J, uint64_t seed, uint64_t first, uint64_t k,
+                 uint64_t *__restrict__ cnt_out, uint32_t *status)
+{
+    __shared__ DevPlan sp;
+    {
+        const int *src = reinterpret_cast<const int *>(plan);
+        int *dst = reinterpret_cast<int *>(&sp);
+        for (int i = threadIdx.x; i < (int)(sizeof(DevPlan) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    uint32_t recs_local[kRecRows];
+    Recs R{recs_local, 1};
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        uint64_t c = 0;
+        if (sample_tree(g, sp, J, seed, first + i, status, nullptr, R) == 0) {
+            uint32_t tmin, tmax;
+            if (validate_tree(sp, R, tmin, tmax) == 0) {
+                bool ovf = false;
+                c = derive_cnt(g, sp, R, tmin, tmax, ovf);
+                if (ovf) latch(status, ST_OVERFLOW);
+            }
+        }
+        cnt_out[i] = c;
+    }
+}
+
+// Pass 2: each sample's instances at rows offs[i] .. offs[i+1]-1 (rows at or
+// beyond max_inst are not written): ne edge ids per row, motif edge e in
+// column e, and the sample id.
+__global__ void __launch_bounds__(kSampleThreads, TM_SAMPLE_MINB)
+    k_list_emit(DevGraph g, const DevPlan *__restrict__ plan, SampleJob J, uint64_t seed, uint64_t first, uint64_t k,
+                const uint64_t *__restrict__ offs, uint64_t max_inst, uint32_t *__restrict__ inst_gids,
+                uint64_t *__restrict__ inst_sample, uint32_t *status)
+{
+    __shared__ DevPlan sp;
+    {
+        const int *src = reinterpret_cast<const int *>(plan);
+        int *dst = reinterpret_cast<int *>(&sp);
+        for (int i = threadIdx.x; i < (int)(sizeof(DevPlan) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    uint32_t recs_local[kRecRows];
+    Recs R{recs_local, 1};
+    uint32_t tree_gids[kMaxTree];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        const uint64_t o = offs[i], n = offs[i + 1] - o;
+        if (n == 0 || o >= max_inst) continue;
+        if (sample_tree(g, sp, J, seed, first + i, status, tree_gids, R)) continue;
+        uint32_t tmin, tmax;
+        if (validate_tree(sp, R, tmin, tmax)) { latch(status, ST_BADSTATE); continue; }
+        const uint64_t got = enumerate_completions(g, sp, R, tmin, tmax, [&](uint64_t idx, const uint32_t *cur) {
+            const uint64_t r = o + idx;
+            if (r >= max_inst) return;
+            uint32_t *row = inst_gids + r * (uint64_t)sp.ne;
+            for (int q = 0; q < sp.ntree; ++q) row[sp.tedge[q]] = tree_gids[q];
+            for (int l = 0; l < sp.nnt; ++l)
+                row[sp.pos_edge[sp.nt_pos[l]]] = __ldg(g.out_gid + __ldg(g.multi_to_out + cur[l]));
+            inst_sample[r] = first + i;
+        });
+        if (got != n) latch(status, ST_BADSTATE);   // the enumeration must agree with DeriveCnt
     }
 }
 
@@ -726,6 +862,69 @@ int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t f
 
 
 void finish_result_acc(tm_motif *mo, uint64_t k, const SampleAcc &a, tm_result *out) { finish_result(mo, k, a, out); }
+
+int run_list(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first, uint64_t max_inst,
+             uint32_t *inst_gids, uint64_t *inst_sample, uint64_t *n_inst)
+{
+    ScratchScope scope(ctx);
+    cudaStream_t st = ctx->stream;
+    *n_inst = 0;
+    if (k == 0 || (mo->W.lo == 0 && mo->W.hi == 0)) return TM_OK;
+    DevPlan *dplan = (DevPlan *)salloc(ctx, sizeof(DevPlan));
+    uint64_t *dcnt = (uint64_t *)salloc(ctx, (size_t)(k + 1) * 8);
+    if (!dplan || !dcnt) return TM_E_NOMEM;
+    copy_h2d(ctx, dplan, &mo->plan, sizeof(DevPlan));
+    cudaMemsetAsync(ctx->status, 0, 4, st);
+    SampleJob J;
+    fill_job(mo, J, dplan);
+    const uint64_t want = (k + kSampleThreads - 1) / kSampleThreads;
+    const unsigned blocks = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)ctx->num_sms * 16));
+    {
+        PhaseScope ph(ctx, TM_PH_SAMPLE);
+        launch(ctx, k_list_count, blocks, kSampleThreads, ctx->g, (const DevPlan *)dplan, J, seed, first, k, dcnt,
+               ctx->status);
+    }
+    int rc = check_cuda(ctx, cudaGetLastError(), "listing count");
+    if (rc) return rc;
+    // row offsets of every sample (exclusive prefix of the counts, on the host)
+    std::vector<uint64_t> offs((size_t)k + 1);
+    copy_d2h(ctx, offs.data() + 1, dcnt, (size_t)k * 8);
+    rc = check_cuda(ctx, cudaStreamSynchronize(st), "listing count copy");
+    if (rc) return rc;
+    uint32_t bits = 0;
+    rc = read_status(ctx, &bits);
+    if (rc) return rc;
+    if (bits & ST_OVERFLOW) return set_err(ctx, TM_E_OVERFLOW, "a completion count exceeds 2^64");
+    if (bits) return set_err(ctx, TM_E_CUDA, "listing reached an inconsistent state");
+    offs[0] = 0;
+    for (uint64_t i = 1; i <= k; ++i) {
+        if (offs[i] > ~0ull - offs[i - 1]) return set_err(ctx, TM_E_OVERFLOW, "instance count exceeds 2^64");
+        offs[i] += offs[i - 1];
+    }
+    *n_inst = offs[k];
+    const uint64_t rows = std::min(max_inst, offs[k]);
+    if (rows == 0 || !inst_gids || !inst_sample) return TM_OK;
+    const size_t ne = mo->ne;
+    uint64_t *doffs = dcnt;   // reuse: k + 1 entries
+    uint32_t *dg = (uint32_t *)salloc(ctx, (size_t)rows * ne * 4);
+    uint64_t *ds = (uint64_t *)salloc(ctx, (size_t)rows * 8);
+    if (!dg || !ds) return TM_E_NOMEM;
+    copy_h2d(ctx, doffs, offs.data(), (size_t)(k + 1) * 8);
+    cudaMemsetAsync(ctx->status, 0, 4, st);
+    {
+        PhaseScope ph(ctx, TM_PH_SAMPLE);
+        launch(ctx, k_list_emit, blocks, kSampleThreads, ctx->g, (const DevPlan *)dplan, J, seed, first, k,
+               (const uint64_t *)doffs, rows, dg, ds, ctx->status);
+    }
+    rc = check_cuda(ctx, cudaGetLastError(), "listing emit");
+    if (rc) return rc;
+    copy_d2h(ctx, inst_gids, dg, (size_t)rows * ne * 4);
+    copy_d2h(ctx, inst_sample, ds, (size_t)rows * 8);
+    rc = read_status(ctx, &bits);
+    if (rc) return rc;
+    if (bits) return set_err(ctx, TM_E_CUDA, "listing disagreed with DeriveCnt (status " + std::to_string(bits) + ")");
+    return TM_OK;
+}
 
 // Same temporal pattern of the spanning tree: same vertices and delta, and
 // per tree node the same endpoints, parent, meeting side, direction, leaf

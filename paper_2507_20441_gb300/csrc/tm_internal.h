@@ -211,6 +211,8 @@ struct SampleJob {
 };
 int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first,
                 tm_result *out, uint32_t *trace_gids, uint64_t *trace_contrib, int32_t *trace_reason);
+int run_list(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first, uint64_t max_inst,
+             uint32_t *inst_gids, uint64_t *inst_sample, uint64_t *n_inst);
 constexpr uint32_t kMaxGroup = 8;         // motifs per group sampling run
 int run_group(tm_ctx *ctx, tm_motif *const *motifs, uint32_t nm, uint64_t k, uint64_t seed, uint64_t first,
               tm_result *out);
