@@ -70,6 +70,7 @@ def lib():
         L.or_time_span.argtypes = [vp]; L.or_time_span.restype = i64
         L.or_export_edges.argtypes = [vp, vp, vp, vp]
         L.or_set_motif.argtypes = [vp, i32, i32, vp, vp, vp, i64, vp, i32]
+        L.or_set_constraints.argtypes = [vp, i32, i32]
         L.or_plan_info.argtypes = [vp, vp, vp, vp, vp]
         L.or_weights.argtypes = [vp, C.POINTER(u64), C.POINTER(u64)]
         L.or_export_weights.argtypes = [vp, i32, i32, vp]
@@ -162,6 +163,13 @@ class Graph:
             raise OracleError(rc, "or_set_motif")
         self.ntree = nv - 1
         self.ne = len(edges)
+        return rc
+
+    def set_constraints(self, c2=True, c3=True):
+        """Constraint toggles of the ablation (R8); weights must be recomputed."""
+        rc = lib().or_set_constraints(self.h, 1 if c2 else 0, 1 if c3 else 0)
+        if rc != OK:
+            raise OracleError(rc, "or_set_constraints")
         return rc
 
     def plan_info(self):

@@ -48,6 +48,11 @@
  *       (Alg. 4).
  *   R7  Weights are exact unsigned 64-bit integers; any candidate-list sum,
  *       product or per-window root total >= 2^64 is reported as overflow.
+ *   R8  Constraint toggles of the ablation (Table of constraints):
+ *       Constraint 1 always holds; without Constraint 2 the candidate list
+ *       keeps the multi-edges to the parent's other endpoint; without
+ *       Constraint 3 a single window [0, 2^34) holds every edge (window unit
+ *       2^33 > any t' span), so every N_phi is 1.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -64,6 +69,8 @@ enum {
 };
 enum { OR_DEDUP = 1, OR_DROP_SELF = 2 };
 enum { OR_MAXV = 8, OR_MAXE = 16 };
+#define OR_WD_OFF ((int64_t)1 << 33)   /* window unit without Constraint 3: above any t' span */
+#define OR_NO_VERTEX 0xFFFFFFFFu        /* never a vertex id (n < 2^32 - 1)             */
 enum { RS_VALID = 0, RS_VERTEX = 1, RS_DELTA = 2, RS_ORDER = 3 };
 
 /* ------------------------------------------------------------------------ */
@@ -161,6 +168,8 @@ typedef struct {
     int a[OR_MAXE], b[OR_MAXE], rank[OR_MAXE];
     int pos_edge[OR_MAXE];
     int64_t delta;
+    int64_t wd;                    /* window unit: delta, or OR_WD_OFF without Constraint 3 */
+    int c2;                        /* 1: Constraint 2 (distinct far endpoints) enforced     */
     int is_tree[OR_MAXE];
     int root, ntree;
     int order[OR_MAXV];            /* tree edges, breadth-first from root  */
@@ -381,6 +390,7 @@ int or_set_motif(or_ctx *C, int nv, int ne, const int32_t *ea, const int32_t *eb
     memset(P, 0, sizeof(*P));
     if (nv < 2 || nv > OR_MAXV || ne < nv - 1 || ne > OR_MAXE || delta <= 0) return OR_E_MOTIF;
     P->nv = nv; P->ne = ne; P->delta = delta;
+    P->wd = delta; P->c2 = 1;
     int seen_rank[OR_MAXE] = {0};
     for (int i = 0; i < ne; ++i) {
         if (ea[i] < 0 || ea[i] >= nv || eb[i] < 0 || eb[i] >= nv || ea[i] == eb[i]) return OR_E_MOTIF;
@@ -437,6 +447,20 @@ int or_set_motif(or_ctx *C, int nv, int ne, const int32_t *ea, const int32_t *eb
     return OR_OK;
 }
 
+/* Constraint toggles for the ablation (R8): c2 = 0 drops Constraint 2 (a
+ * child's candidate list keeps the multi-edges to the parent's other
+ * endpoint); c3 = 0 drops Constraint 3 (one window holds every edge, so
+ * N_phi = 1).  Constraint 1 always holds.  Weights must be recomputed. */
+int or_set_constraints(or_ctx *C, int c2, int c3)
+{
+    if (!C->have_plan) return OR_E_STATE;
+    free_weights(C);
+    C->P.c2 = c2 ? 1 : 0;
+    C->P.wd = c3 ? C->P.delta : OR_WD_OFF;
+    C->nwin = C->g.T / C->P.wd + 1;
+    return OR_OK;
+}
+
 /* sampling order and parents, for tests that read the plan */
 void or_plan_info(const or_ctx *C, int32_t *order, int32_t *parent, int32_t *meet, int32_t *height)
 {
@@ -467,7 +491,7 @@ static int child_candidates(const or_ctx *C, int s, uint32_t ge, int c, int64_t 
     int64_t lo, hi;                              /* inclusive t' range */
     if (P->rank[c] > P->rank[s]) { lo = te + 1; hi = te + d; }
     else { lo = te - d; hi = te - 1; }
-    int64_t wlo = wi * d, whi = (wi + 2) * d - 1;
+    int64_t wlo = wi * P->wd, whi = (wi + 2) * P->wd - 1;
     if (lo < wlo) lo = wlo;
     if (hi > whi) hi = whi;
     if (lo > hi) return 0;
@@ -477,7 +501,7 @@ static int child_candidates(const or_ctx *C, int s, uint32_t ge, int c, int64_t 
     R->list = list;
     R->beg = lower_time(g, list, beg[zg], beg[zg + 1], lo);
     R->end = lower_time(g, list, R->beg, beg[zg + 1], hi + 1);
-    R->excl = og;
+    R->excl = P->c2 ? og : OR_NO_VERTEX;       /* without C2 nothing is excluded */
     R->use_src_as_nbr = !out_dir;
     return R->beg < R->end;
 }
@@ -510,7 +534,7 @@ int or_weights(or_ctx *C, uint64_t *W_lo, uint64_t *W_hi)
     if (!C->have_plan) return OR_E_STATE;
     free_weights(C);
     const or_graph *g = &C->g; const or_plan *P = &C->P;
-    int64_t m = g->m, d = P->delta;
+    int64_t m = g->m;
     int overflow = 0;
     int maxh = 0;
     for (int q = 0; q < P->ntree; ++q) if (P->height[P->order[q]] > maxh) maxh = P->height[P->order[q]];
@@ -523,7 +547,7 @@ int or_weights(or_ctx *C, uint64_t *W_lo, uint64_t *W_hi)
                 if (!w) return OR_E_NOMEM;
                 C->w[s][p] = w;
                 for (int64_t e = 0; e < m; ++e) {
-                    int64_t wi = window_of(g->t[e], p, d);
+                    int64_t wi = window_of(g->t[e], p, P->wd);
                     if (wi < 0) { w[e] = 0; continue; }
                     /* factor i = sum of w_{s_i} over L_{e,s,s_i}; R7: a factor
                      * >= 2^64 or an exact product >= 2^64 is an overflow. */
@@ -558,7 +582,7 @@ int or_weights(or_ctx *C, uint64_t *W_lo, uint64_t *W_hi)
     for (int p = 0; p < 2; ++p) {
         C->rootcum[p] = malloc(sizeof(uint64_t) * (size_t)(m ? m : 1));
         for (int64_t e = 0; e < m; ++e) {
-            int64_t wi = window_of(g->t[e], p, d);
+            int64_t wi = window_of(g->t[e], p, P->wd);
             if (wi < 0) { C->rootcum[p][e] = 0; continue; }
             acc[wi] += child_weight(C, c, p, (uint32_t)e);
             C->rootcum[p][e] = (uint64_t)acc[wi];
@@ -582,7 +606,7 @@ int or_export_weights(const or_ctx *C, int s, int p, uint64_t *out)
     if (!C->have_weights || s < 0 || s >= C->P.ne || !C->P.is_tree[s] || p < 0 || p > 1) return OR_E_ARG;
     for (int64_t e = 0; e < C->g.m; ++e) {
         if (C->w[s][p]) out[e] = C->w[s][p][e];
-        else out[e] = window_of(C->g.t[e], p, C->P.delta) >= 0 ? 1 : 0;
+        else out[e] = window_of(C->g.t[e], p, C->P.wd) >= 0 ? 1 : 0;
     }
     return OR_OK;
 }
@@ -669,8 +693,8 @@ static int validate_and_count(const or_ctx *C, const uint32_t *treegid, uint64_t
         if (!P->is_tree[e]) pair_range(g, phiV[P->a[e]], phiV[P->b[e]], &S.lbeg[e], &S.lend[e]);
     S.lb = b - P->delta; S.ub = a + P->delta;
     uint64_t cnt = derive_rec(&S, 0, -1, -1);
-    int64_t d = P->delta;
-    int N = 1 + ((a >= d && (b / d) == (a / d)) ? 1 : 0);
+    int64_t wd = P->wd;                         /* N_phi counts windows (R4) */
+    int N = 1 + ((a >= wd && (b / wd) == (a / wd)) ? 1 : 0);
     uint64_t c2 = (N == 1) ? cnt * 2 : cnt;
     if (N == 1 && cnt > (UINT64_MAX >> 1)) S.overflow = 1;
     if (S.overflow) *ovf = 1;
@@ -684,7 +708,7 @@ static int validate_and_count(const or_ctx *C, const uint32_t *treegid, uint64_t
 static int sample_one(const or_ctx *C, uint64_t seed, uint64_t j, uint32_t *treegid)
 {
     const or_graph *g = &C->g; const or_plan *P = &C->P;
-    int64_t d = P->delta, m = g->m;
+    int64_t m = g->m;
     draw_state st = { seed, j, 0 };
     u128 r = uniform_u128(&st, C->W);
     /* window: windows ordered by (layer, index) */
@@ -700,10 +724,10 @@ static int sample_one(const or_ctx *C, uint64_t seed, uint64_t j, uint32_t *tree
      * of w_c exceeds r, i.e. probability w_{c,e} / W_i (Alg. 3). */
     uint64_t rr = (uint64_t)r;
     int64_t lo = 0, hi = m;                       /* first gid with t' >= wi*d */
-    while (lo < hi) { int64_t mid = lo + (hi - lo) / 2; if (g->t[mid] < wi * d) lo = mid + 1; else hi = mid; }
+    while (lo < hi) { int64_t mid = lo + (hi - lo) / 2; if (g->t[mid] < wi * P->wd) lo = mid + 1; else hi = mid; }
     int64_t wbeg = lo;
     hi = m;                                       /* first gid with t' >= (wi+2)*d */
-    while (lo < hi) { int64_t mid = lo + (hi - lo) / 2; if (g->t[mid] < (wi + 2) * d) lo = mid + 1; else hi = mid; }
+    while (lo < hi) { int64_t mid = lo + (hi - lo) / 2; if (g->t[mid] < (wi + 2) * P->wd) lo = mid + 1; else hi = mid; }
     int64_t wend = lo;
     lo = wbeg; hi = wend;
     while (lo < hi) { int64_t mid = lo + (hi - lo) / 2; if (C->rootcum[p][mid] <= rr) lo = mid + 1; else hi = mid; }
@@ -826,7 +850,7 @@ static void enum_rec(enum_state *E, int q)
     int c = P->order[q];
     if (q == 0) {
         for (int64_t e = 0; e < g->m; ++e) {
-            if (!in_window(g->t[e], E->wi, d)) continue;
+            if (!in_window(g->t[e], E->wi, P->wd)) continue;
             E->match[c] = (uint32_t)e; E->tree_by_order[0] = (uint32_t)e;
             enum_rec(E, 1);
         }
@@ -843,10 +867,10 @@ static void enum_rec(enum_state *E, int q)
         uint32_t e = list[x];
         uint32_t nbr = out_dir ? g->dst[e] : g->src[e];
         int64_t t = g->t[e], ts = g->t[es];
-        if (!in_window(t, E->wi, d)) continue;                       /* C3 */
+        if (!in_window(t, E->wi, P->wd)) continue;                   /* C3 */
         if (P->rank[c] > P->rank[s]) { if (!(t > ts && t <= ts + d)) continue; }  /* C1 */
         else { if (!(t < ts && t >= ts - d)) continue; }
-        if (nbr == og) continue;                                     /* C2 */
+        if (P->c2 && nbr == og) continue;                            /* C2 */
         E->match[c] = e; E->tree_by_order[q] = e;
         enum_rec(E, q + 1);
     }

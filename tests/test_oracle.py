@@ -315,3 +315,72 @@ def test_overflow_detected(oracle_mod):
     edges = [(0, i) for i in range(1, 8)]
     G.set_motif(8, edges, list(range(7)), 10_000, list(range(7)), 0)
     assert G.weights(allow_overflow=True) is None
+
+
+CONSTRAINT_SETS = [(True, True), (False, True), (True, False), (False, False)]
+
+
+@pytest.mark.parametrize("name", ["triangle", "cycle4", "cycle5_chord", "bowtie", "antiparallel", "parallel"])
+def test_brute_equals_tree_sum_every_constraint_set(oracle_mod, name):
+    """O1 == O4 with and without Constraints 2 and 3 (R8): every M-match's
+    tree restriction is a partial match under each constraint set, counted
+    N_phi times (N_phi = 1 without windows)."""
+    nv, edges, rank = SMALL_MOTIFS[name]
+    trees = spanning_trees(nv, edges)
+    for seed in range(2):
+        n, s, d, t = small_random_graph(200 + seed, n=nv + 2, m=55 if nv <= 4 else 45, t_hi=40)
+        G = oracle_mod.Graph(n, s, d, t)
+        for delta in (5, 12):
+            C = G.brute_count(nv, edges, rank, delta)
+            for tree in trees[:3]:
+                for root in tree:
+                    for c2, c3 in CONSTRAINT_SETS:
+                        G.set_motif(nv, edges, rank, delta, tree, root)
+                        G.set_constraints(c2, c3)
+                        assert G.exact_by_trees() == 2 * C, (seed, delta, tree, root, c2, c3)
+
+
+@pytest.mark.parametrize("name", ["triangle", "cycle4", "bowtie", "antiparallel"])
+def test_window_totals_every_constraint_set(oracle_mod, name):
+    """W_i of the weight DP == brute-force partial-match count per window for
+    every constraint set; without Constraint 3 there is one window."""
+    nv, edges, rank = SMALL_MOTIFS[name]
+    trees = spanning_trees(nv, edges)
+    n, s, d, t = small_random_graph(300, n=nv + 2, m=50, t_hi=30)
+    G = oracle_mod.Graph(n, s, d, t)
+    for delta in (4, 9):
+        for tree in trees[:3]:
+            for root in tree:
+                for c2, c3 in CONSTRAINT_SETS:
+                    G.set_motif(nv, edges, rank, delta, tree, root)
+                    G.set_constraints(c2, c3)
+                    W = G.weights()
+                    Wi = G.window_totals()
+                    if not c3:
+                        assert len(Wi) == 1
+                    assert int(Wi.astype(object).sum()) == W
+                    for i in range(len(Wi)):
+                        assert G.partial_count(i) == int(Wi[i]), (delta, tree, root, c2, c3, i)
+
+
+def test_two_path_partial_matches_without_windows(oracle_mod):
+    """2-path a->b, b->c rooted at a->b with no windows: W counts the edge
+    pairs (i, j) with dst(i) == src(j) and t_i < t_j <= t_i + delta (Constraint
+    1), and with Constraint 2 also c != a -- counted here from the arrays."""
+    n, s, d, t = small_random_graph(12, n=8, m=140, t_hi=60)
+    delta = 9
+    w_c1 = w_c12 = 0
+    for i in range(len(s)):
+        for j in range(len(s)):
+            if d[i] == s[j] and t[i] < t[j] <= t[i] + delta:
+                w_c1 += 1
+                w_c12 += int(d[j] != s[i])
+    G = oracle_mod.Graph(n, s, d, t)
+    edges, rank = [(0, 1), (1, 2)], [0, 1]
+    G.set_motif(3, edges, rank, delta, [0, 1], 0)
+    G.set_constraints(False, False)
+    assert G.weights() == w_c1
+    G.set_motif(3, edges, rank, delta, [0, 1], 0)
+    G.set_constraints(True, False)
+    assert G.weights() == w_c12
+    assert w_c1 > w_c12 > 0

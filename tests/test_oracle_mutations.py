@@ -16,10 +16,10 @@ MUTATIONS = {
                       "if (P->rank[c] > P->rank[s]) { lo = te; hi = te + d; }"),
     "exclusion_dropped": ("if (cand_nbr(g, &R, x) != R.excl)\n                                    sum +=",
                           "if (1)\n                                    sum +="),
-    "window_closed": ("int64_t wlo = wi * d, whi = (wi + 2) * d - 1;",
-                      "int64_t wlo = wi * d, whi = (wi + 2) * d;"),
-    "nphi_ignores_first_window": ("int N = 1 + ((a >= d && (b / d) == (a / d)) ? 1 : 0);",
-                                  "int N = 1 + (((b / d) == (a / d)) ? 1 : 0);"),
+    "window_closed": ("int64_t wlo = wi * P->wd, whi = (wi + 2) * P->wd - 1;",
+                      "int64_t wlo = wi * P->wd, whi = (wi + 2) * P->wd;"),
+    "nphi_ignores_first_window": ("int N = 1 + ((a >= wd && (b / wd) == (a / wd)) ? 1 : 0);",
+                                  "int N = 1 + (((b / wd) == (a / wd)) ? 1 : 0);"),
     "derive_not_strict": ("if (pos > 0 && t <= prev) continue;",
                           "if (pos > 0 && t < prev) continue;"),
     "validate_order_not_strict": ("if (have && S.tau[e] <= prev) return RS_ORDER;",
@@ -34,8 +34,10 @@ MUTATIONS = {
     "window_pick_off_by_one": ("if (r < (u128)C->Wi[i]) { wi = i; break; }", "if (r <= (u128)C->Wi[i]) { wi = i; break; }"),
     "estimate_scale": ("res->estimate = (double)C->W * (double)hits / (2.0 * (double)k);",
                        "res->estimate = (double)C->W * (double)hits / ((double)k);"),
-    "root_total_wrong_layer": ("int64_t wi = window_of(g->t[e], p, d);\n            if (wi < 0) { C->rootcum[p][e] = 0; continue; }",
-                               "int64_t wi = window_of(g->t[e], 0, d);\n            if (wi < 0) { C->rootcum[p][e] = 0; continue; }"),
+    "brute_c2_always_on": ("if (P->c2 && nbr == og) continue;", "if (nbr == og) continue;"),
+    "nphi_uses_delta_not_window_unit": ("int64_t wd = P->wd;", "int64_t wd = P->delta;"),
+    "root_total_wrong_layer": ("int64_t wi = window_of(g->t[e], p, P->wd);\n            if (wi < 0) { C->rootcum[p][e] = 0; continue; }",
+                               "int64_t wi = window_of(g->t[e], 0, P->wd);\n            if (wi < 0) { C->rootcum[p][e] = 0; continue; }"),
 }
 
 
