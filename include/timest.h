@@ -146,6 +146,17 @@ int tm_set_motif(tm_ctx *ctx, uint32_t nv, uint32_t ne, const uint32_t *edges,
  * (Def. 3.5).  Invalidates cached weights.  Errors: TM_E_MOTIF. */
 int tm_set_tree(tm_motif *mo, const uint32_t *tree_edge_ids, uint32_t root_edge);
 
+/* Constraint toggles of the ablation (the paper's table of constraints):
+ * TM_C2 keeps Constraint 2 (a child's candidate list leaves out the
+ * multi-edges to the parent's other endpoint), TM_C3 keeps Constraint 3 (the
+ * 2*delta windows).  Constraint 1 always holds.  Without TM_C3 one window
+ * holds every edge (window unit 2^33 > any t' span), so every N_phi is 1.
+ * The estimate stays unbiased under every setting; only the valid-sample rate
+ * and the variance change.  Default (tm_set_motif): TM_C2 | TM_C3.  Invalidates
+ * cached weights.  Errors: TM_E_ARG (unknown flag). */
+enum { TM_C2 = 1, TM_C3 = 2 };
+int tm_set_constraints(tm_motif *mo, int flags);
+
 /* Every spanning tree of motif (nv, ne, edges, order) (the arguments of
  * tm_set_motif), ranked as in Alg. 7 by constraint looseness (Alg. 8, read
  * over unordered pairs of tree edges sharing a vertex: sum of

@@ -24,6 +24,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "timest.h")
 
 TM_OK, TM_E_ARG, TM_E_DUP, TM_E_SELFLOOP, TM_E_MOTIF, TM_E_NOMEM, TM_E_OVERFLOW, TM_E_STATE, TM_E_TIMEOUT, \
     TM_E_CUDA, TM_E_LIMIT, TM_E_PENDING = range(12)
+TM_C2, TM_C3 = 1, 2
 TM_HOST, TM_DEVICE, TM_DEDUP, TM_DROP_SELF = 0, 1, 2, 4
 _STATUS_NAMES = {0: "TM_OK", 1: "TM_E_ARG", 2: "TM_E_DUP", 3: "TM_E_SELFLOOP", 4: "TM_E_MOTIF", 5: "TM_E_NOMEM",
                  6: "TM_E_OVERFLOW", 7: "TM_E_STATE", 8: "TM_E_TIMEOUT", 9: "TM_E_CUDA", 10: "TM_E_LIMIT",
@@ -126,6 +127,7 @@ def _declare(L):
     L.tm_edges_export.argtypes = [vp, vp, vp, vp]
     L.tm_set_motif.argtypes = [vp, u32, u32, vp, vp, i64, pv]
     L.tm_set_tree.argtypes = [vp, vp, u32]
+    L.tm_set_constraints.argtypes = [vp, i32]
     L.tm_tree_candidates.argtypes = [u32, u32, vp, vp, u32, vp, vp, C.POINTER(u32)]
     L.tm_sample_list.argtypes = [vp, vp, u64, u64, u64, u64, vp, vp, C.POINTER(u64)]
     L.tm_sample_group.argtypes = [vp, vp, u32, u64, u64, u64, vp]
@@ -294,6 +296,12 @@ def tm_set_motif(ctx, nv, edges, order, delta):
 def tm_set_tree(ctx, motif, tree, root):
     tr = np.ascontiguousarray(np.array(tree, dtype=np.uint32))
     _check(lib().tm_set_tree(motif, _ptr(tr), int(root)), ctx, "tm_set_tree")
+
+
+def tm_set_constraints(ctx, motif, c2=True, c3=True):
+    """Keep or drop Constraints 2 and 3 of a motif (ablation)."""
+    flags = (TM_C2 if c2 else 0) | (TM_C3 if c3 else 0)
+    _check(lib().tm_set_constraints(motif, flags), ctx, "tm_set_constraints")
 
 
 def tm_tree_candidates(nv, edges, order):
@@ -499,6 +507,11 @@ class Motif:
 
     def set_tree(self, tree, root):
         tm_set_tree(self.ctx.h, self.h, tree, root)
+        return self
+
+    def set_constraints(self, c2=True, c3=True):
+        """Keep or drop Constraints 2 and 3 (ablation); weights must be recomputed."""
+        tm_set_constraints(self.ctx.h, self.h, c2, c3)
         return self
 
     def plan(self):

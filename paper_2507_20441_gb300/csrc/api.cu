@@ -376,6 +376,8 @@ static int compile_plan(const MotifDesc &M, const int *tree, int root, int64_t d
     memset(&P, 0, sizeof(P));
     P.nv = M.nv; P.ne = M.ne; P.ntree = M.nv - 1;
     P.delta = std::min<int64_t>(delta, (int64_t)1 << 33);
+    P.wdelta = P.delta;
+    P.c2 = 1;
     bool in_tree[kMaxE] = {};
     for (int i = 0; i < P.ntree; ++i) in_tree[tree[i]] = true;
     if (!in_tree[root]) return TM_E_MOTIF;
@@ -725,6 +727,15 @@ int tm_set_tree(tm_motif *mo, const uint32_t *tree_edge_ids, uint32_t root_edge)
     return TM_OK;
 }
 
+int tm_set_constraints(tm_motif *mo, int flags)
+{
+    if (!mo || (flags & ~(TM_C2 | TM_C3))) return TM_E_ARG;
+    release_weights(mo->ctx, mo);
+    mo->plan.c2 = (flags & TM_C2) ? 1 : 0;
+    mo->plan.wdelta = (flags & TM_C3) ? mo->plan.delta : ((int64_t)1 << 33);
+    return TM_OK;
+}
+
 int tm_motif_plan(tm_motif *mo, int32_t *order, int32_t *parent)
 {
     if (!mo) return TM_E_ARG;
@@ -770,7 +781,7 @@ int tm_window_totals(tm_ctx *ctx, tm_motif *mo, uint64_t *host_out, uint64_t cap
 {
     int rc = need_weights(ctx, mo);
     if (rc) return rc;
-    uint64_t nw = (uint64_t)ctx->g.T / (uint64_t)mo->plan.delta + 1;
+    uint64_t nw = (uint64_t)ctx->g.T / (uint64_t)mo->plan.wdelta + 1;
     if (ctx->g.m == 0) nw = 1;
     if (nwin) *nwin = nw;
     if (!host_out) return TM_OK;

@@ -241,10 +241,10 @@ __device__ __forceinline__ uint64_t derive_cnt(const DevGraph &g, const DevPlan 
 __device__ uint64_t complete_count(const DevGraph &g, const DevPlan &P, Recs R, uint32_t tmin, uint32_t tmax,
                                    uint32_t *status)
 {
-    const uint64_t d = (uint64_t)P.delta;
+    const uint64_t wd = (uint64_t)P.wdelta;   // N_phi counts windows
     bool ovf = false;
     uint64_t cnt = derive_cnt(g, P, R, tmin, tmax, ovf);
-    const bool two = (uint64_t)tmin >= d && (uint64_t)tmin / d == (uint64_t)tmax / d;
+    const bool two = (uint64_t)tmin >= wd && (uint64_t)tmin / wd == (uint64_t)tmax / wd;
     if (!two) cnt = mul_chk(cnt, 2, ovf);
     if (ovf) latch(status, ST_OVERFLOW);
     return cnt;
@@ -277,8 +277,8 @@ __device__ int sample_tree(const DevGraph &g, const DevPlan &P, const SampleJob 
     const uint64_t *cdf = p ? J.root_cdf1 : J.root_cdf0;
     const uint32_t wbeg = __ldg(wb + kk), wend = __ldg(wb + kk + 1);
     const uint64_t wi = __ldg((p ? J.win_id1 : J.win_id0) + kk);
-    const uint64_t d = (uint64_t)P.delta;
-    const uint64_t wlo = wi * d, whi = (wi + 2) * d - 1;
+    const uint64_t d = (uint64_t)P.delta, wd = (uint64_t)P.wdelta;
+    const uint64_t wlo = wi * wd, whi = (wi + 2) * wd - 1;
     // the root edge lies between two guide entries: the first edges whose CDF
     // exceeds the bucket bounds below and above rr
     const uint32_t gsh = __ldg((p ? J.win_gshift1 : J.win_gshift0) + kk);
@@ -311,7 +311,7 @@ __device__ int sample_tree(const DevGraph &g, const DevPlan &P, const SampleJob 
         uint32_t a, b, beg;
         const uint32_t *tarr;
         child_range(g, zs ? 1 : 0, out, zg, ppos, pt, P.tlater[q] != 0, tlo, thi, a, b, beg, tarr);
-        const uint32_t pe = (out == !zs) ? ppair : __ldg(g.rev_pair + ppair);
+        const uint32_t pe = !P.c2 ? kNone : (out == !zs) ? ppair : __ldg(g.rev_pair + ppair);
         uint32_t ea = 0, eb = 0, pb = 0;
         if (pe != kNone) {
             pb = __ldg(g.pair_off + pe);
@@ -932,7 +932,7 @@ int run_list(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t firs
 // sampled trees and validation are identical; only DeriveCnt differs.
 static bool same_tree_pattern(const DevPlan &A, const DevPlan &B)
 {
-    if (A.nv != B.nv || A.ntree != B.ntree || A.delta != B.delta) return false;
+    if (A.nv != B.nv || A.ntree != B.ntree || A.delta != B.delta || A.wdelta != B.wdelta || A.c2 != B.c2) return false;
     for (int q = 0; q < A.ntree; ++q) {
         if (A.ea[A.tedge[q]] != B.ea[B.tedge[q]] || A.eb[A.tedge[q]] != B.eb[B.tedge[q]]) return false;
         if (A.tparent[q] != B.tparent[q] || A.tleaf[q] != B.tleaf[q] || A.tzside[q] != B.tzside[q] ||

@@ -112,7 +112,7 @@ std::string make_key(uint32_t nv, uint32_t ne, const uint32_t *edges, const uint
 size_t estimate_bytes(const tm_motif *mo, uint64_t m, uint64_t T)
 {
     uint64_t slots = (uint64_t)mo->plan.nslots;
-    uint64_t nwin = T / (uint64_t)std::max<int64_t>(1, mo->plan.delta) + 2;
+    uint64_t nwin = T / (uint64_t)std::max<int64_t>(1, mo->plan.wdelta) + 2;
     nwin = std::min<uint64_t>(nwin, m + 2);
     // root CDF 16 B and root-search guide about 2 B per edge, 32 B per prefix slot
     return (size_t)((18 + 32 * slots) * std::max<uint64_t>(m, 1) + 96 * nwin + 4096);

@@ -65,8 +65,9 @@ struct DevGraph {
 // first from the root edge c).
 struct DevPlan {
     int32_t nv, ne, ntree;
-    int32_t pad0;
+    int32_t c2;                          // 1: Constraint 2 (distinct far endpoints) enforced
     int64_t delta;                       // capped at 2^33 (no change of meaning)
+    int64_t wdelta;                      // window unit: delta, or 2^33 without Constraint 3
     int32_t ea[kMaxE], eb[kMaxE], rank[kMaxE];
     int32_t pos_edge[kMaxE];             // motif edge at pi position
     int32_t is_tree[kMaxE];

@@ -61,17 +61,18 @@ __global__ void __launch_bounds__(256) k_dp(DevGraph g, DevPlan P, int q, int si
     if (pos >= g.m) return;
     const uint32_t t = __ldg((side ? g.in_t : g.out_t) + pos);
     const uint32_t z = __ldg((side ? g.in_dst : g.out_src) + pos);
-    const uint32_t o = __ldg((side ? g.in_nbr : g.out_nbr) + pos);
+    // the parent's other endpoint; without Constraint 2 nothing is excluded
+    const uint32_t o = P.c2 ? __ldg((side ? g.in_nbr : g.out_nbr) + pos) : kNone;
     const uint32_t pr = __ldg((side ? g.in_pair : g.out_pair) + pos);
-    const int64_t d = P.delta;
+    const int64_t d = P.delta, wd = P.wdelta;
     uint64_t wlo[2], whi[2], prod[2] = {1, 1};
     bool zero[2], ovf[2] = {false, false};
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
-        const int64_t wi = layer_window(t, p, d);
+        const int64_t wi = layer_window(t, p, wd);
         zero[p] = wi < 0;
-        wlo[p] = zero[p] ? 0 : (uint64_t)(wi * d);
-        whi[p] = zero[p] ? 0 : (uint64_t)((wi + 2) * d - 1);
+        wlo[p] = zero[p] ? 0 : (uint64_t)(wi * wd);
+        whi[p] = zero[p] ? 0 : (uint64_t)((wi + 2) * wd - 1);
     }
     if (!first) {
         const uint32_t xp = __ldg(g.in_to_out + pos);   // side 1 reads side 0's partial
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(256) k_dp(DevGraph g, DevPlan P, int q, int si
                     if (__ldg(nbr + x) == o) excl += wx;
                 }
             } else {
-                const uint32_t pe = (out == (side == 0)) ? pr : __ldg(g.rev_pair + pr);
+                const uint32_t pe = !P.c2 ? kNone : (out == (side == 0)) ? pr : __ldg(g.rev_pair + pr);
                 if (pe != kNone) {
                     const uint32_t xb = __ldg(g.pair_off + pe), xe = __ldg(g.pair_off + pe + 1);
                     const uint32_t ea = lower_idx(g.multi_t, xb, xe, lo);
@@ -367,7 +368,7 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     const DevPlan &P = mo->plan;
     cudaStream_t st = ctx->stream;
     const uint32_t m = g.m;
-    const int64_t d = P.delta;
+    const int64_t d = P.wdelta;   // window unit (delta, or one window without Constraint 3)
     int rc = TM_OK;
     cudaMemsetAsync(ctx->status, 0, 4, st);
     // ---- windows of each layer (K2): count both layers, then one block for
@@ -543,14 +544,14 @@ int export_weights(tm_ctx *ctx, tm_motif *mo, int q, int layer, uint64_t *host_o
     if (!out) return TM_E_NOMEM;
     int rc = TM_OK;
     if (P.tleaf[q] && q != 0) {
-        launch(ctx, k_leaf_weights, blocks_for(m, TB), TB, g.g_t, m, layer, P.delta, out);
+        launch(ctx, k_leaf_weights, blocks_for(m, TB), TB, g.g_t, m, layer, P.wdelta, out);
     } else if (q == 0) {
-        RootScan f{nullptr, g.g_t, layer, P.delta, nullptr};
+        RootScan f{nullptr, g.g_t, layer, P.wdelta, nullptr};
         launch(ctx, k_unprefix<RootScan>, blocks_for(m, TB), TB, f, mo->layer[layer].root_cdf, nullptr, m, out);
     } else {
         const OwnerBits ob{g.own_out, g.own_in, g.own_multi};
         bool o = P.tout[q] != 0;
-        DirScan f{nullptr, nullptr, o ? g.out_t : g.in_t, o ? ob.out : ob.in, layer, P.delta};
+        DirScan f{nullptr, nullptr, o ? g.out_t : g.in_t, o ? ob.out : ob.in, layer, P.wdelta};
         launch(ctx, k_unprefix<DirScan>, blocks_for(m, TB), TB, f, mo->layer[layer].pref_dir[P.tslot[q]],
                                                               o ? g.out_gid : g.in_gid, m, out);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "export");
