@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--serve-queries", type=int, default=100)
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--serve-workload", default="",
@@ -328,6 +329,7 @@ def run_ours(args, rank, world, local_rank):
                 "algorithmic_bytes_per_launch": int(algo), "model": model,
                 "launch_ms": round(kern_ms, 4)}
 
+    ablation = None if args.no_ablation else run_ablation(ctx, mo, k, args.seed, stream)
     batched = None if args.no_batch else run_batched(ctx, tg, synth, stream)
     served = None if args.no_serve else run_served(ctx, tg, synth, args.serve_queries, args.serve_rate)
 
@@ -348,6 +350,7 @@ def run_ours(args, rank, world, local_rank):
                         "dp_GBps": round(dp_bytes / (dp_ms / 1e3) / 1e9, 1) if dp_ms else None,
                         "dp_frac_of_peak": round(dp_bytes / (dp_ms / 1e3) / 1e9 / peak, 4) if dp_ms else None},
         "estimate": res.estimate, "W": state["W"], "hits2": res.hits2, "valid": res.valid,
+        "ablation": ablation,
         "batched": batched,
         "served": served,
     }
@@ -404,6 +407,30 @@ def run_batched(ctx, tg, synth, stream, reps=3):
             "autotuned_shape": {k_: tuned[k_] for k_ in ("tile", "threads", "smem_records")},
             "autotune_s": round(tune_s, 3), "shapes_tried": len(table),
             "timing": "best of %d, CUDA events on the library stream, weights precomputed" % reps}
+
+
+def run_ablation(ctx, mo, k, seed, stream):
+    """The paper's constraint ablation on the bench workload: Constraint 1
+    alone, 1+2 and 1+2+3 (the method), same motif, tree and k; per setting
+    W, the invalid-sample rates by reason, the valid rate, the estimate and
+    the weight-pass and sampler times (CUDA events)."""
+    import torch
+    out = {}
+    for name, c2, c3 in (("C1", False, False), ("C1+2", True, False), ("C1+2+3", True, True)):
+        m = ctx.motif(mo.nv, mo.edges, mo.rank, mo.delta).set_constraints(c2, c3)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        W = m.weights()
+        e1.record(stream)
+        r = m.sample(k, seed)
+        e2.record(stream)
+        e2.synchronize()
+        out[name] = {"W": W, "valid_rate": r.valid / k, "invalid_vertex_map": r.rej_vertex / k,
+                     "invalid_delta": r.rej_delta / k, "invalid_order": r.rej_order / k,
+                     "estimate": r.estimate, "weights_ms": round(e0.elapsed_time(e1), 3),
+                     "sample_ms": round(e1.elapsed_time(e2), 3)}
+        m.free()
+    return out
 
 
 def run_served(ctx, tg, synth, nq, rate, weight_budget=0):
