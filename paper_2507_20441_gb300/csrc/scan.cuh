@@ -323,5 +323,185 @@ int segmented_scan_u64(tm_ctx *ctx, const F &f, uint64_t n, uint64_t *out)
     return check_cuda(ctx, cudaGetLastError(), "segmented scan");
 }
 
+// ------------------------------------------ segmented u64, two layers ----
+// The same scan over pairs (layer 0, layer 1) that share their positions: one
+// gather of a 16-byte pair serves both layers.  Heads may differ per layer
+// (bit p of head2()).  Functor interface: value2(pos) -> ulonglong2 and
+// head2(pos) -> bits.
+struct SegAgg2 {
+    uint64_t v0, v1;
+    uint32_t f;     // bit p: the range contains a head of layer p
+    uint32_t pad;
+};
+
+__device__ __forceinline__ SegAgg2 seg_combine2(SegAgg2 a, SegAgg2 b, bool &ovf)
+{
+    SegAgg2 r;
+    r.f = a.f | b.f;
+    r.v0 = (b.f & 1u) ? b.v0 : add_chk(a.v0, b.v0, ovf);
+    r.v1 = (b.f & 2u) ? b.v1 : add_chk(a.v1, b.v1, ovf);
+    r.pad = 0;
+    return r;
+}
+
+__device__ __forceinline__ SegAgg2 seg_shfl_up2(SegAgg2 a, int o)
+{
+    SegAgg2 y;
+    y.v0 = __shfl_up_sync(0xffffffffu, a.v0, o);
+    y.v1 = __shfl_up_sync(0xffffffffu, a.v1, o);
+    y.f = __shfl_up_sync(0xffffffffu, a.f, o);
+    y.pad = 0;
+    return y;
+}
+
+template <class F>
+__global__ void k_segscan2_reduce(F f, uint64_t n, SegAgg2 *__restrict__ aggs, ulonglong2 *__restrict__ stash,
+                                  uint32_t *status)
+{
+    __shared__ SegAgg2 warp_agg[SCAN_THREADS / 32];
+    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
+    bool ovf = false;
+    SegAgg2 a{0, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        const uint64_t i = base + j;
+        if (i < n) {
+            const ulonglong2 v = f.value2(i);
+            if (stash) stash[i] = v;          // gathered once; the rescan reads it back in order
+            SegAgg2 x{v.x, v.y, f.head2(i), 0};
+            a = seg_combine2(a, x, ovf);
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        const SegAgg2 y = seg_shfl_up2(a, o);
+        if (lane >= o) a = seg_combine2(y, a, ovf);
+    }
+    if (lane == 31) warp_agg[warp] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        SegAgg2 t = warp_agg[0];
+        for (int w = 1; w < SCAN_THREADS / 32; ++w) t = seg_combine2(t, warp_agg[w], ovf);
+        aggs[blockIdx.x] = t;
+    }
+    if (ovf) latch(status, ST_OVERFLOW);
+}
+
+__global__ void k_segscan2_carries(SegAgg2 *__restrict__ aggs, uint64_t ntiles, uint32_t *status)
+{
+    __shared__ SegAgg2 warp_tot[32];
+    bool ovf = false;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t per = (ntiles + blockDim.x - 1) / blockDim.x;
+    uint64_t lo = (uint64_t)threadIdx.x * per, hi = lo + per;
+    if (hi > ntiles) hi = ntiles;
+    if (lo > ntiles) lo = ntiles;
+    SegAgg2 a{0, 0, 0, 0};
+    for (uint64_t i = lo; i < hi; ++i) a = seg_combine2(a, aggs[i], ovf);
+    SegAgg2 incl = a;
+    for (int o = 1; o < 32; o <<= 1) {
+        const SegAgg2 y = seg_shfl_up2(incl, o);
+        if (lane >= o) incl = seg_combine2(y, incl, ovf);
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) / 32;
+        const SegAgg2 w = lane < nw ? warp_tot[lane] : SegAgg2{0, 0, 0, 0};
+        SegAgg2 wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const SegAgg2 y = seg_shfl_up2(wi, o);
+            if (lane >= o) wi = seg_combine2(y, wi, ovf);
+        }
+        SegAgg2 ex = seg_shfl_up2(wi, 1);
+        if (lane == 0) ex = SegAgg2{0, 0, 0, 0};
+        if (lane < nw) warp_tot[lane] = ex;
+    }
+    __syncthreads();
+    const SegAgg2 ex_lane = seg_shfl_up2(incl, 1);
+    SegAgg2 run = warp_tot[warp];
+    if (lane > 0) run = seg_combine2(run, ex_lane, ovf);
+    for (uint64_t i = lo; i < hi; ++i) {
+        const SegAgg2 c = aggs[i];
+        aggs[i] = run;
+        run = seg_combine2(run, c, ovf);
+    }
+    if (ovf) latch(status, ST_OVERFLOW);
+}
+
+template <class F>
+__global__ void k_segscan2_final(F f, uint64_t n, const SegAgg2 *__restrict__ carries,
+                                 const ulonglong2 *__restrict__ stash, uint64_t *__restrict__ out0,
+                                 uint64_t *__restrict__ out1, uint32_t *status)
+{
+    __shared__ SegAgg2 warp_agg[SCAN_THREADS / 32];
+    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
+    bool ovf = false;
+    ulonglong2 v[SCAN_ITEMS];
+    uint32_t hbits = 0;
+    SegAgg2 a{0, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        const uint64_t i = base + j;
+        v[j] = make_ulonglong2(0, 0);
+        if (i < n) {
+            v[j] = stash ? stash[i] : f.value2(i);
+            const uint32_t h = f.head2(i);
+            hbits |= h << (2 * j);
+            SegAgg2 x{v[j].x, v[j].y, h, 0};
+            a = seg_combine2(a, x, ovf);
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    SegAgg2 incl = a;
+    for (int o = 1; o < 32; o <<= 1) {
+        const SegAgg2 y = seg_shfl_up2(incl, o);
+        if (lane >= o) incl = seg_combine2(y, incl, ovf);
+    }
+    if (lane == 31) warp_agg[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        SegAgg2 run = carries[blockIdx.x];
+        for (int w = 0; w < SCAN_THREADS / 32; ++w) {
+            const SegAgg2 c = warp_agg[w];
+            warp_agg[w] = run;
+            run = seg_combine2(run, c, ovf);
+        }
+    }
+    __syncthreads();
+    const SegAgg2 excl_lane = seg_shfl_up2(incl, 1);
+    SegAgg2 pre = warp_agg[warp];
+    if (lane > 0) pre = seg_combine2(pre, excl_lane, ovf);
+    uint64_t r0 = pre.v0, r1 = pre.v1;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        const uint64_t i = base + j;
+        if (i < n) {
+            const uint32_t h = (hbits >> (2 * j)) & 3u;
+            r0 = (h & 1u) ? v[j].x : add_chk(r0, v[j].x, ovf);
+            r1 = (h & 2u) ? v[j].y : add_chk(r1, v[j].y, ovf);
+            out0[i] = r0;
+            out1[i] = r1;
+        }
+    }
+    if (ovf) latch(status, ST_OVERFLOW);
+}
+
+template <class F>
+int segmented_scan2_u64(tm_ctx *ctx, const F &f, uint64_t n, uint64_t *out0, uint64_t *out1)
+{
+    if (n == 0) return TM_OK;
+    const uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    ScratchScope scope(ctx);
+    SegAgg2 *aggs = (SegAgg2 *)salloc(ctx, tiles * sizeof(SegAgg2));
+    ulonglong2 *stash = F::kGathered ? (ulonglong2 *)salloc(ctx, n * sizeof(ulonglong2)) : nullptr;
+    if (!aggs || (F::kGathered && !stash)) return TM_E_NOMEM;
+    launch(ctx, k_segscan2_reduce<F>, (unsigned)tiles, SCAN_THREADS, f, n, aggs, stash, ctx->status);
+    launch(ctx, k_segscan2_carries, 1, 1024, aggs, tiles, ctx->status);
+    launch(ctx, k_segscan2_final<F>, (unsigned)tiles, SCAN_THREADS, f, n, aggs, (const ulonglong2 *)stash, out0,
+           out1, ctx->status);
+    return check_cuda(ctx, cudaGetLastError(), "segmented scan");
+}
+
 }  // namespace
 }  // namespace timest

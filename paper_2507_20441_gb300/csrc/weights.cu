@@ -52,10 +52,9 @@ constexpr uint32_t kScanLimit = 48;
 // Overflow rule: a factor >= 2^64, or an exact product >= 2^64 with no zero
 // factor.
 __global__ void __launch_bounds__(256) k_dp(DevGraph g, DevPlan P, int q, int side, int first, int last,
-                                            ChildPrefix cp, uint64_t *__restrict__ o0, uint64_t *__restrict__ o1,
-                                            const uint64_t *__restrict__ i0, const uint64_t *__restrict__ i1,
-                                            const uint8_t *__restrict__ pin, uint8_t *__restrict__ pout,
-                                            uint32_t *status)
+                                            ChildPrefix cp, ulonglong2 *__restrict__ wout,
+                                            const ulonglong2 *__restrict__ in, const uint8_t *__restrict__ pin,
+                                            uint8_t *__restrict__ pout, uint32_t *status)
 {
     const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= g.m) return;
@@ -75,12 +74,14 @@ __global__ void __launch_bounds__(256) k_dp(DevGraph g, DevPlan P, int q, int si
         whi[p] = zero[p] ? 0 : (uint64_t)((wi + 2) * wd - 1);
     }
     if (!first) {
-        const uint32_t xp = __ldg(g.in_to_out + pos);   // side 1 reads side 0's partial
+        const uint32_t xp = __ldg(g.in_to_out + pos);   // side 1 reads side 0's partial (both layers)
+        const ulonglong2 pv = __ldg(in + xp);
+        const uint32_t pb = pin[xp];
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
             if (zero[p]) continue;
-            prod[p] = __ldg((p ? i1 : i0) + xp);
-            ovf[p] = pin[(size_t)p * g.m + xp] != 0;
+            prod[p] = p ? pv.y : pv.x;
+            ovf[p] = (pb >> p) & 1u;
             if (prod[p] == 0) zero[p] = true;
         }
     }
@@ -140,25 +141,19 @@ __global__ void __launch_bounds__(256) k_dp(DevGraph g, DevPlan P, int q, int si
             else prod[p] = mul_chk(prod[p], sum, ovf[p]);
         }
     }
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        (p ? o1 : o0)[pos] = zero[p] ? 0 : prod[p];
-        if (!last) pout[(size_t)p * g.m + pos] = (!zero[p] && ovf[p]) ? 1 : 0;
-    }
+    wout[pos] = make_ulonglong2(zero[0] ? 0 : prod[0], zero[1] ? 0 : prod[1]);   // both layers, one store
+    if (!last) pout[pos] = (uint8_t)(((!zero[0] && ovf[0]) ? 1u : 0u) | ((!zero[1] && ovf[1]) ? 2u : 0u));
     if (last && ((!zero[0] && ovf[0]) || (!zero[1] && ovf[1]))) latch(status, ST_OVERFLOW);
 }
 
 // ---- scans over the three orders ----------------------------------------
 // segment = (owner, window of layer p); owner boundaries come from a bit set.
-struct DirScan {
-    static constexpr bool kGathered = true;
-    const uint64_t *w;          // weights in the order the DP wrote them
-    const uint32_t *perm;       // scan position -> weight position (null: same order)
+// Segment heads of one layer (exports rebuild weights from prefix sums).
+struct DirHead {
     const uint32_t *tarr;       // position -> t'
     const uint32_t *ownbits;    // bit set: position starts a new owner
     int p;
     int64_t d;
-    __device__ uint64_t value(uint64_t i) const { return perm ? __ldg(w + __ldg(perm + i)) : __ldg(w + i); }
     __device__ bool head(uint64_t i) const
     {
         if (i == 0) return true;
@@ -167,18 +162,49 @@ struct DirScan {
     }
 };
 
-struct RootScan {
-    static constexpr bool kGathered = true;
-    const uint64_t *w;          // root weights in list order
+struct RootHead {
     const uint32_t *tarr;       // g_t
     int p;
     int64_t d;
-    const uint32_t *perm;       // gid -> weight position
-    __device__ uint64_t value(uint64_t i) const { return perm ? __ldg(w + __ldg(perm + i)) : __ldg(w + i); }
     __device__ bool head(uint64_t i) const
     {
         if (i == 0) return true;
         return layer_window(__ldg(tarr + i), p, d) != layer_window(__ldg(tarr + i - 1), p, d);
+    }
+};
+
+// Both layers at once (two-lane scans): the pair of weights of a position is
+// one 16-byte gather; heads are per layer (bit p).
+struct DirScan2 {
+    static constexpr bool kGathered = true;
+    const ulonglong2 *w;        // (layer 0, layer 1) weights in the order the DP wrote them
+    const uint32_t *perm;       // scan position -> weight position (null: same order)
+    const uint32_t *tarr;       // position -> t'
+    const uint32_t *ownbits;    // bit set: position starts a new owner
+    int64_t d;
+    __device__ ulonglong2 value2(uint64_t i) const { return __ldg(w + (perm ? __ldg(perm + i) : i)); }
+    __device__ uint32_t head2(uint64_t i) const
+    {
+        if (i == 0 || ((__ldg(ownbits + (i >> 5)) >> (i & 31)) & 1u)) return 3u;
+        const uint32_t a = __ldg(tarr + i), b = __ldg(tarr + i - 1);
+        return (layer_window(a, 0, d) != layer_window(b, 0, d) ? 1u : 0u) |
+               (layer_window(a, 1, d) != layer_window(b, 1, d) ? 2u : 0u);
+    }
+};
+
+struct RootScan2 {
+    static constexpr bool kGathered = true;
+    const ulonglong2 *w;        // root weight pairs in list order
+    const uint32_t *tarr;       // g_t
+    int64_t d;
+    const uint32_t *perm;       // gid -> weight position
+    __device__ ulonglong2 value2(uint64_t i) const { return __ldg(w + (perm ? __ldg(perm + i) : i)); }
+    __device__ uint32_t head2(uint64_t i) const
+    {
+        if (i == 0) return 3u;
+        const uint32_t a = __ldg(tarr + i), b = __ldg(tarr + i - 1);
+        return (layer_window(a, 0, d) != layer_window(b, 0, d) ? 1u : 0u) |
+               (layer_window(a, 1, d) != layer_window(b, 1, d) ? 2u : 0u);
     }
 };
 
@@ -431,11 +457,10 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     }
     // ---- DP over tree nodes in increasing height (K3) + prefixes (K4)
     const OwnerBits ob{g.own_out, g.own_in, g.own_multi};
-    uint64_t *w[2], *pw[2] = {nullptr, nullptr};
-    uint8_t *pend = nullptr;
-    w[0] = (uint64_t *)salloc(ctx, (size_t)(m ? m : 1) * 8);
-    w[1] = (uint64_t *)salloc(ctx, (size_t)(m ? m : 1) * 8);
-    if (!w[0] || !w[1]) return TM_E_NOMEM;
+    ulonglong2 *w = nullptr, *pw = nullptr;   // (layer 0, layer 1) weight pairs
+    uint8_t *pend = nullptr;                  // bit p: pending overflow of layer p's partial
+    w = (ulonglong2 *)salloc(ctx, (size_t)(m ? m : 1) * 16);
+    if (!w) return TM_E_NOMEM;
     ChildPrefix cp{};
     int maxh = 0;
     for (int q = 0; q < P.ntree; ++q) maxh = std::max(maxh, (int)P.height[q]);
@@ -452,23 +477,20 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
         const bool in_order = has[1];
         {
             PhaseScope ph(ctx, TM_PH_DP);
-            if (has[0] && has[1] && !pw[0]) {
-                pw[0] = (uint64_t *)salloc(ctx, (size_t)(m ? m : 1) * 8);
-                pw[1] = (uint64_t *)salloc(ctx, (size_t)(m ? m : 1) * 8);
-                pend = (uint8_t *)salloc(ctx, (size_t)(m ? m : 1) * 2);
-                if (!pw[0] || !pw[1] || !pend) return TM_E_NOMEM;
+            if (has[0] && has[1] && !pw) {
+                pw = (ulonglong2 *)salloc(ctx, (size_t)(m ? m : 1) * 16);
+                pend = (uint8_t *)salloc(ctx, (size_t)(m ? m : 1));
+                if (!pw || !pend) return TM_E_NOMEM;
             }
             if (m) {
                 if (has[0] && has[1]) {
-                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, q, 0, 1, 0, cp, pw[0], pw[1],
-                           (const uint64_t *)nullptr, (const uint64_t *)nullptr, (const uint8_t *)nullptr, pend,
-                           ctx->status);
-                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, q, 1, 0, 1, cp, w[0], w[1], (const uint64_t *)pw[0],
-                           (const uint64_t *)pw[1], (const uint8_t *)pend, (uint8_t *)nullptr, ctx->status);
+                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, q, 0, 1, 0, cp, pw, (const ulonglong2 *)nullptr,
+                           (const uint8_t *)nullptr, pend, ctx->status);
+                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, q, 1, 0, 1, cp, w, (const ulonglong2 *)pw,
+                           (const uint8_t *)pend, (uint8_t *)nullptr, ctx->status);
                 } else {
-                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, q, in_order ? 1 : 0, 1, 1, cp, w[0], w[1],
-                           (const uint64_t *)nullptr, (const uint64_t *)nullptr, (const uint8_t *)nullptr,
-                           (uint8_t *)nullptr, ctx->status);
+                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, q, in_order ? 1 : 0, 1, 1, cp, w,
+                           (const ulonglong2 *)nullptr, (const uint8_t *)nullptr, (uint8_t *)nullptr, ctx->status);
                 }
             }
         }
@@ -477,11 +499,11 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
         if (q == 0) {
             PhaseScope ph(ctx, TM_PH_ROOT);
             GuideArgs ga{};
+            RootScan2 f{w, g.g_t, d, in_order ? g.in_pos : g.out_pos};
+            rc = segmented_scan2_u64(ctx, f, m, mo->layer[0].root_cdf, mo->layer[1].root_cdf);
+            if (rc) return rc;
             for (int p = 0; p < 2; ++p) {
                 LayerData &L = mo->layer[p];
-                RootScan f{w[p], g.g_t, p, d, in_order ? g.in_pos : g.out_pos};
-                rc = segmented_scan_u64(ctx, f, m, L.root_cdf);
-                if (rc) return rc;
                 ga.L[p] = GuideLayer{L.root_cdf, L.win_beg, flag[p], pos[p], L.nwin, L.win_gshift, L.win_goff, L.guide};
             }
             // guide tables of the root search, both layers
@@ -496,16 +518,16 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
             // scan order of the parent's candidate list -> position of the weight
             const uint32_t *dmap = (out == !in_order) ? nullptr : (out ? g.out_to_in : g.in_to_out);
             const uint32_t *mmap = in_order ? g.multi_to_in : g.multi_to_out;
+            LayerData &L0 = mo->layer[0], &L1 = mo->layer[1];
+            DirScan2 fd{w, dmap, out ? g.out_t : g.in_t, out ? ob.out : ob.in, d};
+            rc = segmented_scan2_u64(ctx, fd, m, L0.pref_dir[slot], L1.pref_dir[slot]);
+            if (rc) return rc;
+            DirScan2 fm{w, mmap, g.multi_t, ob.multi, d};
+            rc = segmented_scan2_u64(ctx, fm, m, L0.pref_multi[slot], L1.pref_multi[slot]);
+            if (rc) return rc;
             for (int p = 0; p < 2; ++p) {
-                LayerData &L = mo->layer[p];
-                DirScan fd{w[p], dmap, out ? g.out_t : g.in_t, out ? ob.out : ob.in, p, d};
-                rc = segmented_scan_u64(ctx, fd, m, L.pref_dir[slot]);
-                if (rc) return rc;
-                DirScan fm{w[p], mmap, g.multi_t, ob.multi, p, d};
-                rc = segmented_scan_u64(ctx, fm, m, L.pref_multi[slot]);
-                if (rc) return rc;
-                cp.pd[p][slot] = L.pref_dir[slot];
-                cp.pm[p][slot] = L.pref_multi[slot];
+                cp.pd[p][slot] = mo->layer[p].pref_dir[slot];
+                cp.pm[p][slot] = mo->layer[p].pref_multi[slot];
             }
         }
     }
@@ -546,13 +568,13 @@ int export_weights(tm_ctx *ctx, tm_motif *mo, int q, int layer, uint64_t *host_o
     if (P.tleaf[q] && q != 0) {
         launch(ctx, k_leaf_weights, blocks_for(m, TB), TB, g.g_t, m, layer, P.wdelta, out);
     } else if (q == 0) {
-        RootScan f{nullptr, g.g_t, layer, P.wdelta, nullptr};
-        launch(ctx, k_unprefix<RootScan>, blocks_for(m, TB), TB, f, mo->layer[layer].root_cdf, nullptr, m, out);
+        RootHead f{g.g_t, layer, P.wdelta};
+        launch(ctx, k_unprefix<RootHead>, blocks_for(m, TB), TB, f, mo->layer[layer].root_cdf, nullptr, m, out);
     } else {
         const OwnerBits ob{g.own_out, g.own_in, g.own_multi};
         bool o = P.tout[q] != 0;
-        DirScan f{nullptr, nullptr, o ? g.out_t : g.in_t, o ? ob.out : ob.in, layer, P.wdelta};
-        launch(ctx, k_unprefix<DirScan>, blocks_for(m, TB), TB, f, mo->layer[layer].pref_dir[P.tslot[q]],
+        DirHead f{o ? g.out_t : g.in_t, o ? ob.out : ob.in, layer, P.wdelta};
+        launch(ctx, k_unprefix<DirHead>, blocks_for(m, TB), TB, f, mo->layer[layer].pref_dir[P.tslot[q]],
                                                               o ? g.out_gid : g.in_gid, m, out);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "export");
     }
