@@ -429,8 +429,11 @@ __global__ void k_segscan2_carries(SegAgg2 *__restrict__ aggs, uint64_t ntiles, 
     if (ovf) latch(status, ST_OVERFLOW);
 }
 
+#ifndef TM_SCAN2_MINB
+#define TM_SCAN2_MINB 4   // four blocks of 256 per SM (measured faster than two)
+#endif
 template <class F>
-__global__ void k_segscan2_final(F f, uint64_t n, const SegAgg2 *__restrict__ carries,
+__global__ void __launch_bounds__(SCAN_THREADS, TM_SCAN2_MINB) k_segscan2_final(F f, uint64_t n, const SegAgg2 *__restrict__ carries,
                                  const ulonglong2 *__restrict__ stash, uint64_t *__restrict__ out0,
                                  uint64_t *__restrict__ out1, uint32_t *status)
 {

@@ -51,7 +51,10 @@ constexpr uint32_t kScanLimit = 48;
 // product and pending-overflow bit through the out->in position map.
 // Overflow rule: a factor >= 2^64, or an exact product >= 2^64 with no zero
 // factor.
-__global__ void __launch_bounds__(256) k_dp(DevGraph g, DevPlan P, int q, int side, int first, int last,
+#ifndef TM_DP_MINB
+#define TM_DP_MINB 6   // 40 registers: six blocks of 256 per SM (measured fastest)
+#endif
+__global__ void __launch_bounds__(256, TM_DP_MINB) k_dp(DevGraph g, DevPlan P, int q, int side, int first, int last,
                                             ChildPrefix cp, ulonglong2 *__restrict__ wout,
                                             const ulonglong2 *__restrict__ in, const uint8_t *__restrict__ pin,
                                             uint8_t *__restrict__ pout, uint32_t *status)
