@@ -380,6 +380,32 @@ __global__ void k_compact_input(const uint32_t *__restrict__ src, const uint32_t
 }
 
 // After the GLOBAL sort: flag tuples equal to their predecessor.
+// After a sort by t' alone: order each run of equal t' by (src, dst), one
+// thread per run (runs are short in temporal graphs).  A run longer than
+// kRunMax is left alone and flagged; the caller then sorts by all three keys.
+constexpr uint32_t kRunMax = 32;
+__global__ void k_order_runs(const uint32_t *__restrict__ t, uint32_t *__restrict__ s, uint32_t *__restrict__ d,
+                             uint32_t m, uint32_t *__restrict__ too_long)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m || (i > 0 && t[i - 1] == t[i])) return;   // run heads only
+    const uint32_t ti = t[i];
+    uint32_t j = i + 1;
+    while (j < m && t[j] == ti && j - i < kRunMax) ++j;
+    if (j < m && t[j] == ti) { atomicOr(too_long, 1u); return; }
+    const uint32_t len = j - i;
+    if (len < 2) return;
+    uint64_t key[kRunMax];
+    for (uint32_t k = 0; k < len; ++k) key[k] = ((uint64_t)s[i + k] << 32) | d[i + k];
+    for (uint32_t k = 1; k < len; ++k) {   // insertion sort
+        const uint64_t x = key[k];
+        uint32_t q = k;
+        while (q > 0 && key[q - 1] > x) { key[q] = key[q - 1]; --q; }
+        key[q] = x;
+    }
+    for (uint32_t k = 0; k < len; ++k) { s[i + k] = (uint32_t)(key[k] >> 32); d[i + k] = (uint32_t)key[k]; }
+}
+
 __global__ void k_flag_unique(const uint32_t *__restrict__ t, const uint32_t *__restrict__ s,
                               const uint32_t *__restrict__ d, uint32_t m, uint32_t *__restrict__ keep,
                               unsigned long long *ndup)
@@ -575,26 +601,41 @@ int build_csr(tm_ctx *ctx)
         launch(ctx, k_compact_input, blocks_for(m0, TB), TB, ctx->in_src, ctx->in_dst, ctx->in_t, m0, nullptr, nullptr,
                                                            tmin, T0, S0, D0);
     }
-    // ---- GLOBAL order: LSD by dst, then src, then t'
+    // ---- GLOBAL order (t', src, dst): LSD by t', then each run of equal t'
+    // ordered by (src, dst) in place; a run longer than kRunMax sends the
+    // whole array through the full LSD sort by dst, src and t' instead
     sec.reset();
     sec.reset(new PhaseScope(ctx, TM_PH_CSR_GLOBAL));
     int vbits = bits_for(n ? n - 1 : 0);
     int tbits = bits_for((uint64_t)(tmax - tmin));
-    rc = radix_sort(ctx, D0, S0, T0, m, vbits);
-    if (!rc) rc = radix_sort(ctx, S0, D0, T0, m, vbits);
-    if (!rc) rc = radix_sort(ctx, T0, S0, D0, m, tbits);
+    rc = radix_sort(ctx, T0, S0, D0, m, tbits);
     if (rc) return rc;
-    // ---- duplicates
+    // ---- duplicates (and the run check, read with the same copy)
     {
         uint32_t *keep = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);
-        unsigned long long *nd = (unsigned long long *)salloc(ctx, 8);
+        unsigned long long *nd = (unsigned long long *)salloc(ctx, 16);   // [0] duplicates, [1] a run too long
         if (!keep || !nd) return TM_E_NOMEM;
-        cudaMemsetAsync(nd, 0, 8, st);
-        if (m) launch(ctx, k_flag_unique, blocks_for(m, TB), TB, T0, S0, D0, m, keep, nd);
-        unsigned long long ndup = 0;
-        copy_d2h(ctx, &ndup, nd, 8);
+        cudaMemsetAsync(nd, 0, 16, st);
+        if (m) {
+            launch(ctx, k_order_runs, blocks_for(m, TB), TB, (const uint32_t *)T0, S0, D0, m, (uint32_t *)(nd + 1));
+            launch(ctx, k_flag_unique, blocks_for(m, TB), TB, T0, S0, D0, m, keep, nd);
+        }
+        unsigned long long hnd[2] = {0, 0};
+        copy_d2h(ctx, hnd, nd, 16);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "duplicate scan");
         if (rc) return rc;
+        if (hnd[1]) {
+            rc = radix_sort(ctx, D0, S0, T0, m, vbits);
+            if (!rc) rc = radix_sort(ctx, S0, D0, T0, m, vbits);
+            if (!rc) rc = radix_sort(ctx, T0, S0, D0, m, tbits);
+            if (rc) return rc;
+            cudaMemsetAsync(nd, 0, 8, st);
+            launch(ctx, k_flag_unique, blocks_for(m, TB), TB, T0, S0, D0, m, keep, nd);
+            copy_d2h(ctx, hnd, nd, 8);
+            rc = check_cuda(ctx, cudaStreamSynchronize(st), "duplicate scan");
+            if (rc) return rc;
+        }
+        const unsigned long long ndup = hnd[0];
         if (ndup && !(ctx->load_flags & TM_DEDUP)) {
             return set_err(ctx, TM_E_DUP, "input repeats a (u,v,t) tuple (pass TM_DEDUP to drop repeats)");
         }

@@ -72,6 +72,24 @@ def test_csr_global_order(tg, oracle_mod):
     assert ctx.t_min == G.t_min and ctx.T == G.span
 
 
+@pytest.mark.parametrize("t_hi,m", [(5, 3000), (400, 3000), (1, 700), (60_000, 150_000)])
+def test_csr_global_order_with_equal_times(tg, oracle_mod, t_hi, m):
+    """Runs of equal t' (ordered by (src, dst) after the time sort) short and
+    long: t_hi = 5 or 1 gives runs of hundreds of edges (the full three-key
+    sort), t_hi = 400 and 60,000 runs of a few edges; duplicates dropped."""
+    rng = np.random.default_rng(t_hi)
+    n = 50
+    s = rng.integers(0, n, m).astype(np.uint32)
+    d = ((s + 1 + rng.integers(0, n - 1, m)) % n).astype(np.uint32)
+    t = rng.integers(0, t_hi, m).astype(np.int64) + 77
+    ctx, G = make_pair(tg, oracle_mod, n, s, d, t, flags=2)
+    s1, d1, t1 = ctx.edges()
+    so, do, to = G.edges()
+    assert ctx.m == G.m
+    assert np.array_equal(s1, so) and np.array_equal(d1, do) and np.array_equal(t1.astype(np.int64), to)
+    ctx.close()
+
+
 @pytest.mark.parametrize("flags", [0, 2, 4, 6])
 def test_input_contract(tg, oracle_mod, flags):
     n, s, d, t = small_random_graph(3, n=12, m=300, t_hi=50)
