@@ -82,7 +82,9 @@ def test_csr_global_order_with_equal_times(tg, oracle_mod, t_hi, m):
     s = rng.integers(0, n, m).astype(np.uint32)
     d = ((s + 1 + rng.integers(0, n - 1, m)) % n).astype(np.uint32)
     t = rng.integers(0, t_hi, m).astype(np.int64) + 77
-    ctx, G = make_pair(tg, oracle_mod, n, s, d, t, flags=2)
+    ctx = tg.Context()
+    ctx.load_graph(n, s, d, t, flags=tg.TM_DEDUP)
+    G = oracle_mod.Graph(n, s, d, t, flags=oracle_mod.DEDUP)
     s1, d1, t1 = ctx.edges()
     so, do, to = G.edges()
     assert ctx.m == G.m
