@@ -380,19 +380,27 @@ __global__ void k_compact_input(const uint32_t *__restrict__ src, const uint32_t
 }
 
 // After the GLOBAL sort: flag tuples equal to their predecessor.
-// After a sort by t' alone: order each run of equal t' by (src, dst), one
-// thread per run (runs are short in temporal graphs).  A run longer than
-// kRunMax is left alone and flagged; the caller then sorts by all three keys.
+// After a sort by t' alone: order each run of equal t' by (src, dst).  Runs
+// of up to kRunMax edges are sorted by their head's thread; runs of up to
+// kBlockRunMax are listed (start, length) for k_order_long_runs; a longer run
+// is flagged and the caller sorts by all three keys instead.
 constexpr uint32_t kRunMax = 32;
+constexpr uint32_t kBlockRunMax = 4096;
 __global__ void k_order_runs(const uint32_t *__restrict__ t, uint32_t *__restrict__ s, uint32_t *__restrict__ d,
-                             uint32_t m, uint32_t *__restrict__ too_long)
+                             uint32_t m, uint32_t *__restrict__ too_long, uint2 *__restrict__ long_runs,
+                             uint32_t *__restrict__ n_long)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m || (i > 0 && t[i - 1] == t[i])) return;   // run heads only
     const uint32_t ti = t[i];
     uint32_t j = i + 1;
     while (j < m && t[j] == ti && j - i < kRunMax) ++j;
-    if (j < m && t[j] == ti) { atomicOr(too_long, 1u); return; }
+    if (j < m && t[j] == ti) {
+        while (j < m && t[j] == ti && j - i <= kBlockRunMax) ++j;
+        if (j - i > kBlockRunMax) atomicOr(too_long, 1u);
+        else long_runs[atomicAdd(n_long, 1u)] = make_uint2(i, j - i);   // at most m / 33 runs
+        return;
+    }
     const uint32_t len = j - i;
     if (len < 2) return;
     uint64_t key[kRunMax];
@@ -404,6 +412,42 @@ __global__ void k_order_runs(const uint32_t *__restrict__ t, uint32_t *__restric
         key[q] = x;
     }
     for (uint32_t k = 0; k < len; ++k) { s[i + k] = (uint32_t)(key[k] >> 32); d[i + k] = (uint32_t)key[k]; }
+}
+
+// One block per listed run (33 .. kBlockRunMax edges): bitonic sort of the
+// (src, dst) keys in shared memory.  Blocks stride over the list, whose
+// length is read on the device.
+__global__ void __launch_bounds__(256) k_order_long_runs(uint32_t *__restrict__ s, uint32_t *__restrict__ d,
+                                                         const uint2 *__restrict__ long_runs,
+                                                         const uint32_t *__restrict__ n_long)
+{
+    __shared__ uint64_t key[kBlockRunMax];
+    const uint32_t nl = *n_long;
+    for (uint32_t r = blockIdx.x; r < nl; r += gridDim.x) {
+        const uint2 run = long_runs[r];
+        uint32_t P = 64;
+        while (P < run.y) P <<= 1;
+        for (uint32_t k = threadIdx.x; k < P; k += blockDim.x)
+            key[k] = k < run.y ? (((uint64_t)s[run.x + k] << 32) | d[run.x + k]) : ~0ull;
+        __syncthreads();
+        for (uint32_t size = 2; size <= P; size <<= 1)
+            for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+                for (uint32_t k = threadIdx.x; k < P; k += blockDim.x) {
+                    const uint32_t l = k ^ stride;
+                    if (l > k) {
+                        const bool up = (k & size) == 0;
+                        const uint64_t a = key[k], b = key[l];
+                        if ((a > b) == up) { key[k] = b; key[l] = a; }
+                    }
+                }
+                __syncthreads();
+            }
+        for (uint32_t k = threadIdx.x; k < run.y; k += blockDim.x) {
+            s[run.x + k] = (uint32_t)(key[k] >> 32);
+            d[run.x + k] = (uint32_t)key[k];
+        }
+        __syncthreads();
+    }
 }
 
 __global__ void k_flag_unique(const uint32_t *__restrict__ t, const uint32_t *__restrict__ s,
@@ -613,11 +657,16 @@ int build_csr(tm_ctx *ctx)
     // ---- duplicates (and the run check, read with the same copy)
     {
         uint32_t *keep = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);
-        unsigned long long *nd = (unsigned long long *)salloc(ctx, 16);   // [0] duplicates, [1] a run too long
-        if (!keep || !nd) return TM_E_NOMEM;
-        cudaMemsetAsync(nd, 0, 16, st);
+        // [0] duplicates, [1] a run too long, [2] number of listed runs
+        unsigned long long *nd = (unsigned long long *)salloc(ctx, 24);
+        uint2 *long_runs = (uint2 *)salloc(ctx, ((size_t)m / (kRunMax + 1) + 1) * sizeof(uint2));
+        if (!keep || !nd || !long_runs) return TM_E_NOMEM;
+        cudaMemsetAsync(nd, 0, 24, st);
         if (m) {
-            launch(ctx, k_order_runs, blocks_for(m, TB), TB, (const uint32_t *)T0, S0, D0, m, (uint32_t *)(nd + 1));
+            launch(ctx, k_order_runs, blocks_for(m, TB), TB, (const uint32_t *)T0, S0, D0, m, (uint32_t *)(nd + 1),
+                   long_runs, (uint32_t *)(nd + 2));
+            launch(ctx, k_order_long_runs, (unsigned)ctx->num_sms * 2, 256, S0, D0, (const uint2 *)long_runs,
+                   (const uint32_t *)(nd + 2));
             launch(ctx, k_flag_unique, blocks_for(m, TB), TB, T0, S0, D0, m, keep, nd);
         }
         unsigned long long hnd[2] = {0, 0};

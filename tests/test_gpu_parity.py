@@ -72,11 +72,12 @@ def test_csr_global_order(tg, oracle_mod):
     assert ctx.t_min == G.t_min and ctx.T == G.span
 
 
-@pytest.mark.parametrize("t_hi,m", [(5, 3000), (400, 3000), (1, 700), (60_000, 150_000)])
+@pytest.mark.parametrize("t_hi,m", [(5, 3000), (400, 3000), (1, 700), (1, 6000), (60_000, 150_000)])
 def test_csr_global_order_with_equal_times(tg, oracle_mod, t_hi, m):
-    """Runs of equal t' (ordered by (src, dst) after the time sort) short and
-    long: t_hi = 5 or 1 gives runs of hundreds of edges (the full three-key
-    sort), t_hi = 400 and 60,000 runs of a few edges; duplicates dropped."""
+    """Runs of equal t' are ordered by (src, dst) after the time sort: runs of
+    a few edges by one thread (t_hi = 400, 60,000), runs of hundreds by one
+    block (t_hi = 5, and 1 with 700 edges), a run beyond 4096 edges by the full
+    three-key sort (t_hi = 1 with 6000 edges); duplicates dropped."""
     rng = np.random.default_rng(t_hi)
     n = 50
     s = rng.integers(0, n, m).astype(np.uint32)
