@@ -4,11 +4,14 @@
 //   GLOBAL order (t', src, dst)      -> gid, the edge id used everywhere
 //   out-lists   (src | t', dst)      -> out_off / out_t / out_nbr / out_gid
 //   in-lists    (dst | t', src)      -> in_off / in_t / in_nbr / in_gid
-//   multi-edge  (src, dst | t')      -> pairs, pair_off / multi_t / multi_gid
-// with t' = t - t_min.  Every ordering comes from a stable LSD radix sort
-// (up to 9-bit digits) written here; the OUT and IN orders are stable re-sorts of
-// the GLOBAL order by one endpoint, and the multi-edge order is a stable
-// re-sort of the IN order by source.
+//   multi-edge  (src, dst | t')      -> pairs, pair_off / multi_t / multi_to_*
+// with t' = t - t_min.  The orderings come from a stable LSD radix sort (up to
+// 9-bit digits) written here.  The GLOBAL order is a sort by t' after which
+// each run of equal t' is put in (src, dst) order in place (one thread, one
+// block, or, for a run of more than 4096 edges, the full three-key sort);
+// the OUT and IN orders are stable re-sorts of the GLOBAL order by one
+// endpoint (one two-array sort), and the multi-edge order is a stable re-sort
+// of the IN order by source.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
