@@ -476,12 +476,29 @@ __global__ void k_compact3(const uint32_t *__restrict__ a, const uint32_t *__res
 }
 
 
-__global__ void k_owner_bits(const uint32_t *__restrict__ off, uint32_t nown, uint32_t m, uint32_t *__restrict__ bits)
+// Owner-start bit sets of the out-, in- and multi-edge orders, one 32-bit
+// word of each per thread: position x starts a new owner when its source
+// (out-lists) or destination (in-lists) differs from position x-1's, or when
+// it heads a pair (multi-edge lists, from the pair-head flags).
+__global__ void k_owner_bits(const uint32_t *__restrict__ out_src, const uint32_t *__restrict__ in_dst,
+                             const uint32_t *__restrict__ pair_head, uint32_t m, uint32_t words,
+                             uint32_t *__restrict__ own_out, uint32_t *__restrict__ own_in,
+                             uint32_t *__restrict__ own_multi)
 {
-    uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nown) return;
-    uint32_t b = off[v];
-    if (b < m && off[v + 1] > b) atomicOr(bits + (b >> 5), 1u << (b & 31));
+    const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= words) return;
+    uint32_t bo = 0, bi = 0, bm = 0;
+    for (uint32_t b = 0; b < 32; ++b) {
+        const uint64_t x = (uint64_t)w * 32 + b;
+        if (x >= m) break;
+        const bool first = x == 0;
+        if (first || out_src[x] != out_src[x - 1]) bo |= 1u << b;
+        if (first || in_dst[x] != in_dst[x - 1]) bi |= 1u << b;
+        if (pair_head[x]) bm |= 1u << b;
+    }
+    own_out[w] = bo;
+    own_in[w] = bi;
+    own_multi[w] = bm;
 }
 
 __global__ void k_iota2(uint32_t *__restrict__ a, uint32_t *__restrict__ b, uint32_t m)
@@ -799,13 +816,9 @@ int build_csr(tm_ctx *ctx)
         launch(ctx, k_cross_rank, blocks_for(m, TB), TB, g.out_t, g.out_src, m, g.in_off, g.in_t, g.out_xrank);
         launch(ctx, k_cross_rank, blocks_for(m, TB), TB, g.in_t, g.in_dst, m, g.out_off, g.out_t, g.in_xrank);
         // owner starts of the three orders (segment heads of the weight pass's scans)
-        const size_t words = (size_t)m / 32 + 1;
-        cudaMemsetAsync(g.own_out, 0, words * 4, st);
-        cudaMemsetAsync(g.own_in, 0, words * 4, st);
-        cudaMemsetAsync(g.own_multi, 0, words * 4, st);
-        launch(ctx, k_owner_bits, blocks_for(n, TB), TB, g.out_off, n, m, g.own_out);
-        launch(ctx, k_owner_bits, blocks_for(n, TB), TB, g.in_off, n, m, g.own_in);
-        if (np) launch(ctx, k_owner_bits, blocks_for(np, TB), TB, g.pair_off, np, m, g.own_multi);
+        const uint32_t words = m / 32 + 1;
+        launch(ctx, k_owner_bits, blocks_for(words, TB), TB, (const uint32_t *)g.out_src, (const uint32_t *)g.in_dst,
+               (const uint32_t *)head, m, words, g.own_out, g.own_in, g.own_multi);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "pair tables");
         if (rc) return rc;
     } else {

@@ -212,22 +212,43 @@ struct RootScan2 {
 };
 
 // Window heads of layer p in GLOBAL order.
-__global__ void k_window_heads(const uint32_t *__restrict__ t, uint32_t m, int p, int64_t d, uint32_t *__restrict__ flag)
+// Window heads of both layers (layer p = blockIdx.y) into flag[p*m + i].
+__global__ void k_window_heads(const uint32_t *__restrict__ t, uint32_t m, int64_t d, uint32_t *__restrict__ flag)
 {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = blockIdx.y;
     if (i >= m) return;
-    int64_t w = layer_window(t[i], p, d);
-    flag[i] = (w >= 0 && (i == 0 || layer_window(t[i - 1], p, d) != w)) ? 1u : 0u;
+    const int64_t w = layer_window(t[i], p, d);
+    flag[(size_t)p * m + i] = (w >= 0 && (i == 0 || layer_window(t[i - 1], p, d) != w)) ? 1u : 0u;
 }
 
-__global__ void k_window_fill(const uint32_t *__restrict__ t, const uint32_t *__restrict__ flag,
-                              const uint32_t *__restrict__ pos, uint32_t m, int p, int64_t d,
-                              uint32_t *__restrict__ win_beg, uint32_t *__restrict__ win_id)
+// The exclusive scan ran over both layers' flags back to back: layer 0 has
+// pos[m] windows, layer 1 the rest of the total.
+__global__ void k_window_counts(const uint32_t *__restrict__ pos, uint32_t m, uint32_t *__restrict__ counts)
 {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m || !flag[i]) return;
-    win_beg[pos[i]] = i;
-    win_id[pos[i]] = (uint32_t)layer_window(t[i], p, d);
+    const uint32_t c0 = pos[m];
+    counts[1] -= c0;
+    counts[0] = c0;
+}
+
+struct WinOut {
+    uint32_t *beg[2], *id[2];
+    uint32_t nwin[2];
+};
+
+// Both layers (p = blockIdx.y): window starts and indices; layer 1's scanned
+// positions start at layer 0's count (base).  Also the end sentinels.
+__global__ void k_window_fill(const uint32_t *__restrict__ t, const uint32_t *__restrict__ flag,
+                              const uint32_t *__restrict__ pos, uint32_t m, int64_t d, uint32_t base1, WinOut W)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = blockIdx.y;
+    uint32_t *beg = p ? W.beg[1] : W.beg[0], *wid = p ? W.id[1] : W.id[0];
+    if (i == 0) beg[p ? W.nwin[1] : W.nwin[0]] = m;
+    if (i >= m || !flag[(size_t)p * m + i]) return;
+    const uint32_t k = pos[(size_t)p * m + i] - (p ? base1 : 0);
+    beg[k] = i;
+    wid[k] = (uint32_t)layer_window(t[i], p, d);
 }
 
 // Window totals W_i (last root-CDF entry of each window) and their 128-bit
@@ -284,6 +305,7 @@ __device__ __forceinline__ uint64_t ceil_shift(uint64_t c, uint32_t s) { return 
 struct GuideLayer {
     const uint64_t *cdf;
     const uint32_t *win_beg, *flag, *pos;
+    uint32_t pbase;             // first scanned position of this layer's windows
     uint32_t nwin;
     uint32_t *gshift, *goff, *guide;
 };
@@ -340,7 +362,7 @@ __global__ void k_guide_fill(GuideArgs A, const uint32_t *__restrict__ t, uint32
     const int p = blockIdx.y;
     if (x >= m || layer_window(t[x], p, d) < 0) return;
     const GuideLayer &L = p ? A.L[1] : A.L[0];
-    const uint32_t kk = L.pos[x] + L.flag[x] - 1;
+    const uint32_t kk = L.pos[x] + L.flag[x] - 1 - L.pbase;
     const uint32_t wbeg = L.win_beg[kk], wend = L.win_beg[kk + 1];
     const uint32_t sh = L.gshift[kk];
     uint32_t *G = L.guide + L.goff[kk];
@@ -402,22 +424,22 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     cudaMemsetAsync(ctx->status, 0, 4, st);
     // ---- windows of each layer (K2): count both layers, then one block for
     // everything the motif keeps (windows, root CDF, prefix arrays, totals)
-    uint32_t *flag[2], *pos[2], *dcount;
+    // both layers' flags and scanned positions back to back: [p*m, (p+1)*m)
+    uint32_t *flag_all, *pos_all, *flag[2], *pos[2], *dcount;
     uint32_t nwh[2] = {0, 0};
     {
         PhaseScope ph(ctx, TM_PH_WINDOWS);
         dcount = (uint32_t *)salloc(ctx, 8);
-        if (!dcount) return TM_E_NOMEM;
+        flag_all = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 8);
+        pos_all = (uint32_t *)salloc(ctx, ((size_t)m + 1) * 8);
+        if (!dcount || !flag_all || !pos_all) return TM_E_NOMEM;
+        for (int p = 0; p < 2; ++p) { flag[p] = flag_all + (size_t)p * m; pos[p] = pos_all + (size_t)p * m; }
         cudaMemsetAsync(dcount, 0, 8, st);
-        for (int p = 0; p < 2; ++p) {
-            flag[p] = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);
-            pos[p] = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);
-            if (!flag[p] || !pos[p]) return TM_E_NOMEM;
-            if (m) {
-                launch(ctx, k_window_heads, blocks_for(m, TB), TB, g.g_t, m, p, d, flag[p]);
-                rc = exclusive_scan_u32(ctx, flag[p], pos[p], m, dcount + p);
-                if (rc) return rc;
-            }
+        if (m) {
+            launch(ctx, k_window_heads, dim3(blocks_for(m, TB), 2), TB, g.g_t, m, d, flag_all);
+            rc = exclusive_scan_u32(ctx, flag_all, pos_all, 2 * (uint64_t)m, dcount + 1);
+            if (rc) return rc;
+            launch(ctx, k_window_counts, 1, 1, (const uint32_t *)pos_all, m, dcount);
         }
         copy_d2h(ctx, nwh, dcount, 8);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "window count");
@@ -452,11 +474,10 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     }
     {
         PhaseScope ph(ctx, TM_PH_WINDOWS);
-        for (int p = 0; p < 2; ++p) {
-            LayerData &L = mo->layer[p];
-            if (m) launch(ctx, k_window_fill, blocks_for(m, TB), TB, g.g_t, flag[p], pos[p], m, p, d, L.win_beg, L.win_id);
-            copy_h2d(ctx, L.win_beg + L.nwin, &g.m, 4);
-        }
+        WinOut wo{{mo->layer[0].win_beg, mo->layer[1].win_beg}, {mo->layer[0].win_id, mo->layer[1].win_id},
+                  {nwh[0], nwh[1]}};
+        launch(ctx, k_window_fill, dim3(blocks_for(m ? m : 1, TB), 2), TB, g.g_t, (const uint32_t *)flag_all,
+               (const uint32_t *)pos_all, m, d, nwh[0], wo);
     }
     // ---- DP over tree nodes in increasing height (K3) + prefixes (K4)
     const OwnerBits ob{g.own_out, g.own_in, g.own_multi};
@@ -507,7 +528,8 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
             if (rc) return rc;
             for (int p = 0; p < 2; ++p) {
                 LayerData &L = mo->layer[p];
-                ga.L[p] = GuideLayer{L.root_cdf, L.win_beg, flag[p], pos[p], L.nwin, L.win_gshift, L.win_goff, L.guide};
+                ga.L[p] = GuideLayer{L.root_cdf, L.win_beg, flag[p], pos[p], p ? nwh[0] : 0u, L.nwin, L.win_gshift,
+                                     L.win_goff, L.guide};
             }
             // guide tables of the root search, both layers
             if (m) {
