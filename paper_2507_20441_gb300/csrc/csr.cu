@@ -476,29 +476,29 @@ __global__ void k_compact3(const uint32_t *__restrict__ a, const uint32_t *__res
 }
 
 
-// Owner-start bit sets of the out-, in- and multi-edge orders, one 32-bit
-// word of each per thread: position x starts a new owner when its source
-// (out-lists) or destination (in-lists) differs from position x-1's, or when
-// it heads a pair (multi-edge lists, from the pair-head flags).
+// Owner-start bit sets of the out-, in- and multi-edge orders: position x
+// starts a new owner when its source (out-lists) or destination (in-lists)
+// differs from position x-1's, or when it heads a pair (multi-edge lists,
+// from the pair-head flags).  One thread per position; each warp's ballots
+// are one word of each set.
 __global__ void k_owner_bits(const uint32_t *__restrict__ out_src, const uint32_t *__restrict__ in_dst,
                              const uint32_t *__restrict__ pair_head, uint32_t m, uint32_t words,
                              uint32_t *__restrict__ own_out, uint32_t *__restrict__ own_in,
                              uint32_t *__restrict__ own_multi)
 {
-    const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= words) return;
-    uint32_t bo = 0, bi = 0, bm = 0;
-    for (uint32_t b = 0; b < 32; ++b) {
-        const uint64_t x = (uint64_t)w * 32 + b;
-        if (x >= m) break;
-        const bool first = x == 0;
-        if (first || out_src[x] != out_src[x - 1]) bo |= 1u << b;
-        if (first || in_dst[x] != in_dst[x - 1]) bi |= 1u << b;
-        if (pair_head[x]) bm |= 1u << b;
+    const uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= (uint64_t)words * 32) return;   // whole warps: words * 32 is a multiple of 32
+    const bool in = x < m, first = x == 0;
+    const bool bo = in && (first || out_src[x] != out_src[x - 1]);
+    const bool bi = in && (first || in_dst[x] != in_dst[x - 1]);
+    const bool bm = in && pair_head[x] != 0;
+    const uint32_t wo = __ballot_sync(0xffffffffu, bo), wi = __ballot_sync(0xffffffffu, bi),
+                   wm = __ballot_sync(0xffffffffu, bm);
+    if ((threadIdx.x & 31) == 0) {
+        own_out[x >> 5] = wo;
+        own_in[x >> 5] = wi;
+        own_multi[x >> 5] = wm;
     }
-    own_out[w] = bo;
-    own_in[w] = bi;
-    own_multi[w] = bm;
 }
 
 __global__ void k_iota2(uint32_t *__restrict__ a, uint32_t *__restrict__ b, uint32_t m)
@@ -817,7 +817,7 @@ int build_csr(tm_ctx *ctx)
         launch(ctx, k_cross_rank, blocks_for(m, TB), TB, g.in_t, g.in_dst, m, g.out_off, g.out_t, g.in_xrank);
         // owner starts of the three orders (segment heads of the weight pass's scans)
         const uint32_t words = m / 32 + 1;
-        launch(ctx, k_owner_bits, blocks_for(words, TB), TB, (const uint32_t *)g.out_src, (const uint32_t *)g.in_dst,
+        launch(ctx, k_owner_bits, blocks_for((uint64_t)words * 32, TB), TB, (const uint32_t *)g.out_src, (const uint32_t *)g.in_dst,
                (const uint32_t *)head, m, words, g.own_out, g.own_in, g.own_multi);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "pair tables");
         if (rc) return rc;
