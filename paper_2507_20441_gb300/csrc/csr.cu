@@ -517,6 +517,23 @@ __global__ void k_gather2(const uint32_t *__restrict__ idx, uint32_t m, const ui
     if (y && oy) oy[i] = y[g];
 }
 
+// Two independent gathers (set = blockIdx.y) in one launch.
+struct G2 {
+    const uint32_t *idx, *x, *y;
+    uint32_t *ox, *oy;
+};
+__global__ void k_gather2_pair(G2 a, G2 b, uint32_t m)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const bool s1 = blockIdx.y != 0;   // per-field selects keep the parameters out of local memory
+    const uint32_t *idx = s1 ? b.idx : a.idx, *x = s1 ? b.x : a.x, *y = s1 ? b.y : a.y;
+    uint32_t *ox = s1 ? b.ox : a.ox, *oy = s1 ? b.oy : a.oy;
+    const uint32_t g = idx[i];
+    ox[i] = x[g];
+    if (y && oy) oy[i] = y[g];
+}
+
 // off[v] = first position whose sorted key is >= v, for v in [0, n].
 __global__ void k_offsets(const uint32_t *__restrict__ keys, uint32_t m, uint32_t n, uint32_t *__restrict__ off)
 {
@@ -565,21 +582,32 @@ __global__ void k_rev_pairs(const uint32_t *__restrict__ pair_src, const uint32_
 }
 
 // where each list time falls in the same vertex's other list
-__global__ void k_cross_rank(const uint32_t *__restrict__ own_t, const uint32_t *__restrict__ owner, uint32_t m,
-                             const uint32_t *__restrict__ other_off, const uint32_t *__restrict__ other_t,
-                             uint32_t *__restrict__ xrank)
+// Cross ranks of both lists (blockIdx.y = 0: out-list entries into the
+// owner's in-list; 1: in-list entries into the owner's out-list).
+struct XR {
+    const uint32_t *own_t, *owner, *other_off, *other_t;
+    uint32_t *xrank;
+};
+__global__ void k_cross_rank(XR a, XR b, uint32_t m)
 {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
+    const bool s1 = blockIdx.y != 0;
+    const uint32_t *own_t = s1 ? b.own_t : a.own_t, *owner = s1 ? b.owner : a.owner;
+    const uint32_t *other_off = s1 ? b.other_off : a.other_off, *other_t = s1 ? b.other_t : a.other_t;
+    uint32_t *xrank = s1 ? b.xrank : a.xrank;
     const uint32_t z = owner[i];
     xrank[i] = lower_idx(other_t, other_off[z], other_off[z + 1], own_t[i]);
 }
 
-// inverse of a position -> edge-id permutation
-__global__ void k_inverse(const uint32_t *__restrict__ gid, uint32_t m, uint32_t *__restrict__ pos)
+// inverses of two position -> edge-id permutations (set = blockIdx.y)
+__global__ void k_inverse_pair(const uint32_t *__restrict__ gid0, const uint32_t *__restrict__ gid1, uint32_t m,
+                               uint32_t *__restrict__ pos0, uint32_t *__restrict__ pos1)
 {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) pos[gid[i]] = i;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    if (blockIdx.y) pos1[gid1[i]] = i;
+    else pos0[gid0[i]] = i;
 }
 
 inline unsigned blocks_for(uint64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
@@ -755,8 +783,8 @@ int build_csr(tm_ctx *ctx)
     sec.reset();
     sec.reset(new PhaseScope(ctx, TM_PH_CSR_IN));
     if (m) {
-        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.out_gid, m, g.g_t, g.g_dst, g.out_t, g.out_nbr);
-        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.in_gid, m, g.g_t, g.g_src, g.in_t, g.in_nbr);
+        launch(ctx, k_gather2_pair, dim3(blocks_for(m, TB), 2), TB, G2{g.out_gid, g.g_t, g.g_dst, g.out_t, g.out_nbr},
+               G2{g.in_gid, g.g_t, g.g_src, g.in_t, g.in_nbr}, m);
     }
     launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, g.out_src, m, n, g.out_off);
     launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, g.in_dst, m, n, g.in_off);
@@ -807,14 +835,14 @@ int build_csr(tm_ctx *ctx)
         launch(ctx, k_rev_pairs, blocks_for(np, TB), TB, pair_src, g.pair_dst, g.vpair_off, np, g.rev_pair);
         // list positions by edge id; then, per out-/in-list position, its pair
         // id and its position in the other list (one pass over each order)
-        launch(ctx, k_inverse, blocks_for(m, TB), TB, g.out_gid, m, g.out_pos);
-        launch(ctx, k_inverse, blocks_for(m, TB), TB, g.in_gid, m, g.in_pos);
-        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.out_gid, m, g.g_pair, g.in_pos, g.out_pair, g.out_to_in);
-        launch(ctx, k_gather2, blocks_for(m, TB), TB, g.in_gid, m, g.g_pair, g.out_pos, g.in_pair, g.in_to_out);
+        launch(ctx, k_inverse_pair, dim3(blocks_for(m, TB), 2), TB, (const uint32_t *)g.out_gid,
+               (const uint32_t *)g.in_gid, m, g.out_pos, g.in_pos);
+        launch(ctx, k_gather2_pair, dim3(blocks_for(m, TB), 2), TB, G2{g.out_gid, g.g_pair, g.in_pos, g.out_pair, g.out_to_in},
+               G2{g.in_gid, g.g_pair, g.out_pos, g.in_pair, g.in_to_out}, m);
         launch(ctx, k_gather2, blocks_for(m, TB), TB, multi_gid, m, g.out_pos, g.in_pos, g.multi_to_out, g.multi_to_in);
         // cross ranks between a vertex's out- and in-lists
-        launch(ctx, k_cross_rank, blocks_for(m, TB), TB, g.out_t, g.out_src, m, g.in_off, g.in_t, g.out_xrank);
-        launch(ctx, k_cross_rank, blocks_for(m, TB), TB, g.in_t, g.in_dst, m, g.out_off, g.out_t, g.in_xrank);
+        launch(ctx, k_cross_rank, dim3(blocks_for(m, TB), 2), TB, XR{g.out_t, g.out_src, g.in_off, g.in_t, g.out_xrank},
+               XR{g.in_t, g.in_dst, g.out_off, g.out_t, g.in_xrank}, m);
         // owner starts of the three orders (segment heads of the weight pass's scans)
         const uint32_t words = m / 32 + 1;
         launch(ctx, k_owner_bits, blocks_for((uint64_t)words * 32, TB), TB, (const uint32_t *)g.out_src, (const uint32_t *)g.in_dst,
