@@ -59,7 +59,10 @@ enum {
     TM_HOST = 0,        /* src/dst/t are host pointers                        */
     TM_DEVICE = 1,      /* src/dst/t are device pointers                      */
     TM_DEDUP = 2,       /* drop repeated (u,v,t) tuples instead of TM_E_DUP   */
-    TM_DROP_SELF = 4    /* drop self loops instead of TM_E_SELFLOOP           */
+    TM_DROP_SELF = 4,   /* drop self loops instead of TM_E_SELFLOOP           */
+    TM_PREPROCESS = 8   /* also run tm_preprocess in the same call; with      */
+                        /* TM_DEVICE the arrays are read in place (no staged  */
+                        /* copy), so they must stay valid until it returns    */
 };
 
 typedef struct tm_ctx tm_ctx;
@@ -113,9 +116,11 @@ const char *tm_last_error(tm_ctx *ctx);
 
 /* Load a temporal graph: m tuples (src[i], dst[i], t[i]) over n vertices
  * (Sec. 1.1).  flags: TM_HOST or TM_DEVICE for where the three arrays live,
- * plus TM_DEDUP / TM_DROP_SELF.  Ids must be < n.  Replaces any previous
- * graph (and invalidates motifs' weights).  Errors: TM_E_ARG, TM_E_DUP,
- * TM_E_SELFLOOP, TM_E_LIMIT, TM_E_NOMEM, TM_E_CUDA. */
+ * plus TM_DEDUP / TM_DROP_SELF, and TM_PREPROCESS to build the adjacency in
+ * the same call (then device arrays are read in place instead of staged, and
+ * the call returns once they are no longer read).  Ids must be < n.  Replaces
+ * any previous graph (and invalidates motifs' weights).  Errors: TM_E_ARG,
+ * TM_E_DUP, TM_E_SELFLOOP, TM_E_LIMIT, TM_E_NOMEM, TM_E_CUDA. */
 int tm_graph_load(tm_ctx *ctx, uint32_t n, uint64_t m, const uint32_t *src,
                   const uint32_t *dst, const int64_t *t, int flags);
 

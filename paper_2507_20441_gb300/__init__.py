@@ -25,7 +25,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "timest.h")
 TM_OK, TM_E_ARG, TM_E_DUP, TM_E_SELFLOOP, TM_E_MOTIF, TM_E_NOMEM, TM_E_OVERFLOW, TM_E_STATE, TM_E_TIMEOUT, \
     TM_E_CUDA, TM_E_LIMIT, TM_E_PENDING = range(12)
 TM_C2, TM_C3 = 1, 2
-TM_HOST, TM_DEVICE, TM_DEDUP, TM_DROP_SELF = 0, 1, 2, 4
+TM_HOST, TM_DEVICE, TM_DEDUP, TM_DROP_SELF, TM_PREPROCESS = 0, 1, 2, 4, 8
 _STATUS_NAMES = {0: "TM_OK", 1: "TM_E_ARG", 2: "TM_E_DUP", 3: "TM_E_SELFLOOP", 4: "TM_E_MOTIF", 5: "TM_E_NOMEM",
                  6: "TM_E_OVERFLOW", 7: "TM_E_STATE", 8: "TM_E_TIMEOUT", 9: "TM_E_CUDA", 10: "TM_E_LIMIT",
                  11: "TM_E_PENDING"}
@@ -556,9 +556,11 @@ class Context:
         self._motifs = []
 
     def load_graph(self, n, src, dst, t, flags=TM_HOST, preprocess=True):
-        tm_graph_load(self.h, n, src, dst, t, flags)
-        if preprocess:
-            self.preprocess()
+        if preprocess:   # one call: device inputs are read in place
+            tm_graph_load(self.h, n, src, dst, t, flags | TM_PREPROCESS)
+            self.m, self.t_min, self.T = tm_graph_info(self.h)
+        else:
+            tm_graph_load(self.h, n, src, dst, t, flags)
         return self
 
     def preprocess(self):

@@ -222,8 +222,10 @@ static void free_graph(tm_ctx *ctx)
 
 static void free_input(tm_ctx *ctx)
 {
-    // in_t heads the single staging block (t, then src, then dst)
-    if (ctx->in_t) dfree(ctx, ctx->in_t, ctx->m_in * 16);
+    // in_t heads the single staging block (t, then src, then dst); borrowed
+    // caller arrays are not ours to free
+    if (ctx->in_t && !ctx->in_borrowed) dfree(ctx, ctx->in_t, ctx->m_in * 16);
+    ctx->in_borrowed = false;
     ctx->in_src = ctx->in_dst = nullptr;
     ctx->in_t = nullptr;
 }
@@ -533,6 +535,20 @@ int tm_graph_load(tm_ctx *ctx, uint32_t n, uint64_t m, const uint32_t *src, cons
     ctx->n = n;
     ctx->m_in = m;
     ctx->load_flags = flags;
+    if (m && (flags & TM_DEVICE) && (flags & TM_PREPROCESS)) {
+        // build straight from the caller's device arrays, valid for this call
+        ctx->in_src = const_cast<uint32_t *>(src);
+        ctx->in_dst = const_cast<uint32_t *>(dst);
+        ctx->in_t = const_cast<int64_t *>(t);
+        ctx->in_borrowed = true;
+        ctx->loaded = true;
+        const int rc = tm_preprocess(ctx);
+        if (ctx->in_borrowed) {   // failed: the caller's arrays are not kept
+            free_input(ctx);
+            ctx->loaded = false;
+        }
+        return rc;
+    }
     if (m) {
         char *blk = (char *)dalloc(ctx, m * 16);
         if (!blk) return TM_E_NOMEM;
@@ -552,7 +568,7 @@ int tm_graph_load(tm_ctx *ctx, uint32_t n, uint64_t m, const uint32_t *src, cons
         if (rc) { free_input(ctx); return rc; }
     }
     ctx->loaded = true;
-    return TM_OK;
+    return (flags & TM_PREPROCESS) ? tm_preprocess(ctx) : TM_OK;
 }
 
 int tm_preprocess(tm_ctx *ctx)

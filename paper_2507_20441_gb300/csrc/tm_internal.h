@@ -144,6 +144,7 @@ struct tm_ctx {
     int load_flags = 0;
     uint32_t *in_src = nullptr, *in_dst = nullptr;  // staged input (device)
     int64_t *in_t = nullptr;
+    bool in_borrowed = false;                        // in_* point at the caller's arrays
     timest::DevGraph g;
     std::vector<std::pair<void *, size_t>> graph_bufs;
     uint32_t *status = nullptr;          // device status word
