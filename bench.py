@@ -188,7 +188,7 @@ def graph_stats(gr):
 
 
 def sampler_bytes_per_sample(ntree, nontree, stats, nwin):
-    """The per-sample traffic model of the survey (Sec. 8(d)), every probe of
+    """The per-sample effective-bytes model of the sampler, every probe of
     every search counted at 8 B: the window search over the window totals
     (16 B entries) and the root search over the root CDF, 16 B for the root
     edge record; per non-root tree edge a 16 B record and five searches of the
@@ -317,7 +317,7 @@ def run_ours(args, rank, world, local_rank):
         per_sample = sampler_bytes_per_sample(ntree, len(mo.edges) - ntree, gst, nwin)
         algo = k * per_sample
         kern_ms = samp_ms / max(samp_n, 1)
-        kname, model = "k_sample", f"survey 8(d) effective bytes: {per_sample} B/sample x k"
+        kname, model = "k_sample", f"effective bytes (every search probe at 8 B): {per_sample} B/sample x k"
     else:
         algo = dp_bytes / max(dp_n, 1)
         kern_ms = dp_ms / max(dp_n, 1)
