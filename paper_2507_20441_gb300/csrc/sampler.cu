@@ -397,6 +397,11 @@ constexpr int kSampleThreads = 256;
 #ifndef TM_SAMPLE_MINB
 #define TM_SAMPLE_MINB 6   // 40 registers: six blocks of 256 per SM hide more of the search latency
 #endif
+#ifndef TM_SAMPLE_GRID_PER_SM
+// tm_sample's grid cap in blocks per SM: one wave of resident blocks, each
+// thread striding over samples (measured faster than 2-8 partial waves)
+#define TM_SAMPLE_GRID_PER_SM TM_SAMPLE_MINB
+#endif
 #ifndef TM_RECS_SMEM
 #define TM_RECS_SMEM 0   // per-sample records in local memory: L1 stays large for the searches
 #endif
@@ -822,7 +827,7 @@ int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t f
     fill_job(mo, J, dplan);
     const int threads = kSampleThreads;
     uint64_t want = (k + threads - 1) / threads;
-    uint64_t cap = (uint64_t)ctx->num_sms * 16;
+    uint64_t cap = (uint64_t)ctx->num_sms * TM_SAMPLE_GRID_PER_SM;
     unsigned blocks = (unsigned)std::max<uint64_t>(1, std::min(want, cap));
     uint32_t *dg = nullptr; uint64_t *dc = nullptr; int32_t *dr = nullptr;
     size_t gbytes = 0;
