@@ -136,7 +136,8 @@ __device__ __forceinline__ void os_block_scan512(uint32_t *vals /* smem [512] in
 
 // Keys (and payloads) of one tile are ranked stably per warp chunk: a warp
 // whose 32 digits agree takes its ranks directly; otherwise the lanes with
-// the same digit are found with one ballot per digit bit.
+// the same digit are found with one ballot per digit bit.  A null p0in reads
+// payload 0 as the key's input index.
 template <int NP>
 __global__ void __launch_bounds__(OS_THREADS, NP >= 2 ? 3 : 4)
     k_rs_scatter(RsJobs J, uint32_t n, int shift, int bits, uint32_t ntiles, const uint32_t *__restrict__ offs_all)
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(OS_THREADS, NP >= 2 ? 3 : 4)
     for (int j = 0; j < OS_ITEMS; ++j) {   // keys and payloads in flight before any vote
         const uint32_t i = base + warp * OS_WCHUNK + j * 32 + lane;
         kv[j] = i < n ? __ldg(kin + i) : 0u;
-        if (NP >= 1) av[j % NA] = i < n ? __ldg(p0in + i) : 0u;
+        if (NP >= 1) av[j % NA] = i < n ? (p0in ? __ldg(p0in + i) : i) : 0u;
         if (NP >= 2) bv[j % NB] = i < n ? __ldg(p1in + i) : 0u;
     }
     __syncthreads();
@@ -257,6 +258,35 @@ struct RsHost {
     uint32_t *key, *p0, *p1;
 };
 
+static int rs_prepare(tm_ctx *ctx, int np)
+{
+    // per device and cheap: set on every call
+    cudaError_t e = np == 0 ? cudaFuncSetAttribute(k_rs_scatter<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem(0))
+                  : np == 1 ? cudaFuncSetAttribute(k_rs_scatter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem(1))
+                            : cudaFuncSetAttribute(k_rs_scatter<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem(2));
+    return check_cuda(ctx, e, "radix pass shared memory");
+}
+
+// One LSD pass over digit bits [sh, sh + pb): counts, their scan, the scatter.
+static int rs_pass(tm_ctx *ctx, const RsJobs &in, int nsets, int np, uint32_t n, uint32_t ntiles, int sh, int pb,
+                   uint32_t *counts)
+{
+    const unsigned nblk = ntiles * (unsigned)nsets;
+    const uint64_t ncount = ((uint64_t)ntiles << pb) * (uint64_t)nsets;
+    cudaStream_t st = ctx->stream;
+    launch(ctx, k_rs_count, nblk, OS_THREADS, in, n, sh, pb, ntiles, counts);
+    int rc = exclusive_scan_u32(ctx, counts, counts, ncount, nullptr);
+    if (rc) return rc;
+    ++ctx->kernel_launches;
+    if (np == 0)
+        k_rs_scatter<0><<<nblk, OS_THREADS, os_smem(0), st>>>(in, n, sh, pb, ntiles, counts);
+    else if (np == 1)
+        k_rs_scatter<1><<<nblk, OS_THREADS, os_smem(1), st>>>(in, n, sh, pb, ntiles, counts);
+    else
+        k_rs_scatter<2><<<nblk, OS_THREADS, os_smem(2), st>>>(in, n, sh, pb, ntiles, counts);
+    return check_cuda(ctx, cudaGetLastError(), "radix pass");
+}
+
 int radix_sort_sets(tm_ctx *ctx, const RsHost *sets, int nsets, uint32_t n, int bits)
 {
     ScratchScope scope(ctx);
@@ -276,31 +306,12 @@ int radix_sort_sets(tm_ctx *ctx, const RsHost *sets, int nsets, uint32_t n, int 
         if (!k2 || (np >= 1 && !a2) || (np >= 2 && !b2)) return TM_E_NOMEM;
         in.s[j] = RsSet{sets[j].key, sets[j].p0, sets[j].p1, k2, a2, b2};
     }
-    {
-        // per device and cheap: set on every call
-        cudaError_t e = np == 0 ? cudaFuncSetAttribute(k_rs_scatter<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem(0))
-                      : np == 1 ? cudaFuncSetAttribute(k_rs_scatter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem(1))
-                                : cudaFuncSetAttribute(k_rs_scatter<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem(2));
-        int rc = check_cuda(ctx, e, "radix pass shared memory");
-        if (rc) return rc;
-    }
+    int rc = rs_prepare(ctx, np);
+    if (rc) return rc;
     cudaStream_t st = ctx->stream;
-    const unsigned nblk = ntiles * (unsigned)nsets;
-    int rc = TM_OK;
     for (int pass = 0, sh = 0; pass < npass && rc == TM_OK; ++pass) {
         const int left = npass - pass, pb = (bits - sh + left - 1) / left;
-        const uint64_t ncount = ((uint64_t)ntiles << pb) * (uint64_t)nsets;
-        launch(ctx, k_rs_count, nblk, OS_THREADS, in, n, sh, pb, ntiles, counts);
-        rc = exclusive_scan_u32(ctx, counts, counts, ncount, nullptr);
-        if (rc) break;
-        ++ctx->kernel_launches;
-        if (np == 0)
-            k_rs_scatter<0><<<nblk, OS_THREADS, os_smem(0), st>>>(in, n, sh, pb, ntiles, counts);
-        else if (np == 1)
-            k_rs_scatter<1><<<nblk, OS_THREADS, os_smem(1), st>>>(in, n, sh, pb, ntiles, counts);
-        else
-            k_rs_scatter<2><<<nblk, OS_THREADS, os_smem(2), st>>>(in, n, sh, pb, ntiles, counts);
-        rc = check_cuda(ctx, cudaGetLastError(), "radix pass");
+        rc = rs_pass(ctx, in, nsets, np, n, ntiles, sh, pb, counts);
         // the outputs of this pass are the inputs of the next
         for (int j = 0; j < nsets; ++j) {
             RsSet &x = in.s[j];
@@ -316,6 +327,76 @@ int radix_sort_sets(tm_ctx *ctx, const RsHost *sets, int nsets, uint32_t n, int 
         cudaMemcpyAsync(sets[j].key, x.kin, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
         if (np >= 1) cudaMemcpyAsync(sets[j].p0, x.p0in, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
         if (np >= 2) cudaMemcpyAsync(sets[j].p1, x.p1in, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+    }
+    return rc;
+}
+
+__global__ void k_iota(uint32_t *__restrict__ a, uint32_t m)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) a[i] = i;
+}
+
+// The same sort from read-only inputs into separate outputs (no copies): the
+// passes alternate between the outputs and scratch so that the last one
+// writes the outputs.  A set whose p0_in is null and p0 is not gets payload 0
+// = the input index (the sorting permutation).  Outputs must not alias inputs.
+struct RsTo {
+    const uint32_t *key_in, *p0_in, *p1_in;
+    uint32_t *key, *p0, *p1;
+};
+
+int radix_sort_sets_to(tm_ctx *ctx, const RsTo *sets, int nsets, uint32_t n, int bits)
+{
+    ScratchScope scope(ctx);
+    if (nsets <= 0 || n == 0) return TM_OK;
+    if (nsets > 2) return set_err(ctx, TM_E_LIMIT, "at most two arrays per radix sort");
+    const int np = sets[0].p1 ? 2 : (sets[0].p0 ? 1 : 0);
+    cudaStream_t st = ctx->stream;
+    if (n <= 1 || bits <= 0) {
+        for (int j = 0; j < nsets; ++j) {
+            const RsTo &x = sets[j];
+            cudaMemcpyAsync(x.key, x.key_in, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+            if (np >= 1) {
+                if (x.p0_in) cudaMemcpyAsync(x.p0, x.p0_in, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+                else launch(ctx, k_iota, (n + 255) / 256, 256, x.p0, n);
+            }
+            if (np >= 2) cudaMemcpyAsync(x.p1, x.p1_in, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+        }
+        return TM_OK;
+    }
+    const int npass = (bits + OS_MAXBITS - 1) / OS_MAXBITS;
+    if (npass > OS_MAXPASS) return set_err(ctx, TM_E_LIMIT, "radix key wider than 36 bits");
+    const uint32_t ntiles = (n + OS_TILE - 1) / OS_TILE;
+    uint32_t *counts = (uint32_t *)salloc(ctx, (size_t)nsets * ntiles * OS_MAXRADIX * 4);
+    if (!counts) return TM_E_NOMEM;
+    RsSet scr[2] = {}, dst[2] = {};
+    for (int j = 0; j < nsets; ++j) {
+        dst[j] = RsSet{nullptr, nullptr, nullptr, sets[j].key, sets[j].p0, sets[j].p1};
+        if (npass >= 2) {
+            uint32_t *k2 = (uint32_t *)salloc(ctx, (size_t)n * 4);
+            uint32_t *a2 = np >= 1 ? (uint32_t *)salloc(ctx, (size_t)n * 4) : nullptr;
+            uint32_t *b2 = np >= 2 ? (uint32_t *)salloc(ctx, (size_t)n * 4) : nullptr;
+            if (!k2 || (np >= 1 && !a2) || (np >= 2 && !b2)) return TM_E_NOMEM;
+            scr[j] = RsSet{nullptr, nullptr, nullptr, k2, a2, b2};
+        }
+    }
+    int rc = rs_prepare(ctx, np);
+    if (rc) return rc;
+    RsJobs in{};
+    for (int j = 0; j < nsets; ++j) in.s[j] = RsSet{sets[j].key_in, sets[j].p0_in, sets[j].p1_in, nullptr, nullptr, nullptr};
+    for (int pass = 0, sh = 0; pass < npass && rc == TM_OK; ++pass) {
+        const int left = npass - pass, pb = (bits - sh + left - 1) / left;
+        // pass i writes the outputs when npass - 1 - i is even, else scratch
+        const bool to_dst = ((npass - 1 - pass) & 1) == 0;
+        for (int j = 0; j < nsets; ++j) {
+            const RsSet &o = to_dst ? dst[j] : scr[j];
+            in.s[j].kout = o.kout; in.s[j].p0out = o.p0out; in.s[j].p1out = o.p1out;
+        }
+        rc = rs_pass(ctx, in, nsets, np, n, ntiles, sh, pb, counts);
+        for (int j = 0; j < nsets; ++j)
+            in.s[j] = RsSet{in.s[j].kout, in.s[j].p0out, in.s[j].p1out, nullptr, nullptr, nullptr};
+        sh += pb;
     }
     return rc;
 }
@@ -499,12 +580,6 @@ __global__ void k_owner_bits(const uint32_t *__restrict__ out_src, const uint32_
         own_in[x >> 5] = wi;
         own_multi[x >> 5] = wm;
     }
-}
-
-__global__ void k_iota2(uint32_t *__restrict__ a, uint32_t *__restrict__ b, uint32_t m)
-{
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) { a[i] = i; b[i] = i; }
 }
 
 __global__ void k_gather2(const uint32_t *__restrict__ idx, uint32_t m, const uint32_t *__restrict__ x,
@@ -693,15 +768,28 @@ int build_csr(tm_ctx *ctx)
         launch(ctx, k_compact_input, blocks_for(m0, TB), TB, ctx->in_src, ctx->in_dst, ctx->in_t, m0, nullptr, nullptr,
                                                            tmin, T0, S0, D0);
     }
-    // ---- GLOBAL order (t', src, dst): LSD by t', then each run of equal t'
-    // ordered by (src, dst) in place; a run longer than kRunMax sends the
-    // whole array through the full LSD sort by dst, src and t' instead
+    // every m- and n-sized array of the graph in one block, sized before the
+    // duplicates are known (they are rare; their slots stay unused)
+    {
+        const size_t mf = (size_t)m, a_m = align256((mf ? mf : 1) * 4), a_n = align256(((size_t)n + 1) * 4);
+        const size_t a_b = align256((mf / 32 + 1) * 4);
+        if (!gblock_open(ctx, gb, 23 * a_m + 3 * a_n + 3 * a_b)) return TM_E_NOMEM;
+    }
+    g.g_t = gtake(gb, m); g.g_src = gtake(gb, m); g.g_dst = gtake(gb, m);
+    if (!g.g_t || !g.g_src || !g.g_dst) return TM_E_NOMEM;
+    // ---- GLOBAL order (t', src, dst): LSD by t' straight into the graph's
+    // arrays, then each run of equal t' ordered by (src, dst) in place; a run
+    // longer than kBlockRunMax sends the whole array through the full LSD sort
+    // by dst, src and t' instead
     sec.reset();
     sec.reset(new PhaseScope(ctx, TM_PH_CSR_GLOBAL));
     int vbits = bits_for(n ? n - 1 : 0);
     int tbits = bits_for((uint64_t)(tmax - tmin));
-    rc = radix_sort(ctx, T0, S0, D0, m, tbits);
-    if (rc) return rc;
+    {
+        RsTo ts{T0, S0, D0, g.g_t, g.g_src, g.g_dst};
+        rc = radix_sort_sets_to(ctx, &ts, 1, m, tbits);
+        if (rc) return rc;
+    }
     // ---- duplicates (and the run check, read with the same copy)
     {
         uint32_t *keep = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);
@@ -711,23 +799,23 @@ int build_csr(tm_ctx *ctx)
         if (!keep || !nd || !long_runs) return TM_E_NOMEM;
         cudaMemsetAsync(nd, 0, 24, st);
         if (m) {
-            launch(ctx, k_order_runs, blocks_for(m, TB), TB, (const uint32_t *)T0, S0, D0, m, (uint32_t *)(nd + 1),
-                   long_runs, (uint32_t *)(nd + 2));
-            launch(ctx, k_order_long_runs, (unsigned)ctx->num_sms * 2, 256, S0, D0, (const uint2 *)long_runs,
+            launch(ctx, k_order_runs, blocks_for(m, TB), TB, (const uint32_t *)g.g_t, g.g_src, g.g_dst, m,
+                   (uint32_t *)(nd + 1), long_runs, (uint32_t *)(nd + 2));
+            launch(ctx, k_order_long_runs, (unsigned)ctx->num_sms * 2, 256, g.g_src, g.g_dst, (const uint2 *)long_runs,
                    (const uint32_t *)(nd + 2));
-            launch(ctx, k_flag_unique, blocks_for(m, TB), TB, T0, S0, D0, m, keep, nd);
+            launch(ctx, k_flag_unique, blocks_for(m, TB), TB, g.g_t, g.g_src, g.g_dst, m, keep, nd);
         }
         unsigned long long hnd[2] = {0, 0};
         copy_d2h(ctx, hnd, nd, 16);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "duplicate scan");
         if (rc) return rc;
         if (hnd[1]) {
-            rc = radix_sort(ctx, D0, S0, T0, m, vbits);
-            if (!rc) rc = radix_sort(ctx, S0, D0, T0, m, vbits);
-            if (!rc) rc = radix_sort(ctx, T0, S0, D0, m, tbits);
+            rc = radix_sort(ctx, g.g_dst, g.g_src, g.g_t, m, vbits);
+            if (!rc) rc = radix_sort(ctx, g.g_src, g.g_dst, g.g_t, m, vbits);
+            if (!rc) rc = radix_sort(ctx, g.g_t, g.g_src, g.g_dst, m, tbits);
             if (rc) return rc;
             cudaMemsetAsync(nd, 0, 8, st);
-            launch(ctx, k_flag_unique, blocks_for(m, TB), TB, T0, S0, D0, m, keep, nd);
+            launch(ctx, k_flag_unique, blocks_for(m, TB), TB, g.g_t, g.g_src, g.g_dst, m, keep, nd);
             copy_d2h(ctx, hnd, nd, 8);
             rc = check_cuda(ctx, cudaStreamSynchronize(st), "duplicate scan");
             if (rc) return rc;
@@ -736,24 +824,17 @@ int build_csr(tm_ctx *ctx)
         if (ndup && !(ctx->load_flags & TM_DEDUP)) {
             return set_err(ctx, TM_E_DUP, "input repeats a (u,v,t) tuple (pass TM_DEDUP to drop repeats)");
         }
-        {
-            // every m- and n-sized array of the graph in one block
-            const size_t mf = (size_t)(m - ndup), a_m = align256((mf ? mf : 1) * 4), a_n = align256(((size_t)n + 1) * 4);
-            const size_t a_b = align256((mf / 32 + 1) * 4);
-            if (!gblock_open(ctx, gb, 23 * a_m + 3 * a_n + 3 * a_b)) return TM_E_NOMEM;
-        }
-        g.g_t = gtake(gb, m - ndup); g.g_src = gtake(gb, m - ndup); g.g_dst = gtake(gb, m - ndup);
-        if (!g.g_t || !g.g_src || !g.g_dst) return TM_E_NOMEM;
         if (ndup) {
+            // compact into the work arrays, then back
             uint32_t *pos = (uint32_t *)salloc(ctx, (size_t)m * 4);
             if (!pos) return TM_E_NOMEM;
             rc = exclusive_scan_u32(ctx, keep, pos, m, nullptr);
             if (rc) return rc;
-            launch(ctx, k_compact3, blocks_for(m, TB), TB, T0, S0, D0, m, keep, pos, g.g_t, g.g_src, g.g_dst);
-        } else if (m) {
-            cudaMemcpyAsync(g.g_t, T0, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
-            cudaMemcpyAsync(g.g_src, S0, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
-            cudaMemcpyAsync(g.g_dst, D0, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
+            launch(ctx, k_compact3, blocks_for(m, TB), TB, g.g_t, g.g_src, g.g_dst, m, keep, pos, T0, S0, D0);
+            const size_t bytes = (size_t)(m - ndup) * 4;
+            cudaMemcpyAsync(g.g_t, T0, bytes, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(g.g_src, S0, bytes, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(g.g_dst, D0, bytes, cudaMemcpyDeviceToDevice, st);
         }
         m = (uint32_t)(m - ndup);
     }
@@ -773,11 +854,10 @@ int build_csr(tm_ctx *ctx)
         !g.out_src || !g.out_pair || !g.in_dst || !g.in_pair || !g.out_xrank || !g.in_xrank || !g.out_pos || !g.in_pos)
         return TM_E_NOMEM;
     if (m) {
-        cudaMemcpyAsync(g.out_src, g.g_src, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync(g.in_dst, g.g_dst, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
-        launch(ctx, k_iota2, blocks_for(m, TB), TB, g.out_gid, g.in_gid, m);
-        RsHost sets[2] = {{g.out_src, g.out_gid, nullptr}, {g.in_dst, g.in_gid, nullptr}};
-        rc = radix_sort_sets(ctx, sets, 2, m, vbits);
+        // payload = the input index: gid
+        RsTo sets[2] = {{g.g_src, nullptr, nullptr, g.out_src, g.out_gid, nullptr},
+                        {g.g_dst, nullptr, nullptr, g.in_dst, g.in_gid, nullptr}};
+        rc = radix_sort_sets_to(ctx, sets, 2, m, vbits);
         if (rc) return rc;
     }
     sec.reset();
@@ -803,10 +883,11 @@ int build_csr(tm_ctx *ctx)
         return TM_E_NOMEM;
     uint32_t np = 0;
     if (m) {
-        cudaMemcpyAsync(key, g.in_nbr, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync(multi_gid, g.in_gid, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
-        rc = radix_sort(ctx, key, multi_gid, nullptr, m, vbits);
-        if (rc) return rc;
+        {
+            RsTo ms{g.in_nbr, g.in_gid, nullptr, key, multi_gid, nullptr};
+            rc = radix_sort_sets_to(ctx, &ms, 1, m, vbits);
+            if (rc) return rc;
+        }
         launch(ctx, k_gather2, blocks_for(m, TB), TB, multi_gid, m, g.g_t, g.g_dst, g.multi_t, tmp);
         // key = pair src, tmp = pair dst per multi position
         uint32_t *head = T0;

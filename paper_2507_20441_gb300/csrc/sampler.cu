@@ -70,14 +70,16 @@ __device__ __forceinline__ void find_pair(const DevGraph &g, uint32_t u, uint32_
 // first and the last pi edge are non-tree their times are coupled by the
 // delta span: sum over the first edge's candidates x of the last edge's
 // candidates up to x + delta (two pointers over the two sorted lists).
-__device__ uint64_t derive_simple(const DevGraph &g, const DevPlan &P, Recs &R, uint32_t tmin, uint32_t tmax,
+// Rec supplies the vertex map phi(v) and the tree-node times t(q).
+template <class Rec>
+__device__ uint64_t derive_simple(const DevGraph &g, const DevPlan &P, Rec &R, uint32_t tmin, uint32_t tmax,
                                   bool &ovf)
 {
     const uint64_t d = (uint64_t)P.delta;
     const uint64_t glo = (uint64_t)tmax >= d ? (uint64_t)tmax - d : 0;
     const uint64_t ghi = (uint64_t)tmin + d;
     uint64_t prod = 1;
-    uint32_t ra[2] = {0, 0}, rb[2] = {0, 0};   // ranges of the coupled first / last edges
+    uint32_t ra0 = 0, rb0 = 0, ra1 = 0, rb1 = 0;   // ranges of the coupled first / last edges
     for (int i = 0; i < P.nnt; ++i) {
         const int e = P.pos_edge[P.nt_pos[i]];
         uint32_t b, en;
@@ -94,21 +96,23 @@ __device__ uint64_t derive_simple(const DevGraph &g, const DevPlan &P, Recs &R, 
         const uint32_t x0 = lower_idx(g.multi_t, b, en, lo);
         const uint32_t x1 = lower_idx(g.multi_t, x0, en, hi + 1);
         if (x1 == x0) return 0;
-        if (P.coupled && (i == 0 || i == P.nnt - 1)) {
-            const int w = (i == 0) ? 0 : 1;
-            ra[w] = x0;
-            rb[w] = x1;
+        if (P.coupled && i == 0) {
+            ra0 = x0;
+            rb0 = x1;
+        } else if (P.coupled && i == P.nnt - 1) {
+            ra1 = x0;
+            rb1 = x1;
         } else {
             prod = mul_chk(prod, (uint64_t)(x1 - x0), ovf);
         }
     }
     if (!P.coupled) return prod;
     uint64_t sum = 0;
-    uint32_t j = ra[1];
-    for (uint32_t x = ra[0]; x < rb[0]; ++x) {
+    uint32_t j = ra1;
+    for (uint32_t x = ra0; x < rb0; ++x) {
         const uint64_t cap = (uint64_t)__ldg(g.multi_t + x) + d;
-        while (j < rb[1] && (uint64_t)__ldg(g.multi_t + j) <= cap) ++j;
-        sum = add_chk(sum, (uint64_t)(j - ra[1]), ovf);
+        while (j < rb1 && (uint64_t)__ldg(g.multi_t + j) <= cap) ++j;
+        sum = add_chk(sum, (uint64_t)(j - ra1), ovf);
     }
     return mul_chk(prod, sum, ovf);
 }
@@ -238,27 +242,32 @@ __device__ __forceinline__ uint64_t derive_cnt(const DevGraph &g, const DevPlan 
 
 // DeriveCnt (Alg. 5) of a valid tree and N_phi (windows holding every tree
 // edge): the sample's contribution cnt * 2 / N_phi.
+// cnt * 2 / N_phi: N_phi is 2 when the tree's span [tmin, tmax] lies in two
+// windows (both layers), else 1; N_phi counts windows of the window unit.
+__device__ __forceinline__ uint64_t over_nphi(const DevPlan &P, uint64_t cnt, uint32_t tmin, uint32_t tmax,
+                                              bool &ovf)
+{
+    const uint64_t wd = (uint64_t)P.wdelta;
+    const bool two = (uint64_t)tmin >= wd && (uint64_t)tmin / wd == (uint64_t)tmax / wd;
+    return two ? cnt : mul_chk(cnt, 2, ovf);
+}
+
 __device__ uint64_t complete_count(const DevGraph &g, const DevPlan &P, Recs R, uint32_t tmin, uint32_t tmax,
                                    uint32_t *status)
 {
-    const uint64_t wd = (uint64_t)P.wdelta;   // N_phi counts windows
     bool ovf = false;
-    uint64_t cnt = derive_cnt(g, P, R, tmin, tmax, ovf);
-    const bool two = (uint64_t)tmin >= wd && (uint64_t)tmin / wd == (uint64_t)tmax / wd;
-    if (!two) cnt = mul_chk(cnt, 2, ovf);
+    const uint64_t cnt = over_nphi(P, derive_cnt(g, P, R, tmin, tmax, ovf), tmin, tmax, ovf);
     if (ovf) latch(status, ST_OVERFLOW);
     return cnt;
 }
 
-// The tree of sample j (Alg. 3): a window with probability W_i / W, the root
-// edge through the window's guide table and CDF, then every tree edge from
-// its candidate list.  Fills R; 0, or -1 on an internal inconsistency
-// (latched as ST_BADSTATE).
-__device__ int sample_tree(const DevGraph &g, const DevPlan &P, const SampleJob &J, uint64_t seed, uint64_t j,
-                           uint32_t *status, uint32_t *tg_out, Recs R)
+// The first draws of sample j (Alg. 3): a window with probability W_i / W,
+// then its root edge through the window's guide table and CDF.  Sets the
+// layer p, the window's time range [wlo, whi] and the root edge id; 0, or -1
+// on an internal inconsistency (latched as ST_BADSTATE).
+__device__ __forceinline__ int sample_root(const DevPlan &P, const SampleJob &J, SampleRng &rng, uint32_t *status,
+                                           int &p, uint64_t &wlo, uint64_t &whi, uint32_t &root)
 {
-    SampleRng rng;
-    rng.init(seed, j);
     const u128 W = (u128)J.W_lo | ((u128)J.W_hi << 64);
     u128 r = rng.below128(W, status);
     // window: last k with wcum[k] <= r
@@ -271,107 +280,140 @@ __device__ int sample_tree(const DevGraph &g, const DevPlan &P, const SampleJob 
     const uint32_t k = lo;
     const u128 ck = (u128)__ldg(J.wcum + 2 * (size_t)k) | ((u128)__ldg(J.wcum + 2 * (size_t)k + 1) << 64);
     const uint64_t rr = (uint64_t)(r - ck);
-    const int p = k < J.nw0 ? 0 : 1;
+    p = k < J.nw0 ? 0 : 1;
     const uint32_t kk = p ? k - J.nw0 : k;
     const uint32_t *wb = p ? J.win_beg1 : J.win_beg0;
     const uint64_t *cdf = p ? J.root_cdf1 : J.root_cdf0;
     const uint32_t wbeg = __ldg(wb + kk), wend = __ldg(wb + kk + 1);
     const uint64_t wi = __ldg((p ? J.win_id1 : J.win_id0) + kk);
-    const uint64_t d = (uint64_t)P.delta, wd = (uint64_t)P.wdelta;
-    const uint64_t wlo = wi * wd, whi = (wi + 2) * wd - 1;
+    const uint64_t wd = (uint64_t)P.wdelta;
+    wlo = wi * wd;
+    whi = (wi + 2) * wd - 1;
     // the root edge lies between two guide entries: the first edges whose CDF
     // exceeds the bucket bounds below and above rr
     const uint32_t gsh = __ldg((p ? J.win_gshift1 : J.win_gshift0) + kk);
     const uint32_t *G = (p ? J.guide1 : J.guide0) + __ldg((p ? J.win_goff1 : J.win_goff0) + kk) + (rr >> gsh);
     const uint32_t glo = __ldg(G), ghi = __ldg(G + 1);
     if (glo < wbeg || ghi >= wend || glo > ghi) { latch(status, ST_BADSTATE); return -1; }
-    const uint32_t root = upper_idx64(cdf, glo, ghi + 1, rr);
+    root = upper_idx64(cdf, glo, ghi + 1, rr);
     if (root > ghi) { latch(status, ST_BADSTATE); return -1; }
+    return 0;
+}
+
+// One tree edge of Alg. 3: the edge of tree node q, drawn by weight from its
+// candidate list at the meeting vertex given its parent's edge (source ps,
+// destination pd, time pt, pair id ppair, edge id pgid), in layer p whose
+// window spans [wlo, whi].  Sets the child's time, endpoints and, for a node
+// with children or when `ids` is set, its edge id and pair id; 0, or -1 on an
+// internal inconsistency (latched as ST_BADSTATE).
+__device__ __forceinline__ int sample_child(const DevGraph &g, const DevPlan &P, const SampleJob &J, int q, int p,
+                                            uint64_t wlo, uint64_t whi, SampleRng &rng, uint32_t *status,
+                                            uint32_t ps, uint32_t pd, uint32_t pt, uint32_t ppair, uint32_t pgid,
+                                            bool ids, uint32_t &ct, uint32_t &cs, uint32_t &cd, uint32_t &cgid,
+                                            uint32_t &cpair)
+{
+    const uint64_t d = (uint64_t)P.delta;
+    const bool zs = P.tzside[q] != 0, out = P.tout[q] != 0, leaf = P.tleaf[q] != 0;
+    const uint32_t zg = zs ? pd : ps;
+    const uint32_t og = zs ? ps : pd;
+    uint64_t tlo, thi;
+    if (P.tlater[q]) { tlo = (uint64_t)pt + 1; thi = (uint64_t)pt + d; }
+    else {
+        if (pt == 0) { latch(status, ST_BADSTATE); return -1; }
+        tlo = (uint64_t)pt >= d ? (uint64_t)pt - d : 0;
+        thi = (uint64_t)pt - 1;
+    }
+    tlo = tlo < wlo ? wlo : tlo;
+    thi = thi > whi ? whi : thi;
+    const uint32_t *nbr = out ? g.out_nbr : g.in_nbr;
+    const uint32_t *gids = out ? g.out_gid : g.in_gid;
+    // the parent edge's position in the meeting vertex's out-list (z is its
+    // source) or in-list (z is its destination)
+    const uint32_t ppos = __ldg((zs ? g.in_pos : g.out_pos) + pgid);
+    uint32_t a, b, beg;
+    const uint32_t *tarr;
+    child_range(g, zs ? 1 : 0, out, zg, ppos, pt, P.tlater[q] != 0, tlo, thi, a, b, beg, tarr);
+    const uint32_t pe = !P.c2 ? kNone : (out == !zs) ? ppair : __ldg(g.rev_pair + ppair);
+    uint32_t ea = 0, eb = 0, pb = 0;
+    if (pe != kNone) {
+        pb = __ldg(g.pair_off + pe);
+        const uint32_t pend = __ldg(g.pair_off + pe + 1);
+        ea = lower_idx(g.multi_t, pb, pend, tlo);
+        eb = gallop_idx(g.multi_t, ea, pend, thi + 1);
+    }
+    const int slot = P.tslot[q];
+    const uint64_t *Pd = nullptr, *Pm = nullptr;
+    uint64_t base = 0, base_m = 0, total;
+    if (leaf) {
+        total = (uint64_t)(b - a) - (uint64_t)(eb - ea);
+    } else {
+        Pd = p ? J.pref_dir1[slot] : J.pref_dir0[slot];
+        Pm = p ? J.pref_multi1[slot] : J.pref_multi0[slot];
+        base = (a > beg && (uint64_t)__ldg(tarr + a - 1) >= wlo) ? __ldg(Pd + a - 1) : 0;
+        base_m = (ea > pb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo) ? __ldg(Pm + ea - 1) : 0;
+        const uint64_t sr = b > a ? __ldg(Pd + b - 1) - base : 0;
+        const uint64_t se = eb > ea ? __ldg(Pm + eb - 1) - base_m : 0;
+        total = sr - se;
+    }
+    if (total == 0 || b <= a) { latch(status, ST_BADSTATE); return -1; }
+    const uint64_t rc = rng.below(total, status);
+    // smallest x in [a, b) with F(x) > rc, F(x) = weight of the
+    // non-excluded entries in [a, x]
+    uint32_t xl = a, xh = b - 1;
+    if (eb == ea) {
+        // nothing excluded: F(x) = x - a + 1 for a leaf (the pick is
+        // direct), the prefix difference otherwise
+        if (leaf) xl = a + (uint32_t)rc;
+        else
+            while (xl < xh) {
+                const uint32_t x = xl + ((xh - xl) >> 1);
+                if (__ldg(Pd + x) - base > rc) xh = x; else xl = x + 1;
+            }
+    } else {
+        while (xl < xh) {
+            const uint32_t x = xl + ((xh - xl) >> 1);
+            const uint32_t tx = __ldg(tarr + x);
+            // excluded entries at or before x: those earlier in time, and
+            // the one at time tx if it sorts at or before x (the list
+            // orders equal times by the other endpoint)
+            uint32_t ce = lower_idx(g.multi_t, ea, eb, tx) - ea;
+            if (ea + ce < eb && __ldg(g.multi_t + ea + ce) == tx && og <= __ldg(nbr + x)) ++ce;
+            uint64_t F;
+            if (leaf) F = (uint64_t)(x - a + 1) - ce;
+            else F = (__ldg(Pd + x) - base) - (ce ? __ldg(Pm + ea + ce - 1) - base_m : 0);
+            if (F > rc) xh = x; else xl = x + 1;
+        }
+    }
+    const uint32_t other = __ldg(nbr + xl);
+    ct = __ldg(tarr + xl);
+    cs = out ? zg : other;
+    cd = out ? other : zg;
+    // edge and pair ids are read again only for a node with children (or a trace)
+    if (!leaf || ids) {
+        cgid = __ldg(gids + xl);
+        if (!leaf) cpair = __ldg(g.g_pair + cgid);
+    }
+    return 0;
+}
+
+// The tree of sample j (Alg. 3): the root, then every tree edge from its
+// candidate list.  Fills R; 0, or -1 on an internal inconsistency (latched
+// as ST_BADSTATE).
+__device__ int sample_tree(const DevGraph &g, const DevPlan &P, const SampleJob &J, uint64_t seed, uint64_t j,
+                           uint32_t *status, uint32_t *tg_out, Recs R)
+{
+    SampleRng rng;
+    rng.init(seed, j);
+    int p;
+    uint64_t wlo, whi;
+    uint32_t root;
+    if (sample_root(P, J, rng, status, p, wlo, whi, root)) return -1;
     load_edge(g, root, R, 0);
     for (int q = 1; q < P.ntree; ++q) {
         const int pq = P.tparent[q];
-        const bool zs = P.tzside[q] != 0, out = P.tout[q] != 0, leaf = P.tleaf[q] != 0;
-        const uint32_t ps = R.src(pq), pd = R.dst(pq), pt = R.t(pq), ppair = R.pair(pq);
-        const uint32_t zg = zs ? pd : ps;
-        const uint32_t og = zs ? ps : pd;
-        uint64_t tlo, thi;
-        if (P.tlater[q]) { tlo = (uint64_t)pt + 1; thi = (uint64_t)pt + d; }
-        else {
-            if (pt == 0) { latch(status, ST_BADSTATE); return -1; }
-            tlo = (uint64_t)pt >= d ? (uint64_t)pt - d : 0;
-            thi = (uint64_t)pt - 1;
-        }
-        tlo = tlo < wlo ? wlo : tlo;
-        thi = thi > whi ? whi : thi;
-        const uint32_t *nbr = out ? g.out_nbr : g.in_nbr;
-        const uint32_t *gids = out ? g.out_gid : g.in_gid;
-        // the parent edge's position in the meeting vertex's out-list (z is its
-        // source) or in-list (z is its destination)
-        const uint32_t ppos = __ldg((zs ? g.in_pos : g.out_pos) + R.gid(pq));
-        uint32_t a, b, beg;
-        const uint32_t *tarr;
-        child_range(g, zs ? 1 : 0, out, zg, ppos, pt, P.tlater[q] != 0, tlo, thi, a, b, beg, tarr);
-        const uint32_t pe = !P.c2 ? kNone : (out == !zs) ? ppair : __ldg(g.rev_pair + ppair);
-        uint32_t ea = 0, eb = 0, pb = 0;
-        if (pe != kNone) {
-            pb = __ldg(g.pair_off + pe);
-            const uint32_t pend = __ldg(g.pair_off + pe + 1);
-            ea = lower_idx(g.multi_t, pb, pend, tlo);
-            eb = gallop_idx(g.multi_t, ea, pend, thi + 1);
-        }
-        const int slot = P.tslot[q];
-        const uint64_t *Pd = nullptr, *Pm = nullptr;
-        uint64_t base = 0, base_m = 0, total;
-        if (leaf) {
-            total = (uint64_t)(b - a) - (uint64_t)(eb - ea);
-        } else {
-            Pd = p ? J.pref_dir1[slot] : J.pref_dir0[slot];
-            Pm = p ? J.pref_multi1[slot] : J.pref_multi0[slot];
-            base = (a > beg && (uint64_t)__ldg(tarr + a - 1) >= wlo) ? __ldg(Pd + a - 1) : 0;
-            base_m = (ea > pb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo) ? __ldg(Pm + ea - 1) : 0;
-            const uint64_t sr = b > a ? __ldg(Pd + b - 1) - base : 0;
-            const uint64_t se = eb > ea ? __ldg(Pm + eb - 1) - base_m : 0;
-            total = sr - se;
-        }
-        if (total == 0 || b <= a) { latch(status, ST_BADSTATE); return -1; }
-        const uint64_t rc = rng.below(total, status);
-        // smallest x in [a, b) with F(x) > rc, F(x) = weight of the
-        // non-excluded entries in [a, x]
-        uint32_t xl = a, xh = b - 1;
-        if (eb == ea) {
-            // nothing excluded: F(x) = x - a + 1 for a leaf (the pick is
-            // direct), the prefix difference otherwise
-            if (leaf) xl = a + (uint32_t)rc;
-            else
-                while (xl < xh) {
-                    const uint32_t x = xl + ((xh - xl) >> 1);
-                    if (__ldg(Pd + x) - base > rc) xh = x; else xl = x + 1;
-                }
-        } else {
-            while (xl < xh) {
-                const uint32_t x = xl + ((xh - xl) >> 1);
-                const uint32_t tx = __ldg(tarr + x);
-                // excluded entries at or before x: those earlier in time, and
-                // the one at time tx if it sorts at or before x (the list
-                // orders equal times by the other endpoint)
-                uint32_t ce = lower_idx(g.multi_t, ea, eb, tx) - ea;
-                if (ea + ce < eb && __ldg(g.multi_t + ea + ce) == tx && og <= __ldg(nbr + x)) ++ce;
-                uint64_t F;
-                if (leaf) F = (uint64_t)(x - a + 1) - ce;
-                else F = (__ldg(Pd + x) - base) - (ce ? __ldg(Pm + ea + ce - 1) - base_m : 0);
-                if (F > rc) xh = x; else xl = x + 1;
-            }
-        }
-        const uint32_t other = __ldg(nbr + xl);
-        R.t(q) = __ldg(tarr + xl);
-        R.src(q) = out ? zg : other;
-        R.dst(q) = out ? other : zg;
-        // edge and pair ids are read again only for a node with children (or a trace)
-        if (!leaf || tg_out) {
-            const uint32_t cg = __ldg(gids + xl);
-            R.gid(q) = cg;
-            if (!leaf) R.pair(q) = __ldg(g.g_pair + cg);
-        }
+        if (sample_child(g, P, J, q, p, wlo, whi, rng, status, R.src(pq), R.dst(pq), R.t(pq), R.pair(pq), R.gid(pq),
+                         tg_out != nullptr, R.t(q), R.src(q), R.dst(q), R.gid(q), R.pair(q)))
+            return -1;
     }
     if (tg_out)
         for (int q = 0; q < P.ntree; ++q) tg_out[q] = R.gid(q);
@@ -391,6 +433,133 @@ __device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &
     if (why) return why;
     contrib = complete_count(g, P, R, tmin, tmax, status);
     return 0;
+}
+
+// ---- records in registers ------------------------------------------------
+// A tree of NT nodes (NT = nv - 1, known at compile time) keeps a sample's
+// edges and vertex map in registers: every loop over tree nodes and motif
+// vertices is unrolled, and a runtime index reads through a chain of selects.
+// Same draws, same arithmetic and same results as sample_one.
+
+template <int N>
+__device__ __forceinline__ uint32_t rsel(const uint32_t (&a)[N], int i)
+{
+    uint32_t v = a[0];
+#pragma unroll
+    for (int s = 1; s < N; ++s) v = (i == s) ? a[s] : v;
+    return v;
+}
+
+template <int NT>
+struct RegView {
+    const uint32_t (&tt)[NT];
+    const uint32_t (&ph)[NT + 1];
+    __device__ __forceinline__ uint32_t t(int q) const { return rsel(tt, q); }
+    __device__ __forceinline__ uint32_t phi(int v) const { return rsel(ph, v); }
+};
+
+template <int NT>
+__device__ __forceinline__ int sample_one_reg(const DevGraph &g, const DevPlan &P, const SampleJob &J, uint64_t seed,
+                                              uint64_t j, uint32_t *status, uint64_t &contrib)
+{
+    contrib = 0;
+    SampleRng rng;
+    rng.init(seed, j);
+    int p;
+    uint64_t wlo, whi;
+    uint32_t root;
+    if (sample_root(P, J, rng, status, p, wlo, whi, root)) return -1;
+    // Alg. 3: the root edge, then each node from its parent (parents come first)
+    uint32_t src[NT], dst[NT], t[NT], pair[NT], gid[NT];
+    gid[0] = root;
+    src[0] = __ldg(g.g_src + root);
+    dst[0] = __ldg(g.g_dst + root);
+    t[0] = __ldg(g.g_t + root);
+    pair[0] = __ldg(g.g_pair + root);
+#pragma unroll
+    for (int q = 1; q < NT; ++q) {
+        const int pq = P.tparent[q];
+        uint32_t ps = src[0], pd = dst[0], pt = t[0], pp = pair[0], pg = gid[0];
+#pragma unroll
+        for (int h = 1; h < q; ++h)
+            if (pq == h) { ps = src[h]; pd = dst[h]; pt = t[h]; pp = pair[h]; pg = gid[h]; }
+        gid[q] = 0;
+        pair[q] = 0;
+        if (sample_child(g, P, J, q, p, wlo, whi, rng, status, ps, pd, pt, pp, pg, false, t[q], src[q], dst[q], gid[q],
+                         pair[q]))
+            return -1;
+    }
+    // Alg. 4: the vertex map (1-1), the delta span, the pi order of tree edges
+    uint32_t phi[NT + 1];
+#pragma unroll
+    for (int x = 0; x <= NT; ++x) phi[x] = 0;
+    uint32_t tmin = 0xFFFFFFFFu, tmax = 0;
+#pragma unroll
+    for (int q = 0; q < NT; ++q) {
+        const int e = P.tedge[q];
+        const int va = P.ea[e], vb = P.eb[e];
+#pragma unroll
+        for (int x = 0; x <= NT; ++x) {
+            if (x == va) phi[x] = src[q];
+            if (x == vb) phi[x] = dst[q];
+        }
+        tmin = min(tmin, t[q]);
+        tmax = max(tmax, t[q]);
+    }
+#pragma unroll
+    for (int x = 0; x <= NT; ++x)
+#pragma unroll
+        for (int y = x + 1; y <= NT; ++y)
+            if (phi[x] == phi[y]) return 1;
+    if ((uint64_t)tmax - (uint64_t)tmin > (uint64_t)P.delta) return 2;
+    int64_t prev = -1;
+    for (int pos = 0; pos < P.ne; ++pos) {
+        const int q = P.tnode_of_edge[P.pos_edge[pos]];
+        if (q < 0) continue;
+        const int64_t tq = rsel(t, q);
+        if (tq <= prev) return 3;
+        prev = tq;
+    }
+    // Alg. 5 (plans whose non-tree runs all have length 1) and N_phi
+    bool ovf = false;
+    uint64_t cnt = 1;
+    if (P.nnt > 0) {
+        RegView<NT> v{t, phi};
+        cnt = derive_simple(g, P, v, tmin, tmax, ovf);
+    }
+    cnt = over_nphi(P, cnt, tmin, tmax, ovf);
+    if (ovf) latch(status, ST_OVERFLOW);
+    contrib = cnt;
+    return 0;
+}
+
+// Warp sums of a thread's tallies, then one set of atomics per warp.
+__device__ __forceinline__ void add_tallies(Acc *acc, u128 hits, unsigned long long nv, unsigned long long nr1,
+                                            unsigned long long nr2, unsigned long long nr3)
+{
+    uint64_t hl = (uint64_t)hits, hh = (uint64_t)(hits >> 64);
+    for (int o = 16; o > 0; o >>= 1) {
+        uint64_t ol = __shfl_down_sync(0xffffffffu, hl, o);
+        uint64_t oh = __shfl_down_sync(0xffffffffu, hh, o);
+        uint64_t s = hl + ol;
+        hh += oh + (s < hl ? 1 : 0);
+        hl = s;
+        nv += __shfl_down_sync(0xffffffffu, nv, o);
+        nr1 += __shfl_down_sync(0xffffffffu, nr1, o);
+        nr2 += __shfl_down_sync(0xffffffffu, nr2, o);
+        nr3 += __shfl_down_sync(0xffffffffu, nr3, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (hl) {
+            unsigned long long old = atomicAdd(&acc->hits_lo, (unsigned long long)hl);
+            if (old + hl < old) hh += 1;
+        }
+        if (hh) atomicAdd(&acc->hits_hi, (unsigned long long)hh);
+        if (nv) atomicAdd(&acc->valid, nv);
+        if (nr1) atomicAdd(&acc->rv, nr1);
+        if (nr2) atomicAdd(&acc->rd, nr2);
+        if (nr3) atomicAdd(&acc->ro, nr3);
+    }
 }
 
 constexpr int kSampleThreads = 256;
@@ -440,30 +609,34 @@ __global__ void __launch_bounds__(kSampleThreads, TM_SAMPLE_MINB) k_sample(DevGr
         else if (why == 3) ++nr3;
         if (TRACE) { tr_contrib[i] = c; tr_reason[i] = why; }
     }
-    // warp reduction then one atomic set per warp
-    uint64_t hl = (uint64_t)hits, hh = (uint64_t)(hits >> 64);
-    for (int o = 16; o > 0; o >>= 1) {
-        uint64_t ol = __shfl_down_sync(0xffffffffu, hl, o);
-        uint64_t oh = __shfl_down_sync(0xffffffffu, hh, o);
-        uint64_t s = hl + ol;
-        hh += oh + (s < hl ? 1 : 0);
-        hl = s;
-        nv += __shfl_down_sync(0xffffffffu, nv, o);
-        nr1 += __shfl_down_sync(0xffffffffu, nr1, o);
-        nr2 += __shfl_down_sync(0xffffffffu, nr2, o);
-        nr3 += __shfl_down_sync(0xffffffffu, nr3, o);
+    add_tallies(acc, hits, nv, nr1, nr2, nr3);
+}
+
+// k_sample without a trace for a tree of NT nodes, records in registers.
+template <int NT>
+__global__ void __launch_bounds__(kSampleThreads, TM_SAMPLE_MINB) k_sample_reg(DevGraph g, const DevPlan *__restrict__ plan,
+                                                              SampleJob J, uint64_t seed, uint64_t first, uint64_t k,
+                                                              Acc *acc, uint32_t *status)
+{
+    __shared__ DevPlan sp;
+    {
+        const int *src = reinterpret_cast<const int *>(plan);
+        int *dst = reinterpret_cast<int *>(&sp);
+        for (int i = threadIdx.x; i < (int)(sizeof(DevPlan) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
     }
-    if ((threadIdx.x & 31) == 0) {
-        if (hl) {
-            unsigned long long old = atomicAdd(&acc->hits_lo, (unsigned long long)hl);
-            if (old + hl < old) hh += 1;
-        }
-        if (hh) atomicAdd(&acc->hits_hi, (unsigned long long)hh);
-        if (nv) atomicAdd(&acc->valid, nv);
-        if (nr1) atomicAdd(&acc->rv, nr1);
-        if (nr2) atomicAdd(&acc->rd, nr2);
-        if (nr3) atomicAdd(&acc->ro, nr3);
+    __syncthreads();
+    u128 hits = 0;
+    unsigned long long nv = 0, nr1 = 0, nr2 = 0, nr3 = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        uint64_t c = 0;
+        int why = sample_one_reg<NT>(g, sp, J, seed, first + i, status, c);
+        if (why == 0) { ++nv; hits += c; }
+        else if (why == 1) ++nr1;
+        else if (why == 2) ++nr2;
+        else if (why == 3) ++nr3;
     }
+    add_tallies(acc, hits, nv, nr1, nr2, nr3);
 }
 
 // ---- motif listing (Alg. 5 emitting the instances it counts) -------------
@@ -804,6 +977,22 @@ static void finish_result(tm_motif *mo, uint64_t k, const Acc &a, tm_result *out
     out->estimate = k ? W * h / (2.0 * (double)k) : 0.0;
 }
 
+// The register-record sampler for this plan's tree size; false when the plan
+// is not a spanning tree of nv - 1 nodes or needs the general DeriveCnt (the
+// caller launches k_sample).
+static bool launch_sample_reg(tm_ctx *ctx, const DevPlan &P, unsigned blocks, int threads, const DevPlan *dplan,
+                              const SampleJob &J, uint64_t seed, uint64_t first, uint64_t k, Acc *dacc)
+{
+    if (P.nv != P.ntree + 1 || (P.nnt > 0 && !P.derive_simple)) return false;
+    switch (P.ntree) {
+#define TM_REG_CASE(N) \
+    case N: launch(ctx, k_sample_reg<N>, blocks, threads, ctx->g, dplan, J, seed, first, k, dacc, ctx->status); return true;
+        TM_REG_CASE(1) TM_REG_CASE(2) TM_REG_CASE(3) TM_REG_CASE(4) TM_REG_CASE(5) TM_REG_CASE(6) TM_REG_CASE(7)
+#undef TM_REG_CASE
+    default: return false;
+    }
+}
+
 int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first, tm_result *out,
                 uint32_t *trace_gids, uint64_t *trace_contrib, int32_t *trace_reason)
 {
@@ -842,7 +1031,7 @@ int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t f
             dr = (int32_t *)(t + (size_t)k * 8);
             dg = (uint32_t *)(t + (size_t)k * 12);
             launch(ctx, k_sample<true>, blocks, threads, ctx->g, dplan, J, seed, first, k, dacc, ctx->status, dg, dc, dr);
-        } else {
+        } else if (!launch_sample_reg(ctx, mo->plan, blocks, threads, dplan, J, seed, first, k, dacc)) {
             launch(ctx, k_sample<false>, blocks, threads, ctx->g, dplan, J, seed, first, k, dacc, ctx->status, nullptr,
                                                         nullptr, nullptr);
         }
