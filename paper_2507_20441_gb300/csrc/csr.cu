@@ -38,8 +38,11 @@ namespace {
 //      warps), reorders them by digit in shared memory and writes each
 //      digit's run out contiguously.
 // No block waits on another.
+#ifndef TM_RS_ITEMS
+#define TM_RS_ITEMS 16   // keys per thread (8 and 12 measured slower on 2M and 10M keys)
+#endif
 constexpr int OS_THREADS = 256;
-constexpr int OS_ITEMS = 16;
+constexpr int OS_ITEMS = TM_RS_ITEMS;
 constexpr int OS_TILE = OS_THREADS * OS_ITEMS;     // 4096 keys per tile
 constexpr int OS_WARPS = OS_THREADS / 32;
 constexpr int OS_WCHUNK = OS_ITEMS * 32;           // keys per warp chunk
@@ -426,13 +429,27 @@ __global__ void k_input_stats(const uint32_t *__restrict__ src, const uint32_t *
         lo = x < lo ? x : lo;
         hi = x > hi ? x : hi;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        long long a = __shfl_down_sync(0xffffffffu, lo, o), b = __shfl_down_sync(0xffffffffu, hi, o);
-        lo = a < lo ? a : lo; hi = b > hi ? b : hi;
-        ns += __shfl_down_sync(0xffffffffu, ns, o);
-        nb += __shfl_down_sync(0xffffffffu, nb, o);
+    // warp, then block reduction: one set of atomics per block
+    __shared__ long long s_lo[32], s_hi[32];
+    __shared__ unsigned long long s_ns[32], s_nb[32];
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int o = 16; o > 0; o >>= 1) {
+            long long a = __shfl_down_sync(0xffffffffu, lo, o), b = __shfl_down_sync(0xffffffffu, hi, o);
+            lo = a < lo ? a : lo; hi = b > hi ? b : hi;
+            ns += __shfl_down_sync(0xffffffffu, ns, o);
+            nb += __shfl_down_sync(0xffffffffu, nb, o);
+        }
+        if (pass == 1) break;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+        if (lane == 0) { s_lo[warp] = lo; s_hi[warp] = hi; s_ns[warp] = ns; s_nb[warp] = nb; }
+        __syncthreads();
+        if (warp != 0) return;
+        lo = lane < nw ? s_lo[lane] : LLONG_MAX;
+        hi = lane < nw ? s_hi[lane] : LLONG_MIN;
+        ns = lane < nw ? s_ns[lane] : 0;
+        nb = lane < nw ? s_nb[lane] : 0;
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (threadIdx.x == 0) {
         if (lo != LLONG_MAX) atomicMin(&st->tmin, lo);
         if (hi != LLONG_MIN) atomicMax(&st->tmax, hi);
         if (ns) atomicAdd(&st->nself, ns);
@@ -609,10 +626,14 @@ __global__ void k_gather2_pair(G2 a, G2 b, uint32_t m)
     if (y && oy) oy[i] = y[g];
 }
 
-// off[v] = first position whose sorted key is >= v, for v in [0, n].
-__global__ void k_offsets(const uint32_t *__restrict__ keys, uint32_t m, uint32_t n, uint32_t *__restrict__ off)
+// off[v] = first position whose sorted key is >= v, for v in [0, n].  With
+// m_dev set, the key count is min(m, *m_dev) (a count known only on the
+// device; m bounds the grid).
+__global__ void k_offsets(const uint32_t *__restrict__ keys, uint32_t m, uint32_t n, uint32_t *__restrict__ off,
+                          const uint32_t *__restrict__ m_dev)
 {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m_dev) m = min(m, *m_dev);
     if (i > m) return;
     uint32_t lo = (i == 0) ? 0u : keys[i - 1] + 1u;
     uint32_t hi = (i == m) ? n : keys[i];
@@ -643,13 +664,16 @@ __global__ void k_pair_fill(const uint32_t *__restrict__ msrc, const uint32_t *_
         pair_dst[pid] = mdst[i];
     }
     g_pair[mgid[i]] = pid;
+    if (i == m - 1) pair_off[pid + 1] = m;   // the end of the last pair's list
 }
 
+// reverse pair of every pair (kNone if absent); np_dev = number of pairs
 __global__ void k_rev_pairs(const uint32_t *__restrict__ pair_src, const uint32_t *__restrict__ pair_dst,
-                            const uint32_t *__restrict__ vpair_off, uint32_t np, uint32_t *__restrict__ rev)
+                            const uint32_t *__restrict__ vpair_off, const uint32_t *__restrict__ np_dev,
+                            uint32_t *__restrict__ rev)
 {
     uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
+    if (p >= *np_dev) return;
     uint32_t u = pair_src[p], v = pair_dst[p];
     uint32_t lo = vpair_off[v], hi = vpair_off[v + 1];
     uint32_t r = lower_idx(pair_dst, lo, hi, u);
@@ -773,7 +797,8 @@ int build_csr(tm_ctx *ctx)
     {
         const size_t mf = (size_t)m, a_m = align256((mf ? mf : 1) * 4), a_n = align256(((size_t)n + 1) * 4);
         const size_t a_b = align256((mf / 32 + 1) * 4);
-        if (!gblock_open(ctx, gb, 23 * a_m + 3 * a_n + 3 * a_b)) return TM_E_NOMEM;
+        // (the pair tables are sized by m too: the pair count is read only at the end)
+        if (!gblock_open(ctx, gb, 26 * a_m + 256 + 3 * a_n + 3 * a_b)) return TM_E_NOMEM;
     }
     g.g_t = gtake(gb, m); g.g_src = gtake(gb, m); g.g_dst = gtake(gb, m);
     if (!g.g_t || !g.g_src || !g.g_dst) return TM_E_NOMEM;
@@ -866,8 +891,8 @@ int build_csr(tm_ctx *ctx)
         launch(ctx, k_gather2_pair, dim3(blocks_for(m, TB), 2), TB, G2{g.out_gid, g.g_t, g.g_dst, g.out_t, g.out_nbr},
                G2{g.in_gid, g.g_t, g.g_src, g.in_t, g.in_nbr}, m);
     }
-    launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, g.out_src, m, n, g.out_off);
-    launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, g.in_dst, m, n, g.in_off);
+    launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, g.out_src, m, n, g.out_off, nullptr);
+    launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, g.in_dst, m, n, g.in_off, nullptr);
     uint32_t *key = S0, *tmp = D0;
     // ---- multi-edge order: stable re-sort of the IN order by source
     sec.reset();
@@ -897,23 +922,19 @@ int build_csr(tm_ctx *ctx)
         launch(ctx, k_pair_heads, blocks_for(m, TB), TB, key, tmp, m, head);
         rc = exclusive_scan_u32(ctx, head, pid, m, dnp);
         if (rc) return rc;
-        // total = pid[m-1] + head[m-1]; the scan wrote the exclusive total
-        copy_d2h(ctx, &np, dnp, 4);
-        rc = check_cuda(ctx, cudaStreamSynchronize(st), "pair count");
-        if (rc) return rc;
-        g.npairs = np;
-        GraphBlock pbk;
-        if (!gblock_open(ctx, pbk, 3 * align256(((size_t)np + 1) * 4))) return TM_E_NOMEM;
-        g.pair_off = gtake(pbk, (size_t)np + 1);
-        g.pair_dst = gtake(pbk, np);
-        g.rev_pair = gtake(pbk, np);
-        uint32_t *pair_src = (uint32_t *)salloc(ctx, (size_t)(np ? np : 1) * 4);
+        // dnp = the number of pairs (the scan's total), used on the device;
+        // the pair tables are m-sized slots of the graph block
+        g.pair_off = gtake(gb, (size_t)m + 1);
+        g.pair_dst = gtake(gb, m);
+        g.rev_pair = gtake(gb, m);
+        uint32_t *pair_src = (uint32_t *)salloc(ctx, (size_t)m * 4);
         if (!g.pair_off || !g.pair_dst || !g.rev_pair || !pair_src) return TM_E_NOMEM;
         launch(ctx, k_pair_fill, blocks_for(m, TB), TB, key, tmp, multi_gid, head, pid, m, g.pair_off, pair_src,
                                                       g.pair_dst, g.g_pair);
-        copy_h2d(ctx, g.pair_off + np, &m, 4);
-        launch(ctx, k_offsets, blocks_for((uint64_t)np + 1, TB), TB, pair_src, np, n, g.vpair_off);
-        launch(ctx, k_rev_pairs, blocks_for(np, TB), TB, pair_src, g.pair_dst, g.vpair_off, np, g.rev_pair);
+        launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, pair_src, m, n, g.vpair_off, (const uint32_t *)dnp);
+        launch(ctx, k_rev_pairs, blocks_for(m, TB), TB, pair_src, g.pair_dst, g.vpair_off, (const uint32_t *)dnp,
+               g.rev_pair);
+        copy_d2h(ctx, ctx->status_host + 1, dnp, 4);   // pinned: read after the closing synchronize
         // list positions by edge id; then, per out-/in-list position, its pair
         // id and its position in the other list (one pass over each order)
         launch(ctx, k_inverse_pair, dim3(blocks_for(m, TB), 2), TB, (const uint32_t *)g.out_gid,
@@ -928,8 +949,6 @@ int build_csr(tm_ctx *ctx)
         const uint32_t words = m / 32 + 1;
         launch(ctx, k_owner_bits, blocks_for((uint64_t)words * 32, TB), TB, (const uint32_t *)g.out_src, (const uint32_t *)g.in_dst,
                (const uint32_t *)head, m, words, g.own_out, g.own_in, g.own_multi);
-        rc = check_cuda(ctx, cudaStreamSynchronize(st), "pair tables");
-        if (rc) return rc;
     } else {
         GraphBlock pbk;
         if (!gblock_open(ctx, pbk, 3 * 256)) return TM_E_NOMEM;
@@ -937,11 +956,13 @@ int build_csr(tm_ctx *ctx)
         g.pair_dst = gtake(pbk, 1);
         g.rev_pair = gtake(pbk, 1);
         cudaMemsetAsync(g.pair_off, 0, 4, st);
-        launch(ctx, k_offsets, 1, TB, key, 0, n, g.vpair_off);
+        launch(ctx, k_offsets, 1, TB, key, 0, n, g.vpair_off, nullptr);
     }
     uint32_t bits = 0;
-    int rc2 = read_status(ctx, &bits);
+    int rc2 = read_status(ctx, &bits);   // the build's one closing synchronize
     if (rc2) return rc2;
+    if (m) np = ctx->status_host[1];
+    g.npairs = np;
     if (bits) return set_err(ctx, TM_E_CUDA, "CSR build: device status " + std::to_string(bits));
     return TM_OK;
 }

@@ -148,7 +148,7 @@ struct tm_ctx {
     timest::DevGraph g;
     std::vector<std::pair<void *, size_t>> graph_bufs;
     uint32_t *status = nullptr;          // device status word
-    uint32_t *status_host = nullptr;     // pinned mirror
+    uint32_t *status_host = nullptr;     // pinned: [0] status mirror, [1] the CSR build's pair count
     int num_sms = 0;
     // phase timing (cfg.profile)
     struct PendingPhase { int phase; cudaEvent_t a, b; uint64_t launches; };
