@@ -51,6 +51,10 @@ def run_case(tg, ctx, G, nv, edges, rank, delta, tree, root, k=4000, seed=7, tra
         assert np.array_equal(tg_, to_)
         assert np.array_equal(why_g, why_o)
         assert np.array_equal(cg, co)
+        # the untraced sampler (records in registers) on the same samples
+        rs = mo.sample(k, seed)
+        assert (rs.hits2, rs.valid, rs.rej_vertex, rs.rej_delta, rs.rej_order) == \
+               (ro.hits2, ro.valid, ro.rej_vertex, ro.rej_delta, ro.rej_order)
     else:
         rg = mo.sample(k, seed)
         ro = G.sample(k, seed)
