@@ -1,7 +1,7 @@
 """bench.py's host-side contract (no GPU): the reference arm (the oracle on
 the host cores) prints one JSON line with the keys the benchmark contract
-names, and it samples the same spanning tree and root the library picks by
-default, so both arms run the same plan."""
+names, and it samples the spanning tree the library ranks first (the
+default tree), so both arms run the same plan."""
 import json
 import os
 import subprocess
