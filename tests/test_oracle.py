@@ -384,3 +384,34 @@ def test_two_path_partial_matches_without_windows(oracle_mod):
     G.set_constraints(True, False)
     assert G.weights() == w_c12
     assert w_c1 > w_c12 > 0
+
+
+def _random_motif(rng):
+    """A random connected ordered motif: 2-5 vertices, nv-1 to nv+2 edges
+    (parallel and antiparallel edges allowed, no self loops), random pi."""
+    while True:
+        nv = int(rng.integers(2, 6))
+        ne = int(rng.integers(nv - 1, nv + 3))
+        edges = []
+        for _ in range(ne):
+            a = int(rng.integers(0, nv)); b = int(rng.integers(0, nv - 1)); b += b >= a
+            edges.append((a, b))
+        if spanning_trees(nv, edges):
+            return nv, edges, [int(x) for x in rng.permutation(ne)]
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_brute_equals_tree_sum_random_motifs(oracle_mod, seed):
+    """O1 == O4 (Def. 1.2 against the sum over partial matches of cnt / N_phi,
+    doubled) for random ordered motifs, every spanning tree (up to four) and
+    every root, on random dense multigraphs."""
+    rng = np.random.default_rng(1000 + seed)
+    nv, edges, rank = _random_motif(rng)
+    n, s, d, t = small_random_graph(500 + seed, n=nv + 1, m=50 if nv <= 3 else 70, t_hi=30)
+    G = oracle_mod.Graph(n, s, d, t)
+    for delta in (4, 16):
+        C = G.brute_count(nv, edges, rank, delta)
+        for tree in spanning_trees(nv, edges)[:4]:
+            for root in tree:
+                G.set_motif(nv, edges, rank, delta, tree, root)
+                assert G.exact_by_trees() == 2 * C, (nv, edges, rank, delta, tree, root)
