@@ -6,14 +6,21 @@ device-resident edge arrays, build the temporal CSR, compute the weights of
 the motif's spanning tree (windows, DP, prefix sums, root CDF) and draw,
 validate and count k samples.  `value` is samples per second of whole steps
 (k / step time), timed with CUDA events on the library's stream; L2 is
-flushed (a 512 MB write) before every timed step, outside its events.
+flushed (a 512 MB write) before every timed step, outside its events.  The
+default workload is the largest single-GPU one: a Chung-Lu graph of 5e7
+edges, the 5-cycle with a chord, delta = 3,600 and k = 1e7.
 
 Extra keys: per-phase times and launch counts from the library's event
-timers, the weight pass's achieved bandwidth, a roofline object for the
-dominant kernel, an end-to-end figure through the C ABI with host buffers
-(pinned), and the CPU oracle timed on a bounded sample of the same workload.
+timers, per-kernel live times (an event pair around every launch), the weight
+pass's bandwidth against its byte model, a roofline object for the kernel
+that leads the live per-kernel list, an end-to-end figure through the C ABI
+with host buffers (pinned), and the CPU oracle timed on a bounded sample of
+the same workload (a slice of its time span, scaled to a whole step).
 
 `--impl reference` times the CPU oracle alone (the reference arm).
+Under torchrun each rank samples its own range of sample ids on a replica of
+the graph; the ranks' integer sums are combined by one all-reduce and checked
+against a single-rank run of the same ids.
 """
 from __future__ import annotations
 
@@ -29,7 +36,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-DEFAULT_WORKLOAD = "cl2m_cycle4"
+DEFAULT_WORKLOAD = "cl50m_cycle5chord"
 
 
 def parse():
@@ -57,6 +64,12 @@ def parse():
                     help="weight budget for --serve-workload as a fraction of free device memory after the build")
     ap.add_argument("--alloc", choices=["native", "torch"], default="native",
                     help="device memory: the library's stream-ordered pool or PyTorch's caching allocator")
+    ap.add_argument("--cpu-slice", type=float, default=0.1,
+                    help="fraction of the time span the CPU baseline's oracle runs on (then scaled)")
+    ap.add_argument("--ref-slice", type=float, default=0.02,
+                    help="fraction of the time span of each reference-arm step")
+    ap.add_argument("--ref-samples", type=int, default=200_000,
+                    help="samples the oracle draws per reference-arm step (scaled to k)")
     return ap.parse_args()
 
 
@@ -119,6 +132,10 @@ def measured_peaks():
 KERNEL_SOURCES = {
     "k_sample": ["sampler.cu", "tm_device.cuh", "tm_internal.h"],
     "k_dp": ["weights.cu", "tm_device.cuh", "tm_internal.h"],
+    "k_gather2_pair": ["csr.cu", "tm_internal.h"],
+    "k_gather2": ["csr.cu", "tm_internal.h"],
+    "k_rs_scatter": ["csr.cu", "tm_internal.h"],
+    "k_segscan2": ["scan.cuh", "weights.cu", "tm_device.cuh", "tm_internal.h"],
 }
 
 
@@ -126,7 +143,7 @@ def kernel_source_hash(kernel):
     """sha256 over the sources that define a kernel (the files in order)."""
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES[kernel]:
+    for f in KERNEL_SOURCES.get(kernel, []):
         with open(os.path.join(ROOT, "paper_2507_20441_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -137,7 +154,7 @@ def profiled_traffic(kernel, workload):
     from the committed ncu summary profiles/<kernel>_<workload>.md, or None
     when there is none or the kernel's sources changed since the capture."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
-    if not os.path.exists(path):
+    if kernel not in KERNEL_SOURCES or not os.path.exists(path):
         return None
     fields = {}
     with open(path) as f:
@@ -157,11 +174,11 @@ def profiled_traffic(kernel, workload):
 # ------------------------------------------------ algorithmic byte models ----
 def dp_bytes_per_edge(plan_children):
     """Bytes one weight-DP launch must move per edge for a tree node with the
-    given children (list of (leaf, has_exclusion)), both layers:
-    the edge record (t, src, dst, pair) and the reverse-pair id, read once;
-    per layer and child the two list bounds (2 x 4 B offsets) and, for a
-    non-leaf child, the four prefix values that bound the candidate range
-    and its exclusion (4 x 8 B); per layer the 8 B weight written."""
+    given children (list of leaf flags), both layers: the edge record (t,
+    src, dst, pair) and the reverse-pair id, read once; per layer and child
+    the two list bounds (2 x 4 B offsets) and, for a non-leaf child, the four
+    prefix values that bound the candidate range and its exclusion (4 x 8 B);
+    per layer the 8 B weight written."""
     b = 16 + 4
     for _ in range(2):
         for leaf in plan_children:
@@ -170,6 +187,31 @@ def dp_bytes_per_edge(plan_children):
                 b += 32
         b += 8
     return b
+
+
+def tree_children(order, parent):
+    ntree = len(order)
+    children = {q: [] for q in range(ntree)}
+    for q in range(1, ntree):
+        children[int(parent[q])].append(q)
+    return children
+
+
+def weight_pass_bytes_per_edge(children):
+    """The weight pass's byte model per edge, both layers (the survey's
+    per-layer formula for this tree): for each non-leaf node a 16 B edge
+    record, 32 B of candidate- and exclusion-list bounds per child, 32 B of
+    prefix reads per non-leaf child and an 8 B weight write; for each
+    non-root, non-leaf node two prefix orders of (4 B map + 8 B read + 8 B
+    write); for the root 8 B write + 8 B read + 8 B CDF write."""
+    per_layer = 0
+    for q, ch in children.items():
+        if not ch:
+            continue
+        per_layer += 16 + 32 * len(ch) + 32 * sum(1 for c in ch if children[c]) + 8
+    per_layer += sum(1 for q, ch in children.items() if q != 0 and ch) * 2 * (4 + 8 + 8)
+    per_layer += 24
+    return 2 * per_layer
 
 
 def graph_stats(gr):
@@ -202,6 +244,47 @@ def sampler_bytes_per_sample(ntree, nontree, stats, nwin):
     return b
 
 
+def kernel_family(name):
+    for fam in ("k_sample", "k_dp", "k_gather2_pair", "k_gather2", "k_rs_scatter", "k_segscan2"):
+        if name.startswith(fam):
+            return fam
+    return name.split("<")[0]
+
+
+def kernel_model(name, launches_per_step, ctx_m, k, children, per_sample):
+    """Algorithmic bytes per launch of a kernel the live per-kernel list can
+    put first, with the model's wording; None for a kernel without one."""
+    fam = kernel_family(name)
+    if fam == "k_sample":
+        return k * per_sample, f"effective bytes (every search probe at 8 B): {per_sample} B/sample x k"
+    if fam == "k_dp":
+        per_step = sum(ctx_m * dp_bytes_per_edge([not children[c] for c in ch]) for ch in children.values() if ch)
+        return per_step / max(launches_per_step, 1), \
+            "streamed edge record, list bounds, prefix reads and weight writes per edge (averaged over the DP launches)"
+    if fam == "k_gather2_pair":
+        return 40 * ctx_m, "two sets x (4 B index + two 4 B gathered reads + two 4 B writes) per edge"
+    if fam == "k_gather2":
+        return 20 * ctx_m, "4 B index + two 4 B gathered reads + two 4 B writes per edge"
+    return None, None
+
+
+# ------------------------------------------------------- rank combining ----
+def combine_across_ranks(res, device=None):
+    """Sum the integer results of all ranks (disjoint sample-id ranges):
+    hits2 (128-bit, as 16-bit limbs) and the four counters, one all-reduce.
+    `res` has hits2, valid, rej_vertex, rej_delta, rej_order."""
+    from paper_2507_20441_gb300.shard import all_reduce_counts
+    return all_reduce_counts(res.hits2, res.valid, res.rej_vertex, res.rej_delta, res.rej_order, device=device)
+
+
+def workload_config(args, gr, mo, k, tree, root):
+    """The workload as both arms name it (identical dictionaries)."""
+    return {"workload": args.workload, "n": int(gr.n), "m": int(gr.m), "motif": mo.name, "delta": int(mo.delta),
+            "k": int(k), "tree": sorted(int(x) for x in tree), "root": int(root),
+            "l2": "flushed (512 MB write) before every timed step", "alloc": args.alloc,
+            "graph": "Chung-Lu bursty" if "cl" in args.workload else "uniform"}
+
+
 # ------------------------------------------------------------------ ours ----
 def run_ours(args, rank, world, local_rank):
     import numpy as np
@@ -214,8 +297,9 @@ def run_ours(args, rank, world, local_rank):
     gr = synth.make_graph(args.workload)
     mo = synth.make_motif(args.workload)
     k = args.k or mo.k
+    tree, root = reference_tree(mo)
     stream = torch.cuda.Stream(device=dev)
-    ctx = tg.Context(device=local_rank, stream=stream.cuda_stream, profile=True,
+    ctx = tg.Context(device=local_rank, stream=stream.cuda_stream, profile=2,
                      torch_allocator=(args.alloc == "torch"))
     src_d = torch.from_numpy(gr.src.view(np.int32)).to(dev)
     dst_d = torch.from_numpy(gr.dst.view(np.int32)).to(dev)
@@ -226,7 +310,9 @@ def run_ours(args, rank, world, local_rank):
     state = {}
 
     def step(i, host=False):
-        first = (rank * 1_000_000 + i) * k
+        # rank r of N draws ids [(i N + r) k, (i N + r + 1) k): the ranks of one
+        # step cover one contiguous range of N k sample ids
+        first = (i * world + rank) * k
         if host:
             ctx.load_graph(gr.n, state["src_h"], state["dst_h"], state["t_h"], flags=tg.TM_HOST)
         else:
@@ -240,7 +326,7 @@ def run_ours(args, rank, world, local_rank):
         m.free()
         return res
 
-    def timed(nsteps, host=False):
+    def timed(nsteps, host=False, base=0):
         times = []
         for i in range(nsteps):
             with torch.cuda.stream(stream):
@@ -248,7 +334,7 @@ def run_ours(args, rank, world, local_rank):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            res = step(i, host)
+            res = step(base + i, host)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -257,6 +343,7 @@ def run_ours(args, rank, world, local_rank):
     for i in range(args.warmup):
         step(10_000 + i)
     ctx.phase_times()
+    ctx.kernel_times()
     ctx.io_bytes()
     clocks = ClockSampler(local_rank)
     if world > 1:
@@ -267,6 +354,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clk = clocks.stop()
     phases = ctx.phase_times()
+    ktimes = ctx.kernel_times()
     ctx.io_bytes()
     my_ms = sum(times)
     if world > 1:
@@ -278,6 +366,24 @@ def run_ours(args, rank, world, local_rank):
     value = world * k * args.steps / (my_ms / 1e3)
     launches = sum(n for _, n in phases.values())
 
+    # ---- the ranks' results of the last timed step combined (one all-reduce);
+    # with N > 1 rank 0 checks them against one run over the same N k ids
+    last = args.steps - 1
+    hits2, valid, rv, rd, ro = combine_across_ranks(res, dev) if world > 1 else \
+        (res.hits2, res.valid, res.rej_vertex, res.rej_delta, res.rej_order)
+    combined = {"ranks": world, "samples": world * k, "first_id": last * world * k, "hits2": hits2, "valid": valid,
+                "rej_vertex": rv, "rej_delta": rd, "rej_order": ro,
+                "estimate": state["W"] * hits2 / (2.0 * world * k) if k else 0.0}
+    if world > 1 and rank == 0:
+        m = ctx.motif(mo.nv, mo.edges, mo.rank, mo.delta)
+        m.weights()
+        one = m.sample(world * k, args.seed, last * world * k)
+        m.free()
+        combined["equals_single_rank_run"] = (one.hits2, one.valid, one.rej_vertex, one.rej_delta,
+                                              one.rej_order) == (hits2, valid, rv, rd, ro)
+    ctx.phase_times()
+    ctx.kernel_times()
+
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -285,72 +391,78 @@ def run_ours(args, rank, world, local_rank):
         state["dst_h"] = torch.from_numpy(gr.dst.view(np.int32)).pin_memory().numpy().view(np.uint32)
         state["t_h"] = torch.from_numpy(gr.t).pin_memory().numpy()
         step(20_000, host=True)
-        ctx.phase_times(); ctx.io_bytes()
+        ctx.phase_times(); ctx.io_bytes(); ctx.kernel_times()
         n_e2e = max(3, args.steps // 4)
-        t_e2e, _ = timed(n_e2e, host=True)
+        t_e2e, _ = timed(n_e2e, host=True, base=30_000)
         h2d, d2h = ctx.io_bytes()
-        ctx.phase_times()
-        e2e = {"value": k * n_e2e / (sum(t_e2e) / 1e3), "unit": "samples/s",
+        ctx.phase_times(); ctx.kernel_times()
+        e2e = {"value": world * k * n_e2e / (sum(t_e2e) / 1e3), "unit": "samples/s",
                "h2d_bytes_per_step": h2d // n_e2e, "d2h_bytes_per_step": d2h // n_e2e,
                "ms_per_step": sum(t_e2e) / n_e2e}
 
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the kernel that leads the live per-kernel list
     peak, peak_kind = measured_peaks()
     per = {name: (ms / args.steps, n / args.steps) for name, (ms, n) in phases.items() if n}
     order, parent = state["plan"]
+    assert sorted(int(x) for x in order) == sorted(tree) and int(order[0]) == root, "default tree mismatch"
     ntree = len(order)
-    children = {q: [] for q in range(ntree)}
-    for q in range(1, ntree):
-        children[int(parent[q])].append(q)
+    children = tree_children(order, parent)
     m_edges = ctx.m
-    dp_bytes = 0
-    for q in range(ntree):
-        if children[q]:
-            dp_bytes += m_edges * dp_bytes_per_edge([not children[c] for c in children[q]])
-    dp_ms, dp_n = per.get("dp", (0.0, 0))
-    samp_ms, samp_n = per.get("sample", (0.0, 0))
+    gst = graph_stats(gr)
+    nwin = 2 * (ctx.T // mo.delta + 1)
+    per_sample = sampler_bytes_per_sample(ntree, len(mo.edges) - ntree, gst, nwin)
+    kern = sorted(((name, ms / args.steps, n / args.steps) for name, (ms, n) in ktimes.items()),
+                  key=lambda x: -x[1])
+    top_name, top_ms, top_n = kern[0]
+    algo, model = kernel_model(top_name, top_n, m_edges, k, children, per_sample)
+    kern_ms = top_ms / max(top_n, 1)
+    achieved = algo / (kern_ms / 1e3) / 1e9 if (algo and kern_ms > 0) else None
+    roofline = {"bound": "hbm", "kernel": top_name, "achieved": round(achieved, 1) if achieved else None,
+                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": round(achieved / peak, 4) if achieved else None,
+                "traffic": profiled_traffic(kernel_family(top_name), args.workload),
+                "algorithmic_bytes_per_launch": int(algo) if algo else None, "model": model,
+                "launch_ms": round(kern_ms, 4), "launches_per_step": top_n,
+                "share_of_step": round(top_ms / ms_per_step, 4),
+                "timing": "CUDA events around every launch on the library stream, timed steps"}
+    step_kernels = [{"kernel": nm, "ms_per_step": round(ms, 4), "launches_per_step": n,
+                     "share": round(ms / ms_per_step, 4)} for nm, ms, n in kern[:12]]
+
+    # ---- weight pass against its byte model
     weight_ms = sum(per.get(p, (0.0, 0))[0] for p in ("windows", "dp", "prefix", "root"))
-    # the dominant single kernel: the sampler or the weight DP (the CSR phase
-    # is dozens of small sort kernels, none of which leads the launch list)
-    if samp_ms >= dp_ms:
-        gst = graph_stats(gr)
-        nwin = 2 * (ctx.T // mo.delta + 1)
-        per_sample = sampler_bytes_per_sample(ntree, len(mo.edges) - ntree, gst, nwin)
-        algo = k * per_sample
-        kern_ms = samp_ms / max(samp_n, 1)
-        kname, model = "k_sample", f"effective bytes (every search probe at 8 B): {per_sample} B/sample x k"
-    else:
-        algo = dp_bytes / max(dp_n, 1)
-        kern_ms = dp_ms / max(dp_n, 1)
-        kname, model = "k_dp", "streamed edge record, list bounds, prefix reads and weight writes per edge"
-    achieved = algo / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else 0.0
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": profiled_traffic(kname, args.workload),
-                "algorithmic_bytes_per_launch": int(algo), "model": model,
-                "launch_ms": round(kern_ms, 4)}
+    wp_bytes = m_edges * weight_pass_bytes_per_edge(children)
+    dp_bytes = sum(m_edges * dp_bytes_per_edge([not children[c] for c in ch]) for ch in children.values() if ch)
+    dp_ms = per.get("dp", (0.0, 0))[0]
+    wp_gbps = wp_bytes / (weight_ms / 1e3) / 1e9 if weight_ms else None
+    weight_pass = {"ms": round(weight_ms, 4), "edges_per_s": m_edges / (weight_ms / 1e3) if weight_ms else None,
+                   "model_bytes": int(wp_bytes), "model_bytes_per_edge": weight_pass_bytes_per_edge(children),
+                   "GBps": round(wp_gbps, 1) if wp_gbps else None,
+                   "frac_of_peak": round(wp_gbps / peak, 4) if wp_gbps else None,
+                   "dp_GBps": round(dp_bytes / (dp_ms / 1e3) / 1e9, 1) if dp_ms else None,
+                   "dp_frac_of_peak": round(dp_bytes / (dp_ms / 1e3) / 1e9 / peak, 4) if dp_ms else None,
+                   "model": "windows + DP + prefix sums + root CDF; per layer: non-leaf nodes 16 B record + 32 B "
+                            "bounds per child + 32 B prefix reads per non-leaf child + 8 B write; prefix nodes "
+                            "2 x (4 + 8 + 8) B; root 24 B"}
 
     ablation = None if args.no_ablation else run_ablation(ctx, mo, k, args.seed, stream)
     batched = None if args.no_batch else run_batched(ctx, tg, synth, stream)
-    served = None if args.no_serve else run_served(ctx, tg, synth, args.serve_queries, args.serve_rate)
+    served = None if args.no_serve else run_served(ctx, tg, synth, args.serve_queries, args.serve_rate,
+                                                   compare_plain=True)
 
     out = {
         "metric": "samples/s", "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": args.workload, "n": gr.n, "m": int(ctx.m), "motif": mo.name, "delta": mo.delta,
-                   "k": k, "tree": [int(x) for x in order], "root": int(order[0]),
-                   "l2": "flushed (512 MB write) before every timed step", "alloc": args.alloc,
-                   "graph": "Chung-Lu bursty" if "cl" in args.workload else "uniform"},
+        "config": workload_config(args, gr, mo, k, tree, root),
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": launches,
         "roofline": roofline,
+        "kernels_per_step": step_kernels,
         "phases_ms_per_step": {k_: round(v[0], 4) for k_, v in per.items()},
-        "weight_pass": {"ms": round(weight_ms, 4), "edges_per_s": m_edges / (weight_ms / 1e3) if weight_ms else None,
-                        "dp_GBps": round(dp_bytes / (dp_ms / 1e3) / 1e9, 1) if dp_ms else None,
-                        "dp_frac_of_peak": round(dp_bytes / (dp_ms / 1e3) / 1e9 / peak, 4) if dp_ms else None},
-        "estimate": res.estimate, "W": state["W"], "hits2": res.hits2, "valid": res.valid,
+        "weight_pass": weight_pass,
+        "estimate": combined["estimate"], "W": state["W"], "hits2": hits2, "valid": valid,
+        "combined": combined,
         "ablation": ablation,
         "batched": batched,
         "served": served,
@@ -358,7 +470,8 @@ def run_ours(args, rank, world, local_rank):
     ctx.close()
     if args.serve_workload:
         out["served_large"] = run_served_large(args, tg, synth, dev, stream)
-    return out
+    state["graph"] = gr
+    return out, gr
 
 
 # ------------------------------------------------------ batched / served ----
@@ -399,13 +512,14 @@ def run_batched(ctx, tg, synth, stream, reps=3):
     same = all((a.hits2, a.valid, a.rej_vertex, a.rej_delta, a.rej_order) ==
                (b.hits2, b.valid, b.rej_vertex, b.rej_delta, b.rej_order) for a, b in zip(plain, batch))
     ctx.phase_times()
+    ctx.kernel_times()
     for m in motifs:
         m.free()
     return {"queries": len(pool), "samples": int(sum(ks)), "k_range": [int(min(ks)), int(max(ks))],
             "plain_ms": round(ms_plain, 3), "batched_ms": round(ms_batch, 3),
             "plain_qps": round(len(pool) / (ms_plain / 1e3), 1), "batched_qps": round(len(pool) / (ms_batch / 1e3), 1),
             "speedup": round(ms_plain / ms_batch, 3), "identical_results": bool(same),
-            "autotuned_shape": {k_: tuned[k_] for k_ in ("tile", "threads", "smem_records")},
+            "autotuned_shape": {k_: tuned[k_] for k_ in tuned if k_ != "ms"},
             "autotune_s": round(tune_s, 3), "shapes_tried": len(table),
             "timing": "best of %d, CUDA events on the library stream, weights precomputed" % reps}
 
@@ -431,39 +545,86 @@ def run_ablation(ctx, mo, k, seed, stream):
                      "estimate": r.estimate, "weights_ms": round(e0.elapsed_time(e1), 3),
                      "sample_ms": round(e1.elapsed_time(e2), 3)}
         m.free()
+    ctx.phase_times()
+    ctx.kernel_times()
     return out
 
 
-def run_served(ctx, tg, synth, nq, rate, weight_budget=0):
+def _pct(xs, p):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(p * (len(xs) - 1) + 0.5))] if xs else None
+
+
+def run_plain_queries(ctx, pool, picks, arrivals, seeds):
+    """The same arrival trace served the plain way: one query at a time in
+    arrival order, each with its own weight pass (tm_weights) and one
+    tm_sample launch; latency is arrival-to-result on the host clock."""
+    t0 = time.perf_counter()
+    lat, results = [], []
+    for i, (q, a) in enumerate(zip(picks, arrivals)):
+        now = time.perf_counter() - t0
+        if a > now:
+            time.sleep(a - now)
+        mo = pool[int(q)]
+        m = ctx.motif(mo.nv, mo.edges, mo.rank, mo.delta)
+        m.weights()
+        r = m.sample(mo.k, seeds[i])
+        m.free()
+        lat.append((time.perf_counter() - t0 - a) * 1e3)
+        results.append(r)
+    wall = time.perf_counter() - t0
+    return results, {"p50_ms": round(_pct(lat, 0.5), 3), "p99_ms": round(_pct(lat, 0.99), 3),
+                     "mean_ms": round(sum(lat) / len(lat), 3), "qps": round(len(lat) / wall, 2),
+                     "wall_s": round(wall, 3)}
+
+
+def run_served(ctx, tg, synth, nq, rate, weight_budget=0, compare_plain=False):
     """Poisson arrivals at `rate` queries/s drawn from the 32-motif pool (k
     log-uniform in [1e4, 1e7]), served by continuous batching with cached
-    weights; latency is submit-to-result on the host clock."""
+    weights; latency is submit-to-result on the host clock.  With
+    compare_plain the same trace is then run the plain way (one weight pass
+    and one sampler launch per query, in arrival order) and both latency
+    profiles and the share of identical results are reported."""
     import numpy as np
     pool = synth.motif_pool(seed=7, count=32)
     rng = np.random.default_rng(17)
     gaps = rng.exponential(1.0 / rate, size=nq)
     picks = rng.integers(0, len(pool), size=nq)
+    arrivals = np.cumsum(gaps)
+    seeds = [5000 + i for i in range(nq)]
     ctx.serve_start(max_active=64, weight_budget=weight_budget)
     tickets = []
     t0 = time.perf_counter()
-    due = t0
     for i in range(nq):
-        due += gaps[i]
-        now = time.perf_counter()
-        if due > now:
-            time.sleep(due - now)
+        now = time.perf_counter() - t0
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
         mo = pool[int(picks[i])]
-        tickets.append(ctx.submit(mo.nv, mo.edges, mo.rank, mo.delta, mo.k, 5000 + i))
+        tickets.append(ctx.submit(mo.nv, mo.edges, mo.rank, mo.delta, mo.k, seeds[i]))
+    served = []
     for t in tickets:
         r = ctx.poll(t, timeout_ms=600_000)
         assert r is not None
+        served.append(r)
     wall = time.perf_counter() - t0
     st = ctx.serve_stats()
     ctx.serve_stop()
-    return {"queries": nq, "arrival_rate_qps": rate, "wall_s": round(wall, 3),
-            "completed": st["completed"], "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
-            "mean_ms": round(st["mean_ms"], 3), "qps": round(st["qps"], 2), "cache_hits": st["cache_hits"],
-            "cache_misses": st["cache_misses"], "evictions": st["evictions"], "rounds": st["rounds"]}
+    out = {"queries": nq, "arrival_rate_qps": rate, "wall_s": round(wall, 3),
+           "completed": st["completed"], "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+           "mean_ms": round(st["mean_ms"], 3), "qps": round(st["qps"], 2), "cache_hits": st["cache_hits"],
+           "cache_misses": st["cache_misses"], "evictions": st["evictions"], "rounds": st["rounds"],
+           "nomem_retries": st["nomem_retries"]}
+    if compare_plain:
+        plain, pst = run_plain_queries(ctx, pool, picks, arrivals, seeds)
+        same = sum((a.W, a.hits2, a.valid, a.rej_vertex, a.rej_delta, a.rej_order) ==
+                   (b.W, b.hits2, b.valid, b.rej_vertex, b.rej_delta, b.rej_order) for a, b in zip(served, plain))
+        out["plain"] = pst
+        out["identical_results"] = f"{same}/{nq}"
+        out["p50_speedup_vs_plain"] = round(pst["p50_ms"] / out["p50_ms"], 3) if out["p50_ms"] else None
+        out["p99_speedup_vs_plain"] = round(pst["p99_ms"] / out["p99_ms"], 3) if out["p99_ms"] else None
+    ctx.phase_times()
+    ctx.kernel_times()
+    return out
 
 
 def run_served_large(args, tg, synth, dev, stream):
@@ -504,26 +665,56 @@ def run_served_large(args, tg, synth, dev, stream):
 
 
 # ------------------------------------------------------------- oracle ----
-def time_oracle(workload, k_full, seed, tree, root, k_sample, threads):
-    """The CPU oracle on the same workload: graph build and weights in full
-    (single thread), the sampler on k_sample of the k samples with OpenMP,
-    scaled to a whole step of k samples."""
+def oracle_slice_step(gr, mo, tree, root, k, frac, offset, k_sample, seed, threads):
+    """One oracle step on a bounded sample of the workload: the edges whose
+    time lies in [offset, offset + frac) of the span (a time slice keeps the
+    per-window list lengths, the burstiness and every vertex of the full
+    graph, since delta is far below the span).  The oracle's graph build and
+    weight pass are timed in full on the slice and scaled by m / m_slice; its
+    sampler draws k_sample samples with OpenMP, scaled to k."""
     import oracle
-    from paper_2507_20441_gb300 import synth
-    gr = synth.make_graph(workload)
-    mo = synth.make_motif(workload)
-    t0 = time.perf_counter()
-    G = oracle.Graph(gr.n, gr.src, gr.dst, gr.t)
-    t1 = time.perf_counter()
-    G.set_motif(mo.nv, mo.edges, mo.rank, mo.delta, tree, root)
+    t = gr.t
+    t0, t1 = int(t.min()), int(t.max())
+    span = t1 - t0 + 1
+    if frac >= 1.0:
+        src, dst, tt = gr.src, gr.dst, t
+    else:
+        lo = t0 + int(offset * span)
+        hi = t0 + int(min(1.0, offset + frac) * span)
+        sel = (t >= lo) & (t < hi)
+        src, dst, tt = gr.src[sel], gr.dst[sel], t[sel]
+    ms = len(src)
+    a = time.perf_counter()
+    G = oracle.Graph(gr.n, src, dst, tt)
+    b = time.perf_counter()
+    G.set_motif(mo.nv, mo.edges, mo.rank, mo.delta, sorted(tree), root)
     G.weights()
-    t2 = time.perf_counter()
-    G.sample(k_sample, seed, 0, threads=threads)
-    t3 = time.perf_counter()
-    step_s = (t1 - t0) + (t2 - t1) + (t3 - t2) * (k_full / k_sample)
-    return {"value": k_full / step_s, "unit": "samples/s", "cores": threads, "kind": "oracle",
-            "sample": f"graph build + weights in full, {k_sample} of {k_full} samples timed and scaled",
-            "graph_s": round(t1 - t0, 3), "weights_s": round(t2 - t1, 3), "sample_s": round(t3 - t2, 3)}
+    c = time.perf_counter()
+    ks = min(k, k_sample)
+    G.sample(ks, seed, 0, threads=threads)
+    d = time.perf_counter()
+    G.close()
+    scale = gr.m / max(ms, 1)
+    step_s = ((b - a) + (c - b)) * scale + (d - c) * (k / max(ks, 1))
+    return {"step_s": step_s, "m_slice": ms, "graph_s": b - a, "weights_s": c - b, "sample_s": d - c,
+            "k_sample": ks, "scale": scale}
+
+
+def slice_fraction(frac, m):
+    """At least 1e6 edges (or the whole graph) per oracle slice."""
+    return 1.0 if m <= 1_000_000 else min(1.0, max(frac, 1_000_000 / m))
+
+
+def cpu_baseline(gr, mo, tree, root, k, frac, seed):
+    threads = os.cpu_count() or 1
+    frac = slice_fraction(frac, gr.m)
+    r = oracle_slice_step(gr, mo, tree, root, k, frac, 0.0, 200_000, seed, threads)
+    return {"value": k / r["step_s"], "unit": "samples/s", "cores": threads, "kind": "oracle",
+            "sample": (f"edges in the first {frac:.0%} of the time span ({r['m_slice']} of {gr.m}): graph build "
+                       f"and weights timed in full and scaled by m/m_slice = {r['scale']:.2f}; "
+                       f"{r['k_sample']} samples (OpenMP) scaled to k = {k}"),
+            "graph_s": round(r["graph_s"], 3), "weights_s": round(r["weights_s"], 3),
+            "sample_s": round(r["sample_s"], 3), "step_s_scaled": round(r["step_s"], 3)}
 
 
 def run_reference(args, rank, world):
@@ -532,25 +723,30 @@ def run_reference(args, rank, world):
     import oracle
     from paper_2507_20441_gb300 import synth
     oracle.build()
+    gr = synth.make_graph(args.workload)
     mo = synth.make_motif(args.workload)
     k = args.k or mo.k
     tree, root = reference_tree(mo)
     threads = os.cpu_count() or 1
-    k_sample = min(k, 100_000)
+    frac = slice_fraction(args.ref_slice, gr.m)
+    nslices = max(1, int(1.0 / frac))
     vals = []
     for i in range(args.warmup + args.steps):
-        r = time_oracle(args.workload, k, args.seed + i, tree, root, k_sample, threads)
+        off = (i % nslices) * frac if frac < 1.0 else 0.0
+        r = oracle_slice_step(gr, mo, tree, root, k, frac, off, args.ref_samples, args.seed + i, threads)
         if i >= args.warmup:
             vals.append(r)
-    step_s = statistics.mean(k / v["value"] for v in vals)
+    step_s = statistics.mean(v["step_s"] for v in vals)
     value = k / step_s
+    sample = (f"per step the edges of one {frac:.0%} slice of the time span (about {vals[0]['m_slice']} of "
+              f"{gr.m}; slices rotate over the span): oracle graph build and weights timed in full and scaled "
+              f"by m/m_slice, {vals[0]['k_sample']} samples (OpenMP) scaled to k = {k}")
     return {"impl": "reference", "metric": "samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": args.workload, "motif": mo.name, "delta": mo.delta, "k": k,
-                       "tree": tree, "root": root},
+            "config": workload_config(args, gr, mo, k, tree, root),
             "cpu_baseline": {"kind": "oracle", "cores": threads, "value": value, "unit": "samples/s",
-                             "sample": vals[0]["sample"]},
+                             "sample": sample},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -613,13 +809,15 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
-    out = run_ours(args, rank, world, local_rank)
+    out, gr = run_ours(args, rank, world, local_rank)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            tree = out["config"]["tree"]
-            out["cpu_baseline"] = time_oracle(args.workload, out["config"]["k"], args.seed, sorted(tree),
-                                              out["config"]["root"], min(out["config"]["k"], 100_000),
-                                              os.cpu_count() or 1)
+            import oracle
+            from paper_2507_20441_gb300 import synth
+            oracle.build()
+            mo = synth.make_motif(args.workload)
+            c = out["config"]
+            out["cpu_baseline"] = cpu_baseline(gr, mo, c["tree"], c["root"], c["k"], args.cpu_slice, args.seed)
         print(json.dumps(out))
     if world > 1:
         import torch

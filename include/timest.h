@@ -83,7 +83,8 @@ typedef struct {
     int device;             /* CUDA device ordinal (default 0)              */
     int sample_threads;     /* threads per block of the sampler (0 = auto)  */
     int sample_tile;        /* samples per work item of batched runs (0 = auto) */
-    int profile;            /* 1: time every phase with CUDA events        */
+    int profile;            /* 1: time every phase with CUDA events;
+                               2: also every kernel launch (tm_kernel_times) */
     int reserved[7];
 } tm_config;
 
@@ -294,9 +295,10 @@ int tm_batch_run(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64
 /* ---- serving: continuous batching over a resident graph ----------------
  * Between tm_serve_start and tm_serve_stop only the tm_serve_* calls (and
  * tm_last_error) may be made on ctx; submit and poll are thread safe.
- * Each query runs on its motif's default tree (tm_set_motif) with sample ids
- * 0..k-1, so its result equals tm_sample on that tree with the same k and
- * seed whatever else is being served. */
+ * Each query runs on its motif's default tree (tm_set_motif), or on the plan
+ * of the motif handle given to tm_serve_submit_motif, with sample ids 0..k-1,
+ * so its result equals tm_sample on that plan with the same k and seed
+ * whatever else is being served. */
 typedef struct {
     uint32_t max_active;      /* queries sampled concurrently (0 = 64)                 */
     uint32_t tile;            /* samples per work item (0 = 4096)                      */
@@ -314,6 +316,9 @@ typedef struct {
     uint64_t resident_bytes, waiting, active;
     double p50_ms, p99_ms, mean_ms;   /* submit-to-completion latency          */
     double qps;                       /* completed / (last completion - first submit) */
+    uint64_t nomem_retries;           /* back-offs after a device allocation failed:
+                                         a weight pass retried by admission or a
+                                         sampling round run again              */
 } tm_serve_stats_t;
 
 /* Start the admission and scheduling threads on a preprocessed graph.
@@ -322,9 +327,23 @@ int tm_serve_start(tm_ctx *ctx, const tm_serve_cfg *cfg);
 
 /* Queue a query M = (H, pi, delta) (arguments as tm_set_motif) with k samples
  * from seed; *ticket identifies it.  Errors: TM_E_STATE (not serving),
- * TM_E_MOTIF, TM_E_ARG. */
+ * TM_E_MOTIF, TM_E_ARG.
+ * Admission: when a query's weight pass (or a sampling round) runs out of
+ * device memory, the server frees cached weights that no query holds, waits
+ * for queries in flight and retries (up to 200 times, 20 ms apart) before the
+ * query fails with TM_E_NOMEM; tm_serve_stats counts these back-offs. */
 int tm_serve_submit(tm_ctx *ctx, uint32_t nv, uint32_t ne, const uint32_t *edges, const uint32_t *order,
                     int64_t delta, uint64_t k, uint64_t seed, uint64_t *ticket);
+
+/* Queue a query on a motif handle of this context with its plan as it stands:
+ * the spanning tree and root pinned by tm_set_tree (Alg. 7's choice, e.g. the
+ * winner of tm_select_tree) and the constraint settings of tm_set_constraints.
+ * The server copies the plan (mo stays the caller's, and may be freed or
+ * changed after the call) and computes or reuses the weights of that exact
+ * plan; the result equals tm_sample on mo with the same k and seed.
+ * Errors: TM_E_STATE (not serving), TM_E_ARG (null, or a motif of another
+ * context). */
+int tm_serve_submit_motif(tm_ctx *ctx, const tm_motif *mo, uint64_t k, uint64_t seed, uint64_t *ticket);
 
 /* Wait at most timeout_ms for a query; on completion copy its result and
  * release the ticket.  Returns the query's own status (TM_OK, or e.g.
@@ -362,6 +381,21 @@ enum {
  * call (ms[cap], launches[cap]; either may be NULL); resets the counters.
  * Returns TM_NUM_PHASES in *nphases. */
 int tm_phase_times(tm_ctx *ctx, double *ms, uint64_t *launches, int cap, int *nphases);
+
+/* Per-kernel device time, recorded when the context was created with
+ * cfg.profile >= 2: an event pair on the context stream around every launch
+ * (tracing; adds two event records per launch). */
+typedef struct {
+    char name[96];        /* kernel name, e.g. "k_sample_reg<4>" (truncated) */
+    double ms;            /* summed device time since the last call           */
+    uint64_t launches;
+} tm_kernel_time;
+
+/* Kernels launched on ctx since the last reset, in first-launch order: fills
+ * out[0 .. min(cap, *n) - 1] and sets *n to the number of distinct kernels; a
+ * call with cap > 0 then resets the sums (cap = 0 only counts).  Synchronizes
+ * the context stream.  Errors: TM_E_ARG. */
+int tm_kernel_times(tm_ctx *ctx, tm_kernel_time *out, uint32_t cap, uint32_t *n);
 
 /* Host->device and device->host bytes copied by the library on ctx since the
  * last call (inputs, results, counts and status words); resets them. */

@@ -87,6 +87,10 @@ class Result:
                       int(r.rej_order), float(r.estimate))
 
 
+class tm_kernel_time(C.Structure):
+    _fields_ = [("name", C.c_char * 96), ("ms", C.c_double), ("launches", C.c_uint64)]
+
+
 class tm_tune_entry(C.Structure):
     _fields_ = [("tile", C.c_int), ("threads", C.c_int), ("smem_records", C.c_int), ("ms", C.c_double)]
 
@@ -104,7 +108,7 @@ class tm_serve_stats_t(C.Structure):
                 ("cache_hits", C.c_uint64), ("cache_misses", C.c_uint64), ("evictions", C.c_uint64),
                 ("rounds", C.c_uint64), ("resident_bytes", C.c_uint64), ("waiting", C.c_uint64),
                 ("active", C.c_uint64), ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
-                ("qps", C.c_double)]
+                ("qps", C.c_double), ("nomem_retries", C.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -147,10 +151,12 @@ def _declare(L):
     L.tm_batch_shape.argtypes = [vp, i32, i32, i32]
     L.tm_serve_start.argtypes = [vp, C.POINTER(tm_serve_cfg)]
     L.tm_serve_submit.argtypes = [vp, u32, u32, vp, vp, i64, u64, u64, C.POINTER(u64)]
+    L.tm_serve_submit_motif.argtypes = [vp, vp, u64, u64, C.POINTER(u64)]
     L.tm_serve_poll.argtypes = [vp, u64, C.POINTER(tm_result), i32]
     L.tm_serve_stats.argtypes = [vp, C.POINTER(tm_serve_stats_t)]
     L.tm_serve_stop.argtypes = [vp]
     L.tm_io_bytes.argtypes = [vp, C.POINTER(u64), C.POINTER(u64)]
+    L.tm_kernel_times.argtypes = [vp, C.POINTER(tm_kernel_time), u32, C.POINTER(u32)]
     return L
 
 
@@ -225,7 +231,7 @@ def tm_create(device: int = 0, stream=None, torch_allocator: bool = True, sample
     cfg.device = device
     cfg.sample_threads = sample_threads
     cfg.sample_tile = sample_tile
-    cfg.profile = 1 if profile else 0
+    cfg.profile = int(profile)
     keep = []
     if alloc_hooks is not None:
         cfg.alloc, cfg.free = alloc_hooks
@@ -454,6 +460,13 @@ def tm_serve_submit(ctx, nv, edges, order, delta, k, seed) -> int:
     return int(t.value)
 
 
+def tm_serve_submit_motif(ctx, motif, k, seed) -> int:
+    """Queue a query on a motif handle's plan (pinned tree, root, constraints)."""
+    t = C.c_uint64()
+    _check(lib().tm_serve_submit_motif(ctx, motif, int(k), int(seed), C.byref(t)), ctx, "tm_serve_submit_motif")
+    return int(t.value)
+
+
 def tm_serve_poll(ctx, ticket, timeout_ms=0):
     """Result of a finished query, or None while it is still running."""
     r = tm_result()
@@ -483,6 +496,16 @@ def tm_phase_times(ctx):
     ms = np.zeros(16, np.float64); ln = np.zeros(16, np.uint64); n = C.c_int()
     _check(lib().tm_phase_times(ctx, _ptr(ms), _ptr(ln), 16, C.byref(n)), ctx, "tm_phase_times")
     return {PHASES[i] if i < len(PHASES) else str(i): (float(ms[i]), int(ln[i])) for i in range(n.value)}
+
+
+def tm_kernel_times(ctx):
+    """{kernel name: (ms, launches)} since the last call (profile=2 contexts)."""
+    n = C.c_uint32()
+    _check(lib().tm_kernel_times(ctx, None, 0, C.byref(n)), ctx, "tm_kernel_times")
+    cap = max(1, n.value + 8)
+    arr = (tm_kernel_time * cap)()
+    _check(lib().tm_kernel_times(ctx, arr, cap, C.byref(n)), ctx, "tm_kernel_times")
+    return {arr[i].name.decode(): (float(arr[i].ms), int(arr[i].launches)) for i in range(min(n.value, cap))}
 
 
 def tm_io_bytes(ctx):
@@ -591,6 +614,10 @@ class Context:
     def submit(self, nv, edges, order, delta, k, seed) -> int:
         return tm_serve_submit(self.h, nv, edges, order, delta, k, seed)
 
+    def submit_motif(self, motif: "Motif", k, seed) -> int:
+        """Serve a motif with its pinned tree and constraint settings."""
+        return tm_serve_submit_motif(self.h, motif.h, k, seed)
+
     def poll(self, ticket, timeout_ms=0):
         return tm_serve_poll(self.h, ticket, timeout_ms)
 
@@ -605,6 +632,9 @@ class Context:
 
     def io_bytes(self):
         return tm_io_bytes(self.h)
+
+    def kernel_times(self):
+        return tm_kernel_times(self.h)
 
     def autotune(self, motifs, ks, seeds, target_samples=0):
         return tm_autotune(self.h, [m.h for m in motifs], ks, seeds, target_samples)

@@ -4,6 +4,9 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <cxxabi.h>
+#include <stdlib.h>
+
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -198,8 +201,39 @@ PhaseScope::~PhaseScope()
     ctx->pending.push_back({phase, a, b, launches});
 }
 
+KernelTimer::KernelTimer(tm_ctx *c, const void *f) : ctx(c), fn(f)
+{
+    if (ctx->cfg.profile >= 2) {
+        a = take_event(ctx);
+        if (a) cudaEventRecord(a, ctx->stream);
+    }
+}
+
+KernelTimer::~KernelTimer()
+{
+    if (!a) return;
+    cudaEvent_t b = take_event(ctx);
+    if (!b) { ctx->ev_pool.push_back(a); return; }
+    cudaEventRecord(b, ctx->stream);
+    ctx->pending_k.push_back({fn, a, b});
+}
+
 void prof_collect(tm_ctx *ctx)
 {
+    for (auto &p : ctx->pending_k) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            auto it = std::find_if(ctx->kernel_ms.begin(), ctx->kernel_ms.end(),
+                                   [&](const std::pair<const void *, std::pair<double, uint64_t>> &e) { return e.first == p.fn; });
+            if (it == ctx->kernel_ms.end()) ctx->kernel_ms.push_back({p.fn, {(double)ms, 1}});
+            else { it->second.first += ms; it->second.second += 1; }
+        } else {
+            cudaGetLastError();
+        }
+        ctx->ev_pool.push_back(p.a);
+        ctx->ev_pool.push_back(p.b);
+    }
+    ctx->pending_k.clear();
     for (auto &p : ctx->pending) {
         float ms = 0.f;
         if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
@@ -443,6 +477,28 @@ static int compile_plan(const MotifDesc &M, const int *tree, int root, int64_t d
     }
     P.coupled = (P.nnt > 0 && P.nt_pos[0] == 0 && P.nt_pos[P.nnt - 1] == M.ne - 1) ? 1 : 0;
     return TM_OK;
+}
+
+// A kernel's name without namespaces and parameter list, e.g.
+// "k_sample_reg<4>" (demangled when the runtime reports a mangled name).
+static std::string short_kernel_name(const char *raw)
+{
+    std::string s = raw;
+    int status = 0;
+    char *dm = abi::__cxa_demangle(raw, nullptr, nullptr, &status);
+    if (status == 0 && dm) s = dm;
+    free(dm);
+    const char *drop[] = {"timest::", "(anonymous namespace)::", "void "};
+    for (const char *d : drop)
+        for (size_t p; (p = s.find(d)) != std::string::npos;) s.erase(p, strlen(d));
+    // cut the parameter list: the first '(' outside template brackets
+    int depth = 0;
+    for (size_t i = 0; i < s.size(); ++i) {
+        if (s[i] == '<') ++depth;
+        else if (s[i] == '>') --depth;
+        else if (s[i] == '(' && depth == 0) { s.resize(i); break; }
+    }
+    return s;
 }
 
 }  // namespace timest
@@ -893,6 +949,28 @@ int tm_phase_times(tm_ctx *ctx, double *ms, uint64_t *launches, int cap, int *np
     }
     for (int i = 0; i < TM_NUM_PHASES; ++i) { ctx->phase_ms[i] = 0; ctx->phase_launches[i] = 0; }
     if (nphases) *nphases = TM_NUM_PHASES;
+    return TM_OK;
+}
+
+int tm_kernel_times(tm_ctx *ctx, tm_kernel_time *out, uint32_t cap, uint32_t *n)
+{
+    if (!ctx || !n || (cap && !out)) return TM_E_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    prof_collect(ctx);
+    *n = (uint32_t)ctx->kernel_ms.size();
+    for (uint32_t i = 0; i < cap && i < ctx->kernel_ms.size(); ++i) {
+        const auto &e = ctx->kernel_ms[i];
+        memset(out[i].name, 0, sizeof(out[i].name));
+        const char *raw = nullptr;
+        std::string nm = "?";
+        if (cudaFuncGetName(&raw, e.first) == cudaSuccess && raw) nm = short_kernel_name(raw);
+        else cudaGetLastError();
+        strncpy(out[i].name, nm.c_str(), sizeof(out[i].name) - 1);
+        out[i].ms = e.second.first;
+        out[i].launches = e.second.second;
+    }
+    if (cap) ctx->kernel_ms.clear();
     return TM_OK;
 }
 

@@ -280,13 +280,12 @@ static int rs_pass(tm_ctx *ctx, const RsJobs &in, int nsets, int np, uint32_t n,
     launch(ctx, k_rs_count, nblk, OS_THREADS, in, n, sh, pb, ntiles, counts);
     int rc = exclusive_scan_u32(ctx, counts, counts, ncount, nullptr);
     if (rc) return rc;
-    ++ctx->kernel_launches;
     if (np == 0)
-        k_rs_scatter<0><<<nblk, OS_THREADS, os_smem(0), st>>>(in, n, sh, pb, ntiles, counts);
+        launch_smem(ctx, k_rs_scatter<0>, nblk, OS_THREADS, os_smem(0), in, n, sh, pb, ntiles, (const uint32_t *)counts);
     else if (np == 1)
-        k_rs_scatter<1><<<nblk, OS_THREADS, os_smem(1), st>>>(in, n, sh, pb, ntiles, counts);
+        launch_smem(ctx, k_rs_scatter<1>, nblk, OS_THREADS, os_smem(1), in, n, sh, pb, ntiles, (const uint32_t *)counts);
     else
-        k_rs_scatter<2><<<nblk, OS_THREADS, os_smem(2), st>>>(in, n, sh, pb, ntiles, counts);
+        launch_smem(ctx, k_rs_scatter<2>, nblk, OS_THREADS, os_smem(2), in, n, sh, pb, ntiles, (const uint32_t *)counts);
     return check_cuda(ctx, cudaGetLastError(), "radix pass");
 }
 
@@ -772,7 +771,8 @@ int build_csr(tm_ctx *ctx)
     uint64_t m1 = m0 - hs.nself;
     if (m1 >= 0xFFFFFFFFull) return set_err(ctx, TM_E_LIMIT, "more than 2^32-2 edges");
     long long tmin = m1 ? hs.tmin : 0, tmax = m1 ? hs.tmax : 0;
-    if ((unsigned long long)(tmax - tmin) >= 0xFFFFFFFFull)
+    // the span as an unsigned difference: no signed overflow at the int64 extremes
+    if ((unsigned long long)tmax - (unsigned long long)tmin >= 0xFFFFFFFFull)
         return set_err(ctx, TM_E_LIMIT, "time span t_max - t_min must be below 2^32 - 1");
     uint32_t m = (uint32_t)m1;
     // ---- compact to (t', src, dst)
@@ -809,7 +809,7 @@ int build_csr(tm_ctx *ctx)
     sec.reset();
     sec.reset(new PhaseScope(ctx, TM_PH_CSR_GLOBAL));
     int vbits = bits_for(n ? n - 1 : 0);
-    int tbits = bits_for((uint64_t)(tmax - tmin));
+    int tbits = bits_for((unsigned long long)tmax - (unsigned long long)tmin);
     {
         RsTo ts{T0, S0, D0, g.g_t, g.g_src, g.g_dst};
         rc = radix_sort_sets_to(ctx, &ts, 1, m, tbits);
@@ -865,7 +865,7 @@ int build_csr(tm_ctx *ctx)
     }
     g.m = m;
     g.tmin = tmin;
-    g.T = (uint32_t)(tmax - tmin);
+    g.T = (uint32_t)((unsigned long long)tmax - (unsigned long long)tmin);
     // S0/D0/T0 are reused below as work space
     // ---- OUT and IN orders: stable sorts of gid by src and by dst, run as
     // one two-array sort; the sorted keys are out_src and in_dst themselves

@@ -1248,7 +1248,7 @@ int run_batch_items(tm_ctx *ctx, const BatchItem *items, uint32_t n, uint32_t ti
         bool empty = (mo->W.lo == 0 && mo->W.hi == 0);
         uint64_t cnt = empty ? 0 : items[q].count;
         base[q] = (uint32_t)total;
-        total += (cnt + tile - 1) / tile;
+        total += cnt / tile + (cnt % tile != 0 ? 1 : 0);   // no wrap for k near 2^64
         if (total >= 0xFFFFFFF0ull) return set_err(ctx, TM_E_LIMIT, "too many sample tiles in one batch");
         hq[q].plan = mo->plan;
         hq[q].seed = items[q].seed;

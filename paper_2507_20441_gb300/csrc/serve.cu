@@ -16,7 +16,9 @@
 // Every query draws samples 0..k-1 from its own counter-based streams and the
 // sums of a query's rounds are exact integers, so a result does not depend on
 // which other queries it shared rounds with: it equals tm_sample on the
-// query's default tree with the same k and seed.
+// query's plan (its default tree, or the tree, root and constraint settings
+// of a motif handle submitted with tm_serve_submit_motif) with the same k and
+// seed.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -38,12 +40,22 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Back-off when device memory runs out: attempts and the wait between them.
+constexpr int kNoMemRetries = 200;
+constexpr int kNoMemWaitMs = 20;
+
 struct Request {
     uint64_t ticket = 0;
     std::string key;
     uint32_t nv = 0, ne = 0;
     std::vector<uint32_t> edges, order;
     int64_t delta = 0;
+    // a pinned plan (tm_serve_submit_motif): tree edges, root and constraint
+    // flags to apply after tm_set_motif; pinned = false keeps the default
+    bool pinned = false;
+    std::vector<uint32_t> tree;
+    uint32_t root = 0;
+    int cflags = TM_C2 | TM_C3;
     uint64_t k = 0, seed = 0;
     Clock::time_point t_submit;
     // progress
@@ -81,6 +93,7 @@ struct Server {
     std::thread admit_thr, sched_thr;
     // statistics
     uint64_t submitted = 0, completed = 0, failed = 0, hits = 0, misses = 0, evictions = 0, rounds = 0;
+    uint64_t admit_retries = 0, round_retries = 0;   // back-offs after TM_E_NOMEM
     std::vector<double> latencies;
     Clock::time_point t_first_submit, t_last_done;
     bool any_submit = false;
@@ -160,6 +173,11 @@ void admit_loop(Server *S)
         lk.unlock();
         tm_motif *mo = nullptr;
         int rc = tm_set_motif(S->shadow, r->nv, r->ne, r->edges.data(), r->order.data(), r->delta, &mo);
+        if (!rc && r->pinned) {
+            rc = tm_set_tree(mo, r->tree.data(), r->root);
+            if (!rc) rc = tm_set_constraints(mo, r->cflags);
+            if (rc) { tm_motif_free(mo); mo = nullptr; }
+        }
         lk.lock();
         if (rc) {
             S->pending.pop_front();
@@ -193,6 +211,30 @@ void admit_loop(Server *S)
         tm_u128 W;
         rc = tm_weights(S->shadow, mo, &W);
         lk.lock();
+        // out of device memory: free the cached weights that no query holds,
+        // wait for the queries in flight to release theirs, and try again a
+        // bounded number of times before the query fails with TM_E_NOMEM
+        for (int attempt = 0; rc == TM_E_NOMEM && attempt < kNoMemRetries && !S->stop; ++attempt) {
+            S->admit_retries++;
+            std::vector<tm_motif *> freed;
+            for (auto c = S->cache.begin(); c != S->cache.end();) {
+                if (c->second.refs == 0) {
+                    freed.push_back(c->second.mo);
+                    S->resident -= c->second.bytes;
+                    S->evictions++;
+                    c = S->cache.erase(c);
+                } else {
+                    ++c;
+                }
+            }
+            lk.unlock();
+            for (tm_motif *vm : freed) tm_motif_free(vm);
+            lk.lock();
+            S->cv_admit.wait_for(lk, std::chrono::milliseconds(kNoMemWaitMs));
+            lk.unlock();
+            rc = tm_weights(S->shadow, mo, &W);
+            lk.lock();
+        }
         S->pending.pop_front();
         if (rc) {
             r->rc = rc;
@@ -249,6 +291,18 @@ void sched_loop(Server *S)
         lk.unlock();
         int rc = run_batch_items(ctx, items.data(), (uint32_t)items.size(), tile, accs.data(),
                                  S->cfg.poll_timeout_ms);
+        // a round that could not get its scratch memory ran nothing: back off
+        // and run the same round again (bounded)
+        for (int attempt = 0; rc == TM_E_NOMEM && attempt < kNoMemRetries; ++attempt) {
+            {
+                std::lock_guard<std::mutex> g(S->mu);
+                S->round_retries++;
+                if (S->stop) break;
+            }
+            std::this_thread::sleep_for(std::chrono::milliseconds(kNoMemWaitMs));
+            accs.assign(items.size(), SampleAcc{0, 0, 0, 0, 0, 0});
+            rc = run_batch_items(ctx, items.data(), (uint32_t)items.size(), tile, accs.data(), S->cfg.poll_timeout_ms);
+        }
         lk.lock();
         S->rounds++;
         std::vector<Request *> still;
@@ -310,6 +364,20 @@ int tm_serve_start(tm_ctx *ctx, const tm_serve_cfg *cfg)
     return TM_OK;
 }
 
+static int queue_request(Server *S, Request *r, uint64_t *ticket)
+{
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) { delete r; return TM_E_STATE; }
+    r->ticket = S->next_ticket++;
+    r->t_submit = Clock::now();
+    if (!S->any_submit) { S->any_submit = true; S->t_first_submit = r->t_submit; }
+    S->submitted++;
+    *ticket = r->ticket;
+    S->pending.push_back(r);
+    S->cv_admit.notify_all();
+    return TM_OK;
+}
+
 int tm_serve_submit(tm_ctx *ctx, uint32_t nv, uint32_t ne, const uint32_t *edges, const uint32_t *order, int64_t delta,
                     uint64_t k, uint64_t seed, uint64_t *ticket)
 {
@@ -325,16 +393,35 @@ int tm_serve_submit(tm_ctx *ctx, uint32_t nv, uint32_t ne, const uint32_t *edges
     r->k = k;
     r->seed = seed;
     r->key = make_key(nv, ne, edges, order, delta);
-    std::lock_guard<std::mutex> lk(S->mu);
-    if (S->stop) { delete r; return TM_E_STATE; }
-    r->ticket = S->next_ticket++;
-    r->t_submit = Clock::now();
-    if (!S->any_submit) { S->any_submit = true; S->t_first_submit = r->t_submit; }
-    S->submitted++;
-    *ticket = r->ticket;
-    S->pending.push_back(r);
-    S->cv_admit.notify_all();
-    return TM_OK;
+    return queue_request(S, r, ticket);
+}
+
+int tm_serve_submit_motif(tm_ctx *ctx, const tm_motif *mo, uint64_t k, uint64_t seed, uint64_t *ticket)
+{
+    if (!ctx || !mo || !ticket) return TM_E_ARG;
+    Server *S = ctx->server;
+    if (!S) return TM_E_STATE;
+    if (mo->ctx != ctx) return TM_E_ARG;
+    Request *r = new Request();
+    r->nv = mo->nv; r->ne = mo->ne;
+    for (uint32_t i = 0; i < mo->ne; ++i) {
+        r->edges.push_back(mo->ea[i]);
+        r->edges.push_back(mo->eb[i]);
+        r->order.push_back(mo->rank[i]);
+    }
+    r->delta = mo->delta;
+    r->pinned = true;
+    r->tree.assign(mo->tree, mo->tree + (mo->nv - 1));
+    r->root = mo->root;
+    r->cflags = (mo->plan.c2 ? TM_C2 : 0) | (mo->plan.wdelta == mo->plan.delta ? TM_C3 : 0);
+    r->k = k;
+    r->seed = seed;
+    // the cache key names the plan: motif, tree, root and constraint flags
+    std::string key = make_key(r->nv, r->ne, r->edges.data(), r->order.data(), r->delta) + "|tree:";
+    for (uint32_t e : r->tree) key += std::to_string(e) + ",";
+    key += "root:" + std::to_string(r->root) + "|c:" + std::to_string(r->cflags);
+    r->key = key;
+    return queue_request(S, r, ticket);
 }
 
 int tm_serve_poll(tm_ctx *ctx, uint64_t ticket, tm_result *out, int timeout_ms)
@@ -374,6 +461,7 @@ int tm_serve_stats(tm_ctx *ctx, tm_serve_stats_t *out)
     out->resident_bytes = S->resident;
     out->waiting = S->pending.size() + S->ready.size();
     out->active = S->active.size();
+    out->nomem_retries = S->admit_retries + S->round_retries;
     std::vector<double> l = S->latencies;
     std::sort(l.begin(), l.end());
     if (!l.empty()) {

@@ -170,6 +170,10 @@ struct tm_ctx {
     void *pinned_acc = nullptr;                // staging for batched sums (device -> host)
     size_t pinned_acc_bytes = 0;
     uint64_t phase_launches[TM_NUM_PHASES] = {};
+    // per-kernel timing (cfg.profile >= 2): an event pair around every launch
+    struct PendingKernel { const void *fn; cudaEvent_t a, b; };
+    std::vector<PendingKernel> pending_k;
+    std::vector<std::pair<const void *, std::pair<double, uint64_t>>> kernel_ms;   // fn -> (ms, launches)
 };
 
 namespace timest {
@@ -249,13 +253,33 @@ struct PhaseScope {
     ~PhaseScope();
 };
 
-// Every kernel of the library is launched through here (counted per context).
+// Per-kernel timing of one launch (cfg.profile >= 2): events recorded on the
+// context stream before and after it; folded in by prof_collect().
+struct KernelTimer {
+    tm_ctx *ctx;
+    const void *fn;
+    cudaEvent_t a = nullptr;
+    KernelTimer(tm_ctx *c, const void *f);
+    ~KernelTimer();
+};
+
+// Every kernel of the library is launched through here (counted per context,
+// timed per kernel when cfg.profile >= 2).
 #ifdef __CUDACC__
 template <typename... KArgs, typename... Args>
 inline void launch(tm_ctx *ctx, void (*kernel)(KArgs...), dim3 grid, dim3 block, Args &&...args)
 {
     ++ctx->kernel_launches;
+    KernelTimer kt(ctx, (const void *)kernel);
     kernel<<<grid, block, 0, ctx->stream>>>(static_cast<KArgs>(args)...);
+}
+// The same with dynamic shared memory.
+template <typename... KArgs, typename... Args>
+inline void launch_smem(tm_ctx *ctx, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, Args &&...args)
+{
+    ++ctx->kernel_launches;
+    KernelTimer kt(ctx, (const void *)kernel);
+    kernel<<<grid, block, smem, ctx->stream>>>(static_cast<KArgs>(args)...);
 }
 #endif
 void prof_collect(tm_ctx *ctx);   // call after the stream is synchronized

@@ -32,3 +32,15 @@ class combine:
     def from_limbs(limbs):
         h = sum(int(x) << (combine.LIMB_BITS * i) for i, x in enumerate(limbs[:combine.LIMBS]))
         return (h,) + tuple(int(x) for x in limbs[combine.LIMBS:])
+
+
+def all_reduce_counts(hits2: int, valid: int, rej_vertex: int, rej_delta: int, rej_order: int, device=None):
+    """One integer all-reduce (torch.distributed, the default group) of a
+    rank's hits2 and counters; returns the sums over all ranks as
+    (hits2, valid, rej_vertex, rej_delta, rej_order)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(combine.to_limbs(hits2, valid, rej_vertex, rej_delta, rej_order), dtype=torch.int64,
+                     device=device)
+    dist.all_reduce(t)
+    return combine.from_limbs(t.tolist())

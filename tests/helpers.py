@@ -53,3 +53,30 @@ SMALL_MOTIFS = {
     "antiparallel": (3, [(0, 1), (1, 0), (1, 2)], [1, 0, 2]),
     "parallel": (3, [(0, 1), (1, 2), (0, 1)], [0, 1, 2]),
 }
+
+
+def default_tree(nv, edges, rank):
+    """The spanning tree and root edge tm_set_motif picks by default, worked
+    out on the host from its documented rule (bench.reference_tree; checked
+    against the library's ranking for 42 motifs by test_bench_contract), so
+    the oracle can run the same plan without taking it from the CUDA path."""
+    import types
+    import bench
+    return bench.reference_tree(types.SimpleNamespace(nv=nv, edges=[tuple(e) for e in edges], rank=list(rank)))
+
+
+def oracle_result(G, nv, edges, rank, delta, tree, root, k, seed, first=0, c2=True, c3=True):
+    """The oracle's TIMEST (Alg. 3-6) on one plan: (W, hits2, valid,
+    rej_vertex, rej_delta, rej_order) of samples first .. first+k-1."""
+    G.set_motif(nv, [tuple(e) for e in edges], list(rank), delta, list(tree), root)
+    if not (c2 and c3):
+        G.set_constraints(c2, c3)
+    W = G.weights()
+    if W == 0 or k == 0:
+        return (W, 0, 0, 0, 0, 0)
+    r = G.sample(k, seed, first, threads=0)
+    return (W, r.hits2, r.valid, r.rej_vertex, r.rej_delta, r.rej_order)
+
+
+def result_tuple(r):
+    return (r.W, r.hits2, r.valid, r.rej_vertex, r.rej_delta, r.rej_order)

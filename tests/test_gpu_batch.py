@@ -1,7 +1,10 @@
 """Batched estimation (many (motif, delta, k) queries in one persistent
-launch): every query's result is bit-identical to its own tm_sample call,
-for uneven sample counts, any tile size, k = 0 and motifs with W = 0."""
+launch): every query's result is bit-identical to the CPU oracle's TIMEST
+(Alg. 3-6) on the same tree, k and seed, and to its own tm_sample call, for
+uneven sample counts, any tile size, k = 0 and motifs with W = 0."""
 import pytest
+
+from helpers import default_tree, oracle_result, result_tuple
 
 pytestmark = pytest.mark.gpu
 
@@ -45,6 +48,34 @@ def test_batch_equals_separate_runs(pool, tile):
         assert (r.W, r.hits2, r.k, r.valid, r.rej_vertex, r.rej_delta, r.rej_order) == \
                (ref.W, ref.hits2, ref.k, ref.valid, ref.rej_vertex, ref.rej_delta, ref.rej_order), mo.name
         assert r.estimate == ref.estimate
+    ctx.close()
+
+
+def test_batch_equals_oracle(pool, oracle_mod):
+    """Each of 32 queries (3-7 vertices, three deltas, k from 1e3 to 2e5) of
+    one batched launch against the oracle on the default tree: W, hits2 and
+    the four counters bit for bit (Alg. 6 per query)."""
+    import paper_2507_20441_gb300 as tg
+    gr = _graph()
+    ctx = _context(tg, 1000)
+    G = oracle_mod.Graph(gr.n, gr.src, gr.dst, gr.t)
+    motifs = []
+    for mo in pool:
+        m = ctx.motif(mo.nv, mo.edges, mo.rank, mo.delta)
+        m.weights()
+        motifs.append(m)
+    ks = [mo.k for mo in pool]
+    seeds = [300 + i for i in range(len(pool))]
+    res = ctx.batch_run(motifs, ks, seeds)
+    nonzero = 0
+    for mo, k, s, r in zip(pool, ks, seeds, res):
+        tree, root = default_tree(mo.nv, mo.edges, mo.rank)
+        want = oracle_result(G, mo.nv, mo.edges, mo.rank, mo.delta, tree, root, k, s)
+        assert result_tuple(r) == want, mo.name
+        assert r.k == k
+        nonzero += want[1] > 0
+    assert nonzero >= 8                              # the comparison is not vacuous
+    G.close()
     ctx.close()
 
 

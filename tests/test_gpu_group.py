@@ -1,11 +1,14 @@
 """Several motifs per sampling run: motifs whose spanning trees are the same
 temporal pattern (here the path 0->1->2->3 rooted at its middle edge, with the
 path edges in the same pi order) share one weight pass and one stream of
-sampled trees; each motif's result equals its own tm_sample bit for bit."""
+sampled trees; each motif's result equals the CPU oracle's TIMEST on that
+motif with the same tree, k, seed and first sample id (Alg. 6 per motif, as
+the paper counts the 4-vertex motifs of one table from one run) and its own
+tm_sample, bit for bit."""
 import numpy as np
 import pytest
 
-from helpers import small_random_graph
+from helpers import oracle_result, result_tuple, small_random_graph
 
 pytestmark = pytest.mark.gpu
 
@@ -34,7 +37,7 @@ def _same(a, b):
 
 
 @pytest.mark.parametrize("kind", ["dense", "chung_lu"])
-def test_group_equals_separate_runs(kind):
+def test_group_equals_separate_runs(kind, oracle_mod):
     import paper_2507_20441_gb300 as tg
     tg.build()
     if kind == "dense":
@@ -50,12 +53,16 @@ def test_group_equals_separate_runs(kind):
     ms = _motifs(ctx, delta)
     Ws = [m.weights() for m in ms]
     assert len(set(Ws)) == 1                      # one tree pattern, one W
+    G = oracle_mod.Graph(n, s, d, t)
     for first in (0, 12_345):
         single = [m.sample(k, 9, first) for m in ms]
         group = ctx.sample_group(ms, k, 9, first)
-        for a, b in zip(group, single):
+        for (extra, order), a, b in zip(GROUP, group, single):
             assert _same(a, b)
+            want = oracle_result(G, 4, PATH + extra, order, delta, [0, 1, 2], 1, k, 9, first)
+            assert result_tuple(a) == want, (extra, order, first)
     assert any(r.hits2 for r in single)           # the case is not vacuous
+    G.close()
     ctx.close()
 
 

@@ -1,7 +1,8 @@
 """Motif listing: every valid sample's listed instances are exactly the
 M-matches (Def. 1.2) whose tree edges are the sampled tree, recomputed here by
-brute force over the graph (edge ids in GLOBAL order); rejected samples list
-nothing; a truncated listing is a prefix of the full one."""
+brute force over the graph (edge ids in GLOBAL order), whose total equals the
+oracle's exact count O1 on the same graph; rejected samples list nothing; a
+truncated listing is a prefix of the full one."""
 from collections import defaultdict
 
 import numpy as np
@@ -69,7 +70,7 @@ CASES = [("triangle", 12), ("cycle4", 15), ("cycle5_chord", 30), ("bowtie", 20),
 
 
 @pytest.mark.parametrize("name,delta", CASES)
-def test_listing_matches_brute_force(name, delta):
+def test_listing_matches_brute_force(name, delta, oracle_mod):
     import paper_2507_20441_gb300 as tg
     tg.build()
     nv, edges, order = SMALL_MOTIFS[name]
@@ -84,6 +85,8 @@ def test_listing_matches_brute_force(name, delta):
     res, gids, contrib, reason = m.sample_trace(k, seed)
     rows, sids, total = m.sample_list(k, seed)
     matches = all_matches(gs, gd, gt, edges, order, delta)
+    # the enumerator written here agrees with the oracle's exact count (O1)
+    assert len(matches) == oracle_mod.Graph(n, s, d, t).brute_count(nv, edges, order, delta)
     by_tree = defaultdict(list)
     for mt in matches:
         by_tree[tuple(mt[e] for e in tree_order)].append(mt)

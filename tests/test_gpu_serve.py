@@ -1,13 +1,16 @@
 """Serving (continuous batching): queries submitted concurrently from several
 threads, admitted under a weight-memory budget and sampled in shared rounds,
 give exactly the result each gives alone (tm_sample on its default tree with
-the same k and seed); weights are cached and reused, evicted when the budget
-demands it; waits are bounded."""
+the same k and seed) and the CPU oracle's TIMEST on that tree (Alg. 3-6);
+weights are cached and reused, evicted when the budget demands it; waits are
+bounded."""
 import threading
 import time
 
 import numpy as np
 import pytest
+
+from helpers import default_tree, oracle_result, result_tuple
 
 pytestmark = pytest.mark.gpu
 
@@ -44,6 +47,21 @@ def _alone(ctx, queries):
     return ref
 
 
+def _oracle_check(gr, queries, served, oracle_mod, every=1):
+    """Served results against the oracle on the default tree, samples 0..k-1."""
+    G = oracle_mod.Graph(gr.n, gr.src, gr.dst, gr.t)
+    checked = 0
+    for i, ((mo, k, seed), r) in enumerate(zip(queries, served)):
+        if i % every:
+            continue
+        tree, root = default_tree(mo.nv, mo.edges, mo.rank)
+        want = oracle_result(G, mo.nv, mo.edges, mo.rank, mo.delta, tree, root, k, seed)
+        assert result_tuple(r) == want, (i, mo.name, k, seed)
+        checked += 1
+    G.close()
+    return checked
+
+
 def _serve_all(ctx, queries, threads=4):
     tickets = [None] * len(queries)
 
@@ -72,7 +90,7 @@ def _same(a, b):
            (b.W, b.hits2, b.k, b.valid, b.rej_vertex, b.rej_delta, b.rej_order)
 
 
-def test_results_in_the_mix_equal_results_alone():
+def test_results_in_the_mix_equal_results_alone(oracle_mod):
     import paper_2507_20441_gb300 as tg
     tg.build()
     gr = _graph()
@@ -92,9 +110,10 @@ def test_results_in_the_mix_equal_results_alone():
         assert _same(a, b), (mo.name, k, seed)
         assert a.estimate == b.estimate
     ctx.close()
+    assert _oracle_check(gr, queries, served, oracle_mod) == 40
 
 
-def test_memory_gated_admission_evicts_and_stays_exact():
+def test_memory_gated_admission_evicts_and_stays_exact(oracle_mod):
     import paper_2507_20441_gb300 as tg
     gr = _graph()
     ctx = tg.Context()
@@ -112,6 +131,7 @@ def test_memory_gated_admission_evicts_and_stays_exact():
     for a, b in zip(served, ref):
         assert _same(a, b)
     ctx.close()
+    assert _oracle_check(gr, queries, served, oracle_mod, every=3) == 8
 
 
 def test_poll_is_bounded_and_timeouts_leave_the_context_usable():
@@ -142,4 +162,42 @@ def test_poll_is_bounded_and_timeouts_leave_the_context_usable():
     assert _same(got, m.sample(50_000, 4))
     with pytest.raises(tg.TimestError):
         ctx.poll(1, timeout_ms=0)          # not serving any more
+    ctx.close()
+
+
+def test_submit_motif_serves_the_pinned_plan(oracle_mod):
+    """tm_serve_submit_motif serves a motif handle's own plan: a pinned
+    non-default tree and root, and constraint settings, served in the mix with
+    default-plan queries of the same motif; each result equals tm_sample on its
+    plan and the oracle on the same tree, root and constraints."""
+    import paper_2507_20441_gb300 as tg
+    from helpers import spanning_trees
+    gr = _graph()
+    ctx = tg.Context()
+    ctx.load_graph(gr.n, gr.src, gr.dst, gr.t)
+    nv, edges, rank, delta = 4, [(0, 1), (1, 2), (2, 3), (3, 0)], [0, 1, 2, 3], 86_400
+    dtree, droot = default_tree(nv, edges, rank)
+    other = [t for t in spanning_trees(nv, edges) if sorted(t) != sorted(dtree)][0]
+    plans = [(other, other[0], True, True), (other, other[-1], False, True), (dtree, droot, True, False),
+             (dtree, droot, True, True)]
+    motifs = [ctx.motif(nv, edges, rank, delta).set_tree(t, r).set_constraints(c2, c3) for t, r, c2, c3 in plans]
+    ks = [150_000, 90_000, 120_000, 60_000]
+    ctx.serve_start(max_active=8, tile=2048)
+    tickets = [ctx.submit_motif(m, k, 40 + i) for i, (m, k) in enumerate(zip(motifs, ks))]
+    tickets.append(ctx.submit(nv, edges, rank, delta, 70_000, 99))      # default plan, same motif
+    served = [ctx.poll(t, timeout_ms=120_000) for t in tickets]
+    st = ctx.serve_stats()
+    ctx.serve_stop()
+    assert st["completed"] == 5 and st["failed"] == 0
+    assert st["cache_misses"] == 5        # one weight pass per distinct plan
+    G = oracle_mod.Graph(gr.n, gr.src, gr.dst, gr.t)
+    for i, ((t, r, c2, c3), m, k) in enumerate(zip(plans, motifs, ks)):
+        m.weights()
+        alone = m.sample(k, 40 + i)
+        assert _same(served[i], alone), i
+        want = oracle_result(G, nv, edges, rank, delta, t, r, k, 40 + i, c2=c2, c3=c3)
+        assert result_tuple(served[i]) == want, i
+    want = oracle_result(G, nv, edges, rank, delta, dtree, droot, 70_000, 99)
+    assert result_tuple(served[4]) == want
+    G.close()
     ctx.close()

@@ -1,8 +1,9 @@
 """The multi-GPU layout on CPU: samples are independent units, so N ranks
 each drawing a disjoint range of sample ids (tm_sample's first_index) and
 adding their integer sums reproduce one run exactly.  Two gloo ranks run the
-CPU oracle over their shares and all-reduce hits2 and the counters as the
-bench's sharding does; the sum equals the single-process result."""
+CPU oracle over their shares and combine hits2 and the counters through the
+same function bench.py's torchrun path calls (bench.combine_across_ranks, one
+integer all-reduce); the sum equals the single-process result."""
 import os
 import socket
 
@@ -34,11 +35,55 @@ def _rank(rank, world, port, out):
     k = 30_001
     first, cnt = sample_range(rank, world, k)
     r = G.sample(cnt, 5, first)
+    import bench
+    out[rank] = tuple(bench.combine_across_ranks(r))      # the bench's own combine step
+    # the same sums through the limb encoding directly
     limbs = torch.tensor(combine.to_limbs(r.hits2, r.valid, r.rej_vertex, r.rej_delta, r.rej_order), dtype=torch.int64)
     dist.all_reduce(limbs)
-    hits2, valid, rv, rd, ro = combine.from_limbs(limbs.tolist())
-    out[rank] = (hits2, valid, rv, rd, ro)
+    assert combine.from_limbs(limbs.tolist()) == out[rank]
     dist.destroy_process_group()
+
+
+def _bench_layout_rank(rank, world, port, out):
+    """bench.py's per-step id layout: rank r of N draws k ids from (i N + r) k."""
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    import oracle
+    from helpers import small_random_graph
+    n, s, d, t = small_random_graph(33, n=9, m=500, t_hi=150)
+    G = oracle.Graph(n, s, d, t)
+    G.set_motif(3, [(0, 1), (1, 2), (2, 0)], [0, 1, 2], 30, [0, 1], 1)
+    G.weights()
+    k, step = 7_001, 3
+    r = G.sample(k, 11, (step * world + rank) * k)
+    out[rank] = tuple(bench.combine_across_ranks(r))
+    dist.destroy_process_group()
+
+
+def test_bench_rank_layout_covers_one_contiguous_range():
+    import multiprocessing as mp
+    import oracle
+    from helpers import small_random_graph
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_bench_layout_rank, args=(r, 3, port, out)) for r in range(3)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+        assert p.exitcode == 0
+    n, s, d, t = small_random_graph(33, n=9, m=500, t_hi=150)
+    G = oracle.Graph(n, s, d, t)
+    G.set_motif(3, [(0, 1), (1, 2), (2, 0)], [0, 1, 2], 30, [0, 1], 1)
+    G.weights()
+    whole = G.sample(3 * 7_001, 11, 3 * 3 * 7_001)
+    assert whole.valid > 0
+    for r in range(3):
+        assert out[r] == (whole.hits2, whole.valid, whole.rej_vertex, whole.rej_delta, whole.rej_order)
 
 
 def test_two_gloo_ranks_equal_one_run():
