@@ -347,12 +347,13 @@ __device__ __forceinline__ int sample_child(const DevGraph &g, const DevPlan &P,
     if (leaf) {
         total = (uint64_t)(b - a) - (uint64_t)(eb - ea);
     } else {
-        Pd = p ? J.pref_dir1[slot] : J.pref_dir0[slot];
-        Pm = p ? J.pref_multi1[slot] : J.pref_multi0[slot];
-        base = (a > beg && (uint64_t)__ldg(tarr + a - 1) >= wlo) ? __ldg(Pd + a - 1) : 0;
-        base_m = (ea > pb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo) ? __ldg(Pm + ea - 1) : 0;
-        const uint64_t sr = b > a ? __ldg(Pd + b - 1) - base : 0;
-        const uint64_t se = eb > ea ? __ldg(Pm + eb - 1) - base_m : 0;
+        // layer p's lane of the slot's (layer 0, layer 1) prefix pairs
+        Pd = (const uint64_t *)J.pref_dir[slot] + p;
+        Pm = (const uint64_t *)J.pref_multi[slot] + p;
+        base = (a > beg && (uint64_t)__ldg(tarr + a - 1) >= wlo) ? __ldg(Pd + 2 * (size_t)(a - 1)) : 0;
+        base_m = (ea > pb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo) ? __ldg(Pm + 2 * (size_t)(ea - 1)) : 0;
+        const uint64_t sr = b > a ? __ldg(Pd + 2 * (size_t)(b - 1)) - base : 0;
+        const uint64_t se = eb > ea ? __ldg(Pm + 2 * (size_t)(eb - 1)) - base_m : 0;
         total = sr - se;
     }
     if (total == 0 || b <= a) { latch(status, ST_BADSTATE); return -1; }
@@ -367,7 +368,7 @@ __device__ __forceinline__ int sample_child(const DevGraph &g, const DevPlan &P,
         else
             while (xl < xh) {
                 const uint32_t x = xl + ((xh - xl) >> 1);
-                if (__ldg(Pd + x) - base > rc) xh = x; else xl = x + 1;
+                if (__ldg(Pd + 2 * (size_t)x) - base > rc) xh = x; else xl = x + 1;
             }
     } else {
         while (xl < xh) {
@@ -380,7 +381,7 @@ __device__ __forceinline__ int sample_child(const DevGraph &g, const DevPlan &P,
             if (ea + ce < eb && __ldg(g.multi_t + ea + ce) == tx && og <= __ldg(nbr + x)) ++ce;
             uint64_t F;
             if (leaf) F = (uint64_t)(x - a + 1) - ce;
-            else F = (__ldg(Pd + x) - base) - (ce ? __ldg(Pm + ea + ce - 1) - base_m : 0);
+            else F = (__ldg(Pd + 2 * (size_t)x) - base) - (ce ? __ldg(Pm + 2 * (size_t)(ea + ce - 1)) - base_m : 0);
             if (F > rc) xh = x; else xl = x + 1;
         }
     }
@@ -955,8 +956,8 @@ void fill_job(tm_motif *mo, SampleJob &J, const DevPlan *dplan)
     J.win_goff0 = mo->layer[0].win_goff; J.win_goff1 = mo->layer[1].win_goff;
     J.guide0 = mo->layer[0].guide; J.guide1 = mo->layer[1].guide;
     for (int s = 0; s < kMaxTree; ++s) {
-        J.pref_dir0[s] = mo->layer[0].pref_dir[s]; J.pref_dir1[s] = mo->layer[1].pref_dir[s];
-        J.pref_multi0[s] = mo->layer[0].pref_multi[s]; J.pref_multi1[s] = mo->layer[1].pref_multi[s];
+        J.pref_dir[s] = mo->pref_dir[s];
+        J.pref_multi[s] = mo->pref_multi[s];
     }
     J.W_lo = mo->W.lo;
     J.W_hi = mo->W.hi;

@@ -435,7 +435,7 @@ __global__ void k_segscan2_carries(SegAgg2 *__restrict__ aggs, uint64_t ntiles, 
 template <class F>
 __global__ void __launch_bounds__(SCAN_THREADS, TM_SCAN2_MINB) k_segscan2_final(F f, uint64_t n, const SegAgg2 *__restrict__ carries,
                                  const ulonglong2 *__restrict__ stash, uint64_t *__restrict__ out0,
-                                 uint64_t *__restrict__ out1, uint32_t *status)
+                                 uint64_t *__restrict__ out1, ulonglong2 *__restrict__ outp, uint32_t *status)
 {
     __shared__ SegAgg2 warp_agg[SCAN_THREADS / 32];
     const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
@@ -483,26 +483,35 @@ __global__ void __launch_bounds__(SCAN_THREADS, TM_SCAN2_MINB) k_segscan2_final(
             const uint32_t h = (hbits >> (2 * j)) & 3u;
             r0 = (h & 1u) ? v[j].x : add_chk(r0, v[j].x, ovf);
             r1 = (h & 2u) ? v[j].y : add_chk(r1, v[j].y, ovf);
-            out0[i] = r0;
-            out1[i] = r1;
+            if (outp) {
+                outp[i] = make_ulonglong2(r0, r1);
+            } else {
+                out0[i] = r0;
+                out1[i] = r1;
+            }
         }
     }
     if (ovf) latch(status, ST_OVERFLOW);
 }
 
+// Outputs: out0 / out1 (one array per layer), or outp (the (layer 0,
+// layer 1) pairs interleaved) when it is non-null.  A gathering functor's
+// values are stashed in scan order; with `keep` non-null the stash is that
+// caller-owned array (n pairs), which then holds the gathered values.
 template <class F>
-int segmented_scan2_u64(tm_ctx *ctx, const F &f, uint64_t n, uint64_t *out0, uint64_t *out1)
+int segmented_scan2_u64(tm_ctx *ctx, const F &f, uint64_t n, uint64_t *out0, uint64_t *out1,
+                        ulonglong2 *outp = nullptr, ulonglong2 *keep = nullptr)
 {
     if (n == 0) return TM_OK;
     const uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     ScratchScope scope(ctx);
     SegAgg2 *aggs = (SegAgg2 *)salloc(ctx, tiles * sizeof(SegAgg2));
-    ulonglong2 *stash = F::kGathered ? (ulonglong2 *)salloc(ctx, n * sizeof(ulonglong2)) : nullptr;
+    ulonglong2 *stash = !F::kGathered ? nullptr : keep ? keep : (ulonglong2 *)salloc(ctx, n * sizeof(ulonglong2));
     if (!aggs || (F::kGathered && !stash)) return TM_E_NOMEM;
     launch(ctx, k_segscan2_reduce<F>, (unsigned)tiles, SCAN_THREADS, f, n, aggs, stash, ctx->status);
     launch(ctx, k_segscan2_carries, 1, 1024, aggs, tiles, ctx->status);
     launch(ctx, k_segscan2_final<F>, (unsigned)tiles, SCAN_THREADS, f, n, aggs, (const ulonglong2 *)stash, out0,
-           out1, ctx->status);
+           out1, outp, ctx->status);
     return check_cuda(ctx, cudaGetLastError(), "segmented scan");
 }
 

@@ -151,24 +151,35 @@ void finish_locked(Server *S, Request *r)
     S->cv_admit.notify_all();
 }
 
+// A request whose weights are cached joins the ready queue at once (holding
+// a reference to them); false when they are not resident.  Caller holds mu.
+bool admit_cached_locked(Server *S, Request *r)
+{
+    auto it = S->cache.find(r->key);
+    if (it == S->cache.end()) return false;
+    it->second.refs++;
+    it->second.last_use = ++S->use_clock;
+    r->mo = it->second.mo;
+    S->hits++;
+    S->ready.push_back(r);
+    S->cv_sched.notify_all();
+    return true;
+}
+
 void admit_loop(Server *S)
 {
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
         S->cv_admit.wait(lk, [&] { return S->stop || !S->pending.empty(); });
         if (S->stop) return;
-        Request *r = S->pending.front();
-        auto it = S->cache.find(r->key);
-        if (it != S->cache.end()) {
-            it->second.refs++;
-            it->second.last_use = ++S->use_clock;
-            r->mo = it->second.mo;
-            S->hits++;
-            S->pending.pop_front();
-            S->ready.push_back(r);
-            S->cv_sched.notify_all();
-            continue;
+        // queued requests whose weights became resident (an earlier miss of
+        // the same plan) go first: a miss's weight pass blocks no hit
+        for (auto q = S->pending.begin(); q != S->pending.end();) {
+            if (admit_cached_locked(S, *q)) q = S->pending.erase(q);
+            else ++q;
         }
+        if (S->pending.empty()) continue;
+        Request *r = S->pending.front();
         // miss: build the plan, then wait for room under the budget
         lk.unlock();
         tm_motif *mo = nullptr;
@@ -373,6 +384,9 @@ static int queue_request(Server *S, Request *r, uint64_t *ticket)
     if (!S->any_submit) { S->any_submit = true; S->t_first_submit = r->t_submit; }
     S->submitted++;
     *ticket = r->ticket;
+    // weights already resident: straight to the scheduler, so a hit never
+    // waits behind another query's weight pass
+    if (admit_cached_locked(S, r)) return TM_OK;
     S->pending.push_back(r);
     S->cv_admit.notify_all();
     return TM_OK;

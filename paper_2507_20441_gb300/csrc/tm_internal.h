@@ -104,8 +104,6 @@ struct LayerData {
     uint32_t *win_gshift = nullptr;      // [nwin]
     uint32_t *win_goff = nullptr;        // [nwin + 1]
     uint32_t *guide = nullptr;           // [m/4 + 3 nwin + 1]
-    uint64_t *pref_dir[kMaxTree] = {};   // per slot: prefix in the out/in order
-    uint64_t *pref_multi[kMaxTree] = {}; // per slot: prefix in the multi-edge order
 };
 
 struct Server;
@@ -123,6 +121,11 @@ struct tm_motif {
     bool have_weights = false;
     uint64_t graph_epoch = 0;
     timest::LayerData layer[2];
+    // per prefix slot (non-root, non-leaf tree node): the segmented prefix of
+    // its weights in the order its parent scans (out- or in-list) and in the
+    // multi-edge order, as (layer 0, layer 1) pairs per position
+    ulonglong2 *pref_dir[timest::kMaxTree] = {};
+    ulonglong2 *pref_multi[timest::kMaxTree] = {};
     uint64_t *wcum = nullptr;            // [2*(nw0+nw1+1)] u128 window cumulative (lo,hi)
     uint32_t nwtot = 0;
     tm_u128 W{0, 0};
@@ -211,8 +214,8 @@ struct SampleJob {
     const uint32_t *win_beg0, *win_beg1, *win_id0, *win_id1;
     const uint64_t *root_cdf0, *root_cdf1;
     const uint32_t *win_gshift0, *win_gshift1, *win_goff0, *win_goff1, *guide0, *guide1;
-    const uint64_t *pref_dir0[kMaxTree], *pref_dir1[kMaxTree];
-    const uint64_t *pref_multi0[kMaxTree], *pref_multi1[kMaxTree];
+    const ulonglong2 *pref_dir[kMaxTree];     // (layer 0, layer 1) prefix pairs per slot
+    const ulonglong2 *pref_multi[kMaxTree];
     uint64_t W_lo, W_hi;
 };
 int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t first,

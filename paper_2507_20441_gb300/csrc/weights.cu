@@ -27,10 +27,24 @@ namespace {
 constexpr int TB = 256;
 inline unsigned blocks_for(uint64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
+// Prefix arrays of the child nodes: per position the (layer 0, layer 1)
+// prefix pair, so one 16-byte load serves both layers.
 struct ChildPrefix {
-    const uint64_t *pd[2][kMaxTree];   // [layer][slot] prefix in the out/in order
-    const uint64_t *pm[2][kMaxTree];   // [layer][slot] prefix in the multi-edge order
+    const ulonglong2 *pd[kMaxTree];    // [slot] prefix in the out/in order
+    const ulonglong2 *pm[kMaxTree];    // [slot] prefix in the multi-edge order
 };
+
+__device__ __forceinline__ uint64_t lane_of(const ulonglong2 v, int p) { return p ? v.y : v.x; }
+
+// a[i] for a runtime slot i by a chain of selects: indexing a kernel
+// parameter array at a runtime index would copy it to local memory
+__device__ __forceinline__ const ulonglong2 *pick_slot(const ulonglong2 *const (&a)[kMaxTree], int i)
+{
+    const ulonglong2 *v = a[0];
+#pragma unroll
+    for (int s = 1; s < kMaxTree; ++s) v = (i == s) ? a[s] : v;
+    return v;
+}
 
 // Candidate ranges up to this many entries are scanned for the excluded
 // neighbour; longer ones search the excluded multi-edge list instead.
@@ -41,23 +55,28 @@ constexpr uint32_t kScanLimit = 48;
 // matched to q and both layers.  Threads walk the meeting vertex's own list
 // (out-list order for side 0, in-list order for side 1), so the lanes of a
 // warp share the vertex, its candidate lists and nearby positions in them.
-// Each child's range [a, b) is galloped to from the parent edge's position
-// in that list (or its cross rank into the vertex's other list).  The
-// excluded entries of Claim 3.1 are exactly the entries of [a, b) whose other
-// endpoint is the parent's other endpoint: short ranges are scanned for them
-// in place; long ones search the excluded multi-edge list.
+// Each child's range is galloped to from the parent edge's position in that
+// list (or its cross rank into the vertex's other list).  Both layers share
+// the unclipped range: e's windows of the two layers both contain t, so the
+// bound on the side of e itself is common and only the far bound is clipped,
+// in at most one layer, by a search inside the unclipped range.  The
+// excluded entries of Claim 3.1 are exactly the entries of the range whose
+// other endpoint is the parent's other endpoint: short ranges are scanned for
+// them in place (one pass serves both layers); long ones search the excluded
+// multi-edge list.
 // Results are written in this list order.  A root with children at both ends
 // runs side 0 (first) then side 1 (last), which reads side 0's partial
 // product and pending-overflow bit through the out->in position map.
 // Overflow rule: a factor >= 2^64, or an exact product >= 2^64 with no zero
 // factor.
 #ifndef TM_DP_MINB
-#define TM_DP_MINB 6   // 40 registers: six blocks of 256 per SM (measured fastest)
+#define TM_DP_MINB 4   // 64 registers: no spills (at 40 or 48 registers it spills)
 #endif
-__global__ void __launch_bounds__(256, TM_DP_MINB) k_dp(DevGraph g, DevPlan P, int q, int side, int first, int last,
-                                            ChildPrefix cp, ulonglong2 *__restrict__ wout,
-                                            const ulonglong2 *__restrict__ in, const uint8_t *__restrict__ pin,
-                                            uint8_t *__restrict__ pout, uint32_t *status)
+__global__ void __launch_bounds__(256, TM_DP_MINB) k_dp(DevGraph g, DevPlan P, WinDiv wv, int q, int side, int first,
+                                                        int last, ChildPrefix cp, ulonglong2 *__restrict__ wout,
+                                                        const ulonglong2 *__restrict__ in,
+                                                        const uint8_t *__restrict__ pin, uint8_t *__restrict__ pout,
+                                                        uint32_t *status)
 {
     const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= g.m) return;
@@ -65,16 +84,16 @@ __global__ void __launch_bounds__(256, TM_DP_MINB) k_dp(DevGraph g, DevPlan P, i
     const uint32_t z = __ldg((side ? g.in_dst : g.out_src) + pos);
     // the parent's other endpoint; without Constraint 2 nothing is excluded
     const uint32_t o = P.c2 ? __ldg((side ? g.in_nbr : g.out_nbr) + pos) : kNone;
-    const uint32_t pr = __ldg((side ? g.in_pair : g.out_pair) + pos);
-    const int64_t d = P.delta, wd = P.wdelta;
+    const uint64_t d = (uint64_t)P.delta, wd = (uint64_t)wv.d;
+    const uint32_t qt = wv.quot(t);
     uint64_t wlo[2], whi[2], prod[2] = {1, 1};
     bool zero[2], ovf[2] = {false, false};
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
-        const int64_t wi = layer_window(t, p, wd);
+        const int64_t wi = WinDiv::win_of(qt, p);
         zero[p] = wi < 0;
-        wlo[p] = zero[p] ? 0 : (uint64_t)(wi * wd);
-        whi[p] = zero[p] ? 0 : (uint64_t)((wi + 2) * wd - 1);
+        wlo[p] = zero[p] ? 0 : (uint64_t)wi * wd;
+        whi[p] = zero[p] ? 0 : ((uint64_t)wi + 2) * wd - 1;
     }
     if (!first) {
         const uint32_t xp = __ldg(g.in_to_out + pos);   // side 1 reads side 0's partial (both layers)
@@ -83,7 +102,7 @@ __global__ void __launch_bounds__(256, TM_DP_MINB) k_dp(DevGraph g, DevPlan P, i
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
             if (zero[p]) continue;
-            prod[p] = p ? pv.y : pv.x;
+            prod[p] = lane_of(pv, p);
             ovf[p] = (pb >> p) & 1u;
             if (prod[p] == 0) zero[p] = true;
         }
@@ -99,47 +118,94 @@ __global__ void __launch_bounds__(256, TM_DP_MINB) k_dp(DevGraph g, DevPlan P, i
         const uint32_t beg = __ldg(off + z), end = __ldg(off + z + 1);
         const uint32_t base = ((side == 0) == out) ? gallop_back(tarr, beg, pos, t)
                                                    : __ldg((side == 0 ? g.out_xrank : g.in_xrank) + pos);
+        // per-layer ranges [a[p], b[p]) with times in [lo[p], hi[p]]
+        uint32_t a[2], b[2];
+        uint64_t lo[2], hi[2];
+        if (later) {
+            const uint64_t l0 = (uint64_t)t + 1, hu = (uint64_t)t + d;
+            const uint32_t a0 = gallop_idx(tarr, base, end, l0);
+            const uint32_t bu = gallop_idx(tarr, a0, end, hu + 1);
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            if (zero[p]) continue;
-            uint64_t lo, hi;
-            if (later) { lo = (uint64_t)t + 1; hi = (uint64_t)t + (uint64_t)d; }
-            else { lo = (uint64_t)t >= (uint64_t)d ? (uint64_t)t - (uint64_t)d : 0; hi = (uint64_t)t - 1; }
-            lo = lo < wlo[p] ? wlo[p] : lo;
-            hi = hi > whi[p] ? whi[p] : hi;
-            if (lo > hi) { zero[p] = true; continue; }
-            uint32_t a, b;
-            if (later) { a = gallop_idx(tarr, base, end, lo); b = gallop_idx(tarr, a, end, hi + 1); }
-            else { b = base; a = gallop_back(tarr, beg, base, lo); }
-            const uint64_t *Pd = leaf ? nullptr : cp.pd[p][P.tslot[c]];
-            uint64_t pbase = 0, sum;
-            if (!leaf && b > a) pbase = (a > beg && (uint64_t)__ldg(tarr + a - 1) >= wlo[p]) ? __ldg(Pd + a - 1) : 0;
-            uint64_t excl = 0;
-            if (b - a <= kScanLimit) {
-                uint64_t prev = pbase;
-                for (uint32_t x = a; x < b; ++x) {
-                    uint64_t wx = 1;
-                    if (!leaf) { const uint64_t px = __ldg(Pd + x); wx = px - prev; prev = px; }
-                    if (__ldg(nbr + x) == o) excl += wx;
+            for (int p = 0; p < 2; ++p) {
+                lo[p] = l0;
+                hi[p] = hu < whi[p] ? hu : whi[p];
+                a[p] = a0;
+                b[p] = (zero[p] || hi[p] == hu) ? bu : lower_idx(tarr, a0, bu, hi[p] + 1);
+                if (lo[p] > hi[p]) zero[p] = true;
+            }
+        } else {
+            const uint64_t h0 = (uint64_t)t - 1, lu = (uint64_t)t >= d ? (uint64_t)t - d : 0;
+            const uint32_t au = gallop_back(tarr, beg, base, lu);
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                hi[p] = h0;
+                lo[p] = lu > wlo[p] ? lu : wlo[p];
+                b[p] = base;
+                a[p] = (zero[p] || lo[p] == lu) ? au : lower_idx(tarr, au, base, lo[p]);
+                if (lo[p] > hi[p]) zero[p] = true;
+            }
+        }
+        if (zero[0] && zero[1]) break;
+        const ulonglong2 *Pd = leaf ? nullptr : pick_slot(cp.pd, P.tslot[c]);
+        uint64_t excl[2] = {0, 0};
+        // the union of the live layers' ranges
+        uint32_t ua = 0xFFFFFFFFu, ub = 0;
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+            if (!zero[p]) { ua = min(ua, a[p]); ub = max(ub, b[p]); }
+        if (ub <= ua || ub - ua <= kScanLimit) {
+            for (uint32_t x = ua; x < ub; ++x) {
+                if (__ldg(nbr + x) != o) continue;
+                ulonglong2 wx2 = make_ulonglong2(1, 1);
+                if (!leaf) {
+                    // the entry's weight: its prefix minus the previous entry's in
+                    // the same (vertex, window) segment
+                    const ulonglong2 px = __ldg(Pd + x);
+                    const ulonglong2 pp = x > beg ? __ldg(Pd + x - 1) : make_ulonglong2(0, 0);
+                    const uint32_t tp = x > beg ? __ldg(tarr + x - 1) : 0;
+                    wx2.x = px.x - ((x > beg && (uint64_t)tp >= wlo[0]) ? pp.x : 0);
+                    wx2.y = px.y - ((x > beg && (uint64_t)tp >= wlo[1]) ? pp.y : 0);
                 }
-            } else {
-                const uint32_t pe = !P.c2 ? kNone : (out == (side == 0)) ? pr : __ldg(g.rev_pair + pr);
-                if (pe != kNone) {
-                    const uint32_t xb = __ldg(g.pair_off + pe), xe = __ldg(g.pair_off + pe + 1);
-                    const uint32_t ea = lower_idx(g.multi_t, xb, xe, lo);
-                    const uint32_t eb = gallop_idx(g.multi_t, ea, xe, hi + 1);
-                    if (eb > ea) {
-                        if (leaf) excl = eb - ea;
-                        else {
-                            const uint64_t *Pm = cp.pm[p][P.tslot[c]];
-                            const uint64_t bs = (ea > xb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo[p]) ? __ldg(Pm + ea - 1) : 0;
-                            excl = __ldg(Pm + eb - 1) - bs;
-                        }
+#pragma unroll
+                for (int p = 0; p < 2; ++p)
+                    if (!zero[p] && x >= a[p] && x < b[p]) excl[p] += lane_of(wx2, p);
+            }
+        } else {
+            const uint32_t pr = __ldg((side ? g.in_pair : g.out_pair) + pos);
+            const uint32_t pe = !P.c2 ? kNone : (out == (side == 0)) ? pr : __ldg(g.rev_pair + pr);
+            if (pe != kNone) {
+                const uint32_t xb = __ldg(g.pair_off + pe), xe = __ldg(g.pair_off + pe + 1);
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    if (zero[p]) continue;
+                    const uint32_t ea = lower_idx(g.multi_t, xb, xe, lo[p]);
+                    const uint32_t eb = gallop_idx(g.multi_t, ea, xe, hi[p] + 1);
+                    if (eb <= ea) continue;
+                    if (leaf) {
+                        excl[p] = eb - ea;
+                    } else {
+                        const ulonglong2 *Pm = pick_slot(cp.pm, P.tslot[c]);
+                        const uint64_t bs = (ea > xb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo[p])
+                                                ? lane_of(__ldg(Pm + ea - 1), p) : 0;
+                        excl[p] = lane_of(__ldg(Pm + eb - 1), p) - bs;
                     }
                 }
             }
-            if (leaf) sum = (uint64_t)(b - a) - excl;
-            else sum = (b > a ? __ldg(Pd + b - 1) - pbase : 0) - excl;
+        }
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            if (zero[p]) continue;
+            uint64_t sum;
+            if (leaf) {
+                sum = (uint64_t)(b[p] - a[p]) - excl[p];
+            } else if (b[p] > a[p]) {
+                const uint64_t top = lane_of(__ldg(Pd + b[p] - 1), p);
+                const uint64_t pbase = (a[p] > beg && (uint64_t)__ldg(tarr + a[p] - 1) >= wlo[p])
+                                           ? lane_of(__ldg(Pd + a[p] - 1), p) : 0;
+                sum = top - pbase - excl[p];
+            } else {
+                sum = 0;
+            }
             if (sum == 0) zero[p] = true;
             else prod[p] = mul_chk(prod[p], sum, ovf[p]);
         }
@@ -151,28 +217,36 @@ __global__ void __launch_bounds__(256, TM_DP_MINB) k_dp(DevGraph g, DevPlan P, i
 
 // ---- scans over the three orders ----------------------------------------
 // segment = (owner, window of layer p); owner boundaries come from a bit set.
+// Whether the windows of layer p differ between two times.
+__device__ __forceinline__ uint32_t win_change(const WinDiv &wv, uint32_t ta, uint32_t tb)
+{
+    const uint32_t qa = wv.quot(ta), qb = wv.quot(tb);
+    return (WinDiv::win_of(qa, 0) != WinDiv::win_of(qb, 0) ? 1u : 0u) |
+           (WinDiv::win_of(qa, 1) != WinDiv::win_of(qb, 1) ? 2u : 0u);
+}
+
 // Segment heads of one layer (exports rebuild weights from prefix sums).
 struct DirHead {
     const uint32_t *tarr;       // position -> t'
     const uint32_t *ownbits;    // bit set: position starts a new owner
     int p;
-    int64_t d;
+    WinDiv wv;
     __device__ bool head(uint64_t i) const
     {
         if (i == 0) return true;
         if ((__ldg(ownbits + (i >> 5)) >> (i & 31)) & 1u) return true;
-        return layer_window(__ldg(tarr + i), p, d) != layer_window(__ldg(tarr + i - 1), p, d);
+        return (win_change(wv, __ldg(tarr + i), __ldg(tarr + i - 1)) >> p) & 1u;
     }
 };
 
 struct RootHead {
     const uint32_t *tarr;       // g_t
     int p;
-    int64_t d;
+    WinDiv wv;
     __device__ bool head(uint64_t i) const
     {
         if (i == 0) return true;
-        return layer_window(__ldg(tarr + i), p, d) != layer_window(__ldg(tarr + i - 1), p, d);
+        return (win_change(wv, __ldg(tarr + i), __ldg(tarr + i - 1)) >> p) & 1u;
     }
 };
 
@@ -180,18 +254,16 @@ struct RootHead {
 // one 16-byte gather; heads are per layer (bit p).
 struct DirScan2 {
     static constexpr bool kGathered = true;
-    const ulonglong2 *w;        // (layer 0, layer 1) weights in the order the DP wrote them
+    const ulonglong2 *w;        // (layer 0, layer 1) weights
     const uint32_t *perm;       // scan position -> weight position (null: same order)
     const uint32_t *tarr;       // position -> t'
     const uint32_t *ownbits;    // bit set: position starts a new owner
-    int64_t d;
+    WinDiv wv;
     __device__ ulonglong2 value2(uint64_t i) const { return __ldg(w + (perm ? __ldg(perm + i) : i)); }
     __device__ uint32_t head2(uint64_t i) const
     {
         if (i == 0 || ((__ldg(ownbits + (i >> 5)) >> (i & 31)) & 1u)) return 3u;
-        const uint32_t a = __ldg(tarr + i), b = __ldg(tarr + i - 1);
-        return (layer_window(a, 0, d) != layer_window(b, 0, d) ? 1u : 0u) |
-               (layer_window(a, 1, d) != layer_window(b, 1, d) ? 2u : 0u);
+        return win_change(wv, __ldg(tarr + i), __ldg(tarr + i - 1));
     }
 };
 
@@ -199,36 +271,66 @@ struct RootScan2 {
     static constexpr bool kGathered = true;
     const ulonglong2 *w;        // root weight pairs in list order
     const uint32_t *tarr;       // g_t
-    int64_t d;
+    WinDiv wv;
     const uint32_t *perm;       // gid -> weight position
     __device__ ulonglong2 value2(uint64_t i) const { return __ldg(w + (perm ? __ldg(perm + i) : i)); }
     __device__ uint32_t head2(uint64_t i) const
     {
         if (i == 0) return 3u;
-        const uint32_t a = __ldg(tarr + i), b = __ldg(tarr + i - 1);
-        return (layer_window(a, 0, d) != layer_window(b, 0, d) ? 1u : 0u) |
-               (layer_window(a, 1, d) != layer_window(b, 1, d) ? 2u : 0u);
+        return win_change(wv, __ldg(tarr + i), __ldg(tarr + i - 1));
     }
 };
 
-// Window heads of layer p in GLOBAL order.
-// Window heads of both layers (layer p = blockIdx.y) into flag[p*m + i].
-__global__ void k_window_heads(const uint32_t *__restrict__ t, uint32_t m, int64_t d, uint32_t *__restrict__ flag)
+// ---- windows of both layers (Constraint 3, Alg. 1) ------------------------
+// A window of layer p starts at GLOBAL position i when t'_i lies in a window
+// of layer p and t'_{i-1} does not lie in the same one.  Each thread takes
+// kWinItems consecutive positions; tile = one block's positions.
+constexpr int kWinItems = 8;
+constexpr int kWinTile = TB * kWinItems;
+
+// Head bits of position i (bit p: a window of layer p starts there) and the
+// window indices of both layers.
+__device__ __forceinline__ uint32_t win_heads_at(const uint32_t *__restrict__ t, uint32_t i, const WinDiv &wv,
+                                                 int64_t &w0, int64_t &w1)
 {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int p = blockIdx.y;
-    if (i >= m) return;
-    const int64_t w = layer_window(t[i], p, d);
-    flag[(size_t)p * m + i] = (w >= 0 && (i == 0 || layer_window(t[i - 1], p, d) != w)) ? 1u : 0u;
+    const uint32_t q = wv.quot(__ldg(t + i));
+    w0 = WinDiv::win_of(q, 0);
+    w1 = WinDiv::win_of(q, 1);
+    uint32_t h = (w0 >= 0 ? 1u : 0u) | (w1 >= 0 ? 2u : 0u);
+    if (i > 0) h &= win_change(wv, __ldg(t + i), __ldg(t + i - 1));
+    return h;
 }
 
-// The exclusive scan ran over both layers' flags back to back: layer 0 has
-// pos[m] windows, layer 1 the rest of the total.
-__global__ void k_window_counts(const uint32_t *__restrict__ pos, uint32_t m, uint32_t *__restrict__ counts)
+// Per tile: the number of window starts of each layer (counts[tile] for
+// layer 0, counts[ntile + tile] for layer 1).
+__global__ void __launch_bounds__(TB) k_win_count(const uint32_t *__restrict__ t, uint32_t m, WinDiv wv, uint32_t ntile,
+                                                  uint32_t *__restrict__ counts)
 {
-    const uint32_t c0 = pos[m];
-    counts[1] -= c0;
-    counts[0] = c0;
+    __shared__ uint32_t s0[TB / 32], s1[TB / 32];
+    const uint32_t base = blockIdx.x * (uint32_t)kWinTile + threadIdx.x * kWinItems;
+    uint32_t c0 = 0, c1 = 0;
+#pragma unroll
+    for (int j = 0; j < kWinItems; ++j) {
+        const uint32_t i = base + j;
+        if (i >= m) break;
+        int64_t w0, w1;
+        const uint32_t h = win_heads_at(t, i, wv, w0, w1);
+        c0 += h & 1u;
+        c1 += h >> 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        c0 += __shfl_down_sync(0xffffffffu, c0, o);
+        c1 += __shfl_down_sync(0xffffffffu, c1, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { s0[warp] = c0; s1[warp] = c1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t a = 0, b = 0;
+        for (int w = 0; w < TB / 32; ++w) { a += s0[w]; b += s1[w]; }
+        counts[blockIdx.x] = a;
+        counts[ntile + blockIdx.x] = b;
+    }
 }
 
 struct WinOut {
@@ -236,19 +338,58 @@ struct WinOut {
     uint32_t nwin[2];
 };
 
-// Both layers (p = blockIdx.y): window starts and indices; layer 1's scanned
-// positions start at layer 0's count (base).  Also the end sentinels.
-__global__ void k_window_fill(const uint32_t *__restrict__ t, const uint32_t *__restrict__ flag,
-                              const uint32_t *__restrict__ pos, uint32_t m, int64_t d, uint32_t base1, WinOut W)
+// The windows' first positions and indices, written at the tile's scanned
+// offsets (offs[tile] for layer 0, offs[ntile + tile] - nw0 for layer 1),
+// plus the end sentinels beg[nwin] = m.
+__global__ void __launch_bounds__(TB) k_win_fill(const uint32_t *__restrict__ t, uint32_t m, WinDiv wv, uint32_t ntile,
+                                                 const uint32_t *__restrict__ offs, WinOut W)
 {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int p = blockIdx.y;
-    uint32_t *beg = p ? W.beg[1] : W.beg[0], *wid = p ? W.id[1] : W.id[0];
-    if (i == 0) beg[p ? W.nwin[1] : W.nwin[0]] = m;
-    if (i >= m || !flag[(size_t)p * m + i]) return;
-    const uint32_t k = pos[(size_t)p * m + i] - (p ? base1 : 0);
-    beg[k] = i;
-    wid[k] = (uint32_t)layer_window(t[i], p, d);
+    __shared__ uint32_t s0[TB / 32], s1[TB / 32];
+    const uint32_t base = blockIdx.x * (uint32_t)kWinTile + threadIdx.x * kWinItems;
+    uint32_t hb = 0, c0 = 0, c1 = 0;
+#pragma unroll
+    for (int j = 0; j < kWinItems; ++j) {
+        const uint32_t i = base + j;
+        if (i >= m) break;
+        int64_t w0, w1;
+        const uint32_t h = win_heads_at(t, i, wv, w0, w1);
+        hb |= h << (2 * j);
+        c0 += h & 1u;
+        c1 += h >> 1;
+    }
+    // exclusive ranks of this thread's starts inside the tile, per layer
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t i0 = c0, i1 = c1;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y0 = __shfl_up_sync(0xffffffffu, i0, o), y1 = __shfl_up_sync(0xffffffffu, i1, o);
+        if (lane >= o) { i0 += y0; i1 += y1; }
+    }
+    if (lane == 31) { s0[warp] = i0; s1[warp] = i1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t r0 = 0, r1 = 0;
+        for (int w = 0; w < TB / 32; ++w) {
+            const uint32_t a = s0[w], b = s1[w];
+            s0[w] = r0; s1[w] = r1;
+            r0 += a; r1 += b;
+        }
+    }
+    __syncthreads();
+    uint32_t k0 = offs[blockIdx.x] + s0[warp] + i0 - c0;
+    uint32_t k1 = offs[ntile + blockIdx.x] - W.nwin[0] + s1[warp] + i1 - c1;
+#pragma unroll
+    for (int j = 0; j < kWinItems; ++j) {
+        const uint32_t h = (hb >> (2 * j)) & 3u;
+        if (!h) continue;
+        const uint32_t i = base + j;
+        const uint32_t q = wv.quot(__ldg(t + i));
+        if (h & 1u) { W.beg[0][k0] = i; W.id[0][k0] = (uint32_t)WinDiv::win_of(q, 0); ++k0; }
+        if (h & 2u) { W.beg[1][k1] = i; W.id[1][k1] = (uint32_t)WinDiv::win_of(q, 1); ++k1; }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        W.beg[0][W.nwin[0]] = m;
+        W.beg[1][W.nwin[1]] = m;
+    }
 }
 
 // Window totals W_i (last root-CDF entry of each window) and their 128-bit
@@ -304,8 +445,7 @@ __device__ __forceinline__ uint64_t ceil_shift(uint64_t c, uint32_t s) { return 
 
 struct GuideLayer {
     const uint64_t *cdf;
-    const uint32_t *win_beg, *flag, *pos;
-    uint32_t pbase;             // first scanned position of this layer's windows
+    const uint32_t *win_beg;
     uint32_t nwin;
     uint32_t *gshift, *goff, *guide;
 };
@@ -354,39 +494,45 @@ __global__ void __launch_bounds__(1024) k_guide_setup(GuideArgs A)
     }
 }
 
-// one thread per edge and layer (blockIdx.y): the buckets whose lower bound
-// falls in [cdf[x-1], cdf[x]) start at x
-__global__ void k_guide_fill(GuideArgs A, const uint32_t *__restrict__ t, uint32_t m, int64_t d)
+// One warp per window (layer 0's windows, then layer 1's); the lanes stride
+// over the window's edges: the buckets whose lower bound falls in
+// [cdf[x-1], cdf[x]) start at edge x.
+__global__ void __launch_bounds__(TB) k_guide_fill(GuideArgs A)
 {
-    const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int p = blockIdx.y;
-    if (x >= m || layer_window(t[x], p, d) < 0) return;
+    const uint32_t wv = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nw0 = A.L[0].nwin, nw = nw0 + A.L[1].nwin;
+    if (wv >= nw) return;
+    const int p = wv >= nw0 ? 1 : 0;
     const GuideLayer &L = p ? A.L[1] : A.L[0];
-    const uint32_t kk = L.pos[x] + L.flag[x] - 1 - L.pbase;
+    const uint32_t kk = wv - (p ? nw0 : 0);
     const uint32_t wbeg = L.win_beg[kk], wend = L.win_beg[kk + 1];
     const uint32_t sh = L.gshift[kk];
     uint32_t *G = L.guide + L.goff[kk];
-    const uint64_t c1 = L.cdf[x], c0 = x > wbeg ? L.cdf[x - 1] : 0;
-    const uint64_t j1 = ceil_shift(c1, sh);
-    for (uint64_t j = ceil_shift(c0, sh); j < j1; ++j) G[j] = x;
-    if (x == wend - 1) G[j1] = x;
+    for (uint32_t x = wbeg + lane; x < wend; x += 32) {
+        const uint64_t c1 = L.cdf[x], c0 = x > wbeg ? L.cdf[x - 1] : 0;
+        const uint64_t j1 = ceil_shift(c1, sh);
+        for (uint64_t j = ceil_shift(c0, sh); j < j1; ++j) G[j] = x;
+        if (x == wend - 1) G[j1] = x;
+    }
 }
 
-// Reconstruct w for one order from its segmented prefix (exports).
+// Reconstruct w for one order from its segmented prefix (exports); the
+// prefix of position i is pref[i * stride].
 template <class F>
-__global__ void k_unprefix(F f, const uint64_t *__restrict__ pref, const uint32_t *__restrict__ perm, uint32_t m,
-                           uint64_t *__restrict__ out)
+__global__ void k_unprefix(F f, const uint64_t *__restrict__ pref, int stride, const uint32_t *__restrict__ perm,
+                           uint32_t m, uint64_t *__restrict__ out)
 {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
-    uint64_t w = pref[i] - (f.head(i) ? 0 : pref[i - 1]);
+    uint64_t w = pref[(size_t)i * stride] - (f.head(i) ? 0 : pref[(size_t)(i - 1) * stride]);
     out[perm ? perm[i] : i] = w;
 }
 
-__global__ void k_leaf_weights(const uint32_t *__restrict__ t, uint32_t m, int p, int64_t d, uint64_t *__restrict__ out)
+__global__ void k_leaf_weights(const uint32_t *__restrict__ t, uint32_t m, int p, WinDiv wv, uint64_t *__restrict__ out)
 {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) out[i] = layer_window(t[i], p, d) >= 0 ? 1 : 0;
+    if (i < m) out[i] = wv.win(t[i], p) >= 0 ? 1 : 0;
 }
 
 }  // namespace
@@ -404,6 +550,7 @@ static void free_motif_weights(tm_ctx *ctx, tm_motif *mo)
     mo->bufs.clear();
     mo->bytes = 0;
     for (int p = 0; p < 2; ++p) mo->layer[p] = LayerData();
+    for (int sl = 0; sl < kMaxTree; ++sl) mo->pref_dir[sl] = mo->pref_multi[sl] = nullptr;
     mo->wcum = nullptr;
     mo->have_weights = false;
 }
@@ -419,38 +566,39 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     const DevPlan &P = mo->plan;
     cudaStream_t st = ctx->stream;
     const uint32_t m = g.m;
-    const int64_t d = P.wdelta;   // window unit (delta, or one window without Constraint 3)
+    const WinDiv wv = make_windiv(P.wdelta);   // window unit (delta, or one window without Constraint 3)
     int rc = TM_OK;
     cudaMemsetAsync(ctx->status, 0, 4, st);
-    // ---- windows of each layer (K2): count both layers, then one block for
-    // everything the motif keeps (windows, root CDF, prefix arrays, totals)
-    // both layers' flags and scanned positions back to back: [p*m, (p+1)*m)
-    uint32_t *flag_all, *pos_all, *flag[2], *pos[2], *dcount;
+    // ---- windows of each layer (K2): per tile the window starts of both
+    // layers, one scan over the tile counts, then one block for everything
+    // the motif keeps (windows, root CDF, prefix arrays, totals)
+    const uint32_t ntile = m ? (m + kWinTile - 1) / kWinTile : 0;
+    uint32_t *wcount = nullptr, *woffs = nullptr;
     uint32_t nwh[2] = {0, 0};
     {
         PhaseScope ph(ctx, TM_PH_WINDOWS);
-        dcount = (uint32_t *)salloc(ctx, 8);
-        flag_all = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 8);
-        pos_all = (uint32_t *)salloc(ctx, ((size_t)m + 1) * 8);
-        if (!dcount || !flag_all || !pos_all) return TM_E_NOMEM;
-        for (int p = 0; p < 2; ++p) { flag[p] = flag_all + (size_t)p * m; pos[p] = pos_all + (size_t)p * m; }
-        cudaMemsetAsync(dcount, 0, 8, st);
+        wcount = (uint32_t *)salloc(ctx, ((size_t)2 * ntile + 1) * 4);
+        woffs = (uint32_t *)salloc(ctx, ((size_t)2 * ntile + 2) * 4);
+        if (!wcount || !woffs) return TM_E_NOMEM;
         if (m) {
-            launch(ctx, k_window_heads, dim3(blocks_for(m, TB), 2), TB, g.g_t, m, d, flag_all);
-            rc = exclusive_scan_u32(ctx, flag_all, pos_all, 2 * (uint64_t)m, dcount + 1);
+            launch(ctx, k_win_count, ntile, TB, g.g_t, m, wv, ntile, wcount);
+            rc = exclusive_scan_u32(ctx, wcount, woffs, 2 * (uint64_t)ntile, woffs + 2 * (size_t)ntile);
             if (rc) return rc;
-            launch(ctx, k_window_counts, 1, 1, (const uint32_t *)pos_all, m, dcount);
+            uint32_t both[2] = {0, 0};
+            copy_d2h(ctx, &both[0], woffs + ntile, 4);                  // layer 0's windows
+            copy_d2h(ctx, &both[1], woffs + 2 * (size_t)ntile, 4);      // all windows
+            rc = check_cuda(ctx, cudaStreamSynchronize(st), "window count");
+            if (rc) return rc;
+            nwh[0] = both[0];
+            nwh[1] = both[1] - both[0];
         }
-        copy_d2h(ctx, nwh, dcount, 8);
-        rc = check_cuda(ctx, cudaStreamSynchronize(st), "window count");
-        if (rc) return rc;
     }
     {
         auto al = [](size_t b) { return (b + 255) / 256 * 256; };
         const size_t mm = (size_t)(m ? m : 1);
         auto guide_n = [&](uint32_t nw) { return (size_t)m / 4 + 3 * (size_t)nw + 1; };
         size_t total = al(((size_t)nwh[0] + 1) * 4) * 4 + al(((size_t)nwh[1] + 1) * 4) * 4 + 2 * al(mm * 8) +
-                       (size_t)P.nslots * 4 * al(mm * 8) + al(((size_t)nwh[0] + nwh[1] + 1) * 16) +
+                       (size_t)P.nslots * 2 * al(mm * 16) + al(((size_t)nwh[0] + nwh[1] + 1) * 16) +
                        al(guide_n(nwh[0]) * 4) + al(guide_n(nwh[1]) * 4);
         char *blk = (char *)malloc_motif(ctx, mo, total);
         if (!blk) return TM_E_NOMEM;
@@ -465,10 +613,10 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
             L.win_gshift = (uint32_t *)take(((size_t)nwh[p] + 1) * 4);
             L.win_goff = (uint32_t *)take(((size_t)nwh[p] + 1) * 4);
             L.guide = (uint32_t *)take(guide_n(nwh[p]) * 4);
-            for (int sl = 0; sl < P.nslots; ++sl) {
-                L.pref_dir[sl] = (uint64_t *)take(mm * 8);
-                L.pref_multi[sl] = (uint64_t *)take(mm * 8);
-            }
+        }
+        for (int sl = 0; sl < P.nslots; ++sl) {
+            mo->pref_dir[sl] = (ulonglong2 *)take(mm * 16);
+            mo->pref_multi[sl] = (ulonglong2 *)take(mm * 16);
         }
         mo->wcum = (uint64_t *)take(((size_t)nwh[0] + nwh[1] + 1) * 16);
     }
@@ -476,13 +624,17 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
         PhaseScope ph(ctx, TM_PH_WINDOWS);
         WinOut wo{{mo->layer[0].win_beg, mo->layer[1].win_beg}, {mo->layer[0].win_id, mo->layer[1].win_id},
                   {nwh[0], nwh[1]}};
-        launch(ctx, k_window_fill, dim3(blocks_for(m ? m : 1, TB), 2), TB, g.g_t, (const uint32_t *)flag_all,
-               (const uint32_t *)pos_all, m, d, nwh[0], wo);
+        if (m) launch(ctx, k_win_fill, ntile, TB, g.g_t, m, wv, ntile, (const uint32_t *)woffs, wo);
+        else {
+            cudaMemsetAsync(mo->layer[0].win_beg, 0, 4, st);
+            cudaMemsetAsync(mo->layer[1].win_beg, 0, 4, st);
+        }
     }
     // ---- DP over tree nodes in increasing height (K3) + prefixes (K4)
     const OwnerBits ob{g.own_out, g.own_in, g.own_multi};
     ulonglong2 *w = nullptr, *pw = nullptr;   // (layer 0, layer 1) weight pairs
     uint8_t *pend = nullptr;                  // bit p: pending overflow of layer p's partial
+    ulonglong2 *gathered = nullptr;           // a node's weights gathered into out-list order
     w = (ulonglong2 *)salloc(ctx, (size_t)(m ? m : 1) * 16);
     if (!w) return TM_E_NOMEM;
     ChildPrefix cp{};
@@ -508,12 +660,12 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
             }
             if (m) {
                 if (has[0] && has[1]) {
-                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, q, 0, 1, 0, cp, pw, (const ulonglong2 *)nullptr,
+                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, wv, q, 0, 1, 0, cp, pw, (const ulonglong2 *)nullptr,
                            (const uint8_t *)nullptr, pend, ctx->status);
-                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, q, 1, 0, 1, cp, w, (const ulonglong2 *)pw,
+                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, wv, q, 1, 0, 1, cp, w, (const ulonglong2 *)pw,
                            (const uint8_t *)pend, (uint8_t *)nullptr, ctx->status);
                 } else {
-                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, q, in_order ? 1 : 0, 1, 1, cp, w,
+                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, wv, q, in_order ? 1 : 0, 1, 1, cp, w,
                            (const ulonglong2 *)nullptr, (const uint8_t *)nullptr, (uint8_t *)nullptr, ctx->status);
                 }
             }
@@ -523,37 +675,44 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
         if (q == 0) {
             PhaseScope ph(ctx, TM_PH_ROOT);
             GuideArgs ga{};
-            RootScan2 f{w, g.g_t, d, in_order ? g.in_pos : g.out_pos};
+            RootScan2 f{w, g.g_t, wv, in_order ? g.in_pos : g.out_pos};
             rc = segmented_scan2_u64(ctx, f, m, mo->layer[0].root_cdf, mo->layer[1].root_cdf);
             if (rc) return rc;
             for (int p = 0; p < 2; ++p) {
                 LayerData &L = mo->layer[p];
-                ga.L[p] = GuideLayer{L.root_cdf, L.win_beg, flag[p], pos[p], p ? nwh[0] : 0u, L.nwin, L.win_gshift,
-                                     L.win_goff, L.guide};
+                ga.L[p] = GuideLayer{L.root_cdf, L.win_beg, L.nwin, L.win_gshift, L.win_goff, L.guide};
             }
-            // guide tables of the root search, both layers
-            if (m) {
+            // guide tables of the root search, both layers (a warp per window)
+            if (m && nwh[0] + nwh[1]) {
                 launch(ctx, k_guide_setup, 2, 1024, ga);
-                launch(ctx, k_guide_fill, dim3(blocks_for(m, TB), 2), TB, ga, g.g_t, m, d);
+                launch(ctx, k_guide_fill, blocks_for((uint64_t)(nwh[0] + nwh[1]) * 32, TB), TB, ga);
             }
         } else {
             PhaseScope ph(ctx, TM_PH_PREFIX);
-            int slot = P.tslot[q];
-            bool out = P.tout[q] != 0;
-            // scan order of the parent's candidate list -> position of the weight
-            const uint32_t *dmap = (out == !in_order) ? nullptr : (out ? g.out_to_in : g.in_to_out);
-            const uint32_t *mmap = in_order ? g.multi_to_in : g.multi_to_out;
-            LayerData &L0 = mo->layer[0], &L1 = mo->layer[1];
-            DirScan2 fd{w, dmap, out ? g.out_t : g.in_t, out ? ob.out : ob.in, d};
-            rc = segmented_scan2_u64(ctx, fd, m, L0.pref_dir[slot], L1.pref_dir[slot]);
-            if (rc) return rc;
-            DirScan2 fm{w, mmap, g.multi_t, ob.multi, d};
-            rc = segmented_scan2_u64(ctx, fm, m, L0.pref_multi[slot], L1.pref_multi[slot]);
-            if (rc) return rc;
-            for (int p = 0; p < 2; ++p) {
-                cp.pd[p][slot] = mo->layer[p].pref_dir[slot];
-                cp.pm[p][slot] = mo->layer[p].pref_multi[slot];
+            const int slot = P.tslot[q];
+            const bool out = P.tout[q] != 0;
+            // A non-root node's DP runs in the list order of its far endpoint,
+            // never in the order its parent scans (out-list order when the node
+            // leaves the meeting vertex, in-list order when it enters it): the
+            // parent's order is one gather through a position map.  Multi-edge
+            // lists are grouped by source like the out-lists, so the multi-edge
+            // prefix gathers, within each source's run, from the weights in
+            // out-list order: the DP's own output when the node enters the
+            // meeting vertex, else the gathered copy the first scan keeps.
+            const uint32_t *dmap = out ? g.out_to_in : g.in_to_out;
+            if (out && !gathered) {
+                gathered = (ulonglong2 *)salloc(ctx, (size_t)(m ? m : 1) * 16);
+                if (!gathered) return TM_E_NOMEM;
             }
+            DirScan2 fd{w, dmap, out ? g.out_t : g.in_t, out ? ob.out : ob.in, wv};
+            rc = segmented_scan2_u64(ctx, fd, m, nullptr, nullptr, mo->pref_dir[slot], out ? gathered : nullptr);
+            if (rc) return rc;
+            DirScan2 fm{out ? (const ulonglong2 *)gathered : (const ulonglong2 *)w, g.multi_to_out, g.multi_t,
+                        ob.multi, wv};
+            rc = segmented_scan2_u64(ctx, fm, m, nullptr, nullptr, mo->pref_multi[slot]);
+            if (rc) return rc;
+            cp.pd[slot] = mo->pref_dir[slot];
+            cp.pm[slot] = mo->pref_multi[slot];
         }
     }
     // ---- window totals and their 128-bit running sum (K5)
@@ -589,18 +748,21 @@ int export_weights(tm_ctx *ctx, tm_motif *mo, int q, int layer, uint64_t *host_o
     if (m == 0) return TM_OK;
     uint64_t *out = (uint64_t *)salloc(ctx, (size_t)m * 8);
     if (!out) return TM_E_NOMEM;
+    const WinDiv wv = make_windiv(P.wdelta);
     int rc = TM_OK;
     if (P.tleaf[q] && q != 0) {
-        launch(ctx, k_leaf_weights, blocks_for(m, TB), TB, g.g_t, m, layer, P.wdelta, out);
+        launch(ctx, k_leaf_weights, blocks_for(m, TB), TB, g.g_t, m, layer, wv, out);
     } else if (q == 0) {
-        RootHead f{g.g_t, layer, P.wdelta};
-        launch(ctx, k_unprefix<RootHead>, blocks_for(m, TB), TB, f, mo->layer[layer].root_cdf, nullptr, m, out);
+        RootHead f{g.g_t, layer, wv};
+        launch(ctx, k_unprefix<RootHead>, blocks_for(m, TB), TB, f, (const uint64_t *)mo->layer[layer].root_cdf, 1,
+               (const uint32_t *)nullptr, m, out);
     } else {
         const OwnerBits ob{g.own_out, g.own_in, g.own_multi};
         bool o = P.tout[q] != 0;
-        DirHead f{o ? g.out_t : g.in_t, o ? ob.out : ob.in, layer, P.wdelta};
-        launch(ctx, k_unprefix<DirHead>, blocks_for(m, TB), TB, f, mo->layer[layer].pref_dir[P.tslot[q]],
-                                                              o ? g.out_gid : g.in_gid, m, out);
+        DirHead f{o ? g.out_t : g.in_t, o ? ob.out : ob.in, layer, wv};
+        launch(ctx, k_unprefix<DirHead>, blocks_for(m, TB), TB, f,
+               (const uint64_t *)mo->pref_dir[P.tslot[q]] + layer, 2, (const uint32_t *)(o ? g.out_gid : g.in_gid),
+               m, out);
         rc = check_cuda(ctx, cudaStreamSynchronize(st), "export");
     }
     copy_d2h(ctx, host_out, out, (size_t)m * 8);
