@@ -19,7 +19,9 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libtimest_gb300.so")
+# TIMEST_GB300_LIB names another build of the same library (e.g. one compiled
+# with different launch bounds for a comparison)
+LIB_PATH = os.environ.get("TIMEST_GB300_LIB") or os.path.join(_HERE, "_build", "libtimest_gb300.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "timest.h")
 
 TM_OK, TM_E_ARG, TM_E_DUP, TM_E_SELFLOOP, TM_E_MOTIF, TM_E_NOMEM, TM_E_OVERFLOW, TM_E_STATE, TM_E_TIMEOUT, \

@@ -66,6 +66,11 @@ constexpr size_t os_smem(int np)
 struct RsSet {
     const uint32_t *kin, *p0in, *p1in;
     uint32_t *kout, *p0out, *p1out;
+    const uint32_t *p2in = nullptr;
+    uint32_t *p2out = nullptr;
+    const uint32_t *p3in = nullptr;
+    uint32_t *p3out = nullptr;
+    uint32_t *inv = nullptr;   // when set: inv[payload 0] = output position (the inverse permutation)
 };
 struct RsJobs {
     RsSet s[2];
@@ -140,9 +145,12 @@ __device__ __forceinline__ void os_block_scan512(uint32_t *vals /* smem [512] in
 // Keys (and payloads) of one tile are ranked stably per warp chunk: a warp
 // whose 32 digits agree takes its ranks directly; otherwise the lanes with
 // the same digit are found with one ballot per digit bit.  A null p0in reads
-// payload 0 as the key's input index.
+// payload 0 as the key's input index.  With inv set (a final pass), each
+// element also writes its output position at inv[payload 0].  Payloads 0-2
+// are held in registers from the start; payload 3 is read when the tile is
+// placed in shared memory.
 template <int NP>
-__global__ void __launch_bounds__(OS_THREADS, NP >= 2 ? 3 : 4)
+__global__ void __launch_bounds__(OS_THREADS, NP >= 3 ? 2 : NP >= 2 ? 3 : 4)
     k_rs_scatter(RsJobs J, uint32_t n, int shift, int bits, uint32_t ntiles, const uint32_t *__restrict__ offs_all)
 {
     const uint32_t job = blockIdx.x >= ntiles ? 1u : 0u, tile = blockIdx.x - job * ntiles;
@@ -153,13 +161,20 @@ __global__ void __launch_bounds__(OS_THREADS, NP >= 2 ? 3 : 4)
     uint32_t *__restrict__ kout = job ? J.s[1].kout : J.s[0].kout;
     uint32_t *__restrict__ p0out = job ? J.s[1].p0out : J.s[0].p0out;
     uint32_t *__restrict__ p1out = job ? J.s[1].p1out : J.s[0].p1out;
+    const uint32_t *__restrict__ p2in = job ? J.s[1].p2in : J.s[0].p2in;
+    uint32_t *__restrict__ p2out = job ? J.s[1].p2out : J.s[0].p2out;
+    const uint32_t *__restrict__ p3in = job ? J.s[1].p3in : J.s[0].p3in;
+    uint32_t *__restrict__ p3out = job ? J.s[1].p3out : J.s[0].p3out;
+    uint32_t *__restrict__ inv = job ? J.s[1].inv : J.s[0].inv;
     const uint32_t *__restrict__ offs = offs_all + ((size_t)job * ntiles << bits);
     const uint32_t bias = job * n;   // set 1's scanned offsets start at n
     extern __shared__ __align__(16) unsigned char os_smem_buf[];
     uint32_t *s_key = reinterpret_cast<uint32_t *>(os_smem_buf);
     uint32_t *s_p0 = s_key + OS_TILE;
     uint32_t *s_p1 = s_p0 + (NP >= 1 ? OS_TILE : 0);
-    uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_p1 + (NP >= 2 ? OS_TILE : 0));
+    uint32_t *s_p2 = s_p1 + (NP >= 2 ? OS_TILE : 0);
+    uint32_t *s_p3 = s_p2 + (NP >= 3 ? OS_TILE : 0);
+    uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_p3 + (NP >= 4 ? OS_TILE : 0));
     uint16_t *s_wcnt = s_rank + OS_TILE;                                            // [warp][digit]
     uint32_t *s_tex = reinterpret_cast<uint32_t *>(s_wcnt + OS_WARPS * OS_MAXRADIX);  // digit start in the tile
     uint32_t *s_gpos = s_tex + OS_MAXRADIX;                                         // digit start in the output
@@ -172,14 +187,15 @@ __global__ void __launch_bounds__(OS_THREADS, NP >= 2 ? 3 : 4)
         s_gpos[d] = d < radix ? __ldg(offs + (size_t)d * ntiles + tile) - bias : 0u;
     const uint32_t lt = (1u << lane) - 1u;
     uint16_t *wc = s_wcnt + warp * OS_MAXRADIX;
-    constexpr int NA = NP >= 1 ? OS_ITEMS : 1, NB = NP >= 2 ? OS_ITEMS : 1;
-    uint32_t kv[OS_ITEMS], av[NA], bv[NB];
+    constexpr int NA = NP >= 1 ? OS_ITEMS : 1, NB = NP >= 2 ? OS_ITEMS : 1, NC = NP >= 3 ? OS_ITEMS : 1;
+    uint32_t kv[OS_ITEMS], av[NA], bv[NB], cv[NC];
 #pragma unroll
     for (int j = 0; j < OS_ITEMS; ++j) {   // keys and payloads in flight before any vote
         const uint32_t i = base + warp * OS_WCHUNK + j * 32 + lane;
         kv[j] = i < n ? __ldg(kin + i) : 0u;
         if (NP >= 1) av[j % NA] = i < n ? (p0in ? __ldg(p0in + i) : i) : 0u;
         if (NP >= 2) bv[j % NB] = i < n ? __ldg(p1in + i) : 0u;
+        if (NP >= 3) cv[j % NC] = i < n ? __ldg(p2in + i) : 0u;
     }
     __syncthreads();
     // ---- rank inside each warp's chunk (order: warp, item, lane)
@@ -232,6 +248,8 @@ __global__ void __launch_bounds__(OS_THREADS, NP >= 2 ? 3 : 4)
             s_key[pos] = k;
             if (NP >= 1) s_p0[pos] = av[j % NA];
             if (NP >= 2) s_p1[pos] = bv[j % NB];
+            if (NP >= 3) s_p2[pos] = cv[j % NC];
+            if (NP >= 4) s_p3[pos] = __ldg(p3in + base + li);
         }
     }
     __syncthreads();
@@ -244,6 +262,9 @@ __global__ void __launch_bounds__(OS_THREADS, NP >= 2 ? 3 : 4)
         kout[g] = k;
         if (NP >= 1) p0out[g] = s_p0[p];
         if (NP >= 2) p1out[g] = s_p1[p];
+        if (NP >= 3) p2out[g] = s_p2[p];
+        if (NP >= 4) p3out[g] = s_p3[p];
+        if (NP >= 1 && inv) inv[s_p0[p]] = g;
     }
 }
 
@@ -266,7 +287,9 @@ static int rs_prepare(tm_ctx *ctx, int np)
     // per device and cheap: set on every call
     cudaError_t e = np == 0 ? cudaFuncSetAttribute(k_rs_scatter<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem(0))
                   : np == 1 ? cudaFuncSetAttribute(k_rs_scatter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem(1))
-                            : cudaFuncSetAttribute(k_rs_scatter<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem(2));
+                  : np == 2 ? cudaFuncSetAttribute(k_rs_scatter<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem(2))
+                  : np == 3 ? cudaFuncSetAttribute(k_rs_scatter<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem(3))
+                            : cudaFuncSetAttribute(k_rs_scatter<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem(4));
     return check_cuda(ctx, e, "radix pass shared memory");
 }
 
@@ -284,8 +307,12 @@ static int rs_pass(tm_ctx *ctx, const RsJobs &in, int nsets, int np, uint32_t n,
         launch_smem(ctx, k_rs_scatter<0>, nblk, OS_THREADS, os_smem(0), in, n, sh, pb, ntiles, (const uint32_t *)counts);
     else if (np == 1)
         launch_smem(ctx, k_rs_scatter<1>, nblk, OS_THREADS, os_smem(1), in, n, sh, pb, ntiles, (const uint32_t *)counts);
-    else
+    else if (np == 2)
         launch_smem(ctx, k_rs_scatter<2>, nblk, OS_THREADS, os_smem(2), in, n, sh, pb, ntiles, (const uint32_t *)counts);
+    else if (np == 3)
+        launch_smem(ctx, k_rs_scatter<3>, nblk, OS_THREADS, os_smem(3), in, n, sh, pb, ntiles, (const uint32_t *)counts);
+    else
+        launch_smem(ctx, k_rs_scatter<4>, nblk, OS_THREADS, os_smem(4), in, n, sh, pb, ntiles, (const uint32_t *)counts);
     return check_cuda(ctx, cudaGetLastError(), "radix pass");
 }
 
@@ -333,11 +360,6 @@ int radix_sort_sets(tm_ctx *ctx, const RsHost *sets, int nsets, uint32_t n, int 
     return rc;
 }
 
-__global__ void k_iota(uint32_t *__restrict__ a, uint32_t m)
-{
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) a[i] = i;
-}
 
 // The same sort from read-only inputs into separate outputs (no copies): the
 // passes alternate between the outputs and scratch so that the last one
@@ -346,14 +368,25 @@ __global__ void k_iota(uint32_t *__restrict__ a, uint32_t m)
 struct RsTo {
     const uint32_t *key_in, *p0_in, *p1_in;
     uint32_t *key, *p0, *p1;
+    const uint32_t *p2_in = nullptr;
+    uint32_t *p2 = nullptr;
+    const uint32_t *p3_in = nullptr;
+    uint32_t *p3 = nullptr;
+    uint32_t *inv = nullptr;   // optional: inv[payload 0] = sorted position, written by the last pass
 };
+
+__global__ void k_iota2(uint32_t *__restrict__ a, uint32_t *__restrict__ b, uint32_t m)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) { if (a) a[i] = i; if (b) b[i] = i; }
+}
 
 int radix_sort_sets_to(tm_ctx *ctx, const RsTo *sets, int nsets, uint32_t n, int bits)
 {
     ScratchScope scope(ctx);
     if (nsets <= 0 || n == 0) return TM_OK;
     if (nsets > 2) return set_err(ctx, TM_E_LIMIT, "at most two arrays per radix sort");
-    const int np = sets[0].p1 ? 2 : (sets[0].p0 ? 1 : 0);
+    const int np = sets[0].p3 ? 4 : sets[0].p2 ? 3 : sets[0].p1 ? 2 : (sets[0].p0 ? 1 : 0);
     cudaStream_t st = ctx->stream;
     if (n <= 1 || bits <= 0) {
         for (int j = 0; j < nsets; ++j) {
@@ -361,9 +394,15 @@ int radix_sort_sets_to(tm_ctx *ctx, const RsTo *sets, int nsets, uint32_t n, int
             cudaMemcpyAsync(x.key, x.key_in, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
             if (np >= 1) {
                 if (x.p0_in) cudaMemcpyAsync(x.p0, x.p0_in, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
-                else launch(ctx, k_iota, (n + 255) / 256, 256, x.p0, n);
+                else launch(ctx, k_iota2, (n + 255) / 256, 256, x.p0, (uint32_t *)nullptr, n);
             }
             if (np >= 2) cudaMemcpyAsync(x.p1, x.p1_in, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+            if (np >= 3) cudaMemcpyAsync(x.p2, x.p2_in, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+            if (np >= 4) cudaMemcpyAsync(x.p3, x.p3_in, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+            if (x.inv) {   // an identity order (payload 0 is then the input index)
+                if (x.p0_in) return set_err(ctx, TM_E_ARG, "internal: inverse of a sort with explicit payload 0");
+                launch(ctx, k_iota2, (n + 255) / 256, 256, x.inv, (uint32_t *)nullptr, n);
+            }
         }
         return TM_OK;
     }
@@ -375,29 +414,45 @@ int radix_sort_sets_to(tm_ctx *ctx, const RsTo *sets, int nsets, uint32_t n, int
     RsSet scr[2] = {}, dst[2] = {};
     for (int j = 0; j < nsets; ++j) {
         dst[j] = RsSet{nullptr, nullptr, nullptr, sets[j].key, sets[j].p0, sets[j].p1};
+        dst[j].p2out = sets[j].p2;
+        dst[j].p3out = sets[j].p3;
         if (npass >= 2) {
             uint32_t *k2 = (uint32_t *)salloc(ctx, (size_t)n * 4);
             uint32_t *a2 = np >= 1 ? (uint32_t *)salloc(ctx, (size_t)n * 4) : nullptr;
             uint32_t *b2 = np >= 2 ? (uint32_t *)salloc(ctx, (size_t)n * 4) : nullptr;
-            if (!k2 || (np >= 1 && !a2) || (np >= 2 && !b2)) return TM_E_NOMEM;
+            uint32_t *c2 = np >= 3 ? (uint32_t *)salloc(ctx, (size_t)n * 4) : nullptr;
+            uint32_t *d2 = np >= 4 ? (uint32_t *)salloc(ctx, (size_t)n * 4) : nullptr;
+            if (!k2 || (np >= 1 && !a2) || (np >= 2 && !b2) || (np >= 3 && !c2) || (np >= 4 && !d2)) return TM_E_NOMEM;
             scr[j] = RsSet{nullptr, nullptr, nullptr, k2, a2, b2};
+            scr[j].p2out = c2;
+            scr[j].p3out = d2;
         }
     }
     int rc = rs_prepare(ctx, np);
     if (rc) return rc;
     RsJobs in{};
-    for (int j = 0; j < nsets; ++j) in.s[j] = RsSet{sets[j].key_in, sets[j].p0_in, sets[j].p1_in, nullptr, nullptr, nullptr};
+    for (int j = 0; j < nsets; ++j) {
+        in.s[j] = RsSet{sets[j].key_in, sets[j].p0_in, sets[j].p1_in, nullptr, nullptr, nullptr};
+        in.s[j].p2in = sets[j].p2_in;
+        in.s[j].p3in = sets[j].p3_in;
+    }
     for (int pass = 0, sh = 0; pass < npass && rc == TM_OK; ++pass) {
         const int left = npass - pass, pb = (bits - sh + left - 1) / left;
         // pass i writes the outputs when npass - 1 - i is even, else scratch
         const bool to_dst = ((npass - 1 - pass) & 1) == 0;
         for (int j = 0; j < nsets; ++j) {
             const RsSet &o = to_dst ? dst[j] : scr[j];
-            in.s[j].kout = o.kout; in.s[j].p0out = o.p0out; in.s[j].p1out = o.p1out;
+            in.s[j].kout = o.kout; in.s[j].p0out = o.p0out; in.s[j].p1out = o.p1out; in.s[j].p2out = o.p2out;
+            in.s[j].p3out = o.p3out;
+            in.s[j].inv = pass == npass - 1 ? sets[j].inv : nullptr;
         }
         rc = rs_pass(ctx, in, nsets, np, n, ntiles, sh, pb, counts);
-        for (int j = 0; j < nsets; ++j)
-            in.s[j] = RsSet{in.s[j].kout, in.s[j].p0out, in.s[j].p1out, nullptr, nullptr, nullptr};
+        for (int j = 0; j < nsets; ++j) {
+            RsSet nx{in.s[j].kout, in.s[j].p0out, in.s[j].p1out, nullptr, nullptr, nullptr};
+            nx.p2in = in.s[j].p2out;
+            nx.p3in = in.s[j].p3out;
+            in.s[j] = nx;
+        }
         sh += pb;
     }
     return rc;
@@ -598,31 +653,11 @@ __global__ void k_owner_bits(const uint32_t *__restrict__ out_src, const uint32_
     }
 }
 
-__global__ void k_gather2(const uint32_t *__restrict__ idx, uint32_t m, const uint32_t *__restrict__ x,
-                          const uint32_t *__restrict__ y, uint32_t *__restrict__ ox, uint32_t *__restrict__ oy)
-{
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    uint32_t g = idx[i];
-    ox[i] = x[g];
-    if (y && oy) oy[i] = y[g];
-}
-
-// Two independent gathers (set = blockIdx.y) in one launch.
-struct G2 {
-    const uint32_t *idx, *x, *y;
-    uint32_t *ox, *oy;
-};
-__global__ void k_gather2_pair(G2 a, G2 b, uint32_t m)
+// out[perm[i]] = i
+__global__ void k_invert(const uint32_t *__restrict__ perm, uint32_t m, uint32_t *__restrict__ out)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    const bool s1 = blockIdx.y != 0;   // per-field selects keep the parameters out of local memory
-    const uint32_t *idx = s1 ? b.idx : a.idx, *x = s1 ? b.x : a.x, *y = s1 ? b.y : a.y;
-    uint32_t *ox = s1 ? b.ox : a.ox, *oy = s1 ? b.oy : a.oy;
-    const uint32_t g = idx[i];
-    ox[i] = x[g];
-    if (y && oy) oy[i] = y[g];
+    if (i < m) out[perm[i]] = i;
 }
 
 // off[v] = first position whose sorted key is >= v, for v in [0, n].  With
@@ -649,34 +684,19 @@ __global__ void k_pair_heads(const uint32_t *__restrict__ msrc, const uint32_t *
 }
 
 __global__ void k_pair_fill(const uint32_t *__restrict__ msrc, const uint32_t *__restrict__ mdst,
-                            const uint32_t *__restrict__ mgid, const uint32_t *__restrict__ head,
-                            const uint32_t *__restrict__ pid_excl, uint32_t m, uint32_t *__restrict__ pair_off,
-                            uint32_t *__restrict__ pair_src, uint32_t *__restrict__ pair_dst,
-                            uint32_t *__restrict__ g_pair)
+                            const uint32_t *__restrict__ head, const uint32_t *__restrict__ pid_excl, uint32_t m,
+                            uint32_t *__restrict__ pair_off, uint32_t *__restrict__ pair_src,
+                            uint32_t *__restrict__ pair_dst)
 {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
-    uint32_t pid = pid_excl[i] + head[i] - 1u;
     if (head[i]) {
+        const uint32_t pid = pid_excl[i];
         pair_off[pid] = i;
         pair_src[pid] = msrc[i];
         pair_dst[pid] = mdst[i];
     }
-    g_pair[mgid[i]] = pid;
-    if (i == m - 1) pair_off[pid + 1] = m;   // the end of the last pair's list
-}
-
-// reverse pair of every pair (kNone if absent); np_dev = number of pairs
-__global__ void k_rev_pairs(const uint32_t *__restrict__ pair_src, const uint32_t *__restrict__ pair_dst,
-                            const uint32_t *__restrict__ vpair_off, const uint32_t *__restrict__ np_dev,
-                            uint32_t *__restrict__ rev)
-{
-    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= *np_dev) return;
-    uint32_t u = pair_src[p], v = pair_dst[p];
-    uint32_t lo = vpair_off[v], hi = vpair_off[v + 1];
-    uint32_t r = lower_idx(pair_dst, lo, hi, u);
-    rev[p] = (r < hi && pair_dst[r] == u) ? r : kNone;
+    if (i == m - 1) pair_off[pid_excl[i] + head[i]] = m;   // the end of the last pair's list
 }
 
 // where each list time falls in the same vertex's other list
@@ -696,16 +716,6 @@ __global__ void k_cross_rank(XR a, XR b, uint32_t m)
     uint32_t *xrank = s1 ? b.xrank : a.xrank;
     const uint32_t z = owner[i];
     xrank[i] = lower_idx(other_t, other_off[z], other_off[z + 1], own_t[i]);
-}
-
-// inverses of two position -> edge-id permutations (set = blockIdx.y)
-__global__ void k_inverse_pair(const uint32_t *__restrict__ gid0, const uint32_t *__restrict__ gid1, uint32_t m,
-                               uint32_t *__restrict__ pos0, uint32_t *__restrict__ pos1)
-{
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    if (blockIdx.y) pos1[gid1[i]] = i;
-    else pos0[gid0[i]] = i;
 }
 
 inline unsigned blocks_for(uint64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
@@ -798,7 +808,7 @@ int build_csr(tm_ctx *ctx)
         const size_t mf = (size_t)m, a_m = align256((mf ? mf : 1) * 4), a_n = align256(((size_t)n + 1) * 4);
         const size_t a_b = align256((mf / 32 + 1) * 4);
         // (the pair tables are sized by m too: the pair count is read only at the end)
-        if (!gblock_open(ctx, gb, 26 * a_m + 256 + 3 * a_n + 3 * a_b)) return TM_E_NOMEM;
+        if (!gblock_open(ctx, gb, 21 * a_m + 256 + 3 * a_n + 3 * a_b)) return TM_E_NOMEM;
     }
     g.g_t = gtake(gb, m); g.g_src = gtake(gb, m); g.g_dst = gtake(gb, m);
     if (!g.g_t || !g.g_src || !g.g_dst) return TM_E_NOMEM;
@@ -873,47 +883,57 @@ int build_csr(tm_ctx *ctx)
     sec.reset(new PhaseScope(ctx, TM_PH_CSR_OUT));
     g.out_gid = gtake(gb, m); g.out_t = gtake(gb, m); g.out_nbr = gtake(gb, m); g.out_off = gtake(gb, (size_t)n + 1);
     g.in_gid = gtake(gb, m); g.in_t = gtake(gb, m); g.in_nbr = gtake(gb, m); g.in_off = gtake(gb, (size_t)n + 1);
-    g.out_src = gtake(gb, m); g.out_pair = gtake(gb, m); g.in_dst = gtake(gb, m); g.in_pair = gtake(gb, m);
+    g.out_src = gtake(gb, m); g.in_dst = gtake(gb, m);
     g.out_xrank = gtake(gb, m); g.in_xrank = gtake(gb, m); g.out_pos = gtake(gb, m); g.in_pos = gtake(gb, m);
     if (!g.out_gid || !g.out_t || !g.out_nbr || !g.out_off || !g.in_gid || !g.in_t || !g.in_nbr || !g.in_off ||
-        !g.out_src || !g.out_pair || !g.in_dst || !g.in_pair || !g.out_xrank || !g.in_xrank || !g.out_pos || !g.in_pos)
+        !g.out_src || !g.in_dst || !g.out_xrank || !g.in_xrank || !g.out_pos || !g.in_pos)
         return TM_E_NOMEM;
+    g.out_to_in = gtake(gb, m); g.in_to_out = gtake(gb, m);
+    if (!g.out_to_in || !g.in_to_out) return TM_E_NOMEM;
     if (m) {
-        // payload = the input index: gid
-        RsTo sets[2] = {{g.g_src, nullptr, nullptr, g.out_src, g.out_gid, nullptr},
-                        {g.g_dst, nullptr, nullptr, g.in_dst, g.in_gid, nullptr}};
-        rc = radix_sort_sets_to(ctx, sets, 2, m, vbits);
+        // payloads: the input index (gid), t' and the other endpoint, so every
+        // list array comes out of the sort (no gathers); the last pass also
+        // writes each edge's list position by gid (the inverse permutation).
+        // The in-list sort then carries each edge's out-list position (read in
+        // GLOBAL order), which gives the in -> out map directly.
+        RsTo os{g.g_src, nullptr, g.g_t, g.out_src, g.out_gid, g.out_t};
+        os.p2_in = g.g_dst; os.p2 = g.out_nbr; os.inv = g.out_pos;
+        rc = radix_sort_sets_to(ctx, &os, 1, m, vbits);
+        if (rc) return rc;
+        RsTo is{g.g_dst, nullptr, g.g_t, g.in_dst, g.in_gid, g.in_t};
+        is.p2_in = g.g_src; is.p2 = g.in_nbr; is.p3_in = g.out_pos; is.p3 = g.in_to_out; is.inv = g.in_pos;
+        rc = radix_sort_sets_to(ctx, &is, 1, m, vbits);
         if (rc) return rc;
     }
     sec.reset();
     sec.reset(new PhaseScope(ctx, TM_PH_CSR_IN));
-    if (m) {
-        launch(ctx, k_gather2_pair, dim3(blocks_for(m, TB), 2), TB, G2{g.out_gid, g.g_t, g.g_dst, g.out_t, g.out_nbr},
-               G2{g.in_gid, g.g_t, g.g_src, g.in_t, g.in_nbr}, m);
-    }
     launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, g.out_src, m, n, g.out_off, nullptr);
     launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, g.in_dst, m, n, g.in_off, nullptr);
     uint32_t *key = S0, *tmp = D0;
     // ---- multi-edge order: stable re-sort of the IN order by source
     sec.reset();
     sec.reset(new PhaseScope(ctx, TM_PH_CSR_MULTI));
-    g.multi_t = gtake(gb, m); g.g_pair = gtake(gb, m);
+    g.multi_t = gtake(gb, m);
     uint32_t *multi_gid = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);   // edge id per multi position
-    g.out_to_in = gtake(gb, m); g.in_to_out = gtake(gb, m); g.multi_to_out = gtake(gb, m); g.multi_to_in = gtake(gb, m);
+    g.multi_to_out = gtake(gb, m);
     g.vpair_off = gtake(gb, (size_t)n + 1);
     g.own_out = gtake(gb, (size_t)m / 32 + 1); g.own_in = gtake(gb, (size_t)m / 32 + 1);
     g.own_multi = gtake(gb, (size_t)m / 32 + 1);
-    if (!multi_gid || !g.multi_t || !g.g_pair || !g.vpair_off || !g.out_to_in || !g.in_to_out ||
-        !g.multi_to_out || !g.multi_to_in || !g.own_out || !g.own_in || !g.own_multi)
+    if (!multi_gid || !g.multi_t || !g.vpair_off || !g.multi_to_out || !g.own_out || !g.own_in || !g.own_multi)
         return TM_E_NOMEM;
     uint32_t np = 0;
     if (m) {
         {
-            RsTo ms{g.in_nbr, g.in_gid, nullptr, key, multi_gid, nullptr};
+            // payloads: gid, t' and the destination, straight into the
+            // multi-edge arrays
+            RsTo ms{g.in_nbr, g.in_gid, g.in_t, key, multi_gid, g.multi_t};
+            ms.p2_in = g.in_dst;
+            ms.p2 = tmp;
+            ms.p3_in = g.in_to_out;       // -> each multi-edge entry's out-list position
+            ms.p3 = g.multi_to_out;
             rc = radix_sort_sets_to(ctx, &ms, 1, m, vbits);
             if (rc) return rc;
         }
-        launch(ctx, k_gather2, blocks_for(m, TB), TB, multi_gid, m, g.g_t, g.g_dst, g.multi_t, tmp);
         // key = pair src, tmp = pair dst per multi position
         uint32_t *head = T0;
         uint32_t *pid = (uint32_t *)salloc(ctx, (size_t)m * 4);
@@ -926,22 +946,15 @@ int build_csr(tm_ctx *ctx)
         // the pair tables are m-sized slots of the graph block
         g.pair_off = gtake(gb, (size_t)m + 1);
         g.pair_dst = gtake(gb, m);
-        g.rev_pair = gtake(gb, m);
         uint32_t *pair_src = (uint32_t *)salloc(ctx, (size_t)m * 4);
-        if (!g.pair_off || !g.pair_dst || !g.rev_pair || !pair_src) return TM_E_NOMEM;
-        launch(ctx, k_pair_fill, blocks_for(m, TB), TB, key, tmp, multi_gid, head, pid, m, g.pair_off, pair_src,
-                                                      g.pair_dst, g.g_pair);
+        if (!g.pair_off || !g.pair_dst || !pair_src) return TM_E_NOMEM;
+        launch(ctx, k_pair_fill, blocks_for(m, TB), TB, (const uint32_t *)key, (const uint32_t *)tmp,
+               (const uint32_t *)head, (const uint32_t *)pid, m, g.pair_off, pair_src, g.pair_dst);
         launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, pair_src, m, n, g.vpair_off, (const uint32_t *)dnp);
-        launch(ctx, k_rev_pairs, blocks_for(m, TB), TB, pair_src, g.pair_dst, g.vpair_off, (const uint32_t *)dnp,
-               g.rev_pair);
         copy_d2h(ctx, ctx->status_host + 1, dnp, 4);   // pinned: read after the closing synchronize
-        // list positions by edge id; then, per out-/in-list position, its pair
-        // id and its position in the other list (one pass over each order)
-        launch(ctx, k_inverse_pair, dim3(blocks_for(m, TB), 2), TB, (const uint32_t *)g.out_gid,
-               (const uint32_t *)g.in_gid, m, g.out_pos, g.in_pos);
-        launch(ctx, k_gather2_pair, dim3(blocks_for(m, TB), 2), TB, G2{g.out_gid, g.g_pair, g.in_pos, g.out_pair, g.out_to_in},
-               G2{g.in_gid, g.g_pair, g.out_pos, g.in_pair, g.in_to_out}, m);
-        launch(ctx, k_gather2, blocks_for(m, TB), TB, multi_gid, m, g.out_pos, g.in_pos, g.multi_to_out, g.multi_to_in);
+        // per out-list position its in-list position: the inverse of the
+        // in -> out map
+        launch(ctx, k_invert, blocks_for(m, TB), TB, (const uint32_t *)g.in_to_out, m, g.out_to_in);
         // cross ranks between a vertex's out- and in-lists
         launch(ctx, k_cross_rank, dim3(blocks_for(m, TB), 2), TB, XR{g.out_t, g.out_src, g.in_off, g.in_t, g.out_xrank},
                XR{g.in_t, g.in_dst, g.out_off, g.out_t, g.in_xrank}, m);
@@ -954,7 +967,6 @@ int build_csr(tm_ctx *ctx)
         if (!gblock_open(ctx, pbk, 3 * 256)) return TM_E_NOMEM;
         g.pair_off = gtake(pbk, 1);
         g.pair_dst = gtake(pbk, 1);
-        g.rev_pair = gtake(pbk, 1);
         cudaMemsetAsync(g.pair_off, 0, 4, st);
         launch(ctx, k_offsets, 1, TB, key, 0, n, g.vpair_off, nullptr);
     }

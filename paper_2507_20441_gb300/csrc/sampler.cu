@@ -33,11 +33,11 @@ namespace {
 typedef SampleAcc Acc;
 
 // Per-thread sample state: rows 0..6 tree-edge sources, 7..13 destinations,
-// 14..20 times, 21..27 pair ids, 28..34 edge ids, 35..42 the vertex map,
+// 14..20 times, 21..27 edge ids, 28..35 the vertex map,
 // `stride` apart.  The sampler keeps them in (L1-cached) local memory; a
 // shared-memory layout measured slower because it shrinks L1 for the
 // searches.
-constexpr int kRecRows = 5 * kMaxTree + kMaxV;
+constexpr int kRecRows = 4 * kMaxTree + kMaxV;
 
 struct Recs {
     uint32_t *base;
@@ -45,9 +45,8 @@ struct Recs {
     __device__ __forceinline__ uint32_t &src(int q) { return base[(0 * kMaxTree + q) * stride]; }
     __device__ __forceinline__ uint32_t &dst(int q) { return base[(1 * kMaxTree + q) * stride]; }
     __device__ __forceinline__ uint32_t &t(int q) { return base[(2 * kMaxTree + q) * stride]; }
-    __device__ __forceinline__ uint32_t &pair(int q) { return base[(3 * kMaxTree + q) * stride]; }
-    __device__ __forceinline__ uint32_t &gid(int q) { return base[(4 * kMaxTree + q) * stride]; }
-    __device__ __forceinline__ uint32_t &phi(int v) { return base[(5 * kMaxTree + v) * stride]; }
+    __device__ __forceinline__ uint32_t &gid(int q) { return base[(3 * kMaxTree + q) * stride]; }
+    __device__ __forceinline__ uint32_t &phi(int v) { return base[(4 * kMaxTree + v) * stride]; }
 };
 
 // Multi-edge list range of pair (u, v), or an empty range.
@@ -196,7 +195,6 @@ __device__ __forceinline__ void load_edge(const DevGraph &g, uint32_t gid, Recs 
     R.src(q) = __ldg(g.g_src + gid);
     R.dst(q) = __ldg(g.g_dst + gid);
     R.t(q) = __ldg(g.g_t + gid);
-    R.pair(q) = __ldg(g.g_pair + gid);
 }
 
 // Alg. 4: 0 when the sampled tree is valid, else the reject reason (1 the
@@ -302,15 +300,14 @@ __device__ __forceinline__ int sample_root(const DevPlan &P, const SampleJob &J,
 
 // One tree edge of Alg. 3: the edge of tree node q, drawn by weight from its
 // candidate list at the meeting vertex given its parent's edge (source ps,
-// destination pd, time pt, pair id ppair, edge id pgid), in layer p whose
+// destination pd, time pt, edge id pgid), in layer p whose
 // window spans [wlo, whi].  Sets the child's time, endpoints and, for a node
-// with children or when `ids` is set, its edge id and pair id; 0, or -1 on an
+// with children or when `ids` is set, its edge id; 0, or -1 on an
 // internal inconsistency (latched as ST_BADSTATE).
 __device__ __forceinline__ int sample_child(const DevGraph &g, const DevPlan &P, const SampleJob &J, int q, int p,
                                             uint64_t wlo, uint64_t whi, SampleRng &rng, uint32_t *status,
-                                            uint32_t ps, uint32_t pd, uint32_t pt, uint32_t ppair, uint32_t pgid,
-                                            bool ids, uint32_t &ct, uint32_t &cs, uint32_t &cd, uint32_t &cgid,
-                                            uint32_t &cpair)
+                                            uint32_t ps, uint32_t pd, uint32_t pt, uint32_t pgid,
+                                            bool ids, uint32_t &ct, uint32_t &cs, uint32_t &cd, uint32_t &cgid)
 {
     const uint64_t d = (uint64_t)P.delta;
     const bool zs = P.tzside[q] != 0, out = P.tout[q] != 0, leaf = P.tleaf[q] != 0;
@@ -333,7 +330,9 @@ __device__ __forceinline__ int sample_child(const DevGraph &g, const DevPlan &P,
     uint32_t a, b, beg;
     const uint32_t *tarr;
     child_range(g, zs ? 1 : 0, out, zg, ppos, pt, P.tlater[q] != 0, tlo, thi, a, b, beg, tarr);
-    const uint32_t pe = !P.c2 ? kNone : (out == !zs) ? ppair : __ldg(g.rev_pair + ppair);
+    // the excluded multi-edge list (Constraint 2): zg -> og for a child
+    // leaving the meeting vertex, og -> zg for one entering it
+    const uint32_t pe = !P.c2 ? kNone : out ? pair_of(g, zg, og) : pair_of(g, og, zg);
     uint32_t ea = 0, eb = 0, pb = 0;
     if (pe != kNone) {
         pb = __ldg(g.pair_off + pe);
@@ -389,11 +388,8 @@ __device__ __forceinline__ int sample_child(const DevGraph &g, const DevPlan &P,
     ct = __ldg(tarr + xl);
     cs = out ? zg : other;
     cd = out ? other : zg;
-    // edge and pair ids are read again only for a node with children (or a trace)
-    if (!leaf || ids) {
-        cgid = __ldg(gids + xl);
-        if (!leaf) cpair = __ldg(g.g_pair + cgid);
-    }
+    // the edge id is read only for a node with children (or a trace)
+    if (!leaf || ids) cgid = __ldg(gids + xl);
     return 0;
 }
 
@@ -412,8 +408,8 @@ __device__ int sample_tree(const DevGraph &g, const DevPlan &P, const SampleJob 
     load_edge(g, root, R, 0);
     for (int q = 1; q < P.ntree; ++q) {
         const int pq = P.tparent[q];
-        if (sample_child(g, P, J, q, p, wlo, whi, rng, status, R.src(pq), R.dst(pq), R.t(pq), R.pair(pq), R.gid(pq),
-                         tg_out != nullptr, R.t(q), R.src(q), R.dst(q), R.gid(q), R.pair(q)))
+        if (sample_child(g, P, J, q, p, wlo, whi, rng, status, R.src(pq), R.dst(pq), R.t(pq), R.gid(pq),
+                         tg_out != nullptr, R.t(q), R.src(q), R.dst(q), R.gid(q)))
             return -1;
     }
     if (tg_out)
@@ -471,23 +467,20 @@ __device__ __forceinline__ int sample_one_reg(const DevGraph &g, const DevPlan &
     uint32_t root;
     if (sample_root(P, J, rng, status, p, wlo, whi, root)) return -1;
     // Alg. 3: the root edge, then each node from its parent (parents come first)
-    uint32_t src[NT], dst[NT], t[NT], pair[NT], gid[NT];
+    uint32_t src[NT], dst[NT], t[NT], gid[NT];
     gid[0] = root;
     src[0] = __ldg(g.g_src + root);
     dst[0] = __ldg(g.g_dst + root);
     t[0] = __ldg(g.g_t + root);
-    pair[0] = __ldg(g.g_pair + root);
 #pragma unroll
     for (int q = 1; q < NT; ++q) {
         const int pq = P.tparent[q];
-        uint32_t ps = src[0], pd = dst[0], pt = t[0], pp = pair[0], pg = gid[0];
+        uint32_t ps = src[0], pd = dst[0], pt = t[0], pg = gid[0];
 #pragma unroll
         for (int h = 1; h < q; ++h)
-            if (pq == h) { ps = src[h]; pd = dst[h]; pt = t[h]; pp = pair[h]; pg = gid[h]; }
+            if (pq == h) { ps = src[h]; pd = dst[h]; pt = t[h]; pg = gid[h]; }
         gid[q] = 0;
-        pair[q] = 0;
-        if (sample_child(g, P, J, q, p, wlo, whi, rng, status, ps, pd, pt, pp, pg, false, t[q], src[q], dst[q], gid[q],
-                         pair[q]))
+        if (sample_child(g, P, J, q, p, wlo, whi, rng, status, ps, pd, pt, pg, false, t[q], src[q], dst[q], gid[q]))
             return -1;
     }
     // Alg. 4: the vertex map (1-1), the delta span, the pi order of tree edges

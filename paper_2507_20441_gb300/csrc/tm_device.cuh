@@ -146,6 +146,15 @@ __device__ __forceinline__ void child_range(const DevGraph &g, int side, bool ou
     }
 }
 
+// The pair (multi-edge list) id of (u, v), or kNone when no edge u -> v exists:
+// a search of u's pairs, which are sorted by destination.
+__device__ __forceinline__ uint32_t pair_of(const DevGraph &g, uint32_t u, uint32_t v)
+{
+    const uint32_t lo = __ldg(g.vpair_off + u), hi = __ldg(g.vpair_off + u + 1);
+    const uint32_t p = lower_idx(g.pair_dst, lo, hi, v);
+    return (p < hi && __ldg(g.pair_dst + p) == v) ? p : kNone;
+}
+
 // First index in [lo, hi) with v[i] > x (v non-decreasing).
 __device__ __forceinline__ uint32_t upper_idx64(const uint64_t *__restrict__ v, uint32_t lo, uint32_t hi, uint64_t x)
 {

@@ -36,25 +36,24 @@ struct DevGraph {
     int64_t tmin = 0;
     uint32_t T = 0;                      // max t'
     // GLOBAL order
-    uint32_t *g_t = nullptr, *g_src = nullptr, *g_dst = nullptr, *g_pair = nullptr;
-    // out-lists: per vertex, (t', dst) order; owner (src) and pair id per position
+    uint32_t *g_t = nullptr, *g_src = nullptr, *g_dst = nullptr;
+    // out-lists: per vertex, (t', dst) order; owner (src) per position
     uint32_t *out_off = nullptr, *out_t = nullptr, *out_nbr = nullptr, *out_gid = nullptr;
-    uint32_t *out_src = nullptr, *out_pair = nullptr;
+    uint32_t *out_src = nullptr;
     uint32_t *out_xrank = nullptr;       // where each out-list time falls in the owner's in-list
     uint32_t *out_pos = nullptr;         // [gid] position of the edge in its source's out-list
-    // in-lists: per vertex, (t', src) order; owner (dst) and pair id per position
+    // in-lists: per vertex, (t', src) order; owner (dst) per position
     uint32_t *in_off = nullptr, *in_t = nullptr, *in_nbr = nullptr, *in_gid = nullptr;
-    uint32_t *in_dst = nullptr, *in_pair = nullptr;
+    uint32_t *in_dst = nullptr;
     uint32_t *in_xrank = nullptr;        // where each in-list time falls in the owner's out-list
     uint32_t *in_pos = nullptr;          // [gid] position of the edge in its destination's in-list
     // multi-edge lists: pairs sorted by (src, dst); entries in t' order
     uint32_t *vpair_off = nullptr;       // [n+1] first pair of each source vertex
     uint32_t *pair_dst = nullptr;        // [P]
     uint32_t *pair_off = nullptr;        // [P+1] into multi_*
-    uint32_t *rev_pair = nullptr;        // [P] pair (dst,src) or kNone
     uint32_t *multi_t = nullptr;
-    // position maps between the list orders (same edge): out->in, in->out, multi->out, multi->in
-    uint32_t *out_to_in = nullptr, *in_to_out = nullptr, *multi_to_out = nullptr, *multi_to_in = nullptr;
+    // position maps between the list orders (same edge): out->in, in->out, multi->out
+    uint32_t *out_to_in = nullptr, *in_to_out = nullptr, *multi_to_out = nullptr;
     // bit sets over list positions: bit x set when position x starts a new
     // owner (vertex for the out/in orders, pair for the multi order); m/32+1 words
     uint32_t *own_out = nullptr, *own_in = nullptr, *own_multi = nullptr;

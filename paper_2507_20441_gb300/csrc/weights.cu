@@ -48,7 +48,10 @@ __device__ __forceinline__ const ulonglong2 *pick_slot(const ulonglong2 *const (
 
 // Candidate ranges up to this many entries are scanned for the excluded
 // neighbour; longer ones search the excluded multi-edge list instead.
-constexpr uint32_t kScanLimit = 48;
+#ifndef TM_DP_SCAN_LIMIT
+#define TM_DP_SCAN_LIMIT 48
+#endif
+constexpr uint32_t kScanLimit = TM_DP_SCAN_LIMIT;
 
 // One side of tree node q (Claim 3.2): the product of the factors of q's
 // children that meet q at its tail (side 0) or head (side 1), for every edge
@@ -66,7 +69,9 @@ constexpr uint32_t kScanLimit = 48;
 // multi-edge list.
 // Results are written in this list order.  A root with children at both ends
 // runs side 0 (first) then side 1 (last), which reads side 0's partial
-// product and pending-overflow bit through the out->in position map.
+// product through the out->in position map, and its pending-overflow bits
+// from two bit sets of m/32 words (one per layer; a warp of side 0 writes
+// the word of its 32 positions with a ballot), small enough to stay in L2.
 // Overflow rule: a factor >= 2^64, or an exact product >= 2^64 with no zero
 // factor.
 #ifndef TM_DP_MINB
@@ -75,144 +80,161 @@ constexpr uint32_t kScanLimit = 48;
 __global__ void __launch_bounds__(256, TM_DP_MINB) k_dp(DevGraph g, DevPlan P, WinDiv wv, int q, int side, int first,
                                                         int last, ChildPrefix cp, ulonglong2 *__restrict__ wout,
                                                         const ulonglong2 *__restrict__ in,
-                                                        const uint8_t *__restrict__ pin, uint8_t *__restrict__ pout,
+                                                        const uint32_t *__restrict__ pin, uint32_t *__restrict__ pout,
                                                         uint32_t *status)
 {
     const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pos >= g.m) return;
-    const uint32_t t = __ldg((side ? g.in_t : g.out_t) + pos);
-    const uint32_t z = __ldg((side ? g.in_dst : g.out_src) + pos);
-    // the parent's other endpoint; without Constraint 2 nothing is excluded
-    const uint32_t o = P.c2 ? __ldg((side ? g.in_nbr : g.out_nbr) + pos) : kNone;
-    const uint64_t d = (uint64_t)P.delta, wd = (uint64_t)wv.d;
-    const uint32_t qt = wv.quot(t);
-    uint64_t wlo[2], whi[2], prod[2] = {1, 1};
-    bool zero[2], ovf[2] = {false, false};
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const int64_t wi = WinDiv::win_of(qt, p);
-        zero[p] = wi < 0;
-        wlo[p] = zero[p] ? 0 : (uint64_t)wi * wd;
-        whi[p] = zero[p] ? 0 : ((uint64_t)wi + 2) * wd - 1;
-    }
-    if (!first) {
-        const uint32_t xp = __ldg(g.in_to_out + pos);   // side 1 reads side 0's partial (both layers)
-        const ulonglong2 pv = __ldg(in + xp);
-        const uint32_t pb = pin[xp];
+    // whole warps stay for the pending-bit ballots of side 0
+    if (pos >= g.m && (last || (pos & ~31u) >= g.m)) return;
+    const bool live = pos < g.m;
+    uint32_t pend_bits = 0;
+    if (live) {
+        const uint32_t t = __ldg((side ? g.in_t : g.out_t) + pos);
+        const uint32_t z = __ldg((side ? g.in_dst : g.out_src) + pos);
+        // the parent's other endpoint; without Constraint 2 nothing is excluded
+        const uint32_t o = P.c2 ? __ldg((side ? g.in_nbr : g.out_nbr) + pos) : kNone;
+        const uint64_t d = (uint64_t)P.delta, wd = (uint64_t)wv.d;
+        const uint32_t qt = wv.quot(t);
+        uint64_t wlo[2], whi[2], prod[2] = {1, 1};
+        bool zero[2], ovf[2] = {false, false};
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
-            if (zero[p]) continue;
-            prod[p] = lane_of(pv, p);
-            ovf[p] = (pb >> p) & 1u;
-            if (prod[p] == 0) zero[p] = true;
+            const int64_t wi = WinDiv::win_of(qt, p);
+            zero[p] = wi < 0;
+            wlo[p] = zero[p] ? 0 : (uint64_t)wi * wd;
+            whi[p] = zero[p] ? 0 : ((uint64_t)wi + 2) * wd - 1;
         }
-    }
-    for (int ci = 0; ci < P.nchild[q] && !(zero[0] && zero[1]); ++ci) {
-        const int c = P.child[q][ci];
-        if (P.tzside[c] != side) continue;
-        const bool out = P.tout[c] != 0, later = P.tlater[c] != 0, leaf = P.tleaf[c] != 0;
-        if (!later && t == 0) { zero[0] = zero[1] = true; break; }
-        const uint32_t *off = out ? g.out_off : g.in_off;
-        const uint32_t *tarr = out ? g.out_t : g.in_t;
-        const uint32_t *nbr = out ? g.out_nbr : g.in_nbr;
-        const uint32_t beg = __ldg(off + z), end = __ldg(off + z + 1);
-        const uint32_t base = ((side == 0) == out) ? gallop_back(tarr, beg, pos, t)
-                                                   : __ldg((side == 0 ? g.out_xrank : g.in_xrank) + pos);
-        // per-layer ranges [a[p], b[p]) with times in [lo[p], hi[p]]
-        uint32_t a[2], b[2];
-        uint64_t lo[2], hi[2];
-        if (later) {
-            const uint64_t l0 = (uint64_t)t + 1, hu = (uint64_t)t + d;
-            const uint32_t a0 = gallop_idx(tarr, base, end, l0);
-            const uint32_t bu = gallop_idx(tarr, a0, end, hu + 1);
+        if (!first) {
+            const uint32_t xp = __ldg(g.in_to_out + pos);   // side 1 reads side 0's partial (both layers)
+            const ulonglong2 pv = __ldg(in + xp);
+            const uint32_t words = (g.m + 31) >> 5;
+            const uint32_t pb = ((__ldg(pin + (xp >> 5)) >> (xp & 31)) & 1u) |
+                                (((__ldg(pin + words + (xp >> 5)) >> (xp & 31)) & 1u) << 1);
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
-                lo[p] = l0;
-                hi[p] = hu < whi[p] ? hu : whi[p];
-                a[p] = a0;
-                b[p] = (zero[p] || hi[p] == hu) ? bu : lower_idx(tarr, a0, bu, hi[p] + 1);
-                if (lo[p] > hi[p]) zero[p] = true;
-            }
-        } else {
-            const uint64_t h0 = (uint64_t)t - 1, lu = (uint64_t)t >= d ? (uint64_t)t - d : 0;
-            const uint32_t au = gallop_back(tarr, beg, base, lu);
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                hi[p] = h0;
-                lo[p] = lu > wlo[p] ? lu : wlo[p];
-                b[p] = base;
-                a[p] = (zero[p] || lo[p] == lu) ? au : lower_idx(tarr, au, base, lo[p]);
-                if (lo[p] > hi[p]) zero[p] = true;
+                if (zero[p]) continue;
+                prod[p] = lane_of(pv, p);
+                ovf[p] = (pb >> p) & 1u;
+                if (prod[p] == 0) zero[p] = true;
             }
         }
-        if (zero[0] && zero[1]) break;
-        const ulonglong2 *Pd = leaf ? nullptr : pick_slot(cp.pd, P.tslot[c]);
-        uint64_t excl[2] = {0, 0};
-        // the union of the live layers' ranges
-        uint32_t ua = 0xFFFFFFFFu, ub = 0;
-#pragma unroll
-        for (int p = 0; p < 2; ++p)
-            if (!zero[p]) { ua = min(ua, a[p]); ub = max(ub, b[p]); }
-        if (ub <= ua || ub - ua <= kScanLimit) {
-            for (uint32_t x = ua; x < ub; ++x) {
-                if (__ldg(nbr + x) != o) continue;
-                ulonglong2 wx2 = make_ulonglong2(1, 1);
-                if (!leaf) {
-                    // the entry's weight: its prefix minus the previous entry's in
-                    // the same (vertex, window) segment
-                    const ulonglong2 px = __ldg(Pd + x);
-                    const ulonglong2 pp = x > beg ? __ldg(Pd + x - 1) : make_ulonglong2(0, 0);
-                    const uint32_t tp = x > beg ? __ldg(tarr + x - 1) : 0;
-                    wx2.x = px.x - ((x > beg && (uint64_t)tp >= wlo[0]) ? pp.x : 0);
-                    wx2.y = px.y - ((x > beg && (uint64_t)tp >= wlo[1]) ? pp.y : 0);
-                }
-#pragma unroll
-                for (int p = 0; p < 2; ++p)
-                    if (!zero[p] && x >= a[p] && x < b[p]) excl[p] += lane_of(wx2, p);
-            }
-        } else {
-            const uint32_t pr = __ldg((side ? g.in_pair : g.out_pair) + pos);
-            const uint32_t pe = !P.c2 ? kNone : (out == (side == 0)) ? pr : __ldg(g.rev_pair + pr);
-            if (pe != kNone) {
-                const uint32_t xb = __ldg(g.pair_off + pe), xe = __ldg(g.pair_off + pe + 1);
+        for (int ci = 0; ci < P.nchild[q] && !(zero[0] && zero[1]); ++ci) {
+            const int c = P.child[q][ci];
+            if (P.tzside[c] != side) continue;
+            const bool out = P.tout[c] != 0, later = P.tlater[c] != 0, leaf = P.tleaf[c] != 0;
+            if (!later && t == 0) { zero[0] = zero[1] = true; break; }
+            const uint32_t *off = out ? g.out_off : g.in_off;
+            const uint32_t *tarr = out ? g.out_t : g.in_t;
+            const uint32_t *nbr = out ? g.out_nbr : g.in_nbr;
+            const uint32_t beg = __ldg(off + z), end = __ldg(off + z + 1);
+            const uint32_t base = ((side == 0) == out) ? gallop_back(tarr, beg, pos, t)
+                                                       : __ldg((side == 0 ? g.out_xrank : g.in_xrank) + pos);
+            // per-layer ranges [a[p], b[p]) with times in [lo[p], hi[p]]
+            uint32_t a[2], b[2];
+            uint64_t lo[2], hi[2];
+            if (later) {
+                const uint64_t l0 = (uint64_t)t + 1, hu = (uint64_t)t + d;
+                const uint32_t a0 = gallop_idx(tarr, base, end, l0);
+                const uint32_t bu = gallop_idx(tarr, a0, end, hu + 1);
 #pragma unroll
                 for (int p = 0; p < 2; ++p) {
-                    if (zero[p]) continue;
-                    const uint32_t ea = lower_idx(g.multi_t, xb, xe, lo[p]);
-                    const uint32_t eb = gallop_idx(g.multi_t, ea, xe, hi[p] + 1);
-                    if (eb <= ea) continue;
-                    if (leaf) {
-                        excl[p] = eb - ea;
-                    } else {
-                        const ulonglong2 *Pm = pick_slot(cp.pm, P.tslot[c]);
-                        const uint64_t bs = (ea > xb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo[p])
-                                                ? lane_of(__ldg(Pm + ea - 1), p) : 0;
-                        excl[p] = lane_of(__ldg(Pm + eb - 1), p) - bs;
+                    lo[p] = l0;
+                    hi[p] = hu < whi[p] ? hu : whi[p];
+                    a[p] = a0;
+                    b[p] = (zero[p] || hi[p] == hu) ? bu : lower_idx(tarr, a0, bu, hi[p] + 1);
+                    if (lo[p] > hi[p]) zero[p] = true;
+                }
+            } else {
+                const uint64_t h0 = (uint64_t)t - 1, lu = (uint64_t)t >= d ? (uint64_t)t - d : 0;
+                const uint32_t au = gallop_back(tarr, beg, base, lu);
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    hi[p] = h0;
+                    lo[p] = lu > wlo[p] ? lu : wlo[p];
+                    b[p] = base;
+                    a[p] = (zero[p] || lo[p] == lu) ? au : lower_idx(tarr, au, base, lo[p]);
+                    if (lo[p] > hi[p]) zero[p] = true;
+                }
+            }
+            if (zero[0] && zero[1]) break;
+            const ulonglong2 *Pd = leaf ? nullptr : pick_slot(cp.pd, P.tslot[c]);
+            uint64_t excl[2] = {0, 0};
+            // the union of the live layers' ranges
+            uint32_t ua = 0xFFFFFFFFu, ub = 0;
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+                if (!zero[p]) { ua = min(ua, a[p]); ub = max(ub, b[p]); }
+            if (ub <= ua || ub - ua <= kScanLimit) {
+                for (uint32_t x = ua; x < ub; ++x) {
+                    if (__ldg(nbr + x) != o) continue;
+                    ulonglong2 wx2 = make_ulonglong2(1, 1);
+                    if (!leaf) {
+                        // the entry's weight: its prefix minus the previous entry's in
+                        // the same (vertex, window) segment
+                        const ulonglong2 px = __ldg(Pd + x);
+                        const ulonglong2 pp = x > beg ? __ldg(Pd + x - 1) : make_ulonglong2(0, 0);
+                        const uint32_t tp = x > beg ? __ldg(tarr + x - 1) : 0;
+                        wx2.x = px.x - ((x > beg && (uint64_t)tp >= wlo[0]) ? pp.x : 0);
+                        wx2.y = px.y - ((x > beg && (uint64_t)tp >= wlo[1]) ? pp.y : 0);
+                    }
+#pragma unroll
+                    for (int p = 0; p < 2; ++p)
+                        if (!zero[p] && x >= a[p] && x < b[p]) excl[p] += lane_of(wx2, p);
+                }
+            } else {
+                // the excluded multi-edge list: z -> o for a child leaving z, o -> z
+                // for one entering it
+                const uint32_t pe = !P.c2 ? kNone : out ? pair_of(g, z, o) : pair_of(g, o, z);
+                if (pe != kNone) {
+                    const uint32_t xb = __ldg(g.pair_off + pe), xe = __ldg(g.pair_off + pe + 1);
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        if (zero[p]) continue;
+                        const uint32_t ea = lower_idx(g.multi_t, xb, xe, lo[p]);
+                        const uint32_t eb = gallop_idx(g.multi_t, ea, xe, hi[p] + 1);
+                        if (eb <= ea) continue;
+                        if (leaf) {
+                            excl[p] = eb - ea;
+                        } else {
+                            const ulonglong2 *Pm = pick_slot(cp.pm, P.tslot[c]);
+                            const uint64_t bs = (ea > xb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo[p])
+                                                    ? lane_of(__ldg(Pm + ea - 1), p) : 0;
+                            excl[p] = lane_of(__ldg(Pm + eb - 1), p) - bs;
+                        }
                     }
                 }
             }
-        }
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            if (zero[p]) continue;
-            uint64_t sum;
-            if (leaf) {
-                sum = (uint64_t)(b[p] - a[p]) - excl[p];
-            } else if (b[p] > a[p]) {
-                const uint64_t top = lane_of(__ldg(Pd + b[p] - 1), p);
-                const uint64_t pbase = (a[p] > beg && (uint64_t)__ldg(tarr + a[p] - 1) >= wlo[p])
-                                           ? lane_of(__ldg(Pd + a[p] - 1), p) : 0;
-                sum = top - pbase - excl[p];
-            } else {
-                sum = 0;
+            for (int p = 0; p < 2; ++p) {
+                if (zero[p]) continue;
+                uint64_t sum;
+                if (leaf) {
+                    sum = (uint64_t)(b[p] - a[p]) - excl[p];
+                } else if (b[p] > a[p]) {
+                    const uint64_t top = lane_of(__ldg(Pd + b[p] - 1), p);
+                    const uint64_t pbase = (a[p] > beg && (uint64_t)__ldg(tarr + a[p] - 1) >= wlo[p])
+                                               ? lane_of(__ldg(Pd + a[p] - 1), p) : 0;
+                    sum = top - pbase - excl[p];
+                } else {
+                    sum = 0;
+                }
+                if (sum == 0) zero[p] = true;
+                else prod[p] = mul_chk(prod[p], sum, ovf[p]);
             }
-            if (sum == 0) zero[p] = true;
-            else prod[p] = mul_chk(prod[p], sum, ovf[p]);
+        }
+        wout[pos] = make_ulonglong2(zero[0] ? 0 : prod[0], zero[1] ? 0 : prod[1]);   // both layers, one store
+        pend_bits = ((!zero[0] && ovf[0]) ? 1u : 0u) | ((!zero[1] && ovf[1]) ? 2u : 0u);
+        if (last && pend_bits) latch(status, ST_OVERFLOW);
+    }
+    if (!last) {   // side 0: the warp's pending bits, one word per layer
+        const uint32_t b0 = __ballot_sync(0xffffffffu, pend_bits & 1u);
+        const uint32_t b1 = __ballot_sync(0xffffffffu, (pend_bits >> 1) & 1u);
+        if ((threadIdx.x & 31) == 0) {
+            const uint32_t words = (g.m + 31) >> 5;
+            pout[pos >> 5] = b0;
+            pout[words + (pos >> 5)] = b1;
         }
     }
-    wout[pos] = make_ulonglong2(zero[0] ? 0 : prod[0], zero[1] ? 0 : prod[1]);   // both layers, one store
-    if (!last) pout[pos] = (uint8_t)(((!zero[0] && ovf[0]) ? 1u : 0u) | ((!zero[1] && ovf[1]) ? 2u : 0u));
-    if (last && ((!zero[0] && ovf[0]) || (!zero[1] && ovf[1]))) latch(status, ST_OVERFLOW);
 }
 
 // ---- scans over the three orders ----------------------------------------
@@ -633,7 +655,7 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     // ---- DP over tree nodes in increasing height (K3) + prefixes (K4)
     const OwnerBits ob{g.own_out, g.own_in, g.own_multi};
     ulonglong2 *w = nullptr, *pw = nullptr;   // (layer 0, layer 1) weight pairs
-    uint8_t *pend = nullptr;                  // bit p: pending overflow of layer p's partial
+    uint32_t *pend = nullptr;                 // per layer a bit set: pending overflow of a side-0 partial
     ulonglong2 *gathered = nullptr;           // a node's weights gathered into out-list order
     w = (ulonglong2 *)salloc(ctx, (size_t)(m ? m : 1) * 16);
     if (!w) return TM_E_NOMEM;
@@ -655,18 +677,18 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
             PhaseScope ph(ctx, TM_PH_DP);
             if (has[0] && has[1] && !pw) {
                 pw = (ulonglong2 *)salloc(ctx, (size_t)(m ? m : 1) * 16);
-                pend = (uint8_t *)salloc(ctx, (size_t)(m ? m : 1));
+                pend = (uint32_t *)salloc(ctx, ((size_t)m / 32 + 1) * 8);
                 if (!pw || !pend) return TM_E_NOMEM;
             }
             if (m) {
                 if (has[0] && has[1]) {
                     launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, wv, q, 0, 1, 0, cp, pw, (const ulonglong2 *)nullptr,
-                           (const uint8_t *)nullptr, pend, ctx->status);
+                           (const uint32_t *)nullptr, pend, ctx->status);
                     launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, wv, q, 1, 0, 1, cp, w, (const ulonglong2 *)pw,
-                           (const uint8_t *)pend, (uint8_t *)nullptr, ctx->status);
+                           (const uint32_t *)pend, (uint32_t *)nullptr, ctx->status);
                 } else {
                     launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, wv, q, in_order ? 1 : 0, 1, 1, cp, w,
-                           (const ulonglong2 *)nullptr, (const uint8_t *)nullptr, (uint8_t *)nullptr, ctx->status);
+                           (const ulonglong2 *)nullptr, (const uint32_t *)nullptr, (uint32_t *)nullptr, ctx->status);
                 }
             }
         }
