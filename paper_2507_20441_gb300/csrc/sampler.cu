@@ -242,19 +242,19 @@ __device__ __forceinline__ uint64_t derive_cnt(const DevGraph &g, const DevPlan 
 // edge): the sample's contribution cnt * 2 / N_phi.
 // cnt * 2 / N_phi: N_phi is 2 when the tree's span [tmin, tmax] lies in two
 // windows (both layers), else 1; N_phi counts windows of the window unit.
-__device__ __forceinline__ uint64_t over_nphi(const DevPlan &P, uint64_t cnt, uint32_t tmin, uint32_t tmax,
+// The window quotients come from the divider of the window unit.
+__device__ __forceinline__ uint64_t over_nphi(const WinDiv &wv, uint64_t cnt, uint32_t tmin, uint32_t tmax,
                                               bool &ovf)
 {
-    const uint64_t wd = (uint64_t)P.wdelta;
-    const bool two = (uint64_t)tmin >= wd && (uint64_t)tmin / wd == (uint64_t)tmax / wd;
+    const bool two = (uint64_t)tmin >= (uint64_t)wv.d && wv.quot(tmin) == wv.quot(tmax);
     return two ? cnt : mul_chk(cnt, 2, ovf);
 }
 
-__device__ uint64_t complete_count(const DevGraph &g, const DevPlan &P, Recs R, uint32_t tmin, uint32_t tmax,
-                                   uint32_t *status)
+__device__ uint64_t complete_count(const DevGraph &g, const DevPlan &P, const WinDiv &wv, Recs R, uint32_t tmin,
+                                   uint32_t tmax, uint32_t *status)
 {
     bool ovf = false;
-    const uint64_t cnt = over_nphi(P, derive_cnt(g, P, R, tmin, tmax, ovf), tmin, tmax, ovf);
+    const uint64_t cnt = over_nphi(wv, derive_cnt(g, P, R, tmin, tmax, ovf), tmin, tmax, ovf);
     if (ovf) latch(status, ST_OVERFLOW);
     return cnt;
 }
@@ -268,8 +268,10 @@ __device__ __forceinline__ int sample_root(const DevPlan &P, const SampleJob &J,
 {
     const u128 W = (u128)J.W_lo | ((u128)J.W_hi << 64);
     u128 r = rng.below128(W, status);
-    // window: last k with wcum[k] <= r
-    uint32_t lo = 0, hi = J.nwtot;
+    // window: last k with wcum[k] <= r, between the guide entries of r's bucket
+    const uint32_t jb = (uint32_t)(r >> J.wshift);
+    uint32_t lo = __ldg(J.wguide + jb), hi = __ldg(J.wguide + jb + 1) + 1;
+    if (lo >= hi || hi > J.nwtot) { latch(status, ST_BADSTATE); return -1; }
     while (hi - lo > 1) {
         uint32_t mid = (lo + hi) >> 1;
         u128 c = (u128)__ldg(J.wcum + 2 * (size_t)mid) | ((u128)__ldg(J.wcum + 2 * (size_t)mid + 1) << 64);
@@ -428,7 +430,7 @@ __device__ int sample_one(const DevGraph &g, const DevPlan &P, const SampleJob &
     uint32_t tmin, tmax;
     const int why = validate_tree(P, R, tmin, tmax);
     if (why) return why;
-    contrib = complete_count(g, P, R, tmin, tmax, status);
+    contrib = complete_count(g, P, J.wv, R, tmin, tmax, status);
     return 0;
 }
 
@@ -521,7 +523,7 @@ __device__ __forceinline__ int sample_one_reg(const DevGraph &g, const DevPlan &
         RegView<NT> v{t, phi};
         cnt = derive_simple(g, P, v, tmin, tmax, ovf);
     }
-    cnt = over_nphi(P, cnt, tmin, tmax, ovf);
+    cnt = over_nphi(J.wv, cnt, tmin, tmax, ovf);
     if (ovf) latch(status, ST_OVERFLOW);
     contrib = cnt;
     return 0;
@@ -558,7 +560,7 @@ __device__ __forceinline__ void add_tallies(Acc *acc, u128 hits, unsigned long l
 
 constexpr int kSampleThreads = 256;
 #ifndef TM_SAMPLE_MINB
-#define TM_SAMPLE_MINB 6   // 40 registers: six blocks of 256 per SM hide more of the search latency
+#define TM_SAMPLE_MINB 4   // 64 registers, four blocks of 256 per SM (measured faster than 48 or 40 registers)
 #endif
 #ifndef TM_SAMPLE_GRID_PER_SM
 // tm_sample's grid cap in blocks per SM: one wave of resident blocks, each
@@ -794,7 +796,7 @@ __global__ void __launch_bounds__(kSampleThreads, TM_SAMPLE_MINB)
         if (why == 3) { ++nr3; continue; }
         ++nv;
 #pragma unroll
-        for (int m = 0; m < NM; ++m) hits[m] += complete_count(g, sp[m], R, tmin, tmax, status);
+        for (int m = 0; m < NM; ++m) hits[m] += complete_count(g, sp[m], J.wv, R, tmin, tmax, status);
     }
     for (int o = 16; o > 0; o >>= 1) {
         nv += __shfl_down_sync(0xffffffffu, nv, o);
@@ -940,6 +942,9 @@ void fill_job(tm_motif *mo, SampleJob &J, const DevPlan *dplan)
 {
     J.plan = dplan;
     J.wcum = mo->wcum;
+    J.wguide = mo->wguide;
+    J.wshift = wguide_shift(mo->W.lo, mo->W.hi, mo->nwtot);
+    J.wv = make_windiv(mo->plan.wdelta);
     J.nwtot = mo->nwtot;
     J.nw0 = mo->layer[0].nwin;
     J.win_beg0 = mo->layer[0].win_beg; J.win_beg1 = mo->layer[1].win_beg;

@@ -189,47 +189,4 @@ __device__ __forceinline__ int64_t layer_window(uint32_t t, int p, int64_t d)
     return p + 2 * ((tt - p * d) / (2 * d));
 }
 
-// Windows by one quotient.  With q = floor(t' / d), t' lies in windows q - 1
-// and q (the windows i with i*d <= t' < (i+2)*d); the one of layer p is the
-// one with parity p: q - ((q xor p) & 1), absent (-1) when that is negative.
-// The quotient uses the division by an invariant integer of Granlund and
-// Montgomery ("Division by invariant integers using multiplication", PLDI
-// 1994, Fig. 4.1) for 32-bit dividends: with l = ceil(log2 d) and
-// m' = floor(2^32 (2^l - d) / d) + 1, floor(n / d) = (t1 + ((n - t1) >> sh1)) >> sh2
-// where t1 = mulhi(m', n), sh1 = min(l, 1), sh2 = max(l - 1, 0).  A unit of
-// 2^32 or more leaves every t' < 2^32 in quotient 0.
-struct WinDiv {
-    uint32_t mul;       // m'
-    uint32_t sh1, sh2;
-    uint32_t big;       // 1: d >= 2^32, every quotient is 0
-    int64_t d;          // the window unit
-    __device__ __forceinline__ uint32_t quot(uint32_t n) const
-    {
-        if (big) return 0u;
-        const uint32_t t1 = __umulhi(mul, n);
-        return (t1 + ((n - t1) >> sh1)) >> sh2;
-    }
-    // window index of layer p for quotient q, or -1
-    __device__ __forceinline__ static int64_t win_of(uint32_t q, int p)
-    {
-        return (int64_t)q - (int64_t)((q ^ (uint32_t)p) & 1u);
-    }
-    __device__ __forceinline__ int64_t win(uint32_t t, int p) const { return win_of(quot(t), p); }
-};
-
-inline WinDiv make_windiv(int64_t d)
-{
-    WinDiv w{};
-    w.d = d;
-    if (d >= ((int64_t)1 << 32)) { w.big = 1; w.mul = 0; w.sh1 = w.sh2 = 0; return w; }
-    const uint64_t D = (uint64_t)d;
-    uint32_t l = 0;
-    while (l < 32 && ((uint64_t)1 << l) < D) ++l;   // l = ceil(log2 d)
-    w.mul = (uint32_t)(((((uint64_t)1 << l) - D) << 32) / D + 1);
-    w.sh1 = l < 1 ? l : 1;
-    w.sh2 = l > 1 ? l - 1 : 0;
-    w.big = 0;
-    return w;
-}
-
 }  // namespace timest

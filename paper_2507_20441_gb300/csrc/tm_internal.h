@@ -27,6 +27,66 @@ enum : uint32_t {
     ST_RANGE = 32u         // an id out of range
 };
 
+// Guide table of the window pick: draws r in [j 2^s, (j+1) 2^s) fall in a
+// window between wguide[j] and wguide[j+1].  s = max(0, bitlen(W) -
+// bitlen(nw) - 1), so there are at most 4 nw buckets; the same function
+// sizes the table (weight pass) and reads it (sampler).
+__host__ __device__ inline uint32_t wguide_shift(uint64_t W_lo, uint64_t W_hi, uint32_t nw)
+{
+    int bw = 0;
+    for (uint64_t x = W_hi; x; x >>= 1) ++bw;
+    if (bw) bw += 64;
+    else for (uint64_t x = W_lo; x; x >>= 1) ++bw;
+    int bn = 0;
+    for (uint32_t x = nw; x; x >>= 1) ++bn;
+    const int s = bw - bn - 1;
+    return s > 0 ? (uint32_t)s : 0u;
+}
+
+// Windows by one quotient.  With q = floor(t' / d), t' lies in windows q - 1
+// and q (the windows i with i*d <= t' < (i+2)*d); the one of layer p is the
+// one with parity p: q - ((q xor p) & 1), absent (-1) when that is negative.
+// The quotient uses the division by an invariant integer of Granlund and
+// Montgomery ("Division by invariant integers using multiplication", PLDI
+// 1994, Fig. 4.1) for 32-bit dividends: with l = ceil(log2 d) and
+// m' = floor(2^32 (2^l - d) / d) + 1, floor(n / d) = (t1 + ((n - t1) >> sh1)) >> sh2
+// where t1 = mulhi(m', n), sh1 = min(l, 1), sh2 = max(l - 1, 0).  A unit of
+// 2^32 or more leaves every t' < 2^32 in quotient 0.
+struct WinDiv {
+    uint32_t mul;       // m'
+    uint32_t sh1, sh2;
+    uint32_t big;       // 1: d >= 2^32, every quotient is 0
+    int64_t d;          // the window unit
+    __device__ __forceinline__ uint32_t quot(uint32_t n) const
+    {
+        if (big) return 0u;
+        const uint32_t t1 = __umulhi(mul, n);
+        return (t1 + ((n - t1) >> sh1)) >> sh2;
+    }
+    // window index of layer p for quotient q, or -1
+    __device__ __forceinline__ static int64_t win_of(uint32_t q, int p)
+    {
+        return (int64_t)q - (int64_t)((q ^ (uint32_t)p) & 1u);
+    }
+    __device__ __forceinline__ int64_t win(uint32_t t, int p) const { return win_of(quot(t), p); }
+};
+
+inline WinDiv make_windiv(int64_t d)
+{
+    WinDiv w{};
+    w.d = d;
+    if (d >= ((int64_t)1 << 32)) { w.big = 1; w.mul = 0; w.sh1 = w.sh2 = 0; return w; }
+    const uint64_t D = (uint64_t)d;
+    uint32_t l = 0;
+    while (l < 32 && ((uint64_t)1 << l) < D) ++l;   // l = ceil(log2 d)
+    w.mul = (uint32_t)(((((uint64_t)1 << l) - D) << 32) / D + 1);
+    w.sh1 = l < 1 ? l : 1;
+    w.sh2 = l > 1 ? l - 1 : 0;
+    w.big = 0;
+    return w;
+}
+
+
 // The temporal graph in HBM, all structure-of-arrays, 32-bit ids.
 // gid = position in GLOBAL order (t', src, dst).
 struct DevGraph {
@@ -126,6 +186,7 @@ struct tm_motif {
     ulonglong2 *pref_dir[timest::kMaxTree] = {};
     ulonglong2 *pref_multi[timest::kMaxTree] = {};
     uint64_t *wcum = nullptr;            // [2*(nw0+nw1+1)] u128 window cumulative (lo,hi)
+    uint32_t *wguide = nullptr;          // [4*(nw0+nw1)+2] guide table of the window pick
     uint32_t nwtot = 0;
     tm_u128 W{0, 0};
     size_t bytes = 0;                    // device bytes held
@@ -209,6 +270,9 @@ int export_weights(tm_ctx *ctx, tm_motif *mo, int q, int layer, uint64_t *host_o
 struct SampleJob {
     const DevPlan *plan;                 // device pointer
     const uint64_t *wcum;                // u128 pairs
+    const uint32_t *wguide;              // guide table of the window pick (shift wshift)
+    uint32_t wshift;
+    WinDiv wv;                           // divider of the window unit (N_phi)
     uint32_t nwtot, nw0;
     const uint32_t *win_beg0, *win_beg1, *win_id0, *win_id1;
     const uint64_t *root_cdf0, *root_cdf1;

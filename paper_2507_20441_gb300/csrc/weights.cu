@@ -75,7 +75,7 @@ constexpr uint32_t kScanLimit = TM_DP_SCAN_LIMIT;
 // Overflow rule: a factor >= 2^64, or an exact product >= 2^64 with no zero
 // factor.
 #ifndef TM_DP_MINB
-#define TM_DP_MINB 4   // 64 registers: no spills (at 40 or 48 registers it spills)
+#define TM_DP_MINB 5   // 48 registers, five blocks of 256 per SM (measured faster than 40 or 64 registers)
 #endif
 __global__ void __launch_bounds__(256, TM_DP_MINB) k_dp(DevGraph g, DevPlan P, WinDiv wv, int q, int side, int first,
                                                         int last, ChildPrefix cp, ulonglong2 *__restrict__ wout,
@@ -459,6 +459,29 @@ __global__ void k_window_cum(const uint64_t *__restrict__ cdf0, const uint32_t *
     }
 }
 
+// Guide table of the window pick: entry j is the window holding draw j 2^s
+// (the last k with wcum[k] <= j 2^s), for the ceil(W / 2^s) buckets, then a
+// sentinel (the last window).  One thread per bucket, a binary search each;
+// W is read on the device (the last cumulative entry).
+__global__ void k_wguide(const uint64_t *__restrict__ wcum, uint32_t nw, uint32_t *__restrict__ guide)
+{
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    const u128 W = (u128)wcum[2 * (size_t)nw] | ((u128)wcum[2 * (size_t)nw + 1] << 64);
+    if (W == 0) return;
+    const uint32_t s = wguide_shift((uint64_t)W, (uint64_t)(W >> 64), nw);
+    const uint64_t nb = (uint64_t)((W + ((u128)1 << s) - 1) >> s);
+    if (j > nb) return;
+    if (j == nb) { guide[j] = nw - 1; return; }
+    const u128 x = (u128)j << s;
+    uint32_t lo = 0, hi = nw;   // wcum[0] = 0 <= x; find the last k with wcum[k] <= x
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        const u128 c = (u128)wcum[2 * (size_t)mid] | ((u128)wcum[2 * (size_t)mid + 1] << 64);
+        if (c <= x) lo = mid; else hi = mid;
+    }
+    guide[j] = lo;
+}
+
 // ---- guide table of the root search --------------------------------------
 // Window kk of a layer gets about n/4 buckets of width 2^s over its draws
 // [0, W_kk); the table holds, per bucket j, the first edge whose in-window
@@ -574,6 +597,7 @@ static void free_motif_weights(tm_ctx *ctx, tm_motif *mo)
     for (int p = 0; p < 2; ++p) mo->layer[p] = LayerData();
     for (int sl = 0; sl < kMaxTree; ++sl) mo->pref_dir[sl] = mo->pref_multi[sl] = nullptr;
     mo->wcum = nullptr;
+    mo->wguide = nullptr;
     mo->have_weights = false;
 }
 
@@ -621,7 +645,7 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
         auto guide_n = [&](uint32_t nw) { return (size_t)m / 4 + 3 * (size_t)nw + 1; };
         size_t total = al(((size_t)nwh[0] + 1) * 4) * 4 + al(((size_t)nwh[1] + 1) * 4) * 4 + 2 * al(mm * 8) +
                        (size_t)P.nslots * 2 * al(mm * 16) + al(((size_t)nwh[0] + nwh[1] + 1) * 16) +
-                       al(guide_n(nwh[0]) * 4) + al(guide_n(nwh[1]) * 4);
+                       al(guide_n(nwh[0]) * 4) + al(guide_n(nwh[1]) * 4) + al((4 * ((size_t)nwh[0] + nwh[1]) + 2) * 4);
         char *blk = (char *)malloc_motif(ctx, mo, total);
         if (!blk) return TM_E_NOMEM;
         size_t off = 0;
@@ -641,6 +665,7 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
             mo->pref_multi[sl] = (ulonglong2 *)take(mm * 16);
         }
         mo->wcum = (uint64_t *)take(((size_t)nwh[0] + nwh[1] + 1) * 16);
+        mo->wguide = (uint32_t *)take((4 * ((size_t)nwh[0] + nwh[1]) + 2) * 4);
     }
     {
         PhaseScope ph(ctx, TM_PH_WINDOWS);
@@ -745,6 +770,9 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
         PhaseScope ph(ctx, TM_PH_ROOT);
         launch(ctx, k_window_cum, 1, 1024, mo->layer[0].root_cdf, mo->layer[0].win_beg, nw0, mo->layer[1].root_cdf,
                                          mo->layer[1].win_beg, nw1, mo->wcum);
+        if (mo->nwtot)
+            launch(ctx, k_wguide, blocks_for(4 * (uint64_t)mo->nwtot + 1, TB), TB, (const uint64_t *)mo->wcum,
+                   mo->nwtot, mo->wguide);
         copy_d2h(ctx, Wh, mo->wcum + 2 * (size_t)mo->nwtot, 16);
     }
     uint32_t bits = 0;
