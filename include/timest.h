@@ -406,15 +406,19 @@ typedef struct {
     int tile;            /* samples per work item             */
     int threads;         /* threads per block (128 or 256)    */
     int smem_records;    /* per-sample records in shared (1) or local (0) memory */
+    int coop_min;        /* lanes per long search: 0 = one lane per sample's search;
+                            n = the warp's active lanes together on searches of at
+                            least n entries (tm_coop_search) */
     double ms;           /* best of two timed launches        */
 } tm_tune_entry;
 
 /* Autotune tm_batch_run for this batch: time every shape (6 tile sizes x 2
- * block sizes x 2 record placements) on the same queries with their sample
- * counts scaled to about target_samples in total (0 = 4e6), keep the fastest
- * in ctx and report it in *best (and every shape in table[table_cap]).
- * A shape changes speed only: every sample's outcome depends on its seed and
- * id alone.  Errors: TM_E_STATE (no weights), TM_E_CUDA. */
+ * block sizes x 2 record placements x 2 search modes) on the same queries
+ * with their sample counts scaled to about target_samples in total (0 =
+ * 4e6), keep the fastest in ctx and report it in *best (and every shape in
+ * table[table_cap]).  A shape changes speed only: every sample's outcome
+ * depends on its seed and id alone.  Errors: TM_E_STATE (no weights),
+ * TM_E_CUDA. */
 int tm_autotune(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64_t *k, const uint64_t *seed,
                 uint64_t target_samples, tm_tune_entry *table, uint32_t table_cap, uint32_t *nentries,
                 tm_tune_entry *best);
@@ -423,6 +427,15 @@ int tm_autotune(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, const uint64_
  * threads per block (128 or 256; 0 = 256), per-sample records in shared (1)
  * or local (0) memory.  Errors: TM_E_ARG. */
 int tm_batch_shape(tm_ctx *ctx, int tile, int threads, int smem_records);
+
+/* Warp-cooperative searches in the samplers of ctx (tm_sample, the batched
+ * and served samplers): a sample whose candidate-list pick or pair-list
+ * search spans at least min_entries entries is searched by all active lanes
+ * of its warp at once, each step probing one position per lane and keeping
+ * the bracket a ballot finds (an (n+1)-way split instead of a halving); the
+ * other samples' searches stay one lane each.  0 turns it off (the default).
+ * Changes speed only: every result is identical.  Errors: TM_E_ARG. */
+int tm_coop_search(tm_ctx *ctx, uint32_t min_entries);
 
 /* Free a motif and its device weights. */
 void tm_motif_free(tm_motif *mo);

@@ -94,10 +94,12 @@ class tm_kernel_time(C.Structure):
 
 
 class tm_tune_entry(C.Structure):
-    _fields_ = [("tile", C.c_int), ("threads", C.c_int), ("smem_records", C.c_int), ("ms", C.c_double)]
+    _fields_ = [("tile", C.c_int), ("threads", C.c_int), ("smem_records", C.c_int), ("coop_min", C.c_int),
+                ("ms", C.c_double)]
 
     def as_dict(self):
-        return {"tile": self.tile, "threads": self.threads, "smem_records": self.smem_records, "ms": self.ms}
+        return {"tile": self.tile, "threads": self.threads, "smem_records": self.smem_records,
+                "coop_min": self.coop_min, "ms": self.ms}
 
 
 class tm_serve_cfg(C.Structure):
@@ -151,6 +153,7 @@ def _declare(L):
     L.tm_autotune.argtypes = [vp, u32, vp, vp, vp, u64, C.POINTER(tm_tune_entry), u32, C.POINTER(u32),
                               C.POINTER(tm_tune_entry)]
     L.tm_batch_shape.argtypes = [vp, i32, i32, i32]
+    L.tm_coop_search.argtypes = [vp, u32]
     L.tm_serve_start.argtypes = [vp, C.POINTER(tm_serve_cfg)]
     L.tm_serve_submit.argtypes = [vp, u32, u32, vp, vp, i64, u64, u64, C.POINTER(u64)]
     L.tm_serve_submit_motif.argtypes = [vp, vp, u64, u64, C.POINTER(u64)]
@@ -434,6 +437,11 @@ def tm_batch_shape(ctx, tile=0, threads=0, smem_records=0):
     _check(lib().tm_batch_shape(ctx, int(tile), int(threads), int(smem_records)), ctx, "tm_batch_shape")
 
 
+def tm_coop_search(ctx, min_entries=0):
+    """Warp-cooperative searches from min_entries entries on (0 = off)."""
+    _check(lib().tm_coop_search(ctx, int(min_entries)), ctx, "tm_coop_search")
+
+
 def tm_autotune(ctx, motifs, ks, seeds, target_samples=0):
     """Tune the batched sampler for this batch; returns (best, table)."""
     nq = len(motifs)
@@ -637,6 +645,9 @@ class Context:
 
     def kernel_times(self):
         return tm_kernel_times(self.h)
+
+    def coop_search(self, min_entries=0):
+        tm_coop_search(self.h, min_entries)
 
     def autotune(self, motifs, ks, seeds, target_samples=0):
         return tm_autotune(self.h, [m.h for m in motifs], ks, seeds, target_samples)

@@ -41,6 +41,9 @@ namespace {
 #ifndef TM_RS_ITEMS
 #define TM_RS_ITEMS 16   // keys per thread (8 and 12 measured slower on 2M and 10M keys)
 #endif
+#ifndef TM_RS_MATCH
+#define TM_RS_MATCH 0    // 1: peers of a digit by one match-any instead of a ballot per digit bit
+#endif
 constexpr int OS_THREADS = 256;
 constexpr int OS_ITEMS = TM_RS_ITEMS;
 constexpr int OS_TILE = OS_THREADS * OS_ITEMS;     // 4096 keys per tile
@@ -205,6 +208,9 @@ __global__ void __launch_bounds__(OS_THREADS, NP >= 3 ? 2 : NP >= 2 ? 3 : 4)
         const bool valid = base + li < n;
         const uint32_t d = valid ? ((kv[j] >> shift) & dmask) : radix;
         uint32_t peers;
+#if TM_RS_MATCH
+        peers = __match_any_sync(0xffffffffu, d);   // lanes with the same digit (invalid lanes: digit radix)
+#else
         if (__all_sync(0xffffffffu, d == __shfl_sync(0xffffffffu, d, 0))) {
             peers = 0xffffffffu;
         } else {
@@ -215,6 +221,7 @@ __global__ void __launch_bounds__(OS_THREADS, NP >= 3 ? 2 : NP >= 2 ? 3 : 4)
                 peers &= ((d >> b) & 1u) ? bb : ~bb;
             }
         }
+#endif
         uint32_t cur = valid ? wc[d] : 0;
         __syncwarp();
         if (valid) {
@@ -299,7 +306,6 @@ static int rs_pass(tm_ctx *ctx, const RsJobs &in, int nsets, int np, uint32_t n,
 {
     const unsigned nblk = ntiles * (unsigned)nsets;
     const uint64_t ncount = ((uint64_t)ntiles << pb) * (uint64_t)nsets;
-    cudaStream_t st = ctx->stream;
     launch(ctx, k_rs_count, nblk, OS_THREADS, in, n, sh, pb, ntiles, counts);
     int rc = exclusive_scan_u32(ctx, counts, counts, ncount, nullptr);
     if (rc) return rc;

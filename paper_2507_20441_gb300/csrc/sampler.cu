@@ -49,11 +49,21 @@ struct Recs {
     __device__ __forceinline__ uint32_t &phi(int v) { return base[(4 * kMaxTree + v) * stride]; }
 };
 
+// The pair id of (u, v) (or kNone): a search of u's pairs, sorted by
+// destination; warp-cooperative from coop_min pairs on.
+__device__ __forceinline__ uint32_t pair_of_coop(const DevGraph &g, uint32_t u, uint32_t v, uint32_t coop_min)
+{
+    const uint32_t lo = __ldg(g.vpair_off + u), hi = __ldg(g.vpair_off + u + 1);
+    const uint32_t p = first_true_coop(ProbeGeU32{g.pair_dst, v}, lo, hi, coop_min);
+    return (p < hi && __ldg(g.pair_dst + p) == v) ? p : kNone;
+}
+
 // Multi-edge list range of pair (u, v), or an empty range.
-__device__ __forceinline__ void find_pair(const DevGraph &g, uint32_t u, uint32_t v, uint32_t &beg, uint32_t &end)
+__device__ __forceinline__ void find_pair(const DevGraph &g, uint32_t u, uint32_t v, uint32_t &beg, uint32_t &end,
+                                          uint32_t coop_min = 0xFFFFFFFFu)
 {
     uint32_t lo = __ldg(g.vpair_off + u), hi = __ldg(g.vpair_off + u + 1);
-    uint32_t p = lower_idx(g.pair_dst, lo, hi, v);
+    uint32_t p = first_true_coop(ProbeGeU32{g.pair_dst, v}, lo, hi, coop_min);
     if (p < hi && __ldg(g.pair_dst + p) == v) {
         beg = __ldg(g.pair_off + p);
         end = __ldg(g.pair_off + p + 1);
@@ -72,7 +82,7 @@ __device__ __forceinline__ void find_pair(const DevGraph &g, uint32_t u, uint32_
 // Rec supplies the vertex map phi(v) and the tree-node times t(q).
 template <class Rec>
 __device__ uint64_t derive_simple(const DevGraph &g, const DevPlan &P, Rec &R, uint32_t tmin, uint32_t tmax,
-                                  bool &ovf)
+                                  bool &ovf, uint32_t coop_min = 0xFFFFFFFFu)
 {
     const uint64_t d = (uint64_t)P.delta;
     const uint64_t glo = (uint64_t)tmax >= d ? (uint64_t)tmax - d : 0;
@@ -82,7 +92,7 @@ __device__ uint64_t derive_simple(const DevGraph &g, const DevPlan &P, Rec &R, u
     for (int i = 0; i < P.nnt; ++i) {
         const int e = P.pos_edge[P.nt_pos[i]];
         uint32_t b, en;
-        find_pair(g, R.phi(P.ea[e]), R.phi(P.eb[e]), b, en);
+        find_pair(g, R.phi(P.ea[e]), R.phi(P.eb[e]), b, en, coop_min);
         if (b == en) return 0;
         uint64_t lo = glo, hi = ghi;
         if (P.nt_prev[i] >= 0) { uint64_t x = (uint64_t)R.t(P.nt_prev[i]) + 1; lo = x > lo ? x : lo; }
@@ -334,7 +344,8 @@ __device__ __forceinline__ int sample_child(const DevGraph &g, const DevPlan &P,
     child_range(g, zs ? 1 : 0, out, zg, ppos, pt, P.tlater[q] != 0, tlo, thi, a, b, beg, tarr);
     // the excluded multi-edge list (Constraint 2): zg -> og for a child
     // leaving the meeting vertex, og -> zg for one entering it
-    const uint32_t pe = !P.c2 ? kNone : out ? pair_of(g, zg, og) : pair_of(g, og, zg);
+    const uint32_t pe = !P.c2 ? kNone
+                      : out ? pair_of_coop(g, zg, og, J.coop_min) : pair_of_coop(g, og, zg, J.coop_min);
     uint32_t ea = 0, eb = 0, pb = 0;
     if (pe != kNone) {
         pb = __ldg(g.pair_off + pe);
@@ -366,11 +377,7 @@ __device__ __forceinline__ int sample_child(const DevGraph &g, const DevPlan &P,
         // nothing excluded: F(x) = x - a + 1 for a leaf (the pick is
         // direct), the prefix difference otherwise
         if (leaf) xl = a + (uint32_t)rc;
-        else
-            while (xl < xh) {
-                const uint32_t x = xl + ((xh - xl) >> 1);
-                if (__ldg(Pd + 2 * (size_t)x) - base > rc) xh = x; else xl = x + 1;
-            }
+        else xl = first_true_coop(ProbeGtU64S2{Pd, rc + base}, a, b, J.coop_min);
     } else {
         while (xl < xh) {
             const uint32_t x = xl + ((xh - xl) >> 1);
@@ -521,7 +528,7 @@ __device__ __forceinline__ int sample_one_reg(const DevGraph &g, const DevPlan &
     uint64_t cnt = 1;
     if (P.nnt > 0) {
         RegView<NT> v{t, phi};
-        cnt = derive_simple(g, P, v, tmin, tmax, ovf);
+        cnt = derive_simple(g, P, v, tmin, tmax, ovf, J.coop_min);
     }
     cnt = over_nphi(J.wv, cnt, tmin, tmax, ovf);
     if (ovf) latch(status, ST_OVERFLOW);
@@ -945,6 +952,7 @@ void fill_job(tm_motif *mo, SampleJob &J, const DevPlan *dplan)
     J.wguide = mo->wguide;
     J.wshift = wguide_shift(mo->W.lo, mo->W.hi, mo->nwtot);
     J.wv = make_windiv(mo->plan.wdelta);
+    J.coop_min = mo->ctx ? mo->ctx->coop_min : 0xFFFFFFFFu;
     J.nwtot = mo->nwtot;
     J.nw0 = mo->layer[0].nwin;
     J.win_beg0 = mo->layer[0].win_beg; J.win_beg1 = mo->layer[1].win_beg;

@@ -136,198 +136,13 @@ inline int exclusive_scan_u32(tm_ctx *ctx, const uint32_t *in, uint32_t *out, ui
     return rc;
 }
 
-// ------------------------------------------------------ segmented u64 ----
-struct SegAgg {
-    uint64_t v;     // sum since the last head (or of the whole range)
-    uint32_t f;     // 1 if the range contains a head
-    uint32_t pad;
-};
-
-__device__ __forceinline__ SegAgg seg_combine(SegAgg a, SegAgg b, bool &ovf)
-{
-    SegAgg r;
-    r.f = a.f | b.f;
-    if (b.f) r.v = b.v;
-    else r.v = add_chk(a.v, b.v, ovf);
-    r.pad = 0;
-    return r;
-}
-
-// Load functor interface: __device__ uint64_t value(uint64_t pos) const;
-//                         __device__ bool head(uint64_t pos) const;
-//                         static constexpr bool kGathered (value() is a gather:
-//                         read it once and keep it for the rescan)
-template <class F>
-__global__ void k_segscan_reduce(F f, uint64_t n, SegAgg *__restrict__ aggs, uint64_t *__restrict__ stash,
-                                 uint32_t *status)
-{
-    __shared__ SegAgg warp_agg[SCAN_THREADS / 32];
-    uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
-    bool ovf = false;
-    SegAgg a{0, 0, 0};
-#pragma unroll
-    for (int j = 0; j < SCAN_ITEMS; ++j) {
-        uint64_t i = base + j;
-        if (i < n) {
-            const uint64_t v = f.value(i);
-            if (stash) stash[i] = v;          // gathered once; the rescan reads it back in order
-            SegAgg x{v, f.head(i) ? 1u : 0u, 0};
-            a = seg_combine(a, x, ovf);
-        }
-    }
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int o = 1; o < 32; o <<= 1) {
-        SegAgg y;
-        y.v = __shfl_up_sync(0xffffffffu, a.v, o);
-        y.f = __shfl_up_sync(0xffffffffu, a.f, o);
-        if (lane >= o) a = seg_combine(y, a, ovf);
-    }
-    if (lane == 31) warp_agg[warp] = a;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        SegAgg t = warp_agg[0];
-        for (int w = 1; w < SCAN_THREADS / 32; ++w) t = seg_combine(t, warp_agg[w], ovf);
-        aggs[blockIdx.x] = t;
-    }
-    if (ovf) latch(status, ST_OVERFLOW);
-}
-
-// Turn tile aggregates into per-tile carry-ins (exclusive, segmented), in
-// place.  One block of 1024 threads; each thread owns a contiguous chunk of
-// tiles, and the chunk totals are combined by a warp-shuffle scan.
-__device__ __forceinline__ SegAgg seg_shfl_up(SegAgg a, int o)
-{
-    SegAgg y;
-    y.v = __shfl_up_sync(0xffffffffu, a.v, o);
-    y.f = __shfl_up_sync(0xffffffffu, a.f, o);
-    y.pad = 0;
-    return y;
-}
-
-__global__ void k_segscan_carries(SegAgg *__restrict__ aggs, uint64_t ntiles, uint32_t *status)
-{
-    __shared__ SegAgg warp_tot[32];
-    bool ovf = false;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint64_t per = (ntiles + blockDim.x - 1) / blockDim.x;
-    uint64_t lo = (uint64_t)threadIdx.x * per, hi = lo + per;
-    if (hi > ntiles) hi = ntiles;
-    if (lo > ntiles) lo = ntiles;
-    SegAgg a{0, 0, 0};
-    for (uint64_t i = lo; i < hi; ++i) a = seg_combine(a, aggs[i], ovf);
-    // inclusive scan of chunk totals inside the warp, then across warps
-    SegAgg incl = a;
-    for (int o = 1; o < 32; o <<= 1) {
-        SegAgg y = seg_shfl_up(incl, o);
-        if (lane >= o) incl = seg_combine(y, incl, ovf);
-    }
-    if (lane == 31) warp_tot[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = (blockDim.x + 31) / 32;
-        SegAgg w = lane < nw ? warp_tot[lane] : SegAgg{0, 0, 0};
-        SegAgg wi = w;
-        for (int o = 1; o < 32; o <<= 1) {
-            SegAgg y = seg_shfl_up(wi, o);
-            if (lane >= o) wi = seg_combine(y, wi, ovf);
-        }
-        SegAgg ex = seg_shfl_up(wi, 1);
-        if (lane == 0) ex = SegAgg{0, 0, 0};
-        if (lane < nw) warp_tot[lane] = ex;
-    }
-    __syncthreads();
-    SegAgg ex_lane = seg_shfl_up(incl, 1);
-    SegAgg run = warp_tot[warp];
-    if (lane > 0) run = seg_combine(run, ex_lane, ovf);
-    for (uint64_t i = lo; i < hi; ++i) {
-        SegAgg c = aggs[i];
-        aggs[i] = run;
-        run = seg_combine(run, c, ovf);
-    }
-    if (ovf) latch(status, ST_OVERFLOW);
-}
-
-template <class F>
-__global__ void k_segscan_final(F f, uint64_t n, const SegAgg *__restrict__ carries,
-                                const uint64_t *__restrict__ stash, uint64_t *__restrict__ out, uint32_t *status)
-{
-    __shared__ SegAgg warp_agg[SCAN_THREADS / 32];
-    uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
-    bool ovf = false;
-    uint64_t v[SCAN_ITEMS];
-    uint32_t hbits = 0;
-    SegAgg a{0, 0, 0};
-#pragma unroll
-    for (int j = 0; j < SCAN_ITEMS; ++j) {
-        uint64_t i = base + j;
-        v[j] = 0;
-        if (i < n) {
-            v[j] = stash ? stash[i] : f.value(i);
-            bool h = f.head(i);
-            hbits |= (h ? 1u : 0u) << j;
-            SegAgg x{v[j], h ? 1u : 0u, 0};
-            a = seg_combine(a, x, ovf);
-        }
-    }
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    SegAgg incl = a;
-    for (int o = 1; o < 32; o <<= 1) {
-        SegAgg y;
-        y.v = __shfl_up_sync(0xffffffffu, incl.v, o);
-        y.f = __shfl_up_sync(0xffffffffu, incl.f, o);
-        if (lane >= o) incl = seg_combine(y, incl, ovf);
-    }
-    if (lane == 31) warp_agg[warp] = incl;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        SegAgg run = carries[blockIdx.x];
-        for (int w = 0; w < SCAN_THREADS / 32; ++w) {
-            SegAgg c = warp_agg[w];
-            warp_agg[w] = run;
-            run = seg_combine(run, c, ovf);
-        }
-    }
-    __syncthreads();
-    // exclusive prefix of this thread = warp prefix (+) lanes before it
-    SegAgg excl_lane;
-    excl_lane.v = __shfl_up_sync(0xffffffffu, incl.v, 1);
-    excl_lane.f = __shfl_up_sync(0xffffffffu, incl.f, 1);
-    SegAgg pre = warp_agg[warp];
-    if (lane > 0) pre = seg_combine(pre, excl_lane, ovf);
-    uint64_t run = pre.v;
-#pragma unroll
-    for (int j = 0; j < SCAN_ITEMS; ++j) {
-        uint64_t i = base + j;
-        if (i < n) {
-            if ((hbits >> j) & 1u) run = v[j];
-            else run = add_chk(run, v[j], ovf);
-            out[i] = run;
-        }
-    }
-    if (ovf) latch(status, ST_OVERFLOW);
-}
-
-template <class F>
-int segmented_scan_u64(tm_ctx *ctx, const F &f, uint64_t n, uint64_t *out)
-{
-    if (n == 0) return TM_OK;
-    uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
-    ScratchScope scope(ctx);
-    SegAgg *aggs = (SegAgg *)salloc(ctx, tiles * sizeof(SegAgg));
-    uint64_t *stash = F::kGathered ? (uint64_t *)salloc(ctx, n * sizeof(uint64_t)) : nullptr;
-    if (!aggs || (F::kGathered && !stash)) return TM_E_NOMEM;
-    launch(ctx, k_segscan_reduce<F>, (unsigned)tiles, SCAN_THREADS, f, n, aggs, stash, ctx->status);
-    launch(ctx, k_segscan_carries, 1, 1024, aggs, tiles, ctx->status);
-    launch(ctx, k_segscan_final<F>, (unsigned)tiles, SCAN_THREADS, f, n, aggs, (const uint64_t *)stash, out,
-           ctx->status);
-    return check_cuda(ctx, cudaGetLastError(), "segmented scan");
-}
-
 // ------------------------------------------ segmented u64, two layers ----
-// The same scan over pairs (layer 0, layer 1) that share their positions: one
-// gather of a 16-byte pair serves both layers.  Heads may differ per layer
-// (bit p of head2()).  Functor interface: value2(pos) -> ulonglong2 and
-// head2(pos) -> bits.
+// Inclusive prefix sums that restart at segment heads, with every 64-bit
+// addition inside a segment checked for wrap-around, over pairs (layer 0,
+// layer 1) that share their positions (one gather of a 16-byte pair serves
+// both layers).  Heads may differ per layer (bit p of head2()).  Functor
+// interface: value2(pos) -> ulonglong2, head2(pos) -> bits, and
+// kGathered (value2 is a gather).
 struct SegAgg2 {
     uint64_t v0, v1;
     uint32_t f;     // bit p: the range contains a head of layer p
@@ -494,10 +309,136 @@ __global__ void __launch_bounds__(SCAN_THREADS, TM_SCAN2_MINB) k_segscan2_final(
     if (ovf) latch(status, ST_OVERFLOW);
 }
 
+// ---- one pass with decoupled look-back -------------------------------
+// Each block takes the next tile from a counter (so every tile before it has
+// been started), scans it, publishes its aggregate, then walks back over the
+// tiles before it, combining their aggregates until it meets a published
+// inclusive prefix or both layers have met a segment head (a head cuts the
+// sums off), and publishes its own inclusive prefix.  Waits are bounded: a
+// tile that does not publish within the limit latches ST_TIMEOUT.
+struct SegTile {
+    unsigned long long a0, a1, p0, p1;   // aggregate and inclusive prefix of both layers
+    uint32_t af, pf;                     // their head bits
+    uint32_t status;                     // 0 none, 1 aggregate, 2 inclusive prefix
+    uint32_t pad;
+};
+
+constexpr int kLookbackPolls = 1 << 22;   // with a 64 ns sleep each: a limit of at least a quarter second
+
+__device__ __forceinline__ void seg_publish(SegTile *t, const SegAgg2 &v, uint32_t st)
+{
+    volatile SegTile *vt = t;
+    if (st == 1) { vt->a0 = v.v0; vt->a1 = v.v1; vt->af = v.f; }
+    else { vt->p0 = v.v0; vt->p1 = v.v1; vt->pf = v.f; }
+    __threadfence();
+    vt->status = st;
+}
+
+template <class F>
+__global__ void __launch_bounds__(SCAN_THREADS) k_segscan2_onepass(F f, uint64_t n, SegTile *__restrict__ tiles,
+                                                                   uint32_t *__restrict__ counter,
+                                                                   ulonglong2 *__restrict__ keep,
+                                                                   uint64_t *__restrict__ out0,
+                                                                   uint64_t *__restrict__ out1,
+                                                                   ulonglong2 *__restrict__ outp, uint32_t *status)
+{
+    __shared__ SegAgg2 warp_agg[SCAN_THREADS / 32];
+    __shared__ uint32_t s_tile;
+    if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t base = (uint64_t)tile * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
+    bool ovf = false;
+    ulonglong2 v[SCAN_ITEMS];
+    uint32_t hbits = 0;
+    SegAgg2 a{0, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        const uint64_t i = base + j;
+        v[j] = make_ulonglong2(0, 0);
+        if (i < n) {
+            v[j] = f.value2(i);
+            if (keep) keep[i] = v[j];
+            const uint32_t h = f.head2(i);
+            hbits |= h << (2 * j);
+            SegAgg2 x{v[j].x, v[j].y, h, 0};
+            a = seg_combine2(a, x, ovf);
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    SegAgg2 incl = a;
+    for (int o = 1; o < 32; o <<= 1) {
+        const SegAgg2 y = seg_shfl_up2(incl, o);
+        if (lane >= o) incl = seg_combine2(y, incl, ovf);
+    }
+    if (lane == 31) warp_agg[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        SegAgg2 T = warp_agg[0];
+        for (int w = 1; w < SCAN_THREADS / 32; ++w) T = seg_combine2(T, warp_agg[w], ovf);
+        SegAgg2 ex{0, 0, 0, 0};
+        if (tile == 0) {
+            seg_publish(tiles, T, 2);
+        } else {
+            seg_publish(tiles + tile, T, 1);
+            // look back: ex = the combination of the tiles before this one
+            for (int64_t jt = (int64_t)tile - 1; jt >= 0; --jt) {
+                volatile SegTile *pt = tiles + jt;
+                uint32_t st = pt->status;
+                for (int it = 0; st == 0 && it < kLookbackPolls; ++it) {
+                    __nanosleep(64);
+                    st = pt->status;
+                }
+                if (st == 0) { latch(status, ST_TIMEOUT); break; }
+                __threadfence();
+                if (st == 2) {
+                    const SegAgg2 pre{pt->p0, pt->p1, pt->pf, 0};
+                    ex = seg_combine2(pre, ex, ovf);
+                    break;
+                }
+                const SegAgg2 agg{pt->a0, pt->a1, pt->af, 0};
+                ex = seg_combine2(agg, ex, ovf);
+                if ((ex.f & 3u) == 3u) break;   // both layers restarted: nothing before matters
+            }
+            seg_publish(tiles + tile, seg_combine2(ex, T, ovf), 2);
+        }
+        SegAgg2 run = ex;
+        for (int w = 0; w < SCAN_THREADS / 32; ++w) {
+            const SegAgg2 c = warp_agg[w];
+            warp_agg[w] = run;
+            run = seg_combine2(run, c, ovf);
+        }
+    }
+    __syncthreads();
+    const SegAgg2 excl_lane = seg_shfl_up2(incl, 1);
+    SegAgg2 pre = warp_agg[warp];
+    if (lane > 0) pre = seg_combine2(pre, excl_lane, ovf);
+    uint64_t r0 = pre.v0, r1 = pre.v1;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        const uint64_t i = base + j;
+        if (i < n) {
+            const uint32_t h = (hbits >> (2 * j)) & 3u;
+            r0 = (h & 1u) ? v[j].x : add_chk(r0, v[j].x, ovf);
+            r1 = (h & 2u) ? v[j].y : add_chk(r1, v[j].y, ovf);
+            if (outp) {
+                outp[i] = make_ulonglong2(r0, r1);
+            } else {
+                out0[i] = r0;
+                out1[i] = r1;
+            }
+        }
+    }
+    if (ovf) latch(status, ST_OVERFLOW);
+}
+
 // Outputs: out0 / out1 (one array per layer), or outp (the (layer 0,
 // layer 1) pairs interleaved) when it is non-null.  A gathering functor's
 // values are stashed in scan order; with `keep` non-null the stash is that
 // caller-owned array (n pairs), which then holds the gathered values.
+#ifndef TM_SCAN_ONEPASS
+#define TM_SCAN_ONEPASS 1   // 1: one pass with look-back; 0: reduce, carries, rescan
+#endif
 template <class F>
 int segmented_scan2_u64(tm_ctx *ctx, const F &f, uint64_t n, uint64_t *out0, uint64_t *out1,
                         ulonglong2 *outp = nullptr, ulonglong2 *keep = nullptr)
@@ -505,6 +446,16 @@ int segmented_scan2_u64(tm_ctx *ctx, const F &f, uint64_t n, uint64_t *out0, uin
     if (n == 0) return TM_OK;
     const uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     ScratchScope scope(ctx);
+#if TM_SCAN_ONEPASS
+    if (tiles >= 0xFFFFFFFFull) return set_err(ctx, TM_E_LIMIT, "scan of more than 2^32 tiles");
+    char *st = (char *)salloc(ctx, tiles * sizeof(SegTile) + 256);
+    if (!st) return TM_E_NOMEM;
+    uint32_t *counter = (uint32_t *)(st + tiles * sizeof(SegTile));
+    cudaMemsetAsync(st, 0, tiles * sizeof(SegTile) + 4, ctx->stream);
+    launch(ctx, k_segscan2_onepass<F>, (unsigned)tiles, SCAN_THREADS, f, n, (SegTile *)st, counter, keep, out0, out1,
+           outp, ctx->status);
+    return check_cuda(ctx, cudaGetLastError(), "segmented scan");
+#endif
     SegAgg2 *aggs = (SegAgg2 *)salloc(ctx, tiles * sizeof(SegAgg2));
     ulonglong2 *stash = !F::kGathered ? nullptr : keep ? keep : (ulonglong2 *)salloc(ctx, n * sizeof(ulonglong2));
     if (!aggs || (F::kGathered && !stash)) return TM_E_NOMEM;

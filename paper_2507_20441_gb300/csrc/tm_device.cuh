@@ -155,6 +155,88 @@ __device__ __forceinline__ uint32_t pair_of(const DevGraph &g, uint32_t u, uint3
     return (p < hi && __ldg(g.pair_dst + p) == v) ? p : kNone;
 }
 
+// ---- warp-cooperative search ----------------------------------------------
+// A lane whose search range holds at least coop_min entries is served by all
+// active lanes of its warp together: with n lanes, each step probes n evenly
+// spaced positions at once and a ballot keeps the bracket between the last
+// false and the first true probe, so the range shrinks (n + 1)-fold per step
+// instead of 2-fold.  Lanes with long ranges are served one after the other;
+// the others search alone.  Probe(x) must be monotone (false ... true) on
+// the range; the result is the first x in [lo, hi) with Probe(x), else hi.
+struct ProbeGtU64S2 {            // v[2x] > key (a lane of interleaved prefix pairs)
+    const uint64_t *v;
+    uint64_t key;
+    __device__ __forceinline__ bool operator()(uint32_t x) const { return __ldg(v + 2 * (size_t)x) > key; }
+    __device__ __forceinline__ ProbeGtU64S2 bcast(unsigned mask, int src) const
+    {
+        return ProbeGtU64S2{(const uint64_t *)__shfl_sync(mask, (unsigned long long)v, src),
+                            __shfl_sync(mask, (unsigned long long)key, src)};
+    }
+};
+struct ProbeGeU32 {              // a[x] >= key
+    const uint32_t *a;
+    uint32_t key;
+    __device__ __forceinline__ bool operator()(uint32_t x) const { return __ldg(a + x) >= key; }
+    __device__ __forceinline__ ProbeGeU32 bcast(unsigned mask, int src) const
+    {
+        return ProbeGeU32{(const uint32_t *)__shfl_sync(mask, (unsigned long long)a, src), __shfl_sync(mask, key, src)};
+    }
+};
+
+template <class Probe>
+__device__ __forceinline__ uint32_t first_true_serial(const Probe &pr, uint32_t lo, uint32_t hi)
+{
+    uint32_t n = hi - lo;
+    while (n > 0) {
+        const uint32_t half = n >> 1, mid = lo + half;
+        if (!pr(mid)) { lo = mid + 1; n -= half + 1; }
+        else n = half;
+    }
+    return lo;
+}
+
+template <class Probe>
+__device__ uint32_t first_true_coop(const Probe &pr, uint32_t lo, uint32_t hi, uint32_t coop_min)
+{
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31;
+    const bool mine = hi - lo >= coop_min;
+    unsigned todo = __ballot_sync(act, mine);
+    uint32_t res = hi;
+    if (todo) {
+        const uint32_t n = (uint32_t)__popc(act);
+        const uint32_t rank = (uint32_t)__popc(act & ((1u << lane) - 1u));
+        const int last = 31 - __clz((int)act);
+        while (todo) {
+            const int leader = __ffs((int)todo) - 1;
+            todo &= todo - 1u;
+            const Probe q = pr.bcast(act, leader);
+            uint32_t l = __shfl_sync(act, lo, leader), h = __shfl_sync(act, hi, leader);
+            // invariant: Probe false below l, true from h on (h = the range end if none)
+            while (h - l > n) {
+                const uint32_t pp = l + (uint32_t)(((uint64_t)(rank + 1u) * (h - l)) / (uint64_t)(n + 1u));
+                const unsigned b = __ballot_sync(act, q(pp));
+                if (b) {
+                    const int fl = __ffs((int)b) - 1;
+                    const unsigned below = act & ((1u << fl) - 1u);
+                    const int pl = below ? 31 - __clz((int)below) : fl;
+                    const uint32_t pf = __shfl_sync(act, pp, fl), pb = __shfl_sync(act, pp, pl);
+                    h = pf;
+                    if (below) l = pb + 1u;
+                } else {
+                    l = __shfl_sync(act, pp, last) + 1u;
+                }
+            }
+            const uint32_t x = l + rank;   // at most n candidates left: one probe each
+            const unsigned b = __ballot_sync(act, x < h && q(x));
+            const uint32_t a = b ? l + (uint32_t)__popc(act & ((1u << (__ffs((int)b) - 1)) - 1u)) : h;
+            if (lane == leader) res = a;
+        }
+    }
+    if (!mine) res = first_true_serial(pr, lo, hi);
+    return res;
+}
+
 // First index in [lo, hi) with v[i] > x (v non-decreasing).
 __device__ __forceinline__ uint32_t upper_idx64(const uint64_t *__restrict__ v, uint32_t lo, uint32_t hi, uint64_t x)
 {

@@ -230,6 +230,7 @@ struct tm_ctx {
     timest::Server *server = nullptr;          // serving loop (serve.cu), if running
     int batch_threads = 256;                   // batched sampler shape (set by tm_autotune)
     int batch_smem_recs = 0;
+    uint32_t coop_min = 0xFFFFFFFFu;           // warp-cooperative searches from this length (tm_coop_search)
     void *pinned_acc = nullptr;                // staging for batched sums (device -> host)
     size_t pinned_acc_bytes = 0;
     uint64_t phase_launches[TM_NUM_PHASES] = {};
@@ -273,6 +274,7 @@ struct SampleJob {
     const uint32_t *wguide;              // guide table of the window pick (shift wshift)
     uint32_t wshift;
     WinDiv wv;                           // divider of the window unit (N_phi)
+    uint32_t coop_min;                   // searches of at least this many entries are warp-cooperative
     uint32_t nwtot, nw0;
     const uint32_t *win_beg0, *win_beg1, *win_id0, *win_id1;
     const uint64_t *root_cdf0, *root_cdf1;

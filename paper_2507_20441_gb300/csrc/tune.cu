@@ -35,23 +35,29 @@ extern "C" int tm_autotune(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, co
     const int tiles[] = {512, 1024, 2048, 4096, 8192, 16384};
     const int threads[] = {128, 256};
     const int staging[] = {0, 1};
+    // lanes on one long search: 1 (every search per lane), or the warp's
+    // active lanes together on searches of at least 256 entries
+    const int coops[] = {0, 256};
     const int keep_threads = ctx->batch_threads, keep_smem = ctx->batch_smem_recs;
+    const uint32_t keep_coop = ctx->coop_min;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return check_cuda(ctx, cudaGetLastError(), "autotune events");
-    tm_tune_entry bestv{0, 0, 0, 0.0};
+    tm_tune_entry bestv{0, 0, 0, 0, 0.0};
     uint32_t cnt = 0;
     int rc = TM_OK;
     // warm-up launch (loads the kernels, touches the graph)
     ctx->batch_threads = 256;
     ctx->batch_smem_recs = 0;
     rc = run_batch_items(ctx, items.data(), nq, 2048, acc.data(), 0);
+    for (int co : coops)
     for (int th : threads)
         for (int sm : staging)
             for (int tl : tiles) {
                 if (rc) break;
                 ctx->batch_threads = th;
                 ctx->batch_smem_recs = sm;
+                ctx->coop_min = co ? (uint32_t)co : 0xFFFFFFFFu;
                 float best_ms = 1e30f;
                 for (int rep = 0; rep < 2 && rc == TM_OK; ++rep) {
                     cudaEventRecord(e0, ctx->stream);
@@ -62,7 +68,7 @@ extern "C" int tm_autotune(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, co
                     cudaEventElapsedTime(&ms, e0, e1);
                     best_ms = std::min(best_ms, ms);
                 }
-                tm_tune_entry ent{tl, th, sm, (double)best_ms};
+                tm_tune_entry ent{tl, th, sm, co, (double)best_ms};
                 if (table && cnt < table_cap) table[cnt] = ent;
                 ++cnt;
                 if (bestv.tile == 0 || ent.ms < bestv.ms) bestv = ent;
@@ -72,11 +78,13 @@ extern "C" int tm_autotune(tm_ctx *ctx, uint32_t nq, tm_motif *const *motifs, co
     if (rc) {
         ctx->batch_threads = keep_threads;
         ctx->batch_smem_recs = keep_smem;
+        ctx->coop_min = keep_coop;
         return rc;
     }
     ctx->cfg.sample_tile = bestv.tile;
     ctx->batch_threads = bestv.threads;
     ctx->batch_smem_recs = bestv.smem_records;
+    ctx->coop_min = bestv.coop_min ? (uint32_t)bestv.coop_min : 0xFFFFFFFFu;
     if (nentries) *nentries = cnt;
     if (best) *best = bestv;
     return TM_OK;
@@ -89,5 +97,12 @@ extern "C" int tm_batch_shape(tm_ctx *ctx, int tile, int threads, int smem_recor
     ctx->cfg.sample_tile = tile;
     ctx->batch_threads = threads ? threads : 256;
     ctx->batch_smem_recs = smem_records;
+    return TM_OK;
+}
+
+extern "C" int tm_coop_search(tm_ctx *ctx, uint32_t min_entries)
+{
+    if (!ctx) return TM_E_ARG;
+    ctx->coop_min = min_entries ? min_entries : 0xFFFFFFFFu;
     return TM_OK;
 }

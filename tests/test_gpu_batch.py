@@ -131,9 +131,10 @@ def test_autotune_picks_the_fastest_measured_shape(pool):
     ks = [mo.k for mo in pool]
     seeds = [100 + i for i in range(len(pool))]
     best, table = ctx.autotune(motifs, ks, seeds, target_samples=500_000)
-    assert len(table) == 24
+    assert len(table) == 48
     assert best["ms"] == min(e["ms"] for e in table)
     assert best["tile"] in (512, 1024, 2048, 4096, 8192, 16384) and best["threads"] in (128, 256)
+    assert {e["coop_min"] for e in table} == {0, 256} and best["coop_min"] in (0, 256)
     res = ctx.batch_run(motifs, ks, seeds)          # runs with the tuned shape
     for m, k, s, r in zip(motifs, ks, seeds, res):
         ref = m.sample(k, s)
