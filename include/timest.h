@@ -129,9 +129,9 @@ int tm_graph_load(tm_ctx *ctx, uint32_t n, uint64_t m, const uint32_t *src,
  * preamble; Defs. 3.1-3.3): the GLOBAL order (t', src, dst) that numbers the
  * edges, per-vertex out-lists (t', dst), in-lists (t', src), and per-pair
  * multi-edge lists El_{u,v} (t').  Duplicates / self loops are reported here
- * when tm_graph_load was given device pointers.  The graph takes about 104
- * bytes of device memory per edge (26 u32 arrays of m entries, the pair tables
- * among them, plus 12 bytes per vertex). */
+ * when tm_graph_load was given device pointers.  The graph takes about 80
+ * bytes of device memory per edge (20 u32 arrays of m entries, the pair tables
+ * among them, plus three bit sets of m bits and 12 bytes per vertex). */
 int tm_preprocess(tm_ctx *ctx);
 
 /* Number of edges kept, t_min and T = max t' of the preprocessed graph. */

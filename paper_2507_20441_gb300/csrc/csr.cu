@@ -2,16 +2,23 @@
 //
 // From m raw tuples (u, v, t) it builds, all on the device:
 //   GLOBAL order (t', src, dst)      -> gid, the edge id used everywhere
-//   out-lists   (src | t', dst)      -> out_off / out_t / out_nbr / out_gid
-//   in-lists    (dst | t', src)      -> in_off / in_t / in_nbr / in_gid
-//   multi-edge  (src, dst | t')      -> pairs, pair_off / multi_t / multi_to_*
+//   out-lists   (src | t', dst)      -> out_off / out_t / out_nbr / out_gid / out_pos
+//   in-lists    (dst | t', src)      -> in_off / in_t / in_nbr / in_gid / in_pos / in_to_out
+//   multi-edge  (src, dst | t')      -> pairs, pair_off / pair_dst / multi_t / multi_to_out
 // with t' = t - t_min.  The orderings come from a stable LSD radix sort (up to
-// 9-bit digits) written here.  The GLOBAL order is a sort by t' after which
-// each run of equal t' is put in (src, dst) order in place (one thread, one
-// block, or, for a run of more than 4096 edges, the full three-key sort);
-// the OUT and IN orders are stable re-sorts of the GLOBAL order by one
-// endpoint (one two-array sort), and the multi-edge order is a stable re-sort
-// of the IN order by source.
+// 9-bit digits, up to four payload arrays) written here.  The GLOBAL order is
+// a sort by t' after which each run of equal t' is put in (src, dst) order in
+// place (one thread, one block, or, for a run of more than 4096 edges, the
+// full three-key sort).  The OUT and IN orders are stable re-sorts of the
+// GLOBAL order by one endpoint that carry gid, t' and the other endpoint as
+// payloads, so no list array is gathered; their last pass also writes each
+// edge's list position by gid.  The IN sort carries each edge's out-list
+// position too (read in GLOBAL order), which is the in -> out map, and the
+// multi-edge order is a stable re-sort of the IN order by source carrying
+// gid, t', the destination and that map (-> multi_to_out).  The random
+// accesses left are the list positions written by gid in the sorts' last
+// passes and the cross ranks, found by binary search in the owner's other
+// list.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -659,13 +666,6 @@ __global__ void k_owner_bits(const uint32_t *__restrict__ out_src, const uint32_
     }
 }
 
-// out[perm[i]] = i
-__global__ void k_invert(const uint32_t *__restrict__ perm, uint32_t m, uint32_t *__restrict__ out)
-{
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) out[perm[i]] = i;
-}
-
 // off[v] = first position whose sorted key is >= v, for v in [0, n].  With
 // m_dev set, the key count is min(m, *m_dev) (a count known only on the
 // device; m bounds the grid).
@@ -814,7 +814,7 @@ int build_csr(tm_ctx *ctx)
         const size_t mf = (size_t)m, a_m = align256((mf ? mf : 1) * 4), a_n = align256(((size_t)n + 1) * 4);
         const size_t a_b = align256((mf / 32 + 1) * 4);
         // (the pair tables are sized by m too: the pair count is read only at the end)
-        if (!gblock_open(ctx, gb, 21 * a_m + 256 + 3 * a_n + 3 * a_b)) return TM_E_NOMEM;
+        if (!gblock_open(ctx, gb, 20 * a_m + 256 + 3 * a_n + 3 * a_b)) return TM_E_NOMEM;
     }
     g.g_t = gtake(gb, m); g.g_src = gtake(gb, m); g.g_dst = gtake(gb, m);
     if (!g.g_t || !g.g_src || !g.g_dst) return TM_E_NOMEM;
@@ -894,8 +894,8 @@ int build_csr(tm_ctx *ctx)
     if (!g.out_gid || !g.out_t || !g.out_nbr || !g.out_off || !g.in_gid || !g.in_t || !g.in_nbr || !g.in_off ||
         !g.out_src || !g.in_dst || !g.out_xrank || !g.in_xrank || !g.out_pos || !g.in_pos)
         return TM_E_NOMEM;
-    g.out_to_in = gtake(gb, m); g.in_to_out = gtake(gb, m);
-    if (!g.out_to_in || !g.in_to_out) return TM_E_NOMEM;
+    g.in_to_out = gtake(gb, m);
+    if (!g.in_to_out) return TM_E_NOMEM;
     if (m) {
         // payloads: the input index (gid), t' and the other endpoint, so every
         // list array comes out of the sort (no gathers); the last pass also
@@ -958,9 +958,6 @@ int build_csr(tm_ctx *ctx)
                (const uint32_t *)head, (const uint32_t *)pid, m, g.pair_off, pair_src, g.pair_dst);
         launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, pair_src, m, n, g.vpair_off, (const uint32_t *)dnp);
         copy_d2h(ctx, ctx->status_host + 1, dnp, 4);   // pinned: read after the closing synchronize
-        // per out-list position its in-list position: the inverse of the
-        // in -> out map
-        launch(ctx, k_invert, blocks_for(m, TB), TB, (const uint32_t *)g.in_to_out, m, g.out_to_in);
         // cross ranks between a vertex's out- and in-lists
         launch(ctx, k_cross_rank, dim3(blocks_for(m, TB), 2), TB, XR{g.out_t, g.out_src, g.in_off, g.in_t, g.out_xrank},
                XR{g.in_t, g.in_dst, g.out_off, g.out_t, g.in_xrank}, m);

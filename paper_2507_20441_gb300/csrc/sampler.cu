@@ -629,7 +629,8 @@ __global__ void __launch_bounds__(kSampleThreads, TM_SAMPLE_MINB) k_sample_reg(D
     }
     __syncthreads();
     u128 hits = 0;
-    unsigned long long nv = 0, nr1 = 0, nr2 = 0, nr3 = 0;
+    // per-thread tallies fit 32 bits: the launcher keeps k / (grid threads) below 2^32
+    uint32_t nv = 0, nr1 = 0, nr2 = 0, nr3 = 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
         uint64_t c = 0;
@@ -1025,6 +1026,8 @@ int run_samples(tm_ctx *ctx, tm_motif *mo, uint64_t k, uint64_t seed, uint64_t f
     uint64_t want = (k + threads - 1) / threads;
     uint64_t cap = (uint64_t)ctx->num_sms * TM_SAMPLE_GRID_PER_SM;
     unsigned blocks = (unsigned)std::max<uint64_t>(1, std::min(want, cap));
+    if (k / ((uint64_t)blocks * threads) >= 0xFFFFFFFFull)
+        return set_err(ctx, TM_E_LIMIT, "too many samples in one call (split the range with first_index)");
     uint32_t *dg = nullptr; uint64_t *dc = nullptr; int32_t *dr = nullptr;
     size_t gbytes = 0;
     int rc;

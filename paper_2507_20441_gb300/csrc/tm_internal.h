@@ -112,8 +112,8 @@ struct DevGraph {
     uint32_t *pair_dst = nullptr;        // [P]
     uint32_t *pair_off = nullptr;        // [P+1] into multi_*
     uint32_t *multi_t = nullptr;
-    // position maps between the list orders (same edge): out->in, in->out, multi->out
-    uint32_t *out_to_in = nullptr, *in_to_out = nullptr, *multi_to_out = nullptr;
+    // position maps between the list orders (same edge): in->out, multi->out
+    uint32_t *in_to_out = nullptr, *multi_to_out = nullptr;
     // bit sets over list positions: bit x set when position x starts a new
     // owner (vertex for the out/in orders, pair for the multi order); m/32+1 words
     uint32_t *own_out = nullptr, *own_in = nullptr, *own_multi = nullptr;

@@ -67,7 +67,9 @@ constexpr uint32_t kScanLimit = TM_DP_SCAN_LIMIT;
 // other endpoint is the parent's other endpoint: short ranges are scanned for
 // them in place (one pass serves both layers); long ones search the excluded
 // multi-edge list.
-// Results are written in this list order.  A root with children at both ends
+// Results are written in this list order, or through `scatter` into another
+// order (a node whose parent scans the out-list order while its own DP runs
+// in in-list order writes through the in -> out map).  A root with children at both ends
 // runs side 0 (first) then side 1 (last), which reads side 0's partial
 // product through the out->in position map, and its pending-overflow bits
 // from two bit sets of m/32 words (one per layer; a warp of side 0 writes
@@ -79,6 +81,7 @@ constexpr uint32_t kScanLimit = TM_DP_SCAN_LIMIT;
 #endif
 __global__ void __launch_bounds__(256, TM_DP_MINB) k_dp(DevGraph g, DevPlan P, WinDiv wv, int q, int side, int first,
                                                         int last, ChildPrefix cp, ulonglong2 *__restrict__ wout,
+                                                        const uint32_t *__restrict__ scatter,
                                                         const ulonglong2 *__restrict__ in,
                                                         const uint32_t *__restrict__ pin, uint32_t *__restrict__ pout,
                                                         uint32_t *status)
@@ -222,7 +225,8 @@ __global__ void __launch_bounds__(256, TM_DP_MINB) k_dp(DevGraph g, DevPlan P, W
                 else prod[p] = mul_chk(prod[p], sum, ovf[p]);
             }
         }
-        wout[pos] = make_ulonglong2(zero[0] ? 0 : prod[0], zero[1] ? 0 : prod[1]);   // both layers, one store
+        // both layers, one store; at the position scatter[pos] when a map is given
+        wout[scatter ? __ldg(scatter + pos) : pos] = make_ulonglong2(zero[0] ? 0 : prod[0], zero[1] ? 0 : prod[1]);
         pend_bits = ((!zero[0] && ovf[0]) ? 1u : 0u) | ((!zero[1] && ovf[1]) ? 2u : 0u);
         if (last && pend_bits) latch(status, ST_OVERFLOW);
     }
@@ -681,7 +685,6 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
     const OwnerBits ob{g.own_out, g.own_in, g.own_multi};
     ulonglong2 *w = nullptr, *pw = nullptr;   // (layer 0, layer 1) weight pairs
     uint32_t *pend = nullptr;                 // per layer a bit set: pending overflow of a side-0 partial
-    ulonglong2 *gathered = nullptr;           // a node's weights gathered into out-list order
     w = (ulonglong2 *)salloc(ctx, (size_t)(m ? m : 1) * 16);
     if (!w) return TM_E_NOMEM;
     ChildPrefix cp{};
@@ -707,12 +710,17 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
             }
             if (m) {
                 if (has[0] && has[1]) {
-                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, wv, q, 0, 1, 0, cp, pw, (const ulonglong2 *)nullptr,
-                           (const uint32_t *)nullptr, pend, ctx->status);
-                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, wv, q, 1, 0, 1, cp, w, (const ulonglong2 *)pw,
-                           (const uint32_t *)pend, (uint32_t *)nullptr, ctx->status);
+                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, wv, q, 0, 1, 0, cp, pw, (const uint32_t *)nullptr,
+                           (const ulonglong2 *)nullptr, (const uint32_t *)nullptr, pend, ctx->status);
+                    launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, wv, q, 1, 0, 1, cp, w, (const uint32_t *)nullptr,
+                           (const ulonglong2 *)pw, (const uint32_t *)pend, (uint32_t *)nullptr, ctx->status);
                 } else {
+                    // a non-root node leaving its parent's meeting vertex runs in
+                    // in-list order and is scanned by its parent in out-list
+                    // order: it writes through the in -> out map
+                    const bool to_out = q != 0 && P.tout[q] != 0 && in_order;
                     launch(ctx, k_dp, blocks_for(m, TB), TB, g, P, wv, q, in_order ? 1 : 0, 1, 1, cp, w,
+                           to_out ? (const uint32_t *)g.in_to_out : (const uint32_t *)nullptr,
                            (const ulonglong2 *)nullptr, (const uint32_t *)nullptr, (uint32_t *)nullptr, ctx->status);
                 }
             }
@@ -740,22 +748,17 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
             const bool out = P.tout[q] != 0;
             // A non-root node's DP runs in the list order of its far endpoint,
             // never in the order its parent scans (out-list order when the node
-            // leaves the meeting vertex, in-list order when it enters it): the
-            // parent's order is one gather through a position map.  Multi-edge
+            // leaves the meeting vertex, in-list order when it enters it).  A
+            // node leaving it wrote its weights through the in -> out map, so
+            // they are in out-list order already; for a node entering it the
+            // in-list order is one gather through the same map.  Multi-edge
             // lists are grouped by source like the out-lists, so the multi-edge
             // prefix gathers, within each source's run, from the weights in
-            // out-list order: the DP's own output when the node enters the
-            // meeting vertex, else the gathered copy the first scan keeps.
-            const uint32_t *dmap = out ? g.out_to_in : g.in_to_out;
-            if (out && !gathered) {
-                gathered = (ulonglong2 *)salloc(ctx, (size_t)(m ? m : 1) * 16);
-                if (!gathered) return TM_E_NOMEM;
-            }
-            DirScan2 fd{w, dmap, out ? g.out_t : g.in_t, out ? ob.out : ob.in, wv};
-            rc = segmented_scan2_u64(ctx, fd, m, nullptr, nullptr, mo->pref_dir[slot], out ? gathered : nullptr);
+            // out-list order (w in both cases).
+            DirScan2 fd{w, out ? nullptr : g.in_to_out, out ? g.out_t : g.in_t, out ? ob.out : ob.in, wv};
+            rc = segmented_scan2_u64(ctx, fd, m, nullptr, nullptr, mo->pref_dir[slot]);
             if (rc) return rc;
-            DirScan2 fm{out ? (const ulonglong2 *)gathered : (const ulonglong2 *)w, g.multi_to_out, g.multi_t,
-                        ob.multi, wv};
+            DirScan2 fm{w, g.multi_to_out, g.multi_t, ob.multi, wv};
             rc = segmented_scan2_u64(ctx, fm, m, nullptr, nullptr, mo->pref_multi[slot]);
             if (rc) return rc;
             cp.pd[slot] = mo->pref_dir[slot];
