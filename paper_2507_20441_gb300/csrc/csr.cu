@@ -920,23 +920,20 @@ int build_csr(tm_ctx *ctx)
     sec.reset();
     sec.reset(new PhaseScope(ctx, TM_PH_CSR_MULTI));
     g.multi_t = gtake(gb, m);
-    uint32_t *multi_gid = (uint32_t *)salloc(ctx, (size_t)(m ? m : 1) * 4);   // edge id per multi position
     g.multi_to_out = gtake(gb, m);
     g.vpair_off = gtake(gb, (size_t)n + 1);
     g.own_out = gtake(gb, (size_t)m / 32 + 1); g.own_in = gtake(gb, (size_t)m / 32 + 1);
     g.own_multi = gtake(gb, (size_t)m / 32 + 1);
-    if (!multi_gid || !g.multi_t || !g.vpair_off || !g.multi_to_out || !g.own_out || !g.own_in || !g.own_multi)
+    if (!g.multi_t || !g.vpair_off || !g.multi_to_out || !g.own_out || !g.own_in || !g.own_multi)
         return TM_E_NOMEM;
     uint32_t np = 0;
     if (m) {
         {
-            // payloads: gid, t' and the destination, straight into the
-            // multi-edge arrays
-            RsTo ms{g.in_nbr, g.in_gid, g.in_t, key, multi_gid, g.multi_t};
-            ms.p2_in = g.in_dst;
-            ms.p2 = tmp;
-            ms.p3_in = g.in_to_out;       // -> each multi-edge entry's out-list position
-            ms.p3 = g.multi_to_out;
+            // payloads: t', the destination and each entry's out-list
+            // position, straight into the multi-edge arrays
+            RsTo ms{g.in_nbr, g.in_t, g.in_dst, key, g.multi_t, tmp};
+            ms.p2_in = g.in_to_out;
+            ms.p2 = g.multi_to_out;
             rc = radix_sort_sets_to(ctx, &ms, 1, m, vbits);
             if (rc) return rc;
         }

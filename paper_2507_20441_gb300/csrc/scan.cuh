@@ -311,11 +311,12 @@ __global__ void __launch_bounds__(SCAN_THREADS, TM_SCAN2_MINB) k_segscan2_final(
 
 // ---- one pass with decoupled look-back -------------------------------
 // Each block takes the next tile from a counter (so every tile before it has
-// been started), scans it, publishes its aggregate, then walks back over the
-// tiles before it, combining their aggregates until it meets a published
-// inclusive prefix or both layers have met a segment head (a head cuts the
-// sums off), and publishes its own inclusive prefix.  Waits are bounded: a
-// tile that does not publish within the limit latches ST_TIMEOUT.
+// been started), scans it, publishes its aggregate, then its first warp walks
+// back over the tiles before it, 32 at a time, combining their aggregates
+// until it meets a published inclusive prefix or both layers have met a
+// segment head (a head cuts the sums off), and publishes its own inclusive
+// prefix.  Waits are bounded: a tile that does not publish within the limit
+// latches ST_TIMEOUT.
 struct SegTile {
     unsigned long long a0, a1, p0, p1;   // aggregate and inclusive prefix of both layers
     uint32_t af, pf;                     // their head bits
@@ -373,40 +374,65 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_segscan2_onepass(F f, uint64_t
     }
     if (lane == 31) warp_agg[warp] = incl;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
+        // the tile's aggregate (every lane of warp 0 folds the warp totals)
         SegAgg2 T = warp_agg[0];
         for (int w = 1; w < SCAN_THREADS / 32; ++w) T = seg_combine2(T, warp_agg[w], ovf);
         SegAgg2 ex{0, 0, 0, 0};
         if (tile == 0) {
-            seg_publish(tiles, T, 2);
+            if (lane == 0) seg_publish(tiles, T, 2);
         } else {
-            seg_publish(tiles + tile, T, 1);
-            // look back: ex = the combination of the tiles before this one
-            for (int64_t jt = (int64_t)tile - 1; jt >= 0; --jt) {
-                volatile SegTile *pt = tiles + jt;
-                uint32_t st = pt->status;
-                for (int it = 0; st == 0 && it < kLookbackPolls; ++it) {
-                    __nanosleep(64);
+            if (lane == 0) seg_publish(tiles + tile, T, 1);
+            // look back 32 tiles at a time, lane i at tile (base - i): a tile
+            // ends the walk when it holds an inclusive prefix, when the heads
+            // met so far (from the closest tile outward) cover both layers, or
+            // before tile 0
+            for (int64_t jb = (int64_t)tile - 1;; jb -= 32) {
+                const int64_t j = jb - lane;
+                SegAgg2 v{0, 0, 0, 0};
+                uint32_t st = 2;
+                if (j >= 0) {
+                    volatile SegTile *pt = tiles + j;
                     st = pt->status;
+                    for (int it = 0; st == 0 && it < kLookbackPolls; ++it) {
+                        __nanosleep(64);
+                        st = pt->status;
+                    }
+                    if (st == 0) latch(status, ST_TIMEOUT);
+                    __threadfence();
+                    if (st == 2) v = SegAgg2{pt->p0, pt->p1, pt->pf, 0};
+                    else if (st == 1) v = SegAgg2{pt->a0, pt->a1, pt->af, 0};
                 }
-                if (st == 0) { latch(status, ST_TIMEOUT); break; }
-                __threadfence();
-                if (st == 2) {
-                    const SegAgg2 pre{pt->p0, pt->p1, pt->pf, 0};
-                    ex = seg_combine2(pre, ex, ovf);
-                    break;
+                // heads met from the closest tile (lane 0) up to this lane
+                uint32_t cf = v.f;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, cf, o);
+                    if (lane >= o) cf |= y;
                 }
-                const SegAgg2 agg{pt->a0, pt->a1, pt->af, 0};
-                ex = seg_combine2(agg, ex, ovf);
-                if ((ex.f & 3u) == 3u) break;   // both layers restarted: nothing before matters
+                const bool term = j < 0 || st != 1 || (cf & 3u) == 3u;
+                const unsigned tb = __ballot_sync(0xffffffffu, term);
+                const int L = tb ? __ffs((int)tb) - 1 : 31;   // the last lane to take
+                if (lane > L) v = SegAgg2{0, 0, 0, 0};
+                // fold lanes L .. 0 in tile order (earlier tiles first)
+                for (int o = 1; o < 32; o <<= 1) {
+                    const SegAgg2 y{__shfl_down_sync(0xffffffffu, v.v0, o), __shfl_down_sync(0xffffffffu, v.v1, o),
+                                    __shfl_down_sync(0xffffffffu, v.f, o), 0};
+                    if (lane + o < 32) v = seg_combine2(y, v, ovf);
+                }
+                v = SegAgg2{__shfl_sync(0xffffffffu, v.v0, 0), __shfl_sync(0xffffffffu, v.v1, 0),
+                            __shfl_sync(0xffffffffu, v.f, 0), 0};
+                ex = seg_combine2(v, ex, ovf);
+                if (tb) break;
             }
-            seg_publish(tiles + tile, seg_combine2(ex, T, ovf), 2);
+            if (lane == 0) seg_publish(tiles + tile, seg_combine2(ex, T, ovf), 2);
         }
-        SegAgg2 run = ex;
-        for (int w = 0; w < SCAN_THREADS / 32; ++w) {
-            const SegAgg2 c = warp_agg[w];
-            warp_agg[w] = run;
-            run = seg_combine2(run, c, ovf);
+        if (lane == 0) {
+            SegAgg2 run = ex;
+            for (int w = 0; w < SCAN_THREADS / 32; ++w) {
+                const SegAgg2 c = warp_agg[w];
+                warp_agg[w] = run;
+                run = seg_combine2(run, c, ovf);
+            }
         }
     }
     __syncthreads();

@@ -1,6 +1,6 @@
-"""Parity at the full size of the bench workload (Chung-Lu, n = 1e5,
+"""Parity at the full size of the 2M-edge workload (Chung-Lu, n = 1e5,
 m = 2e6, temporal 4-cycle, delta = 86,400, k = 1e6) in the launch shape
-bench.py times (default tree, one tm_sample of k = 1e6 samples):
+bench.py times for it (default tree, one tm_sample of k = 1e6 samples):
 
 * every weight of every tree edge in both layers, W and every W_i equal the
   oracle's (the oracle computes them all in seconds);

@@ -1,6 +1,8 @@
-"""Parity on the 50M-edge workload (Chung-Lu, n = 2e6, m = 5e7, span 1e8 s,
-5-cycle + chord, delta = 3,600) with the default tree: W, every W_i, every
-weight of every tree edge in both layers, hits2 and counters of 1e6 samples,
+"""Parity on the bench workload at full size (Chung-Lu, n = 2e6, m = 5e7,
+span 1e8 s, 5-cycle + chord, delta = 3,600, k = 1e7) with the default tree:
+W, every W_i, every weight of every tree edge in both layers; hits2 and the
+counters of the whole k = 1e7 run in the launch bench.py times (one
+tm_sample, the register-record sampler) against the oracle's 1e7 samples;
 and the per-sample outcome of 200 sample ids drawn from a 1e7-sample traced
 launch, each recomputed alone by the oracle."""
 import numpy as np
@@ -30,11 +32,12 @@ def test_large_workload(oracle_mod):
     for e in tree:
         for layer in (0, 1):
             assert np.array_equal(m.export_weights(e, layer), G.export_weights(e, layer)), (e, layer)
-    r = m.sample(1_000_000, 3)
-    ro = G.sample(1_000_000, 3)
+    k = mo.k
+    r = m.sample(k, 3)                 # the bench's launch: k = 1e7 in one tm_sample
+    ro = G.sample(k, 3)
     assert (r.hits2, r.valid, r.rej_vertex, r.rej_delta, r.rej_order) == \
            (ro.hits2, ro.valid, ro.rej_vertex, ro.rej_delta, ro.rej_order)
-    k = mo.k
+    assert r.valid > 0
     res, gids, contrib, reason = m.sample_trace(k, 1)
     rng = np.random.default_rng(1)
     for j in rng.choice(k, size=200, replace=False):
