@@ -310,13 +310,6 @@ __device__ __forceinline__ int sample_root(const DevPlan &P, const SampleJob &J,
     return 0;
 }
 
-// Candidate ranges up to this many entries are scanned for an excluded entry
-// before the excluded pair's multi-edge list is looked up.
-#ifndef TM_SAMPLE_EXCL_SCAN
-#define TM_SAMPLE_EXCL_SCAN 32
-#endif
-constexpr uint32_t kSampleExclScan = TM_SAMPLE_EXCL_SCAN;
-
 // One tree edge of Alg. 3: the edge of tree node q, drawn by weight from its
 // candidate list at the meeting vertex given its parent's edge (source ps,
 // destination pd, time pt, edge id pgid), in layer p whose
@@ -349,18 +342,10 @@ __device__ __forceinline__ int sample_child(const DevGraph &g, const DevPlan &P,
     uint32_t a, b, beg;
     const uint32_t *tarr;
     child_range(g, zs ? 1 : 0, out, zg, ppos, pt, P.tlater[q] != 0, tlo, thi, a, b, beg, tarr);
-    // The excluded multi-edge list (Constraint 2): zg -> og for a child
-    // leaving the meeting vertex, og -> zg for one entering it.  Its entries
-    // inside the time range are exactly the range's entries whose other
-    // endpoint is og, so a short range is scanned first: without such an
-    // entry nothing is excluded and the pair list is not looked up.
-    bool excl = P.c2 != 0;
-    if (excl && b - a <= kSampleExclScan) {
-        excl = false;
-        for (uint32_t x = a; x < b; ++x)
-            if (__ldg(nbr + x) == og) { excl = true; break; }
-    }
-    const uint32_t pe = !excl ? kNone
+    // the excluded multi-edge list (Constraint 2): zg -> og for a child
+    // leaving the meeting vertex, og -> zg for one entering it (scanning a
+    // short range for such entries first measured slower than this lookup)
+    const uint32_t pe = !P.c2 ? kNone
                       : out ? pair_of_coop(g, zg, og, J.coop_min) : pair_of_coop(g, og, zg, J.coop_min);
     uint32_t ea = 0, eb = 0, pb = 0;
     if (pe != kNone) {

@@ -543,22 +543,32 @@ __global__ void __launch_bounds__(1024) k_guide_setup(GuideArgs A)
     }
 }
 
-// One warp per window (layer 0's windows, then layer 1's); the lanes stride
-// over the window's edges: the buckets whose lower bound falls in
-// [cdf[x-1], cdf[x]) start at edge x.
-__global__ void __launch_bounds__(TB) k_guide_fill(GuideArgs A)
+// Edges in GLOBAL order, kGuideItems consecutive ones per thread, layer p =
+// blockIdx.y: the buckets whose lower bound falls in [cdf[x-1], cdf[x]) start
+// at edge x.  A thread finds the window of its first edge by a binary search
+// over the window starts, then steps to the next window as its edges cross
+// one, so a window of any size is spread over many threads.
+constexpr int kGuideItems = 8;
+__global__ void __launch_bounds__(TB) k_guide_fill(GuideArgs A, uint32_t m)
 {
-    const uint32_t wv = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t nw0 = A.L[0].nwin, nw = nw0 + A.L[1].nwin;
-    if (wv >= nw) return;
-    const int p = wv >= nw0 ? 1 : 0;
+    const int p = blockIdx.y;
     const GuideLayer &L = p ? A.L[1] : A.L[0];
-    const uint32_t kk = wv - (p ? nw0 : 0);
-    const uint32_t wbeg = L.win_beg[kk], wend = L.win_beg[kk + 1];
-    const uint32_t sh = L.gshift[kk];
-    uint32_t *G = L.guide + L.goff[kk];
-    for (uint32_t x = wbeg + lane; x < wend; x += 32) {
+    const uint32_t x0 = (blockIdx.x * blockDim.x + threadIdx.x) * (uint32_t)kGuideItems;
+    if (x0 >= m || L.nwin == 0) return;
+    // kk = the last window starting at or before x0 (none: x0 precedes every window)
+    uint32_t lo = 0, hi = L.nwin;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (L.win_beg[mid] <= x0) lo = mid + 1; else hi = mid;
+    }
+    int64_t kk = (int64_t)lo - 1;
+    const uint32_t x1 = min(m, x0 + (uint32_t)kGuideItems);
+    for (uint32_t x = x0; x < x1; ++x) {
+        while (kk + 1 < (int64_t)L.nwin && L.win_beg[kk + 1] <= x) ++kk;
+        if (kk < 0) continue;   // before the layer's first window
+        const uint32_t wbeg = L.win_beg[kk], wend = L.win_beg[kk + 1];
+        const uint32_t sh = L.gshift[kk];
+        uint32_t *G = L.guide + L.goff[kk];
         const uint64_t c1 = L.cdf[x], c0 = x > wbeg ? L.cdf[x - 1] : 0;
         const uint64_t j1 = ceil_shift(c1, sh);
         for (uint64_t j = ceil_shift(c0, sh); j < j1; ++j) G[j] = x;
@@ -740,7 +750,8 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
             // guide tables of the root search, both layers (a warp per window)
             if (m && nwh[0] + nwh[1]) {
                 launch(ctx, k_guide_setup, 2, 1024, ga);
-                launch(ctx, k_guide_fill, blocks_for((uint64_t)(nwh[0] + nwh[1]) * 32, TB), TB, ga);
+                launch(ctx, k_guide_fill, dim3(blocks_for(((uint64_t)m + kGuideItems - 1) / kGuideItems, TB), 2), TB,
+                       ga, m);
             }
         } else {
             PhaseScope ph(ctx, TM_PH_PREFIX);
