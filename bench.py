@@ -364,7 +364,8 @@ def run_ours(args, rank, world, local_rank):
         my_ms = float(t.item())
     ms_per_step = my_ms / args.steps
     value = world * k * args.steps / (my_ms / 1e3)
-    launches = sum(n for _, n in phases.values())
+    # sub-phases ("csr.out") nest inside their phase: count top-level phases only
+    launches = sum(n for name, (_, n) in phases.items() if "." not in name)
 
     # ---- the ranks' results of the last timed step combined (one all-reduce);
     # with N > 1 rank 0 checks them against one run over the same N k ids

@@ -167,23 +167,29 @@ __global__ void __launch_bounds__(256, TM_DP_MINB) k_dp(DevGraph g, DevPlan P, W
 #pragma unroll
             for (int p = 0; p < 2; ++p)
                 if (!zero[p]) { ua = min(ua, a[p]); ub = max(ub, b[p]); }
-            if (ub <= ua || ub - ua <= kScanLimit) {
-                for (uint32_t x = ua; x < ub; ++x) {
-                    if (__ldg(nbr + x) != o) continue;
-                    ulonglong2 wx2 = make_ulonglong2(1, 1);
-                    if (!leaf) {
-                        // the entry's weight: its prefix minus the previous entry's in
-                        // the same (vertex, window) segment
-                        const ulonglong2 px = __ldg(Pd + x);
-                        const ulonglong2 pp = x > beg ? __ldg(Pd + x - 1) : make_ulonglong2(0, 0);
-                        const uint32_t tp = x > beg ? __ldg(tarr + x - 1) : 0;
-                        wx2.x = px.x - ((x > beg && (uint64_t)tp >= wlo[0]) ? pp.x : 0);
-                        wx2.y = px.y - ((x > beg && (uint64_t)tp >= wlo[1]) ? pp.y : 0);
-                    }
-#pragma unroll
-                    for (int p = 0; p < 2; ++p)
-                        if (!zero[p] && x >= a[p] && x < b[p]) excl[p] += lane_of(wx2, p);
+            // an excluded entry x (other endpoint o) of the range: its weight,
+            // in each layer whose range holds it
+            auto add_excl = [&](uint32_t x) {
+                ulonglong2 wx2 = make_ulonglong2(1, 1);
+                if (!leaf) {
+                    // the entry's weight: its prefix minus the previous entry's in
+                    // the same (vertex, window) segment
+                    const ulonglong2 px = __ldg(Pd + x);
+                    const ulonglong2 pp = x > beg ? __ldg(Pd + x - 1) : make_ulonglong2(0, 0);
+                    const uint32_t tp = x > beg ? __ldg(tarr + x - 1) : 0;
+                    wx2.x = px.x - ((x > beg && (uint64_t)tp >= wlo[0]) ? pp.x : 0);
+                    wx2.y = px.y - ((x > beg && (uint64_t)tp >= wlo[1]) ? pp.y : 0);
                 }
+#pragma unroll
+                for (int p = 0; p < 2; ++p)
+                    if (!zero[p] && x >= a[p] && x < b[p]) excl[p] += lane_of(wx2, p);
+            };
+            if (!P.c2) {
+                // without Constraint 2 nothing is excluded
+            } else if (ub <= ua || ub - ua <= kScanLimit) {
+                // (reading four neighbours per 16-byte load measured no faster)
+                for (uint32_t x = ua; x < ub; ++x)
+                    if (__ldg(nbr + x) == o) add_excl(x);
             } else {
                 // the excluded multi-edge list: z -> o for a child leaving z, o -> z
                 // for one entering it
