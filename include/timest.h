@@ -140,6 +140,35 @@ int tm_graph_info(tm_ctx *ctx, uint64_t *m, int64_t *t_min, int64_t *T);
 /* Copy the GLOBAL order to host arrays of m entries (tests and debugging). */
 int tm_edges_export(tm_ctx *ctx, uint32_t *src, uint32_t *dst, uint32_t *tprime);
 
+/* One array of the temporal CSR (Sec. 3 preamble, Defs. 3.1-3.3), for tests
+ * and debugging.  gid = position in GLOBAL order (t', src, dst); the OUT order
+ * is (src, t', dst), the IN order (dst, t', src), the MULTI order
+ * (src, dst, t'); all positions are 0-based indexes into those orders.
+ *   OUT_OFF, IN_OFF, VPAIR_OFF : n+1 list starts (VPAIR_OFF: first pair of
+ *                                each source in (src, dst) order)
+ *   OUT_T/NBR/GID/SRC          : m, per OUT position: t', dst, gid, src
+ *   IN_T/NBR/GID/DST           : m, per IN position: t', src, gid, dst
+ *   OUT_POS, IN_POS            : m, per gid: its OUT / IN position
+ *   OUT_XRANK                  : m, per OUT position x (owner z, time t'):
+ *                                the first IN position of z's list with time
+ *                                >= t' (z's in-list end if none); IN_XRANK the
+ *                                same with the roles swapped
+ *   IN_TO_OUT, MULTI_TO_OUT    : m, per IN / MULTI position: the OUT position
+ *   MULTI_T                    : m, per MULTI position: t'
+ *   PAIR_OFF, PAIR_DST         : P+1 run starts in MULTI order, P heads
+ *   OWN_OUT/IN/MULTI           : m/32+1 words, bit x set when position x
+ *                                starts a new owner (vertex, vertex, pair)
+ * host_out holds cap entries; *len (if not null) receives the array's length
+ * whether or not it is copied (host_out null copies nothing).  Errors:
+ * TM_E_ARG (unknown array, cap below the length), TM_E_STATE (no graph). */
+enum {
+    TM_CSR_OUT_OFF = 0, TM_CSR_OUT_T, TM_CSR_OUT_NBR, TM_CSR_OUT_GID, TM_CSR_OUT_SRC, TM_CSR_OUT_POS,
+    TM_CSR_OUT_XRANK, TM_CSR_IN_OFF, TM_CSR_IN_T, TM_CSR_IN_NBR, TM_CSR_IN_GID, TM_CSR_IN_DST, TM_CSR_IN_POS,
+    TM_CSR_IN_XRANK, TM_CSR_IN_TO_OUT, TM_CSR_VPAIR_OFF, TM_CSR_PAIR_OFF, TM_CSR_PAIR_DST, TM_CSR_MULTI_T,
+    TM_CSR_MULTI_TO_OUT, TM_CSR_OWN_OUT, TM_CSR_OWN_IN, TM_CSR_OWN_MULTI, TM_CSR_NUM_ARRAYS
+};
+int tm_csr_export(tm_ctx *ctx, int array, uint32_t *host_out, uint64_t cap, uint64_t *len);
+
 /* Define motif M = (H, pi, delta) (Def. 1.1): nv <= 8 vertices, ne <= 16
  * edges; edges[2i], edges[2i+1] are the tail and head of edge i; order[i] is
  * the position of edge i in pi (a permutation of 0..ne-1); delta >= 1.

@@ -153,6 +153,11 @@ class Graph:
         lib().or_export_edges(self.h, _p(s), _p(d), _p(t))
         return s, d, t
 
+    def csr(self):
+        """The temporal CSR of this graph (see csr_arrays)."""
+        s, d, t = self.edges()
+        return csr_arrays(self.n, s, d, t)
+
     def set_motif(self, nv, edges, rank, delta, tree, root):
         ea = np.array([e[0] for e in edges], np.int32)
         eb = np.array([e[1] for e in edges], np.int32)
@@ -247,3 +252,67 @@ class Graph:
         if rc != OK:
             raise OracleError(rc, "or_brute_count")
         return int(out.value)
+
+
+def csr_arrays(n: int, src, dst, t) -> dict:
+    """The temporal CSR (Sec. 3 preamble, Defs. 3.1-3.3) of a graph given in
+    GLOBAL order (edges sorted by (t', src, dst); gid = position), written out
+    with stable sorts and searches:
+
+    * OUT order (src, t', dst): the GLOBAL order stably sorted by src; IN order
+      (dst, t', src): stably sorted by dst; MULTI order (src, dst, t').
+    * *_off: list starts per vertex; *_pos: position of each gid in a list
+      order; in_to_out / multi_to_out: the OUT position of the same edge.
+    * out_xrank[x]: the first IN position of x's source whose time is >= x's
+      time (the end of that in-list if none); in_xrank the same with OUT and
+      IN swapped.
+    * pair_off / pair_dst: runs of equal (src, dst) in MULTI order;
+      vpair_off: first pair of each source.
+    * own_*: bit x of word x // 32 set when position x starts a new owner.
+
+    Names and layouts follow tm_csr_export."""
+    src = np.asarray(src, np.uint64); dst = np.asarray(dst, np.uint64); t = np.asarray(t, np.uint64)
+    m = src.shape[0]
+    ar = np.arange(m, dtype=np.uint64)
+    out_gid = np.argsort(src, kind="stable")
+    in_gid = np.argsort(dst, kind="stable")
+    multi = np.lexsort((t, dst, src))
+    out_pos = np.empty(m, np.uint64); out_pos[out_gid] = ar
+    in_pos = np.empty(m, np.uint64); in_pos[in_gid] = ar
+
+    def offsets(keys):
+        return np.concatenate([[0], np.cumsum(np.bincount(keys.astype(np.int64), minlength=n))]).astype(np.uint64)
+
+    out_key = (src[out_gid] << np.uint64(32)) | t[out_gid]
+    in_key = (dst[in_gid] << np.uint64(32)) | t[in_gid]
+    ms, md = src[multi], dst[multi]
+    head = np.ones(m, bool)
+    if m:
+        head[1:] = (ms[1:] != ms[:-1]) | (md[1:] != md[:-1])
+    heads = np.flatnonzero(head)
+
+    def bits(starts):
+        words = np.zeros(m // 32 + 1, np.uint64)
+        x = np.flatnonzero(starts).astype(np.uint64)
+        np.bitwise_or.at(words, (x >> np.uint64(5)).astype(np.int64), np.uint64(1) << (x & np.uint64(31)))
+        return words
+
+    def starts(owner):
+        b = np.ones(m, bool)
+        if m:
+            b[1:] = owner[1:] != owner[:-1]
+        return b
+
+    r = {
+        "out_off": offsets(src), "out_t": t[out_gid], "out_nbr": dst[out_gid], "out_gid": out_gid.astype(np.uint64),
+        "out_src": src[out_gid], "out_pos": out_pos,
+        "out_xrank": np.searchsorted(in_key, out_key, side="left").astype(np.uint64),
+        "in_off": offsets(dst), "in_t": t[in_gid], "in_nbr": src[in_gid], "in_gid": in_gid.astype(np.uint64),
+        "in_dst": dst[in_gid], "in_pos": in_pos,
+        "in_xrank": np.searchsorted(out_key, in_key, side="left").astype(np.uint64),
+        "in_to_out": out_pos[in_gid],
+        "vpair_off": offsets(ms[heads]), "pair_off": np.concatenate([heads, [m]]).astype(np.uint64),
+        "pair_dst": md[heads], "multi_t": t[multi], "multi_to_out": out_pos[multi],
+        "own_out": bits(starts(src[out_gid])), "own_in": bits(starts(dst[in_gid])), "own_multi": bits(head),
+    }
+    return {k: v.astype(np.uint32) for k, v in r.items()}

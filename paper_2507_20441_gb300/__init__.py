@@ -133,6 +133,7 @@ def _declare(L):
     L.tm_preprocess.argtypes = [vp]
     L.tm_graph_info.argtypes = [vp, C.POINTER(u64), C.POINTER(i64), C.POINTER(i64)]
     L.tm_edges_export.argtypes = [vp, vp, vp, vp]
+    L.tm_csr_export.argtypes = [vp, i32, vp, u64, C.POINTER(u64)]
     L.tm_set_motif.argtypes = [vp, u32, u32, vp, vp, i64, pv]
     L.tm_set_tree.argtypes = [vp, vp, u32]
     L.tm_set_constraints.argtypes = [vp, i32]
@@ -294,6 +295,21 @@ def tm_edges_export(ctx):
     s = np.zeros(m, np.uint32); d = np.zeros(m, np.uint32); t = np.zeros(m, np.uint32)
     _check(lib().tm_edges_export(ctx, _ptr(s), _ptr(d), _ptr(t)), ctx, "tm_edges_export")
     return s, d, t
+
+
+CSR_ARRAYS = ("out_off", "out_t", "out_nbr", "out_gid", "out_src", "out_pos", "out_xrank",
+              "in_off", "in_t", "in_nbr", "in_gid", "in_dst", "in_pos", "in_xrank", "in_to_out",
+              "vpair_off", "pair_off", "pair_dst", "multi_t", "multi_to_out", "own_out", "own_in", "own_multi")
+
+
+def tm_csr_export(ctx, name):
+    """One array of the temporal CSR (names as CSR_ARRAYS; see tm_csr_export in timest.h)."""
+    which = CSR_ARRAYS.index(name)
+    n = C.c_uint64()
+    _check(lib().tm_csr_export(ctx, which, None, 0, C.byref(n)), ctx, "tm_csr_export")
+    out = np.zeros(n.value, np.uint32)
+    _check(lib().tm_csr_export(ctx, which, _ptr(out), n.value, C.byref(n)), ctx, "tm_csr_export")
+    return out
 
 
 def tm_set_motif(ctx, nv, edges, order, delta):
@@ -602,6 +618,9 @@ class Context:
 
     def edges(self):
         return tm_edges_export(self.h)
+
+    def csr(self, name):
+        return tm_csr_export(self.h, name)
 
     def motif(self, nv, edges, order, delta) -> Motif:
         return Motif(self, nv, edges, order, delta)

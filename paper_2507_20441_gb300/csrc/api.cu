@@ -670,6 +670,47 @@ int tm_edges_export(tm_ctx *ctx, uint32_t *src, uint32_t *dst, uint32_t *tprime)
     return check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "edge export");
 }
 
+int tm_csr_export(tm_ctx *ctx, int array, uint32_t *host_out, uint64_t cap, uint64_t *len)
+{
+    if (!ctx) return TM_E_ARG;
+    if (!ctx->preprocessed) return set_err(ctx, TM_E_STATE, "graph not preprocessed");
+    const DevGraph &g = ctx->g;
+    const uint64_t m = g.m, n1 = (uint64_t)g.n + 1, words = m / 32 + 1;
+    const uint32_t *src = nullptr;
+    uint64_t cnt = m;
+    switch (array) {
+    case TM_CSR_OUT_OFF: src = g.out_off; cnt = n1; break;
+    case TM_CSR_OUT_T: src = g.out_t; break;
+    case TM_CSR_OUT_NBR: src = g.out_nbr; break;
+    case TM_CSR_OUT_GID: src = g.out_gid; break;
+    case TM_CSR_OUT_SRC: src = g.out_src; break;
+    case TM_CSR_OUT_POS: src = g.out_pos; break;
+    case TM_CSR_OUT_XRANK: src = g.out_xrank; break;
+    case TM_CSR_IN_OFF: src = g.in_off; cnt = n1; break;
+    case TM_CSR_IN_T: src = g.in_t; break;
+    case TM_CSR_IN_NBR: src = g.in_nbr; break;
+    case TM_CSR_IN_GID: src = g.in_gid; break;
+    case TM_CSR_IN_DST: src = g.in_dst; break;
+    case TM_CSR_IN_POS: src = g.in_pos; break;
+    case TM_CSR_IN_XRANK: src = g.in_xrank; break;
+    case TM_CSR_IN_TO_OUT: src = g.in_to_out; break;
+    case TM_CSR_VPAIR_OFF: src = g.vpair_off; cnt = n1; break;
+    case TM_CSR_PAIR_OFF: src = g.pair_off; cnt = (uint64_t)g.npairs + 1; break;
+    case TM_CSR_PAIR_DST: src = g.pair_dst; cnt = g.npairs; break;
+    case TM_CSR_MULTI_T: src = g.multi_t; break;
+    case TM_CSR_MULTI_TO_OUT: src = g.multi_to_out; break;
+    case TM_CSR_OWN_OUT: src = g.own_out; cnt = words; break;
+    case TM_CSR_OWN_IN: src = g.own_in; cnt = words; break;
+    case TM_CSR_OWN_MULTI: src = g.own_multi; cnt = words; break;
+    default: return set_err(ctx, TM_E_ARG, "unknown CSR array");
+    }
+    if (len) *len = cnt;
+    if (!host_out) return TM_OK;
+    if (cap < cnt) return set_err(ctx, TM_E_ARG, "CSR export: cap below the array's length");
+    if (cnt && src) copy_d2h(ctx, host_out, src, (size_t)cnt * 4);
+    return check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "CSR export");
+}
+
 // A motif planned on (tree, root); nullptr and *rc on failure.
 static tm_motif *new_motif(tm_ctx *ctx, const MotifDesc &M, const int *tree, int root, int64_t delta, int *rc)
 {

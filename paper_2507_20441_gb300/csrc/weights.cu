@@ -551,16 +551,20 @@ __global__ void __launch_bounds__(1024) k_guide_setup(GuideArgs A)
 
 // Edges in GLOBAL order, kGuideItems consecutive ones per thread, layer p =
 // blockIdx.y: the buckets whose lower bound falls in [cdf[x-1], cdf[x]) start
-// at edge x.  A thread finds the window of its first edge by a binary search
-// over the window starts, then steps to the next window as its edges cross
-// one, so a window of any size is spread over many threads.
+// at edge x.  A warp takes 32 x kGuideItems consecutive edges, lane l the
+// edges l, l + 32, ... of them (coalesced CDF reads); a lane finds the window
+// of its first edge by a binary search over the window starts, then steps to
+// the next window as its edges cross one, so a window of any size is spread
+// over many threads.
 constexpr int kGuideItems = 8;
 __global__ void __launch_bounds__(TB) k_guide_fill(GuideArgs A, uint32_t m)
 {
     const int p = blockIdx.y;
     const GuideLayer &L = p ? A.L[1] : A.L[0];
-    const uint32_t x0 = (blockIdx.x * blockDim.x + threadIdx.x) * (uint32_t)kGuideItems;
-    if (x0 >= m || L.nwin == 0) return;
+    const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t xs = (gt >> 5) * (32u * kGuideItems) + (gt & 31u);
+    if (xs >= m || L.nwin == 0) return;
+    const uint32_t x0 = (uint32_t)xs;
     // kk = the last window starting at or before x0 (none: x0 precedes every window)
     uint32_t lo = 0, hi = L.nwin;
     while (lo < hi) {
@@ -568,8 +572,9 @@ __global__ void __launch_bounds__(TB) k_guide_fill(GuideArgs A, uint32_t m)
         if (L.win_beg[mid] <= x0) lo = mid + 1; else hi = mid;
     }
     int64_t kk = (int64_t)lo - 1;
-    const uint32_t x1 = min(m, x0 + (uint32_t)kGuideItems);
-    for (uint32_t x = x0; x < x1; ++x) {
+    const uint64_t xe = min((uint64_t)m, (uint64_t)(xs + 32u * kGuideItems));
+    for (uint64_t xx = xs; xx < xe; xx += 32) {
+        const uint32_t x = (uint32_t)xx;
         while (kk + 1 < (int64_t)L.nwin && L.win_beg[kk + 1] <= x) ++kk;
         if (kk < 0) continue;   // before the layer's first window
         const uint32_t wbeg = L.win_beg[kk], wend = L.win_beg[kk + 1];
@@ -753,11 +758,11 @@ int compute_weights(tm_ctx *ctx, tm_motif *mo)
                 LayerData &L = mo->layer[p];
                 ga.L[p] = GuideLayer{L.root_cdf, L.win_beg, L.nwin, L.win_gshift, L.win_goff, L.guide};
             }
-            // guide tables of the root search, both layers (a warp per window)
+            // guide tables of the root search, both layers (edge-parallel)
             if (m && nwh[0] + nwh[1]) {
                 launch(ctx, k_guide_setup, 2, 1024, ga);
-                launch(ctx, k_guide_fill, dim3(blocks_for(((uint64_t)m + kGuideItems - 1) / kGuideItems, TB), 2), TB,
-                       ga, m);
+                const uint64_t gwarps = ((uint64_t)m + 32 * kGuideItems - 1) / (32 * kGuideItems);
+                launch(ctx, k_guide_fill, dim3(blocks_for(gwarps * 32, TB), 2), TB, ga, m);
             }
         } else {
             PhaseScope ph(ctx, TM_PH_PREFIX);
