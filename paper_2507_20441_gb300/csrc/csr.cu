@@ -34,8 +34,8 @@ namespace timest {
 namespace {
 
 // ---- radix sort --------------------------------------------------------
-// Keys are sorted least significant digit first, with up to 9-bit digits
-// (a 17-bit vertex id takes two passes, a 25-bit time three).  A pass is
+// Keys are sorted least significant digit first, with up to 7-bit digits
+// (a 21-bit vertex id takes three passes, a 27-bit time four).  A pass is
 //   1. per-tile digit counts (4096 keys per tile), stored digit-major;
 //   2. an exclusive scan of those counts, which gives, for every (digit,
 //      tile), where the tile's run of that digit starts in the output;
@@ -55,14 +55,19 @@ constexpr int OS_ITEMS = TM_RS_ITEMS;
 constexpr int OS_TILE = OS_THREADS * OS_ITEMS;     // 4096 keys per tile
 constexpr int OS_WARPS = OS_THREADS / 32;
 constexpr int OS_WCHUNK = OS_ITEMS * 32;           // keys per warp chunk
-constexpr int OS_MAXBITS = 9;
+#ifndef TM_RS_MAXBITS
+#define TM_RS_MAXBITS 7   // measured: 7-bit digits beat 9 (a 27-bit time in four passes instead of three)
+#endif
+constexpr int OS_MAXBITS = TM_RS_MAXBITS;
 constexpr int OS_MAXRADIX = 1 << OS_MAXBITS;
-constexpr int OS_MAXPASS = 4;
+constexpr int OS_SCAN = 512;   // entries of the block scan of the digit totals (two per thread)
+static_assert(OS_MAXRADIX <= OS_SCAN && OS_THREADS * 2 == OS_SCAN, "digit scan layout");
+constexpr int OS_MAXPASS = (32 + OS_MAXBITS - 1) / OS_MAXBITS;   // any 32-bit key
 // dynamic shared memory of a scatter pass with np payload arrays
-constexpr size_t os_smem(int np)
+[[maybe_unused]] constexpr size_t os_smem(int np)
 {
     return (size_t)OS_TILE * 4 * (1 + np) + (size_t)OS_TILE * 2 + (size_t)OS_WARPS * OS_MAXRADIX * 2 +
-           (size_t)OS_MAXRADIX * 4 * 2;
+           (size_t)(OS_SCAN + OS_MAXRADIX) * 4;
 }
 
 // per-tile digit counts, written to counts[d * ntiles + tile].  Each warp
@@ -186,7 +191,7 @@ __global__ void __launch_bounds__(OS_THREADS, NP >= 3 ? 2 : NP >= 2 ? 3 : 4)
     uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_p3 + (NP >= 4 ? OS_TILE : 0));
     uint16_t *s_wcnt = s_rank + OS_TILE;                                            // [warp][digit]
     uint32_t *s_tex = reinterpret_cast<uint32_t *>(s_wcnt + OS_WARPS * OS_MAXRADIX);  // digit start in the tile
-    uint32_t *s_gpos = s_tex + OS_MAXRADIX;                                         // digit start in the output
+    uint32_t *s_gpos = s_tex + OS_SCAN;                                             // digit start in the output
     __shared__ uint32_t s_wt[OS_WARPS];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const uint32_t radix = 1u << bits, dmask = radix - 1u;
@@ -238,7 +243,7 @@ __global__ void __launch_bounds__(OS_THREADS, NP >= 3 ? 2 : NP >= 2 ? 3 : 4)
     }
     __syncthreads();
     // ---- per digit: tile total and warp offsets
-    for (uint32_t d = t; d < (uint32_t)OS_MAXRADIX; d += OS_THREADS) {
+    for (uint32_t d = t; d < (uint32_t)OS_SCAN; d += OS_THREADS) {   // entries past the radix: 0
         uint32_t run = 0;
         if (d < radix)
             for (int w = 0; w < OS_WARPS; ++w) {
@@ -289,13 +294,17 @@ __global__ void __launch_bounds__(OS_THREADS, NP >= 3 ? 2 : NP >= 2 ? 3 : 4)
 #ifndef TM_RS_STAGED
 #define TM_RS_STAGED 1
 #endif
-constexpr size_t os_smem_staged()
+#ifndef TM_RS_ST_MINB
+#define TM_RS_ST_MINB 4   // blocks per SM the staged pass is compiled for (64 registers)
+#endif
+[[maybe_unused]] constexpr size_t os_smem_staged()
 {
-    return (size_t)OS_TILE * 4 * 2 + (size_t)OS_TILE * 2 + (size_t)OS_WARPS * OS_MAXRADIX * 2 + (size_t)OS_MAXRADIX * 4 * 2;
+    return (size_t)OS_TILE * 4 * 2 + (size_t)OS_TILE * 2 + (size_t)OS_WARPS * OS_MAXRADIX * 2 +
+           (size_t)(OS_SCAN + OS_MAXRADIX) * 4;
 }
 
 template <int NP>
-__global__ void __launch_bounds__(OS_THREADS, 4)
+__global__ void __launch_bounds__(OS_THREADS, TM_RS_ST_MINB)
     k_rs_scatter_st(RsJobs J, uint32_t n, int shift, int bits, uint32_t ntiles, const uint32_t *__restrict__ offs_all)
 {
     const uint32_t job = blockIdx.x >= ntiles ? 1u : 0u, tile = blockIdx.x - job * ntiles;
@@ -309,8 +318,8 @@ __global__ void __launch_bounds__(OS_THREADS, 4)
     uint32_t *s_g = s_buf + OS_TILE;                                              // output position by tile slot
     uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_g + OS_TILE);               // rank, then tile slot, by input
     uint16_t *s_wcnt = s_rank + OS_TILE;                                          // [warp][digit]
-    uint32_t *s_tex = reinterpret_cast<uint32_t *>(s_wcnt + OS_WARPS * OS_MAXRADIX);
-    uint32_t *s_gpos = s_tex + OS_MAXRADIX;
+    uint32_t *s_tex = reinterpret_cast<uint32_t *>(s_wcnt + OS_WARPS * OS_MAXRADIX);   // OS_SCAN entries
+    uint32_t *s_gpos = s_tex + OS_SCAN;
     __shared__ uint32_t s_wt[OS_WARPS];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const uint32_t radix = 1u << bits, dmask = radix - 1u;
@@ -335,6 +344,9 @@ __global__ void __launch_bounds__(OS_THREADS, 4)
         const bool valid = base + li < n;
         const uint32_t d = valid ? ((kv[j] >> shift) & dmask) : radix;
         uint32_t peers;
+#if TM_RS_MATCH
+        peers = __match_any_sync(0xffffffffu, d);
+#else
         if (__all_sync(0xffffffffu, d == __shfl_sync(0xffffffffu, d, 0))) {
             peers = 0xffffffffu;
         } else {
@@ -345,6 +357,7 @@ __global__ void __launch_bounds__(OS_THREADS, 4)
                 peers &= ((d >> b) & 1u) ? bb : ~bb;
             }
         }
+#endif
         uint32_t cur = valid ? wc[d] : 0;
         __syncwarp();
         if (valid) {
@@ -354,7 +367,7 @@ __global__ void __launch_bounds__(OS_THREADS, 4)
         __syncwarp();
     }
     __syncthreads();
-    for (uint32_t d = t; d < (uint32_t)OS_MAXRADIX; d += OS_THREADS) {
+    for (uint32_t d = t; d < (uint32_t)OS_SCAN; d += OS_THREADS) {   // entries past the radix: 0
         uint32_t run = 0;
         if (d < radix)
             for (int w = 0; w < OS_WARPS; ++w) {
@@ -483,11 +496,18 @@ __global__ void __launch_bounds__(OS_THREADS, 4) k_inv_bucket(const uint32_t *__
     }
 }
 
+// four pairs per thread (16-byte loads; the work arrays are 256-byte aligned)
 __global__ void k_inv_fill(const uint32_t *__restrict__ tkey, const uint32_t *__restrict__ tpos, uint32_t n,
                            uint32_t *__restrict__ inv)
 {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) inv[__ldg(tkey + i)] = __ldg(tpos + i);
+    const uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (i + 4 <= n) {
+        const uint4 k = __ldg(reinterpret_cast<const uint4 *>(tkey + i));
+        const uint4 p = __ldg(reinterpret_cast<const uint4 *>(tpos + i));
+        inv[k.x] = p.x; inv[k.y] = p.y; inv[k.z] = p.z; inv[k.w] = p.w;
+    } else {
+        for (uint64_t j = i; j < n; ++j) inv[__ldg(tkey + j)] = __ldg(tpos + j);
+    }
 }
 
 int bits_for(uint64_t maxval)
@@ -567,7 +587,7 @@ int radix_sort_sets(tm_ctx *ctx, const RsHost *sets, int nsets, uint32_t n, int 
     if (nsets > 2) return set_err(ctx, TM_E_LIMIT, "at most two arrays per radix sort");
     const int np = sets[0].p1 ? 2 : (sets[0].p0 ? 1 : 0);
     const int npass = (bits + OS_MAXBITS - 1) / OS_MAXBITS;
-    if (npass > OS_MAXPASS) return set_err(ctx, TM_E_LIMIT, "radix key wider than 36 bits");
+    if (npass > OS_MAXPASS) return set_err(ctx, TM_E_LIMIT, "radix key wider than 32 bits");
     const uint32_t ntiles = (n + OS_TILE - 1) / OS_TILE;
     uint32_t *counts = (uint32_t *)salloc(ctx, (size_t)nsets * ntiles * OS_MAXRADIX * 4);
     if (!counts) return TM_E_NOMEM;
@@ -624,7 +644,8 @@ static int inverse_perm(tm_ctx *ctx, const uint32_t *perm, uint32_t n, uint32_t 
     const uint32_t nb = (uint32_t)(((uint64_t)(n - 1) >> shift) + 1);
     launch(ctx, k_inv_cursor, 1, IB_MAXB, cursor, nb, shift);
     launch(ctx, k_inv_bucket, (n + OS_TILE - 1) / OS_TILE, OS_THREADS, perm, n, shift, nb, cursor, tkey, tpos);
-    launch(ctx, k_inv_fill, (n + 255) / 256, 256, (const uint32_t *)tkey, (const uint32_t *)tpos, n, inv);
+    launch(ctx, k_inv_fill, (unsigned)(((uint64_t)n + 1023) / 1024), 256, (const uint32_t *)tkey, (const uint32_t *)tpos,
+           n, inv);
     return check_cuda(ctx, cudaGetLastError(), "inverse permutation");
 }
 
@@ -674,7 +695,7 @@ int radix_sort_sets_to(tm_ctx *ctx, const RsTo *sets, int nsets, uint32_t n, int
         return TM_OK;
     }
     const int npass = (bits + OS_MAXBITS - 1) / OS_MAXBITS;
-    if (npass > OS_MAXPASS) return set_err(ctx, TM_E_LIMIT, "radix key wider than 36 bits");
+    if (npass > OS_MAXPASS) return set_err(ctx, TM_E_LIMIT, "radix key wider than 32 bits");
     const uint32_t ntiles = (n + OS_TILE - 1) / OS_TILE;
     uint32_t *counts = (uint32_t *)salloc(ctx, (size_t)nsets * ntiles * OS_MAXRADIX * 4);
     if (!counts) return TM_E_NOMEM;

@@ -60,3 +60,15 @@ def test_csr_chung_lu(tg, oracle_mod, n, m):
     from paper_2507_20441_gb300 import synth
     gr = synth.chung_lu_bursty(n, m, 2.1, 30_000_000, 3)
     check_csr(tg, oracle_mod, gr.n, gr.src, gr.dst, gr.t)
+
+
+def test_csr_wide_time_span(tg, oracle_mod):
+    """Times over almost the whole u32 range of t' (negative inputs, span
+    2^32 - 2): the time sort's widest key, five 7-bit passes."""
+    rng = np.random.default_rng(11)
+    n, m = 1000, 5003
+    s = rng.integers(0, n, m).astype(np.uint32)
+    d = ((s + 1 + rng.integers(0, n - 1, m)) % n).astype(np.uint32)
+    t = rng.integers(-2**31 + 1, 2**31 - 1, m).astype(np.int64)
+    t[0], t[1] = -2**31, 2**31 - 2
+    check_csr(tg, oracle_mod, n, s, d, t, dedup=True)
