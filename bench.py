@@ -397,10 +397,13 @@ def run_ours(args, rank, world, local_rank):
         n_e2e = max(5, args.steps // 4)
         t_e2e, _ = timed(n_e2e, host=True, base=30_000)
         h2d, d2h = ctx.io_bytes()
-        ctx.phase_times(); ctx.kernel_times()
+        ph_e2e = ctx.phase_times()
+        ctx.kernel_times()
         e2e = {"value": world * k * n_e2e / (sum(t_e2e) / 1e3), "unit": "samples/s",
                "h2d_bytes_per_step": h2d // n_e2e, "d2h_bytes_per_step": d2h // n_e2e,
-               "ms_per_step": sum(t_e2e) / n_e2e}
+               "ms_per_step": sum(t_e2e) / n_e2e,
+               "phases_ms_per_step": {nm: round(v / n_e2e, 4) for nm, (v, _) in ph_e2e.items()
+                                      if "." not in nm and v > 0}}
 
     # ---- roofline of the kernel that leads the live per-kernel list
     peak, peak_kind = measured_peaks()

@@ -833,7 +833,9 @@ __global__ void k_compact_input(const uint32_t *__restrict__ src, const uint32_t
 }
 
 // After the GLOBAL sort: flag tuples equal to their predecessor.
-// After a sort by t' alone: order each run of equal t' by (src, dst).  Runs
+// After a sort by t' alone: order each run of equal t' by (src, dst), and
+// count the tuples equal to their predecessor (repeats lie inside a run), so
+// the flags above are made only when there are repeats.  Runs
 // of up to kRunMax edges are sorted by their head's thread; runs of up to
 // kBlockRunMax are listed (start, length) for k_order_long_runs; a longer run
 // is flagged and the caller sorts by all three keys instead.
@@ -841,7 +843,7 @@ constexpr uint32_t kRunMax = 32;
 constexpr uint32_t kBlockRunMax = 4096;
 __global__ void k_order_runs(const uint32_t *__restrict__ t, uint32_t *__restrict__ s, uint32_t *__restrict__ d,
                              uint32_t m, uint32_t *__restrict__ too_long, uint2 *__restrict__ long_runs,
-                             uint32_t *__restrict__ n_long)
+                             uint32_t *__restrict__ n_long, unsigned long long *__restrict__ ndup)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m || (i > 0 && t[i - 1] == t[i])) return;   // run heads only
@@ -868,6 +870,8 @@ __global__ void k_order_runs(const uint32_t *__restrict__ t, uint32_t *__restric
         s[i + 1] = (uint32_t)(k1 >> 32); d[i + 1] = (uint32_t)k1;
         if (len > 2) { s[i + 2] = (uint32_t)(k2 >> 32); d[i + 2] = (uint32_t)k2; }
         if (len > 3) { s[i + 3] = (uint32_t)(k3 >> 32); d[i + 3] = (uint32_t)k3; }
+        const uint32_t dups = (k0 == k1) + (len > 2 && k1 == k2) + (len > 3 && k2 == k3);
+        if (dups) atomicAdd(ndup, (unsigned long long)dups);
         return;
     }
     uint64_t key[kRunMax];
@@ -878,7 +882,12 @@ __global__ void k_order_runs(const uint32_t *__restrict__ t, uint32_t *__restric
         while (q > 0 && key[q - 1] > x) { key[q] = key[q - 1]; --q; }
         key[q] = x;
     }
-    for (uint32_t k = 0; k < len; ++k) { s[i + k] = (uint32_t)(key[k] >> 32); d[i + k] = (uint32_t)key[k]; }
+    uint32_t dups = 0;
+    for (uint32_t k = 0; k < len; ++k) {
+        s[i + k] = (uint32_t)(key[k] >> 32); d[i + k] = (uint32_t)key[k];
+        dups += k > 0 && key[k] == key[k - 1];
+    }
+    if (dups) atomicAdd(ndup, (unsigned long long)dups);
 }
 
 // One block per listed run (33 .. kBlockRunMax edges): bitonic sort of the
@@ -886,7 +895,8 @@ __global__ void k_order_runs(const uint32_t *__restrict__ t, uint32_t *__restric
 // length is read on the device.
 __global__ void __launch_bounds__(256) k_order_long_runs(uint32_t *__restrict__ s, uint32_t *__restrict__ d,
                                                          const uint2 *__restrict__ long_runs,
-                                                         const uint32_t *__restrict__ n_long)
+                                                         const uint32_t *__restrict__ n_long,
+                                                         unsigned long long *__restrict__ ndup)
 {
     __shared__ uint64_t key[kBlockRunMax];
     const uint32_t nl = *n_long;
@@ -909,10 +919,13 @@ __global__ void __launch_bounds__(256) k_order_long_runs(uint32_t *__restrict__ 
                 }
                 __syncthreads();
             }
+        uint32_t dups = 0;
         for (uint32_t k = threadIdx.x; k < run.y; k += blockDim.x) {
             s[run.x + k] = (uint32_t)(key[k] >> 32);
             d[run.x + k] = (uint32_t)key[k];
+            dups += k > 0 && key[k] == key[k - 1];
         }
+        if (dups) atomicAdd(ndup, (unsigned long long)dups);
         __syncthreads();
     }
 }
@@ -1144,10 +1157,9 @@ int build_csr(tm_ctx *ctx)
         cudaMemsetAsync(nd, 0, 24, st);
         if (m) {
             launch(ctx, k_order_runs, blocks_for(m, TB), TB, (const uint32_t *)g.g_t, g.g_src, g.g_dst, m,
-                   (uint32_t *)(nd + 1), long_runs, (uint32_t *)(nd + 2));
+                   (uint32_t *)(nd + 1), long_runs, (uint32_t *)(nd + 2), nd);
             launch(ctx, k_order_long_runs, (unsigned)ctx->num_sms * 2, 256, g.g_src, g.g_dst, (const uint2 *)long_runs,
-                   (const uint32_t *)(nd + 2));
-            launch(ctx, k_flag_unique, blocks_for(m, TB), TB, g.g_t, g.g_src, g.g_dst, m, keep, nd);
+                   (const uint32_t *)(nd + 2), nd);
         }
         unsigned long long hnd[2] = {0, 0};
         copy_d2h(ctx, hnd, nd, 16);
@@ -1167,6 +1179,10 @@ int build_csr(tm_ctx *ctx)
         const unsigned long long ndup = hnd[0];
         if (ndup && !(ctx->load_flags & TM_DEDUP)) {
             return set_err(ctx, TM_E_DUP, "input repeats a (u,v,t) tuple (pass TM_DEDUP to drop repeats)");
+        }
+        if (ndup && !hnd[1]) {   // the run kernels only counted the repeats: flag them (same count)
+            cudaMemsetAsync(nd, 0, 8, st);
+            launch(ctx, k_flag_unique, blocks_for(m, TB), TB, g.g_t, g.g_src, g.g_dst, m, keep, nd);
         }
         if (ndup) {
             // compact into the work arrays, then back

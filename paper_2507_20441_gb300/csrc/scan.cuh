@@ -335,8 +335,11 @@ __device__ __forceinline__ void seg_publish(SegTile *t, const SegAgg2 &v, uint32
     vt->status = st;
 }
 
+#ifndef TM_SCAN_MINB
+#define TM_SCAN_MINB 4   // 64 registers, four blocks per SM: measured 1.50 against 1.71 ms uncapped (76 registers)
+#endif
 template <class F>
-__global__ void __launch_bounds__(SCAN_THREADS) k_segscan2_onepass(F f, uint64_t n, SegTile *__restrict__ tiles,
+__global__ void __launch_bounds__(SCAN_THREADS, TM_SCAN_MINB) k_segscan2_onepass(F f, uint64_t n, SegTile *__restrict__ tiles,
                                                                    uint32_t *__restrict__ counter,
                                                                    ulonglong2 *__restrict__ keep,
                                                                    uint64_t *__restrict__ out0,
