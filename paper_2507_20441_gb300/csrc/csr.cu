@@ -1024,10 +1024,12 @@ struct XR {
     const uint32_t *own_t, *owner, *other_off, *other_t;
     uint32_t *xrank;
 };
-// (Letting the first and last lanes of a warp whose entries share one owner
-// search first, and the other lanes only the bracket those give, measured
-// slower: 1.32 against 1.26 ms on 5e7 entries per list, the bracket's extra
-// dependent probes outweighing the probes saved.)
+// Two alternatives measured slower on 5e7 entries per list: letting the
+// first and last lanes of a warp whose entries share one owner search first
+// and the other lanes only the bracket those give (1.32 against 1.25 ms), and
+// merging each vertex's two lists along a merge path in chunks of 128 entries
+// per thread (1.44 ms: the chunk walk is one long chain of dependent loads).
+// The independent searches keep the most loads in flight.
 __global__ void k_cross_rank(XR a, XR b, uint32_t m)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;

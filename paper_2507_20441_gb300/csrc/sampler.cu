@@ -566,7 +566,10 @@ __device__ __forceinline__ void add_tallies(Acc *acc, u128 hits, unsigned long l
     }
 }
 
-constexpr int kSampleThreads = 256;
+#ifndef TM_SAMPLE_THREADS
+#define TM_SAMPLE_THREADS 256
+#endif
+constexpr int kSampleThreads = TM_SAMPLE_THREADS;
 #ifndef TM_SAMPLE_MINB
 #define TM_SAMPLE_MINB 4   // 64 registers, four blocks of 256 per SM (measured faster than 48 or 40 registers)
 #endif

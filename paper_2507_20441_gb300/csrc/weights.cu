@@ -552,10 +552,10 @@ __global__ void __launch_bounds__(1024) k_guide_setup(GuideArgs A)
 // Edges in GLOBAL order, kGuideItems consecutive ones per thread, layer p =
 // blockIdx.y: the buckets whose lower bound falls in [cdf[x-1], cdf[x]) start
 // at edge x.  A warp takes 32 x kGuideItems consecutive edges, lane l the
-// edges l, l + 32, ... of them (coalesced CDF reads); a lane finds the window
-// of its first edge by a binary search over the window starts, then steps to
-// the next window as its edges cross one, so a window of any size is spread
-// over many threads.
+// edges l, l + 32, ... of them (coalesced CDF reads); the warp finds the
+// window of its first edge by a binary search over the window starts, and a
+// lane steps to the next window as its edges cross one, so a window of any
+// size is spread over many threads.
 constexpr int kGuideItems = 8;
 __global__ void __launch_bounds__(TB) k_guide_fill(GuideArgs A, uint32_t m)
 {
@@ -564,8 +564,10 @@ __global__ void __launch_bounds__(TB) k_guide_fill(GuideArgs A, uint32_t m)
     const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t xs = (gt >> 5) * (32u * kGuideItems) + (gt & 31u);
     if (xs >= m || L.nwin == 0) return;
-    const uint32_t x0 = (uint32_t)xs;
-    // kk = the last window starting at or before x0 (none: x0 precedes every window)
+    // kk = the last window starting at or before the warp's first edge x0
+    // (none: x0 precedes every window); the same search in every lane, so
+    // each probe is one broadcast load
+    const uint32_t x0 = (uint32_t)(xs - (gt & 31u));
     uint32_t lo = 0, hi = L.nwin;
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
