@@ -98,14 +98,19 @@ __global__ void __launch_bounds__(256, TM_DP_MINB) k_dp(DevGraph g, DevPlan P, W
         const uint32_t o = P.c2 ? __ldg((side ? g.in_nbr : g.out_nbr) + pos) : kNone;
         const uint64_t d = (uint64_t)P.delta, wd = (uint64_t)wv.d;
         const uint32_t qt = wv.quot(t);
-        uint64_t wlo[2], whi[2], prod[2] = {1, 1};
+        // window bounds as 32-bit times: wlo <= t fits, whi is clamped to the
+        // largest t' (no time lies beyond it), which leaves every comparison
+        // below unchanged and keeps the bounds in half the registers
+        uint32_t wlo[2], whi[2];
+        uint64_t prod[2] = {1, 1};
         bool zero[2], ovf[2] = {false, false};
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
             const int64_t wi = WinDiv::win_of(qt, p);
             zero[p] = wi < 0;
-            wlo[p] = zero[p] ? 0 : (uint64_t)wi * wd;
-            whi[p] = zero[p] ? 0 : ((uint64_t)wi + 2) * wd - 1;
+            const uint64_t whi64 = ((uint64_t)wi + 2) * wd - 1;
+            wlo[p] = zero[p] ? 0u : (uint32_t)((uint64_t)wi * wd);
+            whi[p] = zero[p] ? 0u : (whi64 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)whi64);
         }
         if (!first) {
             const uint32_t xp = __ldg(g.in_to_out + pos);   // side 1 reads side 0's partial (both layers)
@@ -125,7 +130,8 @@ __global__ void __launch_bounds__(256, TM_DP_MINB) k_dp(DevGraph g, DevPlan P, W
             const int c = P.child[q][ci];
             if (P.tzside[c] != side) continue;
             const bool out = P.tout[c] != 0, later = P.tlater[c] != 0, leaf = P.tleaf[c] != 0;
-            if (!later && t == 0) { zero[0] = zero[1] = true; break; }
+            // no earlier time than 0, no later one than the largest t'
+            if ((!later && t == 0) || (later && t == 0xFFFFFFFFu)) { zero[0] = zero[1] = true; break; }
             const uint32_t *off = out ? g.out_off : g.in_off;
             const uint32_t *tarr = out ? g.out_t : g.in_t;
             const uint32_t *nbr = out ? g.out_nbr : g.in_nbr;
@@ -133,22 +139,22 @@ __global__ void __launch_bounds__(256, TM_DP_MINB) k_dp(DevGraph g, DevPlan P, W
             const uint32_t base = ((side == 0) == out) ? gallop_back(tarr, beg, pos, t)
                                                        : __ldg((side == 0 ? g.out_xrank : g.in_xrank) + pos);
             // per-layer ranges [a[p], b[p]) with times in [lo[p], hi[p]]
-            uint32_t a[2], b[2];
-            uint64_t lo[2], hi[2];
+            uint32_t a[2], b[2], lo[2], hi[2];
             if (later) {
-                const uint64_t l0 = (uint64_t)t + 1, hu = (uint64_t)t + d;
+                const uint64_t hu64 = (uint64_t)t + d;
+                const uint32_t l0 = t + 1, hu = hu64 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)hu64;
                 const uint32_t a0 = gallop_idx(tarr, base, end, l0);
-                const uint32_t bu = gallop_idx(tarr, a0, end, hu + 1);
+                const uint32_t bu = gallop_idx(tarr, a0, end, (uint64_t)hu + 1);
 #pragma unroll
                 for (int p = 0; p < 2; ++p) {
                     lo[p] = l0;
                     hi[p] = hu < whi[p] ? hu : whi[p];
                     a[p] = a0;
-                    b[p] = (zero[p] || hi[p] == hu) ? bu : lower_idx(tarr, a0, bu, hi[p] + 1);
+                    b[p] = (zero[p] || hi[p] == hu) ? bu : lower_idx(tarr, a0, bu, (uint64_t)hi[p] + 1);
                     if (lo[p] > hi[p]) zero[p] = true;
                 }
             } else {
-                const uint64_t h0 = (uint64_t)t - 1, lu = (uint64_t)t >= d ? (uint64_t)t - d : 0;
+                const uint32_t h0 = t - 1, lu = (uint64_t)t >= d ? (uint32_t)((uint64_t)t - d) : 0u;
                 const uint32_t au = gallop_back(tarr, beg, base, lu);
 #pragma unroll
                 for (int p = 0; p < 2; ++p) {
@@ -177,8 +183,8 @@ __global__ void __launch_bounds__(256, TM_DP_MINB) k_dp(DevGraph g, DevPlan P, W
                     const ulonglong2 px = __ldg(Pd + x);
                     const ulonglong2 pp = x > beg ? __ldg(Pd + x - 1) : make_ulonglong2(0, 0);
                     const uint32_t tp = x > beg ? __ldg(tarr + x - 1) : 0;
-                    wx2.x = px.x - ((x > beg && (uint64_t)tp >= wlo[0]) ? pp.x : 0);
-                    wx2.y = px.y - ((x > beg && (uint64_t)tp >= wlo[1]) ? pp.y : 0);
+                    wx2.x = px.x - ((x > beg && tp >= wlo[0]) ? pp.x : 0);
+                    wx2.y = px.y - ((x > beg && tp >= wlo[1]) ? pp.y : 0);
                 }
 #pragma unroll
                 for (int p = 0; p < 2; ++p)
@@ -200,13 +206,13 @@ __global__ void __launch_bounds__(256, TM_DP_MINB) k_dp(DevGraph g, DevPlan P, W
                     for (int p = 0; p < 2; ++p) {
                         if (zero[p]) continue;
                         const uint32_t ea = lower_idx(g.multi_t, xb, xe, lo[p]);
-                        const uint32_t eb = gallop_idx(g.multi_t, ea, xe, hi[p] + 1);
+                        const uint32_t eb = gallop_idx(g.multi_t, ea, xe, (uint64_t)hi[p] + 1);
                         if (eb <= ea) continue;
                         if (leaf) {
                             excl[p] = eb - ea;
                         } else {
                             const ulonglong2 *Pm = pick_slot(cp.pm, P.tslot[c]);
-                            const uint64_t bs = (ea > xb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo[p])
+                            const uint64_t bs = (ea > xb && __ldg(g.multi_t + ea - 1) >= wlo[p])
                                                     ? lane_of(__ldg(Pm + ea - 1), p) : 0;
                             excl[p] = lane_of(__ldg(Pm + eb - 1), p) - bs;
                         }
@@ -221,7 +227,7 @@ __global__ void __launch_bounds__(256, TM_DP_MINB) k_dp(DevGraph g, DevPlan P, W
                     sum = (uint64_t)(b[p] - a[p]) - excl[p];
                 } else if (b[p] > a[p]) {
                     const uint64_t top = lane_of(__ldg(Pd + b[p] - 1), p);
-                    const uint64_t pbase = (a[p] > beg && (uint64_t)__ldg(tarr + a[p] - 1) >= wlo[p])
+                    const uint64_t pbase = (a[p] > beg && __ldg(tarr + a[p] - 1) >= wlo[p])
                                                ? lane_of(__ldg(Pd + a[p] - 1), p) : 0;
                     sum = top - pbase - excl[p];
                 } else {
