@@ -274,7 +274,7 @@ __device__ uint64_t complete_count(const DevGraph &g, const DevPlan &P, const Wi
 // layer p, the window's time range [wlo, whi] and the root edge id; 0, or -1
 // on an internal inconsistency (latched as ST_BADSTATE).
 __device__ __forceinline__ int sample_root(const DevPlan &P, const SampleJob &J, SampleRng &rng, uint32_t *status,
-                                           int &p, uint64_t &wlo, uint64_t &whi, uint32_t &root)
+                                           int &p, uint32_t &wlo, uint32_t &whi, uint32_t &root)
 {
     const u128 W = (u128)J.W_lo | ((u128)J.W_hi << 64);
     u128 r = rng.below128(W, status);
@@ -297,8 +297,11 @@ __device__ __forceinline__ int sample_root(const DevPlan &P, const SampleJob &J,
     const uint32_t wbeg = __ldg(wb + kk), wend = __ldg(wb + kk + 1);
     const uint64_t wi = __ldg((p ? J.win_id1 : J.win_id0) + kk);
     const uint64_t wd = (uint64_t)P.wdelta;
-    wlo = wi * wd;
-    whi = (wi + 2) * wd - 1;
+    // 32-bit bounds: the window holds the root's time, so wlo fits; whi is
+    // clamped to the largest t' (no time lies beyond it)
+    wlo = (uint32_t)(wi * wd);
+    const uint64_t whi64 = (wi + 2) * wd - 1;
+    whi = whi64 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)whi64;
     // the root edge lies between two guide entries: the first edges whose CDF
     // exceeds the bucket bounds below and above rr
     const uint32_t gsh = __ldg((p ? J.win_gshift1 : J.win_gshift0) + kk);
@@ -317,7 +320,7 @@ __device__ __forceinline__ int sample_root(const DevPlan &P, const SampleJob &J,
 // with children or when `ids` is set, its edge id; 0, or -1 on an
 // internal inconsistency (latched as ST_BADSTATE).
 __device__ __forceinline__ int sample_child(const DevGraph &g, const DevPlan &P, const SampleJob &J, int q, int p,
-                                            uint64_t wlo, uint64_t whi, SampleRng &rng, uint32_t *status,
+                                            uint32_t wlo, uint32_t whi, SampleRng &rng, uint32_t *status,
                                             uint32_t ps, uint32_t pd, uint32_t pt, uint32_t pgid,
                                             bool ids, uint32_t &ct, uint32_t &cs, uint32_t &cd, uint32_t &cgid)
 {
@@ -332,8 +335,8 @@ __device__ __forceinline__ int sample_child(const DevGraph &g, const DevPlan &P,
         tlo = (uint64_t)pt >= d ? (uint64_t)pt - d : 0;
         thi = (uint64_t)pt - 1;
     }
-    tlo = tlo < wlo ? wlo : tlo;
-    thi = thi > whi ? whi : thi;
+    tlo = tlo < (uint64_t)wlo ? (uint64_t)wlo : tlo;
+    thi = thi > (uint64_t)whi ? (uint64_t)whi : thi;
     const uint32_t *nbr = out ? g.out_nbr : g.in_nbr;
     const uint32_t *gids = out ? g.out_gid : g.in_gid;
     // the parent edge's position in the meeting vertex's out-list (z is its
@@ -363,8 +366,8 @@ __device__ __forceinline__ int sample_child(const DevGraph &g, const DevPlan &P,
         // layer p's lane of the slot's (layer 0, layer 1) prefix pairs
         Pd = (const uint64_t *)J.pref_dir[slot] + p;
         Pm = (const uint64_t *)J.pref_multi[slot] + p;
-        base = (a > beg && (uint64_t)__ldg(tarr + a - 1) >= wlo) ? __ldg(Pd + 2 * (size_t)(a - 1)) : 0;
-        base_m = (ea > pb && (uint64_t)__ldg(g.multi_t + ea - 1) >= wlo) ? __ldg(Pm + 2 * (size_t)(ea - 1)) : 0;
+        base = (a > beg && __ldg(tarr + a - 1) >= wlo) ? __ldg(Pd + 2 * (size_t)(a - 1)) : 0;
+        base_m = (ea > pb && __ldg(g.multi_t + ea - 1) >= wlo) ? __ldg(Pm + 2 * (size_t)(ea - 1)) : 0;
         const uint64_t sr = b > a ? __ldg(Pd + 2 * (size_t)(b - 1)) - base : 0;
         const uint64_t se = eb > ea ? __ldg(Pm + 2 * (size_t)(eb - 1)) - base_m : 0;
         total = sr - se;
@@ -412,7 +415,7 @@ __device__ int sample_tree(const DevGraph &g, const DevPlan &P, const SampleJob 
     SampleRng rng;
     rng.init(seed, j);
     int p;
-    uint64_t wlo, whi;
+    uint32_t wlo, whi;
     uint32_t root;
     if (sample_root(P, J, rng, status, p, wlo, whi, root)) return -1;
     load_edge(g, root, R, 0);
@@ -473,7 +476,7 @@ __device__ __forceinline__ int sample_one_reg(const DevGraph &g, const DevPlan &
     SampleRng rng;
     rng.init(seed, j);
     int p;
-    uint64_t wlo, whi;
+    uint32_t wlo, whi;
     uint32_t root;
     if (sample_root(P, J, rng, status, p, wlo, whi, root)) return -1;
     // Alg. 3: the root edge, then each node from its parent (parents come first)

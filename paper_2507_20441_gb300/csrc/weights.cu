@@ -562,7 +562,10 @@ __global__ void __launch_bounds__(1024) k_guide_setup(GuideArgs A)
 // window of its first edge by a binary search over the window starts, and a
 // lane steps to the next window as its edges cross one, so a window of any
 // size is spread over many threads.
-constexpr int kGuideItems = 8;
+#ifndef TM_GUIDE_ITEMS
+#define TM_GUIDE_ITEMS 32   // measured: 32 edges per lane beat 8 (1.77 against 1.81 ms for the root phase) and 2
+#endif
+constexpr int kGuideItems = TM_GUIDE_ITEMS;
 __global__ void __launch_bounds__(TB) k_guide_fill(GuideArgs A, uint32_t m)
 {
     const int p = blockIdx.y;
