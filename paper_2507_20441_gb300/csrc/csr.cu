@@ -496,17 +496,32 @@ __global__ void __launch_bounds__(OS_THREADS, 4) k_inv_bucket(const uint32_t *__
     }
 }
 
-// four pairs per thread (16-byte loads; the work arrays are 256-byte aligned)
+// 4 x TM_INV_VECS pairs per thread: TM_INV_VECS 16-byte loads of each work
+// array (256-byte aligned) in flight, at vectors i, i + blockDim, ...
+#ifndef TM_INV_VECS
+#define TM_INV_VECS 1
+#endif
 __global__ void k_inv_fill(const uint32_t *__restrict__ tkey, const uint32_t *__restrict__ tpos, uint32_t n,
                            uint32_t *__restrict__ inv)
 {
-    const uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    if (i + 4 <= n) {
-        const uint4 k = __ldg(reinterpret_cast<const uint4 *>(tkey + i));
-        const uint4 p = __ldg(reinterpret_cast<const uint4 *>(tpos + i));
-        inv[k.x] = p.x; inv[k.y] = p.y; inv[k.z] = p.z; inv[k.w] = p.w;
-    } else {
-        for (uint64_t j = i; j < n; ++j) inv[__ldg(tkey + j)] = __ldg(tpos + j);
+    const uint64_t v0 = (uint64_t)blockIdx.x * blockDim.x * TM_INV_VECS + threadIdx.x;
+    uint4 k[TM_INV_VECS], p[TM_INV_VECS];
+#pragma unroll
+    for (int r = 0; r < TM_INV_VECS; ++r) {
+        const uint64_t i = (v0 + (uint64_t)r * blockDim.x) * 4;
+        if (i + 4 <= n) {
+            k[r] = __ldg(reinterpret_cast<const uint4 *>(tkey + i));
+            p[r] = __ldg(reinterpret_cast<const uint4 *>(tpos + i));
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < TM_INV_VECS; ++r) {
+        const uint64_t i = (v0 + (uint64_t)r * blockDim.x) * 4;
+        if (i + 4 <= n) {
+            inv[k[r].x] = p[r].x; inv[k[r].y] = p[r].y; inv[k[r].z] = p[r].z; inv[k[r].w] = p[r].w;
+        } else {
+            for (uint64_t j = i; j < n; ++j) inv[__ldg(tkey + j)] = __ldg(tpos + j);
+        }
     }
 }
 
@@ -644,8 +659,8 @@ static int inverse_perm(tm_ctx *ctx, const uint32_t *perm, uint32_t n, uint32_t 
     const uint32_t nb = (uint32_t)(((uint64_t)(n - 1) >> shift) + 1);
     launch(ctx, k_inv_cursor, 1, IB_MAXB, cursor, nb, shift);
     launch(ctx, k_inv_bucket, (n + OS_TILE - 1) / OS_TILE, OS_THREADS, perm, n, shift, nb, cursor, tkey, tpos);
-    launch(ctx, k_inv_fill, (unsigned)(((uint64_t)n + 1023) / 1024), 256, (const uint32_t *)tkey, (const uint32_t *)tpos,
-           n, inv);
+    launch(ctx, k_inv_fill, (unsigned)(((uint64_t)n + 1024 * TM_INV_VECS - 1) / (1024 * TM_INV_VECS)), 256,
+           (const uint32_t *)tkey, (const uint32_t *)tpos, n, inv);
     return check_cuda(ctx, cudaGetLastError(), "inverse permutation");
 }
 
@@ -809,6 +824,14 @@ __global__ void k_input_stats(const uint32_t *__restrict__ src, const uint32_t *
     }
 }
 
+// Elementwise kernels below take kElemItems elements per thread (i, i +
+// blockDim, ...): with one element per thread the list offsets kernel
+// measured twice as slow.
+#ifndef TM_ELEM_ITEMS
+#define TM_ELEM_ITEMS 4
+#endif
+constexpr int kElemItems = TM_ELEM_ITEMS;
+
 // keep flags for self-loop dropping
 __global__ void k_keep_nonself(const uint32_t *__restrict__ src, const uint32_t *__restrict__ dst, uint64_t m,
                                uint32_t *__restrict__ keep)
@@ -823,13 +846,17 @@ __global__ void k_compact_input(const uint32_t *__restrict__ src, const uint32_t
                                 const uint32_t *__restrict__ pos, long long tmin, uint32_t *__restrict__ ot,
                                 uint32_t *__restrict__ os, uint32_t *__restrict__ od)
 {
-    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    if (keep && !keep[i]) return;
-    uint32_t p = pos ? pos[i] : (uint32_t)i;
-    ot[p] = (uint32_t)(t[i] - tmin);
-    os[p] = src[i];
-    od[p] = dst[i];
+    const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x * kElemItems + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < kElemItems; ++k) {
+        const uint64_t i = i0 + (uint64_t)k * blockDim.x;
+        if (i >= m) break;
+        if (keep && !keep[i]) continue;
+        const uint32_t p = pos ? pos[i] : (uint32_t)i;
+        ot[p] = (uint32_t)(t[i] - tmin);
+        os[p] = src[i];
+        od[p] = dst[i];
+    }
 }
 
 // After the GLOBAL sort: flag tuples equal to their predecessor.
@@ -841,11 +868,11 @@ __global__ void k_compact_input(const uint32_t *__restrict__ src, const uint32_t
 // is flagged and the caller sorts by all three keys instead.
 constexpr uint32_t kRunMax = 32;
 constexpr uint32_t kBlockRunMax = 4096;
-__global__ void k_order_runs(const uint32_t *__restrict__ t, uint32_t *__restrict__ s, uint32_t *__restrict__ d,
-                             uint32_t m, uint32_t *__restrict__ too_long, uint2 *__restrict__ long_runs,
-                             uint32_t *__restrict__ n_long, unsigned long long *__restrict__ ndup)
+__device__ __forceinline__ void order_run_at(uint32_t i, const uint32_t *__restrict__ t, uint32_t *__restrict__ s,
+                                             uint32_t *__restrict__ d, uint32_t m, uint32_t *__restrict__ too_long,
+                                             uint2 *__restrict__ long_runs, uint32_t *__restrict__ n_long,
+                                             unsigned long long *__restrict__ ndup)
 {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m || (i > 0 && t[i - 1] == t[i])) return;   // run heads only
     const uint32_t ti = t[i];
     uint32_t j = i + 1;
@@ -888,6 +915,19 @@ __global__ void k_order_runs(const uint32_t *__restrict__ t, uint32_t *__restric
         dups += k > 0 && key[k] == key[k - 1];
     }
     if (dups) atomicAdd(ndup, (unsigned long long)dups);
+}
+
+__global__ void k_order_runs(const uint32_t *__restrict__ t, uint32_t *__restrict__ s, uint32_t *__restrict__ d,
+                             uint32_t m, uint32_t *__restrict__ too_long, uint2 *__restrict__ long_runs,
+                             uint32_t *__restrict__ n_long, unsigned long long *__restrict__ ndup)
+{
+    const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x * kElemItems + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < kElemItems; ++k) {
+        const uint64_t i = i0 + (uint64_t)k * blockDim.x;
+        if (i >= m) break;
+        order_run_at((uint32_t)i, t, s, d, m, too_long, long_runs, n_long, ndup);
+    }
 }
 
 // One block per listed run (33 .. kBlockRunMax edges): bitonic sort of the
@@ -963,42 +1003,63 @@ __global__ void k_owner_bits(const uint32_t *__restrict__ out_src, const uint32_
                              uint32_t *__restrict__ own_out, uint32_t *__restrict__ own_in,
                              uint32_t *__restrict__ own_multi)
 {
-    const uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= (uint64_t)words * 32) return;   // whole warps: words * 32 is a multiple of 32
-    const bool in = x < m, first = x == 0;
-    const bool bo = in && (first || out_src[x] != out_src[x - 1]);
-    const bool bi = in && (first || in_dst[x] != in_dst[x - 1]);
-    const bool bm = in && pair_head[x] != 0;
-    const uint32_t wo = __ballot_sync(0xffffffffu, bo), wi = __ballot_sync(0xffffffffu, bi),
-                   wm = __ballot_sync(0xffffffffu, bm);
-    if ((threadIdx.x & 31) == 0) {
-        own_out[x >> 5] = wo;
-        own_in[x >> 5] = wi;
-        own_multi[x >> 5] = wm;
+    const uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x * kElemItems + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < kElemItems; ++k) {
+        // a warp's 32 positions are consecutive and start at a multiple of 32,
+        // and words * 32 is a multiple of 32: whole warps leave together
+        const uint64_t x = x0 + (uint64_t)k * blockDim.x;
+        if (x >= (uint64_t)words * 32) break;
+        const bool in = x < m, first = x == 0;
+        const bool bo = in && (first || out_src[x] != out_src[x - 1]);
+        const bool bi = in && (first || in_dst[x] != in_dst[x - 1]);
+        const bool bm = in && pair_head[x] != 0;
+        const uint32_t wo = __ballot_sync(0xffffffffu, bo), wi = __ballot_sync(0xffffffffu, bi),
+                       wm = __ballot_sync(0xffffffffu, bm);
+        if ((threadIdx.x & 31) == 0) {
+            own_out[x >> 5] = wo;
+            own_in[x >> 5] = wi;
+            own_multi[x >> 5] = wm;
+        }
     }
 }
 
 // off[v] = first position whose sorted key is >= v, for v in [0, n].  With
 // m_dev set, the key count is min(m, *m_dev) (a count known only on the
 // device; m bounds the grid).
+#ifndef TM_OFF_ITEMS
+#define TM_OFF_ITEMS 8   // positions per thread (1: one per thread)
+#endif
 __global__ void k_offsets(const uint32_t *__restrict__ keys, uint32_t m, uint32_t n, uint32_t *__restrict__ off,
                           const uint32_t *__restrict__ m_dev)
 {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    // positions [i0, i0 + TM_OFF_ITEMS) of this thread, the previous key carried
+    const uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * TM_OFF_ITEMS;
     if (m_dev) m = min(m, *m_dev);
-    if (i > m) return;
-    uint32_t lo = (i == 0) ? 0u : keys[i - 1] + 1u;
-    uint32_t hi = (i == m) ? n : keys[i];
-    for (uint32_t v = lo; v <= hi && v <= n; ++v) off[v] = i;
+    if (i0 > m) return;
+    uint32_t prev = i0 == 0 ? 0u : __ldg(keys + i0 - 1) + 1u;
+#pragma unroll
+    for (int j = 0; j < TM_OFF_ITEMS; ++j) {
+        const uint64_t i = i0 + j;
+        if (i > m) break;
+        const uint32_t lo = prev;
+        const uint32_t hi = (i == m) ? n : __ldg(keys + i);
+        for (uint32_t v = lo; v <= hi && v <= n; ++v) off[v] = (uint32_t)i;
+        prev = hi + 1u;
+    }
 }
 
 // Pair heads in the multi-edge order (src from the sorted keys, dst gathered).
 __global__ void k_pair_heads(const uint32_t *__restrict__ msrc, const uint32_t *__restrict__ mdst, uint32_t m,
                              uint32_t *__restrict__ head)
 {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    head[i] = (i == 0 || msrc[i] != msrc[i - 1] || mdst[i] != mdst[i - 1]) ? 1u : 0u;
+    const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x * kElemItems + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < kElemItems; ++k) {
+        const uint64_t i = i0 + (uint64_t)k * blockDim.x;
+        if (i >= m) break;
+        head[i] = (i == 0 || msrc[i] != msrc[i - 1] || mdst[i] != mdst[i - 1]) ? 1u : 0u;
+    }
 }
 
 __global__ void k_pair_fill(const uint32_t *__restrict__ msrc, const uint32_t *__restrict__ mdst,
@@ -1006,15 +1067,19 @@ __global__ void k_pair_fill(const uint32_t *__restrict__ msrc, const uint32_t *_
                             uint32_t *__restrict__ pair_off, uint32_t *__restrict__ pair_src,
                             uint32_t *__restrict__ pair_dst)
 {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    if (head[i]) {
-        const uint32_t pid = pid_excl[i];
-        pair_off[pid] = i;
-        pair_src[pid] = msrc[i];
-        pair_dst[pid] = mdst[i];
+    const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x * kElemItems + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < kElemItems; ++k) {
+        const uint32_t i = (uint32_t)(i0 + (uint64_t)k * blockDim.x);
+        if (i0 + (uint64_t)k * blockDim.x >= m) break;
+        if (head[i]) {
+            const uint32_t pid = pid_excl[i];
+            pair_off[pid] = i;
+            pair_src[pid] = msrc[i];
+            pair_dst[pid] = mdst[i];
+        }
+        if (i == m - 1) pair_off[pid_excl[i] + head[i]] = m;   // the end of the last pair's list
     }
-    if (i == m - 1) pair_off[pid_excl[i] + head[i]] = m;   // the end of the last pair's list
 }
 
 // where each list time falls in the same vertex's other list
@@ -1030,16 +1095,50 @@ struct XR {
 // merging each vertex's two lists along a merge path in chunks of 128 entries
 // per thread (1.44 ms: the chunk walk is one long chain of dependent loads).
 // The independent searches keep the most loads in flight.
+// Each thread runs TM_XR_ITEMS searches (entries i, i + stride, ...) in
+// lockstep, so that many independent probes are in flight per thread.
+#ifndef TM_XR_ITEMS
+#define TM_XR_ITEMS 4
+#endif
 __global__ void k_cross_rank(XR a, XR b, uint32_t m)
 {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
+    constexpr int K = TM_XR_ITEMS;
     const bool s1 = blockIdx.y != 0;
     const uint32_t *own_t = s1 ? b.own_t : a.own_t, *owner = s1 ? b.owner : a.owner;
     const uint32_t *other_off = s1 ? b.other_off : a.other_off, *other_t = s1 ? b.other_t : a.other_t;
     uint32_t *xrank = s1 ? b.xrank : a.xrank;
-    const uint32_t z = __ldg(owner + i);
-    xrank[i] = lower_idx(other_t, __ldg(other_off + z), __ldg(other_off + z + 1), __ldg(own_t + i));
+    const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x * K + threadIdx.x;
+    uint32_t lo[K], len[K], key[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const uint64_t i = i0 + (uint64_t)k * blockDim.x;
+        lo[k] = 0; len[k] = 0; key[k] = 0;
+        if (i < m) {
+            const uint32_t z = __ldg(owner + i);
+            key[k] = __ldg(own_t + i);
+            lo[k] = __ldg(other_off + z);
+            len[k] = __ldg(other_off + z + 1) - lo[k];
+        }
+    }
+    // the binary search of lower_idx, all K at once
+    bool more = true;
+    while (more) {
+        more = false;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (len[k] > 0) {
+                const uint32_t half = len[k] >> 1, mid = lo[k] + half;
+                if (__ldg(other_t + mid) < key[k]) { lo[k] = mid + 1; len[k] -= half + 1; }
+                else len[k] = half;
+                more |= len[k] > 0;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const uint64_t i = i0 + (uint64_t)k * blockDim.x;
+        if (i < m) xrank[i] = lo[k];
+    }
 }
 
 inline unsigned blocks_for(uint64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
@@ -1120,11 +1219,11 @@ int build_csr(tm_ctx *ctx)
         launch(ctx, k_keep_nonself, blocks_for(m0, TB), TB, ctx->in_src, ctx->in_dst, m0, keep);
         rc = exclusive_scan_u32(ctx, keep, pos, m0, nullptr);
         if (rc) return rc;
-        launch(ctx, k_compact_input, blocks_for(m0, TB), TB, ctx->in_src, ctx->in_dst, ctx->in_t, m0, keep, pos, tmin,
-                                                           T0, S0, D0);
+        launch(ctx, k_compact_input, blocks_for((m0 + kElemItems - 1) / kElemItems, TB), TB, ctx->in_src, ctx->in_dst,
+               ctx->in_t, m0, keep, pos, tmin, T0, S0, D0);
     } else if (m) {
-        launch(ctx, k_compact_input, blocks_for(m0, TB), TB, ctx->in_src, ctx->in_dst, ctx->in_t, m0, nullptr, nullptr,
-                                                           tmin, T0, S0, D0);
+        launch(ctx, k_compact_input, blocks_for((m0 + kElemItems - 1) / kElemItems, TB), TB, ctx->in_src, ctx->in_dst,
+               ctx->in_t, m0, nullptr, nullptr, tmin, T0, S0, D0);
     }
     // every m- and n-sized array of the graph in one block, sized before the
     // duplicates are known (they are rare; their slots stay unused)
@@ -1158,7 +1257,8 @@ int build_csr(tm_ctx *ctx)
         if (!keep || !nd || !long_runs) return TM_E_NOMEM;
         cudaMemsetAsync(nd, 0, 24, st);
         if (m) {
-            launch(ctx, k_order_runs, blocks_for(m, TB), TB, (const uint32_t *)g.g_t, g.g_src, g.g_dst, m,
+            launch(ctx, k_order_runs, blocks_for(((uint64_t)m + kElemItems - 1) / kElemItems, TB), TB,
+                   (const uint32_t *)g.g_t, g.g_src, g.g_dst, m,
                    (uint32_t *)(nd + 1), long_runs, (uint32_t *)(nd + 2), nd);
             launch(ctx, k_order_long_runs, (unsigned)ctx->num_sms * 2, 256, g.g_src, g.g_dst, (const uint2 *)long_runs,
                    (const uint32_t *)(nd + 2), nd);
@@ -1234,8 +1334,8 @@ int build_csr(tm_ctx *ctx)
     }
     sec.reset();
     sec.reset(new PhaseScope(ctx, TM_PH_CSR_IN));
-    launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, g.out_src, m, n, g.out_off, nullptr);
-    launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, g.in_dst, m, n, g.in_off, nullptr);
+    launch(ctx, k_offsets, blocks_for(((uint64_t)m + TM_OFF_ITEMS) / TM_OFF_ITEMS, TB), TB, g.out_src, m, n, g.out_off, nullptr);
+    launch(ctx, k_offsets, blocks_for(((uint64_t)m + TM_OFF_ITEMS) / TM_OFF_ITEMS, TB), TB, g.in_dst, m, n, g.in_off, nullptr);
     uint32_t *key = S0, *tmp = D0;
     // ---- multi-edge order: stable re-sort of the IN order by source
     sec.reset();
@@ -1263,7 +1363,7 @@ int build_csr(tm_ctx *ctx)
         uint32_t *pid = (uint32_t *)salloc(ctx, (size_t)m * 4);
         uint32_t *dnp = (uint32_t *)salloc(ctx, 4);
         if (!pid || !dnp) return TM_E_NOMEM;
-        launch(ctx, k_pair_heads, blocks_for(m, TB), TB, key, tmp, m, head);
+        launch(ctx, k_pair_heads, blocks_for(((uint64_t)m + kElemItems - 1) / kElemItems, TB), TB, key, tmp, m, head);
         rc = exclusive_scan_u32(ctx, head, pid, m, dnp);
         if (rc) return rc;
         // dnp = the number of pairs (the scan's total), used on the device;
@@ -1272,16 +1372,19 @@ int build_csr(tm_ctx *ctx)
         g.pair_dst = gtake(gb, m);
         uint32_t *pair_src = (uint32_t *)salloc(ctx, (size_t)m * 4);
         if (!g.pair_off || !g.pair_dst || !pair_src) return TM_E_NOMEM;
-        launch(ctx, k_pair_fill, blocks_for(m, TB), TB, (const uint32_t *)key, (const uint32_t *)tmp,
+        launch(ctx, k_pair_fill, blocks_for(((uint64_t)m + kElemItems - 1) / kElemItems, TB), TB, (const uint32_t *)key,
+               (const uint32_t *)tmp,
                (const uint32_t *)head, (const uint32_t *)pid, m, g.pair_off, pair_src, g.pair_dst);
-        launch(ctx, k_offsets, blocks_for((uint64_t)m + 1, TB), TB, pair_src, m, n, g.vpair_off, (const uint32_t *)dnp);
+        launch(ctx, k_offsets, blocks_for(((uint64_t)m + TM_OFF_ITEMS) / TM_OFF_ITEMS, TB), TB, pair_src, m, n, g.vpair_off, (const uint32_t *)dnp);
         copy_d2h(ctx, ctx->status_host + 1, dnp, 4);   // pinned: read after the closing synchronize
         // cross ranks between a vertex's out- and in-lists
-        launch(ctx, k_cross_rank, dim3(blocks_for(m, TB), 2), TB, XR{g.out_t, g.out_src, g.in_off, g.in_t, g.out_xrank},
+        launch(ctx, k_cross_rank, dim3(blocks_for(((uint64_t)m + TM_XR_ITEMS - 1) / TM_XR_ITEMS, TB), 2), TB,
+               XR{g.out_t, g.out_src, g.in_off, g.in_t, g.out_xrank},
                XR{g.in_t, g.in_dst, g.out_off, g.out_t, g.in_xrank}, m);
         // owner starts of the three orders (segment heads of the weight pass's scans)
         const uint32_t words = m / 32 + 1;
-        launch(ctx, k_owner_bits, blocks_for((uint64_t)words * 32, TB), TB, (const uint32_t *)g.out_src, (const uint32_t *)g.in_dst,
+        launch(ctx, k_owner_bits, blocks_for(((uint64_t)words * 32 + kElemItems - 1) / kElemItems, TB), TB,
+               (const uint32_t *)g.out_src, (const uint32_t *)g.in_dst,
                (const uint32_t *)head, m, words, g.own_out, g.own_in, g.own_multi);
     } else {
         GraphBlock pbk;
