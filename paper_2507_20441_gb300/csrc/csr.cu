@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(OS_THREADS, 4) k_inv_bucket(const uint32_t *__
 // 4 x TM_INV_VECS pairs per thread: TM_INV_VECS 16-byte loads of each work
 // array (256-byte aligned) in flight, at vectors i, i + blockDim, ...
 #ifndef TM_INV_VECS
-#define TM_INV_VECS 1
+#define TM_INV_VECS 1   // 2 and 4 measured no faster
 #endif
 __global__ void k_inv_fill(const uint32_t *__restrict__ tkey, const uint32_t *__restrict__ tpos, uint32_t n,
                            uint32_t *__restrict__ inv)
