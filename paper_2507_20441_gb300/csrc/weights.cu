@@ -584,17 +584,32 @@ __global__ void __launch_bounds__(TB) k_guide_fill(GuideArgs A, uint32_t m)
     }
     int64_t kk = (int64_t)lo - 1;
     const uint64_t xe = min((uint64_t)m, (uint64_t)(xs + 32u * kGuideItems));
-    for (uint64_t xx = xs; xx < xe; xx += 32) {
-        const uint32_t x = (uint32_t)xx;
-        while (kk + 1 < (int64_t)L.nwin && L.win_beg[kk + 1] <= x) ++kk;
-        if (kk < 0) continue;   // before the layer's first window
-        const uint32_t wbeg = L.win_beg[kk], wend = L.win_beg[kk + 1];
-        const uint32_t sh = L.gshift[kk];
-        uint32_t *G = L.guide + L.goff[kk];
-        const uint64_t c1 = L.cdf[x], c0 = x > wbeg ? L.cdf[x - 1] : 0;
-        const uint64_t j1 = ceil_shift(c1, sh);
-        for (uint64_t j = ceil_shift(c0, sh); j < j1; ++j) G[j] = x;
-        if (x == wend - 1) G[j1] = x;
+    // kGuideBatch edges' CDF pairs loaded before any is used (independent
+    // loads in flight), then the edges in order
+    constexpr int kGuideBatch = 4;
+    for (uint64_t xb = xs; xb < xe; xb += 32u * kGuideBatch) {
+        uint64_t c1v[kGuideBatch], c0v[kGuideBatch];
+#pragma unroll
+        for (int u = 0; u < kGuideBatch; ++u) {
+            const uint64_t xx = xb + 32u * u;
+            c1v[u] = xx < xe ? L.cdf[xx] : 0;
+            c0v[u] = (xx < xe && xx > 0) ? L.cdf[xx - 1] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kGuideBatch; ++u) {
+            const uint64_t xx = xb + 32u * u;
+            if (xx >= xe) break;
+            const uint32_t x = (uint32_t)xx;
+            while (kk + 1 < (int64_t)L.nwin && L.win_beg[kk + 1] <= x) ++kk;
+            if (kk < 0) continue;   // before the layer's first window
+            const uint32_t wbeg = L.win_beg[kk], wend = L.win_beg[kk + 1];
+            const uint32_t sh = L.gshift[kk];
+            uint32_t *G = L.guide + L.goff[kk];
+            const uint64_t c1 = c1v[u], c0 = x > wbeg ? c0v[u] : 0;
+            const uint64_t j1 = ceil_shift(c1, sh);
+            for (uint64_t j = ceil_shift(c0, sh); j < j1; ++j) G[j] = x;
+            if (x == wend - 1) G[j1] = x;
+        }
     }
 }
 
