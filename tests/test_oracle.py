@@ -20,7 +20,7 @@ import numpy as np
 import pytest
 
 from conftest import read_golden
-from helpers import SMALL_MOTIFS, small_random_graph, spanning_trees
+from helpers import SMALL_MOTIFS, csr_by_loops, csr_case, small_random_graph, spanning_trees
 
 GOLDEN = sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "*.txt")))
 
@@ -417,55 +417,19 @@ def test_brute_equals_tree_sum_random_motifs(oracle_mod, seed):
                 assert G.exact_by_trees() == 2 * C, (nv, edges, rank, delta, tree, root)
 
 
-@pytest.mark.parametrize("seed,n,m,t_hi", [(1, 12, 300, 40), (2, 7, 90, 3), (3, 30, 500, 1000)])
+CSR_CASES = [(1, 12, 300, 40), (2, 7, 90, 3), (3, 30, 500, 1000)]
+
+
+@pytest.mark.parametrize("seed,n,m,t_hi", CSR_CASES)
 def test_csr_arrays_by_loops(oracle_mod, seed, n, m, t_hi):
     """The oracle's temporal CSR (Defs. 3.1-3.3) against lists built one edge
-    at a time by plain loops over the GLOBAL order: each vertex's out-list is
-    its edges in GLOBAL order, an out entry's cross rank counts the owner's
-    in-edges strictly earlier, and the multi-edge lists group (src, dst)."""
-    rng = np.random.default_rng(seed)
-    s = rng.integers(0, n, m); d = (s + 1 + rng.integers(0, n - 1, m)) % n
-    t = rng.integers(0, t_hi, m) + 5
-    G = oracle_mod.Graph(n, s.astype(np.uint32), d.astype(np.uint32), t.astype(np.int64), flags=oracle_mod.DEDUP)
+    at a time by plain loops over the GLOBAL order (helpers.csr_by_loops)."""
+    G = csr_case(oracle_mod, seed, n, m, t_hi)
     gs, gd, gt = (x.tolist() for x in G.edges())
-    me = len(gs)
     # GLOBAL order is (t', src, dst), strictly increasing after de-duplication
-    assert all((gt[i], gs[i], gd[i]) < (gt[i + 1], gs[i + 1], gd[i + 1]) for i in range(me - 1))
-    c = G.csr()
-    out_lists = [[e for e in range(me) if gs[e] == v] for v in range(n)]
-    in_lists = [[e for e in range(me) if gd[e] == v] for v in range(n)]
-    out_gid = [e for v in range(n) for e in out_lists[v]]
-    in_gid = [e for v in range(n) for e in in_lists[v]]
-    assert c["out_gid"].tolist() == out_gid and c["in_gid"].tolist() == in_gid
-    off_o, off_i = [0], [0]
-    for v in range(n):
-        off_o.append(off_o[-1] + len(out_lists[v])); off_i.append(off_i[-1] + len(in_lists[v]))
-    assert c["out_off"].tolist() == off_o and c["in_off"].tolist() == off_i
-    assert c["out_t"].tolist() == [gt[e] for e in out_gid] and c["out_nbr"].tolist() == [gd[e] for e in out_gid]
-    assert c["in_t"].tolist() == [gt[e] for e in in_gid] and c["in_nbr"].tolist() == [gs[e] for e in in_gid]
-    assert c["out_src"].tolist() == [gs[e] for e in out_gid] and c["in_dst"].tolist() == [gd[e] for e in in_gid]
-    pos_o = {e: x for x, e in enumerate(out_gid)}; pos_i = {e: x for x, e in enumerate(in_gid)}
-    assert c["out_pos"].tolist() == [pos_o[e] for e in range(me)]
-    assert c["in_pos"].tolist() == [pos_i[e] for e in range(me)]
-    assert c["in_to_out"].tolist() == [pos_o[e] for e in in_gid]
-    xo = [off_i[gs[e]] + sum(1 for f in in_lists[gs[e]] if gt[f] < gt[e]) for e in out_gid]
-    xi = [off_o[gd[e]] + sum(1 for f in out_lists[gd[e]] if gt[f] < gt[e]) for e in in_gid]
-    assert c["out_xrank"].tolist() == xo and c["in_xrank"].tolist() == xi
-    pairs = sorted({(gs[e], gd[e]) for e in range(me)})
-    multi = [e for (u, v) in pairs for e in sorted((f for f in range(me) if (gs[f], gd[f]) == (u, v)), key=lambda f: gt[f])]
-    assert c["multi_t"].tolist() == [gt[e] for e in multi]
-    assert c["multi_to_out"].tolist() == [pos_o[e] for e in multi]
-    po = [0]
-    for (u, v) in pairs:
-        po.append(po[-1] + sum(1 for f in range(me) if (gs[f], gd[f]) == (u, v)))
-    assert c["pair_off"].tolist() == po and c["pair_dst"].tolist() == [v for _, v in pairs]
-    assert c["vpair_off"].tolist() == [sum(1 for (u, _) in pairs if u < v) for v in range(n + 1)]
-
-    def words(starts):
-        w = [0] * (me // 32 + 1)
-        for x in starts:
-            w[x // 32] |= 1 << (x % 32)
-        return w
-    assert c["own_out"].tolist() == words(off_o[v] for v in range(n) if out_lists[v])
-    assert c["own_in"].tolist() == words(off_i[v] for v in range(n) if in_lists[v])
-    assert c["own_multi"].tolist() == words(po[:-1])
+    assert all((gt[i], gs[i], gd[i]) < (gt[i + 1], gs[i + 1], gd[i + 1]) for i in range(len(gs) - 1))
+    want = csr_by_loops(n, gs, gd, gt)
+    got = G.csr()
+    assert set(got) == set(want)
+    for name in want:
+        assert got[name].tolist() == want[name], name

@@ -55,3 +55,45 @@ def test_planted_mistake_is_caught(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     assert p.returncode != 0, f"planted mistake {name} was not caught by any pin"
+
+
+# Planted mistakes in the oracle's temporal CSR (oracle.csr_arrays, Python):
+# each must make the loop-built CSR (helpers.csr_by_loops) disagree on at
+# least one of the pin cases of test_oracle.py.
+PY_SRC = os.path.join(ROOT, "oracle", "__init__.py")
+PY_MUTATIONS = {
+    "csr_out_sorted_by_dst": ('out_gid = np.argsort(src, kind="stable")', 'out_gid = np.argsort(dst, kind="stable")'),
+    "csr_multi_time_before_dst": ("multi = np.lexsort((t, dst, src))", "multi = np.lexsort((dst, t, src))"),
+    "csr_xrank_counts_ties": ('"out_xrank": np.searchsorted(in_key, out_key, side="left")',
+                              '"out_xrank": np.searchsorted(in_key, out_key, side="right")'),
+    "csr_in_to_out_wrong_map": ('"in_to_out": out_pos[in_gid]', '"in_to_out": in_pos[in_gid]'),
+    "csr_owner_bits_wrong_owner": ('"own_out": bits(starts(src[out_gid]))', '"own_out": bits(starts(dst[out_gid]))'),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTATIONS))
+def test_planted_csr_mistake_is_caught(name, tmp_path, oracle_mod):
+    import importlib.util
+    from helpers import csr_by_loops, csr_case
+    old, new = PY_MUTATIONS[name]
+    src = open(PY_SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    path = tmp_path / "mutant_oracle.py"
+    path.write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location("mutant_oracle", str(path))
+    mutant = importlib.util.module_from_spec(spec)
+    sys.modules["mutant_oracle"] = mutant   # dataclasses look their module up while it runs
+    try:
+        spec.loader.exec_module(mutant)
+    finally:
+        del sys.modules["mutant_oracle"]
+    caught = False
+    for seed, n, m, t_hi in [(1, 12, 300, 40), (2, 7, 90, 3), (3, 30, 500, 1000)]:
+        G = csr_case(oracle_mod, seed, n, m, t_hi)
+        s, d, t = G.edges()
+        got = mutant.csr_arrays(n, s, d, t)
+        want = csr_by_loops(n, s.tolist(), d.tolist(), t.tolist())
+        if any(got[k].tolist() != want[k] for k in want):
+            caught = True
+            break
+    assert caught, f"planted mistake {name} was not caught by the loop-built CSR"
