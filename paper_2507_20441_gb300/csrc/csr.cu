@@ -6,7 +6,7 @@
 //   in-lists    (dst | t', src)      -> in_off / in_t / in_nbr / in_gid / in_pos / in_to_out
 //   multi-edge  (src, dst | t')      -> pairs, pair_off / pair_dst / multi_t / multi_to_out
 // with t' = t - t_min.  The orderings come from a stable LSD radix sort (up to
-// 9-bit digits, up to four payload arrays) written here.  The GLOBAL order is
+// 7-bit digits, up to four payload arrays) written here.  The GLOBAL order is
 // a sort by t' after which each run of equal t' is put in (src, dst) order in
 // place (one thread, one block, or, for a run of more than 4096 edges, the
 // full three-key sort).  The OUT and IN orders are stable re-sorts of the
@@ -17,7 +17,8 @@
 // (read in GLOBAL order), which is the in -> out map, and the multi-edge
 // order is a stable re-sort of the IN order by source carrying t', the
 // destination and that map (-> multi_to_out).  The random accesses left are
-// the cross ranks, found by binary search in the owner's other list.
+// the cross ranks, found by binary searches in the owner's other list (four
+// per thread in lockstep).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -45,7 +46,7 @@ namespace {
 //      digit's run out contiguously.
 // No block waits on another.
 #ifndef TM_RS_ITEMS
-#define TM_RS_ITEMS 16   // keys per thread (8 and 12 measured slower on 2M and 10M keys)
+#define TM_RS_ITEMS 16   // keys per thread (8 and 12 measured slower)
 #endif
 #ifndef TM_RS_MATCH
 #define TM_RS_MATCH 0    // 1: peers of a digit by one match-any instead of a ballot per digit bit
