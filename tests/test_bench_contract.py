@@ -54,3 +54,27 @@ def test_reference_arm_prints_the_contract_line():
     e = r["e2e"]
     assert e["value"] == r["value"] and e["unit"] == r["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_roofline_traffic_comes_from_a_current_capture(tmp_path, monkeypatch):
+    """The `traffic` of the bench's roofline is read from the committed ncu
+    summary of the dominant kernel only while the kernel's sources are the
+    ones that summary was captured on (their sha256 is recorded in it)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    fam = bench.kernel_family("k_sample_reg<4>")
+    assert fam == "k_sample"
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    # sources looked up under the temporary root: copy the current ones
+    csrc = tmp_path / "paper_2507_20441_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in bench.KERNEL_SOURCES[fam]:
+        (csrc / f).write_bytes(open(os.path.join(ROOT, "paper_2507_20441_gb300", "csrc", f), "rb").read())
+    h = bench.kernel_source_hash(fam)
+    (prof / "k_sample_w.md").write_text(f"x\ntraffic_bytes_per_launch: 1234\nsource_sha256: {h}\n")
+    assert bench.profiled_traffic(fam, "w") == 1234
+    assert bench.profiled_traffic(fam, "other") is None            # no summary for that workload
+    (csrc / bench.KERNEL_SOURCES[fam][0]).write_text("// changed\n")
+    assert bench.profiled_traffic(fam, "w") is None                # sources changed since the capture
